@@ -1,0 +1,404 @@
+"""Benchmark of the fused batched FP64 level-step: 2048 x 2048 cells as 4096 patches of 32 x 32
+(radial pulse, rho = 1, K = 4, MC limiter, transverse corrections, same-level ghost copy and
+device CFL rule; one step = ghost fill + one persistent fused level-step + dt update, each a
+CUDA graph replay).  Prints one JSON line (see the keys below).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl claw|reference]
+
+N > 1 runs under torch.distributed.run, one rank per GPU, each advancing its own replica of
+the workload (the path has no data exchange between independent runs): weak scaling.
+--impl reference times the CPU oracle on the host cores on a bounded sample of the same
+workload (same metric and unit).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64 cell-updates/s fused-batched vs plain per-patch launch; % of HBM peak"
+UNIT = "cell-updates/s"
+N_CELLS = 2048 * 2048
+PATCH = 32
+# FP64 arithmetic of the uniform-medium fused kernel per interior cell update (32 x 32 tile),
+# counted from the kernel source phase by phase (a fused multiply-add counts as 2 flops); the
+# derivation and the cross-check against the profiler's FP64 instruction counters are in
+# the design notes.
+FLOPS_PER_CELL = 82.7
+BYTES_PER_CELL = 48.0     # read q^n (p, u, v) + write q^{n+1}: algorithmic HBM traffic
+# FP64 peak of the part: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.index = str(device)
+        try:   # nvidia-smi numbering may differ from CUDA's: address the GPU by its UUID
+            import torch
+            u = str(torch.cuda.get_device_properties(device).uuid)
+            self.index = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+def _oracle_chunk(args):
+    """oracle steps of a chunk of filled 32 x 32 patches (runs in a spawned worker)"""
+    import numpy as np
+
+    import oracle
+    patches, dx, dt = args
+    ones = np.ones((PATCH + 4, PATCH + 4))
+    for qb in patches:
+        oracle.step(qb, ones, 4.0 * ones, dx, dx, dt)
+    return len(patches)
+
+
+def oracle_sample(npatch: int):
+    """the first `npatch` patches of the workload with their ghosts filled (host only)"""
+    import numpy as np
+
+    from paper_1808_02638_gb300 import inputs
+    run = inputs.config1()
+    lev = run.levels[0]
+    glob = np.ones((3, 2048 + 4, 2048 + 4))
+    x = run.xlo + (np.arange(-2, 2048 + 2) + 0.5) * lev.dx
+    X, Y = np.meshgrid(x, x)
+    glob[0] = inputs.radial_pulse(np.clip(X, x[2], x[-3]), np.clip(Y, x[2], x[-3]))
+    glob[1:] = 0.0
+    # patches spread evenly over the domain (the ring and the quiet background alike)
+    stride = max(1, len(lev.boxes) // max(1, npatch))
+    out = []
+    for nb in range(0, len(lev.boxes), stride):
+        ilo, jlo = int(lev.boxes[nb][0]), int(lev.boxes[nb][1])
+        out.append(np.ascontiguousarray(glob[:, jlo:jlo + PATCH + 4, ilo:ilo + PATCH + 4]))
+        if len(out) == npatch:
+            break
+    return out, lev.dx, 0.9 * lev.dx / 2.0
+
+
+def time_oracle(npatch: int, workers: int, reps: int = 1):
+    """wall time of the oracle on `npatch` patches with `workers` spawned processes"""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    patches, dx, dt = oracle_sample(npatch)
+    chunks = [patches[k::workers] for k in range(workers)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_chunk, [(c[:1], dx, dt) for c in chunks])   # warm the workers
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_chunk, [(c, dx, dt) for c in chunks])
+            times.append(time.perf_counter() - t0)
+    return len(patches) * PATCH * PATCH, times
+
+
+def cpu_baseline(target_s: float = 15.0):
+    workers = os.cpu_count() or 1
+    # calibrate on a small sample, then size the sample to ~target_s of wall time
+    cells, t = time_oracle(8 * workers, workers)
+    rate = cells / max(t[0], 1e-9)
+    npatch = int(min(4096, max(workers, rate * target_s / (PATCH * PATCH))))
+    cells, t = time_oracle(npatch, workers)
+    return {"value": cells / t[0], "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"one level-step of {npatch} of the 4096 32x32 patches (ghosts filled), "
+                      f"{workers} spawned worker processes running the single-threaded C oracle, "
+                      f"{t[0]:.1f} s wall"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    workers = os.cpu_count() or 1
+    cells, t = time_oracle(8 * workers, workers)
+    rate = cells / max(t[0], 1e-9)
+    # each step: a bounded sample sized so that warmup + steps stay within ~2 minutes
+    per_step_s = min(10.0, 120.0 / max(1, args.steps + args.warmup))
+    npatch = int(min(4096, max(workers, rate * per_step_s / (PATCH * PATCH))))
+    _, tw = time_oracle(npatch, workers, reps=args.warmup)
+    cells, ts = time_oracle(npatch, workers, reps=args.steps)
+    total = sum(ts)
+    value = cells * len(ts) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "2048x2048 radial pulse as 4096 32x32 patches, rho=1, K=4, MC, "
+                                   "transverse on, one level-step per step (bounded sample)",
+                       "parallelism": f"{workers} host processes"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": f"{npatch} of the 4096 patches per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU leg
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="claw", choices=["claw", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1808_02638_gb300 import claw, inputs
+    from paper_1808_02638_gb300.build import build
+    from paper_1808_02638_gb300.solver import Hierarchy
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    build()   # no-op once built
+
+    run = inputs.config1()
+    lev = run.levels[0]
+    q0 = inputs.init_q(run, lev)
+    H = Hierarchy([run], [[q0]], rho0=1.0, K0=4.0, device=local)
+    H.init_dt()
+    stream = torch.cuda.current_stream()
+    ctx = H.ctx
+    launches0 = claw.claw_launch_count(ctx)
+    H.coarse_step()
+    per_step_launches = claw.claw_launch_count(ctx) - launches0
+    H.coarse_step()
+    torch.cuda.synchronize()
+
+    # one graph per kernel stage and buffer parity: [fill] [fused step] [dt update]
+    def capture(fn):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            fn(s)
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+    graphs = []
+    for parity in range(2):
+        c = H.cur[0]
+        qa, qb = H.q[0][c], H.q[0][1 - c]
+        gf = capture(lambda s, qa=qa: claw.claw_fill_ghost(ctx, 0, qa, None, None, 0.0, s))
+        gs = capture(lambda s, qa=qa, qb=qb: claw.claw_level_step(ctx, 0, qa, qb, None, H.dt, H.smax, s))
+        gd = capture(lambda s: claw.claw_dt_update(ctx, 0, H.smax, H.dt, s))
+        graphs.append((gf, gs, gd))
+        H.cur[0] ^= 1   # the next parity starts from the other buffer
+    # H.cur is back to its value before the loop
+
+    def one_step(k, ev=None):
+        gf, gs, gd = graphs[k & 1]
+        gf.replay()
+        if ev is not None:
+            ev[0].record()
+        gs.replay()
+        if ev is not None:
+            ev[1].record()
+        gd.replay()
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record()
+    for k in range(K):
+        one_step(args.warmup + k, evs[k])
+    end.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = start.elapsed_time(end)
+    kern_ms = [a.elapsed_time(b) for a, b in evs]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    status = H.sync_status()
+    value = world * K * N_CELLS / (total_ms * 1e-3)
+    kern_avg_s = statistics.mean(kern_ms) * 1e-3
+
+    # plain path: one launch per patch (4096 launches per level-step), eager, same stream
+    plain = None
+    if args.plain_steps > 0:
+        H.patchwise = True
+        H.coarse_step()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record()
+        for _ in range(args.plain_steps):
+            H.coarse_step()
+        p1.record()
+        torch.cuda.synchronize()
+        H.patchwise = False
+        pv = args.plain_steps * N_CELLS / (p0.elapsed_time(p1) * 1e-3)
+        plain = {"value": pv, "unit": UNIT, "launches_per_step": len(lev.boxes) + 2,
+                 "fused_over_plain": value / world / pv}
+
+    # end to end: the state lives on the host (pinned); every step copies q in, runs the
+    # level-step through the C ABI and copies q^{n+1} back
+    e2e_steps = max(3, min(20, K // 4))
+    qbytes = H.q[0][0].numel() * 8
+    host_in = torch.empty_like(H.q[0][0], device="cpu").pin_memory()
+    host_in.copy_(H.q[0][H.cur[0]])
+    host_out = torch.empty_like(host_in).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(e2e_steps):
+        H.q[0][H.cur[0]].copy_(host_in, non_blocking=True)
+        H.coarse_step()
+        host_out.copy_(H.q[0][H.cur[0]], non_blocking=True)
+        host_in, host_out = host_out, host_in
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_value = world * e2e_steps * N_CELLS / (e0.elapsed_time(e1) * 1e-3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved_tflops = FLOPS_PER_CELL * N_CELLS / kern_avg_s / 1e12
+    achieved_gbs = BYTES_PER_CELL * N_CELLS / kern_avg_s / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "step_uniform_2048x2048_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2048x2048 cells on [-1,1]^2 as 4096 patches of 32x32 (+2 ghost layers), "
+                               "radial pulse, rho=1, K=4, MC limiter, transverse corrections, same-level "
+                               "ghost copy, device CFL rule, one fused persistent launch per step "
+                               "under CUDA graphs",
+                   "global_batch": world * N_CELLS, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (254 MB of q pools per replica)"},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "fused level-step (uniform medium, MC, 32x32 tiles, tensor bulk-copy staging)",
+                     "kernel_ms": kern_avg_s * 1e3,
+                     "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz (derived)"},
+        "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm, "frac": achieved_gbs / hbm,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+        "plain_per_patch": plain,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes},
+        "gpu_launches": per_step_launches * K,
+        "clocks": clocks,
+        "status": claw.strerror(status),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * claw.h -- C ABI of libclaw.so: the wave-propagation level-step of Qin, LeVeque & Motley,
+ * "Accelerating wave-propagation algorithms with adaptive mesh refinement using the GPU"
+ * (arXiv:1808.02638), as hand-written CUDA kernels for sm_103a (GB300).
+ *
+ * Problem (Sec. 4.1): linear acoustics q_t + A q_x + B q_y = 0, q = (p, u, v), with cell-wise
+ * density rho and bulk modulus K (c = sqrt(K/rho), impedance Z = rho c).  Each level-step is
+ * the unsplit wave-propagation update of Eq. wave_form_2d_2nd_order applied to every patch of
+ * an AMR level (Sec. 2.2), with limited second-order corrections and transverse propagation.
+ *
+ * Conventions shared by every entry point
+ *   - Storage: a box (patch) with an nx x ny interior has CLAW_MBC = 2 ghost layers and is
+ *     stored as planes of (nx+4) x (ny+4) doubles, x fastest.  A q pool holds, for box b,
+ *     the planes p, u, v back to back starting at element qoff[b].  One-plane pools (rho, K)
+ *     hold box b at element coff[b]; an aux pool holds CLAW_NAUX planes for box b starting
+ *     at element CLAW_NAUX * coff[b].  Offsets must be even (16-byte aligned rows) and nx
+ *     even; the pools are allocated and owned by the caller.
+ *   - All pointers to pools and to the dt / smax scalars are DEVICE pointers on the context's
+ *     device.  The library owns only its own tables, allocated in claw_set_level.
+ *   - Every call that takes a stream enqueues work on it and returns without waiting; it
+ *     launches no kernel when it returns an error.  Calls on one context are not thread-safe.
+ *   - Errors are status codes (never aborts or traps).  Errors found on the device (NaN or
+ *     Inf in a new state, a CFL number above 1, a bounded wait that expired) are recorded in
+ *     a device flag and reported by claw_sync_status.
+ */
+#ifndef CLAW_H
+#define CLAW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CLAW_OK 0
+#define CLAW_EINVAL 1   /* bad argument, bad box set (overlap, outside the domain, not nested)  */
+#define CLAW_ECUDA 2    /* a CUDA runtime call failed                                          */
+#define CLAW_ENOMEM 3   /* device or host allocation failed                                    */
+#define CLAW_ECFL 4     /* a level-step ran with a CFL number above 1 (Sec. 2.4)                */
+#define CLAW_ENAN 5     /* a new state held NaN or Inf                                         */
+#define CLAW_ETIMEOUT 6 /* a bounded device wait expired                                      */
+#define CLAW_ESTATE 7   /* call out of order (e.g. level L set before level L-1)               */
+
+#define CLAW_MBC 2
+#define CLAW_MAXLEV 8
+#define CLAW_NAUX 10
+
+/* limiter ids: phi(theta) of the waves (Sec. 2.1; the benchmark of Sec. 4.1 uses van Leer) */
+#define CLAW_LIM_NONE 0
+#define CLAW_LIM_MINMOD 1
+#define CLAW_LIM_SUPERBEE 2
+#define CLAW_LIM_VANLEER 3
+#define CLAW_LIM_MC 4
+
+/* physical boundary conditions (Sec. 2.2 item 1; the benchmark uses outflow = extrapolation) */
+#define CLAW_BC_EXTRAP 0
+#define CLAW_BC_PERIODIC 1
+#define CLAW_BC_WALL 2
+
+typedef struct claw_ctx claw_ctx;
+
+/* One independent problem (a "run").  Level 0 covers [xlo,xhi] x [ylo,yhi] with nx0 x ny0
+ * cells; level L > 0 is ratio[L] times finer than level L-1 in x, y and t (Sec. 2.2). */
+typedef struct claw_problem {
+    double xlo, ylo, xhi, yhi;
+    int32_t nx0, ny0;
+    int32_t nlev;
+    int32_t ratio[CLAW_MAXLEV];  /* ratio[0] is ignored */
+    double cfl;                  /* desired CFL number nu_desired of Eq. cfl */
+    int32_t limiter;             /* CLAW_LIM_* */
+    int32_t order;               /* 1: first order, 2: with the correction fluxes */
+    int32_t transverse;          /* 0 none, 1 fluctuations, 2 fluctuations and corrections */
+    int32_t bc[4];               /* x-low, x-high, y-low, y-high: CLAW_BC_* */
+    int32_t medium;              /* 0: uniform rho0, K0; 1: cell-wise (aux pools) */
+    double rho0, K0;
+} claw_problem;
+
+/* A box of a level in that level's index space [0, NX_L) x [0, NY_L) of run `run`. */
+typedef struct claw_box {
+    int32_t run;
+    int32_t ilo, jlo, nx, ny;
+    int32_t reserved;
+    int64_t qoff;   /* element offset of the box's p plane in the level's q pool */
+    int64_t coff;   /* element offset of the box's plane in one-plane pools */
+} claw_box;
+
+/* Creates a context for nruns problems on CUDA device `device`.  All runs must share
+ * limiter, order, transverse and medium.  Returns CLAW_OK and sets *out, or an error. */
+int claw_create(claw_ctx** out, const claw_problem* runs, int32_t nruns, int32_t device);
+
+/* Frees the context and its device tables (synchronises the device first). */
+void claw_destroy(claw_ctx* ctx);
+
+/* Declares the boxes of level `level` of all runs (Sec. 2.2: disjoint boxes, nested in level
+ * level-1, aligned to its cells).  Validates them on the host, builds and uploads the patch,
+ * tile, ghost-source and averaging tables.  Levels must be set in increasing order; setting a
+ * level again replaces its tables (and invalidates the tables of finer levels).
+ * Errors: CLAW_EINVAL (overlap, out of domain, misaligned, improper nesting, odd nx/offset),
+ * CLAW_ESTATE (level-1 not set), CLAW_ENOMEM, CLAW_ECUDA.  Synchronous. */
+int claw_set_level(claw_ctx* ctx, int32_t level, const claw_box* boxes, int32_t nboxes);
+
+/* Chooses the tile of the fused level-step for a level: tx x ty interior cells per tile
+ * (tx, ty in {16, 32, 64}, tx*ty <= 2048) and the staging of the tile's q planes into shared
+ * memory (0 = cooperative loads, 1 = tensor-memory-accelerator bulk copies).  claw_set_level
+ * installs 32 x 32 with staging 1.  Errors: CLAW_EINVAL. */
+int claw_set_tiling(claw_ctx* ctx, int32_t level, int32_t tx, int32_t ty, int32_t staging);
+
+/* Per-cell coefficient planes for medium = 1 from one-plane pools rho, K (ghosts included):
+ * aux holds, for every cell, Z = sqrt(K rho), c = sqrt(K/rho), K, c^2, 1/(Z_W+Z) and the
+ * two wave-limiter projection factors of the edge to the west, and the same three for the
+ * edge to the south.  Enqueued on `stream`.  Errors: CLAW_EINVAL, CLAW_ECUDA. */
+int claw_medium_aux(claw_ctx* ctx, int32_t level, const double* rho, const double* K, double* aux,
+                    void* stream);
+
+/* Ghost cells of every box of `level` in q (Sec. 2.2): a ghost takes the value at its image
+ * under the physical boundary of the domain, where a cell inside the domain is the box's own
+ * interior, another box of the level, or (level > 0) the space-time interpolation of the
+ * coarser level: (1-tau) qc_old + tau qc_new followed by minmod-limited linear
+ * reconstruction in space.  qc_old / qc_new may be NULL for level 0.  Errors: CLAW_EINVAL,
+ * CLAW_ESTATE, CLAW_ECUDA. */
+int claw_fill_ghost(claw_ctx* ctx, int32_t level, double* q, const double* qc_old,
+                    const double* qc_new, double tau, void* stream);
+
+/* smax[run] = max(smax[run], max c over the cells next to the edges a level-step of `level`
+ * solves: the ring [-1, nx] x [-1, ny] of every box), for the first time step (Eq. cfl).
+ * aux may be NULL for medium = 0.  smax has one entry per run (zero it before the first use;
+ * claw_dt_update resets it). */
+int claw_cfl_max(claw_ctx* ctx, int32_t level, const double* aux, double* smax, void* stream);
+
+/* Eq. cfl on the device, per run r, with dx, dy of level `level` (normally 0): checks that the
+ * step just taken with dt[r] kept smax[r] * dt[r] / min(dx, dy) <= 1 (else the device flag
+ * records CLAW_ECFL), sets dt[r] = cfl * min(dx, dy) / smax[r] and resets smax[r] to 0.
+ * Because every level's time step is the level-0 step over the product of the ratios, the
+ * CFL number is the same on every level, so one dt per run serves the whole hierarchy. */
+int claw_dt_update(claw_ctx* ctx, int32_t level, double* smax, double* dt, void* stream);
+
+/* One level-step of every box of `level` (Eq. wave_form_2d_2nd_order) in one persistent
+ * fused launch: q_new interior = step(q_old with filled ghosts).  dt[r] is the level-0 time
+ * step of run r; level L advances by dt[r] / (ratio[1] ... ratio[L]) (Sec. 2.2: a level R_L
+ * times finer takes R_L times smaller steps).  The largest wave speed seen is
+ * max-accumulated into smax[r].  Only
+ * interior cells of q_new are written.  aux may be NULL for medium = 0.  q_old and q_new must
+ * not overlap.  Errors: CLAW_EINVAL, CLAW_ESTATE, CLAW_ECUDA. */
+int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
+                    const double* aux, const double* dt, double* smax, void* stream);
+
+/* The same step with one kernel launch per box (the per-patch launch pattern of Sec. 3.1.2,
+ * kept as the comparison baseline of the fused launch). */
+int claw_level_step_patchwise(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
+                              const double* aux, const double* dt, double* smax, void* stream);
+
+/* Coarse cells of level fine_level-1 covered by level fine_level := mean of their ratio^2
+ * fine cells (the "updating" of Sec. 2.2-2.3). */
+int claw_average_down(claw_ctx* ctx, int32_t fine_level, const double* q_fine, double* q_coarse,
+                      void* stream);
+
+/* Reverse mode of claw_level_step for a frozen dt (dt as in claw_level_step): given
+ * lam_new, the adjoint of q_new (interior cells read), accumulates (+=) the adjoint of q_old
+ * over all cells, ghosts included, into lam_old and the adjoint of the aux planes into g_aux
+ * (medium = 1; may be NULL for medium = 0).  The limiter branches of the forward step are
+ * recomputed from q_old.  lam_old and g_aux must be zeroed by the caller before the first
+ * accumulation. */
+int claw_level_step_adjoint(claw_ctx* ctx, int32_t level, const double* q_old, const double* lam_new,
+                            double* lam_old, const double* aux, double* g_aux, const double* dt,
+                            void* stream);
+
+/* Reverse of claw_fill_ghost: every ghost adjoint of lam is added to the adjoint of its
+ * source (a box interior of the level, or through the interpolation to lam_c_old /
+ * lam_c_new, which may be NULL for level 0) and set to zero.  qc_old / qc_new are the coarse
+ * states the forward fill read (for the minmod branches). */
+int claw_fill_ghost_adjoint(claw_ctx* ctx, int32_t level, double* lam, double* lam_c_old,
+                            double* lam_c_new, const double* qc_old, const double* qc_new,
+                            double tau, void* stream);
+
+/* Reverse of claw_average_down: lam_f += (1/ratio^2) lam_c on the children, lam_c := 0 on the
+ * covered coarse cells. */
+int claw_average_down_adjoint(claw_ctx* ctx, int32_t fine_level, double* lam_fine,
+                              double* lam_coarse, void* stream);
+
+/* Chain rule from the aux planes to rho and K: g_rho += d aux/d rho . g_aux, same for K. */
+int claw_medium_aux_adjoint(claw_ctx* ctx, int32_t level, const double* rho, const double* K,
+                            const double* g_aux, double* g_rho, double* g_K, void* stream);
+
+/* Waits for the context's device work, returns and clears the first device-side error
+ * (CLAW_ENAN, CLAW_ECFL, CLAW_ETIMEOUT) or CLAW_OK. */
+int claw_sync_status(claw_ctx* ctx);
+
+/* Kernels of the library launched so far (every entry point counts its launches). */
+int64_t claw_launch_count(claw_ctx* ctx);
+
+const char* claw_strerror(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

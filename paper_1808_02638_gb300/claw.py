@@ -1,0 +1,194 @@
+"""ctypes binding of libclaw.so (include/claw.h): the same entry points, with torch tensors
+(device memory) and torch streams marshalled to pointers.  Every step of the level-step path
+runs in the library's CUDA kernels; this module only converts arguments and raises
+:class:`ClawError` on a non-zero status.  Loading fails loudly when the library is missing or
+no CUDA device is present: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libclaw.so")
+
+CLAW_OK, CLAW_EINVAL, CLAW_ECUDA, CLAW_ENOMEM, CLAW_ECFL, CLAW_ENAN, CLAW_ETIMEOUT, CLAW_ESTATE = range(8)
+CLAW_MBC = 2
+CLAW_MAXLEV = 8
+CLAW_NAUX = 10
+LIMITERS = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
+
+
+class ClawError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn}: {strerror(status)} (status {status})")
+
+
+class claw_problem(ctypes.Structure):
+    _fields_ = [("xlo", ctypes.c_double), ("ylo", ctypes.c_double), ("xhi", ctypes.c_double),
+                ("yhi", ctypes.c_double), ("nx0", ctypes.c_int32), ("ny0", ctypes.c_int32),
+                ("nlev", ctypes.c_int32), ("ratio", ctypes.c_int32 * CLAW_MAXLEV),
+                ("cfl", ctypes.c_double), ("limiter", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("transverse", ctypes.c_int32), ("bc", ctypes.c_int32 * 4), ("medium", ctypes.c_int32),
+                ("rho0", ctypes.c_double), ("K0", ctypes.c_double)]
+
+
+class claw_box(ctypes.Structure):
+    _fields_ = [("run", ctypes.c_int32), ("ilo", ctypes.c_int32), ("jlo", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("qoff", ctypes.c_int64), ("coff", ctypes.c_int64)]
+
+
+_lib = None
+VP = ctypes.c_void_p
+I32 = ctypes.c_int32
+DBL = ctypes.c_double
+
+_SIGNATURES = {
+    "claw_create": ([ctypes.POINTER(VP), ctypes.POINTER(claw_problem), I32, I32], ctypes.c_int),
+    "claw_destroy": ([VP], None),
+    "claw_set_level": ([VP, I32, ctypes.POINTER(claw_box), I32], ctypes.c_int),
+    "claw_set_tiling": ([VP, I32, I32, I32, I32], ctypes.c_int),
+    "claw_medium_aux": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
+    "claw_medium_aux_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_fill_ghost": ([VP, I32, VP, VP, VP, DBL, VP], ctypes.c_int),
+    "claw_fill_ghost_adjoint": ([VP, I32, VP, VP, VP, VP, VP, DBL, VP], ctypes.c_int),
+    "claw_cfl_max": ([VP, I32, VP, VP, VP], ctypes.c_int),
+    "claw_dt_update": ([VP, I32, VP, VP, VP], ctypes.c_int),
+    "claw_level_step": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_level_step_patchwise": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_average_down": ([VP, I32, VP, VP, VP], ctypes.c_int),
+    "claw_average_down_adjoint": ([VP, I32, VP, VP, VP], ctypes.c_int),
+    "claw_level_step_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_sync_status": ([VP], ctypes.c_int),
+    "claw_launch_count": ([VP], ctypes.c_int64),
+    "claw_strerror": ([I32], ctypes.c_char_p),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libclaw.so (built by paper_1808_02638_gb300.build) and declare its signatures."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1808_02638_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return load().claw_strerror(int(status)).decode()
+
+
+def _check(fn: str, status: int):
+    if status != CLAW_OK:
+        raise ClawError(fn, status)
+
+
+def _ptr(t):
+    """device pointer of a torch tensor (or None)"""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("libclaw takes device tensors")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+# ------------------------------------------------------------------ entry points
+
+def claw_create(runs, device: int = 0):
+    arr = (claw_problem * len(runs))(*runs)
+    h = VP()
+    _check("claw_create", load().claw_create(ctypes.byref(h), arr, len(runs), device))
+    return h
+
+
+def claw_destroy(ctx):
+    load().claw_destroy(ctx)
+
+
+def claw_set_level(ctx, level: int, boxes):
+    arr = (claw_box * max(1, len(boxes)))(*boxes)
+    _check("claw_set_level", load().claw_set_level(ctx, level, arr, len(boxes)))
+
+
+def claw_set_tiling(ctx, level: int, tx: int, ty: int, staging: int):
+    _check("claw_set_tiling", load().claw_set_tiling(ctx, level, tx, ty, staging))
+
+
+def claw_medium_aux(ctx, level, rho, K, aux, stream=None):
+    _check("claw_medium_aux", load().claw_medium_aux(ctx, level, _ptr(rho), _ptr(K), _ptr(aux), _stream(stream)))
+
+
+def claw_medium_aux_adjoint(ctx, level, rho, K, g_aux, g_rho, g_K, stream=None):
+    _check("claw_medium_aux_adjoint", load().claw_medium_aux_adjoint(
+        ctx, level, _ptr(rho), _ptr(K), _ptr(g_aux), _ptr(g_rho), _ptr(g_K), _stream(stream)))
+
+
+def claw_fill_ghost(ctx, level, q, qc_old=None, qc_new=None, tau=0.0, stream=None):
+    _check("claw_fill_ghost", load().claw_fill_ghost(ctx, level, _ptr(q), _ptr(qc_old), _ptr(qc_new),
+                                                     float(tau), _stream(stream)))
+
+
+def claw_fill_ghost_adjoint(ctx, level, lam, lam_c_old=None, lam_c_new=None, qc_old=None, qc_new=None,
+                            tau=0.0, stream=None):
+    _check("claw_fill_ghost_adjoint", load().claw_fill_ghost_adjoint(
+        ctx, level, _ptr(lam), _ptr(lam_c_old), _ptr(lam_c_new), _ptr(qc_old), _ptr(qc_new), float(tau),
+        _stream(stream)))
+
+
+def claw_cfl_max(ctx, level, aux, smax, stream=None):
+    _check("claw_cfl_max", load().claw_cfl_max(ctx, level, _ptr(aux), _ptr(smax), _stream(stream)))
+
+
+def claw_dt_update(ctx, level, smax, dt, stream=None):
+    _check("claw_dt_update", load().claw_dt_update(ctx, level, _ptr(smax), _ptr(dt), _stream(stream)))
+
+
+def claw_level_step(ctx, level, q_old, q_new, aux, dt, smax, stream=None):
+    _check("claw_level_step", load().claw_level_step(ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt),
+                                                     _ptr(smax), _stream(stream)))
+
+
+def claw_level_step_patchwise(ctx, level, q_old, q_new, aux, dt, smax, stream=None):
+    _check("claw_level_step_patchwise", load().claw_level_step_patchwise(
+        ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax), _stream(stream)))
+
+
+def claw_average_down(ctx, fine_level, q_fine, q_coarse, stream=None):
+    _check("claw_average_down", load().claw_average_down(ctx, fine_level, _ptr(q_fine), _ptr(q_coarse),
+                                                         _stream(stream)))
+
+
+def claw_average_down_adjoint(ctx, fine_level, lam_fine, lam_coarse, stream=None):
+    _check("claw_average_down_adjoint", load().claw_average_down_adjoint(
+        ctx, fine_level, _ptr(lam_fine), _ptr(lam_coarse), _stream(stream)))
+
+
+def claw_level_step_adjoint(ctx, level, q_old, lam_new, lam_old, aux, g_aux, dt, stream=None):
+    _check("claw_level_step_adjoint", load().claw_level_step_adjoint(
+        ctx, level, _ptr(q_old), _ptr(lam_new), _ptr(lam_old), _ptr(aux), _ptr(g_aux), _ptr(dt),
+        _stream(stream)))
+
+
+def claw_sync_status(ctx) -> int:
+    return int(load().claw_sync_status(ctx))
+
+
+def claw_launch_count(ctx) -> int:
+    return int(load().claw_launch_count(ctx))

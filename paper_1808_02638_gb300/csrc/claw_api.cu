@@ -1,0 +1,862 @@
+// claw_api.cu -- the C ABI of libclaw.so (include/claw.h): context, host-side validation of
+// the box sets of Sec. 2.2, the task tables of the ghost fill (Sec. 2.2 items 1-3) and of the
+// averaging (Sec. 2.3), tensor-map descriptors for the staged tiles, and the launches.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "claw_internal.h"
+
+using namespace claw;
+
+struct TmapCache {
+    const double* q = nullptr;
+    int tx = 0, ty = 0;
+    void* dev = nullptr;   // CUtensorMap[nboxes]
+    unsigned long long stamp = 0;
+};
+
+struct claw_ctx {
+    int device = 0;
+    int nsm = 0;
+    int nruns = 0;
+    std::vector<claw_problem> runs;
+    int limiter = 4, order = 2, transverse = 2, medium = 0;
+    double rho0 = 1, K0 = 1;
+    LevelDev lev[CLAW_MAXLEV];
+    bool set[CLAW_MAXLEV] = {};
+    // device scalars
+    int* err = nullptr;
+    double* minh = nullptr;    // [CLAW_MAXLEV][nruns] min(dx, dy) of each level
+    double* cflv = nullptr;    // [nruns] desired CFL
+    // per-level tiles ordered by box for the per-box launches
+    std::vector<int> ptile_start[CLAW_MAXLEV];
+    TileDev* ptiles[CLAW_MAXLEV] = {};
+    std::vector<TmapCache> tmaps[CLAW_MAXLEV];
+    unsigned long long stamp = 0;
+    std::atomic<long long> launches{0};
+    bool tma_ok[CLAW_MAXLEV] = {};
+};
+
+namespace {
+
+struct DevGuard {   // makes the context's device current for the scope of a call
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int level_nx(const claw_problem& p, int L)
+{
+    long long n = p.nx0;
+    for (int l = 1; l <= L; ++l) n *= p.ratio[l];
+    return (int)n;
+}
+int level_ny(const claw_problem& p, int L)
+{
+    long long n = p.ny0;
+    for (int l = 1; l <= L; ++l) n *= p.ratio[l];
+    return (int)n;
+}
+double level_dx(const claw_problem& p, int L) { return (p.xhi - p.xlo) / level_nx(p, L); }
+double level_dy(const claw_problem& p, int L) { return (p.yhi - p.ylo) / level_ny(p, L); }
+
+// physical-boundary image of index k on [0, n): clamp (extrapolation), wrap (periodic),
+// mirror with the normal velocity negated (wall)
+int bc_map(int k, int n, int bclo, int bchi, int* flip)
+{
+    *flip = 0;
+    if (k < 0) {
+        if (bclo == CLAW_BC_PERIODIC) return ((k % n) + n) % n;
+        if (bclo == CLAW_BC_WALL) { *flip = 1; return -1 - k; }
+        return 0;
+    }
+    if (k >= n) {
+        if (bchi == CLAW_BC_PERIODIC) return k % n;
+        if (bchi == CLAW_BC_WALL) { *flip = 1; return 2 * n - 1 - k; }
+        return n - 1;
+    }
+    return k;
+}
+
+int floordiv(int a, int r) { return a >= 0 ? a / r : -((-a + r - 1) / r); }
+
+// boxes of one (run, level), bucketed for point lookups
+struct Locator {
+    static constexpr int B = 16;
+    std::unordered_map<long long, std::vector<int>> buckets;
+    const std::vector<claw_box>* boxes = nullptr;
+    std::vector<int> idx;   // global box index of each entry
+
+    static long long key(int bi, int bj) { return ((long long)bi << 32) ^ (unsigned)bj; }
+
+    void add(const claw_box& b, int n)
+    {
+        for (int bj = floordiv(b.jlo, B); bj <= floordiv(b.jlo + b.ny - 1, B); ++bj)
+            for (int bi = floordiv(b.ilo, B); bi <= floordiv(b.ilo + b.nx - 1, B); ++bi)
+                buckets[key(bi, bj)].push_back(n);
+    }
+    int find(int i, int j) const
+    {
+        auto it = buckets.find(key(floordiv(i, B), floordiv(j, B)));
+        if (it == buckets.end()) return -1;
+        for (int n : it->second) {
+            const claw_box& b = (*boxes)[n];
+            if (i >= b.ilo && i < b.ilo + b.nx && j >= b.jlo && j < b.jlo + b.ny) return n;
+        }
+        return -1;
+    }
+};
+
+long long cell_off(const claw_box& b, int i, int j)   // plane-0 element of level cell (i, j)
+{
+    return b.qoff + (long long)(j - b.jlo + CLAW_MBC) * (b.nx + 2 * CLAW_MBC) + (i - b.ilo + CLAW_MBC);
+}
+long long plane_of(const claw_box& b) { return (long long)(b.nx + 4) * (b.ny + 4); }
+
+template <class T>
+int upload(T** dst, const std::vector<T>& v)
+{
+    if (*dst) {
+        cudaFree(*dst);
+        *dst = nullptr;
+    }
+    if (v.empty()) return CLAW_OK;
+    if (cudaMalloc((void**)dst, v.size() * sizeof(T)) != cudaSuccess) return CLAW_ENOMEM;
+    if (cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return CLAW_ECUDA;
+    return CLAW_OK;
+}
+
+void free_level(claw_ctx* ctx, int L)
+{
+    LevelDev& d = ctx->lev[L];
+    cudaFree(d.patches);
+    cudaFree(d.tiles);
+    cudaFree(d.copies);
+    cudaFree(d.interps);
+    cudaFree(d.avgs);
+    cudaFree(ctx->ptiles[L]);
+    for (auto& t : ctx->tmaps[L]) cudaFree(t.dev);
+    ctx->tmaps[L].clear();
+    ctx->ptiles[L] = nullptr;
+    d.patches = nullptr;
+    d.tiles = nullptr;
+    d.copies = nullptr;
+    d.interps = nullptr;
+    d.avgs = nullptr;
+    d.nboxes = d.ntiles = d.ncopy = d.ninterp = d.navg = 0;
+    d.boxes.clear();
+    d.hpatches.clear();
+    d.htiles.clear();
+    ctx->set[L] = false;
+}
+
+// tiles of a level for its tiling: sorted by area (largest first) for the persistent walk,
+// and grouped by box for the per-box launches
+int build_tiles(claw_ctx* ctx, int L)
+{
+    LevelDev& d = ctx->lev[L];
+    std::vector<TileDev> t;
+    std::vector<int> start;
+    for (int n = 0; n < d.nboxes; ++n) {
+        const claw_box& b = d.boxes[n];
+        start.push_back((int)t.size());
+        for (int y = 0; y < b.ny; y += d.ty)
+            for (int x = 0; x < b.nx; x += d.tx) {
+                TileDev T;
+                T.patch = n;
+                T.x0 = (short)x;
+                T.y0 = (short)y;
+                T.tx = (short)std::min(d.tx, b.nx - x);
+                T.ty = (short)std::min(d.ty, b.ny - y);
+                T.pad = 0;
+                t.push_back(T);
+            }
+    }
+    start.push_back((int)t.size());
+    int rc = upload(&ctx->ptiles[L], t);
+    if (rc) return rc;
+    ctx->ptile_start[L] = start;
+    std::stable_sort(t.begin(), t.end(), [](const TileDev& a, const TileDev& b) {
+        return (int)a.tx * a.ty > (int)b.tx * b.ty;
+    });
+    d.htiles = t;
+    d.ntiles = (int)t.size();
+    for (auto& tm : ctx->tmaps[L]) cudaFree(tm.dev);
+    ctx->tmaps[L].clear();
+    return upload(&d.tiles, t);
+}
+
+struct GhostEntry {
+    int gi, gj;         // ghost cell (level index)
+    int src;            // source box or -1 (interpolation)
+    long long soff;     // source plane-0 element
+    int flags;
+};
+
+// ghost tasks of one level: copy rectangles and interpolated cells
+int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::vector<InterpCell>& cells)
+{
+    LevelDev& d = ctx->lev[L];
+    std::vector<Locator> loc(ctx->nruns), cloc(ctx->nruns);
+    for (int r = 0; r < ctx->nruns; ++r) {
+        loc[r].boxes = &d.boxes;
+        if (L > 0) cloc[r].boxes = &ctx->lev[L - 1].boxes;
+    }
+    for (int n = 0; n < d.nboxes; ++n) loc[d.boxes[n].run].add(d.boxes[n], n);
+    if (L > 0)
+        for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
+            cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
+
+    for (int n = 0; n < d.nboxes; ++n) {
+        const claw_box& b = d.boxes[n];
+        const claw_problem& pr = ctx->runs[b.run];
+        const int NX = level_nx(pr, L), NY = level_ny(pr, L);
+        const int W = b.nx + 4;
+        std::vector<GhostEntry> ent;
+        for (int gj = b.jlo - 2; gj < b.jlo + b.ny + 2; ++gj)
+            for (int gi = b.ilo - 2; gi < b.ilo + b.nx + 2; ++gi) {
+                if (gi >= b.ilo && gi < b.ilo + b.nx && gj >= b.jlo && gj < b.jlo + b.ny) continue;
+                int fx, fy;
+                const int si = bc_map(gi, NX, pr.bc[0], pr.bc[1], &fx);
+                const int sj = bc_map(gj, NY, pr.bc[2], pr.bc[3], &fy);
+                int src = (si >= b.ilo && si < b.ilo + b.nx && sj >= b.jlo && sj < b.jlo + b.ny)
+                              ? n : loc[b.run].find(si, sj);
+                GhostEntry e{gi, gj, src, 0, fx | (fy << 1)};
+                if (src >= 0) {
+                    e.soff = cell_off(d.boxes[src], si, sj);
+                    ent.push_back(e);
+                    continue;
+                }
+                // space-time interpolation from level L-1 at the fine cell (si, sj)
+                if (L == 0) return CLAW_EINVAL;
+                const int rr = d.ratio;
+                const int cNX = level_nx(pr, L - 1), cNY = level_ny(pr, L - 1);
+                const int I = floordiv(si, rr), J = floordiv(sj, rr);
+                const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
+                InterpCell c;
+                std::memset(&c, 0, sizeof(c));
+                c.dst = cell_off(b, gi, gj);
+                c.dplane = plane_of(b);
+                for (int s = 0; s < 5; ++s) {
+                    int cfx, cfy;
+                    const int ci = bc_map(I + di[s], cNX, pr.bc[0], pr.bc[1], &cfx);
+                    const int cj = bc_map(J + dj[s], cNY, pr.bc[2], pr.bc[3], &cfy);
+                    const int m = cloc[b.run].find(ci, cj);
+                    if (m < 0) return CLAW_EINVAL;   // not properly nested
+                    const claw_box& cb = ctx->lev[L - 1].boxes[m];
+                    c.src[s] = cell_off(cb, ci, cj);
+                    c.splane[s] = plane_of(cb);
+                    c.sflags[s] = cfx | (cfy << 1);
+                }
+                c.xi = ((double)(si - I * rr) + 0.5) / rr - 0.5;
+                c.eta = ((double)(sj - J * rr) + 0.5) / rr - 0.5;
+                c.flags = fx | (fy << 1);
+                cells.push_back(c);
+            }
+        // row runs of copies (consecutive ghosts of a row with one source box, one sign and a
+        // constant source step), then stacked into rectangles
+        struct RowRun {
+            int gj, gi0, w, src, flags, sx;
+            long long soff;
+        };
+        std::vector<RowRun> runs;
+        for (size_t k = 0; k < ent.size();) {
+            RowRun R{ent[k].gj, ent[k].gi, 1, ent[k].src, ent[k].flags, 0, ent[k].soff};
+            size_t k2 = k + 1;
+            while (k2 < ent.size() && ent[k2].gj == R.gj && ent[k2].gi == R.gi0 + R.w &&
+                   ent[k2].src == R.src && ent[k2].flags == R.flags) {
+                const long long step = ent[k2].soff - ent[k2 - 1].soff;
+                if (R.w == 1) {
+                    if (step < -1 || step > 1) break;
+                    R.sx = (int)step;
+                } else if (step != R.sx) {
+                    break;
+                }
+                ++R.w;
+                ++k2;
+            }
+            runs.push_back(R);
+            k = k2;
+        }
+        struct Open {
+            RowRun first;
+            int h;
+            long long sy, last_soff;
+            int last_gj;
+        };
+        std::vector<Open> open;
+        auto emit = [&](const Open& o) {
+            const claw_box& sb = d.boxes[o.first.src];
+            CopyRect c;
+            c.dst = cell_off(b, o.first.gi0, o.first.gj);
+            c.src = o.first.soff;
+            c.dplane = plane_of(b);
+            c.splane = plane_of(sb);
+            c.w = o.first.w;
+            c.h = o.h;
+            c.dpitch = W;
+            c.sy = (int)o.sy;
+            c.sx = o.first.sx;
+            c.flags = o.first.flags;
+            rects.push_back(c);
+        };
+        for (const RowRun& R : runs) {
+            bool merged = false;
+            for (Open& o : open) {
+                if (o.last_gj != R.gj - 1 || o.first.gi0 != R.gi0 || o.first.w != R.w ||
+                    o.first.src != R.src || o.first.flags != R.flags || o.first.sx != R.sx)
+                    continue;
+                const long long step = R.soff - o.last_soff;
+                const long long pitch = d.boxes[R.src].nx + 4;
+                if (o.h == 1) {
+                    if (step != 0 && step != pitch && step != -pitch) continue;
+                    o.sy = step;
+                } else if (step != o.sy) {
+                    continue;
+                }
+                ++o.h;
+                o.last_soff = R.soff;
+                o.last_gj = R.gj;
+                merged = true;
+                break;
+            }
+            if (!merged) open.push_back(Open{R, 1, 0, R.soff, R.gj});
+            // retire rectangles that can no longer grow
+            for (size_t q = 0; q < open.size();) {
+                if (open[q].last_gj < R.gj - 1) {
+                    emit(open[q]);
+                    open.erase(open.begin() + q);
+                } else {
+                    ++q;
+                }
+            }
+        }
+        for (const Open& o : open) emit(o);
+    }
+    return CLAW_OK;
+}
+
+// coarse cells of level L-1 covered by each box of level L
+void build_avg_tables(claw_ctx* ctx, int L, std::vector<AvgRect>& out)
+{
+    const LevelDev& f = ctx->lev[L];
+    const LevelDev& c = ctx->lev[L - 1];
+    const int r = f.ratio;
+    for (const claw_box& F : f.boxes)
+        for (const claw_box& C : c.boxes) {
+            if (C.run != F.run) continue;
+            const int i0 = std::max(F.ilo / r, C.ilo), i1 = std::min((F.ilo + F.nx) / r, C.ilo + C.nx);
+            const int j0 = std::max(F.jlo / r, C.jlo), j1 = std::min((F.jlo + F.ny) / r, C.jlo + C.ny);
+            if (i0 >= i1 || j0 >= j1) continue;
+            AvgRect a;
+            a.cdst = cell_off(C, i0, j0);
+            a.fsrc = cell_off(F, i0 * r, j0 * r);
+            a.cplane = plane_of(C);
+            a.fplane = plane_of(F);
+            a.w = i1 - i0;
+            a.h = j1 - j0;
+            a.cpitch = C.nx + 4;
+            a.fpitch = F.nx + 4;
+            out.push_back(a);
+        }
+}
+
+// tensor-map descriptors of one level for a given q pool and tiling (cached per pool)
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+const void* get_tmaps(claw_ctx* ctx, int L, const double* q, cudaStream_t s)
+{
+    LevelDev& d = ctx->lev[L];
+    auto& cache = ctx->tmaps[L];
+    for (auto& t : cache)
+        if (t.q == q && t.tx == d.tx && t.ty == d.ty) {
+            t.stamp = ++ctx->stamp;
+            return t.dev;
+        }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    auto enc = encode_fn();
+    if (!enc) return nullptr;
+    // the copied box must fit inside every box's padded planes (else cooperative loads)
+    for (const claw_box& b : d.boxes)
+        if (d.tx + 4 > b.nx + 4 || d.ty + 4 > b.ny + 4) return nullptr;
+    std::vector<CUtensorMap> maps(d.nboxes);
+    for (int n = 0; n < d.nboxes; ++n) {
+        const claw_box& b = d.boxes[n];
+        const cuuint64_t W = b.nx + 4, H = b.ny + 4;
+        cuuint64_t dims[3] = {W, H, 3};
+        cuuint64_t strides[2] = {W * 8, W * H * 8};
+        cuuint32_t box[3] = {(cuuint32_t)(d.tx + 4), (cuuint32_t)(d.ty + 4), 3};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = enc(&maps[n], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)(q + b.qoff), dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return nullptr;
+    }
+    TmapCache t;
+    t.q = q;
+    t.tx = d.tx;
+    t.ty = d.ty;
+    if (cudaMalloc(&t.dev, maps.size() * sizeof(CUtensorMap)) != cudaSuccess) return nullptr;
+    if (cudaMemcpyAsync(t.dev, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(t.dev);
+        return nullptr;
+    }
+    t.stamp = ++ctx->stamp;
+    if (cache.size() >= 4) {   // evict the least recently used
+        auto old = std::min_element(cache.begin(), cache.end(),
+                                    [](const TmapCache& a, const TmapCache& b) { return a.stamp < b.stamp; });
+        cudaStreamSynchronize(s);
+        cudaFree(old->dev);
+        cache.erase(old);
+    }
+    cache.push_back(t);
+    return t.dev;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CLAW_OK : CLAW_ECUDA; }
+
+bool valid_level(claw_ctx* ctx, int L) { return ctx && L >= 0 && L < CLAW_MAXLEV && ctx->set[L]; }
+
+StepArgs make_args(claw_ctx* ctx, int L, const double* q_old, double* q_new, const double* aux,
+                   const double* dt, double* smax)
+{
+    const LevelDev& d = ctx->lev[L];
+    StepArgs a;
+    a.patches = d.patches;
+    a.tiles = d.tiles;
+    a.tmaps = nullptr;
+    a.ntiles = d.ntiles;
+    a.qold = q_old;
+    a.qnew = q_new;
+    a.aux = aux;
+    a.dt = dt;
+    a.smax = smax;
+    a.err = ctx->err;
+    a.order = ctx->order;
+    a.transverse = ctx->transverse;
+    a.rho0 = ctx->rho0;
+    a.K0 = ctx->K0;
+    return a;
+}
+
+int check_step_args(claw_ctx* ctx, int L, const double* q_old, const double* q_new, const double* aux,
+                    const double* dt, const double* smax)
+{
+    if (!ctx) return CLAW_EINVAL;
+    if (L < 0 || L >= CLAW_MAXLEV) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    if (!q_old || !q_new || !dt || !smax || q_old == q_new) return CLAW_EINVAL;
+    if (ctx->medium == 1 && !aux) return CLAW_EINVAL;
+    return CLAW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int claw_create(claw_ctx** out, const claw_problem* runs, int32_t nruns, int32_t device)
+{
+    if (!out || !runs || nruns <= 0) return CLAW_EINVAL;
+    *out = nullptr;
+    for (int r = 0; r < nruns; ++r) {
+        const claw_problem& p = runs[r];
+        if (p.nlev < 1 || p.nlev > CLAW_MAXLEV || p.nx0 < 1 || p.ny0 < 1 || !(p.xhi > p.xlo) ||
+            !(p.yhi > p.ylo) || !(p.cfl > 0) || p.limiter < 0 || p.limiter > 4 || p.order < 1 ||
+            p.order > 2 || p.transverse < 0 || p.transverse > 2 || p.medium < 0 || p.medium > 1)
+            return CLAW_EINVAL;
+        for (int s = 0; s < 4; ++s)
+            if (p.bc[s] < 0 || p.bc[s] > 2) return CLAW_EINVAL;
+        if ((p.bc[0] == CLAW_BC_PERIODIC) != (p.bc[1] == CLAW_BC_PERIODIC) ||
+            (p.bc[2] == CLAW_BC_PERIODIC) != (p.bc[3] == CLAW_BC_PERIODIC))
+            return CLAW_EINVAL;
+        for (int l = 1; l < p.nlev; ++l)
+            if (p.ratio[l] < 2 || p.ratio[l] > 16) return CLAW_EINVAL;
+        if (p.medium == 0 && !(p.rho0 > 0 && p.K0 > 0)) return CLAW_EINVAL;
+        if (p.limiter != runs[0].limiter || p.order != runs[0].order || p.transverse != runs[0].transverse ||
+            p.medium != runs[0].medium || (p.medium == 0 && (p.rho0 != runs[0].rho0 || p.K0 != runs[0].K0)))
+            return CLAW_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CLAW_ECUDA;
+    claw_ctx* c = new (std::nothrow) claw_ctx;
+    if (!c) return CLAW_ENOMEM;
+    DevGuard g(device);
+    c->device = device;
+    c->nruns = nruns;
+    c->runs.assign(runs, runs + nruns);
+    c->limiter = runs[0].limiter;
+    c->order = runs[0].order;
+    c->transverse = runs[0].transverse;
+    c->medium = runs[0].medium;
+    c->rho0 = runs[0].rho0;
+    c->K0 = runs[0].K0;
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
+    std::vector<double> minh(CLAW_MAXLEV * nruns, 0.0), cfl(nruns);
+    for (int r = 0; r < nruns; ++r) {
+        cfl[r] = runs[r].cfl;
+        for (int L = 0; L < runs[r].nlev; ++L)
+            minh[L * nruns + r] = std::min(level_dx(runs[r], L), level_dy(runs[r], L));
+    }
+    if (cudaMalloc(&c->err, sizeof(int)) != cudaSuccess || cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->minh, minh.size() * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->cflv, cfl.size() * sizeof(double)) != cudaSuccess ||
+        cudaMemcpy(c->minh, minh.data(), minh.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->cflv, cfl.data(), cfl.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        claw_destroy(c);
+        return CLAW_ENOMEM;
+    }
+    *out = c;
+    return CLAW_OK;
+}
+
+void claw_destroy(claw_ctx* ctx)
+{
+    if (!ctx) return;
+    {
+        DevGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        for (int L = 0; L < CLAW_MAXLEV; ++L) free_level(ctx, L);
+        cudaFree(ctx->err);
+        cudaFree(ctx->minh);
+        cudaFree(ctx->cflv);
+    }
+    delete ctx;
+}
+
+int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nboxes)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || nboxes < 0 || (nboxes > 0 && !boxes)) return CLAW_EINVAL;
+    if (L > 0 && !ctx->set[L - 1]) return CLAW_ESTATE;
+    DevGuard g(ctx->device);
+    for (int l = L; l < CLAW_MAXLEV; ++l)
+        if (ctx->set[l]) free_level(ctx, l);
+    LevelDev& d = ctx->lev[L];
+    d.boxes.assign(boxes, boxes + nboxes);
+    d.nboxes = nboxes;
+    d.ratio = 1;
+    bool even = true;
+    // validation: inside the domain, aligned to the coarser level, sizes, offsets
+    for (int n = 0; n < nboxes; ++n) {
+        const claw_box& b = boxes[n];
+        if (b.run < 0 || b.run >= ctx->nruns) return CLAW_EINVAL;
+        const claw_problem& p = ctx->runs[b.run];
+        if (L >= p.nlev) return CLAW_EINVAL;
+        if (L > 0) {
+            if (d.ratio != 1 && d.ratio != p.ratio[L]) return CLAW_EINVAL;   // one ratio per level
+            d.ratio = p.ratio[L];
+        }
+        const int NX = level_nx(p, L), NY = level_ny(p, L);
+        if (b.nx < 1 || b.ny < 1 || b.nx > 4096 || b.ny > 4096 || b.ilo < 0 || b.jlo < 0 ||
+            b.ilo + b.nx > NX || b.jlo + b.ny > NY || b.qoff < 0 || b.coff < 0)
+            return CLAW_EINVAL;
+        if (L > 0) {
+            const int r = p.ratio[L];
+            if (b.ilo % r || b.jlo % r || b.nx % r || b.ny % r) return CLAW_EINVAL;
+        }
+        if ((b.nx & 1) || (b.qoff & 1)) even = false;
+    }
+    // disjointness within each run (bucketed)
+    {
+        std::vector<Locator> loc(ctx->nruns);
+        for (int r = 0; r < ctx->nruns; ++r) loc[r].boxes = &d.boxes;
+        for (int n = 0; n < nboxes; ++n) {
+            const claw_box& b = boxes[n];
+            // compare with boxes already added that share a bucket
+            for (int bj = floordiv(b.jlo, Locator::B); bj <= floordiv(b.jlo + b.ny - 1, Locator::B); ++bj)
+                for (int bi = floordiv(b.ilo, Locator::B); bi <= floordiv(b.ilo + b.nx - 1, Locator::B); ++bi) {
+                    auto it = loc[b.run].buckets.find(Locator::key(bi, bj));
+                    if (it == loc[b.run].buckets.end()) continue;
+                    for (int m : it->second) {
+                        const claw_box& o = boxes[m];
+                        if (b.ilo < o.ilo + o.nx && o.ilo < b.ilo + b.nx && b.jlo < o.jlo + o.ny &&
+                            o.jlo < b.jlo + b.ny)
+                            return CLAW_EINVAL;
+                    }
+                }
+            loc[b.run].add(b, n);
+        }
+    }
+    // patch table
+    d.hpatches.resize(nboxes);
+    for (int n = 0; n < nboxes; ++n) {
+        const claw_box& b = boxes[n];
+        const claw_problem& p = ctx->runs[b.run];
+        PatchDev P;
+        P.qoff = b.qoff;
+        P.aoff = (long long)CLAW_NAUX * b.coff;
+        P.nx = b.nx;
+        P.ny = b.ny;
+        P.run = b.run;
+        P.pad = 0;
+        P.dxinv = 1.0 / level_dx(p, L);
+        P.dyinv = 1.0 / level_dy(p, L);
+        P.dtscale = 1.0;
+        for (int l = 1; l <= L; ++l) P.dtscale /= p.ratio[l];
+        d.hpatches[n] = P;
+    }
+    ctx->tma_ok[L] = even;
+    d.tx = 32;
+    d.ty = 32;
+    d.staging = even ? 1 : 0;
+    std::vector<CopyRect> rects;
+    std::vector<InterpCell> cells;
+    std::vector<AvgRect> avg;
+    int rc = build_ghost_tables(ctx, L, rects, cells);
+    if (rc) return rc;
+    if (L > 0) build_avg_tables(ctx, L, avg);
+    if ((rc = upload(&d.patches, d.hpatches)) || (rc = upload(&d.copies, rects)) ||
+        (rc = upload(&d.interps, cells)) || (rc = upload(&d.avgs, avg)))
+        return rc;
+    d.ncopy = (int)rects.size();
+    d.ninterp = (int)cells.size();
+    d.navg = (int)avg.size();
+    ctx->set[L] = true;
+    rc = build_tiles(ctx, L);
+    if (rc) {
+        ctx->set[L] = false;
+        return rc;
+    }
+    return CLAW_OK;
+}
+
+int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t staging)
+{
+    if (!valid_level(ctx, L)) return CLAW_EINVAL;
+    const bool shape_ok = (tx == 32 && ty == 32) || (tx == 32 && ty == 16) || (tx == 16 && ty == 16);
+    if (!shape_ok || staging < 0 || staging > 1 || (staging == 1 && !ctx->tma_ok[L])) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    LevelDev& d = ctx->lev[L];
+    if (d.tx == tx && d.ty == ty) {
+        d.staging = staging;
+        return CLAW_OK;
+    }
+    d.tx = tx;
+    d.ty = ty;
+    d.staging = staging;
+    return build_tiles(ctx, L);
+}
+
+int claw_medium_aux(claw_ctx* ctx, int32_t L, const double* rho, const double* K, double* aux, void* stream)
+{
+    if (!valid_level(ctx, L) || !rho || !K || !aux) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    ctx->launches += d.nboxes > 0;
+    return cuda_rc(launch_medium_aux(d.patches, d.nboxes, rho, K, aux, 0, (cudaStream_t)stream));
+}
+
+int claw_medium_aux_adjoint(claw_ctx* ctx, int32_t L, const double* rho, const double* K, const double* g_aux,
+                            double* g_rho, double* g_K, void* stream)
+{
+    if (!valid_level(ctx, L) || !rho || !K || !g_aux || !g_rho || !g_K) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    ctx->launches += d.nboxes > 0;
+    return cuda_rc(launch_medium_aux_adjoint(d.patches, d.nboxes, rho, K, g_aux, g_rho, g_K, (cudaStream_t)stream));
+}
+
+int claw_fill_ghost(claw_ctx* ctx, int32_t L, double* q, const double* qc_old, const double* qc_new, double tau,
+                    void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !q) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    const LevelDev& d = ctx->lev[L];
+    if (d.ninterp > 0 && (!qc_old || !qc_new || !(tau >= 0.0 && tau <= 1.0))) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_fill_copy(d.copies, d.ncopy, q, s);
+    ctx->launches += d.ncopy > 0;
+    if (e == cudaSuccess) {
+        e = launch_fill_interp(d.interps, d.ninterp, q, qc_old, qc_new, tau, s);
+        ctx->launches += d.ninterp > 0;
+    }
+    return cuda_rc(e);
+}
+
+int claw_fill_ghost_adjoint(claw_ctx* ctx, int32_t L, double* lam, double* lco, double* lcn, const double* qc_old,
+                            const double* qc_new, double tau, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !lam) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    const LevelDev& d = ctx->lev[L];
+    if (d.ninterp > 0 && (!qc_old || !qc_new)) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // interpolated ghosts first (they read coarse cells only), then the copies
+    cudaError_t e = launch_fill_interp_adjoint(d.interps, d.ninterp, lam, lco, lcn, qc_old, qc_new, tau, s);
+    ctx->launches += d.ninterp > 0;
+    if (e == cudaSuccess) {
+        e = launch_fill_copy_adjoint(d.copies, d.ncopy, lam, s);
+        ctx->launches += d.ncopy > 0;
+    }
+    return cuda_rc(e);
+}
+
+int claw_cfl_max(claw_ctx* ctx, int32_t L, const double* aux, double* smax, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !smax) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    if (ctx->medium == 1 && !aux) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_cfl_max(ctx->lev[L].patches, ctx->lev[L].nboxes, ctx->medium, std::sqrt(ctx->K0 / ctx->rho0), aux,
+                           smax, s);
+    ctx->launches += 1;
+    return cuda_rc(e);
+}
+
+int claw_dt_update(claw_ctx* ctx, int32_t L, double* smax, double* dt, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !smax || !dt) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    ctx->launches += 1;
+    if (L >= CLAW_MAXLEV) return CLAW_EINVAL;
+    return cuda_rc(launch_dt_update(ctx->minh + (size_t)L * ctx->nruns, ctx->cflv, ctx->nruns, smax, dt, ctx->err,
+                                    (cudaStream_t)stream));
+}
+
+int claw_level_step(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,
+                    const double* dt, double* smax, void* stream)
+{
+    int rc = check_step_args(ctx, L, q_old, q_new, aux, dt, smax);
+    if (rc) return rc;
+    DevGuard g(ctx->device);
+    LevelDev& d = ctx->lev[L];
+    if (d.ntiles == 0) return CLAW_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    StepArgs a = make_args(ctx, L, q_old, q_new, aux, dt, smax);
+    int staging = d.staging;
+    if (staging == 1) {
+        a.tmaps = get_tmaps(ctx, L, q_old, s);
+        if (!a.tmaps) staging = 0;   // no descriptor (e.g. first use inside a graph capture)
+    }
+    const int per_sm = step_max_ctas_per_sm(ctx->medium, ctx->limiter, d.tx, d.ty, staging);
+    if (per_sm <= 0) return CLAW_ECUDA;
+    const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
+    ctx->launches += 1;
+    return cuda_rc(launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, staging, grid, s));
+}
+
+int claw_level_step_patchwise(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,
+                              const double* dt, double* smax, void* stream)
+{
+    int rc = check_step_args(ctx, L, q_old, q_new, aux, dt, smax);
+    if (rc) return rc;
+    DevGuard g(ctx->device);
+    LevelDev& d = ctx->lev[L];
+    cudaStream_t s = (cudaStream_t)stream;
+    StepArgs a = make_args(ctx, L, q_old, q_new, aux, dt, smax);
+    const auto& st = ctx->ptile_start[L];
+    for (int n = 0; n < d.nboxes; ++n) {
+        a.tiles = ctx->ptiles[L] + st[n];
+        a.ntiles = st[n + 1] - st[n];
+        ctx->launches += 1;
+        cudaError_t e = launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, 0, a.ntiles, s);
+        if (e != cudaSuccess) return CLAW_ECUDA;
+    }
+    return CLAW_OK;
+}
+
+int claw_average_down(claw_ctx* ctx, int32_t fl, const double* qf, double* qc, void* stream)
+{
+    if (!ctx || fl < 1 || fl >= CLAW_MAXLEV || !qf || !qc) return CLAW_EINVAL;
+    if (!ctx->set[fl]) return CLAW_ESTATE;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[fl];
+    ctx->launches += d.navg > 0;
+    return cuda_rc(launch_average(d.avgs, d.navg, d.ratio, qf, qc, (cudaStream_t)stream));
+}
+
+int claw_average_down_adjoint(claw_ctx* ctx, int32_t fl, double* lf, double* lc, void* stream)
+{
+    if (!ctx || fl < 1 || fl >= CLAW_MAXLEV || !lf || !lc) return CLAW_EINVAL;
+    if (!ctx->set[fl]) return CLAW_ESTATE;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[fl];
+    ctx->launches += d.navg > 0;
+    return cuda_rc(launch_average_adjoint(d.avgs, d.navg, d.ratio, lf, lc, (cudaStream_t)stream));
+}
+
+int claw_level_step_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const double* lam_new, double* lam_old,
+                            const double* aux, double* g_aux, const double* dt, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !q_old || !lam_new || !lam_old || !dt) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    if (ctx->medium == 1 && (!aux || !g_aux)) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    LevelDev& d = ctx->lev[L];
+    if (d.ntiles == 0) return CLAW_OK;
+    StepArgs a = make_args(ctx, L, q_old, nullptr, aux, dt, nullptr);
+    const int grid = std::min(d.ntiles, 2 * ctx->nsm);
+    ctx->launches += 1;
+    return cuda_rc(launch_step_adjoint(a, lam_old, g_aux, ctx->medium, ctx->limiter, d.tx, d.ty, grid,
+                                       (cudaStream_t)stream));
+}
+
+int claw_sync_status(claw_ctx* ctx)
+{
+    if (!ctx) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return CLAW_ECUDA;
+    int f = 0;
+    if (cudaMemcpy(&f, ctx->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CLAW_ECUDA;
+    if (f && cudaMemset(ctx->err, 0, sizeof(int)) != cudaSuccess) return CLAW_ECUDA;
+    if (f & ERR_NAN) return CLAW_ENAN;
+    if (f & ERR_CFL) return CLAW_ECFL;
+    if (f & ERR_TIMEOUT) return CLAW_ETIMEOUT;
+    return CLAW_OK;
+}
+
+int64_t claw_launch_count(claw_ctx* ctx) { return ctx ? (int64_t)ctx->launches.load() : 0; }
+
+const char* claw_strerror(int32_t s)
+{
+    switch (s) {
+    case CLAW_OK: return "ok";
+    case CLAW_EINVAL: return "invalid argument or box set";
+    case CLAW_ECUDA: return "CUDA runtime error";
+    case CLAW_ENOMEM: return "out of memory";
+    case CLAW_ECFL: return "CFL number above 1";
+    case CLAW_ENAN: return "NaN or Inf in the state";
+    case CLAW_ETIMEOUT: return "bounded device wait expired";
+    case CLAW_ESTATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

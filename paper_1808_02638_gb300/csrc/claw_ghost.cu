@@ -1,0 +1,371 @@
+// claw_ghost.cu -- ghost fill (Sec. 2.2: physical boundary, same-level copy, coarse-to-fine
+// space-time interpolation), "updating" average (Sec. 2.2-2.3), per-cell medium planes, the
+// first-step CFL max and the device time-step rule (Eq. cfl), with their reverse modes.
+// These are light, memory-bound kernels; the host builds compact task tables once per regrid
+// (claw_set_level) so that each launch is a flat loop over tasks.
+#include <cuda_runtime.h>
+
+#include "claw_internal.h"
+
+namespace claw {
+
+static inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------------ same-level copy
+// One warp per rectangle; lanes stride over its w*h*3 elements.
+__global__ void fill_copy_kernel(const CopyRect* __restrict__ rects, int n, double* __restrict__ q)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const CopyRect R = rects[warp];
+    const int cells = R.w * R.h;
+    for (int k = lane; k < 3 * cells; k += 32) {
+        const int m = k / cells, e = k - m * cells;
+        const int y = e / R.w, x = e - y * R.w;
+        double v = q[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx];
+        if ((m == 1 && (R.flags & 1)) || (m == 2 && (R.flags & 2))) v = -v;
+        q[R.dst + m * R.dplane + (long long)y * R.dpitch + x] = v;
+    }
+}
+
+// reverse: ghost adjoint flows into its source, then the ghost adjoint is cleared.  Sources
+// are interior cells and several ghosts may share one (extrapolation), hence the atomics.
+__global__ void fill_copy_adjoint_kernel(const CopyRect* __restrict__ rects, int n, double* __restrict__ lam)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const CopyRect R = rects[warp];
+    const int cells = R.w * R.h;
+    for (int k = lane; k < 3 * cells; k += 32) {
+        const int m = k / cells, e = k - m * cells;
+        const int y = e / R.w, x = e - y * R.w;
+        const long long d = R.dst + m * R.dplane + (long long)y * R.dpitch + x;
+        double g = lam[d];
+        lam[d] = 0.0;
+        if ((m == 1 && (R.flags & 1)) || (m == 2 && (R.flags & 2))) g = -g;
+        if (g != 0.0) atomicAdd(&lam[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx], g);
+    }
+}
+
+cudaError_t launch_fill_copy(const CopyRect* r, int n, double* q, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_copy_kernel<<<div_up((long long)n * 32, 256), 256, 0, s>>>(r, n, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_copy_adjoint(const CopyRect* r, int n, double* lam, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_copy_adjoint_kernel<<<div_up((long long)n * 32, 256), 256, 0, s>>>(r, n, lam);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------ interpolation
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    if (!(a * b > 0.0)) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+__device__ __forceinline__ double sgn_of(int flags, int m)
+{
+    return ((m == 1 && (flags & 1)) || (m == 2 && (flags & 2))) ? -1.0 : 1.0;
+}
+
+// thread per (fine ghost cell, component)
+__global__ void fill_interp_kernel(const InterpCell* __restrict__ cells, int n, double* __restrict__ q,
+                                   const double* __restrict__ cold, const double* __restrict__ cnew,
+                                   double tau)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    const int i = k / 3, m = k - 3 * i;
+    const InterpCell C = cells[i];
+    double Q[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const long long o = C.src[s] + m * C.splane[s];
+        Q[s] = sgn_of(C.sflags[s], m) * ((1.0 - tau) * cold[o] + tau * cnew[o]);
+    }
+    const double sx = minmod(Q[2] - Q[0], Q[0] - Q[1]);
+    const double sy = minmod(Q[4] - Q[0], Q[0] - Q[3]);
+    q[C.dst + m * C.dplane] = sgn_of(C.flags, m) * (Q[0] + C.xi * sx + C.eta * sy);
+}
+
+__global__ void fill_interp_adjoint_kernel(const InterpCell* __restrict__ cells, int n,
+                                           double* __restrict__ lam, double* __restrict__ lco,
+                                           double* __restrict__ lcn, const double* __restrict__ cold,
+                                           const double* __restrict__ cnew, double tau)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    const int i = k / 3, m = k - 3 * i;
+    const InterpCell C = cells[i];
+    double Q[5], G[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const long long o = C.src[s] + m * C.splane[s];
+        Q[s] = sgn_of(C.sflags[s], m) * ((1.0 - tau) * cold[o] + tau * cnew[o]);
+    }
+    const long long d = C.dst + m * C.dplane;
+    const double g = sgn_of(C.flags, m) * lam[d];
+    lam[d] = 0.0;
+    G[0] = g;
+    // minmod branches as in the forward kernel
+    double a = Q[2] - Q[0], b = Q[0] - Q[1];
+    if (a * b > 0.0) {
+        if (fabs(a) < fabs(b)) { G[2] += C.xi * g; G[0] -= C.xi * g; }
+        else { G[0] += C.xi * g; G[1] -= C.xi * g; }
+    }
+    a = Q[4] - Q[0];
+    b = Q[0] - Q[3];
+    if (a * b > 0.0) {
+        if (fabs(a) < fabs(b)) { G[4] += C.eta * g; G[0] -= C.eta * g; }
+        else { G[0] += C.eta * g; G[3] -= C.eta * g; }
+    }
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        if (G[s] == 0.0) continue;
+        const long long o = C.src[s] + m * C.splane[s];
+        const double gs = sgn_of(C.sflags[s], m) * G[s];
+        if (lco) atomicAdd(&lco[o], (1.0 - tau) * gs);
+        if (lcn) atomicAdd(&lcn[o], tau * gs);
+    }
+}
+
+cudaError_t launch_fill_interp(const InterpCell* c, int n, double* q, const double* cold,
+                               const double* cnew, double tau, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_interp_kernel<<<div_up(3LL * n, 256), 256, 0, s>>>(c, n, q, cold, cnew, tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_interp_adjoint(const InterpCell* c, int n, double* lam, double* lco,
+                                       double* lcn, const double* cold, const double* cnew,
+                                       double tau, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_interp_adjoint_kernel<<<div_up(3LL * n, 256), 256, 0, s>>>(c, n, lam, lco, lcn, cold, cnew, tau);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------ averaging
+// block per rectangle, thread per (coarse cell, component); the r x r children are summed
+// row by row and divided by r^2
+__global__ void average_kernel(const AvgRect* __restrict__ rects, int ratio, const double* __restrict__ qf,
+                               double* __restrict__ qc)
+{
+    const AvgRect R = rects[blockIdx.x];
+    const int cells = R.w * R.h;
+    const double rr = (double)(ratio * ratio);
+    for (int k = threadIdx.x; k < 3 * cells; k += blockDim.x) {
+        const int m = k / cells, e = k - m * cells;
+        const int y = e / R.w, x = e - y * R.w;
+        const double* f = qf + R.fsrc + m * R.fplane + (long long)y * ratio * R.fpitch + (long long)x * ratio;
+        double s = 0.0;
+        for (int b = 0; b < ratio; ++b)
+            for (int a = 0; a < ratio; ++a) s += f[(long long)b * R.fpitch + a];
+        qc[R.cdst + m * R.cplane + (long long)y * R.cpitch + x] = s / rr;
+    }
+}
+
+__global__ void average_adjoint_kernel(const AvgRect* __restrict__ rects, int ratio, double* __restrict__ lf,
+                                       double* __restrict__ lc)
+{
+    const AvgRect R = rects[blockIdx.x];
+    const int cells = R.w * R.h;
+    const double rr = (double)(ratio * ratio);
+    for (int k = threadIdx.x; k < 3 * cells; k += blockDim.x) {
+        const int m = k / cells, e = k - m * cells;
+        const int y = e / R.w, x = e - y * R.w;
+        const long long c = R.cdst + m * R.cplane + (long long)y * R.cpitch + x;
+        const double g = lc[c] / rr;
+        lc[c] = 0.0;
+        double* f = lf + R.fsrc + m * R.fplane + (long long)y * ratio * R.fpitch + (long long)x * ratio;
+        for (int b = 0; b < ratio; ++b)
+            for (int a = 0; a < ratio; ++a) f[(long long)b * R.fpitch + a] += g;
+    }
+}
+
+cudaError_t launch_average(const AvgRect* r, int n, int ratio, const double* qf, double* qc, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    average_kernel<<<n, 256, 0, s>>>(r, ratio, qf, qc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_average_adjoint(const AvgRect* r, int n, int ratio, double* lf, double* lc, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    average_adjoint_kernel<<<n, 256, 0, s>>>(r, ratio, lf, lc);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------ medium planes
+// block per box, thread per cell of the padded box
+__global__ void medium_aux_kernel(const PatchDev* __restrict__ patches, const double* __restrict__ rho,
+                                  const double* __restrict__ K, double* __restrict__ aux)
+{
+    const PatchDev P = patches[blockIdx.x];
+    const int W = P.nx + 4, H = P.ny + 4;
+    const long long WH = (long long)W * H;
+    const long long co = P.aoff / CLAW_NAUX;
+    const double* r = rho + co;
+    const double* k = K + co;
+    double* a = aux + P.aoff;
+    for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
+        const int j = e / W, i = e - j * W;
+        const double z = sqrt(k[e] * r[e]), c = sqrt(k[e] / r[e]);
+        a[AUX_Z * WH + e] = z;
+        a[AUX_C * WH + e] = c;
+        a[AUX_K * WH + e] = k[e];
+        a[AUX_C2 * WH + e] = c * c;
+        double ixs = 0, fx1 = 0, fx2 = 0, iys = 0, fy1 = 0, fy2 = 0;
+        if (i > 0) {
+            const double zw = sqrt(k[e - 1] * r[e - 1]);
+            const double zz = fma(zw, z, 1.0);
+            ixs = 1.0 / (zw + z);
+            fx1 = zz / fma(zw, zw, 1.0);
+            fx2 = zz / fma(z, z, 1.0);
+        }
+        if (j > 0) {
+            const double zs = sqrt(k[e - W] * r[e - W]);
+            const double zz = fma(zs, z, 1.0);
+            iys = 1.0 / (zs + z);
+            fy1 = zz / fma(zs, zs, 1.0);
+            fy2 = zz / fma(z, z, 1.0);
+        }
+        a[AUX_IXS * WH + e] = ixs;
+        a[AUX_FX1 * WH + e] = fx1;
+        a[AUX_FX2 * WH + e] = fx2;
+        a[AUX_IYS * WH + e] = iys;
+        a[AUX_FY1 * WH + e] = fy1;
+        a[AUX_FY2 * WH + e] = fy2;
+    }
+}
+
+// chain rule through the planes above; each cell gathers from the planes that read it
+// (itself, and the edges to its east and north), so no atomics are needed
+__global__ void medium_aux_adjoint_kernel(const PatchDev* __restrict__ patches, const double* __restrict__ rho,
+                                          const double* __restrict__ K, const double* __restrict__ ga,
+                                          double* __restrict__ g_rho, double* __restrict__ g_K)
+{
+    const PatchDev P = patches[blockIdx.x];
+    const int W = P.nx + 4, H = P.ny + 4;
+    const long long WH = (long long)W * H;
+    const long long co = P.aoff / CLAW_NAUX;
+    const double* r = rho + co;
+    const double* k = K + co;
+    const double* g = ga + P.aoff;
+    for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
+        const int j = e / W, i = e - j * W;
+        const double z = sqrt(k[e] * r[e]), c = sqrt(k[e] / r[e]);
+        // dZ/dK = Z/(2K), dZ/drho = Z/(2 rho), dc/dK = c/(2K), dc/drho = -c/(2 rho)
+        double gz = g[AUX_Z * WH + e];
+        double gc = g[AUX_C * WH + e] + 2.0 * c * g[AUX_C2 * WH + e];
+        double gk = g[AUX_K * WH + e];
+        // edge to the west / south of this cell (this cell is the "right" cell)
+        auto edge_right = [&](int ip, int po, int p1, int p2, int e2) {
+            const double zw = sqrt(k[e2] * r[e2]);
+            const double zz = fma(zw, z, 1.0), s = zw + z;
+            const double d1 = fma(zw, zw, 1.0), d2 = fma(z, z, 1.0);
+            // ixs = 1/s ; fx1 = zz/d1 ; fx2 = zz/d2  -> derivatives w.r.t. z (this cell)
+            gz += g[ip * WH + e] * (-1.0 / (s * s)) + g[p1 * WH + e] * (zw / d1) +
+                  g[p2 * WH + e] * (zw / d2 - zz * 2.0 * z / (d2 * d2));
+            (void)po;
+        };
+        auto edge_left = [&](int ip, int p1, int p2, int e2) {
+            // the cell to the east / north owns the edge; this cell is its "left" cell
+            const double zr = sqrt(k[e2] * r[e2]);
+            const double zz = fma(z, zr, 1.0), s = z + zr;
+            const double d1 = fma(z, z, 1.0), d2 = fma(zr, zr, 1.0);
+            gz += g[ip * WH + e2] * (-1.0 / (s * s)) + g[p1 * WH + e2] * (zr / d1 - zz * 2.0 * z / (d1 * d1)) +
+                  g[p2 * WH + e2] * (zr / d2);
+        };
+        if (i > 0) edge_right(AUX_IXS, 0, AUX_FX1, AUX_FX2, e - 1);
+        if (j > 0) edge_right(AUX_IYS, 0, AUX_FY1, AUX_FY2, e - W);
+        if (i + 1 < W) edge_left(AUX_IXS, AUX_FX1, AUX_FX2, e + 1);
+        if (j + 1 < H) edge_left(AUX_IYS, AUX_FY1, AUX_FY2, e + W);
+        g_K[co + e] += gk + gz * z / (2.0 * k[e]) + gc * c / (2.0 * k[e]);
+        g_rho[co + e] += gz * z / (2.0 * r[e]) - gc * c / (2.0 * r[e]);
+    }
+}
+
+cudaError_t launch_medium_aux(const PatchDev* p, int n, const double* rho, const double* K, double* aux,
+                              long long, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    medium_aux_kernel<<<n, 256, 0, s>>>(p, rho, K, aux);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, const double* rho, const double* K,
+                                      const double* g_aux, double* g_rho, double* g_K, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    medium_aux_adjoint_kernel<<<n, 256, 0, s>>>(p, rho, K, g_aux, g_rho, g_K);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------ CFL
+// block per box: max c over the ring [-1, nx] x [-1, ny] (integer max of the bit patterns),
+// one 64-bit atomic max per box on the run's scalar (zeroed by the host before the launch)
+__global__ void cfl_max_kernel(const PatchDev* __restrict__ patches, int medium, double c0,
+                               const double* __restrict__ aux, unsigned long long* __restrict__ smax)
+{
+    const PatchDev P = patches[blockIdx.x];
+    unsigned long long m = 0ull;
+    if (medium == 0) {
+        m = (unsigned long long)__double_as_longlong(c0);
+    } else {
+        const int W = P.nx + 4;
+        const double* c = aux + P.aoff + AUX_C * (long long)W * (P.ny + 4);
+        const int w = P.nx + 2, n = w * (P.ny + 2);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int r = k / w, i = k - r * w;
+            const unsigned long long v = (unsigned long long)__double_as_longlong(c[(r + 1) * W + (i + 1)]);
+            m = v > m ? v : m;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(smax + P.run, m);
+}
+
+cudaError_t launch_cfl_max(const PatchDev* p, int n, int medium, double c0, const double* aux, double* smax,
+                           cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    cfl_max_kernel<<<n, 128, 0, s>>>(p, medium, c0, aux, reinterpret_cast<unsigned long long*>(smax));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------ time step (Eq. cfl)
+__global__ void dt_update_kernel(const double* __restrict__ minh, const double* __restrict__ cfl, int nruns,
+                                 double* __restrict__ smax, double* __restrict__ dt, int* __restrict__ err)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nruns) return;
+    const double s = smax[r];
+    const double used = dt[r];
+    // CFL number of the step just taken (Sec. 2.4): nu = s dt / dx must not exceed 1
+    if (s * used > minh[r] * (1.0 + 1e-12)) atomicOr(err, ERR_CFL);
+    if (s > 0.0) dt[r] = cfl[r] * minh[r] / s;
+    smax[r] = 0.0;
+}
+
+cudaError_t launch_dt_update(const double* minh, const double* cfl, int nruns, double* smax, double* dt,
+                             int* err, cudaStream_t s)
+{
+    dt_update_kernel<<<div_up(nruns, 128), 128, 0, s>>>(minh, cfl, nruns, smax, dt, err);
+    return cudaGetLastError();
+}
+
+}  // namespace claw

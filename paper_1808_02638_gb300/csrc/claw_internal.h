@@ -1,0 +1,146 @@
+// claw_internal.h -- device table layouts and launch entry points shared by the .cu files of
+// libclaw.so.  Not part of the public ABI (include/claw.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/claw.h"
+
+namespace claw {
+
+// aux planes of a cell (medium = 1); edge quantities belong to the edge west / south of the cell
+enum AuxPlane : int {
+    AUX_Z = 0,    // impedance Z = sqrt(K rho)
+    AUX_C = 1,    // sound speed c = sqrt(K / rho)
+    AUX_K = 2,    // bulk modulus K (= c Z)
+    AUX_C2 = 3,   // c^2
+    AUX_IXS = 4,  // 1 / (Z_{i-1,j} + Z_{i,j})
+    AUX_FX1 = 5,  // (Z_{i-1} Z_i + 1) / (Z_{i-1}^2 + 1): limiter projection, left-going wave
+    AUX_FX2 = 6,  // (Z_{i-1} Z_i + 1) / (Z_i^2 + 1): limiter projection, right-going wave
+    AUX_IYS = 7,  // 1 / (Z_{i,j-1} + Z_{i,j})
+    AUX_FY1 = 8,
+    AUX_FY2 = 9,
+};
+static_assert(CLAW_NAUX == 10, "aux plane count");
+
+// One box of a level, as the kernels see it.
+struct PatchDev {
+    long long qoff;   // element offset of the p plane in the q pool
+    long long aoff;   // element offset of the first aux plane in the aux pool (CLAW_NAUX * coff)
+    int nx, ny;       // interior size
+    int run;          // index into the per-run dt / smax arrays
+    int pad;
+    double dxinv, dyinv;
+    double dtscale;   // this level's dt / level-0 dt = 1 / (ratio_1 ... ratio_L)
+};
+
+// One tile of the fused step: interior cells [x0, x0+tx) x [y0, y0+ty) of box `patch`.
+struct TileDev {
+    int patch;
+    short x0, y0, tx, ty;
+    int pad;
+};
+
+// Rectangle of ghost cells copied from interior cells of the same level (same-level copy and
+// physical boundaries).  Element (x, y) of the rectangle, plane m:
+//   dst + m*dplane + y*dpitch + x   <-   sign_m * src[m*splane + y*sy + x*sx]
+struct CopyRect {
+    long long dst, src;
+    long long dplane, splane;
+    int w, h;
+    int dpitch, sy, sx;
+    int flags;   // bit0: negate u, bit1: negate v
+};
+
+// One fine ghost cell filled by space-time interpolation from the coarser level.
+struct InterpCell {
+    long long dst;        // plane-0 element of the fine ghost cell
+    long long src[5];     // plane-0 element of the coarse cells: centre, west, east, south, north
+    long long dplane;     // fine plane stride
+    long long splane[5];  // coarse plane strides
+    double xi, eta;       // offsets of the fine centre from the coarse centre, in coarse cells
+    int sflags[5];        // wall sign flips of each coarse source (bit0 u, bit1 v)
+    int flags;            // wall sign flips of the fine ghost itself
+};
+
+// Coarse cells [0,w) x [0,h) at cdst, each the mean of r x r fine cells at fsrc.
+struct AvgRect {
+    long long cdst, fsrc;
+    long long cplane, fplane;
+    int w, h, cpitch, fpitch;
+};
+
+// Per (level) device tables.
+struct LevelDev {
+    int nboxes = 0;
+    int ntiles = 0;
+    int ncopy = 0;
+    int ninterp = 0;
+    int navg = 0;          // averaging rects into the coarser level
+    int ratio = 1;
+    int tx = 32, ty = 32, staging = 1;
+    PatchDev* patches = nullptr;
+    TileDev* tiles = nullptr;
+    CopyRect* copies = nullptr;
+    InterpCell* interps = nullptr;
+    AvgRect* avgs = nullptr;
+    void* tmaps = nullptr;   // CUtensorMap per box (128 B each), built for the current tiling
+    int tmap_tx = 0, tmap_ty = 0;
+    // host copies
+    std::vector<claw_box> boxes;
+    std::vector<PatchDev> hpatches;
+    std::vector<TileDev> htiles;
+};
+
+struct StepArgs {
+    const PatchDev* patches;
+    const TileDev* tiles;
+    const void* tmaps;
+    int ntiles;
+    const double* qold;
+    double* qnew;
+    const double* aux;
+    const double* dt;
+    double* smax;
+    int* err;
+    // scheme
+    int order, transverse;
+    double rho0, K0;   // uniform medium
+};
+
+// error flag bits written by kernels
+enum : int { ERR_NAN = 1, ERR_CFL = 2, ERR_TIMEOUT = 4 };
+
+// launchers (claw_step.cu)
+cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int staging,
+                        int grid, cudaStream_t s);
+int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int staging);
+cudaError_t launch_step_adjoint(const StepArgs& a, double* lam_old, double* g_aux, int medium,
+                                int limiter, int tx, int ty, int grid, cudaStream_t s);
+
+// launchers (claw_ghost.cu)
+cudaError_t launch_fill_copy(const CopyRect* r, int n, double* q, cudaStream_t s);
+cudaError_t launch_fill_interp(const InterpCell* c, int n, double* q, const double* cold,
+                               const double* cnew, double tau, cudaStream_t s);
+cudaError_t launch_fill_copy_adjoint(const CopyRect* r, int n, double* lam, cudaStream_t s);
+cudaError_t launch_fill_interp_adjoint(const InterpCell* c, int n, double* lam, double* lco,
+                                       double* lcn, const double* cold, const double* cnew,
+                                       double tau, cudaStream_t s);
+cudaError_t launch_average(const AvgRect* r, int n, int ratio, const double* qf, double* qc,
+                           cudaStream_t s);
+cudaError_t launch_average_adjoint(const AvgRect* r, int n, int ratio, double* lf, double* lc,
+                                   cudaStream_t s);
+cudaError_t launch_medium_aux(const PatchDev* p, int n, const double* rho, const double* K,
+                              double* aux, long long cstride_unused, cudaStream_t s);
+cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, const double* rho,
+                                      const double* K, const double* g_aux, double* g_rho,
+                                      double* g_K, cudaStream_t s);
+cudaError_t launch_cfl_max(const PatchDev* p, int n, int medium, double c0, const double* aux,
+                           double* smax, cudaStream_t s);
+cudaError_t launch_dt_update(const double* minh, const double* cfl, int nruns, double* smax,
+                             double* dt, int* err, cudaStream_t s);
+
+}  // namespace claw

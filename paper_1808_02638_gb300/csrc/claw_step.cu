@@ -1,0 +1,53 @@
+// Dispatch of the fused level-step kernels (instantiated in claw_step_uniform.cu and
+// claw_step_cellwise.cu).
+#include <mutex>
+#include <set>
+
+#include "claw_step.cuh"
+
+namespace claw {
+
+static StepKernel pick(int medium, int limiter, int tx, int ty, int staging)
+{
+    return medium ? step_kernel_cellwise(limiter, tx, ty, staging)
+                  : step_kernel_uniform(limiter, tx, ty, staging);
+}
+
+static cudaError_t prepare(const StepKernel& k)
+{
+    // opt in to the dynamic shared memory once per kernel and device
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair((const void*)k.fn, dev);
+    if (done.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute((const void*)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
+int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int staging)
+{
+    StepKernel k = pick(medium, limiter, tx, ty, staging);
+    if (!k.fn || prepare(k) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k.fn, k.nt, k.smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int staging,
+                        int grid, cudaStream_t s)
+{
+    StepKernel k = pick(medium, limiter, tx, ty, staging);
+    if (!k.fn) return cudaErrorInvalidValue;
+    cudaError_t e = prepare(k);
+    if (e != cudaSuccess) return e;
+    k.fn<<<grid, k.nt, k.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace claw

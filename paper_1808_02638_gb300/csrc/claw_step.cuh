@@ -1,0 +1,611 @@
+// claw_step.cuh -- the fused, persistent level-step kernel (sm_103a, FP64).
+//
+// One launch advances every tile of every box of a level (Eq. wave_form_2d_2nd_order, Sec. 2.1):
+//   Q^{n+1} = Q - dt/dx (A+dQ_{i-1/2} + A-dQ_{i+1/2}) - dt/dy (B+dQ_{j-1/2} + B-dQ_{j+1/2})
+//               - dt/dx (F~_{i+1/2} - F~_{i-1/2}) - dt/dy (G~_{j+1/2} - G~_{j-1/2})
+// for the acoustics system of Sec. 4.1 with the wave-propagation Riemann solver, limiter,
+// correction flux and transverse splitting of LeVeque (2002), the reference Sec. 2.1 defers to.
+//
+// Design (GB300 first, not the paper's per-patch launches of Sec. 3.1):
+//  * persistent CTAs walk a size-sorted tile table; the (tx+4) x (ty+4) x 3 input tile with its
+//    two ghost layers is staged into shared memory by a tensor-memory-accelerator bulk copy
+//    (double-buffered: the next tile streams in while this one is computed) or by coalesced
+//    loads;
+//  * every edge is solved once per tile; waves and fluctuations never leave shared memory;
+//    only Q^{n+1} is written back;
+//  * the path is bound by the FP64 pipe (1/64 of FP32 on this part), so the arithmetic is
+//    arranged to minimise FP64 instructions: the transverse split is applied once per cell
+//    to the summed x-fluctuation (it is linear), constant coefficients fold into per-tile
+//    constants, limiters are division free (phi(b/a) a), wave speeds are reduced on the
+//    integer pipe as bit patterns;
+//  * the CFL reduction (Sec. 2.4, 3.2.2) is a warp-shuffle / shared-memory max per tile folded
+//    by the CTA, with one 64-bit atomic max per CTA and run on the run's device scalar.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "claw_internal.h"
+
+namespace claw {
+
+// ------------------------------------------------------------------------- limiters
+// Lim<L>::f(a, b) = phi(b / a) * a for the wave strength a at an edge and the projected
+// strength b of the same family at the upwind edge; 0 when a b <= 0 (also covers a = 0,
+// where the wave vanishes).  Division free except van Leer.
+template <int L> struct Lim;
+template <> struct Lim<CLAW_LIM_NONE> {
+    static __device__ __forceinline__ double f(double a, double) { return a; }
+};
+template <> struct Lim<CLAW_LIM_MINMOD> {   // max(0, min(1, theta))
+    static __device__ __forceinline__ double f(double a, double b)
+    {
+        if (!(a * b > 0.0)) return 0.0;
+        return a > 0.0 ? fmin(a, b) : fmax(a, b);
+    }
+};
+template <> struct Lim<CLAW_LIM_SUPERBEE> {   // max(0, min(1, 2 theta), min(2, theta))
+    static __device__ __forceinline__ double f(double a, double b)
+    {
+        if (!(a * b > 0.0)) return 0.0;
+        double a2 = a + a, b2 = b + b;
+        return a > 0.0 ? fmax(fmin(a, b2), fmin(a2, b)) : fmin(fmax(a, b2), fmax(a2, b));
+    }
+};
+template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|)
+    static __device__ __forceinline__ double f(double a, double b)
+    {
+        if (!(a * b > 0.0)) return 0.0;
+        return (2.0 * a * b) / (a + b);
+    }
+};
+template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta))
+    static __device__ __forceinline__ double f(double a, double b)
+    {
+        if (!(a * b > 0.0)) return 0.0;
+        double m = 0.5 * (a + b), a2 = a + a, b2 = b + b;
+        return a > 0.0 ? fmin(m, fmin(a2, b2)) : fmax(m, fmax(a2, b2));
+    }
+};
+
+// ------------------------------------------------------------------------- tile geometry
+template <int TX, int TY> struct Geo {
+    static constexpr int SW = TX + 4, SH = TY + 4, QPL = SW * SH;  // staged q plane
+    static constexpr int XEW = TX + 3, XEH = TY + 2;               // x-edges a in [-1,TX+1], rows [-1,TY]
+    static constexpr int YEW = TX + 2, YEH = TY + 3;               // y-edges b in [-1,TY+1], cols [-1,TX]
+    static constexpr int XLW = TX + 1, XLH = TY + 2;               // limited x-edges a in [0,TX]
+    static constexpr int YLW = TX + 2, YLH = TY + 1;               // limited y-edges b in [0,TY]
+    static constexpr int DW = TX, DH = TY + 2;                     // D: cols [0,TX), rows [-1,TY]
+    static constexpr int EW = TX + 2, EH = TY;                     // E: cols [-1,TX], rows [0,TY)
+    static constexpr int QBYTES = 3 * QPL * 8;
+    // shared-memory carve (in doubles), q buffers first (128-byte aligned)
+    static constexpr int QSTRIDE = (3 * QPL + 15) / 16 * 16;
+    static constexpr int NWORK = 2 * XEW * XEH + 2 * YEW * YEH + 2 * XLW * XLH + 2 * YLW * YLH +
+                                 DW * DH + EW * EH;
+    static size_t smem_bytes(int nbuf) { return (size_t)(nbuf * QSTRIDE + NWORK) * 8 + 64; }
+};
+
+// ------------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 3-D tiled bulk tensor copy global -> shared completing on an mbarrier.  Coordinates are
+// (x, y, plane) in elements; x * 8 bytes is a multiple of 16 (x is even by construction).
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z,
+                                            unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// bounded wait: gives up after ~2^22 polls (well beyond a normal copy), reports a timeout
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ bool not_finite(double x)
+{
+    return ((unsigned)(__double_as_longlong(x) >> 32) & 0x7ff00000u) == 0x7ff00000u;
+}
+
+// max of non-negative doubles on the integer pipe (bit patterns order like the values)
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
+{
+    return a > b ? a : b;
+}
+
+// ------------------------------------------------------------------------- the kernel
+// MED: 0 uniform medium (rho0, K0), 1 cell-wise aux planes.
+// STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered).
+template <int MED, int LIM, int TX, int TY, int NT, int STAGE>
+__global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
+{
+    using G = Geo<TX, TY>;
+    constexpr int NBUF = STAGE ? 2 : 1;
+    constexpr int NPER = (TX * TY + NT - 1) / NT;
+    extern __shared__ __align__(128) double smem[];
+    double* qbuf = smem;                            // NBUF x QSTRIDE
+    double* A1x = smem + NBUF * G::QSTRIDE;         // x-edge wave strengths, family 1 / 2
+    double* A2x = A1x + G::XEW * G::XEH;
+    double* B1y = A2x + G::XEW * G::XEH;            // y-edge wave strengths
+    double* B2y = B1y + G::YEW * G::YEH;
+    double* Sx = B2y + G::YEW * G::YEH;             // limited x-edges: const: M2-M1 / var: C_p
+    double* Px = Sx + G::XLW * G::XLH;              //                  const: M1+M2 / var: C_u
+    double* Sy = Px + G::XLW * G::XLH;
+    double* Py = Sy + G::YLW * G::YLH;
+    double* Dx = Py + G::YLW * G::YLH;              // x-fluctuation pressure into each cell
+    double* Ey = Dx + G::DW * G::DH;                // y-fluctuation pressure into each cell
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ey + G::EW * G::EH);
+    __shared__ unsigned long long s_tmax[2];   // per-tile speed max, double-buffered by tile parity
+    __shared__ int s_flag;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_tmax[0] = s_tmax[1] = 0ull;
+        s_flag = 0;
+        if (STAGE) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_barrier_init();
+        }
+    }
+    __syncthreads();
+
+    const CUtensorMap* tmaps = reinterpret_cast<const CUtensorMap*>(A.tmaps);
+    int my_flag = 0;
+    // thread 0 folds the tile maxima of consecutive tiles of the same run and flushes one
+    // 64-bit atomic max per run change (speeds are >= 0: bit patterns order like values)
+    int cur_run = -1;
+    unsigned long long cur_max = 0ull;
+    auto flush = [&]() {
+        if (cur_run >= 0 && cur_max)
+            atomicMax(reinterpret_cast<unsigned long long*>(A.smax) + cur_run, cur_max);
+    };
+    // uniform medium constants (once per CTA)
+    double Z0 = 0, c0 = 0, iZ = 0;
+    if (MED == 0) {
+        Z0 = sqrt(A.K0 * A.rho0);
+        c0 = sqrt(A.K0 / A.rho0);
+        iZ = 1.0 / Z0;
+    }
+
+    auto issue = [&](int t, int b) {
+        const TileDev T = A.tiles[t];
+        mbar_expect_tx(&bar[b], (unsigned)G::QBYTES);
+        tma_load_3d(qbuf + b * G::QSTRIDE, &tmaps[T.patch], T.x0, T.y0, 0, &bar[b]);
+    };
+    if (STAGE && tid == 0 && blockIdx.x < A.ntiles) issue(blockIdx.x, 0);
+
+    int it = 0;
+    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++it) {
+        const int b = STAGE ? (it & 1) : 0;
+        const TileDev T = A.tiles[t];
+        const PatchDev P = A.patches[T.patch];
+        const int tx = T.tx, ty = T.ty, x0 = T.x0, y0 = T.y0;
+        const int W = P.nx + 4;
+        const long long WH = (long long)W * (P.ny + 4);
+        double* sq = qbuf + b * G::QSTRIDE;
+        double* sp = sq;
+        double* su = sq + G::QPL;
+        double* sv = sq + 2 * G::QPL;
+
+        if (STAGE) {
+            const int tn = t + gridDim.x;
+            if (tid == 0 && tn < A.ntiles) issue(tn, b ^ 1);
+            bool ok = mbar_wait_bounded(&bar[b], (unsigned)((it >> 1) & 1));
+            if (__syncthreads_or(!ok)) {   // a copy never landed: report and stop this CTA
+                if (tid == 0) {
+                    atomicOr(A.err, ERR_TIMEOUT);
+                    // let the prefetch in flight (if any) land before the CTA exits
+                    if (tn < A.ntiles) mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+                }
+                return;
+            }
+        } else {
+            const double* src = A.qold + P.qoff;
+            for (int k = tid; k < 3 * G::QPL; k += NT) {
+                const int m = k / G::QPL, rem = k - m * G::QPL;
+                const int jj = rem / G::SW, ii = rem - jj * G::SW;
+                double v = 0.0;
+                if (ii < tx + 4 && jj < ty + 4) v = __ldg(src + m * WH + (long long)(y0 + jj) * W + (x0 + ii));
+                sq[k] = v;
+            }
+            __syncthreads();
+        }
+
+        // ---------------------------------------------------------------- per-tile constants
+        const double dt = __ldg(A.dt + P.run) * P.dtscale;
+        const double lx = dt * P.dxinv, ly = dt * P.dyinv;
+        const bool second = A.order == 2 && LIM >= 0;
+        const bool trans = A.transverse != 0;
+        const bool cw = A.transverse == 2 && A.order == 2;   // correction rides the transverse split
+        // medium access (MED == 1): aux plane k of the cell at tile-local (i, j)
+        const double* aux = MED ? A.aux + P.aoff : nullptr;
+        auto AX = [&](int k, int i, int j) -> double {
+            return __ldg(aux + k * WH + (long long)(y0 + j + 2) * W + (x0 + i + 2));
+        };
+
+        // ---------------------------------------------------------------- phase A: normal Riemann
+        // x-edge a (between cells a-1 and a) on rows r in [-1, ty]
+        {
+            const int w = tx + 3, n = (ty + 2) * w;
+            for (int k = tid; k < n; k += NT) {
+                const int r = k / w - 1, a = k - (r + 1) * w - 1;
+                const int iR = (a + 2) + (r + 2) * G::SW;
+                const double dp = sp[iR] - sp[iR - 1];
+                const double du = su[iR] - su[iR - 1];
+                double a1, a2;
+                if (MED == 0) {   // 2 alpha: du -/+ dp / Z
+                    a1 = fma(-dp, iZ, du);
+                    a2 = fma(dp, iZ, du);
+                } else {
+                    const double zr = AX(AUX_Z, a, r), zl = AX(AUX_Z, a - 1, r), is = AX(AUX_IXS, a, r);
+                    a1 = fma(zr, du, -dp) * is;
+                    a2 = fma(zl, du, dp) * is;
+                }
+                A1x[(r + 1) * G::XEW + (a + 1)] = a1;
+                A2x[(r + 1) * G::XEW + (a + 1)] = a2;
+            }
+        }
+        // y-edge b (between rows b-1 and b) on columns c in [-1, tx]
+        {
+            const int w = tx + 2, n = (ty + 3) * w;
+            for (int k = tid; k < n; k += NT) {
+                const int bb = k / w - 1, c = k - (bb + 1) * w - 1;
+                const int iR = (c + 2) + (bb + 2) * G::SW;
+                const double dp = sp[iR] - sp[iR - G::SW];
+                const double dv = sv[iR] - sv[iR - G::SW];
+                double b1, b2;
+                if (MED == 0) {
+                    b1 = fma(-dp, iZ, dv);
+                    b2 = fma(dp, iZ, dv);
+                } else {
+                    const double zr = AX(AUX_Z, c, bb), zl = AX(AUX_Z, c, bb - 1), is = AX(AUX_IYS, c, bb);
+                    b1 = fma(zr, dv, -dp) * is;
+                    b2 = fma(zl, dv, dp) * is;
+                }
+                B1y[(bb + 1) * G::YEW + (c + 1)] = b1;
+                B2y[(bb + 1) * G::YEW + (c + 1)] = b2;
+            }
+        }
+        // wave speeds seen by this tile (ring [-1,tx] x [-1,ty]): integer max of bit patterns,
+        // warp shuffle, shared atomic
+        if (MED == 0) {
+            if (tid == 0) s_tmax[it & 1] = (unsigned long long)__double_as_longlong(c0);
+        } else {
+            unsigned long long m = 0ull;
+            const int w = tx + 2, n = (ty + 2) * w;
+            for (int k = tid; k < n; k += NT) {
+                const int r = k / w - 1, c = k - (r + 1) * w - 1;
+                m = umax64(m, (unsigned long long)__double_as_longlong(AX(AUX_C, c, r)));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = umax64(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((tid & 31) == 0 && m) atomicMax(&s_tmax[it & 1], m);
+        }
+        __syncthreads();
+
+        // ---------------------------------------------------------------- phase B: limiter, correction
+        if (second) {
+            {
+                const int w = tx + 1, n = (ty + 2) * w;
+                for (int k = tid; k < n; k += NT) {
+                    const int r = k / w - 1, a = k - (r + 1) * w;
+                    const int e = (r + 1) * G::XEW + (a + 1);
+                    const double a1 = A1x[e], a2 = A2x[e];
+                    double m1, m2;
+                    if (MED == 0) {
+                        m1 = Lim<LIM>::f(a1, A1x[e + 1]);   // left-going: upwind edge a+1
+                        m2 = Lim<LIM>::f(a2, A2x[e - 1]);   // right-going: upwind edge a-1
+                        Sx[(r + 1) * G::XLW + a] = m2 - m1;
+                        Px[(r + 1) * G::XLW + a] = m1 + m2;
+                    } else {
+                        m1 = Lim<LIM>::f(a1, A1x[e + 1] * AX(AUX_FX1, a, r));
+                        m2 = Lim<LIM>::f(a2, A2x[e - 1] * AX(AUX_FX2, a, r));
+                        const double kl = fma(-lx, AX(AUX_C2, a - 1, r), AX(AUX_C, a - 1, r));
+                        const double kr = fma(-lx, AX(AUX_C2, a, r), AX(AUX_C, a, r));
+                        const double e1 = kl * m1, e2 = kr * m2;
+                        Sx[(r + 1) * G::XLW + a] = fma(AX(AUX_Z, a, r), e2, -(AX(AUX_Z, a - 1, r) * e1));
+                        Px[(r + 1) * G::XLW + a] = e1 + e2;
+                    }
+                }
+            }
+            {
+                const int w = tx + 2, n = (ty + 1) * w;
+                for (int k = tid; k < n; k += NT) {
+                    const int bb = k / w, c = k - bb * w - 1;
+                    const int e = (bb + 1) * G::YEW + (c + 1);
+                    const double b1 = B1y[e], b2 = B2y[e];
+                    double m1, m2;
+                    if (MED == 0) {
+                        m1 = Lim<LIM>::f(b1, B1y[e + G::YEW]);
+                        m2 = Lim<LIM>::f(b2, B2y[e - G::YEW]);
+                        Sy[bb * G::YLW + (c + 1)] = m2 - m1;
+                        Py[bb * G::YLW + (c + 1)] = m1 + m2;
+                    } else {
+                        m1 = Lim<LIM>::f(b1, B1y[e + G::YEW] * AX(AUX_FY1, c, bb));
+                        m2 = Lim<LIM>::f(b2, B2y[e - G::YEW] * AX(AUX_FY2, c, bb));
+                        const double kl = fma(-ly, AX(AUX_C2, c, bb - 1), AX(AUX_C, c, bb - 1));
+                        const double kr = fma(-ly, AX(AUX_C2, c, bb), AX(AUX_C, c, bb));
+                        const double e1 = kl * m1, e2 = kr * m2;
+                        Sy[bb * G::YLW + (c + 1)] = fma(AX(AUX_Z, c, bb), e2, -(AX(AUX_Z, c, bb - 1) * e1));
+                        Py[bb * G::YLW + (c + 1)] = e1 + e2;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---------------------------------------------------------------- phase C: per-cell terms
+        // uniform medium, with a = 2 alpha and M = phi(theta) a:
+        //   x-normal update  dp = -(lx K/2) ap - (lx kap Z/4) bp,  du = -(lx c/2) au - (lx kap/4) bu
+        //   ap = A2_w + A1_e, au = A2_w - A1_e, bp = S_e - S_w, bu = P_e - P_w,  kap = c (1 - lx c)
+        //   x-fluctuation pressure into the cell D = (K/2) (ap + (1 - lx c) bp)
+        // cell-wise medium: D = K ap + bp,  x-normal (K ap + bp/2, c au + bu/2)
+        double cK = 0, cpa = 0, cpb = 0, cua = 0, cub = 0, cpay = 0, cpby = 0, cva = 0, cvb = 0,
+               kDx = 0, kDy = 0;
+        if (MED == 0) {
+            const double kapx = c0 * (1.0 - lx * c0), kapy = c0 * (1.0 - ly * c0);
+            cpa = -0.5 * lx * A.K0;
+            cpb = -0.25 * lx * kapx * Z0;
+            cua = -0.5 * lx * c0;
+            cub = -0.25 * lx * kapx;
+            cpay = -0.5 * ly * A.K0;
+            cpby = -0.25 * ly * kapy * Z0;
+            cva = -0.5 * ly * c0;
+            cvb = -0.25 * ly * kapy;
+            kDx = cw ? 1.0 - lx * c0 : 0.0;
+            kDy = cw ? 1.0 - ly * c0 : 0.0;
+            (void)cK;
+        }
+        double dP[NPER], dU[NPER], dV[NPER];
+#pragma unroll
+        for (int n = 0; n < NPER; ++n) {
+            dP[n] = dU[n] = dV[n] = 0.0;
+            const int ci = tid + n * NT;
+            const int c = ci % TX, r = ci / TX;
+            if (ci >= TX * TY || c >= tx || r >= ty) continue;
+            const int ex = (r + 1) * G::XEW + (c + 1);
+            const int ey = (r + 1) * G::YEW + (c + 1);
+            const double apx = A2x[ex] + A1x[ex + 1], aux_ = A2x[ex] - A1x[ex + 1];
+            const double apy = B2y[ey] + B1y[ey + G::YEW], avy = B2y[ey] - B1y[ey + G::YEW];
+            double bpx = 0, bux = 0, bpy = 0, bvy = 0;
+            if (second) {
+                bpx = Sx[(r + 1) * G::XLW + c + 1] - Sx[(r + 1) * G::XLW + c];
+                bux = Px[(r + 1) * G::XLW + c + 1] - Px[(r + 1) * G::XLW + c];
+                bpy = Sy[(r + 1) * G::YLW + c + 1] - Sy[r * G::YLW + c + 1];
+                bvy = Py[(r + 1) * G::YLW + c + 1] - Py[r * G::YLW + c + 1];
+            }
+            if (MED == 0) {
+                if (trans) {
+                    Dx[(r + 1) * G::DW + c] = fma(kDx, bpx, apx);
+                    Ey[r * G::EW + c + 1] = fma(kDy, bpy, apy);
+                }
+                dP[n] = fma(cpb, bpx, cpa * apx) + fma(cpby, bpy, cpay * apy);
+                dU[n] = fma(cub, bux, cua * aux_);
+                dV[n] = fma(cvb, bvy, cva * avy);
+            } else {
+                const double Kc = AX(AUX_K, c, r), cc = AX(AUX_C, c, r);
+                if (trans) {
+                    Dx[(r + 1) * G::DW + c] = cw ? fma(Kc, apx, bpx) : Kc * apx;
+                    Ey[r * G::EW + c + 1] = cw ? fma(Kc, apy, bpy) : Kc * apy;
+                }
+                const double tpx = fma(0.5, bpx, Kc * apx), tux = fma(0.5, bux, cc * aux_);
+                const double tpy = fma(0.5, bpy, Kc * apy), tvy = fma(0.5, bvy, cc * avy);
+                dP[n] = fma(-lx, tpx, -(ly * tpy));
+                dU[n] = -lx * tux;
+                dV[n] = -ly * tvy;
+            }
+        }
+        // D on the ghost rows -1, ty and E on the ghost columns -1, tx (transverse only)
+        if (trans) {
+            const int n = 2 * (tx + ty);
+            for (int k = tid; k < n; k += NT) {
+                if (k < 2 * tx) {
+                    const int c = k % tx, r = (k < tx) ? -1 : ty;
+                    const int ex = (r + 1) * G::XEW + (c + 1);
+                    const double apx = A2x[ex] + A1x[ex + 1];
+                    const double bpx = second ? Sx[(r + 1) * G::XLW + c + 1] - Sx[(r + 1) * G::XLW + c] : 0.0;
+                    double d;
+                    if (MED == 0) d = fma(kDx, bpx, apx);
+                    else {
+                        const double Kc = AX(AUX_K, c, r);
+                        d = cw ? fma(Kc, apx, bpx) : Kc * apx;
+                    }
+                    Dx[(r + 1) * G::DW + c] = d;
+                } else {
+                    const int kk = k - 2 * tx;
+                    const int r = kk % ty, c = (kk < ty) ? -1 : tx;
+                    const int ey = (r + 1) * G::YEW + (c + 1);
+                    const double apy = B2y[ey] + B1y[ey + G::YEW];
+                    const double bpy = second ? Sy[(r + 1) * G::YLW + c + 1] - Sy[r * G::YLW + c + 1] : 0.0;
+                    double e;
+                    if (MED == 0) e = fma(kDy, bpy, apy);
+                    else {
+                        const double Kc = AX(AUX_K, c, r);
+                        e = cw ? fma(Kc, apy, bpy) : Kc * apy;
+                    }
+                    Ey[r * G::EW + c + 1] = e;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---------------------------------------------------------------- phase C2 (cell-wise medium):
+        // transverse fluxes at the y-edges (from D) and the x-edges (from E); written over the
+        // wave-strength arrays, which are dead now
+        double* Gp = B1y;
+        double* Gv = B2y;
+        double* Fp = A1x;
+        double* Fu = A2x;
+        if (MED == 1 && trans) {
+            {   // y-edge jj in [0, ty] of column c in [0, tx): lo = (c, jj-1), hi = (c, jj)
+                const int n = (ty + 1) * tx;
+                for (int k = tid; k < n; k += NT) {
+                    const int jj = k / tx, c = k - jj * tx;
+                    const double dlo = Dx[jj * G::DW + c], dhi = Dx[(jj + 1) * G::DW + c];
+                    const double w = -0.5 * lx * AX(AUX_IYS, c, jj);
+                    const double khi = AX(AUX_K, c, jj), klo = AX(AUX_K, c, jj - 1);
+                    const double chi = AX(AUX_C, c, jj), clo = AX(AUX_C, c, jj - 1);
+                    Gp[jj * TX + c] = w * fma(khi, dlo, -(klo * dhi));
+                    Gv[jj * TX + c] = w * fma(chi, dlo, clo * dhi);
+                }
+            }
+            {   // x-edge a in [0, tx] of row r in [0, ty): lo = (a-1, r), hi = (a, r)
+                const int w1 = tx + 1, n = ty * w1;
+                for (int k = tid; k < n; k += NT) {
+                    const int r = k / w1, a = k - r * w1;
+                    const double elo = Ey[r * G::EW + a], ehi = Ey[r * G::EW + a + 1];
+                    const double w = -0.5 * ly * AX(AUX_IXS, a, r);
+                    const double khi = AX(AUX_K, a, r), klo = AX(AUX_K, a - 1, r);
+                    const double chi = AX(AUX_C, a, r), clo = AX(AUX_C, a - 1, r);
+                    Fp[r * (TX + 1) + a] = w * fma(khi, elo, -(klo * ehi));
+                    Fu[r * (TX + 1) + a] = w * fma(chi, elo, clo * ehi);
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---------------------------------------------------------------- phase D: update, store
+        double kT = 0, kU = 0;
+        if (MED == 0 && trans) {
+            kT = 0.125 * lx * ly * c0 * A.K0;
+            kU = 0.125 * lx * ly * c0 * c0;
+        }
+        double* dst = A.qnew + P.qoff;
+#pragma unroll
+        for (int n = 0; n < NPER; ++n) {
+            const int ci = tid + n * NT;
+            const int c = ci % TX, r = ci / TX;
+            if (ci >= TX * TY || c >= tx || r >= ty) continue;
+            const int iq = (c + 2) + (r + 2) * G::SW;
+            double p = sp[iq] + dP[n], u = su[iq] + dU[n], v = sv[iq] + dV[n];
+            if (trans) {
+                if (MED == 0) {
+                    const double dc = Dx[(r + 1) * G::DW + c], dn = Dx[(r + 2) * G::DW + c],
+                                 ds = Dx[r * G::DW + c];
+                    const double ec = Ey[r * G::EW + c + 1], ee = Ey[r * G::EW + c + 2],
+                                 ew = Ey[r * G::EW + c];
+                    const double tp = fma(2.0, dc + ec, -((dn + ds) + (ee + ew)));
+                    p = fma(kT, tp, p);
+                    u = fma(kU, ee - ew, u);
+                    v = fma(kU, dn - ds, v);
+                } else {
+                    const double fpe = Fp[r * (TX + 1) + c + 1], fpw = Fp[r * (TX + 1) + c];
+                    const double gpn = Gp[(r + 1) * TX + c], gps = Gp[r * TX + c];
+                    p = fma(-lx, fpe - fpw, fma(-ly, gpn - gps, p));
+                    u = fma(-lx, Fu[r * (TX + 1) + c + 1] - Fu[r * (TX + 1) + c], u);
+                    v = fma(-ly, Gv[(r + 1) * TX + c] - Gv[r * TX + c], v);
+                }
+            }
+            if (not_finite(p) | not_finite(u) | not_finite(v)) my_flag |= ERR_NAN;
+            const long long o = (long long)(y0 + r + 2) * W + (x0 + c + 2);
+            dst[o] = p;
+            dst[WH + o] = u;
+            dst[2 * WH + o] = v;
+        }
+        __syncthreads();   // the staged tile and work arrays are reused by the next tile
+        if (tid == 0) {
+            const unsigned long long m = s_tmax[it & 1];
+            s_tmax[it & 1] = 0ull;   // next written two tiles later, after two more barriers
+            if (P.run != cur_run) {
+                flush();
+                cur_run = P.run;
+                cur_max = m;
+            } else {
+                cur_max = umax64(cur_max, m);
+            }
+        }
+    }
+
+    // ---------------------------------------------------------------- CFL and error flags
+    if (tid == 0) flush();
+    if (my_flag) atomicOr(&s_flag, my_flag);
+    __syncthreads();
+    if (tid == 0 && s_flag) atomicOr(A.err, s_flag);
+}
+
+}  // namespace claw
+
+namespace claw {
+
+// kernel pointer and dynamic shared memory of one configuration
+struct StepKernel {
+    void (*fn)(const StepArgs);
+    size_t smem;
+    int nt;
+};
+
+template <int MED, int LIM, int TX, int TY, int NT, int STAGE>
+StepKernel step_kernel_entry()
+{
+    StepKernel k;
+    k.fn = step_kernel<MED, LIM, TX, TY, NT, STAGE>;
+    k.smem = Geo<TX, TY>::smem_bytes(STAGE ? 2 : 1);
+    k.nt = NT;
+    return k;
+}
+
+// all tile shapes and stagings of one medium and limiter
+template <int MED, int LIM>
+StepKernel step_kernel_select(int tx, int ty, int staging)
+{
+    if (tx == 32 && ty == 32) return staging ? step_kernel_entry<MED, LIM, 32, 32, 256, 1>()
+                                             : step_kernel_entry<MED, LIM, 32, 32, 256, 0>();
+    if (tx == 32 && ty == 16) return staging ? step_kernel_entry<MED, LIM, 32, 16, 256, 1>()
+                                             : step_kernel_entry<MED, LIM, 32, 16, 256, 0>();
+    if (tx == 16 && ty == 16) return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1>()
+                                             : step_kernel_entry<MED, LIM, 16, 16, 128, 0>();
+    return StepKernel{nullptr, 0, 0};
+}
+
+template <int MED>
+StepKernel step_kernel_for(int lim, int tx, int ty, int staging)
+{
+    switch (lim) {
+    case CLAW_LIM_NONE: return step_kernel_select<MED, CLAW_LIM_NONE>(tx, ty, staging);
+    case CLAW_LIM_MINMOD: return step_kernel_select<MED, CLAW_LIM_MINMOD>(tx, ty, staging);
+    case CLAW_LIM_SUPERBEE: return step_kernel_select<MED, CLAW_LIM_SUPERBEE>(tx, ty, staging);
+    case CLAW_LIM_VANLEER: return step_kernel_select<MED, CLAW_LIM_VANLEER>(tx, ty, staging);
+    case CLAW_LIM_MC: return step_kernel_select<MED, CLAW_LIM_MC>(tx, ty, staging);
+    }
+    return StepKernel{nullptr, 0, 0};
+}
+
+StepKernel step_kernel_uniform(int lim, int tx, int ty, int staging);
+StepKernel step_kernel_cellwise(int lim, int tx, int ty, int staging);
+
+}  // namespace claw

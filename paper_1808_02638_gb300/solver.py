@@ -1,0 +1,204 @@
+"""Host orchestration of the level-steps of one or many runs on libclaw.so.
+
+It owns the device pools (torch tensors) and sequences C-ABI calls in the order of the AMR
+time step of Sec. 2.2: fill the ghosts of level L, take one level-step, then R_L substeps of
+level L+1 whose ghosts are interpolated in space and time from level L, then overwrite the
+covered cells of level L with the fine average ("updating").  The level-0 time step follows
+Eq. cfl from the largest wave speed the previous coarse step saw, computed on the device, so
+a coarse step is a fixed launch sequence that a CUDA graph replays.  No arithmetic of the
+method happens here.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import claw, inputs
+
+MBC = claw.CLAW_MBC
+
+
+def _align(n, a=inputs.ALIGN):
+    return (n + a - 1) // a * a
+
+
+class Hierarchy:
+    """Device state of `runs` (a list of inputs.Run) on one context.
+
+    q0[r][L], rho[r][L], K[r][L]: numpy pools of run r, level L in the inputs layout (rho, K
+    only for a cell-wise medium; a uniform medium passes rho0, K0).  All runs' pools of a level
+    are concatenated into one device pool per level."""
+
+    def __init__(self, runs, q0, rho=None, K=None, rho0=1.0, K0=4.0, device=0, tiling=None):
+        self.runs = runs
+        self.nruns = len(runs)
+        self.nlev = max(len(r.levels) for r in runs)
+        self.medium = 0 if rho is None else 1
+        self.dev = torch.device("cuda", device)
+        probs = []
+        for r in runs:
+            p = claw.claw_problem()
+            p.xlo, p.ylo, p.xhi, p.yhi = r.xlo, r.ylo, r.xhi, r.yhi
+            p.nx0, p.ny0 = r.levels[0].NX, r.levels[0].NY
+            p.nlev = len(r.levels)
+            for L, lev in enumerate(r.levels):
+                p.ratio[L] = lev.ratio if L else 1
+            p.cfl = r.cfl
+            p.limiter, p.order, p.transverse = r.limiter, r.order, r.transverse
+            for s in range(4):
+                p.bc[s] = r.bc[s]
+            p.medium = self.medium
+            p.rho0, p.K0 = rho0, K0
+            probs.append(p)
+        self.ctx = claw.claw_create(probs, device)
+        self.q = []        # per level [A, B]
+        self.cur = []
+        self.aux = []
+        self.rho = []
+        self.K = []
+        self.boxes = []    # per level list of claw_box
+        self.layout = []   # per level list of (run, qbase, cbase)
+        for L in range(self.nlev):
+            boxes, qb, cb = [], 0, 0
+            lay = []
+            for ri, r in enumerate(runs):
+                if L >= len(r.levels):
+                    continue
+                lev = r.levels[L]
+                lay.append((ri, qb, cb))
+                for n, b in enumerate(lev.boxes):
+                    bx = claw.claw_box()
+                    bx.run = ri
+                    bx.ilo, bx.jlo, bx.nx, bx.ny = (int(v) for v in b)
+                    bx.qoff = qb + int(lev.qoff[n])
+                    bx.coff = cb + int(lev.coff[n])
+                    boxes.append(bx)
+                qb += _align(lev.qsize)
+                cb += _align(lev.csize)
+            self.boxes.append(boxes)
+            self.layout.append(lay)
+            claw.claw_set_level(self.ctx, L, boxes)
+            if tiling is not None:
+                claw.claw_set_tiling(self.ctx, L, *tiling)
+            qh = np.zeros(max(qb, inputs.ALIGN))
+            for (ri, qbase, _) in lay:
+                a = np.asarray(q0[ri][L], dtype=np.float64)
+                qh[qbase:qbase + a.size] = a
+            A = torch.from_numpy(qh).to(self.dev)
+            self.q.append([A, torch.zeros_like(A)])
+            self.cur.append(0)
+            if self.medium:
+                rh = np.ones(max(cb, inputs.ALIGN))
+                kh = np.ones(max(cb, inputs.ALIGN))
+                for (ri, _, cbase) in lay:
+                    a = np.asarray(rho[ri][L], dtype=np.float64)
+                    k = np.asarray(K[ri][L], dtype=np.float64)
+                    rh[cbase:cbase + a.size] = a
+                    kh[cbase:cbase + k.size] = k
+                self.rho.append(torch.from_numpy(rh).to(self.dev))
+                self.K.append(torch.from_numpy(kh).to(self.dev))
+                aux = torch.zeros(claw.CLAW_NAUX * rh.size, dtype=torch.float64, device=self.dev)
+                claw.claw_medium_aux(self.ctx, L, self.rho[L], self.K[L], aux)
+                self.aux.append(aux)
+            else:
+                self.rho.append(None)
+                self.K.append(None)
+                self.aux.append(None)
+        self.dt = torch.zeros(self.nruns, dtype=torch.float64, device=self.dev)
+        self.smax = torch.zeros(self.nruns, dtype=torch.float64, device=self.dev)
+        self.patchwise = False
+
+    # -------------------------------------------------------------- stepping
+    def ratio(self, L):
+        return self.runs[0].levels[L].ratio
+
+    def init_dt(self):
+        """dt from Eq. cfl with the largest cell speed on any level (before the first step)."""
+        self.smax.zero_()
+        for L in range(self.nlev):
+            claw.claw_cfl_max(self.ctx, L, self.aux[L], self.smax)
+        claw.claw_dt_update(self.ctx, 0, self.smax, self.dt)
+
+    def step_level(self, L, stream=None):
+        src, dst = self.q[L][self.cur[L]], self.q[L][1 - self.cur[L]]
+        fn = claw.claw_level_step_patchwise if self.patchwise else claw.claw_level_step
+        fn(self.ctx, L, src, dst, self.aux[L], self.dt, self.smax, stream)
+
+    def advance(self, L, cold=None, cnew=None, tau=0.0, stream=None):
+        q = self.q[L][self.cur[L]]
+        claw.claw_fill_ghost(self.ctx, L, q, cold, cnew, tau, stream)
+        self.step_level(L, stream)
+        old, new = self.q[L][self.cur[L]], self.q[L][1 - self.cur[L]]
+        if L + 1 < self.nlev:
+            r = self.ratio(L + 1)
+            for k in range(r):
+                self.advance(L + 1, old, new, k / r, stream)
+            claw.claw_average_down(self.ctx, L + 1, self.q[L + 1][self.cur[L + 1]], new, stream)
+        self.cur[L] ^= 1
+
+    def coarse_step(self, stream=None):
+        self.advance(0, stream=stream)
+        claw.claw_dt_update(self.ctx, 0, self.smax, self.dt, stream)
+
+    def launches_per_coarse_step(self):
+        """kernels one coarse step enqueues (counted from the library's own counter)."""
+        before = claw.claw_launch_count(self.ctx)
+        state = (list(self.cur), self.dt.clone(), self.smax.clone(), [ [a.clone() for a in p] for p in self.q])
+        self.coarse_step()
+        n = claw.claw_launch_count(self.ctx) - before
+        self.cur, dt, sm, qs = state
+        self.dt.copy_(dt)
+        self.smax.copy_(sm)
+        for L in range(self.nlev):
+            for k in range(2):
+                self.q[L][k].copy_(qs[L][k])
+        return n
+
+    def capture(self, ncoarse: int = 2):
+        """CUDA graph of `ncoarse` coarse steps (an even count returns every level to the same
+        buffer parity, so the graph can be replayed)."""
+        s = torch.cuda.Stream(device=self.dev)
+        s.wait_stream(torch.cuda.current_stream(self.dev))
+        g = torch.cuda.CUDAGraph()
+        cur0 = list(self.cur)
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(ncoarse):
+                self.coarse_step(stream=s)
+        torch.cuda.current_stream(self.dev).wait_stream(s)
+        if self.cur != cur0:
+            raise ValueError("capture an even number of coarse steps")
+        return g
+
+    def sync_status(self):
+        return claw.claw_sync_status(self.ctx)
+
+    # -------------------------------------------------------------- readback
+    def pool(self, L):
+        return self.q[L][self.cur[L]]
+
+    def interior(self, run, L, n, pool=None):
+        """(3, ny, nx) numpy interior of box n of run `run` on level L."""
+        lev = self.runs[run].levels[L]
+        qbase = [qb for (ri, qb, _) in self.layout[L] if ri == run][0]
+        b = lev.boxes[n]
+        nx, ny = int(b[2]), int(b[3])
+        off = qbase + int(lev.qoff[n])
+        P = (self.pool(L) if pool is None else pool)
+        v = P[off:off + 3 * (nx + 4) * (ny + 4)].view(3, ny + 4, nx + 4)
+        return v[:, MBC:MBC + ny, MBC:MBC + nx].cpu().numpy()
+
+    def level_numpy(self, run, L):
+        lev = self.runs[run].levels[L]
+        qbase = [qb for (ri, qb, _) in self.layout[L] if ri == run][0]
+        return self.pool(L)[qbase:qbase + lev.qsize].cpu().numpy()
+
+    def close(self):
+        if self.ctx:
+            claw.claw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

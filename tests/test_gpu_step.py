@@ -1,0 +1,259 @@
+"""GPU parity of the fused level-step (C ABI) against the CPU oracle.
+
+Tolerances: max |GPU - oracle| <= 1e-12 max|q| after one step and <= 1e-10 max|q| after 50-100
+steps (the GPU uses fused multiply-adds, division-free limiter forms and reciprocal
+multiplies; the oracle plain IEEE operations in textbook order)."""
+import numpy as np
+import pytest
+
+from paper_1808_02638_gb300 import inputs
+
+from gpu_helpers import M, lib_ready, oracle_single, rel_err, single_grid
+
+pytestmark = pytest.mark.gpu
+
+TOL1, TOLN = 1e-12, 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib_ready()
+
+
+def _hier(run, q, rho=None, K=None, rho0=1.0, K0=4.0, tiling=None):
+    from paper_1808_02638_gb300.solver import Hierarchy
+    if rho is None:
+        return Hierarchy([run], [[q]], rho0=rho0, K0=K0, tiling=tiling)
+    return Hierarchy([run], [[q]], [[rho]], [[K]], tiling=tiling)
+
+
+def _uniform_planes(n, rho0=1.0, K0=4.0):
+    return np.full((n + 4, n + 4), rho0), np.full((n + 4, n + 4), K0)
+
+
+@pytest.mark.parametrize("tiling", [(32, 32, 1), (32, 32, 0), (32, 16, 1), (16, 16, 0), (16, 16, 1)])
+def test_uniform_pulse_100x100_one_and_50_steps(orc, tiling):
+    run, q = single_grid(100)
+    H = _hier(run, q, tiling=tiling)
+    H.init_dt()
+    assert float(H.dt[0]) == pytest.approx(0.9 * 0.02 / 2.0, rel=1e-15)
+    rho, K = _uniform_planes(100)
+    H.coarse_step()
+    want, _ = oracle_single(orc, run, q, rho, K, 1, dt=0.009)
+    got = H.interior(0, 0)
+    assert rel_err(got, want) <= TOL1
+    for _ in range(49):
+        H.coarse_step()
+    want, dts = oracle_single(orc, run, q, rho, K, 50)
+    assert rel_err(H.interior(0, 0), want) <= TOLN
+    assert H.sync_status() == 0
+    assert float(H.smax[0]) == 0.0 and float(H.dt[0]) == pytest.approx(dts[-1], rel=1e-15)
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("order,transverse", [(2, 2), (2, 1), (2, 0), (1, 0), (1, 1)])
+def test_schemes_random_data_one_step(orc, limiter, order, transverse):
+    n = 36
+    run, q = single_grid(n, pulse=False, seed=100 + limiter, limiter=limiter, order=order, transverse=transverse)
+    H = _hier(run, q, rho0=1.3, K0=2.7, tiling=(16, 16, 1))
+    H.dt.fill_(0.004)
+    H.coarse_step()
+    rho, K = _uniform_planes(n, 1.3, 2.7)
+    want, _ = oracle_single(orc, run, q, rho, K, 1, dt=0.004)
+    assert rel_err(H.interior(0, 0), want) <= TOL1
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (2, 2, 2, 2), (2, 0, 1, 1)])
+def test_boundary_conditions_ten_steps(orc, bc):
+    n = 40
+    run, q = single_grid(n, pulse=False, seed=7, bc=bc)
+    H = _hier(run, q, tiling=(16, 16, 0))
+    H.init_dt()
+    for _ in range(10):
+        H.coarse_step()
+    rho, K = _uniform_planes(n)
+    want, _ = oracle_single(orc, run, q, rho, K, 10)
+    assert rel_err(H.interior(0, 0), want) <= TOLN
+
+
+@pytest.mark.parametrize("tiling", [(32, 32, 1), (32, 16, 0), (16, 16, 1)])
+def test_cellwise_medium_one_and_100_steps(orc, tiling):
+    n = 64
+    run, rho2, K2 = inputs.config3(n)
+    run2, q = single_grid(n)
+    lev = run2.levels[0]
+    rho = inputs.coef_pool(lev, rho2, 1)
+    K = inputs.coef_pool(lev, K2, 1)
+    H = _hier(run2, q, rho, K, tiling=tiling)
+    H.init_dt()
+    rp = inputs.box_view(rho, 0, n, n, 1)[0]
+    kp = inputs.box_view(K, 0, n, n, 1)[0]
+    smax = float(np.sqrt(K2 / rho2).max())
+    assert float(H.dt[0]) == pytest.approx(0.9 * (2.0 / n) / smax, rel=1e-15)
+    H.coarse_step()
+    want, _ = oracle_single(orc, run2, q, rp, kp, 1)
+    assert rel_err(H.interior(0, 0), want) <= TOL1
+    for _ in range(99):
+        H.coarse_step()
+    want, _ = oracle_single(orc, run2, q, rp, kp, 100)
+    assert rel_err(H.interior(0, 0), want) <= TOLN
+    assert H.sync_status() == 0
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2, 3, 4])
+def test_uniform_state_preserved_bit_exactly_cellwise(limiter):
+    n = 48
+    run, rho2, K2 = inputs.config3(n)
+    run2, _ = single_grid(n, limiter=limiter)
+    lev = run2.levels[0]
+    q = np.zeros(lev.qsize)
+    v = inputs.box_view(q, 0, n, n, 3)
+    v[0], v[1], v[2] = 1.25, -0.5, 0.75
+    H = _hier(run2, q, inputs.coef_pool(lev, rho2, 1), inputs.coef_pool(lev, K2, 1), tiling=(16, 16, 1))
+    H.init_dt()
+    for _ in range(5):
+        H.coarse_step()
+    got = H.interior(0, 0)
+    assert np.all(got[0] == 1.25) and np.all(got[1] == -0.5) and np.all(got[2] == 0.75)
+
+
+def test_tiled_level_and_patchwise_path_match_oracle_and_each_other(orc):
+    # 128 x 128 as 16 patches of 32 x 32 (the uniform-batch layout at a size the oracle
+    # finishes quickly): same-level ghost copies + extrapolation, fused vs one launch per box
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config1(128, 32)
+    lev = run.levels[0]
+    q = inputs.init_q(run, lev)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    Hp = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    Hp.patchwise = True
+    for h in (H, Hp):
+        h.init_dt()
+        for _ in range(20):
+            h.coarse_step()
+    for nb in range(len(lev.boxes)):
+        assert np.array_equal(H.interior(0, nb), Hp.interior(0, nb))
+    # the oracle on the same single grid
+    srun, sq = single_grid(128)
+    rho, K = _uniform_planes(128)
+    want, _ = oracle_single(orc, srun, sq, rho, K, 20)
+    got = np.zeros_like(want)
+    for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
+        got[:, jlo:jlo + bny, ilo:ilo + bnx] = H.interior(0, nb)
+    assert rel_err(got, want) <= TOLN
+
+
+def test_graph_replay_equals_eager():
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config1(256, 32)
+    q = inputs.init_q(run, run.levels[0])
+    A = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    B = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    for h in (A, B):
+        h.init_dt()
+        h.coarse_step()
+        h.coarse_step()   # warm-up outside capture (descriptors, attributes)
+    g = B.capture(2)
+    for _ in range(3):
+        g.replay()
+        A.coarse_step()
+        A.coarse_step()
+    import torch
+    torch.cuda.synchronize()
+    assert np.array_equal(A.level_numpy(0, 0), B.level_numpy(0, 0))
+
+
+def test_full_size_uniform_batch_sampled_parity_and_symmetry(orc):
+    # 2048^2 as 4096 patches of 32 x 32, the configuration the benchmark times: ghosts equal
+    # the edge-padded global field, sampled patches equal the oracle's one-patch step from the
+    # same input, and after 200 steps the radial pulse keeps its symmetries
+    from paper_1808_02638_gb300.solver import Hierarchy
+    import torch
+    run = inputs.config1()
+    lev = run.levels[0]
+    q = inputs.init_q(run, lev)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    rng = np.random.default_rng(5)
+    sample = rng.choice(len(lev.boxes), 48, replace=False)
+    ones = np.ones((36, 36))
+    for step in range(200):
+        check = step in (0, 100, 199)
+        if check:
+            claw = __import__("paper_1808_02638_gb300.claw", fromlist=["claw"])
+            claw.claw_fill_ghost(H.ctx, 0, H.pool(0))
+            before = H.pool(0).cpu().numpy()
+            dt = float(H.dt[0])
+        H.coarse_step()
+        if check:
+            after = H.pool(0).cpu().numpy()
+            if step == 0:
+                # ghosts of every patch equal the edge-extrapolated global field
+                glob = np.zeros((3, 2048, 2048))
+                for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
+                    glob[:, jlo:jlo + 32, ilo:ilo + 32] = inputs.box_view(before, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
+                gp = np.pad(glob, ((0, 0), (M, M), (M, M)), mode="edge")
+                for nb in sample:
+                    ilo, jlo = int(lev.boxes[nb][0]), int(lev.boxes[nb][1])
+                    assert np.array_equal(inputs.box_view(before, lev.qoff[nb], 32, 32, 3),
+                                          gp[:, jlo:jlo + 36, ilo:ilo + 36])
+            for nb in sample:
+                qin = inputs.box_view(before, lev.qoff[nb], 32, 32, 3).copy()
+                want, _ = orc.step(qin, ones, 4 * ones, lev.dx, lev.dy, dt)
+                got = inputs.box_view(after, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
+                scale = np.abs(after).max()
+                assert np.abs(got - want[:, M:-M, M:-M]).max() <= TOL1 * scale
+    glob = np.zeros((3, 2048, 2048))
+    final = H.pool(0).cpu().numpy()
+    for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
+        glob[:, jlo:jlo + 32, ilo:ilo + 32] = inputs.box_view(final, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
+    p, u, v = glob
+    tol = 1e-12 * np.abs(glob).max()
+    assert np.abs(p - p.T).max() <= tol and np.abs(p - p[:, ::-1]).max() <= tol
+    assert np.abs(u - v.T).max() <= tol and np.abs(u + u[:, ::-1]).max() <= tol
+    assert H.sync_status() == 0
+
+
+def test_errors_are_status_codes():
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, q = single_grid(32)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    bad = claw.claw_box()
+    bad.run, bad.ilo, bad.jlo, bad.nx, bad.ny, bad.qoff, bad.coff = 0, 16, 0, 32, 32, 0, 0
+    with pytest.raises(claw.ClawError) as e:
+        claw.claw_set_level(H.ctx, 0, [bad])          # outside the domain
+    assert e.value.status == claw.CLAW_EINVAL
+    b1 = claw.claw_box()
+    b1.run, b1.ilo, b1.jlo, b1.nx, b1.ny, b1.qoff, b1.coff = 0, 0, 0, 16, 16, 0, 0
+    b2 = claw.claw_box()
+    b2.run, b2.ilo, b2.jlo, b2.nx, b2.ny, b2.qoff, b2.coff = 0, 8, 8, 16, 16, 4096, 4096
+    with pytest.raises(claw.ClawError) as e:
+        claw.claw_set_level(H.ctx, 0, [b1, b2])       # overlapping boxes
+    assert e.value.status == claw.CLAW_EINVAL
+    with pytest.raises(claw.ClawError) as e:
+        claw.claw_set_level(H.ctx, 1, [b1])           # level 0 was cleared by the failed set
+    assert e.value.status in (claw.CLAW_ESTATE, claw.CLAW_EINVAL)
+
+
+def test_nan_input_is_reported_not_trapped():
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, q = single_grid(32)
+    inputs.box_view(q, 0, 32, 32, 3)[0, 10, 10] = np.nan
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    H.coarse_step()
+    assert H.sync_status() == claw.CLAW_ENAN
+    assert H.sync_status() == claw.CLAW_OK   # reading clears the flag
+
+
+def test_cfl_violation_is_reported():
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, q = single_grid(32)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    H.dt.mul_(1.5)                      # nu = 1.35 > 1
+    H.coarse_step()
+    assert H.sync_status() == claw.CLAW_ECFL
