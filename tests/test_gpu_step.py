@@ -40,12 +40,12 @@ def test_uniform_pulse_100x100_one_and_50_steps(orc, tiling):
     rho, K = _uniform_planes(100)
     H.coarse_step()
     want, _ = oracle_single(orc, run, q, rho, K, 1, dt=0.009)
-    got = H.interior(0, 0)
+    got = H.interior(0, 0, 0)
     assert rel_err(got, want) <= TOL1
     for _ in range(49):
         H.coarse_step()
     want, dts = oracle_single(orc, run, q, rho, K, 50)
-    assert rel_err(H.interior(0, 0), want) <= TOLN
+    assert rel_err(H.interior(0, 0, 0), want) <= TOLN
     assert H.sync_status() == 0
     assert float(H.smax[0]) == 0.0 and float(H.dt[0]) == pytest.approx(dts[-1], rel=1e-15)
 
@@ -60,7 +60,7 @@ def test_schemes_random_data_one_step(orc, limiter, order, transverse):
     H.coarse_step()
     rho, K = _uniform_planes(n, 1.3, 2.7)
     want, _ = oracle_single(orc, run, q, rho, K, 1, dt=0.004)
-    assert rel_err(H.interior(0, 0), want) <= TOL1
+    assert rel_err(H.interior(0, 0, 0), want) <= TOL1
 
 
 @pytest.mark.parametrize("bc", [(1, 1, 1, 1), (2, 2, 2, 2), (2, 0, 1, 1)])
@@ -73,7 +73,7 @@ def test_boundary_conditions_ten_steps(orc, bc):
         H.coarse_step()
     rho, K = _uniform_planes(n)
     want, _ = oracle_single(orc, run, q, rho, K, 10)
-    assert rel_err(H.interior(0, 0), want) <= TOLN
+    assert rel_err(H.interior(0, 0, 0), want) <= TOLN
 
 
 @pytest.mark.parametrize("tiling", [(32, 32, 1), (32, 16, 0), (16, 16, 1)])
@@ -92,11 +92,11 @@ def test_cellwise_medium_one_and_100_steps(orc, tiling):
     assert float(H.dt[0]) == pytest.approx(0.9 * (2.0 / n) / smax, rel=1e-15)
     H.coarse_step()
     want, _ = oracle_single(orc, run2, q, rp, kp, 1)
-    assert rel_err(H.interior(0, 0), want) <= TOL1
+    assert rel_err(H.interior(0, 0, 0), want) <= TOL1
     for _ in range(99):
         H.coarse_step()
     want, _ = oracle_single(orc, run2, q, rp, kp, 100)
-    assert rel_err(H.interior(0, 0), want) <= TOLN
+    assert rel_err(H.interior(0, 0, 0), want) <= TOLN
     assert H.sync_status() == 0
 
 
@@ -113,7 +113,7 @@ def test_uniform_state_preserved_bit_exactly_cellwise(limiter):
     H.init_dt()
     for _ in range(5):
         H.coarse_step()
-    got = H.interior(0, 0)
+    got = H.interior(0, 0, 0)
     assert np.all(got[0] == 1.25) and np.all(got[1] == -0.5) and np.all(got[2] == 0.75)
 
 
@@ -132,14 +132,14 @@ def test_tiled_level_and_patchwise_path_match_oracle_and_each_other(orc):
         for _ in range(20):
             h.coarse_step()
     for nb in range(len(lev.boxes)):
-        assert np.array_equal(H.interior(0, nb), Hp.interior(0, nb))
+        assert np.array_equal(H.interior(0, 0, nb), Hp.interior(0, 0, nb))
     # the oracle on the same single grid
     srun, sq = single_grid(128)
     rho, K = _uniform_planes(128)
     want, _ = oracle_single(orc, srun, sq, rho, K, 20)
     got = np.zeros_like(want)
     for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
-        got[:, jlo:jlo + bny, ilo:ilo + bnx] = H.interior(0, nb)
+        got[:, jlo:jlo + bny, ilo:ilo + bnx] = H.interior(0, 0, nb)
     assert rel_err(got, want) <= TOLN
 
 
