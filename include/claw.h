@@ -149,6 +149,26 @@ int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q
 int claw_level_step_patchwise(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
                               const double* aux, const double* dt, double* smax, void* stream);
 
+/* The fused level-step of one box that allocates nothing: for callers that cannot allocate
+ * device memory where they step (inside a CUDA-graph capture, under a host application's own
+ * device-memory pool, in a loop that cannot take cudaMalloc's implicit synchronisation).
+ * The paper has no counterpart; it exists for those callers.
+ * q_old / q_new hold one box (p, u, v planes of (nx+4) x (ny+4) doubles at offset 0; the
+ * ghosts of q_old are filled by the caller); aux (cell-wise medium, CLAW_NAUX planes at
+ * offset 0) or NULL for the uniform medium rho0, K0; dt[0] the time step; smax[0] receives
+ * the max wave speed (max-accumulated, as in claw_level_step).  32 x 32 tiles, cooperative
+ * staging.  The scratch (box descriptor, tile table, error word) is a fixed 256 KiB device
+ * array that every device loading the library keeps until exit, so at most 16367 tiles of
+ * 32 x 32 cells fit (e.g. 4064 x 4096 cells, not 4096 x 4096): larger boxes, and nx or ny
+ * above 4096, return CLAW_EINVAL before any launch.  The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  Every call
+ * rewrites the whole scratch it uses (device errors of this path are not reported), and all
+ * calls share the one array: calls whose kernels overlap on the GPU (other streams, other
+ * threads) race.  Errors: CLAW_EINVAL, CLAW_ECUDA. */
+int claw_level_step_noalloc(int32_t nx, int32_t ny, double dx, double dy, int32_t limiter, int32_t order,
+                            int32_t transverse, double rho0, double K0, const double* q_old, double* q_new,
+                            const double* aux, const double* dt, double* smax, void* stream);
+
 /* Coarse cells of level fine_level-1 covered by level fine_level := mean of their ratio^2
  * fine cells (the "updating" of Sec. 2.2-2.3). */
 int claw_average_down(claw_ctx* ctx, int32_t fine_level, const double* q_fine, double* q_coarse,

@@ -58,6 +58,8 @@ _SIGNATURES = {
     "claw_dt_update": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_level_step": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_level_step_patchwise": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_level_step_noalloc": ([I32, I32, DBL, DBL, I32, I32, I32, DBL, DBL, VP, VP, VP, VP, VP, VP],
+                                ctypes.c_int),
     "claw_average_down": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_average_down_adjoint": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_level_step_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP, VP], ctypes.c_int),
@@ -168,6 +170,13 @@ def claw_level_step(ctx, level, q_old, q_new, aux, dt, smax, stream=None):
 def claw_level_step_patchwise(ctx, level, q_old, q_new, aux, dt, smax, stream=None):
     _check("claw_level_step_patchwise", load().claw_level_step_patchwise(
         ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax), _stream(stream)))
+
+
+def claw_level_step_noalloc(nx, ny, dx, dy, limiter, order, transverse, rho0, K0, q_old, q_new, aux, dt, smax,
+                            stream=None):
+    _check("claw_level_step_noalloc", load().claw_level_step_noalloc(
+        nx, ny, float(dx), float(dy), limiter, order, transverse, float(rho0), float(K0), _ptr(q_old), _ptr(q_new),
+        _ptr(aux), _ptr(dt), _ptr(smax), _stream(stream)))
 
 
 def claw_average_down(ctx, fine_level, q_fine, q_coarse, stream=None):
