@@ -30,11 +30,10 @@ METRIC = "FP64 cell-updates/s fused-batched vs plain per-patch launch; % of HBM 
 UNIT = "cell-updates/s"
 N_CELLS = 2048 * 2048
 PATCH = 32
-# FP64 arithmetic of the uniform-medium fused kernel per interior cell update (32 x 32 tile),
-# counted from the kernel source phase by phase (a fused multiply-add counts as 2 flops); the
-# derivation and the cross-check against the profiler's FP64 instruction counters are in
-# the design notes.
-FLOPS_PER_CELL = 82.7
+# FP64 flops (2 x DFMA + DADD + DMUL) the uniform-medium fused kernel executes per interior cell
+# update with 32 x 32 tiles, from the profiler's per-instruction counters of the current kernel
+# source (recorded with the source hash in profiles/step_uniform_2048x2048_traffic.json).
+FLOPS_PER_CELL = 73.9
 BYTES_PER_CELL = 48.0     # read q^n (p, u, v) + write q^{n+1}: algorithmic HBM traffic
 # FP64 peak of the part: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -363,11 +362,17 @@ def main():
     hbm = peaks.get("hbm_gbs", 6800.0)
     achieved_tflops = FLOPS_PER_CELL * N_CELLS / kern_avg_s / 1e12
     achieved_gbs = BYTES_PER_CELL * N_CELLS / kern_avg_s / 1e9
+    # DRAM traffic of one launch from the last profiler capture, only while the kernel source
+    # is unchanged since that capture
     traffic = None
     tf = os.path.join(ROOT, "profiles", "step_uniform_2048x2048_traffic.json")
     if os.path.exists(tf):
         try:
-            traffic = json.load(open(tf)).get("bytes_per_launch")
+            import hashlib
+            rec = json.load(open(tf))
+            src = open(os.path.join(ROOT, "paper_1808_02638_gb300", "csrc", "claw_step.cuh"), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == rec.get("source_sha256_16"):
+                traffic = rec.get("bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
     line = {
