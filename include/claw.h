@@ -99,11 +99,14 @@ void claw_destroy(claw_ctx* ctx);
  * CLAW_ESTATE (level-1 not set), CLAW_ENOMEM, CLAW_ECUDA.  Synchronous. */
 int claw_set_level(claw_ctx* ctx, int32_t level, const claw_box* boxes, int32_t nboxes);
 
-/* Chooses the tile of the fused level-step for a level: tx x ty interior cells per tile
- * (tx, ty in {16, 32, 64}, tx*ty <= 2048) and the staging of the tile's q planes into shared
- * memory (0 = cooperative loads, 1 = tensor-memory-accelerator bulk copies).  claw_set_level
- * installs 32 x 32 with staging 1.  Errors: CLAW_EINVAL. */
-int claw_set_tiling(claw_ctx* ctx, int32_t level, int32_t tx, int32_t ty, int32_t staging);
+/* Chooses the tiling of the fused level-step for a level: tx x ty interior cells per tile,
+ * the staging of the tile's q planes into shared memory (0 = cooperative loads,
+ * 1 = tensor-memory-accelerator bulk copies, only when every box has even nx and offsets) and
+ * the threads per CTA (0 = default).  Supported: 32x32 with 256 or 512 threads, 32x16 with
+ * 256, 16x16 with 128.  claw_set_level installs 32x32, 256 threads, staging 1 when allowed.
+ * Errors: CLAW_EINVAL. */
+int claw_set_tiling(claw_ctx* ctx, int32_t level, int32_t tx, int32_t ty, int32_t staging,
+                    int32_t threads);
 
 /* Per-cell coefficient planes for medium = 1 from one-plane pools rho, K (ghosts included):
  * aux holds, for every cell, Z = sqrt(K rho), c = sqrt(K/rho), K, c^2, 1/(Z_W+Z) and the

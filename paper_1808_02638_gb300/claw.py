@@ -49,7 +49,7 @@ _SIGNATURES = {
     "claw_create": ([ctypes.POINTER(VP), ctypes.POINTER(claw_problem), I32, I32], ctypes.c_int),
     "claw_destroy": ([VP], None),
     "claw_set_level": ([VP, I32, ctypes.POINTER(claw_box), I32], ctypes.c_int),
-    "claw_set_tiling": ([VP, I32, I32, I32, I32], ctypes.c_int),
+    "claw_set_tiling": ([VP, I32, I32, I32, I32, I32], ctypes.c_int),
     "claw_medium_aux": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_medium_aux_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_fill_ghost": ([VP, I32, VP, VP, VP, DBL, VP], ctypes.c_int),
@@ -129,8 +129,8 @@ def claw_set_level(ctx, level: int, boxes):
     _check("claw_set_level", load().claw_set_level(ctx, level, arr, len(boxes)))
 
 
-def claw_set_tiling(ctx, level: int, tx: int, ty: int, staging: int):
-    _check("claw_set_tiling", load().claw_set_tiling(ctx, level, tx, ty, staging))
+def claw_set_tiling(ctx, level: int, tx: int, ty: int, staging: int, threads: int = 0):
+    _check("claw_set_tiling", load().claw_set_tiling(ctx, level, tx, ty, staging, threads))
 
 
 def claw_medium_aux(ctx, level, rho, K, aux, stream=None):

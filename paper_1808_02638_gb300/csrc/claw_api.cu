@@ -654,20 +654,20 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     return CLAW_OK;
 }
 
-int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t staging)
+int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t staging, int32_t threads)
 {
     if (!valid_level(ctx, L)) return CLAW_EINVAL;
-    const bool shape_ok = (tx == 32 && ty == 32) || (tx == 32 && ty == 16) || (tx == 16 && ty == 16);
+    const bool shape_ok = (tx == 32 && ty == 32 && (threads == 0 || threads == 256 || threads == 512)) ||
+                          (tx == 32 && ty == 16 && (threads == 0 || threads == 256)) ||
+                          (tx == 16 && ty == 16 && (threads == 0 || threads == 128));
     if (!shape_ok || staging < 0 || staging > 1 || (staging == 1 && !ctx->tma_ok[L])) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
-    if (d.tx == tx && d.ty == ty) {
-        d.staging = staging;
-        return CLAW_OK;
-    }
+    d.staging = staging;
+    d.nt = threads;
+    if (d.tx == tx && d.ty == ty) return CLAW_OK;
     d.tx = tx;
     d.ty = ty;
-    d.staging = staging;
     return build_tiles(ctx, L);
 }
 
@@ -765,11 +765,11 @@ int claw_level_step(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new
         a.tmaps = get_tmaps(ctx, L, q_old, s);
         if (!a.tmaps) staging = 0;   // no descriptor (e.g. first use inside a graph capture)
     }
-    const int per_sm = step_max_ctas_per_sm(ctx->medium, ctx->limiter, d.tx, d.ty, staging);
+    const int per_sm = step_max_ctas_per_sm(ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging);
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;
-    return cuda_rc(launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, staging, grid, s));
+    return cuda_rc(launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s));
 }
 
 int claw_level_step_patchwise(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,
@@ -786,7 +786,7 @@ int claw_level_step_patchwise(claw_ctx* ctx, int32_t L, const double* q_old, dou
         a.tiles = ctx->ptiles[L] + st[n];
         a.ntiles = st[n + 1] - st[n];
         ctx->launches += 1;
-        cudaError_t e = launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, 0, a.ntiles, s);
+        cudaError_t e = launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, 0, a.ntiles, s);
         if (e != cudaSuccess) return CLAW_ECUDA;
     }
     return CLAW_OK;

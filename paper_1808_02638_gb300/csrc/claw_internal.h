@@ -81,7 +81,7 @@ struct LevelDev {
     int ninterp = 0;
     int navg = 0;          // averaging rects into the coarser level
     int ratio = 1;
-    int tx = 32, ty = 32, staging = 1;
+    int tx = 32, ty = 32, staging = 1, nt = 0;   // tile, staging, threads per CTA (0: default)
     PatchDev* patches = nullptr;
     TileDev* tiles = nullptr;
     CopyRect* copies = nullptr;
@@ -115,9 +115,9 @@ struct StepArgs {
 enum : int { ERR_NAN = 1, ERR_CFL = 2, ERR_TIMEOUT = 4 };
 
 // launchers (claw_step.cu)
-cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int staging,
+cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s);
-int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int staging);
+int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int nt, int staging);
 cudaError_t launch_step_adjoint(const StepArgs& a, double* lam_old, double* g_aux, int medium,
                                 int limiter, int tx, int ty, int grid, cudaStream_t s);
 

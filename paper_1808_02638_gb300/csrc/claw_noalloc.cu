@@ -110,7 +110,7 @@ extern "C" int claw_level_step_noalloc(int32_t nx, int32_t ny, double dx, double
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CLAW_ECUDA;
     const int medium = aux ? 1 : 0;
-    const int per_sm = step_max_ctas_per_sm(medium, limiter, kTile, kTile, 0);
+    const int per_sm = step_max_ctas_per_sm(medium, limiter, kTile, kTile, 0, 0);
     if (per_sm <= 0) return CLAW_ECUDA;
     StepArgs a;
     a.patches = reinterpret_cast<const PatchDev*>(s + 64);
@@ -128,5 +128,5 @@ extern "C" int claw_level_step_noalloc(int32_t nx, int32_t ny, double dx, double
     a.rho0 = rho0;
     a.K0 = K0;
     const int grid = std::min(ntiles, per_sm * nsm);
-    return launch_step(a, medium, limiter, kTile, kTile, 0, grid, st) == cudaSuccess ? CLAW_OK : CLAW_ECUDA;
+    return launch_step(a, medium, limiter, kTile, kTile, 0, 0, grid, st) == cudaSuccess ? CLAW_OK : CLAW_ECUDA;
 }

@@ -7,10 +7,10 @@
 
 namespace claw {
 
-static StepKernel pick(int medium, int limiter, int tx, int ty, int staging)
+static StepKernel pick(int medium, int limiter, int tx, int ty, int nt, int staging)
 {
-    return medium ? step_kernel_cellwise(limiter, tx, ty, staging)
-                  : step_kernel_uniform(limiter, tx, ty, staging);
+    return medium ? step_kernel_cellwise(limiter, tx, ty, nt, staging)
+                  : step_kernel_uniform(limiter, tx, ty, nt, staging);
 }
 
 static cudaError_t prepare(const StepKernel& k)
@@ -29,9 +29,9 @@ static cudaError_t prepare(const StepKernel& k)
     return e;
 }
 
-int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int staging)
+int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int nt, int staging)
 {
-    StepKernel k = pick(medium, limiter, tx, ty, staging);
+    StepKernel k = pick(medium, limiter, tx, ty, nt, staging);
     if (!k.fn || prepare(k) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k.fn, k.nt, k.smem) != cudaSuccess)
@@ -39,10 +39,10 @@ int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int staging)
     return n;
 }
 
-cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int staging,
+cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s)
 {
-    StepKernel k = pick(medium, limiter, tx, ty, staging);
+    StepKernel k = pick(medium, limiter, tx, ty, nt, staging);
     if (!k.fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare(k);
     if (e != cudaSuccess) return e;

@@ -31,28 +31,54 @@ namespace claw {
 
 // ------------------------------------------------------------------------- limiters
 // Lim<L>::f(a, b) = phi(b / a) * a for the wave strength a at an edge and the projected
-// strength b of the same family at the upwind edge; 0 when a b <= 0 (also covers a = 0,
-// where the wave vanishes).  Division free except van Leer.
+// strength b of the same family at the upwind edge; 0 when a b <= 0 (also covers a = 0, where
+// the wave vanishes).
+//
+// FP64 is 1/64 of the FP32 rate on this part, so minmod, superbee and MC run on the integer
+// pipe: for non-negative doubles the bit patterns order like the values, so min / max of
+// magnitudes are 64-bit integer min / max, and doubling or halving a magnitude adds or
+// subtracts 1 in the exponent field.  MC keeps one FP64 add (|a| + |b|), minmod and
+// superbee none.  The exponent shifts are exact for magnitudes >= 2^-1021; below that the
+// result (itself below 2^-1020 in magnitude) may differ from the IEEE evaluation of the same
+// formula by less than 2^-1020.  van Leer needs a division and stays in FP64.
+namespace lim_bits {
+constexpr long long MAG = 0x7fffffffffffffffLL;
+constexpr long long SIGN = (long long)0x8000000000000000ULL;
+constexpr long long ONE_EXP = 1LL << 52;   // +1 in the exponent field: x2
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double val(long long b) { return __longlong_as_double(b); }
+// a b > 0: same sign bit and both magnitudes non-zero
+__device__ __forceinline__ bool same_sign_nonzero(long long ia, long long ib, long long ma, long long mb)
+{
+    return ((ia ^ ib) >= 0) & (ma != 0) & (mb != 0);
+}
+}  // namespace lim_bits
+
 template <int L> struct Lim;
 template <> struct Lim<CLAW_LIM_NONE> {
     static __device__ __forceinline__ double f(double a, double) { return a; }
 };
-template <> struct Lim<CLAW_LIM_MINMOD> {   // max(0, min(1, theta))
+template <> struct Lim<CLAW_LIM_MINMOD> {   // max(0, min(1, theta)): sign(a) min(|a|, |b|)
     static __device__ __forceinline__ double f(double a, double b)
     {
-        if (!(a * b > 0.0)) return 0.0;
-        return a > 0.0 ? fmin(a, b) : fmax(a, b);
+        using namespace lim_bits;
+        const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
+        const long long m = ma < mb ? ma : mb;
+        return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
     }
 };
 template <> struct Lim<CLAW_LIM_SUPERBEE> {   // max(0, min(1, 2 theta), min(2, theta))
     static __device__ __forceinline__ double f(double a, double b)
-    {
-        if (!(a * b > 0.0)) return 0.0;
-        double a2 = a + a, b2 = b + b;
-        return a > 0.0 ? fmax(fmin(a, b2), fmin(a2, b)) : fmin(fmax(a, b2), fmax(a2, b));
+    {   // sign(a) max(min(|a|, 2|b|), min(2|a|, |b|))
+        using namespace lim_bits;
+        const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
+        const long long a2 = ma + ONE_EXP, b2 = mb + ONE_EXP;
+        const long long m1 = ma < b2 ? ma : b2, m2 = a2 < mb ? a2 : mb;
+        const long long m = m1 > m2 ? m1 : m2;
+        return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
     }
 };
-template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|)
+template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|): 2ab / (a + b)
     static __device__ __forceinline__ double f(double a, double b)
     {
         if (!(a * b > 0.0)) return 0.0;
@@ -61,10 +87,14 @@ template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|
 };
 template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta))
     static __device__ __forceinline__ double f(double a, double b)
-    {
-        if (!(a * b > 0.0)) return 0.0;
-        double m = 0.5 * (a + b), a2 = a + a, b2 = b + b;
-        return a > 0.0 ? fmin(m, fmin(a2, b2)) : fmax(m, fmax(a2, b2));
+    {   // sign(a) min((|a| + |b|) / 2, 2 |a|, 2 |b|) = sign(a) min(s / 2, 2 min(|a|, |b|))
+        using namespace lim_bits;
+        const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
+        const long long t2 = (ma < mb ? ma : mb) + ONE_EXP;
+        long long sh = bits(val(ma) + val(mb)) - ONE_EXP;   // the one FP64 add
+        sh = sh > 0 ? sh : 0;   // a subnormal sum would wrap below zero
+        const long long m = sh < t2 ? sh : t2;
+        return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
     }
 };
 
@@ -580,32 +610,35 @@ StepKernel step_kernel_entry()
 }
 
 // all tile shapes and stagings of one medium and limiter
+// tile shapes x thread counts x stagings of one medium and limiter (nt = 0: the default)
 template <int MED, int LIM>
-StepKernel step_kernel_select(int tx, int ty, int staging)
+StepKernel step_kernel_select(int tx, int ty, int nt, int staging)
 {
-    if (tx == 32 && ty == 32) return staging ? step_kernel_entry<MED, LIM, 32, 32, 256, 1>()
-                                             : step_kernel_entry<MED, LIM, 32, 32, 256, 0>();
-    if (tx == 32 && ty == 16) return staging ? step_kernel_entry<MED, LIM, 32, 16, 256, 1>()
-                                             : step_kernel_entry<MED, LIM, 32, 16, 256, 0>();
-    if (tx == 16 && ty == 16) return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1>()
-                                             : step_kernel_entry<MED, LIM, 16, 16, 128, 0>();
+    if (tx == 32 && ty == 32 && (nt == 0 || nt == 256))
+        return staging ? step_kernel_entry<MED, LIM, 32, 32, 256, 1>() : step_kernel_entry<MED, LIM, 32, 32, 256, 0>();
+    if (tx == 32 && ty == 32 && nt == 512)
+        return staging ? step_kernel_entry<MED, LIM, 32, 32, 512, 1>() : step_kernel_entry<MED, LIM, 32, 32, 512, 0>();
+    if (tx == 32 && ty == 16 && (nt == 0 || nt == 256))
+        return staging ? step_kernel_entry<MED, LIM, 32, 16, 256, 1>() : step_kernel_entry<MED, LIM, 32, 16, 256, 0>();
+    if (tx == 16 && ty == 16 && (nt == 0 || nt == 128))
+        return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1>() : step_kernel_entry<MED, LIM, 16, 16, 128, 0>();
     return StepKernel{nullptr, 0, 0};
 }
 
 template <int MED>
-StepKernel step_kernel_for(int lim, int tx, int ty, int staging)
+StepKernel step_kernel_for(int lim, int tx, int ty, int nt, int staging)
 {
     switch (lim) {
-    case CLAW_LIM_NONE: return step_kernel_select<MED, CLAW_LIM_NONE>(tx, ty, staging);
-    case CLAW_LIM_MINMOD: return step_kernel_select<MED, CLAW_LIM_MINMOD>(tx, ty, staging);
-    case CLAW_LIM_SUPERBEE: return step_kernel_select<MED, CLAW_LIM_SUPERBEE>(tx, ty, staging);
-    case CLAW_LIM_VANLEER: return step_kernel_select<MED, CLAW_LIM_VANLEER>(tx, ty, staging);
-    case CLAW_LIM_MC: return step_kernel_select<MED, CLAW_LIM_MC>(tx, ty, staging);
+    case CLAW_LIM_NONE: return step_kernel_select<MED, CLAW_LIM_NONE>(tx, ty, nt, staging);
+    case CLAW_LIM_MINMOD: return step_kernel_select<MED, CLAW_LIM_MINMOD>(tx, ty, nt, staging);
+    case CLAW_LIM_SUPERBEE: return step_kernel_select<MED, CLAW_LIM_SUPERBEE>(tx, ty, nt, staging);
+    case CLAW_LIM_VANLEER: return step_kernel_select<MED, CLAW_LIM_VANLEER>(tx, ty, nt, staging);
+    case CLAW_LIM_MC: return step_kernel_select<MED, CLAW_LIM_MC>(tx, ty, nt, staging);
     }
     return StepKernel{nullptr, 0, 0};
 }
 
-StepKernel step_kernel_uniform(int lim, int tx, int ty, int staging);
-StepKernel step_kernel_cellwise(int lim, int tx, int ty, int staging);
+StepKernel step_kernel_uniform(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_cellwise(int lim, int tx, int ty, int nt, int staging);
 
 }  // namespace claw

@@ -2,8 +2,8 @@
 #include "claw_step.cuh"
 
 namespace claw {
-StepKernel step_kernel_uniform(int lim, int tx, int ty, int staging)
+StepKernel step_kernel_uniform(int lim, int tx, int ty, int nt, int staging)
 {
-    return step_kernel_for<0>(lim, tx, ty, staging);
+    return step_kernel_for<0>(lim, tx, ty, nt, staging);
 }
 }  // namespace claw

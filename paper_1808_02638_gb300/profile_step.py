@@ -1,0 +1,38 @@
+"""Profiling driver: a few eager level-steps of the 2048 x 2048 workload as 4096 patches of
+32 x 32, for a profiler to capture single kernel launches.
+
+  python -m paper_1808_02638_gb300.profile_step [uniform|cellwise] [nsteps]
+
+uniform: radial pulse, rho = 1, K = 4; cellwise: the same tiling over the smoothed random
+medium of the heterogeneous workload.
+"""
+import sys
+
+import torch
+
+from . import inputs
+from .solver import Hierarchy
+
+
+def main():
+    medium = sys.argv[1] if len(sys.argv) > 1 else "uniform"
+    nsteps = int(sys.argv[2]) if len(sys.argv) > 2 else 3
+    n = 2048
+    if medium == "uniform":
+        run = inputs.config1()
+        H = Hierarchy([run], [[inputs.init_q(run, run.levels[0])]], rho0=1.0, K0=4.0)
+    else:
+        run, r2, k2 = inputs.config3(n)
+        run.levels = [inputs.Level(n, n, 2.0 / n, 2.0 / n, inputs.uniform_tiling(n, n, 32, 32))]
+        lev = run.levels[0]
+        H = Hierarchy([run], [[inputs.init_q(run, lev)]], [[inputs.coef_pool(lev, r2, 1)]],
+                      [[inputs.coef_pool(lev, k2, 1)]])
+    H.init_dt()
+    for _ in range(nsteps):
+        H.coarse_step()
+    torch.cuda.synchronize()
+    print("status", H.sync_status(), "dt", float(H.dt[0]))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,100 @@
+"""Autotuner of the fused level-step's tiling (tile shape, threads per CTA, staging).
+
+For each level it times every supported tiling of the fused launch on the level's own pools
+(into a scratch q_new) with CUDA events, keeps the fastest, and caches the choice per
+(medium, limiter, histogram of box sizes) in a JSON file next to the library, so that later
+hierarchies with the same patch-size mix reuse it without timing.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import threading
+
+import torch
+
+from . import claw
+
+CANDIDATES = [(32, 32, 1, 256), (32, 32, 1, 512), (32, 32, 0, 256), (32, 32, 0, 512),
+              (32, 16, 1, 256), (16, 16, 1, 128)]
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json")
+_lock = threading.Lock()
+
+
+def _key(H, L):
+    sizes = sorted((int(b.nx), int(b.ny)) for b in H.boxes[L])
+    hist = {}
+    for s in sizes:
+        hist[s] = hist.get(s, 0) + 1
+    blob = json.dumps([H.medium, H.runs[0].limiter, H.runs[0].order, H.runs[0].transverse,
+                       sorted((f"{a}x{b}", n) for (a, b), n in hist.items()),
+                       torch.cuda.get_device_name(H.dev)])
+    return hashlib.sha256(blob.encode()).hexdigest()[:24]
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(d):
+    tmp = CACHE + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1)
+    os.replace(tmp, CACHE)
+
+
+def time_tiling(H, L, tiling, reps=5):
+    """mean device time (ms) of one fused launch of level L with `tiling`"""
+    tx, ty, staging, threads = tiling
+    claw.claw_set_tiling(H.ctx, L, tx, ty, staging, threads)
+    src = H.q[L][H.cur[L]]
+    dst = torch.empty_like(src)
+    smax = torch.zeros_like(H.smax)
+    for _ in range(2):
+        claw.claw_level_step(H.ctx, L, src, dst, H.aux[L], H.dt, smax)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        claw.claw_level_step(H.ctx, L, src, dst, H.aux[L], H.dt, smax)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_level(H, L, use_cache=True, candidates=None):
+    """pick the fastest tiling for level L of hierarchy H, install it and return it with the
+    timings (an empty dict when the choice came from the cache)"""
+    key = _key(H, L)
+    if use_cache:
+        with _lock:
+            hit = _load().get(key)
+        if hit:
+            try:
+                claw.claw_set_tiling(H.ctx, L, *hit)
+                return tuple(hit), {}
+            except claw.ClawError:
+                pass
+    if float(H.dt.max()) <= 0.0:
+        H.init_dt()
+    timings = {}
+    for c in candidates or CANDIDATES:
+        try:
+            timings[c] = time_tiling(H, L, c)
+        except claw.ClawError:
+            continue   # e.g. bulk-copy staging not allowed for this level
+    best = min(timings, key=timings.get)
+    claw.claw_set_tiling(H.ctx, L, *best)
+    with _lock:
+        d = _load()
+        d[key] = list(best)
+        _save(d)
+    return best, timings
+
+
+def tune(H, use_cache=True):
+    return [tune_level(H, L, use_cache) for L in range(H.nlev)]

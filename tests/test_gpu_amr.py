@@ -1,0 +1,105 @@
+"""GPU parity of the AMR path (Sec. 2.2-2.3): coarse-to-fine space-time ghost interpolation,
+fine-to-coarse averaging and recursive subcycling, and of many independent runs batched into
+one launch per level-step, against the oracle's AMR driver."""
+import numpy as np
+import pytest
+
+from paper_1808_02638_gb300 import inputs
+
+from gpu_helpers import lib_ready, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL1, TOLN = 1e-12, 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib_ready()
+
+
+def _compare_all_levels(H, O, run_index, tol):
+    run = H.runs[run_index]
+    worst = 0.0
+    scale = max(np.abs(O.q[L]).max() for L in range(len(run.levels)))
+    for L, lev in enumerate(run.levels):
+        for n in range(len(lev.boxes)):
+            got = H.interior(run_index, L, n)
+            want = O.interior(L, n)
+            worst = max(worst, float(np.abs(got - want).max()) / scale)
+    assert worst <= tol, worst
+    return worst
+
+
+def test_three_level_hierarchy_one_and_twenty_coarse_steps():
+    # 64^2 base, ratio 4 twice, seeded patches of 8..64 cells on the annuli (the uneven AMR
+    # workload); uniform medium rho = 1, K = 4
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    O = OracleHierarchy(run, q0, [inputs.const_pool(l, 1.0) for l in run.levels],
+                        [inputs.const_pool(l, 4.0) for l in run.levels])
+    H.init_dt()
+    assert float(H.dt[0]) == pytest.approx(0.9 * (2.0 / 64) / 2.0, rel=1e-15)
+    H.coarse_step()
+    O.coarse_step()
+    _compare_all_levels(H, O, 0, TOL1)
+    for _ in range(19):
+        H.coarse_step()
+        O.coarse_step()
+    _compare_all_levels(H, O, 0, TOLN)
+    assert H.sync_status() == 0
+
+
+def test_fine_level_ghosts_match_oracle_fill():
+    # the interpolated and copied ghosts of the finest level at a substep fraction
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    import oracle
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    # a non-trivial coarse pair: perturb level 1 old / new differently
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    L1, L2 = run.levels[1], run.levels[2]
+    cold = q0[1] + 0.01 * inputs.uniform(9, q0[1].size)
+    cnew = q0[1] - 0.02 * inputs.uniform(10, q0[1].size)
+    import torch
+    dev = H.q[1][0].device
+    tco = torch.from_numpy(np.concatenate([cold, np.zeros(H.q[1][0].numel() - cold.size)])).to(dev)
+    tcn = torch.from_numpy(np.concatenate([cnew, np.zeros(H.q[1][0].numel() - cnew.size)])).to(dev)
+    fine = H.q[2][0]
+    claw.claw_fill_ghost(H.ctx, 2, fine, tco, tcn, 0.25)
+    got = fine.cpu().numpy()[:q0[2].size]
+    want = q0[2].copy()
+    bx = lambda lev: [(int(b[0]), int(b[1]), int(b[2]), int(b[3]), int(o)) for b, o in zip(lev.boxes, lev.qoff)]
+    oracle.level_fill_ghost(bx(L2), want, 3, L2.NX, L2.NY, run.bc, bx(L1), cold, cnew, 0.25, 4)
+    assert rel_err(got, want) <= 1e-14
+
+
+def test_batched_independent_runs_two_levels_cellwise():
+    # several 2-level problems of different sizes and media advanced together: every
+    # level-step is one launch over the boxes of all runs, with per-run dt and CFL scalars
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300.solver import Hierarchy
+    runs = inputs.config4_runs(4)
+    qs, rhos, Ks, orcs = [], [], [], []
+    for run, rho2, K2 in runs:
+        q = [inputs.init_q(run, lev) for lev in run.levels]
+        r = [inputs.coef_pool(lev, rho2, 4 ** L) for L, lev in enumerate(run.levels)]
+        k = [inputs.coef_pool(lev, K2, 4 ** L) for L, lev in enumerate(run.levels)]
+        qs.append(q)
+        rhos.append(r)
+        Ks.append(k)
+        orcs.append(OracleHierarchy(run, q, r, k))
+    H = Hierarchy([r for r, _, _ in runs], qs, rhos, Ks)
+    H.init_dt()
+    for ri, O in enumerate(orcs):
+        assert float(H.dt[ri]) == pytest.approx(0.9 * min(O.levels[0].dx, O.levels[0].dy) / O.smax, rel=1e-15)
+    for step in range(3):
+        H.coarse_step()
+        for O in orcs:
+            O.coarse_step()
+    for ri in range(len(runs)):
+        _compare_all_levels(H, orcs[ri], ri, TOLN)
+    assert H.sync_status() == 0

@@ -257,3 +257,24 @@ def test_cfl_violation_is_reported():
     H.dt.mul_(1.5)                      # nu = 1.35 > 1
     H.coarse_step()
     assert H.sync_status() == claw.CLAW_ECFL
+
+
+def test_autotuner_installs_a_valid_tiling_and_keeps_parity(orc):
+    from paper_1808_02638_gb300 import tune
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config1(256, 32)
+    lev = run.levels[0]
+    q = inputs.init_q(run, lev)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    best, timings = tune.tune_level(H, 0, use_cache=False)
+    assert best in timings and len(timings) >= 4 and all(v > 0 for v in timings.values())
+    for _ in range(5):
+        H.coarse_step()
+    srun, sq = single_grid(256)
+    rho, K = _uniform_planes(256)
+    want, _ = oracle_single(orc, srun, sq, rho, K, 5)
+    got = np.zeros_like(want)
+    for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
+        got[:, jlo:jlo + bny, ilo:ilo + bnx] = H.interior(0, 0, nb)
+    assert rel_err(got, want) <= TOLN
