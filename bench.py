@@ -207,6 +207,48 @@ def run_reference(args, rank: int, world: int):
 
 
 # ----------------------------------------------------------------- GPU leg
+def measure_adjoint(nsteps: int = 400, every: int = 20):
+    """cost of the gradient of the receiver functional on the heterogeneous 256^2 workload:
+    forward rollout (with checkpoints) vs its backward (segment recompute + adjoint steps)"""
+    import numpy as np
+    import torch
+
+    from paper_1808_02638_gb300 import inputs
+    from paper_1808_02638_gb300.adjoint import rollout
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = 256
+    run, r2, k2 = inputs.config3(n)
+    lev = run.levels[0]
+    q, rho, K = inputs.init_q(run, lev), inputs.coef_pool(lev, r2, 1), inputs.coef_pool(lev, k2, 1)
+    H = Hierarchy([run], [[q]], [[rho]], [[K]])
+
+    def t(a, ref):
+        b = np.zeros(ref.numel())
+        b[:a.size] = a
+        return torch.from_numpy(b).to(ref.device).requires_grad_(True)
+
+    i0, j0, nb = inputs.receiver_box(n)
+    times = []
+    for _ in range(2):   # the first pass warms up
+        tq, tr, tk = t(q, H.q[0][0]), t(rho, H.rho[0]), t(K, H.rho[0])
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        out = rollout(H, [tq], [tr], [tk], ncoarse=nsteps, every=every)
+        v = out[0][:3 * (n + 4) ** 2].view(3, n + 4, n + 4)
+        J = (v[0, 2 + j0:2 + j0 + nb, 2 + i0:2 + i0 + nb] ** 2).sum()
+        torch.cuda.synchronize()
+        b = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize()
+        c = time.perf_counter()
+        times.append((b - a, c - b))
+    fwd, bwd = times[-1]
+    return {"workload": "256x256 heterogeneous medium (rho~U[0.5,2], K~U[1,8] smoothed), radial pulse, "
+                        "J = sum p^2 over the 16x16 receiver after 400 steps, checkpoints every 20",
+            "forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "backward_over_forward": bwd / fwd,
+            "note": "wall time of eager launches (no graphs); backward = segment recompute + adjoint steps"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,6 +257,7 @@ def main():
     ap.add_argument("--impl", default="claw", choices=["claw", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -356,6 +399,8 @@ def main():
     torch.cuda.synchronize()
     e2e_value = world * e2e_steps * N_CELLS / (e0.elapsed_time(e1) * 1e-3)
 
+    adjoint = measure_adjoint() if (rank == 0 and not args.no_adjoint) else None
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -402,6 +447,7 @@ def main():
         "tuning_ms": {f"{a}x{b}/s{c}/t{d}": round(v, 4) for (a, b, c, d), v in tune_ms.items()},
         "clocks": clocks,
         "status": claw.strerror(status),
+        "adjoint": adjoint,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()

@@ -124,6 +124,14 @@ int claw_medium_aux(claw_ctx* ctx, int32_t level, const double* rho, const doubl
 int claw_fill_ghost(claw_ctx* ctx, int32_t level, double* q, const double* qc_old,
                     const double* qc_new, double tau, void* stream);
 
+/* The same-level and physical-boundary ghosts (Sec. 2.2 items 1-2) of a one-plane pool such as
+ * rho or K (box b at element coff[b]; no sign flips at walls).  Ghosts that would need the
+ * coarser level are left as they are (coefficients of finer levels are given by the caller).
+ * The _adjoint call adds every such ghost's value into its source cell and zeroes the ghost:
+ * the gradient with respect to the interior field from one with respect to the padded pool. */
+int claw_fill_ghost_coef(claw_ctx* ctx, int32_t level, double* a, void* stream);
+int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t level, double* g, void* stream);
+
 /* smax[run] = max(smax[run], max c over the cells next to the edges a level-step of `level`
  * solves: the ring [-1, nx] x [-1, ny] of every box), for the first time step (Eq. cfl).
  * aux may be NULL for medium = 0.  smax has one entry per run (zero it before the first use;

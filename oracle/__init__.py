@@ -67,11 +67,11 @@ def lib():
             L.orc_fill_bc_adjoint.argtypes = [I, I, I, I, IP, D]
             L.orc_cfl_max.argtypes = [I, I, I, D, D]
             L.orc_cfl_max.restype = dbl
-            L.orc_level_fill_ghost.argtypes = [I, BP, D, I, I, I, I, IP, I, BP, D, D, dbl, I]
+            L.orc_level_fill_ghost.argtypes = [I, BP, D, I, I, I, I, IP, I, BP, D, D, dbl, I, I]
             L.orc_average_down.argtypes = [I, BP, D, I, BP, D, I, I, I]
             L.orc_interp_cell.argtypes = [I, BP, D, D, dbl, I, I, I, I, I, IP, I, I, D]
             L.orc_level_fill_ghost_adjoint.argtypes = [I, BP, D, I, I, I, I, IP, I, BP, D, D, D, D,
-                                                       dbl, I]
+                                                       dbl, I, I]
             L.orc_average_down_adjoint.argtypes = [I, BP, D, I, BP, D, I, I, I]
             _lib = L
     return _lib
@@ -178,7 +178,7 @@ def boxes_array(boxes):
 
 
 def level_fill_ghost(boxes, pool, ncomp, NX, NY, bc, cboxes=None, cold=None, cnew=None,
-                     tau=0.0, r=0):
+                     tau=0.0, r=0, copy_only=False):
     """Fill the ghosts of every box of a level in place (Sec. 2.2 ghost rules)."""
     b, nb = boxes_array(boxes)
     if cboxes is None:
@@ -189,14 +189,14 @@ def level_fill_ghost(boxes, pool, ncomp, NX, NY, bc, cboxes=None, cold=None, cne
     else:
         cb, ncb = boxes_array(cboxes)
     rc = lib().orc_level_fill_ghost(nb, b, _p(pool), ncomp, MBC, NX, NY, _ip(bc), ncb, cb,
-                                    _p(cold), _p(cnew), float(tau), int(r))
+                                    _p(cold), _p(cnew), float(tau), int(r), int(copy_only))
     if rc:
         raise ValueError(f"level_fill_ghost failed ({rc}): improper nesting")
     return pool
 
 
 def level_fill_ghost_adjoint(boxes, gpool, ncomp, NX, NY, bc, cboxes=None, gcold=None,
-                             gcnew=None, cold=None, cnew=None, tau=0.0, r=0):
+                             gcnew=None, cold=None, cnew=None, tau=0.0, r=0, copy_only=False):
     b, nb = boxes_array(boxes)
     if cboxes is None:
         cb, _ = boxes_array([])
@@ -207,7 +207,7 @@ def level_fill_ghost_adjoint(boxes, gpool, ncomp, NX, NY, bc, cboxes=None, gcold
         cb, ncb = boxes_array(cboxes)
     rc = lib().orc_level_fill_ghost_adjoint(nb, b, _p(gpool), ncomp, MBC, NX, NY, _ip(bc), ncb,
                                             cb, _p(gcold), _p(gcnew), _p(cold), _p(cnew),
-                                            float(tau), int(r))
+                                            float(tau), int(r), int(copy_only))
     if rc:
         raise ValueError(f"level_fill_ghost_adjoint failed ({rc})")
     return gpool

@@ -15,7 +15,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import MBC, average_down, cfl_max, level_fill_ghost, step
+from . import (MBC, average_down, average_down_adjoint, cfl_max, level_fill_ghost,
+               level_fill_ghost_adjoint, step, step_adjoint)
 
 
 def _view(pool, off, nx, ny, ncomp):
@@ -99,6 +100,79 @@ class OracleHierarchy:
         self.dt_history.append(dt)
         self.smax_history.append(acc[0])
         return dt
+
+    # ------------------------------------------------------------ reverse mode
+    def _advance_record(self, L, dt, cold, cnew, tau, acc):
+        self.fill(L, self.q[L], cold, cnew, tau)
+        node = {"L": L, "q_in": self.q[L].copy(), "cold": cold, "cnew": cnew, "tau": tau, "dt": dt,
+                "fine": [], "pre_avg": None}
+        qnew, sm = self.step_level(L, node["q_in"], dt)
+        acc[0] = max(acc[0], sm)
+        if L + 1 < len(self.levels):
+            node["pre_avg"] = qnew.copy()
+            fine = self.levels[L + 1]
+            r = fine.ratio
+            for k in range(r):
+                node["fine"].append(self._advance_record(L + 1, dt / r, node["q_in"], node["pre_avg"], k / r, acc))
+            c = self.levels[L]
+            average_down(_boxes(fine, fine.qoff), self.q[L + 1], _boxes(c, c.qoff), qnew, 3, r)
+        self.q[L] = qnew
+        return node
+
+    def _reverse(self, node, lam, g_rho, g_K, lam_cold=None, lam_cnew=None):
+        run = self.run
+        L = node["L"]
+        lev = self.levels[L]
+        lam_pre = lam[L]
+        lam_in = np.zeros_like(lam_pre)
+        if node["fine"]:
+            fine = self.levels[L + 1]
+            average_down_adjoint(_boxes(fine, fine.qoff), lam[L + 1], _boxes(lev, lev.qoff), lam_pre, 3,
+                                 fine.ratio)
+            for f in reversed(node["fine"]):
+                self._reverse(f, lam, g_rho, g_K, lam_in, lam_pre)
+        for n, b in enumerate(lev.boxes):
+            nx, ny = int(b[2]), int(b[3])
+            qb = _view(node["q_in"], lev.qoff[n], nx, ny, 3)
+            lb = _view(lam_pre, lev.qoff[n], nx, ny, 3)
+            r = _view(self.rho[L], lev.coff[n], nx, ny, 1)[0]
+            k = _view(self.K[L], lev.coff[n], nx, ny, 1)[0]
+            lq, gr, gk = step_adjoint(qb, r, k, lb, lev.dx, lev.dy, node["dt"], run.order, run.transverse,
+                                      run.limiter)
+            _view(lam_in, lev.qoff[n], nx, ny, 3)[...] += lq
+            _view(g_rho[L], lev.coff[n], nx, ny, 1)[0] += gr
+            _view(g_K[L], lev.coff[n], nx, ny, 1)[0] += gk
+        if L == 0:
+            level_fill_ghost_adjoint(_boxes(lev, lev.qoff), lam_in, 3, lev.NX, lev.NY, run.bc)
+        else:
+            c = self.levels[L - 1]
+            level_fill_ghost_adjoint(_boxes(lev, lev.qoff), lam_in, 3, lev.NX, lev.NY, run.bc,
+                                     _boxes(c, c.qoff), lam_cold, lam_cnew, node["cold"], node["cnew"],
+                                     node["tau"], lev.ratio)
+        lam[L] = lam_in
+
+    def gradient(self, ncoarse, final_adjoint):
+        """Runs ncoarse coarse steps (recording them) and the reverse sweep.  final_adjoint(q)
+        returns, per level, the adjoint of a functional of the final pools.  Returns (J-adjoint of
+        the initial q pools, of the rho pools, of the K pools), the coefficient adjoints moved from
+        same-level / boundary ghosts to their source cells."""
+        tapes = []
+        for _ in range(ncoarse):
+            lev0 = self.levels[0]
+            dt = self.run.cfl * min(lev0.dx, lev0.dy) / self.smax
+            acc = [0.0]
+            tapes.append(self._advance_record(0, dt, None, None, 0.0, acc))
+            self.smax = acc[0]
+            self.dt_history.append(dt)
+        lam = [np.array(a, dtype=np.float64) for a in final_adjoint(self.q)]
+        g_rho = [np.zeros_like(r) for r in self.rho]
+        g_K = [np.zeros_like(k) for k in self.K]
+        for node in reversed(tapes):
+            self._reverse(node, lam, g_rho, g_K)
+        for L, lev in enumerate(self.levels):
+            for g in (g_rho[L], g_K[L]):
+                level_fill_ghost_adjoint(_boxes(lev, lev.coff), g, 1, lev.NX, lev.NY, self.run.bc, copy_only=True)
+        return lam, g_rho, g_K
 
     def interior(self, L, n):
         lev = self.levels[L]

@@ -699,7 +699,7 @@ int orc_interp_cell(int ncb, const orc_box* cb, const double* cold, const double
 int orc_level_fill_ghost(int nb, const orc_box* boxes, double* pool, int ncomp, int mbc,
                          int NX, int NY, const int* bc,
                          int ncb, const orc_box* cboxes, const double* cold, const double* cnew,
-                         double tau, int r)
+                         double tau, int r, int copy_only)
 {
     int cNX = r > 0 ? NX / r : 0, cNY = r > 0 ? NY / r : 0;
     for (int n = 0; n < nb; ++n) {
@@ -717,6 +717,7 @@ int orc_level_fill_ghost(int nb, const orc_box* boxes, double* pool, int ncomp, 
                     long k = box_cell(&boxes[src], mbc, si, sj), spl = box_plane(&boxes[src], mbc);
                     for (int m = 0; m < ncomp; ++m) val[m] = pool[m * spl + k];
                 } else {
+                    if (copy_only) continue;
                     if (ncb <= 0 || r <= 0) return -2;
                     if (orc_interp_cell(ncb, cboxes, cold, cnew, tau, r, ncomp, mbc, cNX, cNY, bc,
                                         si, sj, val))
@@ -844,7 +845,8 @@ static int interp_cell_adj(int ncb, const orc_box* cb, const double* cold, const
 int orc_level_fill_ghost_adjoint(int nb, const orc_box* boxes, double* gpool, int ncomp, int mbc,
                                  int NX, int NY, const int* bc,
                                  int ncb, const orc_box* cboxes, double* gcold, double* gcnew,
-                                 const double* cold, const double* cnew, double tau, int r)
+                                 const double* cold, const double* cnew, double tau, int r,
+                                 int copy_only)
 {
     /* every ghost value of the forward fill is a function of interior cells only (its own
      * box, another box, or the coarse level), so the reverse is order independent */
@@ -859,6 +861,8 @@ int orc_level_fill_ghost_adjoint(int nb, const orc_box* boxes, double* gpool, in
                 int si = bc_map(gi, NX, bc[0], bc[1], &fx);
                 int sj = bc_map(gj, NY, bc[2], bc[3], &fy);
                 long d = box_cell(b, mbc, gi, gj);
+                int src = box_has(b, si, sj) ? n : find_box(nb, boxes, si, sj);
+                if (src < 0 && copy_only) continue;
                 double gval[8];
                 for (int m = 0; m < ncomp; ++m) {
                     double s = 1.0;
@@ -866,7 +870,6 @@ int orc_level_fill_ghost_adjoint(int nb, const orc_box* boxes, double* gpool, in
                     gval[m] = s * gpool[m * pl + d];
                     gpool[m * pl + d] = 0.0;
                 }
-                int src = box_has(b, si, sj) ? n : find_box(nb, boxes, si, sj);
                 if (src >= 0) {
                     long k = box_cell(&boxes[src], mbc, si, sj), spl = box_plane(&boxes[src], mbc);
                     for (int m = 0; m < ncomp; ++m) gpool[m * spl + k] += gval[m];

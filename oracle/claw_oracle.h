@@ -72,7 +72,9 @@ typedef struct { int32_t ilo, jlo, nx, ny; int64_t off; } orc_box;  /* off: elem
 int orc_level_fill_ghost(int nb, const orc_box* boxes, double* pool, int ncomp, int mbc,
                          int NX, int NY, const int* bc,
                          int ncb, const orc_box* cboxes, const double* cold, const double* cnew,
-                         double tau, int r);
+                         double tau, int r, int copy_only);
+/* copy_only != 0: ghosts that would need the coarser level are left unchanged (coefficient
+ * fields of finer levels are given, not interpolated) */
 
 /* coarse := mean of the r*r fine cells over every coarse interior cell covered by a fine box */
 int orc_average_down(int nf, const orc_box* fboxes, const double* fpool,
@@ -90,7 +92,8 @@ int orc_interp_cell(int ncb, const orc_box* cboxes, const double* cold, const do
 int orc_level_fill_ghost_adjoint(int nb, const orc_box* boxes, double* gpool, int ncomp, int mbc,
                                  int NX, int NY, const int* bc,
                                  int ncb, const orc_box* cboxes, double* gcold, double* gcnew,
-                                 const double* cold, const double* cnew, double tau, int r);
+                                 const double* cold, const double* cnew, double tau, int r,
+                                 int copy_only);
 int orc_average_down_adjoint(int nf, const orc_box* fboxes, double* gfpool,
                              int nc, const orc_box* cboxes, double* gcpool, int ncomp, int mbc, int r);
 

@@ -1,0 +1,151 @@
+"""Differentiable rollouts: gradients of a functional of the final state with respect to the
+initial state and the medium (rho, K), through the hand-written adjoint kernels.
+
+`rollout(H, q0, rho, K, ncoarse, every)` is a torch.autograd.Function over `ncoarse` coarse
+steps of hierarchy H (any number of levels and runs).  The forward keeps a checkpoint of every
+level's state every `every` coarse steps; the backward recomputes one segment at a time from its
+checkpoint (recording each level-step's input state and the pre-average coarse state) and runs
+the reverse of the AMR time step of Sec. 2.2 on the device:
+
+  average (Sec. 2.3)        -> claw_average_down_adjoint
+  fine substeps, last first -> claw_level_step_adjoint + claw_fill_ghost_adjoint (the
+                               interpolation adjoint feeds the coarse old / new states)
+  coarse level-step         -> claw_level_step_adjoint + claw_fill_ghost_adjoint
+
+with the time steps frozen at their forward values.  The medium gradients leave through
+claw_medium_aux_adjoint and claw_fill_ghost_coef_adjoint.  This module only sequences calls:
+every arithmetic operation of the gradient runs in libclaw.so.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import claw
+
+
+class _Node:
+    __slots__ = ("L", "q_in", "cold", "cnew", "tau", "pre_avg", "fine")
+
+    def __init__(self, L, q_in, cold, cnew, tau):
+        self.L, self.q_in, self.cold, self.cnew, self.tau = L, q_in, cold, cnew, tau
+        self.pre_avg = None
+        self.fine = []
+
+
+def _advance_record(H, L, cold, cnew, tau):
+    """one level-step of level L (and its finer substeps), recording what the reverse needs"""
+    q = H.q[L][H.cur[L]]
+    claw.claw_fill_ghost(H.ctx, L, q, cold, cnew, tau)
+    node = _Node(L, q.clone(), cold, cnew, tau)
+    H.step_level(L)
+    new = H.q[L][1 - H.cur[L]]
+    if L + 1 < H.nlev:
+        node.pre_avg = new.clone()
+        r = H.ratio(L + 1)
+        for k in range(r):
+            node.fine.append(_advance_record(H, L + 1, node.q_in, node.pre_avg, k / r))
+        claw.claw_average_down(H.ctx, L + 1, H.q[L + 1][H.cur[L + 1]], new)
+    H.cur[L] ^= 1
+    return node
+
+
+def _reverse(H, node, lam, g_aux, lam_cold=None, lam_cnew=None):
+    """adjoint of `node` (one level-step of level node.L with its substeps).  lam[L] holds the
+    adjoint of each level's state after the node and is replaced by the adjoint of the state
+    before it; the interpolation adjoints of node.L's ghost fill go to lam_cold / lam_cnew (the
+    coarser level's old and pre-average new states)."""
+    L = node.L
+    lam_pre = lam[L]
+    lam_in = torch.zeros_like(lam_pre)
+    if node.fine:
+        # averaging: covered coarse adjoints move to the fine state and are zeroed
+        claw.claw_average_down_adjoint(H.ctx, L + 1, lam[L + 1], lam_pre)
+        for fnode in reversed(node.fine):
+            _reverse(H, fnode, lam, g_aux, lam_cold=lam_in, lam_cnew=lam_pre)
+    claw.claw_level_step_adjoint(H.ctx, L, node.q_in, lam_pre, lam_in, H.aux[L], g_aux[L], H.dt)
+    claw.claw_fill_ghost_adjoint(H.ctx, L, lam_in, lam_cold, lam_cnew, node.cold, node.cnew, node.tau)
+    lam[L] = lam_in
+
+
+class _Rollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, H, ncoarse, every, nlev, dt, *tensors):
+        q0 = tensors[:nlev]
+        rho = tensors[nlev:2 * nlev] if H.medium else [None] * nlev
+        K = tensors[2 * nlev:3 * nlev] if H.medium else [None] * nlev
+        with torch.no_grad():
+            for L in range(nlev):
+                H.cur[L] = 0
+                H.q[L][0].copy_(q0[L])
+                if H.medium:
+                    H.rho[L].copy_(rho[L])
+                    H.K[L].copy_(K[L])
+                    claw.claw_fill_ghost_coef(H.ctx, L, H.rho[L])
+                    claw.claw_fill_ghost_coef(H.ctx, L, H.K[L])
+                    claw.claw_medium_aux(H.ctx, L, H.rho[L], H.K[L], H.aux[L])
+            if dt is None:
+                H.freeze_dt = False
+                H.init_dt()
+            else:   # time steps frozen at the caller's values (e.g. for finite differences)
+                H.freeze_dt = True
+                H.dt.copy_(dt)
+            checkpoints = []
+            for n in range(ncoarse):
+                if n % every == 0:
+                    checkpoints.append(([H.q[L][H.cur[L]].clone() for L in range(nlev)], H.dt.clone()))
+                H.coarse_step()
+            out = [H.q[L][H.cur[L]].clone() for L in range(nlev)]
+        ctx.H, ctx.ncoarse, ctx.every, ctx.nlev = H, ncoarse, every, nlev
+        ctx.checkpoints = checkpoints
+        ctx.frozen = dt is not None
+        H.freeze_dt = False
+        return tuple(out)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        H, nlev, every, ncoarse = ctx.H, ctx.nlev, ctx.every, ctx.ncoarse
+        lam = [g.clone() if g is not None else torch.zeros_like(H.q[L][0]) for L, g in enumerate(grads)]
+        g_aux = [torch.zeros_like(H.aux[L]) if H.medium else None for L in range(nlev)]
+        nseg = len(ctx.checkpoints)
+        for s in reversed(range(nseg)):
+            states, dt0 = ctx.checkpoints[s]
+            n0, n1 = s * every, min((s + 1) * every, ncoarse)
+            # recompute the segment, recording each coarse step
+            for L in range(nlev):
+                H.cur[L] = 0
+                H.q[L][0].copy_(states[L])
+            H.dt.copy_(dt0)
+            tapes = []
+            for _ in range(n0, n1):
+                dt = H.dt.clone()
+                tapes.append((_advance_record(H, 0, None, None, 0.0), dt))
+                if ctx.frozen:
+                    H.smax.zero_()
+                else:
+                    claw.claw_dt_update(H.ctx, 0, H.smax, H.dt)
+            for node, dt in reversed(tapes):
+                H.dt.copy_(dt)   # frozen forward time step
+                _reverse(H, node, lam, g_aux)
+        grads_out = [None, None, None, None, None] + lam
+        if H.medium:
+            g_rho, g_K = [], []
+            for L in range(nlev):
+                gr = torch.zeros_like(H.rho[L])
+                gk = torch.zeros_like(H.K[L])
+                claw.claw_medium_aux_adjoint(H.ctx, L, H.rho[L], H.K[L], g_aux[L], gr, gk)
+                claw.claw_fill_ghost_coef_adjoint(H.ctx, L, gr)
+                claw.claw_fill_ghost_coef_adjoint(H.ctx, L, gk)
+                g_rho.append(gr)
+                g_K.append(gk)
+            grads_out += g_rho + g_K
+        return tuple(grads_out)
+
+
+def rollout(H, q0, rho=None, K=None, ncoarse=1, every=20, dt=None):
+    """final states (one pool per level) after `ncoarse` coarse steps from q0 (pools per level),
+    differentiable with respect to q0 and, for a cell-wise medium, the rho and K pools.
+    dt: None for Eq. cfl time steps, else a device tensor of per-run level-0 time steps used
+    unchanged for every coarse step.  The gradient holds the time steps fixed either way."""
+    nlev = H.nlev
+    tensors = list(q0) + (list(rho) + list(K) if H.medium else [])
+    return _Rollout.apply(H, ncoarse, every, nlev, dt, *tensors)

@@ -54,6 +54,8 @@ _SIGNATURES = {
     "claw_medium_aux_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_fill_ghost": ([VP, I32, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_adjoint": ([VP, I32, VP, VP, VP, VP, VP, DBL, VP], ctypes.c_int),
+    "claw_fill_ghost_coef": ([VP, I32, VP, VP], ctypes.c_int),
+    "claw_fill_ghost_coef_adjoint": ([VP, I32, VP, VP], ctypes.c_int),
     "claw_cfl_max": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_dt_update": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_level_step": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
@@ -152,6 +154,14 @@ def claw_fill_ghost_adjoint(ctx, level, lam, lam_c_old=None, lam_c_new=None, qc_
     _check("claw_fill_ghost_adjoint", load().claw_fill_ghost_adjoint(
         ctx, level, _ptr(lam), _ptr(lam_c_old), _ptr(lam_c_new), _ptr(qc_old), _ptr(qc_new), float(tau),
         _stream(stream)))
+
+
+def claw_fill_ghost_coef(ctx, level, a, stream=None):
+    _check("claw_fill_ghost_coef", load().claw_fill_ghost_coef(ctx, level, _ptr(a), _stream(stream)))
+
+
+def claw_fill_ghost_coef_adjoint(ctx, level, g, stream=None):
+    _check("claw_fill_ghost_coef_adjoint", load().claw_fill_ghost_coef_adjoint(ctx, level, _ptr(g), _stream(stream)))
 
 
 def claw_cfl_max(ctx, level, aux, smax, stream=None):

@@ -41,6 +41,9 @@ struct claw_ctx {
     // per-level tiles ordered by box for the per-box launches
     std::vector<int> ptile_start[CLAW_MAXLEV];
     TileDev* ptiles[CLAW_MAXLEV] = {};
+    // per-level tiles of the adjoint kernel (its own fixed tile edge)
+    TileDev* atiles[CLAW_MAXLEV] = {};
+    int natiles[CLAW_MAXLEV] = {};
     std::vector<TmapCache> tmaps[CLAW_MAXLEV];
     unsigned long long stamp = 0;
     std::atomic<long long> launches{0};
@@ -150,9 +153,15 @@ void free_level(claw_ctx* ctx, int L)
     cudaFree(d.patches);
     cudaFree(d.tiles);
     cudaFree(d.copies);
+    cudaFree(d.ccopies);
+    d.ccopies = nullptr;
+    d.nccopy = 0;
     cudaFree(d.interps);
     cudaFree(d.avgs);
     cudaFree(ctx->ptiles[L]);
+    cudaFree(ctx->atiles[L]);
+    ctx->atiles[L] = nullptr;
+    ctx->natiles[L] = 0;
     for (auto& t : ctx->tmaps[L]) cudaFree(t.dev);
     ctx->tmaps[L].clear();
     ctx->ptiles[L] = nullptr;
@@ -201,7 +210,27 @@ int build_tiles(claw_ctx* ctx, int L)
     d.ntiles = (int)t.size();
     for (auto& tm : ctx->tmaps[L]) cudaFree(tm.dev);
     ctx->tmaps[L].clear();
-    return upload(&d.tiles, t);
+    rc = upload(&d.tiles, t);
+    if (rc) return rc;
+    // adjoint tiles
+    std::vector<TileDev> at;
+    const int e = adjoint_tile();
+    for (int n = 0; n < d.nboxes; ++n) {
+        const claw_box& b = d.boxes[n];
+        for (int y = 0; y < b.ny; y += e)
+            for (int x = 0; x < b.nx; x += e) {
+                TileDev T;
+                T.patch = n;
+                T.x0 = (short)x;
+                T.y0 = (short)y;
+                T.tx = (short)std::min(e, b.nx - x);
+                T.ty = (short)std::min(e, b.ny - y);
+                T.pad = 0;
+                at.push_back(T);
+            }
+    }
+    ctx->natiles[L] = (int)at.size();
+    return upload(&ctx->atiles[L], at);
 }
 
 struct GhostEntry {
@@ -639,6 +668,19 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     int rc = build_ghost_tables(ctx, L, rects, cells);
     if (rc) return rc;
     if (L > 0) build_avg_tables(ctx, L, avg);
+    // the same copies for one-plane pools: offsets from coff, no wall sign flips
+    std::vector<CopyRect> crects;
+    {
+        std::vector<claw_box> saved = d.boxes;
+        for (auto& b : d.boxes) b.qoff = b.coff;
+        std::vector<InterpCell> unused;
+        rc = build_ghost_tables(ctx, L, crects, unused);
+        d.boxes = saved;
+        if (rc) return rc;
+        for (auto& r : crects) r.flags = 0;
+    }
+    if ((rc = upload(&d.ccopies, crects))) return rc;
+    d.nccopy = (int)crects.size();
     if ((rc = upload(&d.patches, d.hpatches)) || (rc = upload(&d.copies, rects)) ||
         (rc = upload(&d.interps, cells)) || (rc = upload(&d.avgs, avg)))
         return rc;
@@ -706,6 +748,26 @@ int claw_fill_ghost(claw_ctx* ctx, int32_t L, double* q, const double* qc_old, c
         ctx->launches += d.ninterp > 0;
     }
     return cuda_rc(e);
+}
+
+int claw_fill_ghost_coef(claw_ctx* ctx, int32_t L, double* a, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !a) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    ctx->launches += d.nccopy > 0;
+    return cuda_rc(launch_fill_copy(d.ccopies, d.nccopy, a, (cudaStream_t)stream, 1));
+}
+
+int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t L, double* g, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !g) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    DevGuard gd(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    ctx->launches += d.nccopy > 0;
+    return cuda_rc(launch_fill_copy_adjoint(d.ccopies, d.nccopy, g, (cudaStream_t)stream, 1));
 }
 
 int claw_fill_ghost_adjoint(claw_ctx* ctx, int32_t L, double* lam, double* lco, double* lcn, const double* qc_old,
@@ -822,9 +884,11 @@ int claw_level_step_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const
     LevelDev& d = ctx->lev[L];
     if (d.ntiles == 0) return CLAW_OK;
     StepArgs a = make_args(ctx, L, q_old, nullptr, aux, dt, nullptr);
-    const int grid = std::min(d.ntiles, 2 * ctx->nsm);
+    a.tiles = ctx->atiles[L];
+    a.ntiles = ctx->natiles[L];
+    const int grid = std::min(a.ntiles, ctx->nsm);
     ctx->launches += 1;
-    return cuda_rc(launch_step_adjoint(a, lam_old, g_aux, ctx->medium, ctx->limiter, d.tx, d.ty, grid,
+    return cuda_rc(launch_step_adjoint(a, lam_new, lam_old, g_aux, ctx->medium, ctx->limiter, grid,
                                        (cudaStream_t)stream));
 }
 

@@ -13,14 +13,14 @@ static inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------------------ same-level copy
 // One warp per rectangle; lanes stride over its w*h*3 elements.
-__global__ void fill_copy_kernel(const CopyRect* __restrict__ rects, int n, double* __restrict__ q)
+__global__ void fill_copy_kernel(const CopyRect* __restrict__ rects, int n, double* __restrict__ q, int ncomp)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
     const CopyRect R = rects[warp];
     const int cells = R.w * R.h;
-    for (int k = lane; k < 3 * cells; k += 32) {
+    for (int k = lane; k < ncomp * cells; k += 32) {
         const int m = k / cells, e = k - m * cells;
         const int y = e / R.w, x = e - y * R.w;
         double v = q[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx];
@@ -31,14 +31,15 @@ __global__ void fill_copy_kernel(const CopyRect* __restrict__ rects, int n, doub
 
 // reverse: ghost adjoint flows into its source, then the ghost adjoint is cleared.  Sources
 // are interior cells and several ghosts may share one (extrapolation), hence the atomics.
-__global__ void fill_copy_adjoint_kernel(const CopyRect* __restrict__ rects, int n, double* __restrict__ lam)
+__global__ void fill_copy_adjoint_kernel(const CopyRect* __restrict__ rects, int n, double* __restrict__ lam,
+                                         int ncomp)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
     const CopyRect R = rects[warp];
     const int cells = R.w * R.h;
-    for (int k = lane; k < 3 * cells; k += 32) {
+    for (int k = lane; k < ncomp * cells; k += 32) {
         const int m = k / cells, e = k - m * cells;
         const int y = e / R.w, x = e - y * R.w;
         const long long d = R.dst + m * R.dplane + (long long)y * R.dpitch + x;
@@ -49,17 +50,17 @@ __global__ void fill_copy_adjoint_kernel(const CopyRect* __restrict__ rects, int
     }
 }
 
-cudaError_t launch_fill_copy(const CopyRect* r, int n, double* q, cudaStream_t s)
+cudaError_t launch_fill_copy(const CopyRect* r, int n, double* q, cudaStream_t s, int ncomp)
 {
     if (n <= 0) return cudaSuccess;
-    fill_copy_kernel<<<div_up((long long)n * 32, 256), 256, 0, s>>>(r, n, q);
+    fill_copy_kernel<<<div_up((long long)n * 32, 256), 256, 0, s>>>(r, n, q, ncomp);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill_copy_adjoint(const CopyRect* r, int n, double* lam, cudaStream_t s)
+cudaError_t launch_fill_copy_adjoint(const CopyRect* r, int n, double* lam, cudaStream_t s, int ncomp)
 {
     if (n <= 0) return cudaSuccess;
-    fill_copy_adjoint_kernel<<<div_up((long long)n * 32, 256), 256, 0, s>>>(r, n, lam);
+    fill_copy_adjoint_kernel<<<div_up((long long)n * 32, 256), 256, 0, s>>>(r, n, lam, ncomp);
     return cudaGetLastError();
 }
 

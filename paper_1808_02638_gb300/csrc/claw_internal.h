@@ -85,6 +85,8 @@ struct LevelDev {
     PatchDev* patches = nullptr;
     TileDev* tiles = nullptr;
     CopyRect* copies = nullptr;
+    CopyRect* ccopies = nullptr;   // the same copies for one-plane coefficient pools (coff offsets)
+    int nccopy = 0;
     InterpCell* interps = nullptr;
     AvgRect* avgs = nullptr;
     void* tmaps = nullptr;   // CUtensorMap per box (128 B each), built for the current tiling
@@ -118,14 +120,15 @@ enum : int { ERR_NAN = 1, ERR_CFL = 2, ERR_TIMEOUT = 4 };
 cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s);
 int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int nt, int staging);
-cudaError_t launch_step_adjoint(const StepArgs& a, double* lam_old, double* g_aux, int medium,
-                                int limiter, int tx, int ty, int grid, cudaStream_t s);
+cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
+                                int medium, int limiter, int grid, cudaStream_t s);
+int adjoint_tile();   // the adjoint kernel's square tile edge
 
 // launchers (claw_ghost.cu)
-cudaError_t launch_fill_copy(const CopyRect* r, int n, double* q, cudaStream_t s);
+cudaError_t launch_fill_copy(const CopyRect* r, int n, double* q, cudaStream_t s, int ncomp = 3);
 cudaError_t launch_fill_interp(const InterpCell* c, int n, double* q, const double* cold,
                                const double* cnew, double tau, cudaStream_t s);
-cudaError_t launch_fill_copy_adjoint(const CopyRect* r, int n, double* lam, cudaStream_t s);
+cudaError_t launch_fill_copy_adjoint(const CopyRect* r, int n, double* lam, cudaStream_t s, int ncomp = 3);
 cudaError_t launch_fill_interp_adjoint(const InterpCell* c, int n, double* lam, double* lco,
                                        double* lcn, const double* cold, const double* cnew,
                                        double tau, cudaStream_t s);

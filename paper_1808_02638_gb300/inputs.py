@@ -203,6 +203,44 @@ def const_pool(lev: Level, value: float) -> np.ndarray:
     return pool
 
 
+def fourier_field(seed: int, nx: int, ny: int, kmax: int = 4, even: bool = False) -> np.ndarray:
+    """Smooth random field on the cell centres of [-1,1]^2 (shape (ny, nx)): a sum of
+    cos/sin modes with wave numbers |kx|, |ky| <= kmax (in units of pi) and seeded U[-1,1]
+    coefficients, normalised to max |f| = 1.  even=True keeps the cos(kx x) cos(ky y) modes
+    only (even in x and in y)."""
+    x = -1.0 + (np.arange(nx) + 0.5) * (2.0 / nx)
+    y = -1.0 + (np.arange(ny) + 0.5) * (2.0 / ny)
+    X, Y = np.meshgrid(x, y)
+    k = np.arange(0, kmax + 1)
+    coef = 2.0 * uniform(seed, 4 * len(k) ** 2) - 1.0
+    f = np.zeros((ny, nx))
+    n = 0
+    for a in k:
+        for b in k:
+            if even:
+                f += coef[n] * np.cos(np.pi * a * X) * np.cos(np.pi * b * Y)
+            else:
+                ph = np.pi * (a * X + b * Y)
+                f += coef[n] * np.cos(ph) + coef[n + 1] * np.sin(ph)
+                ph2 = np.pi * (a * X - b * Y)
+                f += coef[n + 2] * np.cos(ph2) + coef[n + 3] * np.sin(ph2)
+            n += 4
+    return f / np.abs(f).max()
+
+
+def annulus_window(nx: int, ny: int, r0: float = 0.3, width: float = 0.1) -> np.ndarray:
+    """(1 + cos(pi (r - r0)/width))/2 inside |r - r0| < width, else 0, at cell centres of
+    [-1,1]^2: a smooth bump over the pulse's ring."""
+    x = -1.0 + (np.arange(nx) + 0.5) * (2.0 / nx)
+    y = -1.0 + (np.arange(ny) + 0.5) * (2.0 / ny)
+    X, Y = np.meshgrid(x, y)
+    r = np.sqrt(X * X + Y * Y)
+    w = np.zeros_like(r)
+    inside = np.abs(r - r0) < width
+    w[inside] = 0.5 * (1.0 + np.cos(np.pi * (r[inside] - r0) / width))
+    return w
+
+
 # ---------------------------------------------------------------- tilings
 
 def uniform_tiling(NX: int, NY: int, bx: int, by: int) -> np.ndarray:

@@ -107,6 +107,7 @@ class Hierarchy:
         self.dt = torch.zeros(self.nruns, dtype=torch.float64, device=self.dev)
         self.smax = torch.zeros(self.nruns, dtype=torch.float64, device=self.dev)
         self.patchwise = False
+        self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)
 
     # -------------------------------------------------------------- stepping
     def ratio(self, L):
@@ -138,7 +139,10 @@ class Hierarchy:
 
     def coarse_step(self, stream=None):
         self.advance(0, stream=stream)
-        claw.claw_dt_update(self.ctx, 0, self.smax, self.dt, stream)
+        if self.freeze_dt:
+            self.smax.zero_()
+        else:
+            claw.claw_dt_update(self.ctx, 0, self.smax, self.dt, stream)
 
     def launches_per_coarse_step(self):
         """kernels one coarse step enqueues (counted from the library's own counter)."""

@@ -1,0 +1,138 @@
+"""GPU adjoint (claw_level_step_adjoint and the reverse AMR transfers behind
+paper_1808_02638_gb300.adjoint.rollout) against the oracle's reverse mode and against central
+finite differences of a receiver functional in smooth directions."""
+import numpy as np
+import pytest
+
+from paper_1808_02638_gb300 import inputs
+
+from gpu_helpers import lib_ready
+
+pytestmark = pytest.mark.gpu
+M = 2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib_ready()
+
+
+def _tensors(H, pools, kind):
+    import torch
+    out = []
+    for L in range(H.nlev):
+        ref = {"q": H.q[L][0], "c": H.rho[L]}[kind]
+        a = np.zeros(ref.numel())
+        for (ri, qb, cb) in H.layout[L]:
+            base = qb if kind == "q" else cb
+            a[base:base + pools[ri][L].size] = pools[ri][L]
+        out.append(torch.from_numpy(a).to(ref.device).requires_grad_(True))
+    return out
+
+
+def _receiver_J(H, outs, lev0, box):
+    i0, j0, n = box
+    nx, ny = int(lev0.boxes[0][2]), int(lev0.boxes[0][3])
+    v = outs[0][:3 * (nx + 4) * (ny + 4)].view(3, ny + 4, nx + 4)
+    return (v[0, M + j0:M + j0 + n, M + i0:M + i0 + n] ** 2).sum()
+
+
+def _compare(got, want, tol):
+    scale = max(np.abs(w).max() for w in want)
+    err = max(np.abs(g[:w.size] - w).max() for g, w in zip(got, want)) / scale
+    assert err <= tol, err
+    return err
+
+
+@pytest.mark.parametrize("nlev", [1, 2])
+def test_adjoint_matches_oracle_reverse_mode(nlev):
+    import torch
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300.adjoint import rollout
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = 32
+    run = inputs.Run(*inputs.PULSE_DOMAIN)
+    if nlev == 1:
+        run.levels = [inputs.Level(n, n, 2 / n, 2 / n, [(0, 0, n, n)])]
+    else:
+        run.levels = inputs.amr_levels(run, n, 4, [(0.2, 0.45)], [31])
+    r2 = inputs.smooth_field(21, n, n, 0.5, 2.0, sigma=3.0)
+    k2 = inputs.smooth_field(22, n, n, 1.0, 8.0, sigma=3.0)
+    q = [inputs.init_q(run, lev) for lev in run.levels]
+    rho = [inputs.coef_pool(lev, r2, 4 ** L) for L, lev in enumerate(run.levels)]
+    K = [inputs.coef_pool(lev, k2, 4 ** L) for L, lev in enumerate(run.levels)]
+    nsteps = 6 if nlev == 1 else 2
+    box = (18, 10, 6)
+    H = Hierarchy([run], [q], [rho], [K])
+    tq, tr, tk = _tensors(H, [q], "q"), _tensors(H, [rho], "c"), _tensors(H, [K], "c")
+    outs = rollout(H, tq, tr, tk, ncoarse=nsteps, every=4)
+    J = _receiver_J(H, outs, run.levels[0], box)
+    J.backward()
+    torch.cuda.synchronize()
+
+    def final_adjoint(qs):
+        lam = [np.zeros_like(a) for a in qs]
+        i0, j0, nn = box
+        v = inputs.box_view(qs[0], 0, n, n, 3)
+        inputs.box_view(lam[0], 0, n, n, 3)[0, M + j0:M + j0 + nn, M + i0:M + i0 + nn] = \
+            2 * v[0, M + j0:M + j0 + nn, M + i0:M + i0 + nn]
+        return lam
+
+    O = OracleHierarchy(run, q, rho, K)
+    gq, gr, gk = O.gradient(nsteps, final_adjoint)
+    assert float(J) == pytest.approx(float((inputs.box_view(O.q[0], 0, n, n, 3)
+                                            [0, M + 10:M + 16, M + 18:M + 24] ** 2).sum()), rel=1e-11)
+    _compare([t.grad.cpu().numpy() for t in tq], gq, 1e-10)
+    _compare([t.grad.cpu().numpy() for t in tr], gr, 1e-10)
+    _compare([t.grad.cpu().numpy() for t in tk], gk, 1e-10)
+
+
+def test_heterogeneous_receiver_gradient_matches_finite_differences():
+    # 256^2, rho ~ U[0.5,2], K ~ U[1,8] smoothed (sigma 8 cells), radial pulse, J = sum p^2 over
+    # the 16 x 16 receiver box after 400 steps, checkpoints every 20; central differences
+    # (h = 1e-6, time steps frozen) along 8 seeded smooth directions
+    import torch
+    from paper_1808_02638_gb300.adjoint import rollout
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n, nsteps = 256, 400
+    run, r2, k2 = inputs.config3(n)
+    lev = run.levels[0]
+    q = inputs.init_q(run, lev)
+    rho, K = inputs.coef_pool(lev, r2, 1), inputs.coef_pool(lev, k2, 1)
+    box = inputs.receiver_box(n)
+    H = Hierarchy([run], [[q]], [[rho]], [[K]])
+    tq, tr, tk = _tensors(H, [[q]], "q"), _tensors(H, [[rho]], "c"), _tensors(H, [[K]], "c")
+    outs = rollout(H, tq, tr, tk, ncoarse=nsteps, every=20)
+    J = _receiver_J(H, outs, lev, box)
+    J.backward()
+    H.init_dt()
+    dt = H.dt.clone()
+    gq, gr, gk = tq[0].grad, tr[0].grad, tk[0].grad
+    win = inputs.annulus_window(n, n)
+
+    def pad_q(f):
+        a = np.zeros(tq[0].numel())
+        inputs.box_view(a, 0, n, n, 3)[0, M:-M, M:-M] = f
+        return torch.from_numpy(a).to(tq[0].device)
+
+    def pad_c(f):
+        a = np.zeros(tr[0].numel())
+        inputs.box_view(a, 0, n, n, 1)[0, M:-M, M:-M] = f
+        return torch.from_numpy(a).to(tr[0].device)
+
+    def Jof(dq, dr, dk, h):
+        with torch.no_grad():
+            o = rollout(H, [tq[0] + h * dq], [tr[0] + h * dr], [tk[0] + h * dk], ncoarse=nsteps, every=nsteps,
+                        dt=dt)
+            return float(_receiver_J(H, o, lev, box))
+
+    h = 1e-6
+    errs = []
+    for seed in range(3100, 3108):
+        dq = pad_q(win * inputs.fourier_field(seed, n, n, even=True))
+        dr = pad_c(0.25 * inputs.fourier_field(seed + 1000, n, n))
+        dk = pad_c(inputs.fourier_field(seed + 2000, n, n))
+        fd = (Jof(dq, dr, dk, h) - Jof(dq, dr, dk, -h)) / (2 * h)
+        ad = float((gq * dq).sum() + (gr * dr).sum() + (gk * dk).sum())
+        errs.append(abs(ad - fd) / abs(fd))
+    assert max(errs) <= 1e-6, errs
