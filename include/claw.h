@@ -155,6 +155,20 @@ int claw_dt_update(claw_ctx* ctx, int32_t level, double* smax, double* dt, void*
 int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
                     const double* aux, const double* dt, double* smax, void* stream);
 
+/* claw_level_step with fused epilogues selected by `flags`:
+ *   CLAW_ADVANCE_PUSH_GHOSTS: every tile also writes the ghosts of q_new that copy its new cells
+ *     (same-level copies and physical boundaries; each ghost has exactly one source tile), so
+ *     the next step of this level needs no separate fill unless it has interpolated ghosts;
+ *   CLAW_ADVANCE_UPDATE_DT: after the step, Eq. cfl is applied on the device by the last CTA
+ *     to finish (as claw_dt_update with level-0 dx, dy): dt[r] is replaced by the next time step
+ *     and smax[r] reset.  Use it when this level-step ends the coarse step (a hierarchy of one
+ *     level); dt is then both read and written by the launch.
+ * Errors as claw_level_step, CLAW_EINVAL for unknown flags. */
+#define CLAW_ADVANCE_PUSH_GHOSTS 1
+#define CLAW_ADVANCE_UPDATE_DT 2
+int claw_level_advance(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
+                       const double* aux, double* dt, double* smax, int32_t flags, void* stream);
+
 /* The same step with one kernel launch per box (the per-patch launch pattern of Sec. 3.1.2,
  * kept as the comparison baseline of the fused launch). */
 int claw_level_step_patchwise(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,

@@ -60,6 +60,7 @@ _SIGNATURES = {
     "claw_dt_update": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_level_step": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_level_step_patchwise": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_level_advance": ([VP, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
     "claw_level_step_noalloc": ([I32, I32, DBL, DBL, I32, I32, I32, DBL, DBL, VP, VP, VP, VP, VP, VP],
                                 ctypes.c_int),
     "claw_average_down": ([VP, I32, VP, VP, VP], ctypes.c_int),
@@ -175,6 +176,15 @@ def claw_dt_update(ctx, level, smax, dt, stream=None):
 def claw_level_step(ctx, level, q_old, q_new, aux, dt, smax, stream=None):
     _check("claw_level_step", load().claw_level_step(ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt),
                                                      _ptr(smax), _stream(stream)))
+
+
+CLAW_ADVANCE_PUSH_GHOSTS = 1
+CLAW_ADVANCE_UPDATE_DT = 2
+
+
+def claw_level_advance(ctx, level, q_old, q_new, aux, dt, smax, flags, stream=None):
+    _check("claw_level_advance", load().claw_level_advance(
+        ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax), int(flags), _stream(stream)))
 
 
 def claw_level_step_patchwise(ctx, level, q_old, q_new, aux, dt, smax, stream=None):

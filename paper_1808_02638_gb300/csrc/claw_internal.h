@@ -37,11 +37,22 @@ struct PatchDev {
     double dtscale;   // this level's dt / level-0 dt = 1 / (ratio_1 ... ratio_L)
 };
 
-// One tile of the fused step: interior cells [x0, x0+tx) x [y0, y0+ty) of box `patch`.
+// One tile of the fused step: interior cells [x0, x0+tx) x [y0, y0+ty) of box `patch`;
+// pushes [push0, push0 + npush) are the ghost rectangles its new values fill.
 struct TileDev {
     int patch;
     short x0, y0, tx, ty;
-    int pad;
+    int push0, npush;
+};
+
+// Ghost cells of q_new that one tile fills from its own new interior values (same-level copy
+// and physical boundary, written by the tile that computed the source cells).  Element (x, y),
+// plane m:  q_new[dst + m*dplane + y*dpitch + x] = sign_m * new(sx0 + x*ssx, sy0 + y*ssy),
+// source coordinates local to the tile's interior.
+struct PushRect {
+    long long dst, dplane;
+    short sx0, sy0, w, h, ssx, ssy;
+    int dpitch, flags;
 };
 
 // Rectangle of ghost cells copied from interior cells of the same level (same-level copy and
@@ -74,6 +85,16 @@ struct AvgRect {
 };
 
 // Per (level) device tables.
+struct GhostCopy {   // one ghost cell filled by a copy (host-side, for the push tables)
+    long long dst;     // plane-0 element of the ghost
+    long long dplane;
+    int dpitch;
+    int src;           // source box
+    int si, sj;        // source cell (level index)
+    int gi, gj;        // ghost cell (level index), for run detection
+    int flags;
+};
+
 struct LevelDev {
     int nboxes = 0;
     int ntiles = 0;
@@ -91,6 +112,9 @@ struct LevelDev {
     AvgRect* avgs = nullptr;
     void* tmaps = nullptr;   // CUtensorMap per box (128 B each), built for the current tiling
     int tmap_tx = 0, tmap_ty = 0;
+    PushRect* pushes = nullptr;
+    int npush = 0;
+    std::vector<GhostCopy> gcopies;   // every copied ghost of the level (host)
     // host copies
     std::vector<claw_box> boxes;
     std::vector<PatchDev> hpatches;
@@ -98,19 +122,28 @@ struct LevelDev {
 };
 
 struct StepArgs {
-    const PatchDev* patches;
-    const TileDev* tiles;
-    const void* tmaps;
-    int ntiles;
-    const double* qold;
-    double* qnew;
-    const double* aux;
-    const double* dt;
-    double* smax;
-    int* err;
+    const PatchDev* patches = nullptr;
+    const TileDev* tiles = nullptr;
+    const void* tmaps = nullptr;
+    int ntiles = 0;
+    const double* qold = nullptr;
+    double* qnew = nullptr;
+    const double* aux = nullptr;
+    const double* dt = nullptr;
+    double* smax = nullptr;
+    int* err = nullptr;
     // scheme
-    int order, transverse;
-    double rho0, K0;   // uniform medium
+    int order = 2, transverse = 2;
+    double rho0 = 1.0, K0 = 1.0;   // uniform medium
+    // fused epilogues (0 = off)
+    const PushRect* pushes = nullptr;   // fill the same-level / physical ghosts of qnew
+    int push = 0;
+    int dtupd = 0;                      // the last CTA applies Eq. cfl to dt and resets smax
+    double* dt_out = nullptr;
+    const double* minh = nullptr;       // level-0 min(dx, dy) per run
+    const double* cflv = nullptr;       // desired CFL per run
+    unsigned int* done = nullptr;       // CTA completion counter (0 between launches)
+    int nruns = 0;
 };
 
 // error flag bits written by kernels

@@ -177,6 +177,28 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
     return a > b ? a : b;
 }
 
+// fused Eq. cfl, run by thread 0 of every CTA as its last action: the last CTA to finish sees
+// every CTA's speed maximum (each published its atomics before its fence and its count), checks
+// the CFL number of the step just taken, sets the next dt, resets the maxima and re-arms the
+// counter.  No CTA waits on another.
+__device__ __forceinline__ void finish_cta(const StepArgs& A)
+{
+    if (!A.dtupd) return;
+    __threadfence();
+    const unsigned prev = atomicAdd(A.done, 1u);
+    if (prev != gridDim.x - 1) return;
+    __threadfence();
+    for (int r = 0; r < A.nruns; ++r) {
+        const double s = *reinterpret_cast<volatile double*>(A.smax + r);
+        const double used = *reinterpret_cast<volatile double*>(A.dt_out + r);
+        if (s * used > A.minh[r] * (1.0 + 1e-12)) atomicOr(A.err, ERR_CFL);
+        if (s > 0.0) A.dt_out[r] = A.cflv[r] * A.minh[r] / s;
+        A.smax[r] = 0.0;
+    }
+    __threadfence();
+    *reinterpret_cast<volatile unsigned*>(A.done) = 0u;
+}
+
 // ------------------------------------------------------------------------- the kernel
 // MED: 0 uniform medium (rho0, K0), 1 cell-wise aux planes.
 // STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered).
@@ -261,6 +283,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
                     atomicOr(A.err, ERR_TIMEOUT);
                     // let the prefetch in flight (if any) land before the CTA exits
                     if (tn < A.ntiles) mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+                    finish_cta(A);   // keeps the completion count consistent
                 }
                 return;
             }
@@ -566,6 +589,28 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             dst[o] = p;
             dst[WH + o] = u;
             dst[2 * WH + o] = v;
+            if (A.push) {   // keep the new values for the ghost pushes (each cell is its own thread's)
+                sp[iq] = p;
+                su[iq] = u;
+                sv[iq] = v;
+            }
+        }
+        // ghost pushes: the same-level and physical-boundary ghosts of q_new whose source cells
+        // this tile just computed (each ghost has exactly one source, so no two tiles write it)
+        if (A.push && T.npush > 0) {
+            __syncthreads();
+            for (int pr = T.push0; pr < T.push0 + T.npush; ++pr) {
+                const PushRect R = A.pushes[pr];
+                const int cells = (int)R.w * R.h;
+                for (int k = tid; k < 3 * cells; k += NT) {
+                    const int m = k / cells, e = k - m * cells;
+                    const int y = e / R.w, x = e - y * R.w;
+                    const int src = (R.sx0 + x * R.ssx + 2) + (R.sy0 + y * R.ssy + 2) * G::SW;
+                    double val = sq[m * G::QPL + src];
+                    if ((m == 1 && (R.flags & 1)) || (m == 2 && (R.flags & 2))) val = -val;
+                    A.qnew[R.dst + m * R.dplane + (long long)y * R.dpitch + x] = val;
+                }
+            }
         }
         __syncthreads();   // the staged tile and work arrays are reused by the next tile
         if (tid == 0) {
@@ -586,6 +631,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
     if (my_flag) atomicOr(&s_flag, my_flag);
     __syncthreads();
     if (tid == 0 && s_flag) atomicOr(A.err, s_flag);
+    if (tid == 0) finish_cta(A);
 }
 
 }  // namespace claw

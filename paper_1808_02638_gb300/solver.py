@@ -108,6 +108,8 @@ class Hierarchy:
         self.smax = torch.zeros(self.nruns, dtype=torch.float64, device=self.dev)
         self.patchwise = False
         self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)
+        self.fused = False       # one-level hierarchies: one launch per step (ghost push + dt)
+        self._ghosts_ready = False
 
     # -------------------------------------------------------------- stepping
     def ratio(self, L):
@@ -138,6 +140,17 @@ class Hierarchy:
         self.cur[L] ^= 1
 
     def coarse_step(self, stream=None):
+        if self.fused and self.nlev == 1 and not self.patchwise and not self.freeze_dt:
+            # the launch that computes q_new also fills its copied ghosts and applies Eq. cfl
+            if not self._ghosts_ready:
+                claw.claw_fill_ghost(self.ctx, 0, self.q[0][self.cur[0]], None, None, 0.0, stream)
+                self._ghosts_ready = True
+            src, dst = self.q[0][self.cur[0]], self.q[0][1 - self.cur[0]]
+            claw.claw_level_advance(self.ctx, 0, src, dst, self.aux[0], self.dt, self.smax,
+                                    claw.CLAW_ADVANCE_PUSH_GHOSTS | claw.CLAW_ADVANCE_UPDATE_DT, stream)
+            self.cur[0] ^= 1
+            return
+        self._ghosts_ready = False
         self.advance(0, stream=stream)
         if self.freeze_dt:
             self.smax.zero_()
