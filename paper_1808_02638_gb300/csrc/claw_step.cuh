@@ -223,6 +223,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ey + G::EW * G::EH);
     __shared__ unsigned long long s_tmax[2];   // per-tile speed max, double-buffered by tile parity
     __shared__ int s_flag;
+    constexpr int kPushSmem = 32;              // push rectangles of the current tile kept on chip
+    __shared__ PushRect spush[kPushSmem];
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -298,6 +300,9 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             }
             __syncthreads();
         }
+
+        const int npush = A.push ? T.npush : 0;
+        if (tid < npush && tid < kPushSmem) spush[tid] = A.pushes[T.push0 + tid];   // read after phase A's barrier
 
         // ---------------------------------------------------------------- per-tile constants
         const double dt = __ldg(A.dt + P.run) * P.dtscale;
@@ -589,26 +594,39 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             dst[o] = p;
             dst[WH + o] = u;
             dst[2 * WH + o] = v;
-            if (A.push) {   // keep the new values for the ghost pushes (each cell is its own thread's)
-                sp[iq] = p;
-                su[iq] = u;
-                sv[iq] = v;
-            }
-        }
-        // ghost pushes: the same-level and physical-boundary ghosts of q_new whose source cells
-        // this tile just computed (each ghost has exactly one source, so no two tiles write it)
-        if (A.push && T.npush > 0) {
-            __syncthreads();
-            for (int pr = T.push0; pr < T.push0 + T.npush; ++pr) {
-                const PushRect R = A.pushes[pr];
-                const int cells = (int)R.w * R.h;
-                for (int k = tid; k < 3 * cells; k += NT) {
-                    const int m = k / cells, e = k - m * cells;
-                    const int y = e / R.w, x = e - y * R.w;
-                    const int src = (R.sx0 + x * R.ssx + 2) + (R.sy0 + y * R.ssy + 2) * G::SW;
-                    double val = sq[m * G::QPL + src];
-                    if ((m == 1 && (R.flags & 1)) || (m == 2 && (R.flags & 2))) val = -val;
-                    A.qnew[R.dst + m * R.dplane + (long long)y * R.dpitch + x] = val;
+            // ghost pushes: this cell's new value also goes to every ghost of q_new it is the
+            // source of (same-level copies, physical boundaries; each ghost has one source cell,
+            // so no two threads write it).  Sources lie within two cells of their box's edge.
+            if (npush > 0 && (x0 + c < 2 || y0 + r < 2 || x0 + c >= P.nx - 2 || y0 + r >= P.ny - 2)) {
+                for (int pr = 0; pr < npush; ++pr) {
+                    const PushRect& R = pr < kPushSmem ? spush[pr] : A.pushes[T.push0 + pr];
+                    int xa, xb, ya, yb;
+                    if (R.ssx == 0) {
+                        if (c != R.sx0) continue;
+                        xa = 0;
+                        xb = R.w;
+                    } else {
+                        xa = (c - R.sx0) * R.ssx;
+                        if (xa < 0 || xa >= R.w) continue;
+                        xb = xa + 1;
+                    }
+                    if (R.ssy == 0) {
+                        if (r != R.sy0) continue;
+                        ya = 0;
+                        yb = R.h;
+                    } else {
+                        ya = (r - R.sy0) * R.ssy;
+                        if (ya < 0 || ya >= R.h) continue;
+                        yb = ya + 1;
+                    }
+                    const double uu = (R.flags & 1) ? -u : u, vv = (R.flags & 2) ? -v : v;
+                    for (int y = ya; y < yb; ++y)
+                        for (int x = xa; x < xb; ++x) {
+                            const long long o2 = R.dst + (long long)y * R.dpitch + x;
+                            A.qnew[o2] = p;
+                            A.qnew[o2 + R.dplane] = uu;
+                            A.qnew[o2 + 2 * R.dplane] = vv;
+                        }
                 }
             }
         }
