@@ -1,10 +1,11 @@
 """Profiling driver: a few eager level-steps of the 2048 x 2048 workload as 4096 patches of
 32 x 32, for a profiler to capture single kernel launches.
 
-  python -m paper_1808_02638_gb300.profile_step [uniform|cellwise] [nsteps]
+  python -m paper_1808_02638_gb300.profile_step [uniform|cellwise] [nsteps] [fused|split]
 
 uniform: radial pulse, rho = 1, K = 4; cellwise: the same tiling over the smoothed random
-medium of the heterogeneous workload.
+medium of the heterogeneous workload.  fused (default): one launch per step
+(claw_level_advance with the ghost push and Eq. cfl); split: fill, step, dt update.
 """
 import sys
 
@@ -17,6 +18,7 @@ from .solver import Hierarchy
 def main():
     medium = sys.argv[1] if len(sys.argv) > 1 else "uniform"
     nsteps = int(sys.argv[2]) if len(sys.argv) > 2 else 3
+    fused = (sys.argv[3] if len(sys.argv) > 3 else "fused") == "fused"
     n = 2048
     if medium == "uniform":
         run = inputs.config1()
@@ -27,6 +29,7 @@ def main():
         lev = run.levels[0]
         H = Hierarchy([run], [[inputs.init_q(run, lev)]], [[inputs.coef_pool(lev, r2, 1)]],
                       [[inputs.coef_pool(lev, k2, 1)]])
+    H.fused = fused
     H.init_dt()
     for _ in range(nsteps):
         H.coarse_step()
