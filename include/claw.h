@@ -155,10 +155,10 @@ int claw_dt_update(claw_ctx* ctx, int32_t level, double* smax, double* dt, void*
 int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
                     const double* aux, const double* dt, double* smax, void* stream);
 
-/* claw_level_step with fused epilogues selected by `flags`:
- *   CLAW_ADVANCE_PUSH_GHOSTS: every tile also writes the ghosts of q_new that copy its new cells
- *     (same-level copies and physical boundaries; each ghost has exactly one source tile), so
- *     the next step of this level needs no separate fill unless it has interpolated ghosts;
+/* claw_level_step with epilogues selected by `flags`:
+ *   CLAW_ADVANCE_PUSH_GHOSTS: the same-level copies and physical boundaries of q_new are filled
+ *     right after the step (a second launch on the same stream), so the next step of this level
+ *     needs no separate fill unless it has interpolated ghosts;
  *   CLAW_ADVANCE_UPDATE_DT: after the step, Eq. cfl is applied on the device by the last CTA
  *     to finish (as claw_dt_update with level-0 dx, dy): dt[r] is replaced by the next time step
  *     and smax[r] reset.  Use it when this level-step ends the coarse step (a hierarchy of one

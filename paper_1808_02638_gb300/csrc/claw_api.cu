@@ -159,10 +159,9 @@ void free_level(claw_ctx* ctx, int L)
     d.nccopy = 0;
     cudaFree(d.interps);
     cudaFree(d.avgs);
-    cudaFree(d.pushes);
-    d.pushes = nullptr;
-    d.npush = 0;
-    d.gcopies.clear();
+    cudaFree(d.copy_start);
+    cudaFree(d.ccopy_start);
+    d.copy_start = d.ccopy_start = nullptr;
     cudaFree(ctx->ptiles[L]);
     cudaFree(ctx->atiles[L]);
     ctx->atiles[L] = nullptr;
@@ -200,8 +199,7 @@ int build_tiles(claw_ctx* ctx, int L)
                 T.y0 = (short)y;
                 T.tx = (short)std::min(d.tx, b.nx - x);
                 T.ty = (short)std::min(d.ty, b.ny - y);
-                T.push0 = 0;
-                T.npush = 0;
+                T.pad = 0;
                 t.push_back(T);
             }
     }
@@ -212,107 +210,6 @@ int build_tiles(claw_ctx* ctx, int L)
     std::stable_sort(t.begin(), t.end(), [](const TileDev& a, const TileDev& b) {
         return (int)a.tx * a.ty > (int)b.tx * b.ty;
     });
-    // push rectangles: every copied ghost belongs to the tile that computes its source cell
-    {
-        auto key = [](long long box, long long bx, long long by) { return (box << 40) | (by << 20) | bx; };
-        std::unordered_map<long long, int> tile_of;
-        for (int k = 0; k < (int)t.size(); ++k) tile_of[key(t[k].patch, t[k].x0 / d.tx, t[k].y0 / d.ty)] = k;
-        std::vector<std::pair<int, int>> order;   // (tile, entry)
-        order.reserve(d.gcopies.size());
-        for (int e = 0; e < (int)d.gcopies.size(); ++e) {
-            const GhostCopy& g = d.gcopies[e];
-            const claw_box& sb = d.boxes[g.src];
-            const int lx = g.si - sb.ilo, ly = g.sj - sb.jlo;
-            auto it = tile_of.find(key(g.src, lx / d.tx, ly / d.ty));
-            if (it == tile_of.end()) return CLAW_EINVAL;   // cannot happen for interior sources
-            order.push_back({it->second, e});
-        }
-        std::stable_sort(order.begin(), order.end(),
-                         [](const std::pair<int, int>& a, const std::pair<int, int>& b) { return a.first < b.first; });
-        std::vector<PushRect> pr;
-        for (auto& T : t) {
-            T.push0 = 0;
-            T.npush = 0;
-        }
-        struct Run1 {
-            const GhostCopy* g0;
-            int w, sx, sy, ssx;
-        };
-        size_t k = 0;
-        while (k < order.size()) {
-            const int tile = order[k].first;
-            const TileDev& T = t[tile];
-            t[tile].push0 = (int)pr.size();
-            // row runs within this tile's group
-            std::vector<Run1> runs;
-            size_t k2 = k;
-            while (k2 < order.size() && order[k2].first == tile) {
-                const GhostCopy& g = d.gcopies[order[k2].second];
-                const claw_box& sb = d.boxes[g.src];
-                Run1 R{&g, 1, g.si - sb.ilo - T.x0, g.sj - sb.jlo - T.y0, 0};
-                size_t k3 = k2 + 1;
-                while (k3 < order.size() && order[k3].first == tile) {
-                    const GhostCopy& h = d.gcopies[order[k3].second];
-                    const GhostCopy& p = d.gcopies[order[k3 - 1].second];
-                    const int step = h.si - p.si;
-                    if (h.dst != p.dst + 1 || h.gj != p.gj || h.flags != p.flags || h.sj != p.sj || h.src != p.src ||
-                        step < -1 || step > 1 || (R.w > 1 && step != R.ssx))
-                        break;
-                    R.ssx = step;
-                    ++R.w;
-                    ++k3;
-                }
-                runs.push_back(R);
-                k2 = k3;
-            }
-            // stack runs of consecutive ghost rows into rectangles
-            struct Open {
-                Run1 r;
-                int h, ssy, last_sy, last_gj;
-                long long last_dst;
-            };
-            std::vector<Open> open;
-            auto emit = [&](const Open& o) {
-                PushRect P;
-                P.dst = o.r.g0->dst;
-                P.dplane = o.r.g0->dplane;
-                P.sx0 = (short)o.r.sx;
-                P.sy0 = (short)o.r.sy;
-                P.w = (short)o.r.w;
-                P.h = (short)o.h;
-                P.ssx = (short)o.r.ssx;
-                P.ssy = (short)o.ssy;
-                P.dpitch = o.r.g0->dpitch;
-                P.flags = o.r.g0->flags;
-                pr.push_back(P);
-            };
-            for (const Run1& R : runs) {
-                bool merged = false;
-                for (Open& o : open) {
-                    if (o.last_gj != R.g0->gj - 1 || o.r.w != R.w || o.r.sx != R.sx || o.r.ssx != R.ssx ||
-                        o.r.g0->flags != R.g0->flags || o.r.g0->dplane != R.g0->dplane ||
-                        R.g0->dst != o.last_dst + o.r.g0->dpitch)
-                        continue;
-                    const int step = R.sy - o.last_sy;
-                    if (step < -1 || step > 1 || (o.h > 1 && step != o.ssy)) continue;
-                    o.ssy = step;
-                    ++o.h;
-                    o.last_sy = R.sy;
-                    o.last_gj = R.g0->gj;
-                    o.last_dst = R.g0->dst;
-                    merged = true;
-                    break;
-                }
-                if (!merged) open.push_back(Open{R, 1, 0, R.sy, R.g0->gj, R.g0->dst});
-            }
-            for (const Open& o : open) emit(o);
-            t[tile].npush = (int)pr.size() - t[tile].push0;
-            k = k2;
-        }
-        int rc2 = upload(&d.pushes, pr);
-        if (rc2) return rc2;
-        d.npush = (int)pr.size();
-    }
     d.htiles = t;
     d.ntiles = (int)t.size();
     for (auto& tm : ctx->tmaps[L]) cudaFree(tm.dev);
@@ -332,8 +229,7 @@ int build_tiles(claw_ctx* ctx, int L)
                 T.y0 = (short)y;
                 T.tx = (short)std::min(e, b.nx - x);
                 T.ty = (short)std::min(e, b.ny - y);
-                T.push0 = 0;
-                T.npush = 0;
+                T.pad = 0;
                 at.push_back(T);
             }
     }
@@ -350,7 +246,7 @@ struct GhostEntry {
 
 // ghost tasks of one level: copy rectangles and interpolated cells
 int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::vector<InterpCell>& cells,
-                       std::vector<GhostCopy>* record)
+                       std::vector<int>& start)
 {
     LevelDev& d = ctx->lev[L];
     std::vector<Locator> loc(ctx->nruns), cloc(ctx->nruns);
@@ -363,6 +259,7 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
         for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
             cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
 
+    start.assign(1, 0);
     for (int n = 0; n < d.nboxes; ++n) {
         const claw_box& b = d.boxes[n];
         const claw_problem& pr = ctx->runs[b.run];
@@ -381,19 +278,6 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
                 if (src >= 0) {
                     e.soff = cell_off(d.boxes[src], si, sj);
                     ent.push_back(e);
-                    if (record) {
-                        GhostCopy g;
-                        g.dst = cell_off(b, gi, gj);
-                        g.dplane = plane_of(b);
-                        g.dpitch = W;
-                        g.src = src;
-                        g.si = si;
-                        g.sj = sj;
-                        g.gi = gi;
-                        g.gj = gj;
-                        g.flags = e.flags;
-                        record->push_back(g);
-                    }
                     continue;
                 }
                 // space-time interpolation from level L-1 at the fine cell (si, sj)
@@ -501,6 +385,7 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
             }
         }
         for (const Open& o : open) emit(o);
+        start.push_back((int)rects.size());
     }
     return CLAW_OK;
 }
@@ -789,9 +674,10 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     std::vector<CopyRect> rects;
     std::vector<InterpCell> cells;
     std::vector<AvgRect> avg;
-    d.gcopies.clear();
-    int rc = build_ghost_tables(ctx, L, rects, cells, &d.gcopies);
+    std::vector<int> qstart;
+    int rc = build_ghost_tables(ctx, L, rects, cells, qstart);
     if (rc) return rc;
+    if ((rc = upload(&d.copy_start, qstart))) return rc;
     if (L > 0) build_avg_tables(ctx, L, avg);
     // the same copies for one-plane pools: offsets from coff, no wall sign flips
     std::vector<CopyRect> crects;
@@ -799,7 +685,9 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         std::vector<claw_box> saved = d.boxes;
         for (auto& b : d.boxes) b.qoff = b.coff;
         std::vector<InterpCell> unused;
-        rc = build_ghost_tables(ctx, L, crects, unused, nullptr);
+        std::vector<int> cstart;
+        rc = build_ghost_tables(ctx, L, crects, unused, cstart);
+        if (!rc) rc = upload(&d.ccopy_start, cstart);
         d.boxes = saved;
         if (rc) return rc;
         for (auto& r : crects) r.flags = 0;
@@ -866,7 +754,7 @@ int claw_fill_ghost(claw_ctx* ctx, int32_t L, double* q, const double* qc_old, c
     if (d.ninterp > 0 && (!qc_old || !qc_new || !(tau >= 0.0 && tau <= 1.0))) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = launch_fill_copy(d.copies, d.ncopy, q, s);
+    cudaError_t e = d.ncopy ? launch_fill_copy(d.copies, d.copy_start, d.nboxes, q, s) : cudaSuccess;
     ctx->launches += d.ncopy > 0;
     if (e == cudaSuccess) {
         e = launch_fill_interp(d.interps, d.ninterp, q, qc_old, qc_new, tau, s);
@@ -882,7 +770,8 @@ int claw_fill_ghost_coef(claw_ctx* ctx, int32_t L, double* a, void* stream)
     DevGuard g(ctx->device);
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nccopy > 0;
-    return cuda_rc(launch_fill_copy(d.ccopies, d.nccopy, a, (cudaStream_t)stream, 1));
+    return cuda_rc(d.nccopy ? launch_fill_copy(d.ccopies, d.ccopy_start, d.nboxes, a, (cudaStream_t)stream, 1)
+                            : cudaSuccess);
 }
 
 int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t L, double* g, void* stream)
@@ -892,7 +781,8 @@ int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t L, double* g, void* stre
     DevGuard gd(ctx->device);
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nccopy > 0;
-    return cuda_rc(launch_fill_copy_adjoint(d.ccopies, d.nccopy, g, (cudaStream_t)stream, 1));
+    return cuda_rc(d.nccopy ? launch_fill_copy_adjoint(d.ccopies, d.ccopy_start, d.nboxes, g, (cudaStream_t)stream, 1)
+                            : cudaSuccess);
 }
 
 int claw_fill_ghost_adjoint(claw_ctx* ctx, int32_t L, double* lam, double* lco, double* lcn, const double* qc_old,
@@ -907,9 +797,9 @@ int claw_fill_ghost_adjoint(claw_ctx* ctx, int32_t L, double* lam, double* lco, 
     // interpolated ghosts first (they read coarse cells only), then the copies
     cudaError_t e = launch_fill_interp_adjoint(d.interps, d.ninterp, lam, lco, lcn, qc_old, qc_new, tau, s);
     ctx->launches += d.ninterp > 0;
-    if (e == cudaSuccess) {
-        e = launch_fill_copy_adjoint(d.copies, d.ncopy, lam, s);
-        ctx->launches += d.ncopy > 0;
+    if (e == cudaSuccess && d.ncopy) {
+        e = launch_fill_copy_adjoint(d.copies, d.copy_start, d.nboxes, lam, s);
+        ctx->launches += 1;
     }
     return cuda_rc(e);
 }
@@ -970,10 +860,6 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
     if (d.ntiles == 0) return CLAW_OK;
     cudaStream_t s = (cudaStream_t)stream;
     StepArgs a = make_args(ctx, L, q_old, q_new, aux, dt, smax);
-    if (flags & CLAW_ADVANCE_PUSH_GHOSTS) {
-        a.push = 1;
-        a.pushes = d.pushes;
-    }
     if (flags & CLAW_ADVANCE_UPDATE_DT) {
         a.dtupd = 1;
         a.dt_out = dt;
@@ -991,7 +877,12 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;
-    return cuda_rc(launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s));
+    cudaError_t e = launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s);
+    if (e == cudaSuccess && (flags & CLAW_ADVANCE_PUSH_GHOSTS) && d.ncopy) {
+        e = launch_fill_copy(d.copies, d.copy_start, d.nboxes, q_new, s);
+        ctx->launches += 1;
+    }
+    return cuda_rc(e);
 }
 
 int claw_level_step_patchwise(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,

@@ -12,55 +12,130 @@ namespace claw {
 static inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------------------ same-level copy
-// One warp per rectangle; lanes stride over its w*h*3 elements.
-__global__ void fill_copy_kernel(const CopyRect* __restrict__ rects, int n, double* __restrict__ q, int ncomp)
+// One block per destination box; the rectangles of box b are [start[b], start[b+1]).  A box
+// has a few to a few tens of rectangles of a few hundred elements in all, so the block stages
+// a chunk of rectangles in shared memory with the running element count, and every thread
+// takes kCopyBatch elements of the flattened chunk with all loads issued before the stores
+// (the copy is latency-bound: one dependent load-store pair per thread would leave HBM idle).
+constexpr int kCopyThreads = 128;
+constexpr int kCopyChunk = 32;
+constexpr int kCopyBatch = 8;
+
+struct CopyChunk {
+    CopyRect r[kCopyChunk];
+    int end[kCopyChunk];   // inclusive prefix of ncomp * w * h
+    int n, total;
+};
+
+__device__ __forceinline__ void stage_chunk(CopyChunk& c, const CopyRect* __restrict__ rects, int r0, int n,
+                                            int ncomp)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    const CopyRect R = rects[warp];
+    const int tid = threadIdx.x;
+    if (tid < n) c.r[tid] = rects[r0 + tid];
+    __syncthreads();
+    if (tid < 32) {   // warp-inclusive scan of the element counts
+        int v = tid < n ? ncomp * c.r[tid].w * c.r[tid].h : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (tid >= o) v += u;
+        }
+        c.end[tid] = v;
+        if (tid == 31) {
+            c.total = v;
+            c.n = n;
+        }
+    }
+    __syncthreads();
+}
+
+// element k of the staged chunk -> (rectangle, component, x, y)
+__device__ __forceinline__ void locate(const CopyChunk& c, int k, int& ri, int& m, int& x, int& y)
+{
+    ri = 0;
+    while (c.end[ri] <= k) ++ri;
+    const CopyRect& R = c.r[ri];
+    const int e0 = k - (ri ? c.end[ri - 1] : 0);
     const int cells = R.w * R.h;
-    for (int k = lane; k < ncomp * cells; k += 32) {
-        const int m = k / cells, e = k - m * cells;
-        const int y = e / R.w, x = e - y * R.w;
-        double v = q[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx];
-        if ((m == 1 && (R.flags & 1)) || (m == 2 && (R.flags & 2))) v = -v;
-        q[R.dst + m * R.dplane + (long long)y * R.dpitch + x] = v;
+    m = e0 / cells;
+    const int e = e0 - m * cells;
+    y = e / R.w;
+    x = e - y * R.w;
+}
+
+__device__ __forceinline__ bool negated(int flags, int m)
+{
+    return (m == 1 && (flags & 1)) || (m == 2 && (flags & 2));
+}
+
+__global__ void __launch_bounds__(kCopyThreads) fill_copy_kernel(const CopyRect* __restrict__ rects,
+                                                                 const int* __restrict__ start,
+                                                                 double* __restrict__ q, int ncomp)
+{
+    __shared__ CopyChunk c;
+    const int r_lo = start[blockIdx.x], r_hi = start[blockIdx.x + 1];
+    for (int r0 = r_lo; r0 < r_hi; r0 += kCopyChunk) {
+        stage_chunk(c, rects, r0, min(kCopyChunk, r_hi - r0), ncomp);
+        for (int base = 0; base < c.total; base += kCopyThreads * kCopyBatch) {
+            double v[kCopyBatch];
+            long long dst[kCopyBatch];
+#pragma unroll
+            for (int j = 0; j < kCopyBatch; ++j) {
+                const int k = base + j * kCopyThreads + (int)threadIdx.x;
+                dst[j] = -1;
+                if (k < c.total) {
+                    int ri, m, x, y;
+                    locate(c, k, ri, m, x, y);
+                    const CopyRect& R = c.r[ri];
+                    const double s = q[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx];
+                    v[j] = negated(R.flags, m) ? -s : s;
+                    dst[j] = R.dst + m * R.dplane + (long long)y * R.dpitch + x;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kCopyBatch; ++j)
+                if (dst[j] >= 0) q[dst[j]] = v[j];
+        }
+        __syncthreads();   // the chunk is restaged
     }
 }
 
 // reverse: ghost adjoint flows into its source, then the ghost adjoint is cleared.  Sources
 // are interior cells and several ghosts may share one (extrapolation), hence the atomics.
-__global__ void fill_copy_adjoint_kernel(const CopyRect* __restrict__ rects, int n, double* __restrict__ lam,
-                                         int ncomp)
+__global__ void __launch_bounds__(kCopyThreads) fill_copy_adjoint_kernel(const CopyRect* __restrict__ rects,
+                                                                         const int* __restrict__ start,
+                                                                         double* __restrict__ lam, int ncomp)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    const CopyRect R = rects[warp];
-    const int cells = R.w * R.h;
-    for (int k = lane; k < ncomp * cells; k += 32) {
-        const int m = k / cells, e = k - m * cells;
-        const int y = e / R.w, x = e - y * R.w;
-        const long long d = R.dst + m * R.dplane + (long long)y * R.dpitch + x;
-        double g = lam[d];
-        lam[d] = 0.0;
-        if ((m == 1 && (R.flags & 1)) || (m == 2 && (R.flags & 2))) g = -g;
-        if (g != 0.0) atomicAdd(&lam[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx], g);
+    __shared__ CopyChunk c;
+    const int r_lo = start[blockIdx.x], r_hi = start[blockIdx.x + 1];
+    for (int r0 = r_lo; r0 < r_hi; r0 += kCopyChunk) {
+        stage_chunk(c, rects, r0, min(kCopyChunk, r_hi - r0), ncomp);
+        for (int k = threadIdx.x; k < c.total; k += kCopyThreads) {
+            int ri, m, x, y;
+            locate(c, k, ri, m, x, y);
+            const CopyRect& R = c.r[ri];
+            const long long d = R.dst + m * R.dplane + (long long)y * R.dpitch + x;
+            double g = lam[d];
+            lam[d] = 0.0;
+            if (negated(R.flags, m)) g = -g;
+            if (g != 0.0) atomicAdd(&lam[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx], g);
+        }
+        __syncthreads();
     }
 }
 
-cudaError_t launch_fill_copy(const CopyRect* r, int n, double* q, cudaStream_t s, int ncomp)
+cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nboxes, double* q, cudaStream_t s, int ncomp)
 {
-    if (n <= 0) return cudaSuccess;
-    fill_copy_kernel<<<div_up((long long)n * 32, 256), 256, 0, s>>>(r, n, q, ncomp);
+    if (nboxes <= 0) return cudaSuccess;
+    fill_copy_kernel<<<nboxes, kCopyThreads, 0, s>>>(r, start, q, ncomp);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill_copy_adjoint(const CopyRect* r, int n, double* lam, cudaStream_t s, int ncomp)
+cudaError_t launch_fill_copy_adjoint(const CopyRect* r, const int* start, int nboxes, double* lam, cudaStream_t s,
+                                     int ncomp)
 {
-    if (n <= 0) return cudaSuccess;
-    fill_copy_adjoint_kernel<<<div_up((long long)n * 32, 256), 256, 0, s>>>(r, n, lam, ncomp);
+    if (nboxes <= 0) return cudaSuccess;
+    fill_copy_adjoint_kernel<<<nboxes, kCopyThreads, 0, s>>>(r, start, lam, ncomp);
     return cudaGetLastError();
 }
 

@@ -37,22 +37,11 @@ struct PatchDev {
     double dtscale;   // this level's dt / level-0 dt = 1 / (ratio_1 ... ratio_L)
 };
 
-// One tile of the fused step: interior cells [x0, x0+tx) x [y0, y0+ty) of box `patch`;
-// pushes [push0, push0 + npush) are the ghost rectangles its new values fill.
+// One tile of the fused step: interior cells [x0, x0+tx) x [y0, y0+ty) of box `patch`.
 struct TileDev {
     int patch;
     short x0, y0, tx, ty;
-    int push0, npush;
-};
-
-// Ghost cells of q_new that one tile fills from its own new interior values (same-level copy
-// and physical boundary, written by the tile that computed the source cells).  Element (x, y),
-// plane m:  q_new[dst + m*dplane + y*dpitch + x] = sign_m * new(sx0 + x*ssx, sy0 + y*ssy),
-// source coordinates local to the tile's interior.
-struct PushRect {
-    long long dst, dplane;
-    short sx0, sy0, w, h, ssx, ssy;
-    int dpitch, flags;
+    int pad;
 };
 
 // Rectangle of ghost cells copied from interior cells of the same level (same-level copy and
@@ -85,16 +74,6 @@ struct AvgRect {
 };
 
 // Per (level) device tables.
-struct GhostCopy {   // one ghost cell filled by a copy (host-side, for the push tables)
-    long long dst;     // plane-0 element of the ghost
-    long long dplane;
-    int dpitch;
-    int src;           // source box
-    int si, sj;        // source cell (level index)
-    int gi, gj;        // ghost cell (level index), for run detection
-    int flags;
-};
-
 struct LevelDev {
     int nboxes = 0;
     int ntiles = 0;
@@ -112,9 +91,8 @@ struct LevelDev {
     AvgRect* avgs = nullptr;
     void* tmaps = nullptr;   // CUtensorMap per box (128 B each), built for the current tiling
     int tmap_tx = 0, tmap_ty = 0;
-    PushRect* pushes = nullptr;
-    int npush = 0;
-    std::vector<GhostCopy> gcopies;   // every copied ghost of the level (host)
+    int* copy_start = nullptr;    // [nboxes + 1]: the copy rectangles of box b are [start[b], start[b+1])
+    int* ccopy_start = nullptr;
     // host copies
     std::vector<claw_box> boxes;
     std::vector<PatchDev> hpatches;
@@ -135,9 +113,7 @@ struct StepArgs {
     // scheme
     int order = 2, transverse = 2;
     double rho0 = 1.0, K0 = 1.0;   // uniform medium
-    // fused epilogues (0 = off)
-    const PushRect* pushes = nullptr;   // fill the same-level / physical ghosts of qnew
-    int push = 0;
+    // fused epilogue (0 = off)
     int dtupd = 0;                      // the last CTA applies Eq. cfl to dt and resets smax
     double* dt_out = nullptr;
     const double* minh = nullptr;       // level-0 min(dx, dy) per run
@@ -158,10 +134,12 @@ cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double
 int adjoint_tile();   // the adjoint kernel's square tile edge
 
 // launchers (claw_ghost.cu)
-cudaError_t launch_fill_copy(const CopyRect* r, int n, double* q, cudaStream_t s, int ncomp = 3);
+cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nboxes, double* q, cudaStream_t s,
+                             int ncomp = 3);
 cudaError_t launch_fill_interp(const InterpCell* c, int n, double* q, const double* cold,
                                const double* cnew, double tau, cudaStream_t s);
-cudaError_t launch_fill_copy_adjoint(const CopyRect* r, int n, double* lam, cudaStream_t s, int ncomp = 3);
+cudaError_t launch_fill_copy_adjoint(const CopyRect* r, const int* start, int nboxes, double* lam, cudaStream_t s,
+                                     int ncomp = 3);
 cudaError_t launch_fill_interp_adjoint(const InterpCell* c, int n, double* lam, double* lco,
                                        double* lcn, const double* cold, const double* cnew,
                                        double tau, cudaStream_t s);

@@ -223,8 +223,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ey + G::EW * G::EH);
     __shared__ unsigned long long s_tmax[2];   // per-tile speed max, double-buffered by tile parity
     __shared__ int s_flag;
-    constexpr int kPushSmem = 32;              // push rectangles of the current tile kept on chip
-    __shared__ PushRect spush[kPushSmem];
+
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -300,9 +299,6 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             }
             __syncthreads();
         }
-
-        const int npush = A.push ? T.npush : 0;
-        if (tid < npush && tid < kPushSmem) spush[tid] = A.pushes[T.push0 + tid];   // read after phase A's barrier
 
         // ---------------------------------------------------------------- per-tile constants
         const double dt = __ldg(A.dt + P.run) * P.dtscale;
@@ -594,41 +590,6 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             dst[o] = p;
             dst[WH + o] = u;
             dst[2 * WH + o] = v;
-            // ghost pushes: this cell's new value also goes to every ghost of q_new it is the
-            // source of (same-level copies, physical boundaries; each ghost has one source cell,
-            // so no two threads write it).  Sources lie within two cells of their box's edge.
-            if (npush > 0 && (x0 + c < 2 || y0 + r < 2 || x0 + c >= P.nx - 2 || y0 + r >= P.ny - 2)) {
-                for (int pr = 0; pr < npush; ++pr) {
-                    const PushRect& R = pr < kPushSmem ? spush[pr] : A.pushes[T.push0 + pr];
-                    int xa, xb, ya, yb;
-                    if (R.ssx == 0) {
-                        if (c != R.sx0) continue;
-                        xa = 0;
-                        xb = R.w;
-                    } else {
-                        xa = (c - R.sx0) * R.ssx;
-                        if (xa < 0 || xa >= R.w) continue;
-                        xb = xa + 1;
-                    }
-                    if (R.ssy == 0) {
-                        if (r != R.sy0) continue;
-                        ya = 0;
-                        yb = R.h;
-                    } else {
-                        ya = (r - R.sy0) * R.ssy;
-                        if (ya < 0 || ya >= R.h) continue;
-                        yb = ya + 1;
-                    }
-                    const double uu = (R.flags & 1) ? -u : u, vv = (R.flags & 2) ? -v : v;
-                    for (int y = ya; y < yb; ++y)
-                        for (int x = xa; x < xb; ++x) {
-                            const long long o2 = R.dst + (long long)y * R.dpitch + x;
-                            A.qnew[o2] = p;
-                            A.qnew[o2 + R.dplane] = uu;
-                            A.qnew[o2 + 2 * R.dplane] = vv;
-                        }
-                }
-            }
         }
         __syncthreads();   // the staged tile and work arrays are reused by the next tile
         if (tid == 0) {
