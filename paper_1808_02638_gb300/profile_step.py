@@ -4,8 +4,8 @@
   python -m paper_1808_02638_gb300.profile_step [uniform|cellwise] [nsteps] [fused|split]
 
 uniform: radial pulse, rho = 1, K = 4; cellwise: the same tiling over the smoothed random
-medium of the heterogeneous workload.  fused (default): one launch per step
-(claw_level_advance with the ghost push and Eq. cfl); split: fill, step, dt update.
+medium of the heterogeneous workload.  fused (default): claw_level_advance (the step with Eq.
+cfl on its last CTA, then the ghost copy of q^{n+1}); split: fill, step, dt update.
 """
 import sys
 

@@ -108,7 +108,7 @@ class Hierarchy:
         self.smax = torch.zeros(self.nruns, dtype=torch.float64, device=self.dev)
         self.patchwise = False
         self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)
-        self.fused = False       # one-level hierarchies: one launch per step (ghost push + dt)
+        self.fused = False       # one-level hierarchies: step with Eq. cfl on the device, then push ghosts
         self._ghosts_ready = False
 
     # -------------------------------------------------------------- stepping
@@ -141,7 +141,7 @@ class Hierarchy:
 
     def coarse_step(self, stream=None):
         if self.fused and self.nlev == 1 and not self.patchwise and not self.freeze_dt:
-            # the launch that computes q_new also fills its copied ghosts and applies Eq. cfl
+            # the step applies Eq. cfl on its last CTA; the copied ghosts of q_new follow at once
             if not self._ghosts_ready:
                 claw.claw_fill_ghost(self.ctx, 0, self.q[0][self.cur[0]], None, None, 0.0, stream)
                 self._ghosts_ready = True
