@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ey + G::EW * G::EH);
     __shared__ unsigned long long s_tmax[2];   // per-tile speed max, double-buffered by tile parity
     __shared__ int s_flag;
+    __shared__ double s_k[16];                 // per-tile constants, written by thread 0
 
 
     const int tid = threadIdx.x;
@@ -301,11 +302,35 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
         }
 
         // ---------------------------------------------------------------- per-tile constants
-        const double dt = __ldg(A.dt + P.run) * P.dtscale;
-        const double lx = dt * P.dxinv, ly = dt * P.dyinv;
+        // Computed once per tile by thread 0 (every thread doing it cost several FP64 slots per
+        // cell); first read after the barrier that ends phase A, last read in phase D, which
+        // the end-of-tile barrier separates from the next tile's write.
         const bool second = A.order == 2 && LIM >= 0;
         const bool trans = A.transverse != 0;
         const bool cw = A.transverse == 2 && A.order == 2;   // correction rides the transverse split
+        if (tid == 0) {
+            const double dt = __ldg(A.dt + P.run) * P.dtscale;
+            const double lx = dt * P.dxinv, ly = dt * P.dyinv;
+            s_k[12] = lx;
+            s_k[13] = ly;
+            s_k[14] = -0.5 * lx;
+            s_k[15] = -0.5 * ly;
+            if (MED == 0) {
+                const double kapx = c0 * (1.0 - lx * c0), kapy = c0 * (1.0 - ly * c0);
+                s_k[0] = -0.5 * lx * A.K0;            // cpa
+                s_k[1] = -0.25 * lx * kapx * Z0;      // cpb
+                s_k[2] = -0.5 * lx * c0;              // cua
+                s_k[3] = -0.25 * lx * kapx;           // cub
+                s_k[4] = -0.5 * ly * A.K0;            // cpay
+                s_k[5] = -0.25 * ly * kapy * Z0;      // cpby
+                s_k[6] = -0.5 * ly * c0;              // cva
+                s_k[7] = -0.25 * ly * kapy;           // cvb
+                s_k[8] = cw ? 1.0 - lx * c0 : 0.0;    // kDx
+                s_k[9] = cw ? 1.0 - ly * c0 : 0.0;    // kDy
+                s_k[10] = trans ? 0.125 * lx * ly * c0 * A.K0 : 0.0;   // kT
+                s_k[11] = trans ? 0.125 * lx * ly * c0 * c0 : 0.0;     // kU
+            }
+        }
         // medium access (MED == 1): aux plane k of the cell at tile-local (i, j)
         const double* aux = MED ? A.aux + P.aoff : nullptr;
         auto AX = [&](int k, int i, int j) -> double {
@@ -373,6 +398,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
         __syncthreads();
 
         // ---------------------------------------------------------------- phase B: limiter, correction
+        const double lx = s_k[12], ly = s_k[13];
         if (second) {
             {
                 const int w = tx + 1, n = (ty + 2) * w;
@@ -429,22 +455,20 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
         //   ap = A2_w + A1_e, au = A2_w - A1_e, bp = S_e - S_w, bu = P_e - P_w,  kap = c (1 - lx c)
         //   x-fluctuation pressure into the cell D = (K/2) (ap + (1 - lx c) bp)
         // cell-wise medium: D = K ap + bp,  x-normal (K ap + bp/2, c au + bu/2)
-        double cK = 0, cpa = 0, cpb = 0, cua = 0, cub = 0, cpay = 0, cpby = 0, cva = 0, cvb = 0,
-               kDx = 0, kDy = 0;
+        double cpa = 0, cpb = 0, cua = 0, cub = 0, cpay = 0, cpby = 0, cva = 0, cvb = 0, kDx = 0, kDy = 0;
         if (MED == 0) {
-            const double kapx = c0 * (1.0 - lx * c0), kapy = c0 * (1.0 - ly * c0);
-            cpa = -0.5 * lx * A.K0;
-            cpb = -0.25 * lx * kapx * Z0;
-            cua = -0.5 * lx * c0;
-            cub = -0.25 * lx * kapx;
-            cpay = -0.5 * ly * A.K0;
-            cpby = -0.25 * ly * kapy * Z0;
-            cva = -0.5 * ly * c0;
-            cvb = -0.25 * ly * kapy;
-            kDx = cw ? 1.0 - lx * c0 : 0.0;
-            kDy = cw ? 1.0 - ly * c0 : 0.0;
-            (void)cK;
+            cpa = s_k[0];
+            cpb = s_k[1];
+            cua = s_k[2];
+            cub = s_k[3];
+            cpay = s_k[4];
+            cpby = s_k[5];
+            cva = s_k[6];
+            cvb = s_k[7];
+            kDx = s_k[8];
+            kDy = s_k[9];
         }
+        // dP, dU, dV: Q plus the normal updates (the transverse terms are added in phase D)
         double dP[NPER], dU[NPER], dV[NPER];
 #pragma unroll
         for (int n = 0; n < NPER; ++n) {
@@ -452,6 +476,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             const int ci = tid + n * NT;
             const int c = ci % TX, r = ci / TX;
             if (ci >= TX * TY || c >= tx || r >= ty) continue;
+            const int iq = (c + 2) + (r + 2) * G::SW;
             const int ex = (r + 1) * G::XEW + (c + 1);
             const int ey = (r + 1) * G::YEW + (c + 1);
             const double apx = A2x[ex] + A1x[ex + 1], aux_ = A2x[ex] - A1x[ex + 1];
@@ -468,9 +493,9 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
                     Dx[(r + 1) * G::DW + c] = fma(kDx, bpx, apx);
                     Ey[r * G::EW + c + 1] = fma(kDy, bpy, apy);
                 }
-                dP[n] = fma(cpb, bpx, cpa * apx) + fma(cpby, bpy, cpay * apy);
-                dU[n] = fma(cub, bux, cua * aux_);
-                dV[n] = fma(cvb, bvy, cva * avy);
+                dP[n] = fma(cpa, apx, fma(cpb, bpx, fma(cpay, apy, fma(cpby, bpy, sp[iq]))));
+                dU[n] = fma(cua, aux_, fma(cub, bux, su[iq]));
+                dV[n] = fma(cva, avy, fma(cvb, bvy, sv[iq]));
             } else {
                 const double Kc = AX(AUX_K, c, r), cc = AX(AUX_C, c, r);
                 if (trans) {
@@ -479,9 +504,9 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
                 }
                 const double tpx = fma(0.5, bpx, Kc * apx), tux = fma(0.5, bux, cc * aux_);
                 const double tpy = fma(0.5, bpy, Kc * apy), tvy = fma(0.5, bvy, cc * avy);
-                dP[n] = fma(-lx, tpx, -(ly * tpy));
-                dU[n] = -lx * tux;
-                dV[n] = -ly * tvy;
+                dP[n] = fma(-lx, tpx, fma(-ly, tpy, sp[iq]));
+                dU[n] = fma(-lx, tux, su[iq]);
+                dV[n] = fma(-ly, tvy, sv[iq]);
             }
         }
         // D on the ghost rows -1, ty and E on the ghost columns -1, tx (transverse only)
@@ -531,7 +556,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
                 for (int k = tid; k < n; k += NT) {
                     const int jj = k / tx, c = k - jj * tx;
                     const double dlo = Dx[jj * G::DW + c], dhi = Dx[(jj + 1) * G::DW + c];
-                    const double w = -0.5 * lx * AX(AUX_IYS, c, jj);
+                    const double w = s_k[14] * AX(AUX_IYS, c, jj);
                     const double khi = AX(AUX_K, c, jj), klo = AX(AUX_K, c, jj - 1);
                     const double chi = AX(AUX_C, c, jj), clo = AX(AUX_C, c, jj - 1);
                     Gp[jj * TX + c] = w * fma(khi, dlo, -(klo * dhi));
@@ -543,7 +568,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
                 for (int k = tid; k < n; k += NT) {
                     const int r = k / w1, a = k - r * w1;
                     const double elo = Ey[r * G::EW + a], ehi = Ey[r * G::EW + a + 1];
-                    const double w = -0.5 * ly * AX(AUX_IXS, a, r);
+                    const double w = s_k[15] * AX(AUX_IXS, a, r);
                     const double khi = AX(AUX_K, a, r), klo = AX(AUX_K, a - 1, r);
                     const double chi = AX(AUX_C, a, r), clo = AX(AUX_C, a - 1, r);
                     Fp[r * (TX + 1) + a] = w * fma(khi, elo, -(klo * ehi));
@@ -556,8 +581,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
         // ---------------------------------------------------------------- phase D: update, store
         double kT = 0, kU = 0;
         if (MED == 0 && trans) {
-            kT = 0.125 * lx * ly * c0 * A.K0;
-            kU = 0.125 * lx * ly * c0 * c0;
+            kT = s_k[10];
+            kU = s_k[11];
         }
         double* dst = A.qnew + P.qoff;
 #pragma unroll
@@ -565,8 +590,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             const int ci = tid + n * NT;
             const int c = ci % TX, r = ci / TX;
             if (ci >= TX * TY || c >= tx || r >= ty) continue;
-            const int iq = (c + 2) + (r + 2) * G::SW;
-            double p = sp[iq] + dP[n], u = su[iq] + dU[n], v = sv[iq] + dV[n];
+            double p = dP[n], u = dU[n], v = dV[n];
             if (trans) {
                 if (MED == 0) {
                     const double dc = Dx[(r + 1) * G::DW + c], dn = Dx[(r + 2) * G::DW + c],
