@@ -30,12 +30,19 @@ METRIC = "FP64 cell-updates/s fused-batched vs plain per-patch launch; % of HBM 
 UNIT = "cell-updates/s"
 N_CELLS = 2048 * 2048
 PATCH = 32
-# FP64 flops (2 x DFMA + DADD + DMUL) the uniform-medium fused kernel executes per interior cell
-# update with 32 x 32 tiles, from the profiler's per-instruction counters of the current kernel
-# source (recorded with the source hash in profiles/step_uniform_2048x2048_traffic.json).
-FLOPS_PER_CELL = 72.19
+# Algorithmic FP64 work of one cell-update of the uniform-medium MC scheme with transverse
+# corrections, every edge solved once (the halo edges a tile recomputes are not counted):
+#   per x-edge and per y-edge  2 DADD + 2 DFMA (Riemann: dp, du, two wave strengths)
+#                              4 DADD (two MC limiters, one add each; limited sum and difference)
+#   per cell                   8 DADD + 10 DFMA (normal update, transverse pressures D, E)
+#                              6 DADD + 4 DFMA (transverse update)
+# = 26 DADD + 18 DFMA: 44 FP64-pipe instructions, 62 flops (an FMA counts 2).
+ALG_FP64_INSTR_PER_CELL = 44
+ALG_FLOPS_PER_CELL = 62
 BYTES_PER_CELL = 48.0     # read q^n (p, u, v) + write q^{n+1}: algorithmic HBM traffic
-# FP64 peak of the part: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz
+# The FP64 pipe of the part issues 2 FP64 instructions (any of DADD, DMUL, DFMA) per SM per
+# clock: 152 SMs x 2 x 2.07 GHz = 629 G instructions/s; 1.259 TFLOP/s if all were FMAs.
+FP64_ISSUE_PEAK_G = 152 * 2 * 2.07
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
@@ -271,7 +278,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_1808_02638_gb300 import claw, inputs
+    from paper_1808_02638_gb300 import claw, inputs, replicas
     from paper_1808_02638_gb300.build import build
     from paper_1808_02638_gb300.solver import Hierarchy
 
@@ -282,8 +289,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if rank == 0:
         build()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     build()   # no-op once built
 
     run = inputs.config1()
@@ -354,26 +360,21 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     start.record()
     for k in range(K):
         one_step(args.warmup + k, evs[k])
     end.record()
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     clocks = sampler.stop()
-    total_ms = start.elapsed_time(end)
     kern_ms = [a.elapsed_time(b) for a, b, _ in evs]
     fill_ms = [b.elapsed_time(c) for _, b, c in evs]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # every rank advances its own replica: the job's cell-updates over its slowest rank's time
+    dev = torch.device("cuda", local)
+    value, total_ms, _ = replicas.whole_job_rate(K * N_CELLS, start.elapsed_time(end), dist, dev)
     status = H.sync_status()
-    value = world * K * N_CELLS / (total_ms * 1e-3)
     kern_avg_s = statistics.mean(kern_ms) * 1e-3
 
     # plain path: one launch per patch (4096 launches per level-step), eager, same stream
@@ -413,7 +414,7 @@ def main():
         host_in, host_out = host_out, host_in
     e1.record()
     torch.cuda.synchronize()
-    e2e_value = world * e2e_steps * N_CELLS / (e0.elapsed_time(e1) * 1e-3)
+    e2e_value, _, _ = replicas.whole_job_rate(e2e_steps * N_CELLS, e0.elapsed_time(e1), dist, dev)
 
     adjoint = measure_adjoint() if (rank == 0 and not args.no_adjoint) else None
 
@@ -423,7 +424,8 @@ def main():
         return
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved_tflops = FLOPS_PER_CELL * N_CELLS / kern_avg_s / 1e12
+    achieved_gops = ALG_FP64_INSTR_PER_CELL * N_CELLS / kern_avg_s / 1e9
+    achieved_tflops = ALG_FLOPS_PER_CELL * N_CELLS / kern_avg_s / 1e12
     achieved_gbs = BYTES_PER_CELL * N_CELLS / kern_avg_s / 1e9
     # DRAM traffic of one launch from the last profiler capture, only while the kernel source
     # is unchanged since that capture
@@ -451,13 +453,18 @@ def main():
         "step": "two CUDA-graph replays: the persistent level-step launch (all 4096 patches, Eq. cfl) and "
                 "the ghost copy of q^{n+1}",
         "ghost_fill_ms": statistics.mean(fill_ms),
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "fused level-step (uniform medium, MC), autotuned tiling "
+        "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_ISSUE_PEAK_G,
+                     "unit": "G FP64 instructions/s", "frac": achieved_gops / FP64_ISSUE_PEAK_G, "traffic": traffic,
+                     "per_cell_update": f"{ALG_FP64_INSTR_PER_CELL} FP64 instructions (26 DADD + 18 DFMA), "
+                                        f"{ALG_FLOPS_PER_CELL} flops, {BYTES_PER_CELL:.0f} B",
+                     "kernel": "level-step (uniform medium, MC), autotuned tiling "
                                f"{tiling[0]}x{tiling[1]} tiles, {tiling[3]} threads, "
                                f"{'tensor bulk-copy' if tiling[2] else 'cooperative'} staging",
                      "kernel_ms": kern_avg_s * 1e3,
-                     "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz (derived)"},
+                     "peak_source": "FP64 pipe: 152 SMs x 2 instructions/clk x 2.07 GHz (derived; a measured "
+                                    "DFMA loop reaches 1.91 per SM per clk)",
+                     "flops": {"achieved_tflops": achieved_tflops, "peak_tflops": FP64_PEAK_TFLOPS,
+                               "frac": achieved_tflops / FP64_PEAK_TFLOPS}},
         "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm, "frac": achieved_gbs / hbm,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
         "plain_per_patch": plain,
