@@ -34,11 +34,12 @@ PATCH = 32
 # corrections, every edge solved once (the halo edges a tile recomputes are not counted):
 #   per x-edge and per y-edge  2 DADD + 2 DFMA (Riemann: dp, du, two wave strengths)
 #                              4 DADD (two MC limiters, one add each; limited sum and difference)
-#   per cell                   8 DADD + 10 DFMA (normal update, transverse pressures D, E)
-#                              6 DADD + 4 DFMA (transverse update)
-# = 26 DADD + 18 DFMA: 44 FP64-pipe instructions, 62 flops (an FMA counts 2).
-ALG_FP64_INSTR_PER_CELL = 44
-ALG_FLOPS_PER_CELL = 62
+#   per cell                   8 DADD + 10 DFMA (normal update with the centre transverse term,
+#                              transverse pressures D, E)
+#                              5 DADD + 3 DFMA (rest of the transverse update)
+# = 25 DADD + 17 DFMA: 42 FP64-pipe instructions, 59 flops (an FMA counts 2).
+ALG_FP64_INSTR_PER_CELL = 42
+ALG_FLOPS_PER_CELL = 59
 BYTES_PER_CELL = 48.0     # read q^n (p, u, v) + write q^{n+1}: algorithmic HBM traffic
 # The FP64 pipe of the part issues 2 FP64 instructions (any of DADD, DMUL, DFMA) per SM per
 # clock: 152 SMs x 2 x 2.07 GHz = 629 G instructions/s; 1.259 TFLOP/s if all were FMAs.
@@ -455,7 +456,7 @@ def main():
         "ghost_fill_ms": statistics.mean(fill_ms),
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_ISSUE_PEAK_G,
                      "unit": "G FP64 instructions/s", "frac": achieved_gops / FP64_ISSUE_PEAK_G, "traffic": traffic,
-                     "per_cell_update": f"{ALG_FP64_INSTR_PER_CELL} FP64 instructions (26 DADD + 18 DFMA), "
+                     "per_cell_update": f"{ALG_FP64_INSTR_PER_CELL} FP64 instructions (25 DADD + 17 DFMA), "
                                         f"{ALG_FLOPS_PER_CELL} flops, {BYTES_PER_CELL:.0f} B",
                      "kernel": "level-step (uniform medium, MC), autotuned tiling "
                                f"{tiling[0]}x{tiling[1]} tiles, {tiling[3]} threads, "

@@ -316,19 +316,23 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             s_k[14] = -0.5 * lx;
             s_k[15] = -0.5 * ly;
             if (MED == 0) {
+                // the centre part 2 kT (D + E) of the transverse pressure update folds into the
+                // normal-update coefficients (D = ap + kDx bp, E likewise); phase D adds the rest
                 const double kapx = c0 * (1.0 - lx * c0), kapy = c0 * (1.0 - ly * c0);
-                s_k[0] = -0.5 * lx * A.K0;            // cpa
-                s_k[1] = -0.25 * lx * kapx * Z0;      // cpb
-                s_k[2] = -0.5 * lx * c0;              // cua
-                s_k[3] = -0.25 * lx * kapx;           // cub
-                s_k[4] = -0.5 * ly * A.K0;            // cpay
-                s_k[5] = -0.25 * ly * kapy * Z0;      // cpby
-                s_k[6] = -0.5 * ly * c0;              // cva
-                s_k[7] = -0.25 * ly * kapy;           // cvb
-                s_k[8] = cw ? 1.0 - lx * c0 : 0.0;    // kDx
-                s_k[9] = cw ? 1.0 - ly * c0 : 0.0;    // kDy
-                s_k[10] = trans ? 0.125 * lx * ly * c0 * A.K0 : 0.0;   // kT
-                s_k[11] = trans ? 0.125 * lx * ly * c0 * c0 : 0.0;     // kU
+                const double kDx = cw ? 1.0 - lx * c0 : 0.0, kDy = cw ? 1.0 - ly * c0 : 0.0;
+                const double kT = trans ? 0.125 * lx * ly * c0 * A.K0 : 0.0;
+                s_k[0] = fma(-0.5 * lx, A.K0, 2.0 * kT);              // cpa
+                s_k[1] = fma(-0.25 * lx * kapx, Z0, 2.0 * kT * kDx);  // cpb
+                s_k[2] = -0.5 * lx * c0;                              // cua
+                s_k[3] = -0.25 * lx * kapx;                           // cub
+                s_k[4] = fma(-0.5 * ly, A.K0, 2.0 * kT);              // cpay
+                s_k[5] = fma(-0.25 * ly * kapy, Z0, 2.0 * kT * kDy);  // cpby
+                s_k[6] = -0.5 * ly * c0;                              // cva
+                s_k[7] = -0.25 * ly * kapy;                           // cvb
+                s_k[8] = kDx;
+                s_k[9] = kDy;
+                s_k[10] = -kT;
+                s_k[11] = trans ? 0.125 * lx * ly * c0 * c0 : 0.0;   // kU
             }
         }
         // medium access (MED == 1): aux plane k of the cell at tile-local (i, j)
@@ -452,6 +456,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
         // ---------------------------------------------------------------- phase C: per-cell terms
         // uniform medium, with a = 2 alpha and M = phi(theta) a:
         //   x-normal update  dp = -(lx K/2) ap - (lx kap Z/4) bp,  du = -(lx c/2) au - (lx kap/4) bu
+        //   (dp also carries the centre term 2 kT D of the transverse update)
         //   ap = A2_w + A1_e, au = A2_w - A1_e, bp = S_e - S_w, bu = P_e - P_w,  kap = c (1 - lx c)
         //   x-fluctuation pressure into the cell D = (K/2) (ap + (1 - lx c) bp)
         // cell-wise medium: D = K ap + bp,  x-normal (K ap + bp/2, c au + bu/2)
@@ -593,12 +598,9 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
             double p = dP[n], u = dU[n], v = dV[n];
             if (trans) {
                 if (MED == 0) {
-                    const double dc = Dx[(r + 1) * G::DW + c], dn = Dx[(r + 2) * G::DW + c],
-                                 ds = Dx[r * G::DW + c];
-                    const double ec = Ey[r * G::EW + c + 1], ee = Ey[r * G::EW + c + 2],
-                                 ew = Ey[r * G::EW + c];
-                    const double tp = fma(2.0, dc + ec, -((dn + ds) + (ee + ew)));
-                    p = fma(kT, tp, p);
+                    const double dn = Dx[(r + 2) * G::DW + c], ds = Dx[r * G::DW + c];
+                    const double ee = Ey[r * G::EW + c + 2], ew = Ey[r * G::EW + c];
+                    p = fma(kT, (dn + ds) + (ee + ew), p);   // kT holds -kT; 2 kT (dc + ec) is in p
                     u = fma(kU, ee - ew, u);
                     v = fma(kU, dn - ds, v);
                 } else {
