@@ -188,6 +188,60 @@ def cpu_baseline(target_s: float = 15.0):
                       f"oracle on a share of the patches, {wall:.1f} s wall"}
 
 
+def cpu_per_config():
+    """single-threaded oracle rates on bounded samples of the other workloads (cell-updates/s)"""
+    import numpy as np
+
+    import oracle
+    from oracle.amr import OracleHierarchy, run_single_grid
+    from paper_1808_02638_gb300 import inputs
+    oracle.build()
+    out = {}
+
+    def cells_per_coarse(run):
+        tot, sub = 0, 1
+        for L, lev in enumerate(run.levels):
+            sub *= lev.ratio if L else 1
+            tot += sub * sum(int(b[2]) * int(b[3]) for b in lev.boxes)
+        return tot
+
+    def single(name, run, rho, K, nsteps, sample):
+        lev = run.levels[0]
+        q = inputs.box_view(inputs.init_q(run, lev), 0, lev.NX, lev.NY, 3)
+        t0 = time.perf_counter()
+        run_single_grid(q, rho, K, lev.dx, lev.dy, nsteps, bc=run.bc)
+        dt = time.perf_counter() - t0
+        out[name] = {"value": lev.NX * lev.NY * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                     "sample": sample, "seconds": dt}
+
+    def amr(name, run, rho, K, ncoarse, sample):
+        q0 = [inputs.init_q(run, lev) for lev in run.levels]
+        O = OracleHierarchy(run, q0, rho, K)
+        t0 = time.perf_counter()
+        for _ in range(ncoarse):
+            O.coarse_step()
+        dt = time.perf_counter() - t0
+        out[name] = {"value": cells_per_coarse(run) * ncoarse / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                     "sample": sample, "seconds": dt}
+
+    run = inputs.config0()
+    one = np.ones((104, 104))
+    single("c0", run, one, 4.0 * one, 50, "all 50 steps of the 100x100 grid")
+    run = inputs.config2()
+    amr("c2", run, [inputs.const_pool(l, 1.0) for l in run.levels], [inputs.const_pool(l, 4.0) for l in run.levels],
+        2, "2 of the 20 coarse steps of the 3-level hierarchy")
+    run, r2, k2 = inputs.config3(256)
+    lev = run.levels[0]
+    rho = inputs.box_view(inputs.coef_pool(lev, r2, 1), 0, 256, 256, 1)[0]
+    K = inputs.box_view(inputs.coef_pool(lev, k2, 1), 0, 256, 256, 1)[0]
+    single("c3", run, rho, K, 20, "20 of the 400 forward steps of the 256x256 heterogeneous grid")
+    run, r2, k2 = inputs.config4_runs(1)[0]
+    amr("c4", run, [inputs.coef_pool(l, r2, 4 ** L) for L, l in enumerate(run.levels)],
+        [inputs.coef_pool(l, k2, 4 ** L) for L, l in enumerate(run.levels)], 1,
+        "1 coarse step of the first of the 64 runs")
+    return out
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -215,48 +269,6 @@ def run_reference(args, rank: int, world: int):
 
 
 # ----------------------------------------------------------------- GPU leg
-def measure_adjoint(nsteps: int = 400, every: int = 20):
-    """cost of the gradient of the receiver functional on the heterogeneous 256^2 workload:
-    forward rollout (with checkpoints) vs its backward (segment recompute + adjoint steps)"""
-    import numpy as np
-    import torch
-
-    from paper_1808_02638_gb300 import inputs
-    from paper_1808_02638_gb300.adjoint import rollout
-    from paper_1808_02638_gb300.solver import Hierarchy
-    n = 256
-    run, r2, k2 = inputs.config3(n)
-    lev = run.levels[0]
-    q, rho, K = inputs.init_q(run, lev), inputs.coef_pool(lev, r2, 1), inputs.coef_pool(lev, k2, 1)
-    H = Hierarchy([run], [[q]], [[rho]], [[K]])
-
-    def t(a, ref):
-        b = np.zeros(ref.numel())
-        b[:a.size] = a
-        return torch.from_numpy(b).to(ref.device).requires_grad_(True)
-
-    i0, j0, nb = inputs.receiver_box(n)
-    times = []
-    for _ in range(2):   # the first pass warms up
-        tq, tr, tk = t(q, H.q[0][0]), t(rho, H.rho[0]), t(K, H.rho[0])
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        out = rollout(H, [tq], [tr], [tk], ncoarse=nsteps, every=every)
-        v = out[0][:3 * (n + 4) ** 2].view(3, n + 4, n + 4)
-        J = (v[0, 2 + j0:2 + j0 + nb, 2 + i0:2 + i0 + nb] ** 2).sum()
-        torch.cuda.synchronize()
-        b = time.perf_counter()
-        J.backward()
-        torch.cuda.synchronize()
-        c = time.perf_counter()
-        times.append((b - a, c - b))
-    fwd, bwd = times[-1]
-    return {"workload": "256x256 heterogeneous medium (rho~U[0.5,2], K~U[1,8] smoothed), radial pulse, "
-                        "J = sum p^2 over the 16x16 receiver after 400 steps, checkpoints every 20",
-            "forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "backward_over_forward": bwd / fwd,
-            "note": "wall time of eager launches (no graphs); backward = segment recompute + adjoint steps"}
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -265,7 +277,8 @@ def main():
     ap.add_argument("--impl", default="claw", choices=["claw", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
-    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-workload measurements (0, 2, 3 with its adjoint, 4 with its adjoint)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -417,7 +430,10 @@ def main():
     torch.cuda.synchronize()
     e2e_value, _, _ = replicas.whole_job_rate(e2e_steps * N_CELLS, e0.elapsed_time(e1), dist, dev)
 
-    adjoint = measure_adjoint() if (rank == 0 and not args.no_adjoint) else None
+    per_config = None
+    if rank == 0 and not args.no_configs:
+        from paper_1808_02638_gb300 import measure
+        per_config = measure.run_all()
 
     if rank != 0:
         if dist:
@@ -474,10 +490,12 @@ def main():
         "tuning_ms": {f"{a}x{b}/s{c}/t{d}": round(v, 4) for (a, b, c, d), v in tune_ms.items()},
         "clocks": clocks,
         "status": claw.strerror(status),
-        "adjoint": adjoint,
+        "adjoint": per_config["c3"]["adjoint"] if per_config else None,
+        "per_config": per_config,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["per_config"] = cpu_per_config()
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

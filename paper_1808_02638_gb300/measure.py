@@ -1,0 +1,250 @@
+"""Per-workload GPU measurements: the fused batched level-steps (CUDA-graph replays) against the
+plain path (one launch per patch, eager) on the same hierarchy, and the adjoint's cost.
+
+  python -m paper_1808_02638_gb300.measure [names...]     (names: c0 c2 c3 c4; default all)
+
+Each workload reports interior cell-updates per second (a cell advanced one step on its level;
+ghost cells and halo recomputation are not counted), algorithmic HBM bytes per second (q read
+and written, 48 B per cell-update; 64 B with the cell-wise medium's rho, K), the fraction of the
+measured copy bandwidth, and the fraction of the FP64 pipe's issue rate used by the algorithmic
+FP64 instructions of the step (42 per cell-update uniform, 78 cell-wise; the kernel source
+states how they are counted).  Times are CUDA events around graph replays of whole coarse steps
+(ghost fill, every level-step with its substeps, averaging, the Eq. cfl update).
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+
+import numpy as np
+import torch
+
+from . import claw, inputs
+from .solver import Hierarchy
+
+FP64_INSTR_UNIFORM = 42
+FP64_INSTR_CELLWISE = 78
+BYTES_UNIFORM = 48.0
+BYTES_CELLWISE = 64.0
+FP64_ISSUE_PEAK_G = 152 * 2 * 2.07   # G FP64 instructions / s: 152 SMs x 2 per clock x 2.07 GHz
+
+
+def _hbm_peak():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    try:
+        with open(os.path.join(root, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def cell_updates_per_coarse_step(H):
+    total = 0
+    for run in H.runs:
+        sub = 1
+        for L, lev in enumerate(run.levels):
+            if L:
+                sub *= lev.ratio
+            total += sub * sum(int(b[2]) * int(b[3]) for b in lev.boxes)
+    return total
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_fused(H, ncoarse, warm=2):
+    """ms per coarse step over graph replays of two coarse steps"""
+    H.coarse_step()
+    H.coarse_step()
+    g = H.capture(2)
+    for _ in range(warm):
+        g.replay()
+    torch.cuda.synchronize()
+    reps = max(1, ncoarse // 2)
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / (2 * reps)
+
+
+def time_plain(H, ncoarse):
+    """ms per coarse step with one eager launch per patch per level-step"""
+    H.patchwise = True
+    try:
+        H.coarse_step()
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(ncoarse):
+            H.coarse_step()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / ncoarse
+    finally:
+        H.patchwise = False
+
+
+def _report(name, H, ms, plain_ms, fp64_per_cell, bytes_per_cell, extra=None):
+    hbm, hbm_src = _hbm_peak()
+    cells = cell_updates_per_coarse_step(H)
+    rate = cells / (ms * 1e-3)
+    gbs = rate * bytes_per_cell / 1e9
+    gops = rate * fp64_per_cell / 1e9
+    out = {"workload": name, "cell_updates_per_coarse_step": cells, "ms_per_coarse_step": ms,
+           "cell_updates_per_s": rate, "alg_gbs": gbs, "hbm_frac": gbs / hbm, "hbm_peak_source": hbm_src,
+           "fp64_gops": gops, "fp64_issue_frac": gops / FP64_ISSUE_PEAK_G,
+           "launches_per_coarse_step": H.launches_per_coarse_step(), "status": claw.strerror(H.sync_status())}
+    if plain_ms is not None:
+        out["plain_ms_per_coarse_step"] = plain_ms
+        out["plain_cell_updates_per_s"] = cells / (plain_ms * 1e-3)
+        out["fused_over_plain"] = plain_ms / ms
+    if extra:
+        out.update(extra)
+    return out
+
+
+# ----------------------------------------------------------------- workloads
+def config0():
+    run = inputs.config0()
+    H = Hierarchy([run], [[inputs.init_q(run, run.levels[0])]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    ms = time_fused(H, 50)
+    plain = time_plain(H, 10)
+    return _report("100x100 single grid, radial pulse, rho=1, K=4, MC, 50 steps", H, ms, plain,
+                   FP64_INSTR_UNIFORM, BYTES_UNIFORM, {"l2": "L2-resident (0.3 MB)"})
+
+
+def config2():
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    H.init_dt()
+    ms = time_fused(H, 20)
+    plain = time_plain(H, 2)
+    boxes = [len(l.boxes) for l in run.levels]
+    return _report("3-level AMR, 64^2 base, ratio 4 twice, seeded 8..64 patches on the annuli "
+                   f"(boxes per level {boxes}), radial pulse, rho=1, K=4, 20 coarse steps",
+                   H, ms, plain, FP64_INSTR_UNIFORM, BYTES_UNIFORM, {"l2": "L2-resident (about 30 MB)"})
+
+
+def _cellwise_single(n):
+    run, r2, k2 = inputs.config3(n)
+    lev = run.levels[0]
+    q = inputs.init_q(run, lev)
+    rho, K = inputs.coef_pool(lev, r2, 1), inputs.coef_pool(lev, k2, 1)
+    return run, q, rho, K
+
+
+def _tensors(H, pools, kind):
+    """per-level device copies of the per-run pools (requires_grad), in the hierarchy's layout"""
+    out = []
+    for L in range(H.nlev):
+        ref = H.q[L][0] if kind == "q" else H.rho[L]
+        a = np.zeros(ref.numel()) if kind == "q" else np.ones(ref.numel())
+        for (ri, qb, cb) in H.layout[L]:
+            base = qb if kind == "q" else cb
+            p = pools[ri][L]
+            a[base:base + p.size] = p
+        out.append(torch.from_numpy(a).to(ref.device).requires_grad_(True))
+    return out
+
+
+def _receiver_energy(H, outs):
+    """sum over runs of sum p^2 over each run's 16 x 16 level-0 receiver box"""
+    J = 0.0
+    for ri, run in enumerate(H.runs):
+        lev = run.levels[0]
+        qbase = [qb for (r, qb, _) in H.layout[0] if r == ri][0]
+        nx, ny = int(lev.boxes[0][2]), int(lev.boxes[0][3])
+        i0, j0, n = inputs.receiver_box(nx)
+        v = outs[0][qbase:qbase + 3 * (nx + 4) * (ny + 4)].view(3, ny + 4, nx + 4)
+        J = J + (v[0, 2 + j0:2 + j0 + n, 2 + i0:2 + i0 + n] ** 2).sum()
+    return J
+
+
+def time_adjoint(H, q, rho, K, ncoarse, every, passes=2):
+    """(forward ms, backward ms, gradients finite) of a checkpointed rollout and its reverse
+    sweep (eager launches); the last of `passes` passes is reported (the first warms up)"""
+    from .adjoint import rollout
+    for _ in range(passes):
+        tq, tr, tk = _tensors(H, q, "q"), _tensors(H, rho, "c"), _tensors(H, K, "c")
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        outs = rollout(H, tq, tr, tk, ncoarse=ncoarse, every=every)
+        J = _receiver_energy(H, outs)
+        e1.record()
+        torch.cuda.synchronize()
+        b0, b1 = _events()
+        b0.record()
+        J.backward()
+        b1.record()
+        torch.cuda.synchronize()
+    finite = all(bool(torch.isfinite(t.grad).all()) for t in tq + tr + tk)
+    return e0.elapsed_time(e1), b0.elapsed_time(b1), finite
+
+
+def config3(nsteps=400, every=20):
+    run, q, rho, K = _cellwise_single(256)
+    H = Hierarchy([run], [[q]], [[rho]], [[K]])
+    H.init_dt()
+    ms = time_fused(H, 40)
+    fwd, bwd, ok = time_adjoint(H, [[q]], [[rho]], [[K]], nsteps, every)
+    return _report("256x256 heterogeneous medium, 400 steps, checkpoints every 20, J = sum p^2 over the "
+                   "16x16 receiver", H, ms, None, FP64_INSTR_CELLWISE, BYTES_CELLWISE,
+                   {"adjoint": {"forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+                                "gradients_finite": ok,
+                                "note": "eager launches; backward = segment recompute + adjoint steps"}})
+
+
+def config4(nruns=64, ncoarse=100, every=20):
+    runs = inputs.config4_runs(nruns)
+    qs = [[inputs.init_q(run, lev) for lev in run.levels] for run, _, _ in runs]
+    rhos = [[inputs.coef_pool(lev, r2, 4 ** L) for L, lev in enumerate(run.levels)] for run, r2, _ in runs]
+    Ks = [[inputs.coef_pool(lev, k2, 4 ** L) for L, lev in enumerate(run.levels)] for run, _, k2 in runs]
+    H = Hierarchy([r for r, _, _ in runs], qs, rhos, Ks)
+    from . import tune
+    tiling = {}
+    for L in range(H.nlev):
+        tiling[L] = tune.tune_level(H, L, use_cache=False)[0]
+    H.init_dt()
+    ms = time_fused(H, 20)
+    plain = time_plain(H, 2)
+    H.init_dt()
+    fwd, bwd, ok = time_adjoint(H, qs, rhos, Ks, ncoarse, every)
+    nbox = [sum(len(r.levels[L].boxes) for r, _, _ in runs) for L in range(2)]
+    return _report(f"{nruns} independent 2-level runs (N in [64,256], ratio 4 on seeded annuli; boxes per "
+                   f"level {nbox}), per-run heterogeneous media, all runs in one launch per level-step",
+                   H, ms, plain, FP64_INSTR_CELLWISE, BYTES_CELLWISE,
+                   {"tiling": {str(L): list(t) for L, t in tiling.items()},
+                    "adjoint": {"coarse_steps": ncoarse, "every": every, "forward_ms": fwd, "backward_ms": bwd,
+                                "backward_over_forward": bwd / fwd, "gradients_finite": ok,
+                                "functional": "sum over runs of sum p^2 over each run's 16x16 receiver"}})
+
+
+WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4}
+
+
+def run_all(names=None):
+    out = {}
+    for name in names or WORKLOADS:
+        out[name] = WORKLOADS[name]()
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    from .build import build
+    build()
+    torch.cuda.set_device(0)
+    names = sys.argv[1:] or None
+    print(json.dumps(run_all(names), indent=1))
+
+
+if __name__ == "__main__":
+    main()
