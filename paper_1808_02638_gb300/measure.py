@@ -1,7 +1,9 @@
 """Per-workload GPU measurements: the fused batched level-steps (CUDA-graph replays) against the
 plain path (one launch per patch, eager) on the same hierarchy, and the adjoint's cost.
 
-  python -m paper_1808_02638_gb300.measure [names...]     (names: c0 c2 c3 c4; default all)
+  python -m paper_1808_02638_gb300.measure [names...] [--nruns N] [--ncoarse N] [--every N] [--no-plain]
+
+(names: c0 c2 c3 c4; default all; the options shrink the batched workload for a profiler)
 
 Each workload reports interior cell-updates per second (a cell advanced one step on its level;
 ghost cells and halo recomputation are not counted), algorithmic HBM bytes per second (q read
@@ -52,6 +54,12 @@ def cell_updates_per_coarse_step(H):
 
 def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def tune_all(H):
+    """autotuned tiling of every level (installed on H), keyed by level"""
+    from . import tune
+    return {str(L): list(tune.tune_level(H, L, use_cache=False)[0]) for L in range(H.nlev)}
 
 
 def time_fused(H, ncoarse, warm=2):
@@ -113,10 +121,11 @@ def config0():
     run = inputs.config0()
     H = Hierarchy([run], [[inputs.init_q(run, run.levels[0])]], rho0=1.0, K0=4.0)
     H.init_dt()
+    tiling = tune_all(H)
     ms = time_fused(H, 50)
     plain = time_plain(H, 10)
     return _report("100x100 single grid, radial pulse, rho=1, K=4, MC, 50 steps", H, ms, plain,
-                   FP64_INSTR_UNIFORM, BYTES_UNIFORM, {"l2": "L2-resident (0.3 MB)"})
+                   FP64_INSTR_UNIFORM, BYTES_UNIFORM, {"l2": "L2-resident (0.3 MB)", "tiling": tiling})
 
 
 def config2():
@@ -124,12 +133,14 @@ def config2():
     q0 = [inputs.init_q(run, lev) for lev in run.levels]
     H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
     H.init_dt()
+    tiling = tune_all(H)
     ms = time_fused(H, 20)
     plain = time_plain(H, 2)
     boxes = [len(l.boxes) for l in run.levels]
     return _report("3-level AMR, 64^2 base, ratio 4 twice, seeded 8..64 patches on the annuli "
                    f"(boxes per level {boxes}), radial pulse, rho=1, K=4, 20 coarse steps",
-                   H, ms, plain, FP64_INSTR_UNIFORM, BYTES_UNIFORM, {"l2": "L2-resident (about 30 MB)"})
+                   H, ms, plain, FP64_INSTR_UNIFORM, BYTES_UNIFORM,
+                   {"l2": "L2-resident (about 30 MB)", "tiling": tiling})
 
 
 def _cellwise_single(n):
@@ -193,35 +204,34 @@ def config3(nsteps=400, every=20):
     run, q, rho, K = _cellwise_single(256)
     H = Hierarchy([run], [[q]], [[rho]], [[K]])
     H.init_dt()
+    tiling = tune_all(H)
     ms = time_fused(H, 40)
     fwd, bwd, ok = time_adjoint(H, [[q]], [[rho]], [[K]], nsteps, every)
     return _report("256x256 heterogeneous medium, 400 steps, checkpoints every 20, J = sum p^2 over the "
                    "16x16 receiver", H, ms, None, FP64_INSTR_CELLWISE, BYTES_CELLWISE,
-                   {"adjoint": {"forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+                   {"tiling": tiling,
+                    "adjoint": {"forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
                                 "gradients_finite": ok,
                                 "note": "eager launches; backward = segment recompute + adjoint steps"}})
 
 
-def config4(nruns=64, ncoarse=100, every=20):
+def config4(nruns=64, ncoarse=100, every=20, plain=True):
     runs = inputs.config4_runs(nruns)
     qs = [[inputs.init_q(run, lev) for lev in run.levels] for run, _, _ in runs]
     rhos = [[inputs.coef_pool(lev, r2, 4 ** L) for L, lev in enumerate(run.levels)] for run, r2, _ in runs]
     Ks = [[inputs.coef_pool(lev, k2, 4 ** L) for L, lev in enumerate(run.levels)] for run, _, k2 in runs]
     H = Hierarchy([r for r, _, _ in runs], qs, rhos, Ks)
-    from . import tune
-    tiling = {}
-    for L in range(H.nlev):
-        tiling[L] = tune.tune_level(H, L, use_cache=False)[0]
     H.init_dt()
+    tiling = tune_all(H)
     ms = time_fused(H, 20)
-    plain = time_plain(H, 2)
+    plain = time_plain(H, 2) if plain else None
     H.init_dt()
     fwd, bwd, ok = time_adjoint(H, qs, rhos, Ks, ncoarse, every)
     nbox = [sum(len(r.levels[L].boxes) for r, _, _ in runs) for L in range(2)]
     return _report(f"{nruns} independent 2-level runs (N in [64,256], ratio 4 on seeded annuli; boxes per "
                    f"level {nbox}), per-run heterogeneous media, all runs in one launch per level-step",
                    H, ms, plain, FP64_INSTR_CELLWISE, BYTES_CELLWISE,
-                   {"tiling": {str(L): list(t) for L, t in tiling.items()},
+                   {"tiling": tiling,
                     "adjoint": {"coarse_steps": ncoarse, "every": every, "forward_ms": fwd, "backward_ms": bwd,
                                 "backward_over_forward": bwd / fwd, "gradients_finite": ok,
                                 "functional": "sum over runs of sum p^2 over each run's 16x16 receiver"}})
@@ -239,11 +249,21 @@ def run_all(names=None):
 
 
 def main():
+    import argparse
     from .build import build
+    ap = argparse.ArgumentParser()
+    ap.add_argument("names", nargs="*")
+    ap.add_argument("--nruns", type=int, default=64)
+    ap.add_argument("--ncoarse", type=int, default=100)
+    ap.add_argument("--every", type=int, default=20)
+    ap.add_argument("--no-plain", action="store_true")
+    a = ap.parse_args()
     build()
     torch.cuda.set_device(0)
-    names = sys.argv[1:] or None
-    print(json.dumps(run_all(names), indent=1))
+    if a.names == ["c4"]:
+        print(json.dumps({"c4": config4(a.nruns, a.ncoarse, a.every, not a.no_plain)}, indent=1))
+    else:
+        print(json.dumps(run_all(a.names or None), indent=1))
 
 
 if __name__ == "__main__":
