@@ -9,7 +9,11 @@
 // Each reverse phase is a gather where it can be (every adjoint written by one thread);
 // accumulations that two threads share use shared-memory atomics, and contributions to cells
 // shared with neighbouring tiles (the two ghost layers) reach lam_old / g_aux through global
-// FP64 atomics.  A uniform medium runs the same code with constant medium planes.
+// FP64 atomics.  The medium adjoint is kept for the Z, c and K planes only: the chain rule
+// through c^2 and through the edge planes (1/(Z_L+Z_R) and the limiter projection factors,
+// functions of the two cells' Z) is applied where those planes are read, which keeps the
+// tile's shared memory small enough for two CTAs per SM.  A uniform medium runs the same code
+// with constant medium planes and no medium adjoint.
 #include <cuda_runtime.h>
 
 #include "claw_step.cuh"
@@ -136,12 +140,14 @@ struct AGeo {
     static constexpr int O_BVY = O_BPY + EN;
     static constexpr int O_FB = O_BVY + EN;             // adjoints of Fp, Fu, Gp, Gv
     static constexpr int O_GB = O_FB + 2 * FN;
-    static constexpr int O_MED = O_GB + 2 * GN;         // medium-plane adjoints, CLAW_NAUX planes
-    static constexpr int NTOT = O_MED + CLAW_NAUX * QPL;
+    static constexpr int O_MED = O_GB + 2 * GN;         // medium adjoints: Z, c, K planes
+    static constexpr int NMED = 3;
+    static size_t smem_bytes(int med) { return (size_t)(O_MED + (med ? NMED * QPL : 0)) * 8; }
 };
+static_assert(AUX_Z == 0 && AUX_C == 1 && AUX_K == 2, "medium adjoint planes are the first three aux planes");
 
 template <int MED, int LIM>
-__global__ void __launch_bounds__(ANT, 1)
+__global__ void __launch_bounds__(ANT, 2)
     step_adjoint_kernel(const StepArgs A, const double* __restrict__ lam_new, double* __restrict__ lam_old,
                         double* __restrict__ g_aux)
 {
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(ANT, 1)
     double* Fub = Fpb + G::FN;
     double* Gpb = sm + G::O_GB;
     double* Gvb = Gpb + G::GN;
-    double* medb = sm + G::O_MED;   // [CLAW_NAUX][QPL]
+    double* medb = sm + G::O_MED;   // [3][QPL]: Z, c, K
 
     const int tid = threadIdx.x;
     const bool second = A.order == 2;
@@ -216,6 +222,7 @@ __global__ void __launch_bounds__(ANT, 1)
             case AUX_K: return A.K0;
             case AUX_C2: return c0 * c0;
             case AUX_IXS: case AUX_IYS: return iZs;
+            case AUX_IZ: return 1.0 / fma(Z0, Z0, 1.0);
             default: return 1.0;
             }
         };
@@ -226,8 +233,16 @@ __global__ void __launch_bounds__(ANT, 1)
         auto YL = [](int c, int b) { return (c + 1) + b * G::YLW; };
         auto DI = [](int c, int r) { return c + (r + 1) * G::DW; };
         auto EI = [](int c, int r) { return (c + 1) + r * G::EW; };
-        auto medadd = [&](int k, int i, int j, double v) {
+        auto medadd = [&](int k, int i, int j, double v) {   // k: AUX_Z, AUX_C or AUX_K
             if (MED) atomicAdd(&medb[k * G::QPL + CI(i, j)], v);
+        };
+        // adjoint of the projection factors of an edge (Z_L of the west / south cell, Z_R of
+        // the east / north cell): f1 = (Z_L Z_R + 1) iz_L, f2 = (Z_L Z_R + 1) iz_R with
+        // iz = 1 / (Z^2 + 1); returns the Z_L and Z_R adjoints
+        auto proj_adj = [&](double zl, double zr, double izl, double izr, double f1, double f2, double g1,
+                            double g2, double& gzl, double& gzr) {
+            gzl = izl * fma(-2.0 * zl, f1, zr) * g1 + zr * izr * g2;
+            gzr = zl * izl * g1 + izr * fma(-2.0 * zr, f2, zl) * g2;
         };
 
         // ---------------------------------------------------------------- stage, clear
@@ -243,7 +258,7 @@ __global__ void __launch_bounds__(ANT, 1)
             }
             for (int k = tid; k < G::O_MED - G::O_A1B; k += ANT) sm[G::O_A1B + k] = 0.0;
             if (MED)
-                for (int k = tid; k < CLAW_NAUX * G::QPL; k += ANT) medb[k] = 0.0;
+                for (int k = tid; k < G::NMED * G::QPL; k += ANT) medb[k] = 0.0;
         }
         __syncthreads();
 
@@ -365,7 +380,10 @@ __global__ void __launch_bounds__(ANT, 1)
                     medadd(AUX_K, c, r, wG * dlo * gp);
                     medadd(AUX_C, c, r, wG * dlo * gv);
                     const double gpf = fma(Kc, dlo, -(klo * dme)), gvf = fma(cc, dlo, clo * dme);
-                    medadd(AUX_IYS, c, r, -0.5 * lx * (gpf * gp + gvf * gv));
+                    // iys = 1/(Z_lo + Z_hi): d iys / dZ = -iys^2 for both cells
+                    const double gz = -is * is * (-0.5 * lx * (gpf * gp + gvf * gv));
+                    medadd(AUX_Z, c, r - 1, gz);
+                    medadd(AUX_Z, c, r, gz);
                 }
                 Db[DI(c, r)] = acc;
             }
@@ -393,7 +411,9 @@ __global__ void __launch_bounds__(ANT, 1)
                     medadd(AUX_K, c, r, wF * elo * fp);
                     medadd(AUX_C, c, r, wF * elo * fu);
                     const double fpf = fma(Kc, elo, -(klo * eme)), fuf = fma(cc, elo, clo * eme);
-                    medadd(AUX_IXS, c, r, -0.5 * ly * (fpf * fp + fuf * fu));
+                    const double gz = -is * is * (-0.5 * ly * (fpf * fp + fuf * fu));
+                    medadd(AUX_Z, c - 1, r, gz);
+                    medadd(AUX_Z, c, r, gz);
                 }
                 Eb[EI(c, r)] = acc;
             }
@@ -503,13 +523,12 @@ __global__ void __launch_bounds__(ANT, 1)
                 const double kr = fma(-lx, AX(AUX_C2, a, r), AX(AUX_C, a, r));
                 const double m1 = M1x[XL(a, r)], m2 = M2x[XL(a, r)];
                 const double ge2 = fma(zr, gcp, gcu), ge1 = fma(-zl, gcp, gcu);
-                medadd(AUX_Z, a, r, kr * m2 * gcp);
-                medadd(AUX_Z, a - 1, r, -(kl * m1 * gcp));
                 const double gkl = m1 * ge1, gkr = m2 * ge2;
-                medadd(AUX_C, a - 1, r, gkl);
-                medadd(AUX_C2, a - 1, r, -lx * gkl);
-                medadd(AUX_C, a, r, gkr);
-                medadd(AUX_C2, a, r, -lx * gkr);
+                // kappa = c - l c^2: d kappa / dc = 1 - 2 l c (the c^2 plane folded into c)
+                if (MED) {
+                    medadd(AUX_C, a - 1, r, gkl * fma(-2.0 * lx, AX(AUX_C, a - 1, r), 1.0));
+                    medadd(AUX_C, a, r, gkr * fma(-2.0 * lx, AX(AUX_C, a, r), 1.0));
+                }
                 const double gm1 = kl * ge1, gm2 = kr * ge2;
                 const double f1 = AX(AUX_FX1, a, r), f2 = AX(AUX_FX2, a, r);
                 const double up1 = A1[XE(a + 1, r)], up2 = A2[XE(a - 1, r)];
@@ -517,11 +536,17 @@ __global__ void __launch_bounds__(ANT, 1)
                 LimD<LIM>::f(A1[XE(a, r)], up1 * f1, da, db);
                 atomicAdd(&A1b[XE(a, r)], da * gm1);
                 atomicAdd(&A1b[XE(a + 1, r)], f1 * db * gm1);
-                medadd(AUX_FX1, a, r, up1 * db * gm1);
+                const double gf1 = up1 * db * gm1;
                 LimD<LIM>::f(A2[XE(a, r)], up2 * f2, da, db);
                 atomicAdd(&A2b[XE(a, r)], da * gm2);
                 atomicAdd(&A2b[XE(a - 1, r)], f2 * db * gm2);
-                medadd(AUX_FX2, a, r, up2 * db * gm2);
+                const double gf2 = up2 * db * gm2;
+                if (MED) {
+                    double gzl, gzr;
+                    proj_adj(zl, zr, AX(AUX_IZ, a - 1, r), AX(AUX_IZ, a, r), f1, f2, gf1, gf2, gzl, gzr);
+                    medadd(AUX_Z, a, r, fma(kr * m2, gcp, gzr));
+                    medadd(AUX_Z, a - 1, r, fma(-(kl * m1), gcp, gzl));
+                }
             }
             for (int k = tid; k < (ty + 1) * (tx + 2); k += ANT) {
                 const int b = k / (tx + 2), c = k % (tx + 2) - 1;
@@ -531,13 +556,11 @@ __global__ void __launch_bounds__(ANT, 1)
                 const double kr = fma(-ly, AX(AUX_C2, c, b), AX(AUX_C, c, b));
                 const double m1 = M1y[YL(c, b)], m2 = M2y[YL(c, b)];
                 const double ge2 = fma(zr, gcp, gcv), ge1 = fma(-zl, gcp, gcv);
-                medadd(AUX_Z, c, b, kr * m2 * gcp);
-                medadd(AUX_Z, c, b - 1, -(kl * m1 * gcp));
                 const double gkl = m1 * ge1, gkr = m2 * ge2;
-                medadd(AUX_C, c, b - 1, gkl);
-                medadd(AUX_C2, c, b - 1, -ly * gkl);
-                medadd(AUX_C, c, b, gkr);
-                medadd(AUX_C2, c, b, -ly * gkr);
+                if (MED) {
+                    medadd(AUX_C, c, b - 1, gkl * fma(-2.0 * ly, AX(AUX_C, c, b - 1), 1.0));
+                    medadd(AUX_C, c, b, gkr * fma(-2.0 * ly, AX(AUX_C, c, b), 1.0));
+                }
                 const double gm1 = kl * ge1, gm2 = kr * ge2;
                 const double f1 = AX(AUX_FY1, c, b), f2 = AX(AUX_FY2, c, b);
                 const double up1 = B1[YE(c, b + 1)], up2 = B2[YE(c, b - 1)];
@@ -545,11 +568,17 @@ __global__ void __launch_bounds__(ANT, 1)
                 LimD<LIM>::f(B1[YE(c, b)], up1 * f1, da, db);
                 atomicAdd(&B1b[YE(c, b)], da * gm1);
                 atomicAdd(&B1b[YE(c, b + 1)], f1 * db * gm1);
-                medadd(AUX_FY1, c, b, up1 * db * gm1);
+                const double gf1 = up1 * db * gm1;
                 LimD<LIM>::f(B2[YE(c, b)], up2 * f2, da, db);
                 atomicAdd(&B2b[YE(c, b)], da * gm2);
                 atomicAdd(&B2b[YE(c, b - 1)], f2 * db * gm2);
-                medadd(AUX_FY2, c, b, up2 * db * gm2);
+                const double gf2 = up2 * db * gm2;
+                if (MED) {
+                    double gzl, gzr;
+                    proj_adj(zl, zr, AX(AUX_IZ, c, b - 1), AX(AUX_IZ, c, b), f1, f2, gf1, gf2, gzl, gzr);
+                    medadd(AUX_Z, c, b, fma(kr * m2, gcp, gzr));
+                    medadd(AUX_Z, c, b - 1, fma(-(kl * m1), gcp, gzl));
+                }
             }
             __syncthreads();
         }
@@ -570,9 +599,11 @@ __global__ void __launch_bounds__(ANT, 1)
             atomicAdd(&pb[iR - 1], -gdp);
             atomicAdd(&ub[iR], gdu);
             atomicAdd(&ub[iR - 1], -gdu);
-            medadd(AUX_IXS, a, r, fma(n1, g1, n2 * g2));
-            medadd(AUX_Z, a, r, du * gn1);
-            medadd(AUX_Z, a - 1, r, du * gn2);
+            if (MED) {   // is = 1/(Z_L + Z_R): d is / dZ = -is^2 for both cells
+                const double gs = -is * is * fma(n1, g1, n2 * g2);
+                medadd(AUX_Z, a, r, fma(du, gn1, gs));
+                medadd(AUX_Z, a - 1, r, fma(du, gn2, gs));
+            }
         }
         for (int k = tid; k < (ty + 3) * (tx + 2); k += ANT) {
             const int b = k / (tx + 2) - 1, c = k % (tx + 2) - 1;
@@ -588,9 +619,11 @@ __global__ void __launch_bounds__(ANT, 1)
             atomicAdd(&pb[iR - G::SW], -gdp);
             atomicAdd(&vb[iR], gdv);
             atomicAdd(&vb[iR - G::SW], -gdv);
-            medadd(AUX_IYS, c, b, fma(n1, g1, n2 * g2));
-            medadd(AUX_Z, c, b, dv * gn1);
-            medadd(AUX_Z, c, b - 1, dv * gn2);
+            if (MED) {
+                const double gs = -is * is * fma(n1, g1, n2 * g2);
+                medadd(AUX_Z, c, b, fma(dv, gn1, gs));
+                medadd(AUX_Z, c, b - 1, fma(dv, gn2, gs));
+            }
         }
         __syncthreads();
 
@@ -606,7 +639,7 @@ __global__ void __launch_bounds__(ANT, 1)
             }
             if (MED && g_aux) {
                 double* ga = g_aux + P.aoff;
-                for (int k = tid; k < CLAW_NAUX * G::QPL; k += ANT) {
+                for (int k = tid; k < G::NMED * G::QPL; k += ANT) {
                     const int m = k / G::QPL, rem = k - m * G::QPL;
                     const int jj = rem / G::SW, ii = rem - jj * G::SW;
                     if (ii >= tx + 4 || jj >= ty + 4) continue;
@@ -620,22 +653,55 @@ __global__ void __launch_bounds__(ANT, 1)
 }
 
 template <int MED>
-cudaError_t launch_adj_med(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux, int limiter,
-                           int grid, cudaStream_t s)
+void (*adj_kernel(int limiter))(const StepArgs, const double*, double*, double*)
 {
-    const size_t smem = (size_t)AGeo::NTOT * 8;
-    void (*fn)(const StepArgs, const double*, double*, double*) = nullptr;
     switch (limiter) {
-    case CLAW_LIM_NONE: fn = step_adjoint_kernel<MED, CLAW_LIM_NONE>; break;
-    case CLAW_LIM_MINMOD: fn = step_adjoint_kernel<MED, CLAW_LIM_MINMOD>; break;
-    case CLAW_LIM_SUPERBEE: fn = step_adjoint_kernel<MED, CLAW_LIM_SUPERBEE>; break;
-    case CLAW_LIM_VANLEER: fn = step_adjoint_kernel<MED, CLAW_LIM_VANLEER>; break;
-    case CLAW_LIM_MC: fn = step_adjoint_kernel<MED, CLAW_LIM_MC>; break;
-    default: return cudaErrorInvalidValue;
+    case CLAW_LIM_NONE: return step_adjoint_kernel<MED, CLAW_LIM_NONE>;
+    case CLAW_LIM_MINMOD: return step_adjoint_kernel<MED, CLAW_LIM_MINMOD>;
+    case CLAW_LIM_SUPERBEE: return step_adjoint_kernel<MED, CLAW_LIM_SUPERBEE>;
+    case CLAW_LIM_VANLEER: return step_adjoint_kernel<MED, CLAW_LIM_VANLEER>;
+    case CLAW_LIM_MC: return step_adjoint_kernel<MED, CLAW_LIM_MC>;
     }
-    cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return nullptr;
+}
+
+// kernel with its shared-memory attribute set, and its resident CTAs per SM (cached per device)
+template <int MED>
+cudaError_t prepare_adj(int limiter, void (**fn)(const StepArgs, const double*, double*, double*), int* per_sm)
+{
+    constexpr int kDev = 64;
+    static int cached[kDev][5] = {};
+    *fn = adj_kernel<MED>(limiter);
+    if (!*fn || limiter < 0 || limiter > 4) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t ed = cudaGetDevice(&dev);
+    if (ed != cudaSuccess) return ed;
+    if (dev < 0 || dev >= kDev) return cudaErrorInvalidDevice;
+    int* c = cached[dev];
+    const size_t smem = AGeo::smem_bytes(MED);
+    if (!c[limiter]) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, *fn, ANT, smem);
+        if (e != cudaSuccess) return e;
+        c[limiter] = n > 0 ? n : 1;
+    }
+    *per_sm = c[limiter];
+    return cudaSuccess;
+}
+
+template <int MED>
+cudaError_t launch_adj_med(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux, int limiter,
+                           int nsm, cudaStream_t s)
+{
+    void (*fn)(const StepArgs, const double*, double*, double*) = nullptr;
+    int per_sm = 1;
+    cudaError_t e = prepare_adj<MED>(limiter, &fn, &per_sm);
     if (e != cudaSuccess) return e;
-    fn<<<grid, ANT, smem, s>>>(a, lam_new, lam_old, g_aux);
+    const int grid = a.ntiles < per_sm * nsm ? a.ntiles : per_sm * nsm;
+    if (grid <= 0) return cudaSuccess;
+    fn<<<grid, ANT, AGeo::smem_bytes(MED), s>>>(a, lam_new, lam_old, g_aux);
     return cudaGetLastError();
 }
 
@@ -644,10 +710,10 @@ cudaError_t launch_adj_med(const StepArgs& a, const double* lam_new, double* lam
 int adjoint_tile() { return ATX; }
 
 cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux, int medium,
-                                int limiter, int grid, cudaStream_t s)
+                                int limiter, int nsm, cudaStream_t s)
 {
-    return medium ? launch_adj_med<1>(a, lam_new, lam_old, g_aux, limiter, grid, s)
-                  : launch_adj_med<0>(a, lam_new, lam_old, nullptr, limiter, grid, s);
+    return medium ? launch_adj_med<1>(a, lam_new, lam_old, g_aux, limiter, nsm, s)
+                  : launch_adj_med<0>(a, lam_new, lam_old, nullptr, limiter, nsm, s);
 }
 
 }  // namespace claw

@@ -937,9 +937,8 @@ int claw_level_step_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const
     StepArgs a = make_args(ctx, L, q_old, nullptr, aux, dt, nullptr);
     a.tiles = ctx->atiles[L];
     a.ntiles = ctx->natiles[L];
-    const int grid = std::min(a.ntiles, ctx->nsm);
     ctx->launches += 1;
-    return cuda_rc(launch_step_adjoint(a, lam_new, lam_old, g_aux, ctx->medium, ctx->limiter, grid,
+    return cuda_rc(launch_step_adjoint(a, lam_new, lam_old, g_aux, ctx->medium, ctx->limiter, ctx->nsm,
                                        (cudaStream_t)stream));
 }
 

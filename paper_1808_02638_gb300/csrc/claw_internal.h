@@ -23,8 +23,9 @@ enum AuxPlane : int {
     AUX_IYS = 7,  // 1 / (Z_{i,j-1} + Z_{i,j})
     AUX_FY1 = 8,
     AUX_FY2 = 9,
+    AUX_IZ = 10,  // 1 / (Z^2 + 1): derivatives of the projection factors (reverse mode)
 };
-static_assert(CLAW_NAUX == 10, "aux plane count");
+static_assert(CLAW_NAUX == 11, "aux plane count");
 
 // One box of a level, as the kernels see it.
 struct PatchDev {
@@ -130,7 +131,7 @@ cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int 
                         int grid, cudaStream_t s);
 int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int nt, int staging);
 cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
-                                int medium, int limiter, int grid, cudaStream_t s);
+                                int medium, int limiter, int nsm, cudaStream_t s);   // grid: resident CTAs x nsm
 int adjoint_tile();   // the adjoint kernel's square tile edge
 
 // launchers (claw_ghost.cu)
