@@ -162,6 +162,7 @@ void free_level(claw_ctx* ctx, int L)
     cudaFree(d.copy_start);
     cudaFree(d.ccopy_start);
     d.copy_start = d.ccopy_start = nullptr;
+    d.ncopy_blocks = d.nccopy_blocks = 0;
     cudaFree(ctx->ptiles[L]);
     cudaFree(ctx->atiles[L]);
     ctx->atiles[L] = nullptr;
@@ -245,6 +246,9 @@ struct GhostEntry {
 };
 
 // ghost tasks of one level: copy rectangles and interpolated cells
+constexpr int kRectRows = 32;          // copy rectangles are split into pieces of at most this many rows
+constexpr long long kBlockCells = 1024;  // cells per block of the copy kernel (about)
+
 int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::vector<InterpCell>& cells,
                        std::vector<int>& start)
 {
@@ -259,7 +263,6 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
         for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
             cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
 
-    start.assign(1, 0);
     for (int n = 0; n < d.nboxes; ++n) {
         const claw_box& b = d.boxes[n];
         const claw_problem& pr = ctx->runs[b.run];
@@ -351,7 +354,14 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
             c.sy = (int)o.sy;
             c.sx = o.first.sx;
             c.flags = o.first.flags;
-            rects.push_back(c);
+            // at most kRectRows rows per rectangle, so that long strips spread over blocks
+            for (int k0 = 0; k0 < o.h; k0 += kRectRows) {
+                CopyRect piece = c;
+                piece.h = std::min(kRectRows, o.h - k0);
+                piece.dst = c.dst + (long long)k0 * c.dpitch;
+                piece.src = c.src + (long long)k0 * c.sy;
+                rects.push_back(piece);
+            }
         };
         for (const RowRun& R : runs) {
             bool merged = false;
@@ -385,8 +395,21 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
             }
         }
         for (const Open& o : open) emit(o);
-        start.push_back((int)rects.size());
     }
+    // blocks of the copy kernel: consecutive rectangles up to about kBlockCells cells (and at
+    // most 32 rectangles, the kernel's staging chunk)
+    start.assign(1, 0);
+    long long cells_in = 0;
+    for (size_t i = 0; i < rects.size(); ++i) {
+        const long long c = (long long)rects[i].w * rects[i].h;
+        const int nin = (int)i - start.back();
+        if (nin > 0 && (cells_in + c > kBlockCells || nin >= 32)) {
+            start.push_back((int)i);
+            cells_in = 0;
+        }
+        cells_in += c;
+    }
+    if (!rects.empty()) start.push_back((int)rects.size());
     return CLAW_OK;
 }
 
@@ -678,6 +701,9 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     int rc = build_ghost_tables(ctx, L, rects, cells, qstart);
     if (rc) return rc;
     if ((rc = upload(&d.copy_start, qstart))) return rc;
+    d.ncopy_blocks = qstart.empty() ? 0 : (int)qstart.size() - 1;
+    d.max_rows = 0;
+    for (const claw_box& b : d.boxes) d.max_rows = std::max(d.max_rows, b.ny + 4);
     if (L > 0) build_avg_tables(ctx, L, avg);
     // the same copies for one-plane pools: offsets from coff, no wall sign flips
     std::vector<CopyRect> crects;
@@ -688,6 +714,7 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         std::vector<int> cstart;
         rc = build_ghost_tables(ctx, L, crects, unused, cstart);
         if (!rc) rc = upload(&d.ccopy_start, cstart);
+        d.nccopy_blocks = cstart.empty() ? 0 : (int)cstart.size() - 1;
         d.boxes = saved;
         if (rc) return rc;
         for (auto& r : crects) r.flags = 0;
@@ -732,7 +759,7 @@ int claw_medium_aux(claw_ctx* ctx, int32_t L, const double* rho, const double* K
     DevGuard g(ctx->device);
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nboxes > 0;
-    return cuda_rc(launch_medium_aux(d.patches, d.nboxes, rho, K, aux, 0, (cudaStream_t)stream));
+    return cuda_rc(launch_medium_aux(d.patches, d.nboxes, d.max_rows, rho, K, aux, (cudaStream_t)stream));
 }
 
 int claw_medium_aux_adjoint(claw_ctx* ctx, int32_t L, const double* rho, const double* K, const double* g_aux,
@@ -742,7 +769,7 @@ int claw_medium_aux_adjoint(claw_ctx* ctx, int32_t L, const double* rho, const d
     DevGuard g(ctx->device);
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nboxes > 0;
-    return cuda_rc(launch_medium_aux_adjoint(d.patches, d.nboxes, rho, K, g_aux, g_rho, g_K, (cudaStream_t)stream));
+    return cuda_rc(launch_medium_aux_adjoint(d.patches, d.nboxes, d.max_rows, rho, K, g_aux, g_rho, g_K, (cudaStream_t)stream));
 }
 
 int claw_fill_ghost(claw_ctx* ctx, int32_t L, double* q, const double* qc_old, const double* qc_new, double tau,
@@ -754,7 +781,7 @@ int claw_fill_ghost(claw_ctx* ctx, int32_t L, double* q, const double* qc_old, c
     if (d.ninterp > 0 && (!qc_old || !qc_new || !(tau >= 0.0 && tau <= 1.0))) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = d.ncopy ? launch_fill_copy(d.copies, d.copy_start, d.nboxes, q, s) : cudaSuccess;
+    cudaError_t e = d.ncopy ? launch_fill_copy(d.copies, d.copy_start, d.ncopy_blocks, q, s) : cudaSuccess;
     ctx->launches += d.ncopy > 0;
     if (e == cudaSuccess) {
         e = launch_fill_interp(d.interps, d.ninterp, q, qc_old, qc_new, tau, s);
@@ -770,7 +797,7 @@ int claw_fill_ghost_coef(claw_ctx* ctx, int32_t L, double* a, void* stream)
     DevGuard g(ctx->device);
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nccopy > 0;
-    return cuda_rc(d.nccopy ? launch_fill_copy(d.ccopies, d.ccopy_start, d.nboxes, a, (cudaStream_t)stream, 1)
+    return cuda_rc(d.nccopy ? launch_fill_copy(d.ccopies, d.ccopy_start, d.nccopy_blocks, a, (cudaStream_t)stream, 1)
                             : cudaSuccess);
 }
 
@@ -781,7 +808,7 @@ int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t L, double* g, void* stre
     DevGuard gd(ctx->device);
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nccopy > 0;
-    return cuda_rc(d.nccopy ? launch_fill_copy_adjoint(d.ccopies, d.ccopy_start, d.nboxes, g, (cudaStream_t)stream, 1)
+    return cuda_rc(d.nccopy ? launch_fill_copy_adjoint(d.ccopies, d.ccopy_start, d.nccopy_blocks, g, (cudaStream_t)stream, 1)
                             : cudaSuccess);
 }
 
@@ -798,7 +825,7 @@ int claw_fill_ghost_adjoint(claw_ctx* ctx, int32_t L, double* lam, double* lco, 
     cudaError_t e = launch_fill_interp_adjoint(d.interps, d.ninterp, lam, lco, lcn, qc_old, qc_new, tau, s);
     ctx->launches += d.ninterp > 0;
     if (e == cudaSuccess && d.ncopy) {
-        e = launch_fill_copy_adjoint(d.copies, d.copy_start, d.nboxes, lam, s);
+        e = launch_fill_copy_adjoint(d.copies, d.copy_start, d.ncopy_blocks, lam, s);
         ctx->launches += 1;
     }
     return cuda_rc(e);
@@ -811,7 +838,7 @@ int claw_cfl_max(claw_ctx* ctx, int32_t L, const double* aux, double* smax, void
     if (ctx->medium == 1 && !aux) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = launch_cfl_max(ctx->lev[L].patches, ctx->lev[L].nboxes, ctx->medium, std::sqrt(ctx->K0 / ctx->rho0), aux,
+    cudaError_t e = launch_cfl_max(ctx->lev[L].patches, ctx->lev[L].nboxes, ctx->lev[L].max_rows, ctx->medium, std::sqrt(ctx->K0 / ctx->rho0), aux,
                            smax, s);
     ctx->launches += 1;
     return cuda_rc(e);
@@ -879,7 +906,7 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
     ctx->launches += 1;
     cudaError_t e = launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s);
     if (e == cudaSuccess && (flags & CLAW_ADVANCE_PUSH_GHOSTS) && d.ncopy) {
-        e = launch_fill_copy(d.copies, d.copy_start, d.nboxes, q_new, s);
+        e = launch_fill_copy(d.copies, d.copy_start, d.ncopy_blocks, q_new, s);
         ctx->launches += 1;
     }
     return cuda_rc(e);

@@ -12,11 +12,11 @@ namespace claw {
 static inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------------------ same-level copy
-// One block per destination box; the rectangles of box b are [start[b], start[b+1]).  A box
-// has a few to a few tens of rectangles of a few hundred elements in all, so the block stages
-// a chunk of rectangles in shared memory with the running element count, and every thread
-// takes kCopyBatch elements of the flattened chunk with all loads issued before the stores
-// (the copy is latency-bound: one dependent load-store pair per thread would leave HBM idle).
+// Block k copies the rectangles [start[k], start[k+1]) (the host groups consecutive
+// rectangles, at most 32 rows each, into blocks of about a thousand cells).  The block stages
+// its rectangles in shared memory with the running element count, and every thread takes
+// kCopyBatch elements of the flattened range with all loads issued before the stores (the
+// copy is latency-bound: one dependent load-store pair per thread would leave HBM idle).
 constexpr int kCopyThreads = 128;
 constexpr int kCopyChunk = 32;
 constexpr int kCopyBatch = 8;
@@ -124,18 +124,18 @@ __global__ void __launch_bounds__(kCopyThreads) fill_copy_adjoint_kernel(const C
     }
 }
 
-cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nboxes, double* q, cudaStream_t s, int ncomp)
+cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nblocks, double* q, cudaStream_t s, int ncomp)
 {
-    if (nboxes <= 0) return cudaSuccess;
-    fill_copy_kernel<<<nboxes, kCopyThreads, 0, s>>>(r, start, q, ncomp);
+    if (nblocks <= 0) return cudaSuccess;
+    fill_copy_kernel<<<nblocks, kCopyThreads, 0, s>>>(r, start, q, ncomp);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill_copy_adjoint(const CopyRect* r, const int* start, int nboxes, double* lam, cudaStream_t s,
+cudaError_t launch_fill_copy_adjoint(const CopyRect* r, const int* start, int nblocks, double* lam, cudaStream_t s,
                                      int ncomp)
 {
-    if (nboxes <= 0) return cudaSuccess;
-    fill_copy_adjoint_kernel<<<nboxes, kCopyThreads, 0, s>>>(r, start, lam, ncomp);
+    if (nblocks <= 0) return cudaSuccess;
+    fill_copy_adjoint_kernel<<<nblocks, kCopyThreads, 0, s>>>(r, start, lam, ncomp);
     return cudaGetLastError();
 }
 
@@ -288,12 +288,14 @@ __global__ void medium_aux_kernel(const PatchDev* __restrict__ patches, const do
 {
     const PatchDev P = patches[blockIdx.x];
     const int W = P.nx + 4, H = P.ny + 4;
+    const int j0 = blockIdx.y * kBoxRows, j1 = min(H, j0 + kBoxRows);
+    if (j0 >= H) return;
     const long long WH = (long long)W * H;
     const long long co = P.aoff / CLAW_NAUX;
     const double* r = rho + co;
     const double* k = K + co;
     double* a = aux + P.aoff;
-    for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
+    for (int e = j0 * W + threadIdx.x; e < j1 * W; e += blockDim.x) {
         const int j = e / W, i = e - j * W;
         const double z = sqrt(k[e] * r[e]), c = sqrt(k[e] / r[e]);
         a[AUX_Z * WH + e] = z;
@@ -333,12 +335,14 @@ __global__ void medium_aux_adjoint_kernel(const PatchDev* __restrict__ patches, 
 {
     const PatchDev P = patches[blockIdx.x];
     const int W = P.nx + 4, H = P.ny + 4;
+    const int j0 = blockIdx.y * kBoxRows, j1 = min(H, j0 + kBoxRows);
+    if (j0 >= H) return;
     const long long WH = (long long)W * H;
     const long long co = P.aoff / CLAW_NAUX;
     const double* r = rho + co;
     const double* k = K + co;
     const double* g = ga + P.aoff;
-    for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
+    for (int e = j0 * W + threadIdx.x; e < j1 * W; e += blockDim.x) {
         const int j = e / W, i = e - j * W;
         const double z = sqrt(k[e] * r[e]), c = sqrt(k[e] / r[e]);
         // dZ/dK = Z/(2K), dZ/drho = Z/(2 rho), dc/dK = c/(2K), dc/drho = -c/(2 rho)
@@ -372,38 +376,45 @@ __global__ void medium_aux_adjoint_kernel(const PatchDev* __restrict__ patches, 
     }
 }
 
-cudaError_t launch_medium_aux(const PatchDev* p, int n, const double* rho, const double* K, double* aux,
-                              long long, cudaStream_t s)
+static inline dim3 box_rows_grid(int n, int max_rows)
+{
+    return dim3((unsigned)n, (unsigned)((max_rows + kBoxRows - 1) / kBoxRows));
+}
+
+cudaError_t launch_medium_aux(const PatchDev* p, int n, int max_rows, const double* rho, const double* K,
+                              double* aux, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    medium_aux_kernel<<<n, 256, 0, s>>>(p, rho, K, aux);
+    medium_aux_kernel<<<box_rows_grid(n, max_rows), 128, 0, s>>>(p, rho, K, aux);
     return cudaGetLastError();
 }
 
-cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, const double* rho, const double* K,
+cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, int max_rows, const double* rho, const double* K,
                                       const double* g_aux, double* g_rho, double* g_K, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    medium_aux_adjoint_kernel<<<n, 256, 0, s>>>(p, rho, K, g_aux, g_rho, g_K);
+    medium_aux_adjoint_kernel<<<box_rows_grid(n, max_rows), 128, 0, s>>>(p, rho, K, g_aux, g_rho, g_K);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------ CFL
-// block per box: max c over the ring [-1, nx] x [-1, ny] (integer max of the bit patterns),
-// one 64-bit atomic max per box on the run's scalar (zeroed by the host before the launch)
+// block per (box, chunk of rows): max c over the ring [-1, nx] x [-1, ny] (integer max of the
+// bit patterns), one 64-bit atomic max per warp on the run's scalar (zeroed by the host first)
 __global__ void cfl_max_kernel(const PatchDev* __restrict__ patches, int medium, double c0,
                                const double* __restrict__ aux, unsigned long long* __restrict__ smax)
 {
     const PatchDev P = patches[blockIdx.x];
     unsigned long long m = 0ull;
+    const int r0 = blockIdx.y * kBoxRows, r1 = min(P.ny + 2, r0 + kBoxRows);   // ring rows, from -1
+    if (r0 >= P.ny + 2) return;
     if (medium == 0) {
         m = (unsigned long long)__double_as_longlong(c0);
     } else {
         const int W = P.nx + 4;
         const double* c = aux + P.aoff + AUX_C * (long long)W * (P.ny + 4);
-        const int w = P.nx + 2, n = w * (P.ny + 2);
+        const int w = P.nx + 2, n = w * (r1 - r0);
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int r = k / w, i = k - r * w;
+            const int r = r0 + k / w, i = k % w;
             const unsigned long long v = (unsigned long long)__double_as_longlong(c[(r + 1) * W + (i + 1)]);
             m = v > m ? v : m;
         }
@@ -416,11 +427,12 @@ __global__ void cfl_max_kernel(const PatchDev* __restrict__ patches, int medium,
     if ((threadIdx.x & 31) == 0 && m) atomicMax(smax + P.run, m);
 }
 
-cudaError_t launch_cfl_max(const PatchDev* p, int n, int medium, double c0, const double* aux, double* smax,
-                           cudaStream_t s)
+cudaError_t launch_cfl_max(const PatchDev* p, int n, int max_rows, int medium, double c0, const double* aux,
+                           double* smax, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    cfl_max_kernel<<<n, 128, 0, s>>>(p, medium, c0, aux, reinterpret_cast<unsigned long long*>(smax));
+    cfl_max_kernel<<<box_rows_grid(n, max_rows), 128, 0, s>>>(p, medium, c0, aux,
+                                                            reinterpret_cast<unsigned long long*>(smax));
     return cudaGetLastError();
 }
 

@@ -92,8 +92,10 @@ struct LevelDev {
     AvgRect* avgs = nullptr;
     void* tmaps = nullptr;   // CUtensorMap per box (128 B each), built for the current tiling
     int tmap_tx = 0, tmap_ty = 0;
-    int* copy_start = nullptr;    // [nboxes + 1]: the copy rectangles of box b are [start[b], start[b+1])
+    int* copy_start = nullptr;    // [ncopy_blocks + 1]: block k copies rectangles [start[k], start[k+1])
     int* ccopy_start = nullptr;
+    int ncopy_blocks = 0, nccopy_blocks = 0;
+    int max_rows = 0;             // largest (ny + 4) of the level's boxes
     // host copies
     std::vector<claw_box> boxes;
     std::vector<PatchDev> hpatches;
@@ -135,11 +137,11 @@ cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double
 int adjoint_tile();   // the adjoint kernel's square tile edge
 
 // launchers (claw_ghost.cu)
-cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nboxes, double* q, cudaStream_t s,
+cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nblocks, double* q, cudaStream_t s,
                              int ncomp = 3);
 cudaError_t launch_fill_interp(const InterpCell* c, int n, double* q, const double* cold,
                                const double* cnew, double tau, cudaStream_t s);
-cudaError_t launch_fill_copy_adjoint(const CopyRect* r, const int* start, int nboxes, double* lam, cudaStream_t s,
+cudaError_t launch_fill_copy_adjoint(const CopyRect* r, const int* start, int nblocks, double* lam, cudaStream_t s,
                                      int ncomp = 3);
 cudaError_t launch_fill_interp_adjoint(const InterpCell* c, int n, double* lam, double* lco,
                                        double* lcn, const double* cold, const double* cnew,
@@ -148,12 +150,15 @@ cudaError_t launch_average(const AvgRect* r, int n, int ratio, const double* qf,
                            cudaStream_t s);
 cudaError_t launch_average_adjoint(const AvgRect* r, int n, int ratio, double* lf, double* lc,
                                    cudaStream_t s);
-cudaError_t launch_medium_aux(const PatchDev* p, int n, const double* rho, const double* K,
-                              double* aux, long long cstride_unused, cudaStream_t s);
-cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, const double* rho,
+// box-wise kernels: blockIdx.x = box, blockIdx.y = a chunk of kBoxRows rows (max_rows: the
+// largest padded height of the boxes, so every row of every box has a block)
+constexpr int kBoxRows = 16;
+cudaError_t launch_medium_aux(const PatchDev* p, int n, int max_rows, const double* rho, const double* K,
+                              double* aux, cudaStream_t s);
+cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, int max_rows, const double* rho,
                                       const double* K, const double* g_aux, double* g_rho,
                                       double* g_K, cudaStream_t s);
-cudaError_t launch_cfl_max(const PatchDev* p, int n, int medium, double c0, const double* aux,
+cudaError_t launch_cfl_max(const PatchDev* p, int n, int max_rows, int medium, double c0, const double* aux,
                            double* smax, cudaStream_t s);
 cudaError_t launch_dt_update(const double* minh, const double* cfl, int nruns, double* smax,
                              double* dt, int* err, cudaStream_t s);
