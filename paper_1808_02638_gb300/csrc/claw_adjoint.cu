@@ -6,8 +6,10 @@
 // branch, then walks the phases backwards:
 //   update -> transverse fluxes -> per-cell terms -> edge gathers -> limiter / correction ->
 //   normal Riemann -> q_old and the medium planes.
-// Each reverse phase is a gather where it can be (every adjoint written by one thread);
-// accumulations that two threads share use shared-memory atomics, and contributions to cells
+// Each reverse phase is a gather where it can be (every adjoint written by one thread): the
+// wave-strength and state adjoints are stored per edge and summed per cell by the thread of
+// the cell (a shared-memory FP64 atomic costs an FP64-pipe slot on this part, like a DFMA);
+// only the medium adjoint accumulates with shared-memory atomics.  Contributions to cells
 // shared with neighbouring tiles (the two ghost layers) reach lam_old / g_aux through global
 // FP64 atomics.  The medium adjoint is kept for the Z, c and K planes only: the chain rule
 // through c^2 and through the edge planes (1/(Z_L+Z_R) and the limiter projection factors,
@@ -109,16 +111,16 @@ struct AGeo {
     static constexpr int FN = (ATX + 1) * ATY, GN = ATX * (ATY + 1);
     // shared-memory carve (doubles)
     static constexpr int O_Q = 0;                       // p, u, v
-    static constexpr int O_QB = O_Q + 3 * QPL;          // adjoint of p, u, v
-    static constexpr int O_A1 = O_QB + 3 * QPL;
+    static constexpr int O_A1 = O_Q + 3 * QPL;
     static constexpr int O_A2 = O_A1 + XE;
     static constexpr int O_B1 = O_A2 + XE;
     static constexpr int O_B2 = O_B1 + YE;
-    static constexpr int O_A1B = O_B2 + YE;
-    static constexpr int O_A2B = O_A1B + XE;
+    static constexpr int O_A1B = O_B2 + YE;             // wave-strength adjoints, then the per-edge
+    static constexpr int O_A2B = O_A1B + XE;            // state adjoints of the normal solver
     static constexpr int O_B1B = O_A2B + XE;
     static constexpr int O_B2B = O_B1B + YE;
-    static constexpr int O_M1X = O_B2B + YE;            // limited strengths
+    static constexpr int O_M1X = O_B2B + YE;            // limited strengths, then the limiter's
+                                                        // contributions to the upwind edge's adjoint
     static constexpr int O_M2X = O_M1X + XL;
     static constexpr int O_M1Y = O_M2X + XL;
     static constexpr int O_M2Y = O_M1Y + YL;
@@ -156,9 +158,6 @@ __global__ void __launch_bounds__(ANT, 2)
     double* sp = sm + G::O_Q;
     double* su = sp + G::QPL;
     double* sv = su + G::QPL;
-    double* pb = sm + G::O_QB;
-    double* ub = pb + G::QPL;
-    double* vb = ub + G::QPL;
     double* A1 = sm + G::O_A1;
     double* A2 = sm + G::O_A2;
     double* B1 = sm + G::O_B1;
@@ -254,9 +253,9 @@ __global__ void __launch_bounds__(ANT, 2)
                 double v = 0.0;
                 if (ii < tx + 4 && jj < ty + 4) v = __ldg(src + m * WH + (long long)(y0 + jj) * W + (x0 + ii));
                 sm[G::O_Q + k] = v;
-                sm[G::O_QB + k] = 0.0;
             }
-            for (int k = tid; k < G::O_MED - G::O_A1B; k += ANT) sm[G::O_A1B + k] = 0.0;
+            // accumulators only: every other work array is written before it is read
+            for (int k = tid; k < G::O_M1X - G::O_A1B; k += ANT) sm[G::O_A1B + k] = 0.0;
             if (MED)
                 for (int k = tid; k < G::NMED * G::QPL; k += ANT) medb[k] = 0.0;
         }
@@ -332,12 +331,6 @@ __global__ void __launch_bounds__(ANT, 2)
             if (c < 0 || c >= tx || r < 0 || r >= ty) return 0.0;
             return __ldg(ln + m * WH + (long long)(y0 + r + 2) * W + (x0 + c + 2));
         };
-        for (int k = tid; k < tx * ty; k += ANT) {
-            const int r = k / tx, c = k % tx;
-            pb[CI(c, r)] += LAM(0, c, r);
-            ub[CI(c, r)] += LAM(1, c, r);
-            vb[CI(c, r)] += LAM(2, c, r);
-        }
         if (trans) {
             for (int k = tid; k < ty * (tx + 1); k += ANT) {   // x-edge a of row r
                 const int r = k / (tx + 1), a = k % (tx + 1);
@@ -533,14 +526,18 @@ __global__ void __launch_bounds__(ANT, 2)
                 const double f1 = AX(AUX_FX1, a, r), f2 = AX(AUX_FX2, a, r);
                 const double up1 = A1[XE(a + 1, r)], up2 = A2[XE(a - 1, r)];
                 double da, db;
+                // own edge: plain update (only this thread touches the slot here); the upwind
+                // edge's share goes to this edge's M slot (read above, dead now) for a gather
                 LimD<LIM>::f(A1[XE(a, r)], up1 * f1, da, db);
-                atomicAdd(&A1b[XE(a, r)], da * gm1);
-                atomicAdd(&A1b[XE(a + 1, r)], f1 * db * gm1);
-                const double gf1 = up1 * db * gm1;
+                A1b[XE(a, r)] += da * gm1;
+                const double dg1 = db * gm1;
+                M1x[XL(a, r)] = f1 * dg1;        // to A1b of edge a+1
+                const double gf1 = up1 * dg1;
                 LimD<LIM>::f(A2[XE(a, r)], up2 * f2, da, db);
-                atomicAdd(&A2b[XE(a, r)], da * gm2);
-                atomicAdd(&A2b[XE(a - 1, r)], f2 * db * gm2);
-                const double gf2 = up2 * db * gm2;
+                A2b[XE(a, r)] += da * gm2;
+                const double dg2 = db * gm2;
+                M2x[XL(a, r)] = f2 * dg2;        // to A2b of edge a-1
+                const double gf2 = up2 * dg2;
                 if (MED) {
                     double gzl, gzr;
                     proj_adj(zl, zr, AX(AUX_IZ, a - 1, r), AX(AUX_IZ, a, r), f1, f2, gf1, gf2, gzl, gzr);
@@ -566,13 +563,15 @@ __global__ void __launch_bounds__(ANT, 2)
                 const double up1 = B1[YE(c, b + 1)], up2 = B2[YE(c, b - 1)];
                 double da, db;
                 LimD<LIM>::f(B1[YE(c, b)], up1 * f1, da, db);
-                atomicAdd(&B1b[YE(c, b)], da * gm1);
-                atomicAdd(&B1b[YE(c, b + 1)], f1 * db * gm1);
-                const double gf1 = up1 * db * gm1;
+                B1b[YE(c, b)] += da * gm1;
+                const double dg1 = db * gm1;
+                M1y[YL(c, b)] = f1 * dg1;        // to B1b of edge b+1
+                const double gf1 = up1 * dg1;
                 LimD<LIM>::f(B2[YE(c, b)], up2 * f2, da, db);
-                atomicAdd(&B2b[YE(c, b)], da * gm2);
-                atomicAdd(&B2b[YE(c, b - 1)], f2 * db * gm2);
-                const double gf2 = up2 * db * gm2;
+                B2b[YE(c, b)] += da * gm2;
+                const double dg2 = db * gm2;
+                M2y[YL(c, b)] = f2 * dg2;        // to B2b of edge b-1
+                const double gf2 = up2 * dg2;
                 if (MED) {
                     double gzl, gzr;
                     proj_adj(zl, zr, AX(AUX_IZ, c, b - 1), AX(AUX_IZ, c, b), f1, f2, gf1, gf2, gzl, gzr);
@@ -585,20 +584,27 @@ __global__ void __launch_bounds__(ANT, 2)
 
         // ---------------------------------------------------------------- reverse: normal Riemann
         // a1 = (Z_R du - dp) is, a2 = (Z_L du + dp) is
+        // per edge: the adjoints of dp and du, stored in the edge's A1b / A2b slots for the
+        // per-cell gather below
         for (int k = tid; k < (ty + 2) * (tx + 3); k += ANT) {
             const int r = k / (tx + 3) - 1, a = k % (tx + 3) - 1;
-            const double g1 = A1b[XE(a, r)], g2 = A2b[XE(a, r)];
-            if (g1 == 0.0 && g2 == 0.0) continue;
+            double g1 = A1b[XE(a, r)], g2 = A2b[XE(a, r)];
+            if (second) {
+                if (a >= 1) g1 += M1x[XL(a - 1, r)];
+                if (a <= tx - 1) g2 += M2x[XL(a + 1, r)];
+            }
+            if (g1 == 0.0 && g2 == 0.0) {
+                A1b[XE(a, r)] = 0.0;
+                A2b[XE(a, r)] = 0.0;
+                continue;
+            }
             const int iR = CI(a, r);
             const double dp = sp[iR] - sp[iR - 1], du = su[iR] - su[iR - 1];
             const double zr = AX(AUX_Z, a, r), zl = AX(AUX_Z, a - 1, r), is = AX(AUX_IXS, a, r);
             const double n1 = fma(zr, du, -dp), n2 = fma(zl, du, dp);
             const double gn1 = is * g1, gn2 = is * g2;
-            const double gdp = gn2 - gn1, gdu = fma(zr, gn1, zl * gn2);
-            atomicAdd(&pb[iR], gdp);
-            atomicAdd(&pb[iR - 1], -gdp);
-            atomicAdd(&ub[iR], gdu);
-            atomicAdd(&ub[iR - 1], -gdu);
+            A1b[XE(a, r)] = gn2 - gn1;              // adjoint of dp = p_a - p_{a-1}
+            A2b[XE(a, r)] = fma(zr, gn1, zl * gn2); // adjoint of du
             if (MED) {   // is = 1/(Z_L + Z_R): d is / dZ = -is^2 for both cells
                 const double gs = -is * is * fma(n1, g1, n2 * g2);
                 medadd(AUX_Z, a, r, fma(du, gn1, gs));
@@ -607,18 +613,23 @@ __global__ void __launch_bounds__(ANT, 2)
         }
         for (int k = tid; k < (ty + 3) * (tx + 2); k += ANT) {
             const int b = k / (tx + 2) - 1, c = k % (tx + 2) - 1;
-            const double g1 = B1b[YE(c, b)], g2 = B2b[YE(c, b)];
-            if (g1 == 0.0 && g2 == 0.0) continue;
+            double g1 = B1b[YE(c, b)], g2 = B2b[YE(c, b)];
+            if (second) {
+                if (b >= 1) g1 += M1y[YL(c, b - 1)];
+                if (b <= ty - 1) g2 += M2y[YL(c, b + 1)];
+            }
+            if (g1 == 0.0 && g2 == 0.0) {
+                B1b[YE(c, b)] = 0.0;
+                B2b[YE(c, b)] = 0.0;
+                continue;
+            }
             const int iR = CI(c, b);
             const double dp = sp[iR] - sp[iR - G::SW], dv = sv[iR] - sv[iR - G::SW];
             const double zr = AX(AUX_Z, c, b), zl = AX(AUX_Z, c, b - 1), is = AX(AUX_IYS, c, b);
             const double n1 = fma(zr, dv, -dp), n2 = fma(zl, dv, dp);
             const double gn1 = is * g1, gn2 = is * g2;
-            const double gdp = gn2 - gn1, gdv = fma(zr, gn1, zl * gn2);
-            atomicAdd(&pb[iR], gdp);
-            atomicAdd(&pb[iR - G::SW], -gdp);
-            atomicAdd(&vb[iR], gdv);
-            atomicAdd(&vb[iR - G::SW], -gdv);
+            B1b[YE(c, b)] = gn2 - gn1;
+            B2b[YE(c, b)] = fma(zr, gn1, zl * gn2);
             if (MED) {
                 const double gs = -is * is * fma(n1, g1, n2 * g2);
                 medadd(AUX_Z, c, b, fma(dv, gn1, gs));
@@ -629,21 +640,36 @@ __global__ void __launch_bounds__(ANT, 2)
 
         // ---------------------------------------------------------------- flush to global
         {
+            // cell (i, j) of the staged block, i in [-2, tx+1], j in [-2, ty+1]: it is the right
+            // cell of x-edge i and the left cell of x-edge i+1 (edges a in [-1, tx+1] on rows
+            // [-1, ty]), likewise for the y-edges (b in [-1, ty+1] on columns [-1, tx])
             double* lo = lam_old + P.qoff;
-            for (int k = tid; k < 3 * G::QPL; k += ANT) {
-                const int m = k / G::QPL, rem = k - m * G::QPL;
-                const int jj = rem / G::SW, ii = rem - jj * G::SW;
-                if (ii >= tx + 4 || jj >= ty + 4) continue;
-                const double v = sm[G::O_QB + k];
-                if (v != 0.0) atomicAdd(lo + m * WH + (long long)(y0 + jj) * W + (x0 + ii), v);
+            const int w4 = tx + 4, n4 = w4 * (ty + 4);
+            auto gx = [&](const double* arr, int a, int r) -> double {
+                return (a >= -1 && a <= tx + 1 && r >= -1 && r <= ty) ? arr[XE(a, r)] : 0.0;
+            };
+            auto gy = [&](const double* arr, int c, int b) -> double {
+                return (b >= -1 && b <= ty + 1 && c >= -1 && c <= tx) ? arr[YE(c, b)] : 0.0;
+            };
+            for (int k = tid; k < n4; k += ANT) {
+                const int j = k / w4 - 2, i = k % w4 - 2;
+                double p = gx(A1b, i, j) - gx(A1b, i + 1, j) + gy(B1b, i, j) - gy(B1b, i, j + 1);
+                double u = gx(A2b, i, j) - gx(A2b, i + 1, j);
+                double v = gy(B2b, i, j) - gy(B2b, i, j + 1);
+                p += LAM(0, i, j);
+                u += LAM(1, i, j);
+                v += LAM(2, i, j);
+                const long long o = (long long)(y0 + j + 2) * W + (x0 + i + 2);
+                if (p != 0.0) atomicAdd(lo + o, p);
+                if (u != 0.0) atomicAdd(lo + WH + o, u);
+                if (v != 0.0) atomicAdd(lo + 2 * WH + o, v);
             }
             if (MED && g_aux) {
                 double* ga = g_aux + P.aoff;
-                for (int k = tid; k < G::NMED * G::QPL; k += ANT) {
-                    const int m = k / G::QPL, rem = k - m * G::QPL;
-                    const int jj = rem / G::SW, ii = rem - jj * G::SW;
-                    if (ii >= tx + 4 || jj >= ty + 4) continue;
-                    const double v = medb[k];
+                for (int k = tid; k < G::NMED * n4; k += ANT) {
+                    const int m = k / n4, rem = k - m * n4;
+                    const int jj = rem / w4, ii = rem - jj * w4;
+                    const double v = medb[m * G::QPL + jj * G::SW + ii];
                     if (v != 0.0) atomicAdd(ga + m * WH + (long long)(y0 + jj) * W + (x0 + ii), v);
                 }
             }

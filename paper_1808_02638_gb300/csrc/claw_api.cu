@@ -247,7 +247,7 @@ struct GhostEntry {
 
 // ghost tasks of one level: copy rectangles and interpolated cells
 constexpr int kRectRows = 32;          // copy rectangles are split into pieces of at most this many rows
-constexpr long long kBlockCells = 1024;  // cells per block of the copy kernel (about)
+constexpr long long kBlockCells = 256;   // cells per block of the copy kernel (about): one batch per thread
 
 int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::vector<InterpCell>& cells,
                        std::vector<int>& start)

@@ -13,7 +13,7 @@ static inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------------------ same-level copy
 // Block k copies the rectangles [start[k], start[k+1]) (the host groups consecutive
-// rectangles, at most 32 rows each, into blocks of about a thousand cells).  The block stages
+// rectangles, at most 32 rows each, into blocks of about 256 cells).  The block stages
 // its rectangles in shared memory with the running element count, and every thread takes
 // kCopyBatch elements of the flattened range with all loads issued before the stores (the
 // copy is latency-bound: one dependent load-store pair per thread would leave HBM idle).
