@@ -43,7 +43,7 @@ extern "C" {
 
 #define CLAW_MBC 2
 #define CLAW_MAXLEV 8
-#define CLAW_NAUX 11
+#define CLAW_NAUX 10
 
 /* limiter ids: phi(theta) of the waves (Sec. 2.1; the benchmark of Sec. 4.1 uses van Leer) */
 #define CLAW_LIM_NONE 0
@@ -110,9 +110,8 @@ int claw_set_tiling(claw_ctx* ctx, int32_t level, int32_t tx, int32_t ty, int32_
 
 /* Per-cell coefficient planes for medium = 1 from one-plane pools rho, K (ghosts included):
  * aux holds, for every cell, Z = sqrt(K rho), c = sqrt(K/rho), K, c^2, 1/(Z_W+Z) and the
- * two wave-limiter projection factors of the edge to the west, the same three for the edge
- * to the south, and 1/(Z^2+1) (used by the reverse mode).  Enqueued on `stream`.
- * Errors: CLAW_EINVAL, CLAW_ECUDA. */
+ * two wave-limiter projection factors of the edge to the west, and the same three for the
+ * edge to the south.  Enqueued on `stream`.  Errors: CLAW_EINVAL, CLAW_ECUDA. */
 int claw_medium_aux(claw_ctx* ctx, int32_t level, const double* rho, const double* K, double* aux,
                     void* stream);
 
@@ -203,10 +202,10 @@ int claw_average_down(claw_ctx* ctx, int32_t fine_level, const double* q_fine, d
 /* Reverse mode of claw_level_step for a frozen dt (dt as in claw_level_step): given
  * lam_new, the adjoint of q_new (interior cells read), accumulates (+=) the adjoint of q_old
  * over all cells, ghosts included, into lam_old and the adjoint of the medium into g_aux
- * (medium = 1; may be NULL for medium = 0).  g_aux has the aux layout; the chain rule through
- * the derived planes (c^2, the edge planes) is applied here, so only the Z, c and K planes of
- * g_aux receive contributions (the others are left as they are).  The limiter branches of
- * the forward step are recomputed from q_old.  lam_old and g_aux must be zeroed by the caller
+ * (medium = 1; may be NULL for medium = 0).  g_aux has the aux layout; the c^2 plane's
+ * adjoint is folded into the c plane here (that plane of g_aux is left as it is), every other
+ * plane receives its own adjoint.  The limiter branches of the forward step are recomputed
+ * from q_old.  lam_old and g_aux must be zeroed by the caller
  * before the first accumulation. */
 int claw_level_step_adjoint(claw_ctx* ctx, int32_t level, const double* q_old, const double* lam_new,
                             double* lam_old, const double* aux, double* g_aux, const double* dt,

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libclaw.so")
 CLAW_OK, CLAW_EINVAL, CLAW_ECUDA, CLAW_ENOMEM, CLAW_ECFL, CLAW_ENAN, CLAW_ETIMEOUT, CLAW_ESTATE = range(8)
 CLAW_MBC = 2
 CLAW_MAXLEV = 8
-CLAW_NAUX = 11
+CLAW_NAUX = 10
 LIMITERS = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
 
 

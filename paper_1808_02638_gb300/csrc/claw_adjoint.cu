@@ -9,13 +9,13 @@
 // Each reverse phase is a gather where it can be (every adjoint written by one thread): the
 // wave-strength and state adjoints are stored per edge and summed per cell by the thread of
 // the cell (a shared-memory FP64 atomic costs an FP64-pipe slot on this part, like a DFMA);
-// only the medium adjoint accumulates with shared-memory atomics.  Contributions to cells
-// shared with neighbouring tiles (the two ghost layers) reach lam_old / g_aux through global
-// FP64 atomics.  The medium adjoint is kept for the Z, c and K planes only: the chain rule
-// through c^2 and through the edge planes (1/(Z_L+Z_R) and the limiter projection factors,
-// functions of the two cells' Z) is applied where those planes are read, which keeps the
-// tile's shared memory small enough for two CTAs per SM.  A uniform medium runs the same code
-// with constant medium planes and no medium adjoint.
+// only the per-cell medium adjoint (Z, c, K) accumulates with shared-memory atomics.  The
+// adjoints of the per-edge planes (1/(Z_L+Z_R) and the limiter projection factors) are owned
+// by the edge's thread and go to g_aux with global FP64 atomics; their chain rule to Z runs
+// once per gradient in claw_medium_aux_adjoint, not once per step.  The c^2 plane is folded
+// into c where it is read.  Contributions to cells shared with neighbouring tiles (the two
+// ghost layers) reach lam_old / g_aux through global FP64 atomics.  A uniform medium runs the
+// same code with constant medium planes and no medium adjoint.
 #include <cuda_runtime.h>
 
 #include "claw_step.cuh"
@@ -221,7 +221,6 @@ __global__ void __launch_bounds__(ANT, 2)
             case AUX_K: return A.K0;
             case AUX_C2: return c0 * c0;
             case AUX_IXS: case AUX_IYS: return iZs;
-            case AUX_IZ: return 1.0 / fma(Z0, Z0, 1.0);
             default: return 1.0;
             }
         };
@@ -235,13 +234,10 @@ __global__ void __launch_bounds__(ANT, 2)
         auto medadd = [&](int k, int i, int j, double v) {   // k: AUX_Z, AUX_C or AUX_K
             if (MED) atomicAdd(&medb[k * G::QPL + CI(i, j)], v);
         };
-        // adjoint of the projection factors of an edge (Z_L of the west / south cell, Z_R of
-        // the east / north cell): f1 = (Z_L Z_R + 1) iz_L, f2 = (Z_L Z_R + 1) iz_R with
-        // iz = 1 / (Z^2 + 1); returns the Z_L and Z_R adjoints
-        auto proj_adj = [&](double zl, double zr, double izl, double izr, double f1, double f2, double g1,
-                            double g2, double& gzl, double& gzr) {
-            gzl = izl * fma(-2.0 * zl, f1, zr) * g1 + zr * izr * g2;
-            gzr = zl * izl * g1 + izr * fma(-2.0 * zr, f2, zl) * g2;
+        // adjoint of an edge plane k (held at the edge's east / north cell (i, j)): global atomic
+        double* gedge = (MED && g_aux) ? g_aux + P.aoff : nullptr;
+        auto edgeadd = [&](int k, int i, int j, double v) {
+            if (MED && v != 0.0) atomicAdd(gedge + k * WH + (long long)(y0 + j + 2) * W + (x0 + i + 2), v);
         };
 
         // ---------------------------------------------------------------- stage, clear
@@ -373,10 +369,7 @@ __global__ void __launch_bounds__(ANT, 2)
                     medadd(AUX_K, c, r, wG * dlo * gp);
                     medadd(AUX_C, c, r, wG * dlo * gv);
                     const double gpf = fma(Kc, dlo, -(klo * dme)), gvf = fma(cc, dlo, clo * dme);
-                    // iys = 1/(Z_lo + Z_hi): d iys / dZ = -iys^2 for both cells
-                    const double gz = -is * is * (-0.5 * lx * (gpf * gp + gvf * gv));
-                    medadd(AUX_Z, c, r - 1, gz);
-                    medadd(AUX_Z, c, r, gz);
+                    edgeadd(AUX_IYS, c, r, -0.5 * lx * fma(gpf, gp, gvf * gv));
                 }
                 Db[DI(c, r)] = acc;
             }
@@ -404,9 +397,7 @@ __global__ void __launch_bounds__(ANT, 2)
                     medadd(AUX_K, c, r, wF * elo * fp);
                     medadd(AUX_C, c, r, wF * elo * fu);
                     const double fpf = fma(Kc, elo, -(klo * eme)), fuf = fma(cc, elo, clo * eme);
-                    const double gz = -is * is * (-0.5 * ly * (fpf * fp + fuf * fu));
-                    medadd(AUX_Z, c - 1, r, gz);
-                    medadd(AUX_Z, c, r, gz);
+                    edgeadd(AUX_IXS, c, r, -0.5 * ly * fma(fpf, fp, fuf * fu));
                 }
                 Eb[EI(c, r)] = acc;
             }
@@ -539,10 +530,10 @@ __global__ void __launch_bounds__(ANT, 2)
                 M2x[XL(a, r)] = f2 * dg2;        // to A2b of edge a-1
                 const double gf2 = up2 * dg2;
                 if (MED) {
-                    double gzl, gzr;
-                    proj_adj(zl, zr, AX(AUX_IZ, a - 1, r), AX(AUX_IZ, a, r), f1, f2, gf1, gf2, gzl, gzr);
-                    medadd(AUX_Z, a, r, fma(kr * m2, gcp, gzr));
-                    medadd(AUX_Z, a - 1, r, fma(-(kl * m1), gcp, gzl));
+                    edgeadd(AUX_FX1, a, r, gf1);
+                    edgeadd(AUX_FX2, a, r, gf2);
+                    medadd(AUX_Z, a, r, kr * m2 * gcp);
+                    medadd(AUX_Z, a - 1, r, -(kl * m1 * gcp));
                 }
             }
             for (int k = tid; k < (ty + 1) * (tx + 2); k += ANT) {
@@ -573,10 +564,10 @@ __global__ void __launch_bounds__(ANT, 2)
                 M2y[YL(c, b)] = f2 * dg2;        // to B2b of edge b-1
                 const double gf2 = up2 * dg2;
                 if (MED) {
-                    double gzl, gzr;
-                    proj_adj(zl, zr, AX(AUX_IZ, c, b - 1), AX(AUX_IZ, c, b), f1, f2, gf1, gf2, gzl, gzr);
-                    medadd(AUX_Z, c, b, fma(kr * m2, gcp, gzr));
-                    medadd(AUX_Z, c, b - 1, fma(-(kl * m1), gcp, gzl));
+                    edgeadd(AUX_FY1, c, b, gf1);
+                    edgeadd(AUX_FY2, c, b, gf2);
+                    medadd(AUX_Z, c, b, kr * m2 * gcp);
+                    medadd(AUX_Z, c, b - 1, -(kl * m1 * gcp));
                 }
             }
             __syncthreads();
@@ -605,10 +596,10 @@ __global__ void __launch_bounds__(ANT, 2)
             const double gn1 = is * g1, gn2 = is * g2;
             A1b[XE(a, r)] = gn2 - gn1;              // adjoint of dp = p_a - p_{a-1}
             A2b[XE(a, r)] = fma(zr, gn1, zl * gn2); // adjoint of du
-            if (MED) {   // is = 1/(Z_L + Z_R): d is / dZ = -is^2 for both cells
-                const double gs = -is * is * fma(n1, g1, n2 * g2);
-                medadd(AUX_Z, a, r, fma(du, gn1, gs));
-                medadd(AUX_Z, a - 1, r, fma(du, gn2, gs));
+            if (MED) {
+                edgeadd(AUX_IXS, a, r, fma(n1, g1, n2 * g2));
+                medadd(AUX_Z, a, r, du * gn1);
+                medadd(AUX_Z, a - 1, r, du * gn2);
             }
         }
         for (int k = tid; k < (ty + 3) * (tx + 2); k += ANT) {
@@ -631,9 +622,9 @@ __global__ void __launch_bounds__(ANT, 2)
             B1b[YE(c, b)] = gn2 - gn1;
             B2b[YE(c, b)] = fma(zr, gn1, zl * gn2);
             if (MED) {
-                const double gs = -is * is * fma(n1, g1, n2 * g2);
-                medadd(AUX_Z, c, b, fma(dv, gn1, gs));
-                medadd(AUX_Z, c, b - 1, fma(dv, gn2, gs));
+                edgeadd(AUX_IYS, c, b, fma(n1, g1, n2 * g2));
+                medadd(AUX_Z, c, b, dv * gn1);
+                medadd(AUX_Z, c, b - 1, dv * gn2);
             }
         }
         __syncthreads();

@@ -323,7 +323,6 @@ __global__ void medium_aux_kernel(const PatchDev* __restrict__ patches, const do
         a[AUX_IYS * WH + e] = iys;
         a[AUX_FY1 * WH + e] = fy1;
         a[AUX_FY2 * WH + e] = fy2;
-        a[AUX_IZ * WH + e] = 1.0 / fma(z, z, 1.0);
     }
 }
 

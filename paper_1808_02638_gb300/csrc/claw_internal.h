@@ -23,9 +23,8 @@ enum AuxPlane : int {
     AUX_IYS = 7,  // 1 / (Z_{i,j-1} + Z_{i,j})
     AUX_FY1 = 8,
     AUX_FY2 = 9,
-    AUX_IZ = 10,  // 1 / (Z^2 + 1): derivatives of the projection factors (reverse mode)
 };
-static_assert(CLAW_NAUX == 11, "aux plane count");
+static_assert(CLAW_NAUX == 10, "aux plane count");
 
 // One box of a level, as the kernels see it.
 struct PatchDev {
