@@ -322,47 +322,11 @@ def main():
     # per buffer parity two graphs: the persistent level-step launch that advances every patch
     # and applies Eq. cfl on its last CTA, then the copy of the same-level / boundary ghosts of
     # q^{n+1}; events bracket the step graph so the dominant kernel is timed on its own
-    def capture(fn):
-        s = torch.cuda.Stream()
-        s.wait_stream(torch.cuda.current_stream())
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
-            fn(s)
-        torch.cuda.current_stream().wait_stream(s)
-        return g
-
-    flags = claw.CLAW_ADVANCE_UPDATE_DT
-    claw.claw_fill_ghost(ctx, 0, H.q[0][H.cur[0]])
-    c0 = H.cur[0]
-    graphs = []   # graphs[i] reads buffer c0 ^ i and writes the other: (step, ghost fill)
-    for parity in range(2):
-        c = H.cur[0]
-        qa, qb = H.q[0][c], H.q[0][1 - c]
-        # first launch eagerly (descriptor cache, attributes), then capture
-        claw.claw_level_advance(ctx, 0, qa, qb, None, H.dt, H.smax, flags)
-        claw.claw_fill_ghost(ctx, 0, qb)
-        gs = capture(lambda s, qa=qa, qb=qb: claw.claw_level_advance(ctx, 0, qa, qb, None, H.dt, H.smax, flags, s))
-        gf = capture(lambda s, qb=qb: claw.claw_fill_ghost(ctx, 0, qb, None, None, 0.0, s))
-        graphs.append((gs, gf))
-        H.cur[0] ^= 1
-    torch.cuda.synchronize()
-    launches0 = claw.claw_launch_count(ctx)
-    claw.claw_level_advance(ctx, 0, H.q[0][H.cur[0]], H.q[0][1 - H.cur[0]], None, H.dt, H.smax, flags)
-    claw.claw_fill_ghost(ctx, 0, H.q[0][1 - H.cur[0]])
-    per_step_launches = claw.claw_launch_count(ctx) - launches0
-    H.cur[0] ^= 1
+    stepper = H.fused_stepper()
+    per_step_launches = stepper.launches_per_step
 
     def one_step(k, ev=None):
-        gs, gf = graphs[H.cur[0] ^ c0]
-        if ev is not None:
-            ev[0].record()
-        gs.replay()
-        if ev is not None:
-            ev[1].record()
-        gf.replay()
-        if ev is not None:
-            ev[2].record()
-        H.cur[0] ^= 1
+        stepper.step(ev)
 
     for k in range(args.warmup):
         one_step(k)

@@ -186,6 +186,12 @@ class Hierarchy:
             raise ValueError("capture an even number of coarse steps")
         return g
 
+    def fused_stepper(self):
+        """One-level hierarchies: a stepper whose step() replays, for the current buffer parity,
+        a CUDA graph of the persistent level-step (Eq. cfl applied by its last CTA) and then a
+        graph of the ghost copy of q^{n+1} (same-level copies and physical boundaries)."""
+        return FusedStepper(self)
+
     def sync_status(self):
         return claw.claw_sync_status(self.ctx)
 
@@ -219,3 +225,62 @@ class Hierarchy:
             self.close()
         except Exception:
             pass
+
+
+class FusedStepper:
+    """Graphs of one level-step of a one-level hierarchy, one pair per buffer parity.
+
+    step(events) replays the step graph and the ghost-copy graph of the current parity and flips
+    the parity; `events` (three CUDA events, optional) are recorded before the step, between the
+    two graphs and after the copy, on the current stream."""
+
+    def __init__(self, H: Hierarchy):
+        if H.nlev != 1 or H.patchwise:
+            raise ValueError("the fused stepper is for one-level hierarchies on the tiled path")
+        self.H = H
+        ctx = H.ctx
+        flags = claw.CLAW_ADVANCE_UPDATE_DT
+
+        def capture(fn):
+            s = torch.cuda.Stream(device=H.dev)
+            s.wait_stream(torch.cuda.current_stream(H.dev))
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                fn(s)
+            torch.cuda.current_stream(H.dev).wait_stream(s)
+            return g
+
+        claw.claw_fill_ghost(ctx, 0, H.q[0][H.cur[0]])
+        self.c0 = H.cur[0]
+        self.graphs = []   # graphs[i] reads buffer c0 ^ i and writes the other: (step, ghost copy)
+        for _ in range(2):
+            c = H.cur[0]
+            qa, qb = H.q[0][c], H.q[0][1 - c]
+            # one eager launch first (tensor-map cache, kernel attributes), then capture
+            claw.claw_level_advance(ctx, 0, qa, qb, H.aux[0], H.dt, H.smax, flags)
+            claw.claw_fill_ghost(ctx, 0, qb)
+            gs = capture(lambda s, qa=qa, qb=qb: claw.claw_level_advance(ctx, 0, qa, qb, H.aux[0], H.dt, H.smax,
+                                                                          flags, s))
+            gf = capture(lambda s, qb=qb: claw.claw_fill_ghost(ctx, 0, qb, None, None, 0.0, s))
+            self.graphs.append((gs, gf))
+            H.cur[0] ^= 1
+        torch.cuda.synchronize(H.dev)
+        # launches of one step, counted by the library
+        before = claw.claw_launch_count(ctx)
+        claw.claw_level_advance(ctx, 0, H.q[0][H.cur[0]], H.q[0][1 - H.cur[0]], H.aux[0], H.dt, H.smax, flags)
+        claw.claw_fill_ghost(ctx, 0, H.q[0][1 - H.cur[0]])
+        self.launches_per_step = claw.claw_launch_count(ctx) - before
+        H.cur[0] ^= 1
+
+    def step(self, events=None):
+        H = self.H
+        gs, gf = self.graphs[H.cur[0] ^ self.c0]
+        if events is not None:
+            events[0].record()
+        gs.replay()
+        if events is not None:
+            events[1].record()
+        gf.replay()
+        if events is not None:
+            events[2].record()
+        H.cur[0] ^= 1

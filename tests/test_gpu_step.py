@@ -214,6 +214,71 @@ def test_full_size_uniform_batch_sampled_parity_and_symmetry(orc):
     assert H.sync_status() == 0
 
 
+def _tilings():
+    from paper_1808_02638_gb300 import tune
+    return ["tuned"] + [tuple(c) for c in tune.CANDIDATES]
+
+
+@pytest.mark.parametrize("tiling", _tilings())
+def test_full_size_bench_launch_path_sampled_parity(orc, tiling):
+    # the launch path bench.py times, at its full size: 2048^2 as 4096 patches, the tiling the
+    # autotuner picks (or each candidate), CUDA-graph replays of the persistent level-step with
+    # the device Eq. cfl update followed by the ghost-copy graph.  At steps 0, 100 and 199:
+    # sampled patches equal the oracle's one-patch step from the same input, and every ghost of
+    # q^{n+1} equals the edge-extrapolated global field; after 200 steps the symmetries hold.
+    from paper_1808_02638_gb300 import claw, tune
+    from paper_1808_02638_gb300.solver import Hierarchy
+    import torch
+    run = inputs.config1()
+    lev = run.levels[0]
+    q = inputs.init_q(run, lev)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    if tiling == "tuned":
+        tune.tune_level(H, 0, use_cache=False)
+    else:
+        claw.claw_set_tiling(H.ctx, 0, *tiling)
+    H.coarse_step()
+    H.coarse_step()
+    st = H.fused_stepper()
+    assert st.launches_per_step == 2
+    rng = np.random.default_rng(7)
+    sample = rng.choice(len(lev.boxes), 32, replace=False)
+    ones = np.ones((36, 36))
+
+    def glob_of(pool):
+        g = np.zeros((3, 2048, 2048))
+        for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
+            g[:, jlo:jlo + 32, ilo:ilo + 32] = inputs.box_view(pool, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
+        return g
+
+    for step in range(200):
+        check = step in (0, 100, 199)
+        if check:
+            torch.cuda.synchronize()
+            before = H.pool(0).cpu().numpy()
+            dt = float(H.dt[0])
+        st.step()
+        if check:
+            torch.cuda.synchronize()
+            after = H.pool(0).cpu().numpy()
+            scale = np.abs(after).max()
+            for nb in sample:
+                qin = inputs.box_view(before, lev.qoff[nb], 32, 32, 3).copy()
+                want, _ = orc.step(qin, ones, 4 * ones, lev.dx, lev.dy, dt)
+                got = inputs.box_view(after, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
+                assert np.abs(got - want[:, M:-M, M:-M]).max() <= TOL1 * scale
+            gp = np.pad(glob_of(after), ((0, 0), (M, M), (M, M)), mode="edge")
+            for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
+                assert np.array_equal(inputs.box_view(after, lev.qoff[nb], 32, 32, 3),
+                                      gp[:, jlo:jlo + 36, ilo:ilo + 36])
+    p, u, v = glob_of(H.pool(0).cpu().numpy())
+    tol = 1e-12 * max(np.abs(p).max(), 1.0)
+    assert np.abs(p - p.T).max() <= tol and np.abs(p - p[:, ::-1]).max() <= tol
+    assert np.abs(u - v.T).max() <= tol and np.abs(u + u[:, ::-1]).max() <= tol
+    assert H.sync_status() == 0
+
+
 def test_errors_are_status_codes():
     from paper_1808_02638_gb300 import claw
     from paper_1808_02638_gb300.solver import Hierarchy
