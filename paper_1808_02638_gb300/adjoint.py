@@ -1,6 +1,7 @@
 """Differentiable rollouts: gradients of a functional of the final state with respect to the
 initial state and the medium (rho, K), through the hand-written adjoint kernels.
 
+`LevelStep.apply(H, L, dt, q_old, rho, K)` is one level-step of level L as a differentiable map.
 `rollout(H, q0, rho, K, ncoarse, every)` is a torch.autograd.Function over `ncoarse` coarse
 steps of hierarchy H (any number of levels and runs).  The forward keeps a checkpoint of every
 level's state every `every` coarse steps; the backward recomputes one segment at a time from its
@@ -139,6 +140,66 @@ class _Rollout(torch.autograd.Function):
                 g_K.append(gk)
             grads_out += g_rho + g_K
         return tuple(grads_out)
+
+
+def _ghost_mask(H, L):
+    """1.0 on the ghost cells of every box of level L (all planes), 0.0 on interiors and padding"""
+    cache = H.__dict__.setdefault("_ghost_masks", {})
+    if L not in cache:
+        import numpy as np
+        m = np.zeros(H.q[L][0].numel())
+        for (ri, qb, _) in H.layout[L]:
+            lev = H.runs[ri].levels[L]
+            for n, b in enumerate(lev.boxes):
+                nx, ny = int(b[2]), int(b[3])
+                off = qb + int(lev.qoff[n])
+                v = m[off:off + 3 * (nx + 4) * (ny + 4)].reshape(3, ny + 4, nx + 4)
+                v[...] = 1.0
+                v[:, 2:2 + ny, 2:2 + nx] = 0.0
+        cache[L] = torch.from_numpy(m).to(H.q[L][0].device)
+    return cache[L]
+
+
+class LevelStep(torch.autograd.Function):
+    """One level-step of level L of hierarchy H (Eq. wave_form_2d_2nd_order on every box) as a
+    differentiable map (q_old, rho, K) -> q_new with the time step frozen.
+
+    q_old: a q pool of level L with its ghosts filled by the caller; q_new equals q_old on the
+    ghost cells and the stepped values on the interiors.  rho, K (cell-wise medium only): the
+    level's coefficient pools, ghosts included (treated as independent inputs).  dt: device
+    tensor of per-run level-0 time steps.  The backward runs claw_level_step_adjoint (and
+    claw_medium_aux_adjoint for rho, K); ghost cells of q_new pass their adjoint straight back."""
+
+    @staticmethod
+    def forward(ctx, H, L, dt, q_old, rho=None, K=None):
+        aux = None
+        if H.medium:
+            aux = torch.zeros_like(H.aux[L])
+            claw.claw_medium_aux(H.ctx, L, rho, K, aux)
+        q_new = q_old.detach().clone()
+        smax = torch.zeros_like(H.smax)
+        claw.claw_level_step(H.ctx, L, q_old.detach(), q_new, aux, dt, smax)
+        ctx.H, ctx.L = H, L
+        ctx.save_for_backward(q_old.detach(), dt, aux if aux is not None else torch.empty(0),
+                              rho.detach() if rho is not None else torch.empty(0),
+                              K.detach() if K is not None else torch.empty(0))
+        return q_new
+
+    @staticmethod
+    def backward(ctx, lam_new):
+        H, L = ctx.H, ctx.L
+        q_old, dt, aux, rho, K = ctx.saved_tensors
+        lam_new = lam_new.contiguous()
+        lam_old = lam_new * _ghost_mask(H, L)
+        g_rho = g_K = None
+        if H.medium:
+            g_aux = torch.zeros_like(aux)
+            claw.claw_level_step_adjoint(H.ctx, L, q_old, lam_new, lam_old, aux, g_aux, dt)
+            g_rho, g_K = torch.zeros_like(rho), torch.zeros_like(K)
+            claw.claw_medium_aux_adjoint(H.ctx, L, rho, K, g_aux, g_rho, g_K)
+        else:
+            claw.claw_level_step_adjoint(H.ctx, L, q_old, lam_new, lam_old, None, None, dt)
+        return None, None, None, lam_old, g_rho, g_K
 
 
 def rollout(H, q0, rho=None, K=None, ncoarse=1, every=20, dt=None):

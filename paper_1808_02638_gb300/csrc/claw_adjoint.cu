@@ -98,7 +98,7 @@ template <> struct LimD<CLAW_LIM_MC> {
     }
 };
 
-constexpr int ATX = 16, ATY = 16, ANT = 256;
+constexpr int ATX = 16, ATY = 16, ANT = 384;
 
 struct AGeo {
     static constexpr int SW = ATX + 4, SH = ATY + 4, QPL = SW * SH;

@@ -87,6 +87,60 @@ def test_adjoint_matches_oracle_reverse_mode(nlev):
     _compare([t.grad.cpu().numpy() for t in tk], gk, 1e-10)
 
 
+@pytest.mark.parametrize("medium", ["uniform", "cellwise"])
+def test_level_step_function_matches_oracle_step_adjoint(medium):
+    # one level-step as a torch.autograd.Function: the gradient of <w, q_new> (w on interiors)
+    # with respect to q_old (all cells), rho and K equals the oracle's reverse mode of its step
+    import torch
+    import oracle
+    from paper_1808_02638_gb300.adjoint import LevelStep
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = 40
+    run = inputs.Run(*inputs.PULSE_DOMAIN)
+    run.levels = [inputs.Level(n, n, 2 / n, 2 / n, [(0, 0, n, n)])]
+    lev = run.levels[0]
+    q = inputs.init_q(run, lev) + 0.05 * inputs.uniform(41, inputs.init_q(run, lev).size)
+    r2 = inputs.smooth_field(42, n, n, 0.5, 2.0, sigma=3.0)
+    k2 = inputs.smooth_field(43, n, n, 1.0, 8.0, sigma=3.0)
+    rho_p, K_p = inputs.coef_pool(lev, r2, 1), inputs.coef_pool(lev, k2, 1)
+    if medium == "uniform":
+        H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+        rho_p = inputs.const_pool(lev, 1.0)
+        K_p = inputs.const_pool(lev, 4.0)
+    else:
+        H = Hierarchy([run], [[q]], [[rho_p]], [[K_p]])
+    H.init_dt()
+    dt = H.dt.clone()
+    dev = H.q[0][0].device
+    tq = torch.zeros_like(H.q[0][0])
+    tq[:q.size] = torch.from_numpy(q)
+    tq.requires_grad_(True)
+    w = np.zeros_like(q)
+    inputs.box_view(w, 0, n, n, 3)[:, M:-M, M:-M] = inputs.uniform(44, 3 * n * n).reshape(3, n, n) - 0.5
+    tw = torch.zeros_like(tq.detach())
+    tw[:w.size] = torch.from_numpy(w)
+    if medium == "uniform":
+        out = LevelStep.apply(H, 0, dt, tq)
+    else:
+        tr = torch.ones_like(H.rho[0]); tr[:rho_p.size] = torch.from_numpy(rho_p); tr.requires_grad_(True)
+        tk = torch.ones_like(H.K[0]); tk[:K_p.size] = torch.from_numpy(K_p); tk.requires_grad_(True)
+        out = LevelStep.apply(H, 0, dt, tq, tr, tk)
+    (out * tw).sum().backward()
+    qb = inputs.box_view(q, 0, n, n, 3)
+    rb = inputs.box_view(rho_p, 0, n, n, 1)[0]
+    kb = inputs.box_view(K_p, 0, n, n, 1)[0]
+    lb = inputs.box_view(w, 0, n, n, 3)
+    lq, gr, gk = oracle.step_adjoint(qb, rb, kb, lb, lev.dx, lev.dy, float(dt[0]), run.order, run.transverse,
+                                     run.limiter)
+    got = inputs.box_view(tq.grad.cpu().numpy()[:q.size], 0, n, n, 3)
+    assert np.abs(got - lq).max() <= 1e-11 * np.abs(lq).max()
+    if medium == "cellwise":
+        gotr = inputs.box_view(tr.grad.cpu().numpy()[:rho_p.size], 0, n, n, 1)[0]
+        gotk = inputs.box_view(tk.grad.cpu().numpy()[:K_p.size], 0, n, n, 1)[0]
+        assert np.abs(gotr - gr).max() <= 1e-10 * np.abs(gr).max()
+        assert np.abs(gotk - gk).max() <= 1e-10 * np.abs(gk).max()
+
+
 def test_heterogeneous_receiver_gradient_matches_finite_differences():
     # 256^2, rho ~ U[0.5,2], K ~ U[1,8] smoothed (sigma 8 cells), radial pulse, J = sum p^2 over
     # the 16 x 16 receiver box after 400 steps, checkpoints every 20; central differences
