@@ -838,9 +838,9 @@ int claw_cfl_max(claw_ctx* ctx, int32_t L, const double* aux, double* smax, void
     if (ctx->medium == 1 && !aux) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = launch_cfl_max(ctx->lev[L].patches, ctx->lev[L].nboxes, ctx->lev[L].max_rows, ctx->medium, std::sqrt(ctx->K0 / ctx->rho0), aux,
-                           smax, s);
-    ctx->launches += 1;
+    cudaError_t e = launch_cfl_max(ctx->lev[L].patches, ctx->lev[L].nboxes, ctx->lev[L].max_rows, ctx->medium,
+                                   std::sqrt(ctx->K0 / ctx->rho0), aux, smax, s);
+    ctx->launches += ctx->lev[L].nboxes > 0;
     return cuda_rc(e);
 }
 

@@ -301,6 +301,56 @@ def test_errors_are_status_codes():
     assert e.value.status in (claw.CLAW_ESTATE, claw.CLAW_EINVAL)
 
 
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (7, 1), (2, 2), (3, 5), (33, 17), (4096, 8), (8, 4096)])
+def test_tiny_and_extreme_box_shapes_match_oracle(orc, shape):
+    # boxes smaller than a tile, odd sizes (cooperative staging), and the widest and tallest
+    # boxes the tables accept: 5 steps of random data against the oracle's single grid
+    from paper_1808_02638_gb300.solver import Hierarchy
+    nx, ny = shape
+    run = inputs.Run(*inputs.PULSE_DOMAIN)
+    run.levels = [inputs.Level(nx, ny, 2.0 / nx, 2.0 / ny, [(0, 0, nx, ny)])]
+    lev = run.levels[0]
+    q = np.zeros(lev.qsize)
+    v = inputs.box_view(q, 0, nx, ny, 3)
+    v[...] = inputs.uniform(60 + nx + 7 * ny, v.size).reshape(v.shape) - 0.5
+    v[0] += 1.0
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    for _ in range(5):
+        H.coarse_step()
+    got = H.interior(0, 0, 0)
+    ones = np.ones((ny + 4, nx + 4))
+    want, _ = oracle_single(orc, run, q, ones, 4.0 * ones, 5)
+    assert rel_err(got, want) <= TOLN
+    assert H.sync_status() == 0
+
+
+def test_empty_level_and_box_limits():
+    # a level without boxes is a valid no-op for every entry point; boxes past 4096 cells per
+    # side are rejected before any launch
+    import torch
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, q = single_grid(32)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    claw.claw_set_level(H.ctx, 0, [])
+    scratch = torch.zeros(64, dtype=torch.float64, device=H.dev)
+    before = claw.claw_launch_count(H.ctx)
+    claw.claw_fill_ghost(H.ctx, 0, scratch)
+    claw.claw_level_step(H.ctx, 0, scratch, scratch, None, H.dt, H.smax)
+    claw.claw_cfl_max(H.ctx, 0, None, H.smax)
+    claw.claw_level_step_adjoint(H.ctx, 0, scratch, scratch, scratch, None, None, H.dt)
+    assert claw.claw_launch_count(H.ctx) == before
+    assert bool((scratch == 0).all())
+    assert H.sync_status() == 0
+    big = inputs.Run(*inputs.PULSE_DOMAIN)
+    big.levels = [inputs.Level(4104, 8, 2.0 / 4104, 0.25, [(0, 0, 4104, 8)])]
+    with pytest.raises(claw.ClawError) as e:
+        Hierarchy([big], [[np.zeros(big.levels[0].qsize)]], rho0=1.0, K0=4.0)
+    assert e.value.status == claw.CLAW_EINVAL
+
+
 def test_nan_input_is_reported_not_trapped():
     from paper_1808_02638_gb300 import claw
     from paper_1808_02638_gb300.solver import Hierarchy
