@@ -62,6 +62,7 @@ def lib():
             L.orc_philim.restype = dbl
             L.orc_riemann_x.argtypes = [dbl] * 8 + [D, D]
             L.orc_step.argtypes = [I, I, I, dbl, dbl, dbl, I, I, I, D, D, D, D, D]
+            L.orc_step_edges.argtypes = [I, I, I, dbl, dbl, dbl, I, I, I, D, D, D, D, D, D]
             L.orc_step_adjoint.argtypes = [I, I, I, dbl, dbl, dbl, I, I, I, D, D, D, D, D, D, D]
             L.orc_fill_bc.argtypes = [I, I, I, I, IP, D]
             L.orc_fill_bc_adjoint.argtypes = [I, I, I, I, IP, D]
@@ -120,6 +121,28 @@ def step(q, rho, K, dx, dy, dt, order=2, transverse=2, limiter="mc"):
     if rc:
         raise ValueError(f"orc_step failed ({rc})")
     return qn, sm.value
+
+
+def step_edges(q, rho, K, dx, dy, dt, order=2, transverse=2, limiter="mc"):
+    """:func:`step` that also returns the step's per-edge quantities (Sec. 2.3 conservation fix).
+
+    Returns (qnew, smax, edges) with edges a dict of (3, H, W) arrays: "amx", "apx" (A-dQ, A+dQ
+    of the x-edge between cells (i-1, j) and (i, j), stored at (i, j)), "amy", "apy" (y-edges,
+    stored at the upper cell), "F" and "G" (the correction-plus-transverse fluxes of the x- and
+    y-edges, same storage)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    _, H, W = q.shape
+    nx, ny = W - 2 * MBC, H - 2 * MBC
+    qn = q.copy()
+    sm = ctypes.c_double(0.0)
+    e = np.zeros((6, 3, H, W))
+    rc = lib().orc_step_edges(nx, ny, MBC, dx, dy, dt, order, transverse, _lim(limiter),
+                              _p(q), _p(rho), _p(K), _p(qn), ctypes.byref(sm), _p(e))
+    if rc:
+        raise ValueError(f"orc_step_edges failed ({rc})")
+    return qn, sm.value, dict(zip(("amx", "apx", "amy", "apy", "F", "G"), e))
 
 
 def step_adjoint(q, rho, K, lam_new, dx, dy, dt, order=2, transverse=2, limiter="mc"):

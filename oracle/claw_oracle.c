@@ -228,10 +228,15 @@ static void cell_speeds(const geom* g, const double* rho, const double* K, doubl
     }
 }
 
-int orc_step(int nx, int ny, int mbc, double dx, double dy, double dt,
-             int order, int transverse, int limiter,
-             const double* q, const double* rho, const double* K,
-             double* qnew, double* smax)
+/* One step of every interior cell (Eq. wave_form_2d_2nd_order).  When `edges` is not NULL it
+ * receives six planes-of-3 arrays of the patch layout: A-dQ, A+dQ at x-edges, B-dQ, B+dQ at
+ * y-edges (each stored at the edge's right / upper cell), the x-edge correction-plus-transverse
+ * flux F~ and the y-edge flux G~ (same storage): the per-edge quantities the conservation fix of
+ * Sec. 2.3 reads at coarse-fine interfaces. */
+int orc_step_edges(int nx, int ny, int mbc, double dx, double dy, double dt,
+                   int order, int transverse, int limiter,
+                   const double* q, const double* rho, const double* K,
+                   double* qnew, double* smax, double* edges)
 {
     if (nx < 1 || ny < 1 || mbc < 2 || !(dx > 0) || !(dy > 0)) return -1;
     geom G = {nx, ny, mbc, nx + 2 * mbc, ny + 2 * mbc};
@@ -263,8 +268,20 @@ int orc_step(int nx, int ny, int mbc, double dx, double dy, double dt,
             }
         }
     if (smax) *smax = sm;
+    if (edges) {
+        const double* src[6] = {amx, apx, amy, apy, F, Gt};
+        for (int a = 0; a < 6; ++a) memcpy(edges + (long)a * 3 * pl, src[a], sizeof(double) * 3 * pl);
+    }
     free(rec); free(c); free(Z); free(amx); free(apx); free(amy); free(apy); free(F); free(Gt);
     return 0;
+}
+
+int orc_step(int nx, int ny, int mbc, double dx, double dy, double dt,
+             int order, int transverse, int limiter,
+             const double* q, const double* rho, const double* K,
+             double* qnew, double* smax)
+{
+    return orc_step_edges(nx, ny, mbc, dx, dy, dt, order, transverse, limiter, q, rho, K, qnew, smax, 0);
 }
 
 void orc_riemann_x(double pl, double ul, double rhol, double Kl,

@@ -39,6 +39,15 @@ int orc_step(int nx, int ny, int mbc, double dx, double dy, double dt,
              const double* q, const double* rho, const double* K,
              double* qnew, double* smax);
 
+/* orc_step that also returns, in `edges` (18 planes of the patch layout, or NULL), the
+ * per-edge quantities of the step: A-dQ, A+dQ at x-edges, B-dQ, B+dQ at y-edges (3 planes
+ * each, stored at the edge's right / upper cell), the x-edge correction-plus-transverse flux
+ * F~ and the y-edge flux G~ (same storage).  The conservation fix of Sec. 2.3 reads them. */
+int orc_step_edges(int nx, int ny, int mbc, double dx, double dy, double dt,
+                   int order, int transverse, int limiter,
+                   const double* q, const double* rho, const double* K,
+                   double* qnew, double* smax, double* edges);
+
 /* Reverse mode of orc_step for a frozen dt: given lam_new (adjoint of qnew, interior
  * cells only are read) accumulate (+=) the adjoint of q (all cells incl. ghosts) into
  * lam_q, and of rho, K (all cells) into g_rho, g_K. */
