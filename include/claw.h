@@ -228,6 +228,34 @@ int claw_average_down_adjoint(claw_ctx* ctx, int32_t fine_level, double* lam_fin
 int claw_medium_aux_adjoint(claw_ctx* ctx, int32_t level, const double* rho, const double* K,
                             const double* g_aux, double* g_rho, double* g_K, void* stream);
 
+/* ---- Conservation fix at coarse-fine interfaces (Sec. 2.3, "refluxing"), uniform medium.
+ * For the acoustics system in conservation form (medium = 0), every coarse cell C of level
+ * fine_level-1 that the fine level does not cover but that shares an edge e with it is
+ * corrected after the average so that the flux through e equals the average of the fine fluxes
+ * through the r fine edges over the r substeps.  In flux form, with C left of e:
+ *   Q_C += -(dt/dx) [ (1/r^2) sum_{k,b} (A (Q_F^k - Q_C^n) - A+dQ_b^k + F~_b^k) - (A-dQ_e + F~_e) ]
+ * (the paper's C1 + C2 + C3; mirrored for C right of e and in y), F~ being the correction flux
+ * plus the transverse terms of the edge.  The interface (records, one per coarse cell and side,
+ * periodic boundaries wrapping) is built by claw_set_level of the fine level.  `buf` is a device
+ * buffer of 3 doubles per record, owned by the caller; dt are the per-run level-0 time steps
+ * (the levels' own steps follow from the ratios).  Sequence per coarse step of level L-1:
+ *   claw_reflux_coarse(L, q_{L-1}^n)                       (ghosts of q_{L-1}^n filled)
+ *   for each substep k: claw_reflux_fine(L, q_L^k, q_{L-1}^n) (ghosts of q_L^k filled)
+ *   claw_average_down(L, ...), then claw_reflux_apply(L, q_{L-1}^{n+1}).
+ * Errors: CLAW_EINVAL (medium = 1, NULL pointers, level 0), CLAW_ESTATE, CLAW_ECUDA. */
+int claw_reflux_count(claw_ctx* ctx, int32_t fine_level);   /* records, or minus an error code */
+/* buf := minus the coarse part (A-dQ_e + F~_e, or -A+dQ_e + F~_e for C right of e) of each record */
+int claw_reflux_coarse(claw_ctx* ctx, int32_t fine_level, const double* q_c_old, const double* dt,
+                       double* buf, void* stream);
+/* buf += (1/r^2) sum over the record's r fine edges of the fine part, from the fine state q_f of
+ * one substep and the coarse state q_c_old the coarse step started from */
+int claw_reflux_fine(claw_ctx* ctx, int32_t fine_level, const double* q_f, const double* q_c_old,
+                     const double* dt, double* buf, void* stream);
+/* q_c_new of every corrected coarse cell += -side (dt_c / h) buf, summed per cell in table order
+ * (deterministic) */
+int claw_reflux_apply(claw_ctx* ctx, int32_t fine_level, const double* buf, const double* dt,
+                      double* q_c_new, void* stream);
+
 /* Waits for the context's device work, returns and clears the first device-side error
  * (CLAW_ENAN, CLAW_ECFL, CLAW_ETIMEOUT) or CLAW_OK. */
 int claw_sync_status(claw_ctx* ctx);

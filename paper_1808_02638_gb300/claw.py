@@ -52,6 +52,10 @@ _SIGNATURES = {
     "claw_set_tiling": ([VP, I32, I32, I32, I32, I32], ctypes.c_int),
     "claw_medium_aux": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_medium_aux_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_reflux_count": ([VP, I32], ctypes.c_int),
+    "claw_reflux_coarse": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
+    "claw_reflux_fine": ([VP, I32, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_reflux_apply": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_fill_ghost": ([VP, I32, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_adjoint": ([VP, I32, VP, VP, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_coef": ([VP, I32, VP, VP], ctypes.c_int),
@@ -138,6 +142,28 @@ def claw_set_tiling(ctx, level: int, tx: int, ty: int, staging: int, threads: in
 
 def claw_medium_aux(ctx, level, rho, K, aux, stream=None):
     _check("claw_medium_aux", load().claw_medium_aux(ctx, level, _ptr(rho), _ptr(K), _ptr(aux), _stream(stream)))
+
+
+def claw_reflux_count(ctx, fine_level):
+    n = load().claw_reflux_count(ctx, fine_level)
+    if n < 0:
+        raise ClawError("claw_reflux_count", -n)
+    return n
+
+
+def claw_reflux_coarse(ctx, fine_level, q_c_old, dt, buf, stream=None):
+    _check("claw_reflux_coarse", load().claw_reflux_coarse(ctx, fine_level, _ptr(q_c_old), _ptr(dt), _ptr(buf),
+                                                           _stream(stream)))
+
+
+def claw_reflux_fine(ctx, fine_level, q_f, q_c_old, dt, buf, stream=None):
+    _check("claw_reflux_fine", load().claw_reflux_fine(ctx, fine_level, _ptr(q_f), _ptr(q_c_old), _ptr(dt), _ptr(buf),
+                                                       _stream(stream)))
+
+
+def claw_reflux_apply(ctx, fine_level, buf, dt, q_c_new, stream=None):
+    _check("claw_reflux_apply", load().claw_reflux_apply(ctx, fine_level, _ptr(buf), _ptr(dt), _ptr(q_c_new),
+                                                         _stream(stream)))
 
 
 def claw_medium_aux_adjoint(ctx, level, rho, K, g_aux, g_rho, g_K, stream=None):

@@ -159,6 +159,11 @@ void free_level(claw_ctx* ctx, int L)
     d.nccopy = 0;
     cudaFree(d.interps);
     cudaFree(d.avgs);
+    cudaFree(d.reflux);
+    cudaFree(d.reflux_group);
+    d.reflux = nullptr;
+    d.reflux_group = nullptr;
+    d.nreflux = d.nreflux_groups = 0;
     cudaFree(d.copy_start);
     cudaFree(d.ccopy_start);
     d.copy_start = d.ccopy_start = nullptr;
@@ -411,6 +416,73 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
     }
     if (!rects.empty()) start.push_back((int)rects.size());
     return CLAW_OK;
+}
+
+// coarse-fine interface of level L for the conservation fix: every coarse cell of level L-1
+// that no box of level L covers but that shares an edge with one, per fine box side; periodic
+// boundaries wrap, other boundaries end the interface.  Records are grouped by coarse cell.
+void build_reflux_tables(claw_ctx* ctx, int L, std::vector<RefluxRec>& recs, std::vector<int>& group)
+{
+    const LevelDev& f = ctx->lev[L];
+    const LevelDev& c = ctx->lev[L - 1];
+    const int r = f.ratio;
+    std::vector<Locator> floc(ctx->nruns), cloc(ctx->nruns);
+    for (int q = 0; q < ctx->nruns; ++q) {
+        floc[q].boxes = &f.boxes;
+        cloc[q].boxes = &c.boxes;
+    }
+    for (int n = 0; n < f.nboxes; ++n) floc[f.boxes[n].run].add(f.boxes[n], n);
+    for (int n = 0; n < (int)c.boxes.size(); ++n) cloc[c.boxes[n].run].add(c.boxes[n], n);
+    auto wrap = [](int k, int n, int lo, int hi, bool& ok) {
+        ok = true;
+        if (k >= 0 && k < n) return k;
+        if ((k < 0 && lo == CLAW_BC_PERIODIC) || (k >= n && hi == CLAW_BC_PERIODIC)) return ((k % n) + n) % n;
+        ok = false;
+        return k;
+    };
+    recs.clear();
+    for (int nf = 0; nf < f.nboxes; ++nf) {
+        const claw_box& b = f.boxes[nf];
+        const claw_problem& p = ctx->runs[b.run];
+        const int NXc = level_nx(p, L - 1), NYc = level_ny(p, L - 1);
+        const int I0 = b.ilo / r, I1 = (b.ilo + b.nx) / r, J0 = b.jlo / r, J1 = (b.jlo + b.ny) / r;
+        auto add = [&](int I, int J, int dir, int side, int fi, int fj) {
+            bool okx, oky;
+            const int Im = wrap(I, NXc, p.bc[0], p.bc[1], okx), Jm = wrap(J, NYc, p.bc[2], p.bc[3], oky);
+            if (!okx || !oky) return;
+            if (floc[b.run].find(Im * r, Jm * r) >= 0) return;   // covered: a fine-fine edge
+            const int nc = cloc[b.run].find(Im, Jm);
+            if (nc < 0) return;                                 // excluded by proper nesting
+            RefluxRec R;
+            R.cbox = nc;
+            R.fbox = nf;
+            R.ci = (short)(Im - c.boxes[nc].ilo);
+            R.cj = (short)(Jm - c.boxes[nc].jlo);
+            R.fi = (short)fi;
+            R.fj = (short)fj;
+            R.dir = (short)dir;
+            R.side = (short)side;
+            recs.push_back(R);
+        };
+        for (int J = J0; J < J1; ++J) {
+            add(I1, J, 0, -1, b.nx - 1, J * r - b.jlo);
+            add(I0 - 1, J, 0, +1, 0, J * r - b.jlo);
+        }
+        for (int I = I0; I < I1; ++I) {
+            add(I, J1, 1, -1, I * r - b.ilo, b.ny - 1);
+            add(I, J0 - 1, 1, +1, I * r - b.ilo, 0);
+        }
+    }
+    std::stable_sort(recs.begin(), recs.end(), [](const RefluxRec& x, const RefluxRec& y) {
+        if (x.cbox != y.cbox) return x.cbox < y.cbox;
+        if (x.cj != y.cj) return x.cj < y.cj;
+        return x.ci < y.ci;
+    });
+    group.clear();
+    for (size_t i = 0; i < recs.size(); ++i)
+        if (i == 0 || recs[i].cbox != recs[i - 1].cbox || recs[i].ci != recs[i - 1].ci || recs[i].cj != recs[i - 1].cj)
+            group.push_back((int)i);
+    if (!recs.empty()) group.push_back((int)recs.size());
 }
 
 // coarse cells of level L-1 covered by each box of level L
@@ -705,6 +777,14 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     d.max_rows = 0;
     for (const claw_box& b : d.boxes) d.max_rows = std::max(d.max_rows, b.ny + 4);
     if (L > 0) build_avg_tables(ctx, L, avg);
+    if (L > 0) {
+        std::vector<RefluxRec> rrec;
+        std::vector<int> rgroup;
+        build_reflux_tables(ctx, L, rrec, rgroup);
+        if ((rc = upload(&d.reflux, rrec)) || (rc = upload(&d.reflux_group, rgroup))) return rc;
+        d.nreflux = (int)rrec.size();
+        d.nreflux_groups = rgroup.empty() ? 0 : (int)rgroup.size() - 1;
+    }
     // the same copies for one-plane pools: offsets from coff, no wall sign flips
     std::vector<CopyRect> crects;
     {
@@ -967,6 +1047,59 @@ int claw_level_step_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const
     ctx->launches += 1;
     return cuda_rc(launch_step_adjoint(a, lam_new, lam_old, g_aux, ctx->medium, ctx->limiter, ctx->nsm,
                                        (cudaStream_t)stream));
+}
+
+static int reflux_check(claw_ctx* ctx, int L)
+{
+    if (!ctx || L < 1 || L >= CLAW_MAXLEV) return CLAW_EINVAL;
+    if (!ctx->set[L] || !ctx->set[L - 1]) return CLAW_ESTATE;
+    if (ctx->medium != 0) return CLAW_EINVAL;   // the fix assumes conservation form (uniform medium)
+    return CLAW_OK;
+}
+
+int claw_reflux_count(claw_ctx* ctx, int32_t L)
+{
+    int rc = reflux_check(ctx, L);
+    return rc ? -rc : ctx->lev[L].nreflux;
+}
+
+int claw_reflux_coarse(claw_ctx* ctx, int32_t L, const double* q_c_old, const double* dt, double* buf, void* stream)
+{
+    int rc = reflux_check(ctx, L);
+    if (rc) return rc;
+    if (!q_c_old || !dt || !buf) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    const StepArgs k = make_args(ctx, L - 1, nullptr, nullptr, nullptr, dt, nullptr);
+    ctx->launches += d.nreflux > 0;
+    return cuda_rc(launch_reflux_coarse(d.reflux, d.nreflux, ctx->lev[L - 1].patches, q_c_old, dt, buf, k,
+                                        ctx->limiter, (cudaStream_t)stream));
+}
+
+int claw_reflux_fine(claw_ctx* ctx, int32_t L, const double* q_f, const double* q_c_old, const double* dt, double* buf,
+                     void* stream)
+{
+    int rc = reflux_check(ctx, L);
+    if (rc) return rc;
+    if (!q_f || !q_c_old || !dt || !buf) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    const StepArgs k = make_args(ctx, L, nullptr, nullptr, nullptr, dt, nullptr);
+    ctx->launches += d.nreflux > 0;
+    return cuda_rc(launch_reflux_fine(d.reflux, d.nreflux, ctx->lev[L - 1].patches, d.patches, q_f, q_c_old, dt, buf,
+                                      d.ratio, k, ctx->limiter, (cudaStream_t)stream));
+}
+
+int claw_reflux_apply(claw_ctx* ctx, int32_t L, const double* buf, const double* dt, double* q_c_new, void* stream)
+{
+    int rc = reflux_check(ctx, L);
+    if (rc) return rc;
+    if (!buf || !dt || !q_c_new) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    ctx->launches += d.nreflux_groups > 0;
+    return cuda_rc(launch_reflux_apply(d.reflux, d.reflux_group, d.nreflux_groups, ctx->lev[L - 1].patches, dt, buf,
+                                       q_c_new, (cudaStream_t)stream));
 }
 
 int claw_sync_status(claw_ctx* ctx)

@@ -55,6 +55,16 @@ struct CopyRect {
     int flags;   // bit0: negate u, bit1: negate v
 };
 
+// One coarse-fine interface edge of the conservation fix (Sec. 2.3): coarse cell C = (ci, cj)
+// of coarse box cbox, not covered by the fine level, shares an edge with the fine region; the r
+// fine cells next to that edge start at (fi, fj) of fine box fbox and run along the edge.
+// dir 0: x-edge, 1: y-edge; side +1: C is left of / below the edge, -1: right of / above.
+struct RefluxRec {
+    int cbox, fbox;
+    short ci, cj, fi, fj;
+    short dir, side;
+};
+
 // One fine ghost cell filled by space-time interpolation from the coarser level.
 struct InterpCell {
     long long dst;        // plane-0 element of the fine ghost cell
@@ -95,6 +105,10 @@ struct LevelDev {
     int* ccopy_start = nullptr;
     int ncopy_blocks = 0, nccopy_blocks = 0;
     int max_rows = 0;             // largest (ny + 4) of the level's boxes
+    RefluxRec* reflux = nullptr;  // interface with the coarser level, grouped by coarse cell
+    int nreflux = 0;
+    int* reflux_group = nullptr;  // [ngroups + 1]: records of coarse cell g are [group[g], group[g+1])
+    int nreflux_groups = 0;
     // host copies
     std::vector<claw_box> boxes;
     std::vector<PatchDev> hpatches;
@@ -157,6 +171,15 @@ cudaError_t launch_medium_aux(const PatchDev* p, int n, int max_rows, const doub
 cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, int max_rows, const double* rho,
                                       const double* K, const double* g_aux, double* g_rho,
                                       double* g_K, cudaStream_t s);
+// conservation fix (uniform medium): buf holds 3 doubles per interface record
+// (k: the scheme's order, transverse mode and uniform medium rho0, K0)
+cudaError_t launch_reflux_coarse(const RefluxRec* rec, int n, const PatchDev* cp, const double* qc, const double* dt,
+                                 double* buf, const StepArgs& k, int limiter, cudaStream_t s);
+cudaError_t launch_reflux_fine(const RefluxRec* rec, int n, const PatchDev* cp, const PatchDev* fp, const double* qf,
+                               const double* qc, const double* dt, double* buf, int ratio, const StepArgs& k,
+                               int limiter, cudaStream_t s);
+cudaError_t launch_reflux_apply(const RefluxRec* rec, const int* group, int ngroups, const PatchDev* cp,
+                                const double* dt, const double* buf, double* qc, cudaStream_t s);
 cudaError_t launch_cfl_max(const PatchDev* p, int n, int max_rows, int medium, double c0, const double* aux,
                            double* smax, cudaStream_t s);
 cudaError_t launch_dt_update(const double* minh, const double* cfl, int nruns, double* smax,

@@ -1,0 +1,245 @@
+// claw_reflux.cu -- the conservation fix of Sec. 2.3 ("refluxing") for a uniform medium, where
+// the acoustics system is in conservation form: f(Q) = A Q, g(Q) = B Q.
+//
+// A coarse cell C next to the fine region (not covered by it) is updated by the coarse step with
+// the flux F_e through its edge e; the fine cells along e see r fine fluxes per substep.  After
+// the fine substeps and the average, C is corrected so that the flux through e is the average
+// of the fine ones.  With C left of e and fine cells F_b right of their edges e_b:
+//   F_e   - f(Q_C^n) = A-dQ_e + F~_e                                  (coarse part)
+//   F_b^k - f(Q_C^n) = A (Q_F^k - Q_C^n) - A+dQ_b^k + F~_b^k            (fine part, substep k)
+//   Q_C^{n+1} += -(dt/dx) [ (1/r^2) sum_{k,b} (F_b^k - f(Q_C^n)) - (F_e - f(Q_C^n)) ]
+// (the paper's C1 + C2 + C3), mirrored for C right of e (+A-dQ_b, -A+dQ_e, opposite sign) and
+// in y.  F~ is the correction flux plus the transverse terms the other direction's sweep puts
+// on the edge.  Each edge's quantities are evaluated here from the state the step read, with the
+// step's own formulation (wave strengths scaled by 2, the same limiter functions), so the fix
+// matches the fused kernel's update to rounding.
+#include <cuda_runtime.h>
+
+#include "claw_step.cuh"
+
+namespace claw {
+namespace {
+
+struct UMed {
+    double c, Z, iZ, K, irho;
+};
+
+// A-dQ, A+dQ and F~ of the edge between normal indices e-1 and e on line t of a box (local
+// interior coordinates; dir 0: x-edge, normal index i, line j; dir 1: y-edge), components in
+// the edge's order (p, normal velocity, transverse velocity).
+template <int LIM>
+__device__ void edge_terms(const double* q, int W, long long WH, int dir, int e, int t, const UMed& md, double ln,
+                           double lt, int order, int transverse, double am[3], double ap[3], double f[3])
+{
+    const int mn = dir == 0 ? 1 : 2, mt = dir == 0 ? 2 : 1;
+    auto Q = [&](int m, int n, int l) -> double {
+        const int i = dir == 0 ? n : l, j = dir == 0 ? l : n;
+        return q[m * WH + (long long)(j + 2) * W + (i + 2)];
+    };
+    // normal strengths (x2) of the edge between n-1 and n on line l
+    auto strengths = [&](int n, int l, double& a1, double& a2) {
+        const double dp = Q(0, n, l) - Q(0, n - 1, l), du = Q(mn, n, l) - Q(mn, n - 1, l);
+        a1 = fma(-dp, md.iZ, du);
+        a2 = fma(dp, md.iZ, du);
+    };
+    // transverse strengths (x2) of the edge between lines l-1 and l on normal index n
+    auto tstrengths = [&](int n, int l, double& b1, double& b2) {
+        const double dp = Q(0, n, l) - Q(0, n, l - 1), dv = Q(mt, n, l) - Q(mt, n, l - 1);
+        b1 = fma(-dp, md.iZ, dv);
+        b2 = fma(dp, md.iZ, dv);
+    };
+    const double c = md.c, Z = md.Z;
+    double a1, a2;
+    strengths(e, t, a1, a2);
+    am[0] = 0.5 * c * Z * a1;
+    am[1] = -0.5 * c * a1;
+    am[2] = 0.0;
+    ap[0] = 0.5 * c * Z * a2;
+    ap[1] = 0.5 * c * a2;
+    ap[2] = 0.0;
+    f[0] = f[1] = f[2] = 0.0;
+    const bool second = order == 2;
+    if (second) {   // normal correction flux: (1/2) sum |s| (1 - ln |s|) W~
+        double b1, b2, c1, c2;
+        strengths(e + 1, t, b1, b2);
+        strengths(e - 1, t, c1, c2);
+        const double m1 = Lim<LIM>::f(a1, b1), m2 = Lim<LIM>::f(a2, c2);
+        const double kap = c * (1.0 - ln * c);
+        f[0] += 0.25 * kap * Z * (m2 - m1);
+        f[1] += 0.25 * kap * (m1 + m2);
+    }
+    if (transverse) {
+        const bool cw = transverse == 2 && second;
+        // pressure of the transverse fluctuations into cell (n, t): the up-going part of the
+        // transverse edge t (with -C) and the down-going part of edge t+1 (with +C)
+        auto P = [&](int n) -> double {
+            double lo1, lo2, hi1, hi2;
+            tstrengths(n, t, lo1, lo2);
+            tstrengths(n, t + 1, hi1, hi2);
+            double r = 0.5 * c * Z * (lo2 + hi1);
+            if (cw) {
+                double p1, p2, q1, q2;
+                tstrengths(n, t - 1, p1, p2);
+                tstrengths(n, t + 2, q1, q2);
+                const double s_lo = Lim<LIM>::f(lo2, p2) - Lim<LIM>::f(lo1, hi1);
+                const double s_hi = Lim<LIM>::f(hi2, lo2) - Lim<LIM>::f(hi1, q1);
+                r += 0.5 * c * (1.0 - lt * c) * Z * (s_hi - s_lo);
+            }
+            return r;
+        };
+        const double PL = P(e - 1), PR = P(e);
+        f[0] -= 0.25 * lt * c * (PL - PR);
+        f[1] -= 0.25 * lt * c * md.iZ * (PL + PR);
+    }
+}
+
+__device__ __forceinline__ UMed umed(const StepArgs& k)
+{
+    UMed m;
+    m.Z = sqrt(k.K0 * k.rho0);
+    m.c = sqrt(k.K0 / k.rho0);
+    m.iZ = 1.0 / m.Z;
+    m.K = k.K0;
+    m.irho = 1.0 / k.rho0;
+    return m;
+}
+
+// edge-local (p, normal, transverse) -> (p, u, v)
+__device__ __forceinline__ void to_puv(int dir, const double in[3], double out[3])
+{
+    out[0] = in[0];
+    out[1] = dir == 0 ? in[1] : in[2];
+    out[2] = dir == 0 ? in[2] : in[1];
+}
+
+template <int LIM>
+__global__ void reflux_coarse_kernel(const RefluxRec* __restrict__ recs, int n, const PatchDev* __restrict__ cp,
+                                     const double* __restrict__ qc, const double* __restrict__ dt,
+                                     double* __restrict__ buf, const StepArgs k)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const RefluxRec R = recs[r];
+    const PatchDev P = cp[R.cbox];
+    const int W = P.nx + 4;
+    const long long WH = (long long)W * (P.ny + 4);
+    const double d = __ldg(dt + P.run) * P.dtscale;
+    const double lx = d * P.dxinv, ly = d * P.dyinv;
+    const UMed md = umed(k);
+    const int cn = R.dir == 0 ? R.ci : R.cj, cl = R.dir == 0 ? R.cj : R.ci;
+    const int e = R.side > 0 ? cn + 1 : cn;   // C's east / north edge, or its west / south edge
+    double am[3], ap[3], f[3], t[3], o[3];
+    edge_terms<LIM>(qc + P.qoff, W, WH, R.dir, e, cl, md, R.dir == 0 ? lx : ly, R.dir == 0 ? ly : lx, k.order,
+                    k.transverse, am, ap, f);
+    for (int m = 0; m < 3; ++m) t[m] = (R.side > 0 ? am[m] : -ap[m]) + f[m];
+    to_puv(R.dir, t, o);
+    for (int m = 0; m < 3; ++m) buf[3 * r + m] = -o[m];
+}
+
+template <int LIM>
+__global__ void reflux_fine_kernel(const RefluxRec* __restrict__ recs, int n, const PatchDev* __restrict__ cp,
+                                   const PatchDev* __restrict__ fp, const double* __restrict__ qf,
+                                   const double* __restrict__ qc, const double* __restrict__ dt,
+                                   double* __restrict__ buf, int ratio, const StepArgs k)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const RefluxRec R = recs[r];
+    const PatchDev C = cp[R.cbox], F = fp[R.fbox];
+    const int Wc = C.nx + 4, Wf = F.nx + 4;
+    const long long WHc = (long long)Wc * (C.ny + 4), WHf = (long long)Wf * (F.ny + 4);
+    const double d = __ldg(dt + F.run) * F.dtscale;
+    const double lx = d * F.dxinv, ly = d * F.dyinv;
+    const UMed md = umed(k);
+    const long long co = C.qoff + (long long)(R.cj + 2) * Wc + (R.ci + 2);
+    double qC[3];
+    for (int m = 0; m < 3; ++m) qC[m] = qc[co + m * WHc];
+    const int mn = R.dir == 0 ? 1 : 2;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < ratio; ++b) {
+        const int fi = R.dir == 0 ? R.fi : R.fi + b, fj = R.dir == 0 ? R.fj + b : R.fj;
+        const int fn = R.dir == 0 ? fi : fj, fl = R.dir == 0 ? fj : fi;
+        const int e = R.side > 0 ? fn : fn + 1;   // the fine cell's west / south or east / north edge
+        double am[3], ap[3], f[3];
+        edge_terms<LIM>(qf + F.qoff, Wf, WHf, R.dir, e, fl, md, R.dir == 0 ? lx : ly, R.dir == 0 ? ly : lx,
+                        k.order, k.transverse, am, ap, f);
+        const long long fo = F.qoff + (long long)(fj + 2) * Wf + (fi + 2);
+        const double dp = qf[fo] - qC[0], dn = qf[fo + mn * WHf] - qC[mn];
+        // A (Q_F - Q_C) in the edge's order: (K dn, dp / rho, 0)
+        const double fl3[3] = {md.K * dn, dp * md.irho, 0.0};
+        double t[3], o[3];
+        for (int m = 0; m < 3; ++m) t[m] = fl3[m] + (R.side > 0 ? -ap[m] : am[m]) + f[m];
+        to_puv(R.dir, t, o);
+        for (int m = 0; m < 3; ++m) acc[m] += o[m];
+    }
+    const double w = 1.0 / ((double)ratio * ratio);
+    for (int m = 0; m < 3; ++m) buf[3 * r + m] += w * acc[m];
+}
+
+// one thread per corrected coarse cell: its records in table order (deterministic sums)
+__global__ void reflux_apply_kernel(const RefluxRec* __restrict__ recs, const int* __restrict__ group, int ng,
+                                    const PatchDev* __restrict__ cp, const double* __restrict__ dt,
+                                    const double* __restrict__ buf, double* __restrict__ qc)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const int r0 = group[g], r1 = group[g + 1];
+    const RefluxRec R0 = recs[r0];
+    const PatchDev C = cp[R0.cbox];
+    const double d = __ldg(dt + C.run) * C.dtscale;
+    double corr[3] = {0.0, 0.0, 0.0};
+    for (int r = r0; r < r1; ++r) {
+        const RefluxRec R = recs[r];
+        const double s = -R.side * d * (R.dir == 0 ? C.dxinv : C.dyinv);
+        for (int m = 0; m < 3; ++m) corr[m] = fma(s, buf[3 * r + m], corr[m]);
+    }
+    const int W = C.nx + 4;
+    const long long WH = (long long)W * (C.ny + 4);
+    const long long o = C.qoff + (long long)(R0.cj + 2) * W + (R0.ci + 2);
+    for (int m = 0; m < 3; ++m) qc[o + m * WH] += corr[m];
+}
+
+}  // namespace
+
+static inline int blocks_for(int n) { return (n + 127) / 128; }
+
+cudaError_t launch_reflux_coarse(const RefluxRec* rec, int n, const PatchDev* cp, const double* qc, const double* dt,
+                                 double* buf, const StepArgs& k, int limiter, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    switch (limiter) {
+    case CLAW_LIM_NONE: reflux_coarse_kernel<CLAW_LIM_NONE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
+    case CLAW_LIM_MINMOD: reflux_coarse_kernel<CLAW_LIM_MINMOD><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
+    case CLAW_LIM_SUPERBEE: reflux_coarse_kernel<CLAW_LIM_SUPERBEE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
+    case CLAW_LIM_VANLEER: reflux_coarse_kernel<CLAW_LIM_VANLEER><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
+    case CLAW_LIM_MC: reflux_coarse_kernel<CLAW_LIM_MC><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reflux_fine(const RefluxRec* rec, int n, const PatchDev* cp, const PatchDev* fp, const double* qf,
+                               const double* qc, const double* dt, double* buf, int ratio, const StepArgs& k,
+                               int limiter, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    switch (limiter) {
+    case CLAW_LIM_NONE: reflux_fine_kernel<CLAW_LIM_NONE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_MINMOD: reflux_fine_kernel<CLAW_LIM_MINMOD><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_SUPERBEE: reflux_fine_kernel<CLAW_LIM_SUPERBEE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_VANLEER: reflux_fine_kernel<CLAW_LIM_VANLEER><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_MC: reflux_fine_kernel<CLAW_LIM_MC><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reflux_apply(const RefluxRec* rec, const int* group, int ngroups, const PatchDev* cp,
+                                const double* dt, const double* buf, double* qc, cudaStream_t s)
+{
+    if (ngroups <= 0) return cudaSuccess;
+    reflux_apply_kernel<<<blocks_for(ngroups), 128, 0, s>>>(rec, group, ngroups, cp, dt, buf, qc);
+    return cudaGetLastError();
+}
+
+}  // namespace claw

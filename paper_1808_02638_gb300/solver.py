@@ -5,8 +5,9 @@ time step of Sec. 2.2: fill the ghosts of level L, take one level-step, then R_L
 level L+1 whose ghosts are interpolated in space and time from level L, then overwrite the
 covered cells of level L with the fine average ("updating").  The level-0 time step follows
 Eq. cfl from the largest wave speed the previous coarse step saw, computed on the device, so
-a coarse step is a fixed launch sequence that a CUDA graph replays.  No arithmetic of the
-method happens here.
+a coarse step is a fixed launch sequence that a CUDA graph replays.  With `reflux=True` (uniform
+medium) the conservation fix of Sec. 2.3 corrects the coarse cells next to each finer level
+after the average.  No arithmetic of the method happens here.
 """
 from __future__ import annotations
 
@@ -29,7 +30,7 @@ class Hierarchy:
     only for a cell-wise medium; a uniform medium passes rho0, K0).  All runs' pools of a level
     are concatenated into one device pool per level."""
 
-    def __init__(self, runs, q0, rho=None, K=None, rho0=1.0, K0=4.0, device=0, tiling=None):
+    def __init__(self, runs, q0, rho=None, K=None, rho0=1.0, K0=4.0, device=0, tiling=None, reflux=False):
         self.runs = runs
         self.nruns = len(runs)
         self.nlev = max(len(r.levels) for r in runs)
@@ -107,6 +108,13 @@ class Hierarchy:
         self.dt = torch.zeros(self.nruns, dtype=torch.float64, device=self.dev)
         self.smax = torch.zeros(self.nruns, dtype=torch.float64, device=self.dev)
         self.patchwise = False
+        self.reflux = bool(reflux)
+        if self.reflux and self.medium:
+            raise ValueError("the conservation fix needs the uniform medium (conservation form)")
+        # per fine level: 3 doubles per interface record of the conservation fix
+        self.rbuf = [None] + [torch.zeros(max(1, 3 * claw.claw_reflux_count(self.ctx, L)), dtype=torch.float64,
+                                          device=self.dev) if self.reflux else None
+                              for L in range(1, self.nlev)]
         self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)
         self.fused = False       # one-level hierarchies: step with Eq. cfl on the device, then push ghosts
         self._ghosts_ready = False
@@ -130,6 +138,10 @@ class Hierarchy:
     def advance(self, L, cold=None, cnew=None, tau=0.0, stream=None):
         q = self.q[L][self.cur[L]]
         claw.claw_fill_ghost(self.ctx, L, q, cold, cnew, tau, stream)
+        if self.reflux and L > 0:             # this substep's fine fluxes at level L's interface
+            claw.claw_reflux_fine(self.ctx, L, q, cold, self.dt, self.rbuf[L], stream)
+        if self.reflux and L + 1 < self.nlev:  # the coarse fluxes at the finer level's interface
+            claw.claw_reflux_coarse(self.ctx, L + 1, q, self.dt, self.rbuf[L + 1], stream)
         self.step_level(L, stream)
         old, new = self.q[L][self.cur[L]], self.q[L][1 - self.cur[L]]
         if L + 1 < self.nlev:
@@ -137,6 +149,8 @@ class Hierarchy:
             for k in range(r):
                 self.advance(L + 1, old, new, k / r, stream)
             claw.claw_average_down(self.ctx, L + 1, self.q[L + 1][self.cur[L + 1]], new, stream)
+            if self.reflux:
+                claw.claw_reflux_apply(self.ctx, L + 1, self.rbuf[L + 1], self.dt, new, stream)
         self.cur[L] ^= 1
 
     def coarse_step(self, stream=None):

@@ -103,3 +103,111 @@ def test_batched_independent_runs_two_levels_cellwise():
     for ri in range(len(runs)):
         _compare_all_levels(H, orcs[ri], ri, TOLN)
     assert H.sync_status() == 0
+
+
+# ------------------------------------------------------------ conservation fix (Sec. 2.3)
+def _flowing_pulse(run):
+    q = []
+    for lev in run.levels:
+        a = inputs.init_q(run, lev, fn=lambda x, y: inputs.radial_pulse(x - 0.1, y + 0.05)).copy()
+        for n, b in enumerate(lev.boxes):
+            v = inputs.box_view(a, lev.qoff[n], int(b[2]), int(b[3]), 3)
+            v[1] += 0.3
+            v[2] -= 0.2
+        q.append(a)
+    return q
+
+
+def _composite(H, run_index=0):
+    """sum over every cell not covered by a finer level of q times the cell area"""
+    run = H.runs[run_index]
+    tot = np.zeros(3)
+    for L, lev in enumerate(run.levels):
+        for n, b in enumerate(lev.boxes):
+            nx, ny = int(b[2]), int(b[3])
+            v = H.interior(run_index, L, n)
+            mask = np.ones((ny, nx), bool)
+            if L + 1 < len(run.levels):
+                r = run.levels[L + 1].ratio
+                for fb in run.levels[L + 1].boxes:
+                    i0, j0 = int(fb[0]) // r - int(b[0]), int(fb[1]) // r - int(b[1])
+                    i1, j1 = i0 + int(fb[2]) // r, j0 + int(fb[3]) // r
+                    mask[max(j0, 0):max(min(j1, ny), 0), max(i0, 0):max(min(i1, nx), 0)] = False
+            tot += (v * mask).sum(axis=(1, 2)) * lev.dx * lev.dy
+    return tot
+
+
+def test_reflux_three_levels_matches_oracle():
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
+    O = OracleHierarchy(run, q0, [inputs.const_pool(l, 1.0) for l in run.levels],
+                        [inputs.const_pool(l, 4.0) for l in run.levels], reflux=True)
+    H.init_dt()
+    H.coarse_step()
+    O.coarse_step()
+    _compare_all_levels(H, O, 0, TOL1)
+    for _ in range(19):
+        H.coarse_step()
+        O.coarse_step()
+    _compare_all_levels(H, O, 0, TOLN)
+    assert H.sync_status() == 0
+
+
+def test_reflux_conserves_the_composite_integral_on_a_periodic_domain():
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.Run(*inputs.PULSE_DOMAIN, bc=(1, 1, 1, 1))
+    run.levels = inputs.amr_levels(run, 32, 4, [(0.2, 0.45)], [2002])
+    q0 = _flowing_pulse(run)
+    drift = {}
+    for reflux in (True, False):
+        H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=reflux)
+        H.init_dt()
+        m0 = _composite(H)
+        for _ in range(8):
+            H.coarse_step()
+        drift[reflux] = np.abs(_composite(H) - m0)
+        assert H.sync_status() == 0
+    scale = 4.0 * 1.5
+    assert (drift[True] <= 1e-13 * scale).all(), drift[True]
+    assert drift[False].max() >= 1e-6 * scale, drift[False]
+
+
+def test_reflux_graph_replay_equals_eager():
+    import torch
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    A = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
+    B = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
+    for h in (A, B):
+        h.init_dt()
+        h.coarse_step()
+        h.coarse_step()
+    g = B.capture(2)
+    for _ in range(2):
+        A.coarse_step()
+        A.coarse_step()
+        g.replay()
+    torch.cuda.synchronize()
+    for L in range(A.nlev):
+        assert torch.equal(A.pool(L), B.pool(L))
+
+
+def test_reflux_needs_the_uniform_medium():
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    runs = inputs.config4_runs(1)
+    run, r2, k2 = runs[0]
+    q = [inputs.init_q(run, lev) for lev in run.levels]
+    rho = [inputs.coef_pool(lev, r2, 4 ** L) for L, lev in enumerate(run.levels)]
+    K = [inputs.coef_pool(lev, k2, 4 ** L) for L, lev in enumerate(run.levels)]
+    with pytest.raises(ValueError):
+        Hierarchy([run], [q], [rho], [K], reflux=True)
+    H = Hierarchy([run], [q], [rho], [K])
+    buf = H.q[0][0].clone()
+    with pytest.raises(claw.ClawError) as e:
+        claw.claw_reflux_coarse(H.ctx, 1, H.q[0][0], H.dt, buf)
+    assert e.value.status == claw.CLAW_EINVAL
