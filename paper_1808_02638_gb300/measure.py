@@ -137,10 +137,20 @@ def config2():
     ms = time_fused(H, 20)
     plain = time_plain(H, 2)
     boxes = [len(l.boxes) for l in run.levels]
+    # the same hierarchy with the conservation fix of Sec. 2.3 (same tilings)
+    R = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
+    for L, t in tiling.items():
+        claw.claw_set_tiling(R.ctx, int(L), *t)
+    R.init_dt()
+    ms_r = time_fused(R, 20)
+    nrec = [claw.claw_reflux_count(R.ctx, L) for L in range(1, R.nlev)]
     return _report("3-level AMR, 64^2 base, ratio 4 twice, seeded 8..64 patches on the annuli "
                    f"(boxes per level {boxes}), radial pulse, rho=1, K=4, 20 coarse steps",
                    H, ms, plain, FP64_INSTR_UNIFORM, BYTES_UNIFORM,
-                   {"l2": "L2-resident (about 30 MB)", "tiling": tiling})
+                   {"l2": "L2-resident (about 30 MB)", "tiling": tiling,
+                    "reflux": {"ms_per_coarse_step": ms_r, "overhead": ms_r / ms - 1.0,
+                               "interface_records_per_level": nrec,
+                               "launches_per_coarse_step": R.launches_per_coarse_step()}})
 
 
 def _cellwise_single(n):
