@@ -237,22 +237,25 @@ int claw_medium_aux_adjoint(claw_ctx* ctx, int32_t level, const double* rho, con
  * (the paper's C1 + C2 + C3; mirrored for C right of e and in y), F~ being the correction flux
  * plus the transverse terms of the edge.  The interface (records, one per coarse cell and side,
  * periodic boundaries wrapping) is built by claw_set_level of the fine level.  `buf` is a device
- * buffer of 3 doubles per record, owned by the caller; dt are the per-run level-0 time steps
+ * buffer of claw_reflux_buffer_size doubles (3 per record for the coarse parts, then 3 per record
+ * and fine edge for the fine parts), owned by the caller; dt are the per-run level-0 time steps
  * (the levels' own steps follow from the ratios).  Sequence per coarse step of level L-1:
  *   claw_reflux_coarse(L, q_{L-1}^n)                       (ghosts of q_{L-1}^n filled)
  *   for each substep k: claw_reflux_fine(L, q_L^k, q_{L-1}^n) (ghosts of q_L^k filled)
  *   claw_average_down(L, ...), then claw_reflux_apply(L, q_{L-1}^{n+1}).
  * Errors: CLAW_EINVAL (medium = 1, NULL pointers, level 0), CLAW_ESTATE, CLAW_ECUDA. */
-int claw_reflux_count(claw_ctx* ctx, int32_t fine_level);   /* records, or minus an error code */
-/* buf := minus the coarse part (A-dQ_e + F~_e, or -A+dQ_e + F~_e for C right of e) of each record */
+int claw_reflux_count(claw_ctx* ctx, int32_t fine_level);         /* records, or minus an error code */
+int claw_reflux_buffer_size(claw_ctx* ctx, int32_t fine_level);   /* doubles of buf, or minus an error */
+/* buf := minus the coarse part (A-dQ_e + F~_e, or -A+dQ_e + F~_e for C right of e) of each record,
+ * and zero fine parts */
 int claw_reflux_coarse(claw_ctx* ctx, int32_t fine_level, const double* q_c_old, const double* dt,
                        double* buf, void* stream);
-/* buf += (1/r^2) sum over the record's r fine edges of the fine part, from the fine state q_f of
- * one substep and the coarse state q_c_old the coarse step started from */
+/* the fine part of each record's r fine edges (one slot each) += that of one substep, from the
+ * fine state q_f of the substep and the coarse state q_c_old the coarse step started from */
 int claw_reflux_fine(claw_ctx* ctx, int32_t fine_level, const double* q_f, const double* q_c_old,
                      const double* dt, double* buf, void* stream);
-/* q_c_new of every corrected coarse cell += -side (dt_c / h) buf, summed per cell in table order
- * (deterministic) */
+/* q_c_new of every corrected coarse cell += -side (dt_c / h) (coarse part + (1/r^2) fine parts),
+ * summed per cell in table order (deterministic) */
 int claw_reflux_apply(claw_ctx* ctx, int32_t fine_level, const double* buf, const double* dt,
                       double* q_c_new, void* stream);
 

@@ -53,6 +53,7 @@ _SIGNATURES = {
     "claw_medium_aux": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_medium_aux_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_reflux_count": ([VP, I32], ctypes.c_int),
+    "claw_reflux_buffer_size": ([VP, I32], ctypes.c_int),
     "claw_reflux_coarse": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_reflux_fine": ([VP, I32, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_reflux_apply": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
@@ -148,6 +149,13 @@ def claw_reflux_count(ctx, fine_level):
     n = load().claw_reflux_count(ctx, fine_level)
     if n < 0:
         raise ClawError("claw_reflux_count", -n)
+    return n
+
+
+def claw_reflux_buffer_size(ctx, fine_level):
+    n = load().claw_reflux_buffer_size(ctx, fine_level)
+    if n < 0:
+        raise ClawError("claw_reflux_buffer_size", -n)
     return n
 
 

@@ -1063,6 +1063,12 @@ int claw_reflux_count(claw_ctx* ctx, int32_t L)
     return rc ? -rc : ctx->lev[L].nreflux;
 }
 
+int claw_reflux_buffer_size(claw_ctx* ctx, int32_t L)
+{
+    int rc = reflux_check(ctx, L);
+    return rc ? -rc : 3 * ctx->lev[L].nreflux * (1 + ctx->lev[L].ratio);
+}
+
 int claw_reflux_coarse(claw_ctx* ctx, int32_t L, const double* q_c_old, const double* dt, double* buf, void* stream)
 {
     int rc = reflux_check(ctx, L);
@@ -1072,7 +1078,7 @@ int claw_reflux_coarse(claw_ctx* ctx, int32_t L, const double* q_c_old, const do
     const LevelDev& d = ctx->lev[L];
     const StepArgs k = make_args(ctx, L - 1, nullptr, nullptr, nullptr, dt, nullptr);
     ctx->launches += d.nreflux > 0;
-    return cuda_rc(launch_reflux_coarse(d.reflux, d.nreflux, ctx->lev[L - 1].patches, q_c_old, dt, buf, k,
+    return cuda_rc(launch_reflux_coarse(d.reflux, d.nreflux, ctx->lev[L - 1].patches, q_c_old, dt, buf, d.ratio, k,
                                         ctx->limiter, (cudaStream_t)stream));
 }
 
@@ -1098,8 +1104,8 @@ int claw_reflux_apply(claw_ctx* ctx, int32_t L, const double* buf, const double*
     DevGuard g(ctx->device);
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nreflux_groups > 0;
-    return cuda_rc(launch_reflux_apply(d.reflux, d.reflux_group, d.nreflux_groups, ctx->lev[L - 1].patches, dt, buf,
-                                       q_c_new, (cudaStream_t)stream));
+    return cuda_rc(launch_reflux_apply(d.reflux, d.nreflux, d.reflux_group, d.nreflux_groups, d.ratio,
+                                       ctx->lev[L - 1].patches, dt, buf, q_c_new, (cudaStream_t)stream));
 }
 
 int claw_sync_status(claw_ctx* ctx)

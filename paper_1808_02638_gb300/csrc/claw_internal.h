@@ -171,15 +171,16 @@ cudaError_t launch_medium_aux(const PatchDev* p, int n, int max_rows, const doub
 cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, int max_rows, const double* rho,
                                       const double* K, const double* g_aux, double* g_rho,
                                       double* g_K, cudaStream_t s);
-// conservation fix (uniform medium): buf holds 3 doubles per interface record
+// conservation fix (uniform medium): buf holds 3 doubles per interface record (the coarse
+// parts) followed by 3 per record and fine edge (the fine parts, summed over the substeps)
 // (k: the scheme's order, transverse mode and uniform medium rho0, K0)
 cudaError_t launch_reflux_coarse(const RefluxRec* rec, int n, const PatchDev* cp, const double* qc, const double* dt,
-                                 double* buf, const StepArgs& k, int limiter, cudaStream_t s);
+                                 double* buf, int ratio, const StepArgs& k, int limiter, cudaStream_t s);
 cudaError_t launch_reflux_fine(const RefluxRec* rec, int n, const PatchDev* cp, const PatchDev* fp, const double* qf,
                                const double* qc, const double* dt, double* buf, int ratio, const StepArgs& k,
                                int limiter, cudaStream_t s);
-cudaError_t launch_reflux_apply(const RefluxRec* rec, const int* group, int ngroups, const PatchDev* cp,
-                                const double* dt, const double* buf, double* qc, cudaStream_t s);
+cudaError_t launch_reflux_apply(const RefluxRec* rec, int n, const int* group, int ngroups, int ratio,
+                                const PatchDev* cp, const double* dt, const double* buf, double* qc, cudaStream_t s);
 cudaError_t launch_cfl_max(const PatchDev* p, int n, int max_rows, int medium, double c0, const double* aux,
                            double* smax, cudaStream_t s);
 cudaError_t launch_dt_update(const double* minh, const double* cfl, int nruns, double* smax,

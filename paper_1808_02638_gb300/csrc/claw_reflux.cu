@@ -115,7 +115,7 @@ __device__ __forceinline__ void to_puv(int dir, const double in[3], double out[3
 template <int LIM>
 __global__ void reflux_coarse_kernel(const RefluxRec* __restrict__ recs, int n, const PatchDev* __restrict__ cp,
                                      const double* __restrict__ qc, const double* __restrict__ dt,
-                                     double* __restrict__ buf, const StepArgs k)
+                                     double* __restrict__ buf, int ratio, const StepArgs k)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -134,16 +134,21 @@ __global__ void reflux_coarse_kernel(const RefluxRec* __restrict__ recs, int n, 
     for (int m = 0; m < 3; ++m) t[m] = (R.side > 0 ? am[m] : -ap[m]) + f[m];
     to_puv(R.dir, t, o);
     for (int m = 0; m < 3; ++m) buf[3 * r + m] = -o[m];
+    for (int b = 0; b < ratio; ++b)
+        for (int m = 0; m < 3; ++m) buf[3 * (n + r * ratio + b) + m] = 0.0;
 }
 
+// one thread per (record, fine edge b): slot (r, b) of the fine part accumulates over substeps
+// (buf holds the coarse parts first, 3 per record, then the fine slots, 3 per record and edge)
 template <int LIM>
 __global__ void reflux_fine_kernel(const RefluxRec* __restrict__ recs, int n, const PatchDev* __restrict__ cp,
                                    const PatchDev* __restrict__ fp, const double* __restrict__ qf,
                                    const double* __restrict__ qc, const double* __restrict__ dt,
                                    double* __restrict__ buf, int ratio, const StepArgs k)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * ratio) return;
+    const int r = t / ratio, b = t - r * ratio;
     const RefluxRec R = recs[r];
     const PatchDev C = cp[R.cbox], F = fp[R.fbox];
     const int Wc = C.nx + 4, Wf = F.nx + 4;
@@ -155,8 +160,7 @@ __global__ void reflux_fine_kernel(const RefluxRec* __restrict__ recs, int n, co
     double qC[3];
     for (int m = 0; m < 3; ++m) qC[m] = qc[co + m * WHc];
     const int mn = R.dir == 0 ? 1 : 2;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < ratio; ++b) {
+    {
         const int fi = R.dir == 0 ? R.fi : R.fi + b, fj = R.dir == 0 ? R.fj + b : R.fj;
         const int fn = R.dir == 0 ? fi : fj, fl = R.dir == 0 ? fj : fi;
         const int e = R.side > 0 ? fn : fn + 1;   // the fine cell's west / south or east / north edge
@@ -167,18 +171,17 @@ __global__ void reflux_fine_kernel(const RefluxRec* __restrict__ recs, int n, co
         const double dp = qf[fo] - qC[0], dn = qf[fo + mn * WHf] - qC[mn];
         // A (Q_F - Q_C) in the edge's order: (K dn, dp / rho, 0)
         const double fl3[3] = {md.K * dn, dp * md.irho, 0.0};
-        double t[3], o[3];
-        for (int m = 0; m < 3; ++m) t[m] = fl3[m] + (R.side > 0 ? -ap[m] : am[m]) + f[m];
-        to_puv(R.dir, t, o);
-        for (int m = 0; m < 3; ++m) acc[m] += o[m];
+        double tt[3], o[3];
+        for (int m = 0; m < 3; ++m) tt[m] = fl3[m] + (R.side > 0 ? -ap[m] : am[m]) + f[m];
+        to_puv(R.dir, tt, o);
+        double* slot = buf + 3 * (n + t);
+        for (int m = 0; m < 3; ++m) slot[m] += o[m];
     }
-    const double w = 1.0 / ((double)ratio * ratio);
-    for (int m = 0; m < 3; ++m) buf[3 * r + m] += w * acc[m];
 }
 
 // one thread per corrected coarse cell: its records in table order (deterministic sums)
-__global__ void reflux_apply_kernel(const RefluxRec* __restrict__ recs, const int* __restrict__ group, int ng,
-                                    const PatchDev* __restrict__ cp, const double* __restrict__ dt,
+__global__ void reflux_apply_kernel(const RefluxRec* __restrict__ recs, int n, const int* __restrict__ group, int ng,
+                                    int ratio, const PatchDev* __restrict__ cp, const double* __restrict__ dt,
                                     const double* __restrict__ buf, double* __restrict__ qc)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -187,11 +190,16 @@ __global__ void reflux_apply_kernel(const RefluxRec* __restrict__ recs, const in
     const RefluxRec R0 = recs[r0];
     const PatchDev C = cp[R0.cbox];
     const double d = __ldg(dt + C.run) * C.dtscale;
+    const double w = 1.0 / ((double)ratio * ratio);
     double corr[3] = {0.0, 0.0, 0.0};
     for (int r = r0; r < r1; ++r) {
         const RefluxRec R = recs[r];
         const double s = -R.side * d * (R.dir == 0 ? C.dxinv : C.dyinv);
-        for (int m = 0; m < 3; ++m) corr[m] = fma(s, buf[3 * r + m], corr[m]);
+        for (int m = 0; m < 3; ++m) {
+            double fine = 0.0;
+            for (int b = 0; b < ratio; ++b) fine += buf[3 * (n + r * ratio + b) + m];
+            corr[m] = fma(s, fma(w, fine, buf[3 * r + m]), corr[m]);
+        }
     }
     const int W = C.nx + 4;
     const long long WH = (long long)W * (C.ny + 4);
@@ -204,15 +212,15 @@ __global__ void reflux_apply_kernel(const RefluxRec* __restrict__ recs, const in
 static inline int blocks_for(int n) { return (n + 127) / 128; }
 
 cudaError_t launch_reflux_coarse(const RefluxRec* rec, int n, const PatchDev* cp, const double* qc, const double* dt,
-                                 double* buf, const StepArgs& k, int limiter, cudaStream_t s)
+                                 double* buf, int ratio, const StepArgs& k, int limiter, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     switch (limiter) {
-    case CLAW_LIM_NONE: reflux_coarse_kernel<CLAW_LIM_NONE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
-    case CLAW_LIM_MINMOD: reflux_coarse_kernel<CLAW_LIM_MINMOD><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
-    case CLAW_LIM_SUPERBEE: reflux_coarse_kernel<CLAW_LIM_SUPERBEE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
-    case CLAW_LIM_VANLEER: reflux_coarse_kernel<CLAW_LIM_VANLEER><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
-    case CLAW_LIM_MC: reflux_coarse_kernel<CLAW_LIM_MC><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, k); break;
+    case CLAW_LIM_NONE: reflux_coarse_kernel<CLAW_LIM_NONE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_MINMOD: reflux_coarse_kernel<CLAW_LIM_MINMOD><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_SUPERBEE: reflux_coarse_kernel<CLAW_LIM_SUPERBEE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_VANLEER: reflux_coarse_kernel<CLAW_LIM_VANLEER><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_MC: reflux_coarse_kernel<CLAW_LIM_MC><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, qc, dt, buf, ratio, k); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -224,21 +232,21 @@ cudaError_t launch_reflux_fine(const RefluxRec* rec, int n, const PatchDev* cp, 
 {
     if (n <= 0) return cudaSuccess;
     switch (limiter) {
-    case CLAW_LIM_NONE: reflux_fine_kernel<CLAW_LIM_NONE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
-    case CLAW_LIM_MINMOD: reflux_fine_kernel<CLAW_LIM_MINMOD><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
-    case CLAW_LIM_SUPERBEE: reflux_fine_kernel<CLAW_LIM_SUPERBEE><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
-    case CLAW_LIM_VANLEER: reflux_fine_kernel<CLAW_LIM_VANLEER><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
-    case CLAW_LIM_MC: reflux_fine_kernel<CLAW_LIM_MC><<<blocks_for(n), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_NONE: reflux_fine_kernel<CLAW_LIM_NONE><<<blocks_for(n * ratio), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_MINMOD: reflux_fine_kernel<CLAW_LIM_MINMOD><<<blocks_for(n * ratio), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_SUPERBEE: reflux_fine_kernel<CLAW_LIM_SUPERBEE><<<blocks_for(n * ratio), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_VANLEER: reflux_fine_kernel<CLAW_LIM_VANLEER><<<blocks_for(n * ratio), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
+    case CLAW_LIM_MC: reflux_fine_kernel<CLAW_LIM_MC><<<blocks_for(n * ratio), 128, 0, s>>>(rec, n, cp, fp, qf, qc, dt, buf, ratio, k); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_reflux_apply(const RefluxRec* rec, const int* group, int ngroups, const PatchDev* cp,
-                                const double* dt, const double* buf, double* qc, cudaStream_t s)
+cudaError_t launch_reflux_apply(const RefluxRec* rec, int n, const int* group, int ngroups, int ratio,
+                                const PatchDev* cp, const double* dt, const double* buf, double* qc, cudaStream_t s)
 {
     if (ngroups <= 0) return cudaSuccess;
-    reflux_apply_kernel<<<blocks_for(ngroups), 128, 0, s>>>(rec, group, ngroups, cp, dt, buf, qc);
+    reflux_apply_kernel<<<blocks_for(ngroups), 128, 0, s>>>(rec, n, group, ngroups, ratio, cp, dt, buf, qc);
     return cudaGetLastError();
 }
 

@@ -111,8 +111,8 @@ class Hierarchy:
         self.reflux = bool(reflux)
         if self.reflux and self.medium:
             raise ValueError("the conservation fix needs the uniform medium (conservation form)")
-        # per fine level: 3 doubles per interface record of the conservation fix
-        self.rbuf = [None] + [torch.zeros(max(1, 3 * claw.claw_reflux_count(self.ctx, L)), dtype=torch.float64,
+        # per fine level: the conservation fix's coarse and fine parts of every interface record
+        self.rbuf = [None] + [torch.zeros(max(1, claw.claw_reflux_buffer_size(self.ctx, L)), dtype=torch.float64,
                                           device=self.dev) if self.reflux else None
                               for L in range(1, self.nlev)]
         self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)

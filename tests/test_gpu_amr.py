@@ -211,3 +211,6 @@ def test_reflux_needs_the_uniform_medium():
     with pytest.raises(claw.ClawError) as e:
         claw.claw_reflux_coarse(H.ctx, 1, H.q[0][0], H.dt, buf)
     assert e.value.status == claw.CLAW_EINVAL
+    with pytest.raises(claw.ClawError) as e:
+        claw.claw_reflux_buffer_size(H.ctx, 1)
+    assert e.value.status == claw.CLAW_EINVAL
