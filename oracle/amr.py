@@ -300,6 +300,31 @@ class OracleHierarchy:
                 level_fill_ghost_adjoint(_boxes(lev, lev.coff), g, 1, lev.NX, lev.NY, self.run.bc, copy_only=True)
         return lam, g_rho, g_K
 
+    # ------------------------------------------------------------ regridding (Sec. 2.2)
+    def regrid(self, tol, buffer, cutoff, max_size, nest=2):
+        """Rebuilds levels 1.. top-down from the current state (all levels at the same time):
+        flags of level L-1 (oracle.regrid.flag_level, ghosts filled first), grown by `buffer`,
+        kept `nest` cells inside level L-1, clustered with `cutoff` and `max_size` (fine cells);
+        the new level L takes old level-L values where it had them, else the coarse interpolation.
+        Uniform medium (constant coefficient pools)."""
+        from .regrid import new_boxes, transfer
+        run = self.run
+        for Lf in range(1, len(self.levels)):
+            coarse = self.levels[Lf - 1]
+            if Lf - 1 == 0:
+                self.fill(0, self.q[0])
+            else:
+                self.fill(Lf - 1, self.q[Lf - 1], self.q[Lf - 2], self.q[Lf - 2], 0.0)
+            old = self.levels[Lf]
+            boxes = new_boxes(coarse, self.q[Lf - 1], tol, buffer, cutoff, max_size, nest, old.ratio)
+            new = type(old)(old.NX, old.NY, old.dx, old.dy, boxes, old.ratio)   # the caller's level type
+            self.q[Lf] = transfer(old, self.q[Lf], new, coarse, self.q[Lf - 1], run.bc)
+            self.rho[Lf] = np.full(new.csize, float(self.rho[Lf].flat[0]) if self.rho[Lf].size else 1.0)
+            self.K[Lf] = np.full(new.csize, float(self.K[Lf].flat[0]) if self.K[Lf].size else 1.0)
+            self.levels[Lf] = new
+        self._iface = {Lf: interface(self.levels, Lf, run.bc) for Lf in range(1, len(self.levels))} \
+            if self.reflux else {}
+
     def interior(self, L, n):
         lev = self.levels[L]
         nx, ny = int(lev.boxes[n][2]), int(lev.boxes[n][3])
