@@ -259,6 +259,36 @@ int claw_reflux_fine(claw_ctx* ctx, int32_t fine_level, const double* q_f, const
 int claw_reflux_apply(claw_ctx* ctx, int32_t fine_level, const double* buf, const double* dt,
                       double* q_c_new, void* stream);
 
+/* ---- Regridding (Sec. 2.2: every K steps the finer levels are regenerated from flagged cells
+ * clustered with the algorithm of Berger and Rigoutsos; Sec. 4.3: cutoff and regrid interval).
+ * The flag grid of a level holds, for each run with that level, NX x NY bytes of the level's
+ * index space, row-major, the runs back to back in run order.  Levels are rebuilt top-down:
+ * flags of level L -> claw_regrid_boxes -> claw_set_level(L+1, new boxes) ->
+ * claw_regrid_transfer(L+1, old boxes, ...). */
+long long claw_flag_grid_size(claw_ctx* ctx, int32_t level);   /* bytes, or minus an error code */
+/* flags[cell] = 1 where some component of q differs from a face neighbour by more than tol, 0
+ * elsewhere, for every interior cell of the level's boxes (ghosts of q filled; other bytes of
+ * the grid are not written).  flags: device pointer.  Errors: CLAW_EINVAL, CLAW_ESTATE. */
+int claw_flag_cells(claw_ctx* ctx, int32_t level, const double* q, double tol, uint8_t* flags, void* stream);
+/* Host only.  New boxes of level+1 for run `run` from its flag grid of `level` (host pointer):
+ * the flags grown by `buffer` cells (square neighbourhood, clipped to the domain), kept where
+ * the square of radius `nest` around the cell lies in the level's boxes (the domain outside
+ * counts as covered), then clustered in level cells: a box is accepted when flags fill at least
+ * `cutoff` of it and no side exceeds max_size / ratio; otherwise it is cut at a hole of a row or
+ * column signature (the one nearest the middle), else at the strongest sign change of a
+ * signature's second difference, else at the middle of its longer side.  Writes (ilo, jlo, nx,
+ * ny) in level+1 cells to boxes[4k..4k+3].  Returns the count, -CLAW_ENOMEM when more than
+ * max_boxes, -CLAW_EINVAL / -CLAW_ESTATE on bad arguments. */
+int claw_regrid_boxes(claw_ctx* ctx, int32_t level, int32_t run, const uint8_t* flags, int32_t buffer, int32_t nest,
+                      double cutoff, int32_t max_size, int32_t* boxes, int32_t max_boxes);
+/* After claw_set_level(level, new boxes): every interior cell of the new boxes takes the value of
+ * the old level (old_boxes with their qoff in q_old, host array) where an old box held it, else
+ * the conservative space interpolation from q_coarse (level-1, same time).  Waits for its
+ * launches (the temporary tables are freed).  Errors: CLAW_EINVAL (a new box not nested in the
+ * coarse level), CLAW_ESTATE, CLAW_ENOMEM, CLAW_ECUDA. */
+int claw_regrid_transfer(claw_ctx* ctx, int32_t level, const claw_box* old_boxes, int32_t n_old, const double* q_old,
+                         double* q_new, const double* q_coarse, void* stream);
+
 /* Waits for the context's device work, returns and clears the first device-side error
  * (CLAW_ENAN, CLAW_ECFL, CLAW_ETIMEOUT) or CLAW_OK. */
 int claw_sync_status(claw_ctx* ctx);

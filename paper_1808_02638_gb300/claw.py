@@ -52,6 +52,10 @@ _SIGNATURES = {
     "claw_set_tiling": ([VP, I32, I32, I32, I32, I32], ctypes.c_int),
     "claw_medium_aux": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_medium_aux_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_flag_grid_size": ([VP, I32], ctypes.c_longlong),
+    "claw_flag_cells": ([VP, I32, VP, ctypes.c_double, VP, VP], ctypes.c_int),
+    "claw_regrid_boxes": ([VP, I32, I32, VP, I32, I32, ctypes.c_double, I32, VP, I32], ctypes.c_int),
+    "claw_regrid_transfer": ([VP, I32, VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_reflux_count": ([VP, I32], ctypes.c_int),
     "claw_reflux_buffer_size": ([VP, I32], ctypes.c_int),
     "claw_reflux_coarse": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
@@ -143,6 +147,37 @@ def claw_set_tiling(ctx, level: int, tx: int, ty: int, staging: int, threads: in
 
 def claw_medium_aux(ctx, level, rho, K, aux, stream=None):
     _check("claw_medium_aux", load().claw_medium_aux(ctx, level, _ptr(rho), _ptr(K), _ptr(aux), _stream(stream)))
+
+
+def claw_flag_grid_size(ctx, level):
+    n = load().claw_flag_grid_size(ctx, level)
+    if n < 0:
+        raise ClawError("claw_flag_grid_size", int(-n))
+    return int(n)
+
+
+def claw_flag_cells(ctx, level, q, tol, flags, stream=None):
+    _check("claw_flag_cells", load().claw_flag_cells(ctx, level, _ptr(q), float(tol), _ptr(flags), _stream(stream)))
+
+
+def claw_regrid_boxes(ctx, level, run, flags_host, buffer, nest, cutoff, max_size):
+    """new (ilo, jlo, nx, ny) boxes of level+1 for one run from its host flag grid (numpy uint8)"""
+    import numpy as np
+    f = np.ascontiguousarray(flags_host, dtype=np.uint8)
+    cap = max(16, f.size // 4)
+    out = np.zeros(4 * cap, dtype=np.int32)
+    n = load().claw_regrid_boxes(ctx, level, run, f.ctypes.data_as(ctypes.c_void_p), int(buffer), int(nest),
+                                 float(cutoff), int(max_size), out.ctypes.data_as(ctypes.c_void_p), cap)
+    if n < 0:
+        raise ClawError("claw_regrid_boxes", -n)
+    return [tuple(int(v) for v in out[4 * k:4 * k + 4]) for k in range(n)]
+
+
+def claw_regrid_transfer(ctx, level, old_boxes, q_old, q_new, q_coarse, stream=None):
+    arr = (claw_box * max(1, len(old_boxes)))(*old_boxes)
+    _check("claw_regrid_transfer", load().claw_regrid_transfer(ctx, level, ctypes.cast(arr, ctypes.c_void_p),
+                                                               len(old_boxes), _ptr(q_old), _ptr(q_new),
+                                                               _ptr(q_coarse), _stream(stream)))
 
 
 def claw_reflux_count(ctx, fine_level):

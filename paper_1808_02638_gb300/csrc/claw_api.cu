@@ -12,6 +12,7 @@
 #include <map>
 #include <new>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "claw_internal.h"
@@ -161,6 +162,8 @@ void free_level(claw_ctx* ctx, int L)
     cudaFree(d.avgs);
     cudaFree(d.reflux);
     cudaFree(d.reflux_group);
+    cudaFree(d.flagboxes);
+    d.flagboxes = nullptr;
     d.reflux = nullptr;
     d.reflux_group = nullptr;
     d.nreflux = d.nreflux_groups = 0;
@@ -251,6 +254,35 @@ struct GhostEntry {
 };
 
 // ghost tasks of one level: copy rectangles and interpolated cells
+// interpolation of the fine cell (si, sj) of level L (inside the domain) from level L-1 into
+// the element dst of plane stride dplane; flags: sign flips of the destination (walls)
+int make_interp(claw_ctx* ctx, int L, const claw_problem& pr, const Locator& cl, long long dst, long long dplane,
+                int si, int sj, int flags, InterpCell& c)
+{
+    const int rr = ctx->lev[L].ratio;
+    const int cNX = level_nx(pr, L - 1), cNY = level_ny(pr, L - 1);
+    const int I = floordiv(si, rr), J = floordiv(sj, rr);
+    const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
+    std::memset(&c, 0, sizeof(c));
+    c.dst = dst;
+    c.dplane = dplane;
+    for (int s = 0; s < 5; ++s) {
+        int cfx, cfy;
+        const int ci = bc_map(I + di[s], cNX, pr.bc[0], pr.bc[1], &cfx);
+        const int cj = bc_map(J + dj[s], cNY, pr.bc[2], pr.bc[3], &cfy);
+        const int m = cl.find(ci, cj);
+        if (m < 0) return CLAW_EINVAL;
+        const claw_box& cb = ctx->lev[L - 1].boxes[m];
+        c.src[s] = cell_off(cb, ci, cj);
+        c.splane[s] = plane_of(cb);
+        c.sflags[s] = cfx | (cfy << 1);
+    }
+    c.xi = ((double)(si - I * rr) + 0.5) / rr - 0.5;
+    c.eta = ((double)(sj - J * rr) + 0.5) / rr - 0.5;
+    c.flags = flags;
+    return CLAW_OK;
+}
+
 constexpr int kRectRows = 32;          // copy rectangles are split into pieces of at most this many rows
 constexpr long long kBlockCells = 256;   // cells per block of the copy kernel (about): one batch per thread
 
@@ -290,28 +322,9 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
                 }
                 // space-time interpolation from level L-1 at the fine cell (si, sj)
                 if (L == 0) return CLAW_EINVAL;
-                const int rr = d.ratio;
-                const int cNX = level_nx(pr, L - 1), cNY = level_ny(pr, L - 1);
-                const int I = floordiv(si, rr), J = floordiv(sj, rr);
-                const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
                 InterpCell c;
-                std::memset(&c, 0, sizeof(c));
-                c.dst = cell_off(b, gi, gj);
-                c.dplane = plane_of(b);
-                for (int s = 0; s < 5; ++s) {
-                    int cfx, cfy;
-                    const int ci = bc_map(I + di[s], cNX, pr.bc[0], pr.bc[1], &cfx);
-                    const int cj = bc_map(J + dj[s], cNY, pr.bc[2], pr.bc[3], &cfy);
-                    const int m = cloc[b.run].find(ci, cj);
-                    if (m < 0) return CLAW_EINVAL;   // not properly nested
-                    const claw_box& cb = ctx->lev[L - 1].boxes[m];
-                    c.src[s] = cell_off(cb, ci, cj);
-                    c.splane[s] = plane_of(cb);
-                    c.sflags[s] = cfx | (cfy << 1);
-                }
-                c.xi = ((double)(si - I * rr) + 0.5) / rr - 0.5;
-                c.eta = ((double)(sj - J * rr) + 0.5) / rr - 0.5;
-                c.flags = fx | (fy << 1);
+                if (make_interp(ctx, L, pr, cloc[b.run], cell_off(b, gi, gj), plane_of(b), si, sj, fx | (fy << 1), c))
+                    return CLAW_EINVAL;   // not properly nested
                 cells.push_back(c);
             }
         // row runs of copies (consecutive ghosts of a row with one source box, one sign and a
@@ -614,6 +627,125 @@ int check_step_args(claw_ctx* ctx, int L, const double* q_old, const double* q_n
     if (!q_old || !q_new || !dt || !smax || q_old == q_new) return CLAW_EINVAL;
     if (ctx->medium == 1 && !aux) return CLAW_EINVAL;
     return CLAW_OK;
+}
+
+// ------------------------------------------------------------------ regridding (host)
+// Berger-Rigoutsos clustering of a flag grid (row-major NY x NX): a box is accepted when its
+// flags fill at least `cutoff` of it and it fits max_size; otherwise it is cut at a hole of a
+// signature (the hole nearest the middle), else at the strongest sign change of a signature's
+// second difference, else at the middle of its longer side, and both parts are processed again.
+struct IBox {
+    int i0, j0, nx, ny;
+};
+
+int hole_cut(const std::vector<long long>& sig)
+{
+    const int n = (int)sig.size();
+    int best = -1;
+    for (int k = 1; k < n - 1; ++k) {
+        if (sig[k] != 0) continue;
+        if (best < 0 || std::abs(2 * k + 1 - n) < std::abs(2 * best + 1 - n)) best = k;
+    }
+    if (best < 0) return -1;
+    return (2 * best + 1 >= n) ? best : best + 1;
+}
+
+// (strength, cut) of the strongest sign change of the second difference, cut -1 when none
+std::pair<long long, int> inflection_cut(const std::vector<long long>& sig)
+{
+    const int n = (int)sig.size();
+    std::pair<long long, int> best(-1, -1);
+    if (n < 4) return best;
+    std::vector<long long> lap(n - 2);
+    for (int t = 0; t < n - 2; ++t) lap[t] = sig[t] - 2 * sig[t + 1] + sig[t + 2];
+    for (int t = 0; t + 1 < n - 2; ++t) {
+        const long long a = lap[t], b = lap[t + 1];
+        if ((a < 0 && b > 0) || (a > 0 && b < 0)) {
+            const long long st = a > b ? a - b : b - a;
+            if (best.second < 0 || st > best.first) best = {st, t + 2};
+        }
+    }
+    return best;
+}
+
+std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int NY, double cutoff, int max_size)
+{
+    std::vector<IBox> out, stack{IBox{0, 0, NX, NY}};
+    auto at = [&](int i, int j) { return f[(size_t)j * NX + i] != 0; };
+    while (!stack.empty()) {
+        IBox b = stack.back();
+        stack.pop_back();
+        int ci0 = -1, ci1 = -1, cj0 = -1, cj1 = -1;
+        for (int j = b.j0; j < b.j0 + b.ny; ++j)
+            for (int i = b.i0; i < b.i0 + b.nx; ++i)
+                if (at(i, j)) {
+                    if (ci0 < 0 || i < ci0) ci0 = i;
+                    if (i > ci1) ci1 = i;
+                    if (cj0 < 0) cj0 = j;
+                    cj1 = j;
+                }
+        if (ci0 < 0) continue;
+        b = IBox{ci0, cj0, ci1 - ci0 + 1, cj1 - cj0 + 1};
+        std::vector<long long> sx(b.nx, 0), sy(b.ny, 0);
+        long long count = 0;
+        for (int j = 0; j < b.ny; ++j)
+            for (int i = 0; i < b.nx; ++i)
+                if (at(b.i0 + i, b.j0 + j)) {
+                    ++sx[i];
+                    ++sy[j];
+                    ++count;
+                }
+        const double eff = (double)count / (double)((long long)b.nx * b.ny);
+        if (eff >= cutoff && b.nx <= max_size && b.ny <= max_size) {
+            out.push_back(b);
+            continue;
+        }
+        int dir = -1, k = -1;
+        if (eff < cutoff) {
+            const int kx = hole_cut(sx), ky = hole_cut(sy);
+            if (kx >= 0) {
+                dir = 0;
+                k = kx;
+            } else if (ky >= 0) {
+                dir = 1;
+                k = ky;
+            } else {
+                const auto ix = inflection_cut(sx), iy = inflection_cut(sy);
+                if (ix.second >= 0 && (iy.second < 0 || ix.first >= iy.first)) {
+                    dir = 0;
+                    k = ix.second;
+                } else if (iy.second >= 0) {
+                    dir = 1;
+                    k = iy.second;
+                }
+            }
+        }
+        if (dir < 0) {
+            if (b.nx >= b.ny) {
+                dir = 0;
+                k = b.nx / 2;
+            } else {
+                dir = 1;
+                k = b.ny / 2;
+            }
+        }
+        if (dir == 0) {
+            stack.push_back(IBox{b.i0 + k, b.j0, b.nx - k, b.ny});
+            stack.push_back(IBox{b.i0, b.j0, k, b.ny});
+        } else {
+            stack.push_back(IBox{b.i0, b.j0 + k, b.nx, b.ny - k});
+            stack.push_back(IBox{b.i0, b.j0, b.nx, k});
+        }
+    }
+    return out;
+}
+
+long long flag_grid_offset(const claw_ctx* ctx, int L, int run)
+{
+    long long off = 0;
+    for (int r = 0; r < run; ++r)
+        if (L < ctx->runs[r].nlev) off += (long long)level_nx(ctx->runs[r], L) * level_ny(ctx->runs[r], L);
+    return off;
 }
 
 }  // namespace
@@ -1106,6 +1238,139 @@ int claw_reflux_apply(claw_ctx* ctx, int32_t L, const double* buf, const double*
     ctx->launches += d.nreflux_groups > 0;
     return cuda_rc(launch_reflux_apply(d.reflux, d.nreflux, d.reflux_group, d.nreflux_groups, d.ratio,
                                        ctx->lev[L - 1].patches, dt, buf, q_c_new, (cudaStream_t)stream));
+}
+
+long long claw_flag_grid_size(claw_ctx* ctx, int32_t L)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV) return -CLAW_EINVAL;
+    return flag_grid_offset(ctx, L, ctx->nruns);
+}
+
+int claw_flag_cells(claw_ctx* ctx, int32_t L, const double* q, double tol, uint8_t* flags, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !q || !flags || !(tol >= 0.0)) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    DevGuard g(ctx->device);
+    LevelDev& d = ctx->lev[L];
+    if (d.nboxes == 0) return CLAW_OK;
+    if (!d.flagboxes) {
+        std::vector<FlagBox> fb(d.nboxes);
+        for (int n = 0; n < d.nboxes; ++n) {
+            const claw_box& b = d.boxes[n];
+            const int NX = level_nx(ctx->runs[b.run], L);
+            fb[n].qoff = b.qoff;
+            fb[n].goff = flag_grid_offset(ctx, L, b.run) + (long long)b.jlo * NX + b.ilo;
+            fb[n].nx = b.nx;
+            fb[n].ny = b.ny;
+            fb[n].pitch = NX;
+            fb[n].pad = 0;
+        }
+        int rc = upload(&d.flagboxes, fb);
+        if (rc) return rc;
+    }
+    ctx->launches += 1;
+    return cuda_rc(launch_flags(d.flagboxes, d.nboxes, d.max_rows, q, tol, flags, (cudaStream_t)stream));
+}
+
+int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flags, int32_t buffer, int32_t nest,
+                      double cutoff, int32_t max_size, int32_t* boxes, int32_t max_boxes)
+{
+    if (!ctx || L < 0 || L + 1 >= CLAW_MAXLEV || run < 0 || run >= ctx->nruns || !flags || buffer < 0 || nest < 0 ||
+        !(cutoff > 0.0 && cutoff <= 1.0) || max_size < 1 || max_boxes < 0 || (max_boxes > 0 && !boxes))
+        return -CLAW_EINVAL;
+    if (!ctx->set[L]) return -CLAW_ESTATE;
+    const claw_problem& p = ctx->runs[run];
+    if (L + 1 >= p.nlev) return -CLAW_EINVAL;
+    const int NX = level_nx(p, L), NY = level_ny(p, L), r = p.ratio[L + 1];
+    // flags grown by `buffer` cells (square neighbourhood), clipped to the domain
+    std::vector<unsigned char> f((size_t)NX * NY, 0);
+    for (int j = 0; j < NY; ++j)
+        for (int i = 0; i < NX; ++i) {
+            if (!flags[(size_t)j * NX + i]) continue;
+            for (int jj = std::max(0, j - buffer); jj <= std::min(NY - 1, j + buffer); ++jj)
+                for (int ii = std::max(0, i - buffer); ii <= std::min(NX - 1, i + buffer); ++ii)
+                    f[(size_t)jj * NX + ii] = 1;
+        }
+    // keep cells `nest` cells inside the level's coverage (the domain outside counts as covered)
+    std::vector<unsigned char> cov((size_t)NX * NY, 0);
+    for (const claw_box& b : ctx->lev[L].boxes)
+        if (b.run == run)
+            for (int j = b.jlo; j < b.jlo + b.ny; ++j)
+                for (int i = b.ilo; i < b.ilo + b.nx; ++i) cov[(size_t)j * NX + i] = 1;
+    for (int j = 0; j < NY; ++j)
+        for (int i = 0; i < NX; ++i) {
+            if (!f[(size_t)j * NX + i]) continue;
+            bool ok = true;
+            for (int jj = j - nest; jj <= j + nest && ok; ++jj)
+                for (int ii = i - nest; ii <= i + nest && ok; ++ii)
+                    if (ii >= 0 && ii < NX && jj >= 0 && jj < NY && !cov[(size_t)jj * NX + ii]) ok = false;
+            if (!ok) f[(size_t)j * NX + i] = 0;
+        }
+    const std::vector<IBox> out = cluster_flags(f, NX, NY, cutoff, std::max(1, max_size / r));
+    if ((long long)out.size() > max_boxes) return -CLAW_ENOMEM;
+    for (size_t k = 0; k < out.size(); ++k) {
+        boxes[4 * k] = out[k].i0 * r;
+        boxes[4 * k + 1] = out[k].j0 * r;
+        boxes[4 * k + 2] = out[k].nx * r;
+        boxes[4 * k + 3] = out[k].ny * r;
+    }
+    return (int)out.size();
+}
+
+int claw_regrid_transfer(claw_ctx* ctx, int32_t L, const claw_box* old_boxes, int32_t n_old, const double* q_old,
+                         double* q_new, const double* q_coarse, void* stream)
+{
+    if (!ctx || L < 1 || L >= CLAW_MAXLEV || n_old < 0 || (n_old > 0 && (!old_boxes || !q_old)) || !q_new ||
+        !q_coarse)
+        return CLAW_EINVAL;
+    if (!ctx->set[L] || !ctx->set[L - 1]) return CLAW_ESTATE;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    std::vector<claw_box> olds(old_boxes, old_boxes + n_old);
+    std::vector<Locator> oloc(ctx->nruns), cloc(ctx->nruns);
+    for (int q = 0; q < ctx->nruns; ++q) {
+        oloc[q].boxes = &olds;
+        cloc[q].boxes = &ctx->lev[L - 1].boxes;
+    }
+    for (int n = 0; n < n_old; ++n) {
+        if (olds[n].run < 0 || olds[n].run >= ctx->nruns) return CLAW_EINVAL;
+        oloc[olds[n].run].add(olds[n], n);
+    }
+    for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
+        cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
+    std::vector<CellCopy> copies;
+    std::vector<InterpCell> cells;
+    for (const claw_box& b : d.boxes) {
+        const claw_problem& pr = ctx->runs[b.run];
+        for (int gj = b.jlo; gj < b.jlo + b.ny; ++gj)
+            for (int gi = b.ilo; gi < b.ilo + b.nx; ++gi) {
+                const int m = oloc[b.run].find(gi, gj);
+                if (m >= 0) {
+                    copies.push_back(CellCopy{cell_off(b, gi, gj), cell_off(olds[m], gi, gj), plane_of(b),
+                                              plane_of(olds[m])});
+                    continue;
+                }
+                InterpCell c;
+                if (make_interp(ctx, L, pr, cloc[b.run], cell_off(b, gi, gj), plane_of(b), gi, gj, 0, c))
+                    return CLAW_EINVAL;   // the new box is not nested in the coarse level
+                cells.push_back(c);
+            }
+    }
+    CellCopy* dc = nullptr;
+    InterpCell* di = nullptr;
+    int rc = upload(&dc, copies);
+    if (!rc) rc = upload(&di, cells);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = launch_cell_copy(dc, (int)copies.size(), q_old, q_new, s);
+        if (e == cudaSuccess) e = launch_fill_interp(di, (int)cells.size(), q_new, q_coarse, q_coarse, 0.0, s);
+        ctx->launches += (copies.size() > 0) + (cells.size() > 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the tables are freed below
+    }
+    cudaFree(dc);
+    cudaFree(di);
+    return rc ? rc : cuda_rc(e);
 }
 
 int claw_sync_status(claw_ctx* ctx)

@@ -65,6 +65,16 @@ struct RefluxRec {
     short dir, side;
 };
 
+// Regridding: a box of the level being flagged (interior rows of the flag grid start at goff,
+// rows pitch bytes apart) and a cell copied from an old fine pool into a new one.
+struct FlagBox {
+    long long qoff, goff;
+    int nx, ny, pitch, pad;
+};
+struct CellCopy {
+    long long dst, src, dplane, splane;
+};
+
 // One fine ghost cell filled by space-time interpolation from the coarser level.
 struct InterpCell {
     long long dst;        // plane-0 element of the fine ghost cell
@@ -109,6 +119,7 @@ struct LevelDev {
     int nreflux = 0;
     int* reflux_group = nullptr;  // [ngroups + 1]: records of coarse cell g are [group[g], group[g+1])
     int nreflux_groups = 0;
+    FlagBox* flagboxes = nullptr; // the boxes as flag-grid writers (built on first use)
     // host copies
     std::vector<claw_box> boxes;
     std::vector<PatchDev> hpatches;
@@ -171,6 +182,11 @@ cudaError_t launch_medium_aux(const PatchDev* p, int n, int max_rows, const doub
 cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, int max_rows, const double* rho,
                                       const double* K, const double* g_aux, double* g_rho,
                                       double* g_K, cudaStream_t s);
+// regridding
+cudaError_t launch_flags(const FlagBox* boxes, int nb, int max_rows, const double* q, double tol,
+                         unsigned char* flags, cudaStream_t s);
+cudaError_t launch_cell_copy(const CellCopy* c, int n, const double* src, double* dst, cudaStream_t s);
+
 // conservation fix (uniform medium): buf holds 3 doubles per interface record (the coarse
 // parts) followed by 3 per record and fine edge (the fine parts, summed over the substeps)
 // (k: the scheme's order, transverse mode and uniform medium rho0, K0)

@@ -59,23 +59,9 @@ class Hierarchy:
         self.K = []
         self.boxes = []    # per level list of claw_box
         self.layout = []   # per level list of (run, qbase, cbase)
+        self.tiling = tiling
         for L in range(self.nlev):
-            boxes, qb, cb = [], 0, 0
-            lay = []
-            for ri, r in enumerate(runs):
-                if L >= len(r.levels):
-                    continue
-                lev = r.levels[L]
-                lay.append((ri, qb, cb))
-                for n, b in enumerate(lev.boxes):
-                    bx = claw.claw_box()
-                    bx.run = ri
-                    bx.ilo, bx.jlo, bx.nx, bx.ny = (int(v) for v in b)
-                    bx.qoff = qb + int(lev.qoff[n])
-                    bx.coff = cb + int(lev.coff[n])
-                    boxes.append(bx)
-                qb += _align(lev.qsize)
-                cb += _align(lev.csize)
+            boxes, lay, qb, cb = self._layout(L)
             self.boxes.append(boxes)
             self.layout.append(lay)
             claw.claw_set_level(self.ctx, L, boxes)
@@ -117,6 +103,77 @@ class Hierarchy:
                               for L in range(1, self.nlev)]
         self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)
         self.fused = False       # one-level hierarchies: step with Eq. cfl on the device, then push ghosts
+        self._ghosts_ready = False
+
+    def _layout(self, L):
+        """(claw boxes, [(run, q base, coefficient base)], q size, coefficient size) of level L"""
+        boxes, qb, cb = [], 0, 0
+        lay = []
+        for ri, r in enumerate(self.runs):
+            if L >= len(r.levels):
+                continue
+            lev = r.levels[L]
+            lay.append((ri, qb, cb))
+            for n, b in enumerate(lev.boxes):
+                bx = claw.claw_box()
+                bx.run = ri
+                bx.ilo, bx.jlo, bx.nx, bx.ny = (int(v) for v in b)
+                bx.qoff = qb + int(lev.qoff[n])
+                bx.coff = cb + int(lev.coff[n])
+                boxes.append(bx)
+            qb += _align(lev.qsize)
+            cb += _align(lev.csize)
+        return boxes, lay, qb, cb
+
+    # -------------------------------------------------------------- regridding (Sec. 2.2)
+    def regrid(self, tol, buffer, cutoff, max_size, nest=2):
+        """Rebuilds levels 1.. top-down from the current state (every level at the same time, as
+        after a coarse step): the flags of level L-1 (claw_flag_cells: some component differs
+        from a face neighbour by more than tol), grown by `buffer` cells and kept `nest` cells
+        inside level L-1, are clustered into the new boxes of level L (claw_regrid_boxes: cutoff,
+        max_size in level-L cells); the new level takes the old level's values where it had them
+        and the conservative interpolation from level L-1 elsewhere (claw_regrid_transfer).
+        Uniform medium.  Captured graphs and autotuned tilings of the rebuilt levels are stale."""
+        if self.medium:
+            raise ValueError("regridding is built for the uniform medium")
+        for Lf in range(1, self.nlev):
+            Lc = Lf - 1
+            qc = self.q[Lc][self.cur[Lc]]
+            if Lc == 0:
+                claw.claw_fill_ghost(self.ctx, 0, qc)
+            else:
+                qcc = self.q[Lc - 1][self.cur[Lc - 1]]
+                claw.claw_fill_ghost(self.ctx, Lc, qc, qcc, qcc, 0.0)
+            flags = torch.zeros(max(1, claw.claw_flag_grid_size(self.ctx, Lc)), dtype=torch.uint8, device=self.dev)
+            claw.claw_flag_cells(self.ctx, Lc, qc, tol, flags)
+            fh = flags.cpu().numpy()
+            off = 0
+            for ri, run in enumerate(self.runs):
+                if Lc >= len(run.levels):
+                    continue
+                lc = run.levels[Lc]
+                grid = fh[off:off + lc.NX * lc.NY].reshape(lc.NY, lc.NX)
+                off += lc.NX * lc.NY
+                if Lf >= len(run.levels):
+                    continue
+                nb = claw.claw_regrid_boxes(self.ctx, Lc, ri, grid, buffer, nest, cutoff, max_size)
+                old = run.levels[Lf]
+                run.levels[Lf] = inputs.Level(old.NX, old.NY, old.dx, old.dy,
+                                              np.array(nb, dtype=np.int32).reshape(-1, 4), old.ratio)
+            old_boxes, old_pool = self.boxes[Lf], self.q[Lf][self.cur[Lf]]
+            boxes, lay, qb, _ = self._layout(Lf)
+            claw.claw_set_level(self.ctx, Lf, boxes)   # also clears the finer levels' tables
+            if self.tiling is not None:
+                claw.claw_set_tiling(self.ctx, Lf, *self.tiling)
+            new = torch.zeros(max(qb, inputs.ALIGN), dtype=torch.float64, device=self.dev)
+            claw.claw_regrid_transfer(self.ctx, Lf, old_boxes, old_pool, new, qc)
+            self.boxes[Lf], self.layout[Lf] = boxes, lay
+            self.q[Lf] = [new, torch.zeros_like(new)]
+            self.cur[Lf] = 0
+            if self.reflux:
+                self.rbuf[Lf] = torch.zeros(max(1, claw.claw_reflux_buffer_size(self.ctx, Lf)),
+                                            dtype=torch.float64, device=self.dev)
+            self.__dict__.pop("_ghost_masks", None)
         self._ghosts_ready = False
 
     # -------------------------------------------------------------- stepping

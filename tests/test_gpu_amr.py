@@ -214,3 +214,108 @@ def test_reflux_needs_the_uniform_medium():
     with pytest.raises(claw.ClawError) as e:
         claw.claw_reflux_buffer_size(H.ctx, 1)
     assert e.value.status == claw.CLAW_EINVAL
+
+
+# ------------------------------------------------------------ regridding (Sec. 2.2)
+def _upload_level(H, L, pool_np):
+    import torch
+    t = H.q[L][H.cur[L]]
+    t.zero_()
+    t[:pool_np.size] = torch.from_numpy(pool_np).to(t.device)
+
+
+def test_flags_match_the_oracle_on_the_same_state():
+    import torch
+    from oracle import regrid as org
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    O = OracleHierarchy(run, q0, [inputs.const_pool(l, 1.0) for l in run.levels],
+                        [inputs.const_pool(l, 4.0) for l in run.levels])
+    for _ in range(3):
+        O.coarse_step()
+    O.fill(0, O.q[0])
+    O.fill(1, O.q[1], O.q[0], O.q[0], 0.0)
+    H = Hierarchy([run], [O.q], rho0=1.0, K0=4.0)
+    for L in (0, 1):
+        _upload_level(H, L, O.q[L])          # ghosts included: the same state on both sides
+        for tol in (0.005, 0.03):
+            flags = torch.zeros(claw.claw_flag_grid_size(H.ctx, L), dtype=torch.uint8, device=H.dev)
+            claw.claw_flag_cells(H.ctx, L, H.q[L][H.cur[L]], tol, flags)
+            lev = run.levels[L]
+            got = flags.cpu().numpy().reshape(lev.NY, lev.NX).astype(bool)
+            want = org.flag_level(lev, O.q[L], tol)
+            assert np.array_equal(got, want) and want.any()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_clustering_matches_the_oracle(seed):
+    from oracle import regrid as org
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    rng = np.random.default_rng(seed)
+    for L in (0, 1):
+        lev = run.levels[L]
+        blobs = np.zeros((lev.NY, lev.NX), bool)
+        for _ in range(6):                   # a few random blobs plus sparse noise
+            cx, cy, rx, ry = rng.integers(0, lev.NX), rng.integers(0, lev.NY), rng.integers(1, 12), rng.integers(1, 12)
+            blobs[max(0, cy - ry):cy + ry, max(0, cx - rx):cx + rx] = True
+        flags = blobs | (rng.random((lev.NY, lev.NX)) < 0.01)
+        for (buffer, cutoff, cap) in ((2, 0.7, 64), (0, 0.5, 32), (3, 0.9, 260)):
+            got = claw.claw_regrid_boxes(H.ctx, L, 0, flags.astype(np.uint8), buffer, 2, cutoff, cap)
+            f = org.dilate(flags, buffer) & org.nest_mask(lev, 2)
+            want = [(i0 * 4, j0 * 4, nx * 4, ny * 4) for (i0, j0, nx, ny) in org.cluster(f, cutoff, max(1, cap // 4))]
+            assert got == want
+
+
+def _run_with_regrid(hier, steps, every, params):
+    for k in range(steps):
+        hier.coarse_step()
+        if (k + 1) % every == 0:
+            hier.regrid(**params)
+
+
+def test_regrid_end_to_end_matches_the_oracle():
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300.solver import Hierarchy
+    params = dict(tol=0.02, buffer=2, cutoff=0.7, max_size=64, nest=2)
+    run_g, run_o = inputs.config2(), inputs.config2()   # each side rebuilds its own levels
+    q0 = [inputs.init_q(run_g, lev) for lev in run_g.levels]
+    H = Hierarchy([run_g], [q0], rho0=1.0, K0=4.0)
+    O = OracleHierarchy(run_o, q0, [inputs.const_pool(l, 1.0) for l in run_o.levels],
+                        [inputs.const_pool(l, 4.0) for l in run_o.levels])
+    H.init_dt()
+    for k in range(12):
+        H.coarse_step()
+        O.coarse_step()
+        if (k + 1) % 4 == 0:
+            H.regrid(**params)
+            O.regrid(**params)
+            for L in (1, 2):
+                assert np.array_equal(run_g.levels[L].boxes, run_o.levels[L].boxes)
+            _compare_all_levels(H, O, 0, TOLN)
+    _compare_all_levels(H, O, 0, TOLN)
+    assert H.sync_status() == 0
+
+
+def test_regrid_keeps_the_reflux_conservation():
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.Run(*inputs.PULSE_DOMAIN, bc=(1, 1, 1, 1))
+    run.levels = inputs.amr_levels(run, 32, 4, [(0.2, 0.45)], [2002])
+    q0 = _flowing_pulse(run)
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
+    H.init_dt()
+    m0 = _composite(H)
+    for k in range(6):
+        H.coarse_step()
+        if k == 2:
+            H.regrid(tol=0.02, buffer=2, cutoff=0.7, max_size=64, nest=2)
+    drift = np.abs(_composite(H) - m0)
+    # the transfer is conservative where it interpolates and the fine data it drops was
+    # averaged into the coarse level: the composite integral survives the regrid
+    assert (drift <= 1e-13 * 6.0).all(), drift
