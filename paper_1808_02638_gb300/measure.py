@@ -3,7 +3,7 @@ plain path (one launch per patch, eager) on the same hierarchy, and the adjoint'
 
   python -m paper_1808_02638_gb300.measure [names...] [--nruns N] [--ncoarse N] [--every N] [--no-plain]
 
-(names: c0 c2 c3 c4; default all; the options shrink the batched workload for a profiler)
+(names: c0 c2 c3 c4 e1; default all; the options shrink the batched workload for a profiler)
 
 Each workload reports interior cell-updates per second (a cell advanced one step on its level;
 ghost cells and halo recomputation are not counted), algorithmic HBM bytes per second (q read
@@ -247,7 +247,62 @@ def config4(nruns=64, ncoarse=100, every=20, plain=True):
                                 "functional": "sum over runs of sum p^2 over each run's 16x16 receiver"}})
 
 
-WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4}
+def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=0.002, max_size=260):
+    """Analog of the paper's benchmark (Sec. 4.1-4.2): radial pulse in a uniform medium, outflow
+    (extrapolation) boundaries, van Leer, 3 levels of ratio 2 over a 1000^2 base tiled in 4 x 4
+    patches of 250^2, patches of at most 260^2 generated by regridding (tol on neighbour
+    differences, buffer = regrid interval, cutoff 0.7, every 8 coarse steps); the fine levels are
+    built at t = 0 by regridding and set from the initial condition.  Times whole coarse steps
+    (eager launches: the hierarchy changes every regrid) including the regrids."""
+    import time
+    run = inputs.Run(*inputs.PULSE_DOMAIN, limiter=3)
+    d0 = 2.0 / base
+    step = base // 4
+    b0 = [(i, j, step, step) for j in range(0, base, step) for i in range(0, base, step)]
+    run.levels = [inputs.Level(base, base, d0, d0, b0)]
+    for L in range(1, nlev):
+        n = base * ratio ** L
+        run.levels.append(inputs.Level(n, n, 2.0 / n, 2.0 / n, np.zeros((0, 4), dtype=np.int32), ratio))
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    params = dict(tol=tol, buffer=regrid_every, cutoff=cutoff, max_size=max_size, nest=2)
+    for _ in range(nlev - 1):       # refine level by level at t = 0
+        H.regrid(**params)
+    for L, lev in enumerate(run.levels):   # the new levels take the initial condition itself
+        a = inputs.init_q(run, lev)
+        t = H.q[L][H.cur[L]]
+        t.zero_()
+        t[:a.size] = torch.from_numpy(a).to(t.device)
+    H.init_dt()
+    torch.cuda.synchronize()
+    cells = 0
+    regrid_s = 0.0
+    t0 = time.perf_counter()
+    for k in range(ncoarse):
+        cells += cell_updates_per_coarse_step(H)
+        H.coarse_step()
+        if (k + 1) % regrid_every == 0:
+            torch.cuda.synchronize()
+            r0 = time.perf_counter()
+            H.regrid(**params)
+            torch.cuda.synchronize()
+            regrid_s += time.perf_counter() - r0
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    boxes = [len(lev.boxes) for lev in run.levels]
+    ncells = [int(lev.ncells) for lev in run.levels]
+    return {"workload": f"{base}^2 base, {nlev} levels of ratio {ratio}, patches <= {max_size}^2 by regridding "
+                        f"(tol {tol}, cutoff {cutoff}, every {regrid_every} coarse steps), van Leer, radial pulse, "
+                        f"{ncoarse} coarse steps",
+            "coarse_steps": ncoarse, "simulated_time": float(ncoarse) * float(H.dt[0]),
+            "cell_updates": cells, "wall_s": wall, "cell_updates_per_s": cells / wall,
+            "regrid_s": regrid_s, "regrids": ncoarse // regrid_every,
+            "final_boxes_per_level": boxes, "final_cells_per_level": ncells,
+            "status": claw.strerror(H.sync_status()),
+            "note": "eager launches (the hierarchy changes at every regrid); wall clock includes the regrids"}
+
+
+WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4, "e1": e1}
 
 
 def run_all(names=None):
