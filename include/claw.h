@@ -274,7 +274,8 @@ int claw_flag_cells(claw_ctx* ctx, int32_t level, const double* q, double tol, u
  * the flags grown by `buffer` cells (square neighbourhood, clipped to the domain), kept where
  * the square of radius `nest` around the cell lies in the level's boxes (the domain outside
  * counts as covered), then clustered in level cells: a box is accepted when flags fill at least
- * `cutoff` of it and no side exceeds max_size / ratio; otherwise it is cut at a hole of a row or
+ * `cutoff` of it, no side exceeds max_size / ratio and all its cells pass that nesting test;
+ * otherwise it is cut at a hole of a row or
  * column signature (the one nearest the middle), else at the strongest sign change of a
  * signature's second difference, else at the middle of its longer side.  Writes (ilo, jlo, nx,
  * ny) in level+1 cells to boxes[4k..4k+3].  Returns the count, -CLAW_ENOMEM when more than

@@ -10,9 +10,10 @@ definitions:
   nest_mask       cells of level L at least `nest` cells inside level L's coverage (domain
                   edges do not count as coverage edges)
   cluster         Berger-Rigoutsos: accept the flags' bounding box when its efficiency reaches
-                  cutoff and it fits max_size; otherwise cut at a hole of a signature (the one
-                  nearest the middle), else at the strongest inflection of a signature's second
-                  difference, else at the middle of the longer side; recurse on both parts
+                  cutoff, it fits max_size and all its cells are allowed (nesting); otherwise cut
+                  at a hole of a signature (the one nearest the middle), else at the strongest
+                  inflection of a signature's second difference, else at the middle of the longer
+                  side; recurse on both parts
   regrid          levels 1.. rebuilt top-down; new fine cells copy old fine values where the old
                   level had them, else the conservative space interpolation from the coarse level
 """
@@ -104,8 +105,9 @@ def _inflection(sig):
     return best
 
 
-def cluster(flags, cutoff, max_size):
-    """boxes (i0, j0, nx, ny) covering every flagged cell of `flags` (NY, NX)"""
+def cluster(flags, cutoff, max_size, allowed=None):
+    """boxes (i0, j0, nx, ny) covering every flagged cell of `flags` (NY, NX); with `allowed`
+    (flags must lie inside it) every box lies inside it too"""
     out = []
     stack = [(0, 0, flags.shape[1], flags.shape[0])]
     while stack:
@@ -119,7 +121,8 @@ def cluster(flags, cutoff, max_size):
         j0, ny = j0 + int(rows[0]), int(rows[-1] - rows[0] + 1)
         sub = flags[j0:j0 + ny, i0:i0 + nx]
         eff = sub.sum() / float(nx * ny)
-        if eff >= cutoff and nx <= max_size and ny <= max_size:
+        inside = allowed is None or bool(allowed[j0:j0 + ny, i0:i0 + nx].all())
+        if eff >= cutoff and nx <= max_size and ny <= max_size and inside:
             out.append((i0, j0, nx, ny))
             continue
         sx = [int(v) for v in sub.sum(axis=0)]
@@ -151,9 +154,10 @@ def cluster(flags, cutoff, max_size):
 
 def new_boxes(coarse, cpool, tol, buffer, cutoff, max_size, nest, ratio):
     """fine boxes (fine index space) for the level above `coarse` from its state (ghosts filled)"""
-    f = dilate(flag_level(coarse, cpool, tol), buffer) & nest_mask(coarse, nest)
+    m = nest_mask(coarse, nest)
+    f = dilate(flag_level(coarse, cpool, tol), buffer) & m
     return [(i0 * ratio, j0 * ratio, nx * ratio, ny * ratio) for (i0, j0, nx, ny) in
-            cluster(f, cutoff, max(1, max_size // ratio))]
+            cluster(f, cutoff, max(1, max_size // ratio), m)]
 
 
 def transfer(fine_old, fpool_old, fine_new, coarse, cpool, bc):

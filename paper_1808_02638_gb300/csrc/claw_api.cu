@@ -631,7 +631,8 @@ int check_step_args(claw_ctx* ctx, int L, const double* q_old, const double* q_n
 
 // ------------------------------------------------------------------ regridding (host)
 // Berger-Rigoutsos clustering of a flag grid (row-major NY x NX): a box is accepted when its
-// flags fill at least `cutoff` of it and it fits max_size; otherwise it is cut at a hole of a
+// flags fill at least `cutoff` of it, it fits max_size and every cell of it is allowed (the
+// nesting mask, which holds all flags); otherwise it is cut at a hole of a
 // signature (the hole nearest the middle), else at the strongest sign change of a signature's
 // second difference, else at the middle of its longer side, and both parts are processed again.
 struct IBox {
@@ -668,7 +669,8 @@ std::pair<long long, int> inflection_cut(const std::vector<long long>& sig)
     return best;
 }
 
-std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int NY, double cutoff, int max_size)
+std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int NY, double cutoff, int max_size,
+                                const std::vector<unsigned char>& allowed)
 {
     std::vector<IBox> out, stack{IBox{0, 0, NX, NY}};
     auto at = [&](int i, int j) { return f[(size_t)j * NX + i] != 0; };
@@ -696,7 +698,14 @@ std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int
                     ++count;
                 }
         const double eff = (double)count / (double)((long long)b.nx * b.ny);
-        if (eff >= cutoff && b.nx <= max_size && b.ny <= max_size) {
+        bool inside = true;
+        for (int j = b.j0; j < b.j0 + b.ny && inside; ++j)
+            for (int i = b.i0; i < b.i0 + b.nx; ++i)
+                if (!allowed[(size_t)j * NX + i]) {
+                    inside = false;
+                    break;
+                }
+        if (eff >= cutoff && b.nx <= max_size && b.ny <= max_size && inside) {
             out.push_back(b);
             continue;
         }
@@ -1297,16 +1306,26 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
         if (b.run == run)
             for (int j = b.jlo; j < b.jlo + b.ny; ++j)
                 for (int i = b.ilo; i < b.ilo + b.nx; ++i) cov[(size_t)j * NX + i] = 1;
+    // uncovered cells of the square of radius `nest` around each cell, the square clipped to the
+    // domain, from a 2D prefix sum of the uncovered indicator
+    std::vector<long long> P((size_t)(NX + 1) * (NY + 1), 0);
+    for (int j = 0; j < NY; ++j)
+        for (int i = 0; i < NX; ++i)
+            P[(size_t)(j + 1) * (NX + 1) + (i + 1)] = P[(size_t)j * (NX + 1) + (i + 1)] +
+                                                     P[(size_t)(j + 1) * (NX + 1) + i] - P[(size_t)j * (NX + 1) + i] +
+                                                     (cov[(size_t)j * NX + i] ? 0 : 1);
+    std::vector<unsigned char> allowed((size_t)NX * NY, 0);
     for (int j = 0; j < NY; ++j)
         for (int i = 0; i < NX; ++i) {
-            if (!f[(size_t)j * NX + i]) continue;
-            bool ok = true;
-            for (int jj = j - nest; jj <= j + nest && ok; ++jj)
-                for (int ii = i - nest; ii <= i + nest && ok; ++ii)
-                    if (ii >= 0 && ii < NX && jj >= 0 && jj < NY && !cov[(size_t)jj * NX + ii]) ok = false;
+            const int a0 = std::max(0, i - nest), a1 = std::min(NX, i + nest + 1);
+            const int b0 = std::max(0, j - nest), b1 = std::min(NY, j + nest + 1);
+            const long long bad = P[(size_t)b1 * (NX + 1) + a1] - P[(size_t)b0 * (NX + 1) + a1] -
+                                  P[(size_t)b1 * (NX + 1) + a0] + P[(size_t)b0 * (NX + 1) + a0];
+            const bool ok = bad == 0;
+            allowed[(size_t)j * NX + i] = ok;
             if (!ok) f[(size_t)j * NX + i] = 0;
         }
-    const std::vector<IBox> out = cluster_flags(f, NX, NY, cutoff, std::max(1, max_size / r));
+    const std::vector<IBox> out = cluster_flags(f, NX, NY, cutoff, std::max(1, max_size / r), allowed);
     if ((long long)out.size() > max_boxes) return -CLAW_ENOMEM;
     for (size_t k = 0; k < out.size(); ++k) {
         boxes[4 * k] = out[k].i0 * r;

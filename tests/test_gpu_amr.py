@@ -268,8 +268,9 @@ def test_clustering_matches_the_oracle(seed):
         flags = blobs | (rng.random((lev.NY, lev.NX)) < 0.01)
         for (buffer, cutoff, cap) in ((2, 0.7, 64), (0, 0.5, 32), (3, 0.9, 260)):
             got = claw.claw_regrid_boxes(H.ctx, L, 0, flags.astype(np.uint8), buffer, 2, cutoff, cap)
-            f = org.dilate(flags, buffer) & org.nest_mask(lev, 2)
-            want = [(i0 * 4, j0 * 4, nx * 4, ny * 4) for (i0, j0, nx, ny) in org.cluster(f, cutoff, max(1, cap // 4))]
+            m = org.nest_mask(lev, 2)
+            f = org.dilate(flags, buffer) & m
+            want = [(i0 * 4, j0 * 4, nx * 4, ny * 4) for (i0, j0, nx, ny) in org.cluster(f, cutoff, max(1, cap // 4), m)]
             assert got == want
 
 

@@ -65,6 +65,23 @@ def test_cluster_splits_to_the_size_cap(rg):
     assert sorted(boxes) == sorted((i, j, 10, 10) for i in range(0, 40, 10) for j in range(0, 40, 10))
 
 
+def test_cluster_keeps_boxes_inside_the_allowed_region(rg):
+    allowed = np.zeros((30, 30), bool)
+    allowed[2:28, 2:10] = True
+    allowed[20:28, 2:28] = True           # an L-shaped region (nesting mask)
+    flags = allowed.copy()
+    flags[5:7, 5:7] = False               # efficiency below 1 everywhere near the corner
+    for cutoff in (0.5, 0.7, 0.9):
+        boxes = rg.cluster(flags, cutoff, 100, allowed)
+        cov = np.zeros_like(flags)
+        for (i0, j0, nx, ny) in boxes:
+            assert allowed[j0:j0 + ny, i0:i0 + nx].all()
+            cov[j0:j0 + ny, i0:i0 + nx] = True
+        assert (cov | ~flags).all()
+    # without the region the same flags give a box reaching outside it
+    assert any(not allowed[j0:j0 + ny, i0:i0 + nx].all() for (i0, j0, nx, ny) in rg.cluster(flags, 0.5, 100))
+
+
 @pytest.mark.parametrize("seed,density,cutoff,cap", [(1, 0.05, 0.5, 16), (2, 0.2, 0.7, 8), (3, 0.6, 0.9, 64)])
 def test_cluster_properties_on_random_flags(rg, seed, density, cutoff, cap):
     h = np.random.default_rng(seed).random((48, 40)) < density
