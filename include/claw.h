@@ -284,7 +284,9 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t level, int32_t run, const uint8_t* 
                       double cutoff, int32_t max_size, int32_t* boxes, int32_t max_boxes);
 /* After claw_set_level(level, new boxes): every interior cell of the new boxes takes the value of
  * the old level (old_boxes with their qoff in q_old, host array) where an old box held it, else
- * the conservative space interpolation from q_coarse (level-1, same time).  Waits for its
+ * the conservative space interpolation from q_coarse (level-1, same time), read from the coarse
+ * box holding the cell's parent with its ghosts, which must be filled (the new boxes lie two
+ * coarse cells inside the coarse level, as claw_regrid_boxes makes them).  Waits for its
  * launches (the temporary tables are freed).  Errors: CLAW_EINVAL (a new box not nested in the
  * coarse level), CLAW_ESTATE, CLAW_ENOMEM, CLAW_ECUDA. */
 int claw_regrid_transfer(claw_ctx* ctx, int32_t level, const claw_box* old_boxes, int32_t n_old, const double* q_old,

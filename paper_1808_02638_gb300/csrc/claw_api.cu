@@ -669,48 +669,53 @@ std::pair<long long, int> inflection_cut(const std::vector<long long>& sig)
     return best;
 }
 
+// 2D prefix sum of a 0/1 grid: S(i, j) = sum over [0, i) x [0, j)
+struct Prefix {
+    int NX = 0, NY = 0;
+    std::vector<long long> P;
+    Prefix(const std::vector<unsigned char>& g, int nx, int ny, bool invert) : NX(nx), NY(ny), P((size_t)(nx + 1) * (ny + 1), 0)
+    {
+        for (int j = 0; j < NY; ++j)
+            for (int i = 0; i < NX; ++i)
+                P[(size_t)(j + 1) * (NX + 1) + (i + 1)] = P[(size_t)j * (NX + 1) + (i + 1)] +
+                                                         P[(size_t)(j + 1) * (NX + 1) + i] - P[(size_t)j * (NX + 1) + i] +
+                                                         ((g[(size_t)j * NX + i] != 0) != invert ? 1 : 0);
+    }
+    long long sum(int i0, int j0, int i1, int j1) const   // over [i0, i1) x [j0, j1)
+    {
+        return P[(size_t)j1 * (NX + 1) + i1] - P[(size_t)j0 * (NX + 1) + i1] - P[(size_t)j1 * (NX + 1) + i0] +
+               P[(size_t)j0 * (NX + 1) + i0];
+    }
+};
+
 std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int NY, double cutoff, int max_size,
                                 const std::vector<unsigned char>& allowed)
 {
+    const Prefix F(f, NX, NY, false), BAD(allowed, NX, NY, true);
     std::vector<IBox> out, stack{IBox{0, 0, NX, NY}};
-    auto at = [&](int i, int j) { return f[(size_t)j * NX + i] != 0; };
     while (!stack.empty()) {
         IBox b = stack.back();
         stack.pop_back();
-        int ci0 = -1, ci1 = -1, cj0 = -1, cj1 = -1;
-        for (int j = b.j0; j < b.j0 + b.ny; ++j)
-            for (int i = b.i0; i < b.i0 + b.nx; ++i)
-                if (at(i, j)) {
-                    if (ci0 < 0 || i < ci0) ci0 = i;
-                    if (i > ci1) ci1 = i;
-                    if (cj0 < 0) cj0 = j;
-                    cj1 = j;
-                }
-        if (ci0 < 0) continue;
+        // trim to the flags' bounding box, from column and row counts
+        int ci0 = b.i0, ci1 = b.i0 + b.nx - 1, cj0 = b.j0, cj1 = b.j0 + b.ny - 1;
+        if (F.sum(b.i0, b.j0, b.i0 + b.nx, b.j0 + b.ny) == 0) continue;
+        while (F.sum(ci0, b.j0, ci0 + 1, b.j0 + b.ny) == 0) ++ci0;
+        while (F.sum(ci1, b.j0, ci1 + 1, b.j0 + b.ny) == 0) --ci1;
+        while (F.sum(ci0, cj0, ci1 + 1, cj0 + 1) == 0) ++cj0;
+        while (F.sum(ci0, cj1, ci1 + 1, cj1 + 1) == 0) --cj1;
         b = IBox{ci0, cj0, ci1 - ci0 + 1, cj1 - cj0 + 1};
-        std::vector<long long> sx(b.nx, 0), sy(b.ny, 0);
-        long long count = 0;
-        for (int j = 0; j < b.ny; ++j)
-            for (int i = 0; i < b.nx; ++i)
-                if (at(b.i0 + i, b.j0 + j)) {
-                    ++sx[i];
-                    ++sy[j];
-                    ++count;
-                }
+        const long long count = F.sum(b.i0, b.j0, b.i0 + b.nx, b.j0 + b.ny);
         const double eff = (double)count / (double)((long long)b.nx * b.ny);
-        bool inside = true;
-        for (int j = b.j0; j < b.j0 + b.ny && inside; ++j)
-            for (int i = b.i0; i < b.i0 + b.nx; ++i)
-                if (!allowed[(size_t)j * NX + i]) {
-                    inside = false;
-                    break;
-                }
+        const bool inside = BAD.sum(b.i0, b.j0, b.i0 + b.nx, b.j0 + b.ny) == 0;
         if (eff >= cutoff && b.nx <= max_size && b.ny <= max_size && inside) {
             out.push_back(b);
             continue;
         }
         int dir = -1, k = -1;
         if (eff < cutoff) {
+            std::vector<long long> sx(b.nx), sy(b.ny);
+            for (int i = 0; i < b.nx; ++i) sx[i] = F.sum(b.i0 + i, b.j0, b.i0 + i + 1, b.j0 + b.ny);
+            for (int j = 0; j < b.ny; ++j) sy[j] = F.sum(b.i0, b.j0 + j, b.i0 + b.nx, b.j0 + j + 1);
             const int kx = hole_cut(sx), ky = hole_cut(sy);
             if (kx >= 0) {
                 dir = 0;
@@ -1291,15 +1296,15 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     const claw_problem& p = ctx->runs[run];
     if (L + 1 >= p.nlev) return -CLAW_EINVAL;
     const int NX = level_nx(p, L), NY = level_ny(p, L), r = p.ratio[L + 1];
-    // flags grown by `buffer` cells (square neighbourhood), clipped to the domain
-    std::vector<unsigned char> f((size_t)NX * NY, 0);
-    for (int j = 0; j < NY; ++j)
-        for (int i = 0; i < NX; ++i) {
-            if (!flags[(size_t)j * NX + i]) continue;
-            for (int jj = std::max(0, j - buffer); jj <= std::min(NY - 1, j + buffer); ++jj)
-                for (int ii = std::max(0, i - buffer); ii <= std::min(NX - 1, i + buffer); ++ii)
-                    f[(size_t)jj * NX + ii] = 1;
-        }
+    // flags grown by `buffer` cells (square neighbourhood, clipped to the domain)
+    std::vector<unsigned char> fin(flags, flags + (size_t)NX * NY), f((size_t)NX * NY, 0);
+    {
+        const Prefix FL(fin, NX, NY, false);
+        for (int j = 0; j < NY; ++j)
+            for (int i = 0; i < NX; ++i)
+                f[(size_t)j * NX + i] = FL.sum(std::max(0, i - buffer), std::max(0, j - buffer), std::min(NX, i + buffer + 1),
+                                              std::min(NY, j + buffer + 1)) > 0;
+    }
     // keep cells `nest` cells inside the level's coverage (the domain outside counts as covered)
     std::vector<unsigned char> cov((size_t)NX * NY, 0);
     for (const claw_box& b : ctx->lev[L].boxes)
@@ -1307,21 +1312,13 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
             for (int j = b.jlo; j < b.jlo + b.ny; ++j)
                 for (int i = b.ilo; i < b.ilo + b.nx; ++i) cov[(size_t)j * NX + i] = 1;
     // uncovered cells of the square of radius `nest` around each cell, the square clipped to the
-    // domain, from a 2D prefix sum of the uncovered indicator
-    std::vector<long long> P((size_t)(NX + 1) * (NY + 1), 0);
-    for (int j = 0; j < NY; ++j)
-        for (int i = 0; i < NX; ++i)
-            P[(size_t)(j + 1) * (NX + 1) + (i + 1)] = P[(size_t)j * (NX + 1) + (i + 1)] +
-                                                     P[(size_t)(j + 1) * (NX + 1) + i] - P[(size_t)j * (NX + 1) + i] +
-                                                     (cov[(size_t)j * NX + i] ? 0 : 1);
+    // domain (the domain outside counts as covered)
+    const Prefix UNC(cov, NX, NY, true);
     std::vector<unsigned char> allowed((size_t)NX * NY, 0);
     for (int j = 0; j < NY; ++j)
         for (int i = 0; i < NX; ++i) {
-            const int a0 = std::max(0, i - nest), a1 = std::min(NX, i + nest + 1);
-            const int b0 = std::max(0, j - nest), b1 = std::min(NY, j + nest + 1);
-            const long long bad = P[(size_t)b1 * (NX + 1) + a1] - P[(size_t)b0 * (NX + 1) + a1] -
-                                  P[(size_t)b1 * (NX + 1) + a0] + P[(size_t)b0 * (NX + 1) + a0];
-            const bool ok = bad == 0;
+            const bool ok = UNC.sum(std::max(0, i - nest), std::max(0, j - nest), std::min(NX, i + nest + 1),
+                                    std::min(NY, j + nest + 1)) == 0;
             allowed[(size_t)j * NX + i] = ok;
             if (!ok) f[(size_t)j * NX + i] = 0;
         }
@@ -1357,34 +1354,73 @@ int claw_regrid_transfer(claw_ctx* ctx, int32_t L, const claw_box* old_boxes, in
     }
     for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
         cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
-    std::vector<CellCopy> copies;
-    std::vector<InterpCell> cells;
+    std::vector<RectCopy> copies;
+    std::vector<InterpRun> runs;
+    const int r = d.ratio;
+    std::vector<unsigned char> mask;
     for (const claw_box& b : d.boxes) {
-        const claw_problem& pr = ctx->runs[b.run];
-        for (int gj = b.jlo; gj < b.jlo + b.ny; ++gj)
-            for (int gi = b.ilo; gi < b.ilo + b.nx; ++gi) {
-                const int m = oloc[b.run].find(gi, gj);
-                if (m >= 0) {
-                    copies.push_back(CellCopy{cell_off(b, gi, gj), cell_off(olds[m], gi, gj), plane_of(b),
-                                              plane_of(olds[m])});
+        // old boxes overlapping b: copied rectangles
+        mask.assign((size_t)b.nx * b.ny, 0);
+        std::vector<int> seen;
+        for (int bj = floordiv(b.jlo, Locator::B); bj <= floordiv(b.jlo + b.ny - 1, Locator::B); ++bj)
+            for (int bi = floordiv(b.ilo, Locator::B); bi <= floordiv(b.ilo + b.nx - 1, Locator::B); ++bi) {
+                auto it = oloc[b.run].buckets.find(Locator::key(bi, bj));
+                if (it == oloc[b.run].buckets.end()) continue;
+                for (int m : it->second) {
+                    if (std::find(seen.begin(), seen.end(), m) != seen.end()) continue;
+                    seen.push_back(m);
+                    const claw_box& o = olds[m];
+                    const int i0 = std::max(b.ilo, o.ilo), i1 = std::min(b.ilo + b.nx, o.ilo + o.nx);
+                    const int j0 = std::max(b.jlo, o.jlo), j1 = std::min(b.jlo + b.ny, o.jlo + o.ny);
+                    if (i0 >= i1 || j0 >= j1) continue;
+                    copies.push_back(RectCopy{cell_off(b, i0, j0), cell_off(o, i0, j0), plane_of(b), plane_of(o), i1 - i0,
+                                              j1 - j0, b.nx + 4, o.nx + 4});
+                    for (int j = j0; j < j1; ++j)
+                        std::memset(&mask[(size_t)(j - b.jlo) * b.nx + (i0 - b.ilo)], 1, (size_t)(i1 - i0));
+                }
+            }
+        // the rest: row runs of cells over one coarse box each
+        for (int j = 0; j < b.ny; ++j) {
+            int i = 0;
+            while (i < b.nx) {
+                if (mask[(size_t)j * b.nx + i]) {
+                    ++i;
                     continue;
                 }
-                InterpCell c;
-                if (make_interp(ctx, L, pr, cloc[b.run], cell_off(b, gi, gj), plane_of(b), gi, gj, 0, c))
-                    return CLAW_EINVAL;   // the new box is not nested in the coarse level
-                cells.push_back(c);
+                const int gj = b.jlo + j, gi = b.ilo + i;
+                const int cm = cloc[b.run].find(floordiv(gi, r), floordiv(gj, r));
+                if (cm < 0) return CLAW_EINVAL;   // the new box is not nested in the coarse level
+                const claw_box& cb = ctx->lev[L - 1].boxes[cm];
+                int e = i + 1;
+                while (e < b.nx && !mask[(size_t)j * b.nx + e] && floordiv(b.ilo + e, r) < cb.ilo + cb.nx) ++e;
+                InterpRun R;
+                R.dst = cell_off(b, gi, gj);
+                R.dplane = plane_of(b);
+                R.cbase = cb.qoff;
+                R.cplane = plane_of(cb);
+                R.n = e - i;
+                R.gi0 = gi;
+                R.gj = gj;
+                R.cilo = cb.ilo;
+                R.cjlo = cb.jlo;
+                R.cpitch = cb.nx + 4;
+                R.r = r;
+                R.pad = 0;
+                runs.push_back(R);
+                i = e;
             }
+        }
     }
-    CellCopy* dc = nullptr;
-    InterpCell* di = nullptr;
+    RectCopy* dc = nullptr;
+    InterpRun* di = nullptr;
     int rc = upload(&dc, copies);
-    if (!rc) rc = upload(&di, cells);
+    if (!rc) rc = upload(&di, runs);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (!rc) {
-        e = launch_cell_copy(dc, (int)copies.size(), q_old, q_new, s);
-        if (e == cudaSuccess) e = launch_fill_interp(di, (int)cells.size(), q_new, q_coarse, q_coarse, 0.0, s);
-        ctx->launches += (copies.size() > 0) + (cells.size() > 0);
+        e = launch_rect_copy(dc, (int)copies.size(), q_old, q_new, s);
+        if (e == cudaSuccess) e = launch_interp_runs(di, (int)runs.size(), q_coarse, q_new, s);
+        ctx->launches += (copies.size() > 0) + (runs.size() > 0);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the tables are freed below
     }
     cudaFree(dc);

@@ -71,8 +71,13 @@ struct FlagBox {
     long long qoff, goff;
     int nx, ny, pitch, pad;
 };
-struct CellCopy {
+struct RectCopy {     // w x h cells (3 planes) from one pool into another
     long long dst, src, dplane, splane;
+    int w, h, dpitch, spitch;
+};
+struct InterpRun {    // n fine cells of row gj from column gi0, interpolated from one coarse box
+    long long dst, dplane, cbase, cplane;   // cbase: the coarse box's qoff
+    int n, gi0, gj, cilo, cjlo, cpitch, r, pad;
 };
 
 // One fine ghost cell filled by space-time interpolation from the coarser level.
@@ -185,7 +190,8 @@ cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, int max_rows, co
 // regridding
 cudaError_t launch_flags(const FlagBox* boxes, int nb, int max_rows, const double* q, double tol,
                          unsigned char* flags, cudaStream_t s);
-cudaError_t launch_cell_copy(const CellCopy* c, int n, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_rect_copy(const RectCopy* c, int n, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_interp_runs(const InterpRun* r, int n, const double* qc, double* qf, cudaStream_t s);
 
 // conservation fix (uniform medium): buf holds 3 doubles per interface record (the coarse
 // parts) followed by 3 per record and fine edge (the fine parts, summed over the substeps)

@@ -34,13 +34,43 @@ __global__ void flag_kernel(const FlagBox* __restrict__ boxes, const double* __r
     }
 }
 
-__global__ void cell_copy_kernel(const CellCopy* __restrict__ c, int n, const double* __restrict__ src,
+__global__ void rect_copy_kernel(const RectCopy* __restrict__ c, const double* __restrict__ src,
                                  double* __restrict__ dst)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const CellCopy C = c[k];
-    for (int m = 0; m < 3; ++m) dst[C.dst + m * C.dplane] = src[C.src + m * C.splane];
+    const RectCopy C = c[blockIdx.x];
+    const int cells = C.w * C.h;
+    for (int k = threadIdx.x; k < 3 * cells; k += blockDim.x) {
+        const int m = k / cells, e = k - m * cells;
+        const int y = e / C.w, x = e - y * C.w;
+        dst[C.dst + m * C.dplane + (long long)y * C.dpitch + x] = src[C.src + m * C.splane + (long long)y * C.spitch + x];
+    }
+}
+
+__device__ __forceinline__ double minmod2(double a, double b)
+{
+    if (!(a * b > 0.0)) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+// conservative space interpolation (minmod-limited slopes) of each fine cell of a run from its
+// coarse cell and the four face neighbours, read from the coarse box's padded planes (ghosts filled)
+__global__ void interp_runs_kernel(const InterpRun* __restrict__ runs, const double* __restrict__ qc,
+                                   double* __restrict__ qf)
+{
+    const InterpRun R = runs[blockIdx.x];
+    for (int k = threadIdx.x; k < 3 * R.n; k += blockDim.x) {
+        const int m = k / R.n, t = k - m * R.n;
+        const int gi = R.gi0 + t;
+        const int I = gi >= 0 ? gi / R.r : -((-gi + R.r - 1) / R.r);
+        const int J = R.gj >= 0 ? R.gj / R.r : -((-R.gj + R.r - 1) / R.r);
+        const double* c = qc + R.cbase + m * R.cplane + (long long)(J - R.cjlo + 2) * R.cpitch + (I - R.cilo + 2);
+        const double q0 = c[0];
+        const double sx = minmod2(c[1] - q0, q0 - c[-1]);
+        const double sy = minmod2(c[R.cpitch] - q0, q0 - c[-R.cpitch]);
+        const double xi = ((double)(gi - I * R.r) + 0.5) / R.r - 0.5;
+        const double eta = ((double)(R.gj - J * R.r) + 0.5) / R.r - 0.5;
+        qf[R.dst + m * R.dplane + t] = q0 + xi * sx + eta * sy;
+    }
 }
 
 }  // namespace
@@ -54,10 +84,17 @@ cudaError_t launch_flags(const FlagBox* boxes, int nb, int max_rows, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_cell_copy(const CellCopy* c, int n, const double* src, double* dst, cudaStream_t s)
+cudaError_t launch_rect_copy(const RectCopy* c, int n, const double* src, double* dst, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    cell_copy_kernel<<<(n + 127) / 128, 128, 0, s>>>(c, n, src, dst);
+    rect_copy_kernel<<<n, 128, 0, s>>>(c, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp_runs(const InterpRun* r, int n, const double* qc, double* qf, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    interp_runs_kernel<<<n, 128, 0, s>>>(r, qc, qf);
     return cudaGetLastError();
 }
 
