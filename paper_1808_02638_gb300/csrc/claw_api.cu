@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <thread>
 #include <unordered_map>
 #include <utility>
 #include <vector>
@@ -669,17 +670,37 @@ std::pair<long long, int> inflection_cut(const std::vector<long long>& sig)
     return best;
 }
 
+// fn(lo, hi) over [0, n) in contiguous chunks on up to 16 host threads (grids of a regrid)
+template <typename F>
+void parallel_for(int n, F fn)
+{
+    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int nt = std::max(1, std::min(hw, n / 64));
+    if (nt <= 1) {
+        fn(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(fn, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
+    for (auto& x : th) x.join();
+}
+
 // 2D prefix sum of a 0/1 grid: S(i, j) = sum over [0, i) x [0, j)
 struct Prefix {
     int NX = 0, NY = 0;
     std::vector<long long> P;
     Prefix(const std::vector<unsigned char>& g, int nx, int ny, bool invert) : NX(nx), NY(ny), P((size_t)(nx + 1) * (ny + 1), 0)
     {
-        for (int j = 0; j < NY; ++j)
-            for (int i = 0; i < NX; ++i)
-                P[(size_t)(j + 1) * (NX + 1) + (i + 1)] = P[(size_t)j * (NX + 1) + (i + 1)] +
-                                                         P[(size_t)(j + 1) * (NX + 1) + i] - P[(size_t)j * (NX + 1) + i] +
-                                                         ((g[(size_t)j * NX + i] != 0) != invert ? 1 : 0);
+        parallel_for(NY, [&](int j0, int j1) {   // prefix along each row
+            for (int j = j0; j < j1; ++j) {
+                long long* row = &P[(size_t)(j + 1) * (NX + 1)];
+                for (int i = 0; i < NX; ++i) row[i + 1] = row[i] + (((g[(size_t)j * NX + i] != 0) != invert) ? 1 : 0);
+            }
+        });
+        parallel_for(NX + 1, [&](int i0, int i1) {   // then down each column
+            for (int j = 1; j <= NY; ++j)
+                for (int i = i0; i < i1; ++i) P[(size_t)j * (NX + 1) + i] += P[(size_t)(j - 1) * (NX + 1) + i];
+        });
     }
     long long sum(int i0, int j0, int i1, int j1) const   // over [i0, i1) x [j0, j1)
     {
@@ -1300,10 +1321,12 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     std::vector<unsigned char> fin(flags, flags + (size_t)NX * NY), f((size_t)NX * NY, 0);
     {
         const Prefix FL(fin, NX, NY, false);
-        for (int j = 0; j < NY; ++j)
-            for (int i = 0; i < NX; ++i)
-                f[(size_t)j * NX + i] = FL.sum(std::max(0, i - buffer), std::max(0, j - buffer), std::min(NX, i + buffer + 1),
-                                              std::min(NY, j + buffer + 1)) > 0;
+        parallel_for(NY, [&](int ja, int jb) {
+            for (int j = ja; j < jb; ++j)
+                for (int i = 0; i < NX; ++i)
+                    f[(size_t)j * NX + i] = FL.sum(std::max(0, i - buffer), std::max(0, j - buffer),
+                                                  std::min(NX, i + buffer + 1), std::min(NY, j + buffer + 1)) > 0;
+        });
     }
     // keep cells `nest` cells inside the level's coverage (the domain outside counts as covered)
     std::vector<unsigned char> cov((size_t)NX * NY, 0);
@@ -1315,13 +1338,15 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     // domain (the domain outside counts as covered)
     const Prefix UNC(cov, NX, NY, true);
     std::vector<unsigned char> allowed((size_t)NX * NY, 0);
-    for (int j = 0; j < NY; ++j)
-        for (int i = 0; i < NX; ++i) {
-            const bool ok = UNC.sum(std::max(0, i - nest), std::max(0, j - nest), std::min(NX, i + nest + 1),
-                                    std::min(NY, j + nest + 1)) == 0;
-            allowed[(size_t)j * NX + i] = ok;
-            if (!ok) f[(size_t)j * NX + i] = 0;
-        }
+    parallel_for(NY, [&](int ja, int jb) {
+        for (int j = ja; j < jb; ++j)
+            for (int i = 0; i < NX; ++i) {
+                const bool ok = UNC.sum(std::max(0, i - nest), std::max(0, j - nest), std::min(NX, i + nest + 1),
+                                        std::min(NY, j + nest + 1)) == 0;
+                allowed[(size_t)j * NX + i] = ok;
+                if (!ok) f[(size_t)j * NX + i] = 0;
+            }
+    });
     const std::vector<IBox> out = cluster_flags(f, NX, NY, cutoff, std::max(1, max_size / r), allowed);
     if ((long long)out.size() > max_boxes) return -CLAW_ENOMEM;
     for (size_t k = 0; k < out.size(); ++k) {
