@@ -303,6 +303,7 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
 
 
 WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4, "e1": e1}
+# (bench.py reports every workload above; e1 runs 200 coarse steps there)
 
 
 def run_all(names=None):
