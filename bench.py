@@ -374,7 +374,8 @@ def main():
                  "fused_over_plain": value / world / pv}
 
     # end to end: the state lives on the host (pinned); every step copies q in, runs the
-    # level-step through the C ABI and copies q^{n+1} back
+    # level-step through the C ABI and copies q^{n+1} back (Hierarchy.steps_from_host: the copy
+    # out of one step overlaps the copy into the next, piece by piece)
     H.fused = True          # first e2e step fills the ghosts; later steps carry pushed ghosts
     H._ghosts_ready = False
     e2e_steps = max(3, min(20, K // 4))
@@ -385,11 +386,7 @@ def main():
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for k in range(e2e_steps):
-        H.q[0][H.cur[0]].copy_(host_in, non_blocking=True)
-        H.coarse_step()
-        host_out.copy_(H.q[0][H.cur[0]], non_blocking=True)
-        host_in, host_out = host_out, host_in
+    H.steps_from_host(host_in, host_out, e2e_steps)
     e1.record()
     torch.cuda.synchronize()
     e2e_value, _, _ = replicas.whole_job_rate(e2e_steps * N_CELLS, e0.elapsed_time(e1), dist, dev)

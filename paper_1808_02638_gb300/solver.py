@@ -228,6 +228,43 @@ class Hierarchy:
         else:
             claw.claw_dt_update(self.ctx, 0, self.smax, self.dt, stream)
 
+    def steps_from_host(self, host_a, host_b, nsteps, chunks=8):
+        """One-level hierarchies: `nsteps` coarse steps with the state resident in pinned host
+        memory.  Every step copies the whole state from the host into the current pool, advances
+        it, and copies the new state back to the other host buffer; the next step reads that one.
+        The copies are split into `chunks` pieces on two copy streams, so that a piece can go back
+        in as soon as it has come out: the copy out of one step overlaps the copy into the next.
+        Returns the host buffer holding the final state."""
+        if self.nlev != 1:
+            raise ValueError("host-resident stepping is for one-level hierarchies")
+        comp = torch.cuda.current_stream(self.dev)
+        s_in, s_out = torch.cuda.Stream(device=self.dev), torch.cuda.Stream(device=self.dev)
+        n = host_a.numel()
+        bounds = [(c * n // chunks, (c + 1) * n // chunks) for c in range(chunks)]
+        out_done = [None] * chunks
+        src, dst = host_a, host_b
+        s_in.wait_stream(comp)
+        for _ in range(nsteps):
+            q = self.q[0][self.cur[0]]
+            for c, (a, b) in enumerate(bounds):
+                if out_done[c] is not None:
+                    s_in.wait_event(out_done[c])   # this piece has left the device
+                with torch.cuda.stream(s_in):
+                    q[a:b].copy_(src[a:b], non_blocking=True)
+            comp.wait_stream(s_in)
+            self.coarse_step()
+            s_out.wait_stream(comp)
+            qn = self.q[0][self.cur[0]]
+            for c, (a, b) in enumerate(bounds):
+                with torch.cuda.stream(s_out):
+                    dst[a:b].copy_(qn[a:b], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s_out)
+                out_done[c] = ev
+            src, dst = dst, src
+        comp.wait_stream(s_out)
+        return src
+
     def launches_per_coarse_step(self):
         """kernels one coarse step enqueues (counted from the library's own counter)."""
         before = claw.claw_launch_count(self.ctx)

@@ -279,6 +279,28 @@ def test_full_size_bench_launch_path_sampled_parity(orc, tiling):
     assert H.sync_status() == 0
 
 
+def test_host_resident_steps_equal_device_steps():
+    # the pipelined host loop (state copied in and out every step, in pieces on two streams)
+    # produces bit for bit the states of the same steps on the device
+    import torch
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config1(256, 32)
+    q = inputs.init_q(run, run.levels[0])
+    A = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    B = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    for h in (A, B):
+        h.init_dt()
+        h.fused = True
+    ha = torch.empty_like(B.q[0][0], device="cpu").pin_memory()
+    hb = torch.empty_like(ha).pin_memory()
+    ha.copy_(B.q[0][B.cur[0]])
+    for _ in range(6):
+        A.coarse_step()
+    out = B.steps_from_host(ha, hb, 6, chunks=5)
+    torch.cuda.synchronize()
+    assert torch.equal(out, A.pool(0).cpu()) and float(A.dt[0]) == float(B.dt[0])
+
+
 def test_errors_are_status_codes():
     from paper_1808_02638_gb300 import claw
     from paper_1808_02638_gb300.solver import Hierarchy
