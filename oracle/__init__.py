@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "claw_oracle.c")
+_SRC_SWE = os.path.join(_HERE, "swe_oracle.c")
 _HDR = os.path.join(_HERE, "claw_oracle.h")
 _LIBDIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
@@ -33,11 +34,11 @@ LIMITERS = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (gcc, strict IEEE)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_SWE), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-std=c11", "-o", tmp, _SRC, "-lm"]
+               "-std=c11", "-o", tmp, _SRC, _SRC_SWE, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -74,6 +75,10 @@ def lib():
             L.orc_level_fill_ghost_adjoint.argtypes = [I, BP, D, I, I, I, I, IP, I, BP, D, D, D, D,
                                                        dbl, I, I]
             L.orc_average_down_adjoint.argtypes = [I, BP, D, I, BP, D, I, I, I]
+            L.orc_swe_step.argtypes = [I, I, I, dbl, dbl, dbl, I, I, I, dbl, D, D, D]
+            L.orc_swe_roe_x.argtypes = [dbl] * 7 + [D, D]
+            L.orc_swe_cfl_max.argtypes = [I, I, I, dbl, D]
+            L.orc_swe_cfl_max.restype = dbl
             _lib = L
     return _lib
 
@@ -164,6 +169,35 @@ def step_adjoint(q, rho, K, lam_new, dx, dy, dt, order=2, transverse=2, limiter=
     if rc:
         raise ValueError(f"orc_step_adjoint failed ({rc})")
     return lq, gr, gk
+
+
+def swe_step(q, dx, dy, dt, grav, order=2, transverse=2, limiter="mc"):
+    """One shallow-water step (q = (h, hu, hv), Roe solver) on one patch whose ghosts are
+    filled.  Returns (qnew, smax) like :func:`step`."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    _, H, W = q.shape
+    qn = q.copy()
+    sm = ctypes.c_double(0.0)
+    rc = lib().orc_swe_step(W - 2 * MBC, H - 2 * MBC, MBC, dx, dy, dt, order, transverse,
+                            _lim(limiter), float(grav), _p(q), _p(qn), ctypes.byref(sm))
+    if rc:
+        raise ValueError(f"orc_swe_step failed ({rc})")
+    return qn, sm.value
+
+
+def swe_roe_x(left, right, grav):
+    """Waves (3, 3) and speeds (3,) of the Roe solve at one x-edge; states are (h, hu, hv)."""
+    w = np.zeros(9)
+    s = np.zeros(3)
+    lib().orc_swe_roe_x(*[float(v) for v in left], *[float(v) for v in right], float(grav),
+                        _p(w), _p(s))
+    return w.reshape(3, 3), s
+
+
+def swe_cfl_max(q, grav) -> float:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    _, H, W = q.shape
+    return lib().orc_swe_cfl_max(W - 2 * MBC, H - 2 * MBC, MBC, float(grav), _p(q))
 
 
 def fill_bc(a, bc=(0, 0, 0, 0)):

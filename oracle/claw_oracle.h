@@ -67,6 +67,19 @@ int orc_fill_bc_adjoint(int nx, int ny, int mbc, int ncomp, const int* bc, doubl
 /* max of c = sqrt(K/rho) over the cells next to the edges the step solves for its update */
 double orc_cfl_max(int nx, int ny, int mbc, const double* rho, const double* K);
 
+/* ---------------------------------------------------------------- shallow water (swe_oracle.c)
+ * q = (h, hu, hv).  One unsplit step of the same form with the Roe solver; grav = g.
+ * Returns 0, -1 on bad arguments / allocation failure, -2 if a cell of the stencil has
+ * h <= 0.  *smax: largest |s| over the edges whose waves enter the update. */
+int orc_swe_step(int nx, int ny, int mbc, double dx, double dy, double dt,
+                 int order, int transverse, int limiter, double grav,
+                 const double* q, double* qnew, double* smax);
+/* Roe solve at one x-edge: waves[0..8] = W1, W2, W3 (h, hu, hv); speeds[0..2] */
+void orc_swe_roe_x(double hl, double hul, double hvl, double hr, double hur, double hvr,
+                   double grav, double* waves, double* speeds);
+/* max over the cells [-1, nx] x [-1, ny] of |u| + sqrt(g h) and |v| + sqrt(g h) */
+double orc_swe_cfl_max(int nx, int ny, int mbc, double grav, const double* q);
+
 /* ---------------------------------------------------------------- AMR (one run) */
 typedef struct { int32_t ilo, jlo, nx, ny; int64_t off; } orc_box;  /* off: element offset of
                                                                         the box's first plane */
