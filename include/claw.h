@@ -7,6 +7,11 @@
  * density rho and bulk modulus K (c = sqrt(K/rho), impedance Z = rho c).  Each level-step is
  * the unsplit wave-propagation update of Eq. wave_form_2d_2nd_order applied to every patch of
  * an AMR level (Sec. 2.2), with limited second-order corrections and transverse propagation.
+ * A second system goes through the same step and AMR machinery (the framework takes any system
+ * through its normal and transverse Riemann solvers, Sec. 3.1, 3.3): the nonlinear shallow
+ * water equations on a flat bottom, q = (h, hu, hv), with the Roe solvers (system =
+ * CLAW_SYS_SHALLOW_WATER; the level-step, ghost filling, averaging, regridding and the CFL
+ * control apply; the adjoint and the conservation fix are acoustics-only).
  *
  * Conventions shared by every entry point
  *   - Storage: a box (patch) with an nx x ny interior has CLAW_MBC = 2 ghost layers and is
@@ -52,6 +57,10 @@ extern "C" {
 #define CLAW_LIM_VANLEER 3
 #define CLAW_LIM_MC 4
 
+/* systems */
+#define CLAW_SYS_ACOUSTICS 0
+#define CLAW_SYS_SHALLOW_WATER 1
+
 /* physical boundary conditions (Sec. 2.2 item 1; the benchmark uses outflow = extrapolation) */
 #define CLAW_BC_EXTRAP 0
 #define CLAW_BC_PERIODIC 1
@@ -73,6 +82,9 @@ typedef struct claw_problem {
     int32_t bc[4];               /* x-low, x-high, y-low, y-high: CLAW_BC_* */
     int32_t medium;              /* 0: uniform rho0, K0; 1: cell-wise (aux pools) */
     double rho0, K0;
+    int32_t system;              /* CLAW_SYS_*: 0 acoustics (all of the above), 1 shallow water */
+    int32_t reserved;            /* 0 */
+    double grav;                 /* shallow water: gravitational acceleration g > 0 */
 } claw_problem;
 
 /* A box of a level in that level's index space [0, NX_L) x [0, NY_L) of run `run`. */
@@ -85,7 +97,8 @@ typedef struct claw_box {
 } claw_box;
 
 /* Creates a context for nruns problems on CUDA device `device`.  All runs must share
- * limiter, order, transverse and medium.  Returns CLAW_OK and sets *out, or an error. */
+ * limiter, order, transverse, medium, system and grav.  Shallow water needs medium = 0 (rho0,
+ * K0 are ignored) and grav > 0.  Returns CLAW_OK and sets *out, or an error. */
 int claw_create(claw_ctx** out, const claw_problem* runs, int32_t nruns, int32_t device);
 
 /* Frees the context and its device tables (synchronises the device first). */
@@ -102,9 +115,10 @@ int claw_set_level(claw_ctx* ctx, int32_t level, const claw_box* boxes, int32_t 
 /* Chooses the tiling of the fused level-step for a level: tx x ty interior cells per tile,
  * the staging of the tile's q planes into shared memory (0 = cooperative loads,
  * 1 = tensor-memory-accelerator bulk copies, only when every box has even nx and offsets) and
- * the threads per CTA (0 = default).  Supported: 32x32 with 256 or 512 threads, 32x16 with
- * 256, 16x16 with 128.  claw_set_level installs 32x32, 256 threads, staging 1 when allowed.
- * Errors: CLAW_EINVAL. */
+ * the threads per CTA (0 = default).  Supported for acoustics: 32x32 with 256 or 512 threads,
+ * 32x16 with 256, 16x16 with 128; claw_set_level installs 32x32, 256 threads.  Supported for
+ * shallow water: 16x16 with 256 threads, 32x16 with 512; claw_set_level installs 16x16.
+ * Staging 1 is installed when allowed.  Errors: CLAW_EINVAL. */
 int claw_set_tiling(claw_ctx* ctx, int32_t level, int32_t tx, int32_t ty, int32_t staging,
                     int32_t threads);
 
@@ -135,8 +149,13 @@ int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t level, double* g, void* 
 /* smax[run] = max(smax[run], max c over the cells next to the edges a level-step of `level`
  * solves: the ring [-1, nx] x [-1, ny] of every box), for the first time step (Eq. cfl).
  * aux may be NULL for medium = 0.  smax has one entry per run (zero it before the first use;
- * claw_dt_update resets it). */
+ * claw_dt_update resets it).  Acoustics only (CLAW_EINVAL for shallow water). */
 int claw_cfl_max(claw_ctx* ctx, int32_t level, const double* aux, double* smax, void* stream);
+
+/* The same for a system whose speeds depend on the state (shallow water): smax[run] =
+ * max(smax[run], max over the same ring cells of |u| + sqrt(g h) and |v| + sqrt(g h)) from the
+ * level's q pool (ghosts filled).  A cell with h <= 0 gives NaN.  CLAW_EINVAL for acoustics. */
+int claw_cfl_max_state(claw_ctx* ctx, int32_t level, const double* q, double* smax, void* stream);
 
 /* Eq. cfl on the device, per run r, with dx, dy of level `level` (normally 0): checks that the
  * step just taken with dt[r] kept smax[r] * dt[r] / min(dx, dy) <= 1 (else the device flag
@@ -151,7 +170,8 @@ int claw_dt_update(claw_ctx* ctx, int32_t level, double* smax, double* dt, void*
  * times finer takes R_L times smaller steps).  The largest wave speed seen is
  * max-accumulated into smax[r].  Only
  * interior cells of q_new are written.  aux may be NULL for medium = 0.  q_old and q_new must
- * not overlap.  Errors: CLAW_EINVAL, CLAW_ESTATE, CLAW_ECUDA. */
+ * not overlap.  Shallow water: a depth h <= 0 in a cell the step reads is reported as
+ * CLAW_ENAN (the Roe solver is for wet states).  Errors: CLAW_EINVAL, CLAW_ESTATE, CLAW_ECUDA. */
 int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
                     const double* aux, const double* dt, double* smax, void* stream);
 

@@ -25,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import (MBC, average_down, average_down_adjoint, cfl_max, level_fill_ghost,
-               level_fill_ghost_adjoint, step, step_adjoint, step_edges)
+               level_fill_ghost_adjoint, step, step_adjoint, step_edges, swe_cfl_max, swe_step)
 
 
 def _view(pool, off, nx, ny, ncomp):
@@ -89,13 +89,19 @@ def interface(levels, Lf, bc):
 class OracleHierarchy:
     """State of one run on the oracle: per level a q pool and coefficient pools."""
 
-    def __init__(self, run, q, rho, K, reflux=False):
+    def __init__(self, run, q, rho=None, K=None, reflux=False, system="acoustics", grav=1.0):
+        """system="shallow_water": q = (h, hu, hv) stepped by the shallow-water oracle with
+        gravity grav (rho, K unused)."""
         self.run = run
         self.reflux = reflux
+        self.swe = system == "shallow_water"
+        self.grav = grav
+        if self.swe and reflux:
+            raise ValueError("the conservation fix is written for acoustics")
         self.levels = run.levels
         self.q = [np.array(a, dtype=np.float64, copy=True) for a in q]
-        self.rho = [np.asarray(a, dtype=np.float64) for a in rho]
-        self.K = [np.asarray(a, dtype=np.float64) for a in K]
+        self.rho = [np.asarray(a, dtype=np.float64) for a in rho] if not self.swe else None
+        self.K = [np.asarray(a, dtype=np.float64) for a in K] if not self.swe else None
         self.smax = max(self.level_cfl_max(L) for L in range(len(self.levels)))
         self._iface = {Lf: interface(self.levels, Lf, run.bc) for Lf in range(1, len(self.levels))} if reflux else {}
         self.dt_history = []
@@ -104,6 +110,12 @@ class OracleHierarchy:
     def level_cfl_max(self, L):
         lev = self.levels[L]
         s = 0.0
+        if self.swe:   # speeds of the state: ghosts first (level L from level L-1 at the same time)
+            qc = self.q[L - 1] if L else None
+            self.fill(L, self.q[L], qc, qc, 0.0)
+            for n, b in enumerate(lev.boxes):
+                s = max(s, swe_cfl_max(_view(self.q[L], lev.qoff[n], int(b[2]), int(b[3]), 3), self.grav))
+            return s
         for n, b in enumerate(lev.boxes):
             nx, ny = int(b[2]), int(b[3])
             r = _view(self.rho[L], lev.coff[n], nx, ny, 1)[0]
@@ -129,6 +141,12 @@ class OracleHierarchy:
         for n, b in enumerate(lev.boxes):
             nx, ny = int(b[2]), int(b[3])
             qb = _view(qold, lev.qoff[n], nx, ny, 3)
+            if self.swe:
+                out, s = swe_step(qb, lev.dx, lev.dy, dt, self.grav, run.order, run.transverse, run.limiter)
+                _view(qnew, lev.qoff[n], nx, ny, 3)[:, MBC:MBC + ny, MBC:MBC + nx] = \
+                    out[:, MBC:MBC + ny, MBC:MBC + nx]
+                sm = max(sm, s)
+                continue
             r = _view(self.rho[L], lev.coff[n], nx, ny, 1)[0]
             k = _view(self.K[L], lev.coff[n], nx, ny, 1)[0]
             if edges is None:

@@ -17,6 +17,8 @@ CLAW_MBC = 2
 CLAW_MAXLEV = 8
 CLAW_NAUX = 10
 LIMITERS = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
+CLAW_SYS_ACOUSTICS, CLAW_SYS_SHALLOW_WATER = 0, 1
+SYSTEMS = {"acoustics": CLAW_SYS_ACOUSTICS, "shallow_water": CLAW_SYS_SHALLOW_WATER}
 
 
 class ClawError(RuntimeError):
@@ -31,7 +33,8 @@ class claw_problem(ctypes.Structure):
                 ("nlev", ctypes.c_int32), ("ratio", ctypes.c_int32 * CLAW_MAXLEV),
                 ("cfl", ctypes.c_double), ("limiter", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("transverse", ctypes.c_int32), ("bc", ctypes.c_int32 * 4), ("medium", ctypes.c_int32),
-                ("rho0", ctypes.c_double), ("K0", ctypes.c_double)]
+                ("rho0", ctypes.c_double), ("K0", ctypes.c_double), ("system", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("grav", ctypes.c_double)]
 
 
 class claw_box(ctypes.Structure):
@@ -66,6 +69,7 @@ _SIGNATURES = {
     "claw_fill_ghost_coef": ([VP, I32, VP, VP], ctypes.c_int),
     "claw_fill_ghost_coef_adjoint": ([VP, I32, VP, VP], ctypes.c_int),
     "claw_cfl_max": ([VP, I32, VP, VP, VP], ctypes.c_int),
+    "claw_cfl_max_state": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_dt_update": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_level_step": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_level_step_patchwise": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
@@ -236,6 +240,10 @@ def claw_fill_ghost_coef_adjoint(ctx, level, g, stream=None):
 
 def claw_cfl_max(ctx, level, aux, smax, stream=None):
     _check("claw_cfl_max", load().claw_cfl_max(ctx, level, _ptr(aux), _ptr(smax), _stream(stream)))
+
+
+def claw_cfl_max_state(ctx, level, q, smax, stream=None):
+    _check("claw_cfl_max_state", load().claw_cfl_max_state(ctx, level, _ptr(q), _ptr(smax), _stream(stream)))
 
 
 def claw_dt_update(ctx, level, smax, dt, stream=None):

@@ -34,6 +34,9 @@ struct claw_ctx {
     std::vector<claw_problem> runs;
     int limiter = 4, order = 2, transverse = 2, medium = 0;
     double rho0 = 1, K0 = 1;
+    int system = CLAW_SYS_ACOUSTICS;
+    double grav = 0;
+    int kind() const { return system == CLAW_SYS_SHALLOW_WATER ? KIND_SWE : medium; }
     LevelDev lev[CLAW_MAXLEV];
     bool set[CLAW_MAXLEV] = {};
     // device scalars
@@ -616,6 +619,7 @@ StepArgs make_args(claw_ctx* ctx, int L, const double* q_old, double* q_new, con
     a.transverse = ctx->transverse;
     a.rho0 = ctx->rho0;
     a.K0 = ctx->K0;
+    a.grav = ctx->grav;
     return a;
 }
 
@@ -626,7 +630,7 @@ int check_step_args(claw_ctx* ctx, int L, const double* q_old, const double* q_n
     if (L < 0 || L >= CLAW_MAXLEV) return CLAW_EINVAL;
     if (!ctx->set[L]) return CLAW_ESTATE;
     if (!q_old || !q_new || !dt || !smax || q_old == q_new) return CLAW_EINVAL;
-    if (ctx->medium == 1 && !aux) return CLAW_EINVAL;
+    if (ctx->kind() == KIND_CELLWISE && !aux) return CLAW_EINVAL;
     return CLAW_OK;
 }
 
@@ -804,9 +808,14 @@ int claw_create(claw_ctx** out, const claw_problem* runs, int32_t nruns, int32_t
             return CLAW_EINVAL;
         for (int l = 1; l < p.nlev; ++l)
             if (p.ratio[l] < 2 || p.ratio[l] > 16) return CLAW_EINVAL;
-        if (p.medium == 0 && !(p.rho0 > 0 && p.K0 > 0)) return CLAW_EINVAL;
+        if (p.system != CLAW_SYS_ACOUSTICS && p.system != CLAW_SYS_SHALLOW_WATER) return CLAW_EINVAL;
+        if (p.system == CLAW_SYS_SHALLOW_WATER && (p.medium != 0 || !(p.grav > 0) || !std::isfinite(p.grav)))
+            return CLAW_EINVAL;
+        if (p.system == CLAW_SYS_ACOUSTICS && p.medium == 0 && !(p.rho0 > 0 && p.K0 > 0)) return CLAW_EINVAL;
         if (p.limiter != runs[0].limiter || p.order != runs[0].order || p.transverse != runs[0].transverse ||
-            p.medium != runs[0].medium || (p.medium == 0 && (p.rho0 != runs[0].rho0 || p.K0 != runs[0].K0)))
+            p.medium != runs[0].medium || p.system != runs[0].system ||
+            (p.system == CLAW_SYS_SHALLOW_WATER && p.grav != runs[0].grav) ||
+            (p.system == CLAW_SYS_ACOUSTICS && p.medium == 0 && (p.rho0 != runs[0].rho0 || p.K0 != runs[0].K0)))
             return CLAW_EINVAL;
     }
     int ndev = 0;
@@ -823,6 +832,8 @@ int claw_create(claw_ctx** out, const claw_problem* runs, int32_t nruns, int32_t
     c->medium = runs[0].medium;
     c->rho0 = runs[0].rho0;
     c->K0 = runs[0].K0;
+    c->system = runs[0].system;
+    c->grav = runs[0].system == CLAW_SYS_SHALLOW_WATER ? runs[0].grav : 0.0;
     cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
     std::vector<double> minh(CLAW_MAXLEV * nruns, 0.0), cfl(nruns);
     for (int r = 0; r < nruns; ++r) {
@@ -930,8 +941,8 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         d.hpatches[n] = P;
     }
     ctx->tma_ok[L] = even;
-    d.tx = 32;
-    d.ty = 32;
+    d.tx = ctx->kind() == KIND_SWE ? 16 : 32;
+    d.ty = ctx->kind() == KIND_SWE ? 16 : 32;
     d.staging = even ? 1 : 0;
     std::vector<CopyRect> rects;
     std::vector<InterpCell> cells;
@@ -986,9 +997,13 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
 int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t staging, int32_t threads)
 {
     if (!valid_level(ctx, L)) return CLAW_EINVAL;
-    const bool shape_ok = (tx == 32 && ty == 32 && (threads == 0 || threads == 256 || threads == 512)) ||
-                          (tx == 32 && ty == 16 && (threads == 0 || threads == 256)) ||
-                          (tx == 16 && ty == 16 && (threads == 0 || threads == 128));
+    const bool shape_ok =
+        ctx->kind() == KIND_SWE
+            ? (tx == 16 && ty == 16 && (threads == 0 || threads == 256)) ||
+                  (tx == 32 && ty == 16 && (threads == 0 || threads == 512))
+            : (tx == 32 && ty == 32 && (threads == 0 || threads == 256 || threads == 512)) ||
+                  (tx == 32 && ty == 16 && (threads == 0 || threads == 256)) ||
+                  (tx == 16 && ty == 16 && (threads == 0 || threads == 128));
     if (!shape_ok || staging < 0 || staging > 1 || (staging == 1 && !ctx->tma_ok[L])) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
@@ -1082,12 +1097,24 @@ int claw_cfl_max(claw_ctx* ctx, int32_t L, const double* aux, double* smax, void
 {
     if (!ctx || L < 0 || L >= CLAW_MAXLEV || !smax) return CLAW_EINVAL;
     if (!ctx->set[L]) return CLAW_ESTATE;
-    if (ctx->medium == 1 && !aux) return CLAW_EINVAL;
+    if (ctx->kind() == KIND_SWE || (ctx->medium == 1 && !aux)) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = launch_cfl_max(ctx->lev[L].patches, ctx->lev[L].nboxes, ctx->lev[L].max_rows, ctx->medium,
                                    std::sqrt(ctx->K0 / ctx->rho0), aux, smax, s);
     ctx->launches += ctx->lev[L].nboxes > 0;
+    return cuda_rc(e);
+}
+
+int claw_cfl_max_state(claw_ctx* ctx, int32_t L, const double* q, double* smax, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !q || !smax) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    if (ctx->kind() != KIND_SWE) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    const LevelDev& d = ctx->lev[L];
+    cudaError_t e = launch_cfl_max_state(d.patches, d.nboxes, d.max_rows, ctx->grav, q, smax, (cudaStream_t)stream);
+    ctx->launches += d.nboxes > 0;
     return cuda_rc(e);
 }
 
@@ -1116,11 +1143,11 @@ int claw_level_step(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new
         a.tmaps = get_tmaps(ctx, L, q_old, s);
         if (!a.tmaps) staging = 0;   // no descriptor (e.g. first use inside a graph capture)
     }
-    const int per_sm = step_max_ctas_per_sm(ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging);
+    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging);
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;
-    return cuda_rc(launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s));
+    return cuda_rc(launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s));
 }
 
 int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux, double* dt,
@@ -1147,11 +1174,11 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
         a.tmaps = get_tmaps(ctx, L, q_old, s);
         if (!a.tmaps) staging = 0;
     }
-    const int per_sm = step_max_ctas_per_sm(ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging);
+    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging);
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;
-    cudaError_t e = launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s);
+    cudaError_t e = launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s);
     if (e == cudaSuccess && (flags & CLAW_ADVANCE_PUSH_GHOSTS) && d.ncopy) {
         e = launch_fill_copy(d.copies, d.copy_start, d.ncopy_blocks, q_new, s);
         ctx->launches += 1;
@@ -1173,7 +1200,7 @@ int claw_level_step_patchwise(claw_ctx* ctx, int32_t L, const double* q_old, dou
         a.tiles = ctx->ptiles[L] + st[n];
         a.ntiles = st[n + 1] - st[n];
         ctx->launches += 1;
-        cudaError_t e = launch_step(a, ctx->medium, ctx->limiter, d.tx, d.ty, d.nt, 0, a.ntiles, s);
+        cudaError_t e = launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, 0, a.ntiles, s);
         if (e != cudaSuccess) return CLAW_ECUDA;
     }
     return CLAW_OK;
@@ -1204,6 +1231,7 @@ int claw_level_step_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const
 {
     if (!ctx || L < 0 || L >= CLAW_MAXLEV || !q_old || !lam_new || !lam_old || !dt) return CLAW_EINVAL;
     if (!ctx->set[L]) return CLAW_ESTATE;
+    if (ctx->kind() == KIND_SWE) return CLAW_EINVAL;   // the adjoint is written for acoustics
     if (ctx->medium == 1 && (!aux || !g_aux)) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
@@ -1220,7 +1248,8 @@ static int reflux_check(claw_ctx* ctx, int L)
 {
     if (!ctx || L < 1 || L >= CLAW_MAXLEV) return CLAW_EINVAL;
     if (!ctx->set[L] || !ctx->set[L - 1]) return CLAW_ESTATE;
-    if (ctx->medium != 0) return CLAW_EINVAL;   // the fix assumes conservation form (uniform medium)
+    // the fix is written for acoustics in conservation form (uniform medium)
+    if (ctx->medium != 0 || ctx->kind() == KIND_SWE) return CLAW_EINVAL;
     return CLAW_OK;
 }
 

@@ -435,6 +435,46 @@ cudaError_t launch_cfl_max(const PatchDev* p, int n, int max_rows, int medium, d
     return cudaGetLastError();
 }
 
+// the same ring for shallow water: max of |u| + sqrt(g h), |v| + sqrt(g h) from the state
+__global__ void cfl_max_state_kernel(const PatchDev* __restrict__ patches, double grav,
+                                     const double* __restrict__ q, unsigned long long* __restrict__ smax)
+{
+    const PatchDev P = patches[blockIdx.x];
+    unsigned long long m = 0ull;
+    const int r0 = blockIdx.y * kBoxRows, r1 = min(P.ny + 2, r0 + kBoxRows);
+    if (r0 >= P.ny + 2) return;
+    const int W = P.nx + 4;
+    const long long WH = (long long)W * (P.ny + 4);
+    const double* b = q + P.qoff;
+    const int w = P.nx + 2, n = w * (r1 - r0);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int r = r0 + k / w, i = k % w;
+        const long long o = (long long)(r + 1) * W + (i + 1);
+        const double h = b[o];
+        const double c = sqrt(grav * h);
+        const double su = fabs(b[WH + o] / h) + c, sv = fabs(b[2 * WH + o] / h) + c;
+        const unsigned long long vu = (unsigned long long)__double_as_longlong(su);
+        const unsigned long long vv = (unsigned long long)__double_as_longlong(sv);
+        m = vu > m ? vu : m;
+        m = vv > m ? vv : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(smax + P.run, m);
+}
+
+cudaError_t launch_cfl_max_state(const PatchDev* p, int n, int max_rows, double grav, const double* q,
+                                 double* smax, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    cfl_max_state_kernel<<<box_rows_grid(n, max_rows), 128, 0, s>>>(p, grav, q,
+                                                                  reinterpret_cast<unsigned long long*>(smax));
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------ time step (Eq. cfl)
 __global__ void dt_update_kernel(const double* __restrict__ minh, const double* __restrict__ cfl, int nruns,
                                  double* __restrict__ smax, double* __restrict__ dt, int* __restrict__ err)

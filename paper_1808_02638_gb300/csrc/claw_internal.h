@@ -145,6 +145,7 @@ struct StepArgs {
     // scheme
     int order = 2, transverse = 2;
     double rho0 = 1.0, K0 = 1.0;   // uniform medium
+    double grav = 0.0;             // shallow water
     // fused epilogue (0 = off)
     int dtupd = 0;                      // the last CTA applies Eq. cfl to dt and resets smax
     double* dt_out = nullptr;
@@ -157,10 +158,13 @@ struct StepArgs {
 // error flag bits written by kernels
 enum : int { ERR_NAN = 1, ERR_CFL = 2, ERR_TIMEOUT = 4 };
 
-// launchers (claw_step.cu)
-cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int nt, int staging,
+// kernel family of a level-step: acoustics in a uniform / cell-wise medium, shallow water
+enum : int { KIND_UNIFORM = 0, KIND_CELLWISE = 1, KIND_SWE = 2 };
+
+// launchers (claw_step.cu; kind: KIND_*)
+cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s);
-int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int nt, int staging);
+int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging);
 cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
                                 int medium, int limiter, int nsm, cudaStream_t s);   // grid: resident CTAs x nsm
 int adjoint_tile();   // the adjoint kernel's square tile edge
@@ -205,6 +209,8 @@ cudaError_t launch_reflux_apply(const RefluxRec* rec, int n, const int* group, i
                                 const PatchDev* cp, const double* dt, const double* buf, double* qc, cudaStream_t s);
 cudaError_t launch_cfl_max(const PatchDev* p, int n, int max_rows, int medium, double c0, const double* aux,
                            double* smax, cudaStream_t s);
+cudaError_t launch_cfl_max_state(const PatchDev* p, int n, int max_rows, double grav, const double* q,
+                                 double* smax, cudaStream_t s);
 cudaError_t launch_dt_update(const double* minh, const double* cfl, int nruns, double* smax,
                              double* dt, int* err, cudaStream_t s);
 

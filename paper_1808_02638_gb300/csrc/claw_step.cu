@@ -1,5 +1,5 @@
-// Dispatch of the fused level-step kernels (instantiated in claw_step_uniform.cu and
-// claw_step_cellwise.cu).
+// Dispatch of the fused level-step kernels (instantiated in claw_step_uniform.cu,
+// claw_step_cellwise.cu and claw_step_swe.cu).
 #include <mutex>
 #include <set>
 
@@ -7,10 +7,14 @@
 
 namespace claw {
 
-static StepKernel pick(int medium, int limiter, int tx, int ty, int nt, int staging)
+static StepKernel pick(int kind, int limiter, int tx, int ty, int nt, int staging)
 {
-    return medium ? step_kernel_cellwise(limiter, tx, ty, nt, staging)
-                  : step_kernel_uniform(limiter, tx, ty, nt, staging);
+    switch (kind) {
+    case KIND_UNIFORM: return step_kernel_uniform(limiter, tx, ty, nt, staging);
+    case KIND_CELLWISE: return step_kernel_cellwise(limiter, tx, ty, nt, staging);
+    case KIND_SWE: return step_kernel_swe(limiter, tx, ty, nt, staging);
+    }
+    return StepKernel{nullptr, 0, 0};
 }
 
 static cudaError_t prepare(const StepKernel& k)
@@ -29,9 +33,9 @@ static cudaError_t prepare(const StepKernel& k)
     return e;
 }
 
-int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int nt, int staging)
+int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging)
 {
-    StepKernel k = pick(medium, limiter, tx, ty, nt, staging);
+    StepKernel k = pick(kind, limiter, tx, ty, nt, staging);
     if (!k.fn || prepare(k) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k.fn, k.nt, k.smem) != cudaSuccess)
@@ -39,10 +43,10 @@ int step_max_ctas_per_sm(int medium, int limiter, int tx, int ty, int nt, int st
     return n;
 }
 
-cudaError_t launch_step(const StepArgs& a, int medium, int limiter, int tx, int ty, int nt, int staging,
+cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s)
 {
-    StepKernel k = pick(medium, limiter, tx, ty, nt, staging);
+    StepKernel k = pick(kind, limiter, tx, ty, nt, staging);
     if (!k.fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare(k);
     if (e != cudaSuccess) return e;

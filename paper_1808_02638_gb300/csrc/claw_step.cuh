@@ -691,5 +691,6 @@ StepKernel step_kernel_for(int lim, int tx, int ty, int nt, int staging)
 
 StepKernel step_kernel_uniform(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_cellwise(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_swe(int lim, int tx, int ty, int nt, int staging);
 
 }  // namespace claw

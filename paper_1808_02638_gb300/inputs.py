@@ -151,6 +151,19 @@ def init_q(run: Run, lev: Level, fn=radial_pulse) -> np.ndarray:
     return pool
 
 
+def init_swe(run: Run, lev: Level, depth=radial_pulse, u0: float = 0.0, v0: float = 0.0) -> np.ndarray:
+    """shallow-water q pool of a level: h = depth(x, y) at cell centres (ghosts included),
+    hu = h u0, hv = h v0.  The default depth is the benchmark's ring pulse (1 <= h <= 2)."""
+    pool = np.zeros(lev.qsize)
+    for n, b in enumerate(lev.boxes):
+        x, y = cell_centres(run, lev, b)
+        v = box_view(pool, lev.qoff[n], int(b[2]), int(b[3]), 3)
+        v[0] = depth(x, y)
+        v[1] = v[0] * u0
+        v[2] = v[0] * v0
+    return pool
+
+
 def gaussian_smooth(a: np.ndarray, sigma: float, truncate: float = 4.0) -> np.ndarray:
     """Separable Gaussian filter, kernel truncated at truncate*sigma, edges mirrored with
     the edge cell repeated (d c b a | a b c d | d c b a)."""

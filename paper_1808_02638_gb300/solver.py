@@ -28,13 +28,18 @@ class Hierarchy:
 
     q0[r][L], rho[r][L], K[r][L]: numpy pools of run r, level L in the inputs layout (rho, K
     only for a cell-wise medium; a uniform medium passes rho0, K0).  All runs' pools of a level
-    are concatenated into one device pool per level."""
+    are concatenated into one device pool per level.  system="shallow_water" steps q = (h, hu, hv)
+    of the shallow water equations with gravity `grav` instead (no medium)."""
 
-    def __init__(self, runs, q0, rho=None, K=None, rho0=1.0, K0=4.0, device=0, tiling=None, reflux=False):
+    def __init__(self, runs, q0, rho=None, K=None, rho0=1.0, K0=4.0, device=0, tiling=None, reflux=False,
+                 system="acoustics", grav=1.0):
         self.runs = runs
         self.nruns = len(runs)
         self.nlev = max(len(r.levels) for r in runs)
         self.medium = 0 if rho is None else 1
+        self.system = claw.SYSTEMS[system]
+        if self.system == claw.CLAW_SYS_SHALLOW_WATER and self.medium:
+            raise ValueError("shallow water has no medium")
         self.dev = torch.device("cuda", device)
         probs = []
         for r in runs:
@@ -50,6 +55,8 @@ class Hierarchy:
                 p.bc[s] = r.bc[s]
             p.medium = self.medium
             p.rho0, p.K0 = rho0, K0
+            p.system = self.system
+            p.grav = grav
             probs.append(p)
         self.ctx = claw.claw_create(probs, device)
         self.q = []        # per level [A, B]
@@ -181,10 +188,17 @@ class Hierarchy:
         return self.runs[0].levels[L].ratio
 
     def init_dt(self):
-        """dt from Eq. cfl with the largest cell speed on any level (before the first step)."""
+        """dt from Eq. cfl with the largest cell speed on any level (before the first step).
+        Shallow water: the speeds come from the state, so the ghosts are filled first (level L
+        from level L-1 at the same time)."""
         self.smax.zero_()
         for L in range(self.nlev):
-            claw.claw_cfl_max(self.ctx, L, self.aux[L], self.smax)
+            if self.system == claw.CLAW_SYS_SHALLOW_WATER:
+                qc = self.q[L - 1][self.cur[L - 1]] if L else None
+                claw.claw_fill_ghost(self.ctx, L, self.q[L][self.cur[L]], qc, qc, 0.0)
+                claw.claw_cfl_max_state(self.ctx, L, self.q[L][self.cur[L]], self.smax)
+            else:
+                claw.claw_cfl_max(self.ctx, L, self.aux[L], self.smax)
         claw.claw_dt_update(self.ctx, 0, self.smax, self.dt)
 
     def step_level(self, L, stream=None):

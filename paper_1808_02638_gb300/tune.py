@@ -18,6 +18,12 @@ from . import claw
 
 CANDIDATES = [(32, 32, 1, 256), (32, 32, 1, 512), (32, 32, 0, 256), (32, 32, 0, 512),
               (32, 16, 1, 256), (16, 16, 1, 128)]
+CANDIDATES_SWE = [(16, 16, 1, 256), (16, 16, 0, 256), (32, 16, 1, 512), (32, 16, 0, 512)]
+
+
+def candidates_for(H):
+    """the tilings the level-step of H's system supports"""
+    return CANDIDATES_SWE if getattr(H, "system", 0) == claw.CLAW_SYS_SHALLOW_WATER else CANDIDATES
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json")
 _lock = threading.Lock()
 
@@ -27,7 +33,7 @@ def _key(H, L):
     hist = {}
     for s in sizes:
         hist[s] = hist.get(s, 0) + 1
-    blob = json.dumps([H.medium, H.runs[0].limiter, H.runs[0].order, H.runs[0].transverse,
+    blob = json.dumps([H.medium, getattr(H, "system", 0), H.runs[0].limiter, H.runs[0].order, H.runs[0].transverse,
                        sorted((f"{a}x{b}", n) for (a, b), n in hist.items()),
                        torch.cuda.get_device_name(H.dev)])
     return hashlib.sha256(blob.encode()).hexdigest()[:24]
@@ -82,7 +88,7 @@ def tune_level(H, L, use_cache=True, candidates=None):
     if float(H.dt.max()) <= 0.0:
         H.init_dt()
     timings = {}
-    for c in candidates or CANDIDATES:
+    for c in candidates or candidates_for(H):
         try:
             timings[c] = time_tiling(H, L, c)
         except claw.ClawError:

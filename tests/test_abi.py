@@ -34,12 +34,26 @@ def test_library_loads_and_binding_covers_the_header():
     assert claw.load().claw_strerror(5).decode() == "NaN or Inf in the state"
 
 
-def test_binding_structs_match_header_layout():
+def test_binding_structs_match_header_layout(tmp_path):
+    # the C compiler's offsets of every field of the header's structs equal the binding's
     from paper_1808_02638_gb300 import claw
-    # claw_box: 6 int32 + 2 int64; claw_problem: 4 doubles, 3 ints, 8 ratios, 1 double, ...
-    assert ctypes.sizeof(claw.claw_box) == 40
-    assert claw.claw_problem.cfl.offset == 4 * 8 + 3 * 4 + 8 * 4 + 4   # aligned to 8
-    assert claw.claw_problem.rho0.offset % 8 == 0
+    structs = {"claw_problem": claw.claw_problem, "claw_box": claw.claw_box}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "claw.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln)}
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
 
 
 def test_product_package_does_not_import_the_oracle():
