@@ -239,6 +239,18 @@ def cpu_per_config():
     amr("c4", run, [inputs.coef_pool(l, r2, 4 ** L) for L, l in enumerate(run.levels)],
         [inputs.coef_pool(l, k2, 4 ** L) for L, l in enumerate(run.levels)], 1,
         "1 coarse step of the first of the 64 runs")
+    # shallow water: 64 of the 4096 32x32 patches of the 2048^2 workload, one step each
+    run = inputs.config1()
+    lev = run.levels[0]
+    qs = inputs.init_swe(run, lev)
+    t0 = time.perf_counter()
+    for nb in range(64):
+        qb = inputs.box_view(qs, lev.qoff[nb], 32, 32, 3).copy()
+        oracle.swe_step(qb, lev.dx, lev.dy, 5e-4, 1.0)
+    dt = time.perf_counter() - t0
+    out["swe1"] = {"value": 64 * 32 * 32 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "one step of 64 of the 4096 32x32 patches of the shallow-water workload",
+                   "seconds": dt}
     return out
 
 

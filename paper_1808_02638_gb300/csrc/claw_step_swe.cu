@@ -22,6 +22,19 @@
 // A fluctuation with coefficients d_p on r_p splits on the transverse eigenvectors
 // (1, un, ut - c), (0, 1, 0), (1, un, ut + c) with strengths (d1 + d3)/2 - d2/(2c),
 // c (d3 - d1), (d1 + d3)/2 + d2/(2c): no second Roe solve is needed.
+//
+// Algorithmic FP64 instructions per cell-update (each edge once, no halo recomputation; a
+// reciprocal or reciprocal square root costs 5 FP64-pipe instructions and a division 8, as the
+// profiler's instruction counters show for the CUDA routines):
+//   P0  rsqrt + 3 DMUL                                                        8
+//   PA  per edge: sum, reciprocal, two averages (4), celerity (2 + rsqrt + 2),
+//       jumps 3, strengths 7                                         2 x 29 = 58
+//   PB  per edge: speeds 2, |r|^2 of waves 1, 3 with one reciprocal (11), upwind projections
+//       2 x (1 + 2 + 2), limiters 3, h_p 3 x 4 + 1                    2 x 39 = 78
+//   PC  per cell and direction: two sides of 42 (speeds 2, parts 3, normal 7, transverse input
+//       3, split 27) less the 9 accumulations into zero; the update Q - l N   2 x 75 + 6 = 156
+//   PD  transverse differences, 3 x 8                                        24
+//   total 324 (the tile's halo adds about a third in the kernel).
 #include "claw_step.cuh"
 
 namespace claw {
@@ -62,8 +75,12 @@ __device__ __forceinline__ void tsplit(double d1, double d2, double d3, double u
     const double b3 = fma(0.5, dh, t);
     const double b2 = c * (d3 - d1);
     const double m1 = ut - c, m3 = ut + c;
-    const double gm1 = neg(m1) * b1, gm2 = neg(ut) * b2, gm3 = neg(m3) * b3;
-    const double gp1 = pos(m1) * b1, gp2 = pos(ut) * b2, gp3 = pos(m3) * b3;
+    // each family goes one way: its product lands in the down- or the up-going part
+    const double g1 = m1 * b1, g2 = ut * b2, g3 = m3 * b3;
+    const bool n1 = __double_as_longlong(m1) < 0, n2 = __double_as_longlong(ut) < 0,
+               n3 = __double_as_longlong(m3) < 0;
+    const double gm1 = n1 ? g1 : 0.0, gm2 = n2 ? g2 : 0.0, gm3 = n3 ? g3 : 0.0;
+    const double gp1 = n1 ? 0.0 : g1, gp2 = n2 ? 0.0 : g2, gp3 = n3 ? 0.0 : g3;
     const double Gm = gm1 + gm3, Gp = gp1 + gp3;
     bm[0] += Gm;
     bm[1] += fma(un, Gm, gm2);
@@ -256,19 +273,21 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
             const int u1 = __double_as_longlong(s1) > 0 ? eb : ef;
             const int u2 = __double_as_longlong(un) > 0 ? eb : ef;
             const int u3 = __double_as_longlong(s3) > 0 ? eb : ef;
+            // 1 / (r1 . r1) and 1 / (r3 . r3) from one reciprocal of their product
+            const double w = fma(ut, ut, 1.0);
+            const double rr1 = fma(s1, s1, w), rr3 = fma(s3, s3, w);
+            const double ip = 1.0 / (rr1 * rr3);
             double mu1, mu2, mu3;
             {   // wave 1 on (1, un - c, ut)
                 const double unI = E[u1], utI = E[plane + u1], cI = E[2 * plane + u1];
-                const double rr = fma(s1, s1, fma(ut, ut, 1.0));
                 const double ri = fma(unI - cI, s1, fma(utI, ut, 1.0));
-                mu1 = Lim<LIM>::f(a1, E[4 * plane + u1] * ri / rr);
+                mu1 = Lim<LIM>::f(a1, E[4 * plane + u1] * ri * (rr3 * ip));
             }
             mu2 = Lim<LIM>::f(a2, E[5 * plane + u2]);
             {   // wave 3 on (1, un + c, ut)
                 const double unI = E[u3], utI = E[plane + u3], cI = E[2 * plane + u3];
-                const double rr = fma(s3, s3, fma(ut, ut, 1.0));
                 const double ri = fma(unI + cI, s3, fma(utI, ut, 1.0));
-                mu3 = Lim<LIM>::f(a3, E[6 * plane + u3] * ri / rr);
+                mu3 = Lim<LIM>::f(a3, E[6 * plane + u3] * ri * (rr1 * ip));
             }
             const double k1 = fabs(s1), k2 = fabs(un), k3 = fabs(s3);
             const double hl = -0.5 * l;

@@ -3,14 +3,14 @@ plain path (one launch per patch, eager) on the same hierarchy, and the adjoint'
 
   python -m paper_1808_02638_gb300.measure [names...] [--nruns N] [--ncoarse N] [--every N] [--no-plain]
 
-(names: c0 c2 c3 c4 e1; default all; the options shrink the batched workload for a profiler)
+(names: c0 c2 c3 c4 e1 swe1; default all; the options shrink the batched workload for a profiler)
 
 Each workload reports interior cell-updates per second (a cell advanced one step on its level;
 ghost cells and halo recomputation are not counted), algorithmic HBM bytes per second (q read
 and written, 48 B per cell-update; 64 B with the cell-wise medium's rho, K), the fraction of the
 measured copy bandwidth, and the fraction of the FP64 pipe's issue rate used by the algorithmic
-FP64 instructions of the step (42 per cell-update uniform, 78 cell-wise; the kernel source
-states how they are counted).  Times are CUDA events around graph replays of whole coarse steps
+FP64 instructions of the step (42 per cell-update uniform, 78 cell-wise, 324 shallow water; the
+kernel sources state how they are counted).  Times are CUDA events around graph replays of whole coarse steps
 (ghost fill, every level-step with its substeps, averaging, the Eq. cfl update).
 """
 from __future__ import annotations
@@ -27,6 +27,7 @@ from .solver import Hierarchy
 
 FP64_INSTR_UNIFORM = 42
 FP64_INSTR_CELLWISE = 78
+FP64_INSTR_SWE = 324     # shallow water, Roe solvers (claw_step_swe.cu states the count)
 BYTES_UNIFORM = 48.0
 BYTES_CELLWISE = 64.0
 FP64_ISSUE_PEAK_G = 152 * 2 * 2.07   # G FP64 instructions / s: 152 SMs x 2 per clock x 2.07 GHz
@@ -247,6 +248,37 @@ def config4(nruns=64, ncoarse=100, every=20, plain=True):
                                 "functional": "sum over runs of sum p^2 over each run's 16x16 receiver"}})
 
 
+def time_stepper(H, nsteps, warm=3):
+    """ms per step of a one-level hierarchy through its fused stepper (graph replays of the
+    persistent step with the device Eq. cfl update, then of the ghost copy)"""
+    st = H.fused_stepper()
+    for _ in range(warm):
+        st.step()
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(nsteps):
+        st.step()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / nsteps
+
+
+def swe1(nsteps=50, n=2048):
+    """The second system through the same path: shallow water (g = 1) on the bench's 2048^2 as
+    4096 patches of 32^2, the ring pulse as depth (1 <= h <= 2), at rest, MC, transverse 2."""
+    run = inputs.config1(n)
+    H = Hierarchy([run], [[inputs.init_swe(run, run.levels[0])]], system="shallow_water", grav=1.0)
+    H.init_dt()
+    tiling = tune_all(H)
+    ms = time_stepper(H, nsteps)
+    plain = time_plain(H, 5)
+    return _report(f"shallow water, {n}^2 as {(n // 32) ** 2} patches of 32^2, ring-pulse depth, g = 1, MC, "
+                   f"{nsteps} steps", H, ms, plain, FP64_INSTR_SWE, BYTES_UNIFORM,
+                   {"l2": "streams from HBM (254 MB of q pools)", "tiling": tiling,
+                    "dt_final": float(H.dt[0])})
+
+
 def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=0.002, max_size=260):
     """Analog of the paper's benchmark (Sec. 4.1-4.2): radial pulse in a uniform medium, outflow
     (extrapolation) boundaries, van Leer, 3 levels of ratio 2 over a 1000^2 base tiled in 4 x 4
@@ -302,7 +334,7 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
             "note": "eager launches (the hierarchy changes at every regrid); wall clock includes the regrids"}
 
 
-WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4, "e1": e1}
+WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4, "e1": e1, "swe1": swe1}
 # (bench.py reports every workload above; e1 runs 200 coarse steps there)
 
 

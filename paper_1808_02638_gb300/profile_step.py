@@ -1,10 +1,10 @@
 """Profiling driver: a few eager level-steps of the 2048 x 2048 workload as 4096 patches of
 32 x 32, for a profiler to capture single kernel launches.
 
-  python -m paper_1808_02638_gb300.profile_step [uniform|cellwise] [nsteps] [fused|split] [tx,ty,staging,threads]
+  python -m paper_1808_02638_gb300.profile_step [uniform|cellwise|swe] [nsteps] [fused|split] [tx,ty,staging,threads]
 
 uniform: radial pulse, rho = 1, K = 4; cellwise: the same tiling over the smoothed random
-medium of the heterogeneous workload.  fused (default): claw_level_advance (the step with Eq.
+medium of the heterogeneous workload; swe: shallow water (g = 1) with the ring pulse as depth.  fused (default): claw_level_advance (the step with Eq.
 cfl on its last CTA, then the ghost copy of q^{n+1}); split: fill, step, dt update.  The tiling
 defaults to 32 x 32 tiles, tensor bulk-copy staging, 256 threads.
 """
@@ -25,6 +25,10 @@ def main():
     if medium == "uniform":
         run = inputs.config1()
         H = Hierarchy([run], [[inputs.init_q(run, run.levels[0])]], rho0=1.0, K0=4.0, tiling=tiling)
+    elif medium == "swe":
+        run = inputs.config1()
+        H = Hierarchy([run], [[inputs.init_swe(run, run.levels[0])]], tiling=tiling, system="shallow_water",
+                      grav=1.0)
     else:
         run, r2, k2 = inputs.config3(n)
         run.levels = [inputs.Level(n, n, 2.0 / n, 2.0 / n, inputs.uniform_tiling(n, n, 32, 32))]
