@@ -114,7 +114,9 @@ int claw_set_level(claw_ctx* ctx, int32_t level, const claw_box* boxes, int32_t 
 
 /* Chooses the tiling of the fused level-step for a level: tx x ty interior cells per tile,
  * the staging of the tile's q planes into shared memory (0 = cooperative loads,
- * 1 = tensor-memory-accelerator bulk copies, only when every box has even nx and offsets) and
+ * 1 = tensor-memory-accelerator bulk copies into two buffers, 2 = bulk copies into one buffer with
+ * three CTAs per SM, acoustics 32x16 with 256 threads only; 1 and 2 only when every box has even
+ * nx and offsets) and
  * the threads per CTA (0 = default).  Supported for acoustics: 32x32 with 256 or 512 threads,
  * 32x16 with 256, 16x16 with 128; claw_set_level installs 32x32, 256 threads.  Supported for
  * shallow water: 16x16 with 256 threads, 32x16 with 512; claw_set_level installs 16x16.

@@ -1004,7 +1004,11 @@ int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t st
             : (tx == 32 && ty == 32 && (threads == 0 || threads == 256 || threads == 512)) ||
                   (tx == 32 && ty == 16 && (threads == 0 || threads == 256)) ||
                   (tx == 16 && ty == 16 && (threads == 0 || threads == 128));
-    if (!shape_ok || staging < 0 || staging > 1 || (staging == 1 && !ctx->tma_ok[L])) return CLAW_EINVAL;
+    // staging 2 (one bulk-copy buffer, three CTAs per SM) exists for the acoustics 32x16 tiles
+    const bool staging2_ok = ctx->kind() != KIND_SWE && tx == 32 && ty == 16 && (threads == 0 || threads == 256);
+    if (!shape_ok || staging < 0 || staging > 2 || (staging == 2 && !staging2_ok) ||
+        (staging >= 1 && !ctx->tma_ok[L]))
+        return CLAW_EINVAL;
     DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
     d.staging = staging;
@@ -1139,7 +1143,7 @@ int claw_level_step(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new
     cudaStream_t s = (cudaStream_t)stream;
     StepArgs a = make_args(ctx, L, q_old, q_new, aux, dt, smax);
     int staging = d.staging;
-    if (staging == 1) {
+    if (staging >= 1) {
         a.tmaps = get_tmaps(ctx, L, q_old, s);
         if (!a.tmaps) staging = 0;   // no descriptor (e.g. first use inside a graph capture)
     }
@@ -1170,7 +1174,7 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
         a.nruns = ctx->nruns;
     }
     int staging = d.staging;
-    if (staging == 1) {
+    if (staging >= 1) {
         a.tmaps = get_tmaps(ctx, L, q_old, s);
         if (!a.tmaps) staging = 0;
     }

@@ -201,12 +201,14 @@ __device__ __forceinline__ void finish_cta(const StepArgs& A)
 
 // ------------------------------------------------------------------------- the kernel
 // MED: 0 uniform medium (rho0, K0), 1 cell-wise aux planes.
-// STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered).
+// STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered: the next tile streams in
+// during the whole of this one), 2 tensor bulk copies into one buffer (the next tile is requested
+// once this one's state has been read, in phase D) with registers capped for three CTAs per SM.
 template <int MED, int LIM, int TX, int TY, int NT, int STAGE>
-__global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
+__global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const StepArgs A)
 {
     using G = Geo<TX, TY>;
-    constexpr int NBUF = STAGE ? 2 : 1;
+    constexpr int NBUF = STAGE == 1 ? 2 : 1;
     constexpr int NPER = (TX * TY + NT - 1) / NT;
     extern __shared__ __align__(128) double smem[];
     double* qbuf = smem;                            // NBUF x QSTRIDE
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
 
     int it = 0;
     for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++it) {
-        const int b = STAGE ? (it & 1) : 0;
+        const int b = STAGE == 1 ? (it & 1) : 0;
         const TileDev T = A.tiles[t];
         const PatchDev P = A.patches[T.patch];
         const int tx = T.tx, ty = T.ty, x0 = T.x0, y0 = T.y0;
@@ -278,13 +280,17 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
 
         if (STAGE) {
             const int tn = t + gridDim.x;
-            if (tid == 0 && tn < A.ntiles) issue(tn, b ^ 1);
-            bool ok = mbar_wait_bounded(&bar[b], (unsigned)((it >> 1) & 1));
+            if (STAGE == 1 && tid == 0 && tn < A.ntiles) issue(tn, b ^ 1);
+            // each buffer's barrier completes once per use: every other tile with two buffers,
+            // every tile with one
+            const unsigned par = STAGE == 1 ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1);
+            bool ok = mbar_wait_bounded(&bar[b], par);
             if (__syncthreads_or(!ok)) {   // a copy never landed: report and stop this CTA
                 if (tid == 0) {
                     atomicOr(A.err, ERR_TIMEOUT);
                     // let the prefetch in flight (if any) land before the CTA exits
-                    if (tn < A.ntiles) mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+                    if (STAGE == 1 && tn < A.ntiles)
+                        mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
                     finish_cta(A);   // keeps the completion count consistent
                 }
                 return;
@@ -584,6 +590,9 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepArgs A)
         }
 
         // ---------------------------------------------------------------- phase D: update, store
+        // one staging buffer: the tile's state was last read in phase C (behind the barrier
+        // above), so the next tile's copy can land while this one finishes
+        if (STAGE == 2 && tid == 0 && t + (int)gridDim.x < A.ntiles) issue(t + gridDim.x, 0);
         double kT = 0, kU = 0;
         if (MED == 0 && trans) {
             kT = s_k[10];
@@ -655,7 +664,7 @@ StepKernel step_kernel_entry()
 {
     StepKernel k;
     k.fn = step_kernel<MED, LIM, TX, TY, NT, STAGE>;
-    k.smem = Geo<TX, TY>::smem_bytes(STAGE ? 2 : 1);
+    k.smem = Geo<TX, TY>::smem_bytes(STAGE == 1 ? 2 : 1);
     k.nt = NT;
     return k;
 }
@@ -669,8 +678,10 @@ StepKernel step_kernel_select(int tx, int ty, int nt, int staging)
         return staging ? step_kernel_entry<MED, LIM, 32, 32, 256, 1>() : step_kernel_entry<MED, LIM, 32, 32, 256, 0>();
     if (tx == 32 && ty == 32 && nt == 512)
         return staging ? step_kernel_entry<MED, LIM, 32, 32, 512, 1>() : step_kernel_entry<MED, LIM, 32, 32, 512, 0>();
-    if (tx == 32 && ty == 16 && (nt == 0 || nt == 256))
+    if (tx == 32 && ty == 16 && (nt == 0 || nt == 256)) {
+        if (staging == 2) return step_kernel_entry<MED, LIM, 32, 16, 256, 2>();
         return staging ? step_kernel_entry<MED, LIM, 32, 16, 256, 1>() : step_kernel_entry<MED, LIM, 32, 16, 256, 0>();
+    }
     if (tx == 16 && ty == 16 && (nt == 0 || nt == 128))
         return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1>() : step_kernel_entry<MED, LIM, 16, 16, 128, 0>();
     return StepKernel{nullptr, 0, 0};

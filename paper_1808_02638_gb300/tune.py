@@ -17,7 +17,7 @@ import torch
 from . import claw
 
 CANDIDATES = [(32, 32, 1, 256), (32, 32, 1, 512), (32, 32, 0, 256), (32, 32, 0, 512),
-              (32, 16, 1, 256), (16, 16, 1, 128)]
+              (32, 16, 1, 256), (32, 16, 2, 256), (16, 16, 1, 128)]
 CANDIDATES_SWE = [(16, 16, 1, 256), (16, 16, 0, 256), (32, 16, 1, 512), (32, 16, 0, 512)]
 
 

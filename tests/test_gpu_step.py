@@ -31,7 +31,7 @@ def _uniform_planes(n, rho0=1.0, K0=4.0):
     return np.full((n + 4, n + 4), rho0), np.full((n + 4, n + 4), K0)
 
 
-@pytest.mark.parametrize("tiling", [(32, 32, 1), (32, 32, 0), (32, 16, 1), (16, 16, 0), (16, 16, 1)])
+@pytest.mark.parametrize("tiling", [(32, 32, 1), (32, 32, 0), (32, 16, 1), (32, 16, 2), (16, 16, 0), (16, 16, 1)])
 def test_uniform_pulse_100x100_one_and_50_steps(orc, tiling):
     run, q = single_grid(100)
     H = _hier(run, q, tiling=tiling)
@@ -76,7 +76,7 @@ def test_boundary_conditions_ten_steps(orc, bc):
     assert rel_err(H.interior(0, 0, 0), want) <= TOLN
 
 
-@pytest.mark.parametrize("tiling", [(32, 32, 1), (32, 16, 0), (16, 16, 1)])
+@pytest.mark.parametrize("tiling", [(32, 32, 1), (32, 16, 0), (32, 16, 2), (16, 16, 1)])
 def test_cellwise_medium_one_and_100_steps(orc, tiling):
     n = 64
     run, rho2, K2 = inputs.config3(n)
