@@ -175,6 +175,10 @@ def time_oracle(npatch: int, workers: int, reps: int = 1):
     return len(patches) * PATCH * PATCH, times
 
 
+STAGINGS = {0: "cooperative", 1: "tensor bulk-copy (two buffers)",
+            2: "tensor bulk-copy (one buffer, three CTAs per SM)"}
+
+
 def cpu_baseline(target_s: float = 15.0):
     workers = os.cpu_count() or 1
     # calibrate on one full level-step, then repeat it to fill ~target_s of wall time
@@ -449,7 +453,7 @@ def main():
                                         f"{ALG_FLOPS_PER_CELL} flops, {BYTES_PER_CELL:.0f} B",
                      "kernel": "level-step (uniform medium, MC), autotuned tiling "
                                f"{tiling[0]}x{tiling[1]} tiles, {tiling[3]} threads, "
-                               f"{'tensor bulk-copy' if tiling[2] else 'cooperative'} staging",
+                               f"{STAGINGS[tiling[2]]} staging",
                      "kernel_ms": kern_avg_s * 1e3,
                      "peak_source": "FP64 pipe: 152 SMs x 2 instructions/clk x 2.07 GHz (derived; independent "
                                     "DFMA, DADD or DMUL loops measured 1.684 per SM per clk, 530 G/s)",
