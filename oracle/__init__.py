@@ -76,6 +76,7 @@ def lib():
                                                        dbl, I, I]
             L.orc_average_down_adjoint.argtypes = [I, BP, D, I, BP, D, I, I, I]
             L.orc_swe_step.argtypes = [I, I, I, dbl, dbl, dbl, I, I, I, dbl, D, D, D]
+            L.orc_swe_step_edges.argtypes = [I, I, I, dbl, dbl, dbl, I, I, I, dbl, D, D, D, D]
             L.orc_swe_roe_x.argtypes = [dbl] * 7 + [D, D]
             L.orc_swe_cfl_max.argtypes = [I, I, I, dbl, D]
             L.orc_swe_cfl_max.restype = dbl
@@ -183,6 +184,20 @@ def swe_step(q, dx, dy, dt, grav, order=2, transverse=2, limiter="mc"):
     if rc:
         raise ValueError(f"orc_swe_step failed ({rc})")
     return qn, sm.value
+
+
+def swe_step_edges(q, dx, dy, dt, grav, order=2, transverse=2, limiter="mc"):
+    """:func:`swe_step` that also returns the per-edge quantities, like :func:`step_edges`."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    _, H, W = q.shape
+    qn = q.copy()
+    sm = ctypes.c_double(0.0)
+    e = np.zeros((6, 3, H, W))
+    rc = lib().orc_swe_step_edges(W - 2 * MBC, H - 2 * MBC, MBC, dx, dy, dt, order, transverse,
+                                  _lim(limiter), float(grav), _p(q), _p(qn), ctypes.byref(sm), _p(e))
+    if rc:
+        raise ValueError(f"orc_swe_step_edges failed ({rc})")
+    return qn, sm.value, dict(zip(("amx", "apx", "amy", "apy", "F", "G"), e))
 
 
 def swe_roe_x(left, right, grav):

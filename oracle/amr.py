@@ -9,7 +9,8 @@ the average of the fine cells ("updating", Sec. 2.2-2.3).  dt on level 0 follows
 rule dt = nu_desired * min(dx, dy) / s (Eq. cfl) with s the largest speed seen on any level
 in the previous coarse step (or by cfl_max before the first), and dt_{L+1} = dt_L / r_L.
 The conservation fix of Sec. 2.3 ("refluxing", `reflux=True`; meaningful for a uniform
-medium, where acoustics is in conservation form) corrects, after the average, every coarse
+medium, where acoustics is in conservation form, and for shallow water, whose Roe solver is
+conservative: A-dQ + A+dQ = f(Q_R) - f(Q_L)) corrects, after the average, every coarse
 cell C that is not covered by the finer level but shares an edge e with it: the flux C's update
 used through e is replaced by the average of the fine fluxes through the r fine edges over the r
 substeps.  In flux form (f(Q) = A Q, A- / A+ the fluctuations, F~ the correction-plus-transverse
@@ -17,7 +18,8 @@ flux), with C left of e and the fine cells F_b right of their edges e_b:
     F_e   = f(Q_C^n) + A-dQ_e + F~_e                              (coarse step)
     F_b^k = f(Q_F^k) - A+dQ_b^k + F~_b^k                          (fine substep k)
     Q_C  += -(dt/dx) [ (1/r^2) sum_{k,b} (F_b^k - f(Q_C^n)) - (F_e - f(Q_C^n)) ]
-where F_b^k - f(Q_C^n) = A (Q_F^k - Q_C^n) - A+dQ_b^k + F~_b^k is the paper's C1 + C2 + C3 and
+where F_b^k - f(Q_C^n) = A (Q_F^k - Q_C^n) - A+dQ_b^k + F~_b^k is the paper's C1 + C2 + C3 (for
+shallow water f(Q_F^k) - f(Q_C^n) - A+dQ_b^k + F~_b^k with the equations' flux f) and
 F_e - f(Q_C^n) = A-dQ_e + F~_e its coarse part; mirrored for C right of e and in y.
 """
 from __future__ import annotations
@@ -25,7 +27,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import (MBC, average_down, average_down_adjoint, cfl_max, level_fill_ghost,
-               level_fill_ghost_adjoint, step, step_adjoint, step_edges, swe_cfl_max, swe_step)
+               level_fill_ghost_adjoint, step, step_adjoint, step_edges, swe_cfl_max, swe_step,
+               swe_step_edges)
 
 
 def _view(pool, off, nx, ny, ncomp):
@@ -96,8 +99,6 @@ class OracleHierarchy:
         self.reflux = reflux
         self.swe = system == "shallow_water"
         self.grav = grav
-        if self.swe and reflux:
-            raise ValueError("the conservation fix is written for acoustics")
         self.levels = run.levels
         self.q = [np.array(a, dtype=np.float64, copy=True) for a in q]
         self.rho = [np.asarray(a, dtype=np.float64) for a in rho] if not self.swe else None
@@ -142,7 +143,12 @@ class OracleHierarchy:
             nx, ny = int(b[2]), int(b[3])
             qb = _view(qold, lev.qoff[n], nx, ny, 3)
             if self.swe:
-                out, s = swe_step(qb, lev.dx, lev.dy, dt, self.grav, run.order, run.transverse, run.limiter)
+                if edges is None:
+                    out, s = swe_step(qb, lev.dx, lev.dy, dt, self.grav, run.order, run.transverse, run.limiter)
+                else:
+                    out, s, e = swe_step_edges(qb, lev.dx, lev.dy, dt, self.grav, run.order, run.transverse,
+                                               run.limiter)
+                    edges.append(e)
                 _view(qnew, lev.qoff[n], nx, ny, 3)[:, MBC:MBC + ny, MBC:MBC + nx] = \
                     out[:, MBC:MBC + ny, MBC:MBC + nx]
                 sm = max(sm, s)
@@ -160,8 +166,18 @@ class OracleHierarchy:
         return qnew, sm
 
     # ---------------------------------------------------------- conservation fix (Sec. 2.3)
-    def _flux_diff(self, L, n, i, j, d, dq):
-        """A dq (d = 0) or B dq (d = 1) with the medium of cell (i, j) of box n of level L"""
+    def _flux_diff(self, L, n, i, j, d, qf, qc):
+        """f(qf) - f(qc) (d = 0) or g(qf) - g(qc) (d = 1): for acoustics A (qf - qc) or
+        B (qf - qc) with the medium of cell (i, j) of box n of level L; for shallow water the
+        nonlinear fluxes of the equations themselves"""
+        if self.swe:
+            def flux(q):
+                h, hu, hv = q
+                g2 = 0.5 * self.grav * h * h
+                return np.array([hu, hu * hu / h + g2, hu * hv / h]) if d == 0 else \
+                    np.array([hv, hu * hv / h, hv * hv / h + g2])
+            return flux(qf) - flux(qc)
+        dq = qf - qc
         lev = self.levels[L]
         b = lev.boxes[n]
         nx, ny = int(b[2]), int(b[3])
@@ -197,7 +213,7 @@ class OracleHierarchy:
             acc = np.zeros(3)
             for (fi, fj) in cells:
                 i, j = MBC + fi, MBC + fj
-                t = self._flux_diff(Lf, n_f, fi, fj, d, qf[:, j, i] - qc)
+                t = self._flux_diff(Lf, n_f, fi, fj, d, qf[:, j, i], qc)
                 if d == 0:
                     t = t + (-e["apx"][:, j, i] + e["F"][:, j, i] if side > 0 else e["amx"][:, j, i + 1] + e["F"][:, j, i + 1])
                 else:

@@ -74,6 +74,10 @@ double orc_cfl_max(int nx, int ny, int mbc, const double* rho, const double* K);
 int orc_swe_step(int nx, int ny, int mbc, double dx, double dy, double dt,
                  int order, int transverse, int limiter, double grav,
                  const double* q, double* qnew, double* smax);
+/* orc_swe_step that also returns the 18 per-edge planes of orc_step_edges (or NULL) */
+int orc_swe_step_edges(int nx, int ny, int mbc, double dx, double dy, double dt,
+                       int order, int transverse, int limiter, double grav,
+                       const double* q, double* qnew, double* smax, double* edges);
 /* Roe solve at one x-edge: waves[0..8] = W1, W2, W3 (h, hu, hv); speeds[0..2] */
 void orc_swe_roe_x(double hl, double hul, double hvl, double hr, double hur, double hvr,
                    double grav, double* waves, double* speeds);

@@ -201,9 +201,12 @@ static int salloc(double** out, long n)
     return *out ? 0 : -1;
 }
 
-int orc_swe_step(int nx, int ny, int mbc, double dx, double dy, double dt,
-                 int order, int transverse, int limiter, double grav,
-                 const double* q, double* qnew, double* smax)
+/* One step of every interior cell; with `edges` not NULL it also receives the six per-edge
+ * planes-of-3 arrays A-dQ, A+dQ (x-edges), B-dQ, B+dQ (y-edges), F~, G~ stored at the edge's
+ * right / upper cell, as orc_step_edges does for acoustics (the conservation fix reads them). */
+int orc_swe_step_edges(int nx, int ny, int mbc, double dx, double dy, double dt,
+                       int order, int transverse, int limiter, double grav,
+                       const double* q, double* qnew, double* smax, double* edges)
 {
     if (nx < 1 || ny < 1 || mbc < 2 || !(dx > 0) || !(dy > 0) || !(grav > 0)) return -1;
     sgeom G = {nx, ny, mbc, nx + 2 * mbc, ny + 2 * mbc};
@@ -238,8 +241,19 @@ int orc_swe_step(int nx, int ny, int mbc, double dx, double dy, double dt,
             }
         }
     if (smax) *smax = sm;
+    if (edges) {
+        const double* src[6] = {amx, apx, amy, apy, F, Gt};
+        for (int a = 0; a < 6; ++a) memcpy(edges + (long)a * 3 * pl, src[a], sizeof(double) * 3 * pl);
+    }
     free(rec); free(amx); free(apx); free(amy); free(apy); free(F); free(Gt);
     return 0;
+}
+
+int orc_swe_step(int nx, int ny, int mbc, double dx, double dy, double dt,
+                 int order, int transverse, int limiter, double grav,
+                 const double* q, double* qnew, double* smax)
+{
+    return orc_swe_step_edges(nx, ny, mbc, dx, dy, dt, order, transverse, limiter, grav, q, qnew, smax, 0);
 }
 
 void orc_swe_roe_x(double hl, double hul, double hvl, double hr, double hur, double hvr,

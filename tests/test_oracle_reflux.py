@@ -73,6 +73,28 @@ def test_reflux_conserves_the_composite_integral_on_a_periodic_domain(orc, nlev,
     assert drift[False].max() >= 1e-6 * scale, drift[False]
 
 
+@pytest.mark.parametrize("nlev,ncoarse", [(2, 6), (3, 2)])
+def test_shallow_water_reflux_conserves_the_composite_integral(orc, nlev, ncoarse):
+    # the same fix with the shallow-water flux f: the Roe solver is conservative
+    # (A-dQ + A+dQ = f(Q_R) - f(Q_L)), so the flux form holds with f(Q_F) - f(Q_C) for A dQ
+    from oracle.amr import OracleHierarchy
+    run = inputs.Run(*inputs.PULSE_DOMAIN, bc=(1, 1, 1, 1))
+    annuli, seeds = [(0.2, 0.45), (0.25, 0.35)][:nlev - 1], [2002, 2003][:nlev - 1]
+    run.levels = inputs.amr_levels(run, 32, 4, annuli, seeds)
+    q0 = [inputs.init_swe(run, lev, depth=lambda x, y: inputs.radial_pulse(x - 0.1, y + 0.05), u0=0.3, v0=-0.2)
+          for lev in run.levels]
+    drift = {}
+    for reflux in (True, False):
+        O = OracleHierarchy(run, q0, reflux=reflux, system="shallow_water", grav=1.0)
+        m0 = _composite(O)
+        for _ in range(ncoarse):
+            O.coarse_step()
+        drift[reflux] = np.abs(_composite(O) - m0)
+    scale = 4.0 * 2.0   # domain area x max |q|
+    assert (drift[True] <= 1e-13 * scale).all(), drift[True]
+    assert drift[False].max() >= 1e-6 * scale, drift[False]
+
+
 def test_interface_records_follow_the_box_geometry(orc):
     from oracle.amr import interface
     run = inputs.Run(*inputs.PULSE_DOMAIN)
