@@ -620,6 +620,7 @@ StepArgs make_args(claw_ctx* ctx, int L, const double* q_old, double* q_new, con
     a.rho0 = ctx->rho0;
     a.K0 = ctx->K0;
     a.grav = ctx->grav;
+    a.swe = ctx->kind() == KIND_SWE;
     return a;
 }
 
@@ -1252,8 +1253,8 @@ static int reflux_check(claw_ctx* ctx, int L)
 {
     if (!ctx || L < 1 || L >= CLAW_MAXLEV) return CLAW_EINVAL;
     if (!ctx->set[L] || !ctx->set[L - 1]) return CLAW_ESTATE;
-    // the fix is written for acoustics in conservation form (uniform medium)
-    if (ctx->medium != 0 || ctx->kind() == KIND_SWE) return CLAW_EINVAL;
+    // the fix needs conservation form: acoustics in a uniform medium, or shallow water
+    if (ctx->medium != 0) return CLAW_EINVAL;
     return CLAW_OK;
 }
 

@@ -146,6 +146,7 @@ struct StepArgs {
     int order = 2, transverse = 2;
     double rho0 = 1.0, K0 = 1.0;   // uniform medium
     double grav = 0.0;             // shallow water
+    int swe = 0;                   // 1: the shallow water system (the conservation fix reads it)
     // fused epilogue (0 = off)
     int dtupd = 0;                      // the last CTA applies Eq. cfl to dt and resets smax
     double* dt_out = nullptr;

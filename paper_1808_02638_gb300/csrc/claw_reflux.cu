@@ -1,5 +1,7 @@
 // claw_reflux.cu -- the conservation fix of Sec. 2.3 ("refluxing") for a uniform medium, where
-// the acoustics system is in conservation form: f(Q) = A Q, g(Q) = B Q.
+// the acoustics system is in conservation form: f(Q) = A Q, g(Q) = B Q, and for the shallow water
+// equations, whose Roe solver is conservative (A-dQ + A+dQ = f(Q_R) - f(Q_L)): there A (Q_F - Q_C)
+// below becomes f(Q_F) - f(Q_C) with the equations' own flux.
 //
 // A coarse cell C next to the fine region (not covered by it) is updated by the coarse step with
 // the flux F_e through its edge e; the fine cells along e see r fine fluxes per substep.  After
@@ -93,6 +95,163 @@ __device__ void edge_terms(const double* q, int W, long long WH, int dir, int e,
     }
 }
 
+// ------------------------------------------------------------------ shallow water
+// Roe state and wave strengths of one edge (the step kernel's formulation: per-cell sqrt(h) and
+// momenta over sqrt(h), one reciprocal, one reciprocal square root for c and 1/(2c))
+struct SEdge {
+    double un, ut, c, i2c, a1, a2, a3;
+};
+
+__device__ __forceinline__ SEdge swe_solve(double hl, double nl, double tl, double hr, double nr, double tr, double hg)
+{
+    const double rl = rsqrt(hl), rr = rsqrt(hr);
+    const double inv = 1.0 / (hl * rl + hr * rr);
+    SEdge E;
+    E.un = (nl * rl + nr * rr) * inv;
+    E.ut = (tl * rl + tr * rr) * inv;
+    const double x = (hl + hr) * hg;
+    const double rc = rsqrt(x);
+    E.c = x * rc;
+    E.i2c = 0.5 * rc;
+    const double dh = hr - hl, dn = nr - nl, dt = tr - tl;
+    E.a1 = fma(E.un + E.c, dh, -dn) * E.i2c;
+    E.a2 = fma(-E.ut, dh, dt);
+    E.a3 = fma(-(E.un - E.c), dh, dn) * E.i2c;
+    return E;
+}
+
+// h_p = |s_p| (1 - l |s_p|) mu_p / 2 of an edge from itself and its two neighbours along the sweep
+template <int LIM>
+__device__ __forceinline__ void swe_limited(const SEdge& E, const SEdge& Eb, const SEdge& Ef, double l, double h[3])
+{
+    const double s1 = E.un - E.c, s3 = E.un + E.c;
+    const SEdge& U1 = s1 > 0.0 ? Eb : Ef;
+    const SEdge& U2 = E.un > 0.0 ? Eb : Ef;
+    const SEdge& U3 = s3 > 0.0 ? Eb : Ef;
+    const double w = fma(E.ut, E.ut, 1.0);
+    const double rr1 = fma(s1, s1, w), rr3 = fma(s3, s3, w);
+    const double ip = 1.0 / (rr1 * rr3);
+    const double ri1 = fma(U1.un - U1.c, s1, fma(U1.ut, E.ut, 1.0));
+    const double ri3 = fma(U3.un + U3.c, s3, fma(U3.ut, E.ut, 1.0));
+    const double mu1 = Lim<LIM>::f(E.a1, U1.a1 * ri1 * (rr3 * ip));
+    const double mu2 = Lim<LIM>::f(E.a2, U2.a2);
+    const double mu3 = Lim<LIM>::f(E.a3, U3.a3 * ri3 * (rr1 * ip));
+    const double k1 = fabs(s1), k2 = fabs(E.un), k3 = fabs(s3), hl = -0.5 * l;
+    h[0] = fma(hl * k1, k1, 0.5 * k1) * mu1;
+    h[1] = fma(hl * k2, k2, 0.5 * k2) * mu2;
+    h[2] = fma(hl * k3, k3, 0.5 * k3) * mu3;
+}
+
+// the fluctuation an edge sends into the cell on its right (right) or left, with the correction
+// at the weight the transverse mode gives (hw = +1: full C, -1: none), split across the sweep:
+// adds the part going to lower transverse indices to bm and the rest to bp, (h, n, t) order
+__device__ __forceinline__ void swe_side_split(const SEdge& E, const double h[3], bool right, double hw,
+                                               double bm[3], double bp[3])
+{
+    const double s[3] = {E.un - E.c, E.un, E.un + E.c};
+    const double a[3] = {E.a1, E.a2, E.a3};
+    double d[3];
+    for (int p = 0; p < 3; ++p) {
+        const double hp = right ? -h[p] : h[p];
+        const double lam = right ? (s[p] > 0.0 ? s[p] : 0.0) : (s[p] < 0.0 ? s[p] : 0.0);
+        d[p] = fma(hw, hp, fma(lam, a[p], hp));
+    }
+    const double dh = d[0] + d[2], t = d[1] * E.i2c;
+    const double b[3] = {fma(0.5, dh, -t), E.c * (d[2] - d[0]), fma(0.5, dh, t)};
+    const double m[3] = {E.ut - E.c, E.ut, E.ut + E.c};
+    double gm[3], gp[3];
+    for (int q = 0; q < 3; ++q) {
+        const double g = m[q] * b[q];
+        gm[q] = m[q] < 0.0 ? g : 0.0;
+        gp[q] = m[q] < 0.0 ? 0.0 : g;
+    }
+    const double Gm = gm[0] + gm[2], Gp = gp[0] + gp[2];
+    bm[0] += Gm;
+    bm[1] += fma(E.un, Gm, gm[1]);
+    bm[2] += fma(E.ut, Gm, E.c * (gm[2] - gm[0]));
+    bp[0] += Gp;
+    bp[1] += fma(E.un, Gp, gp[1]);
+    bp[2] += fma(E.ut, Gp, E.c * (gp[2] - gp[0]));
+}
+
+// A-dQ, A+dQ and F~ (correction plus the other sweep's transverse terms) of the edge between
+// normal indices e-1 and e on line t, components (h, normal momentum, transverse momentum)
+template <int LIM>
+__device__ void swe_edge_terms(const double* q, int W, long long WH, int dir, int e, int t, double hg, double ln,
+                               double lt, int order, int transverse, double am[3], double ap[3], double f[3])
+{
+    const int mn = dir == 0 ? 1 : 2, mt = dir == 0 ? 2 : 1;
+    auto Q = [&](int m, int n, int l) -> double {
+        const int i = dir == 0 ? n : l, j = dir == 0 ? l : n;
+        return q[m * WH + (long long)(j + 2) * W + (i + 2)];
+    };
+    // along the normal: edge between (n-1, l) and (n, l); across: between (n, l-1) and (n, l)
+    auto solve = [&](bool along, int n, int l) -> SEdge {
+        const int nm = along ? mn : mt, tm = along ? mt : mn;
+        const int n0 = along ? n - 1 : n, l0 = along ? l : l - 1;
+        return swe_solve(Q(0, n0, l0), Q(nm, n0, l0), Q(tm, n0, l0), Q(0, n, l), Q(nm, n, l), Q(tm, n, l), hg);
+    };
+    const bool second = order == 2;
+    const double hw = (transverse == 2 && second) ? 1.0 : -1.0;
+    const SEdge E = solve(true, e, t);
+    const double s[3] = {E.un - E.c, E.un, E.un + E.c};
+    const double a[3] = {E.a1, E.a2, E.a3};
+    double cm[3] = {0.0, 0.0, 0.0}, cp[3] = {0.0, 0.0, 0.0};   // coefficients on r_p
+    for (int p = 0; p < 3; ++p) {
+        if (s[p] < 0.0) cm[p] = s[p] * a[p];
+        else cp[p] = s[p] * a[p];
+    }
+    auto vec = [&](const double c3[3], double out[3]) {   // sum_p c_p r_p, r = (1, un -/+ c, ut), (0, 0, 1)
+        out[0] = c3[0] + c3[2];
+        out[1] = fma(s[0], c3[0], s[2] * c3[2]);
+        out[2] = fma(E.ut, c3[0] + c3[2], c3[1]);
+    };
+    vec(cm, am);
+    vec(cp, ap);
+    f[0] = f[1] = f[2] = 0.0;
+    if (second) {
+        double h[3];
+        swe_limited<LIM>(E, solve(true, e - 1, t), solve(true, e + 1, t), ln, h);
+        vec(h, f);
+    }
+    if (transverse) {
+        // the transverse sweep's fluctuations entering cell (k, t), split along the normal
+        auto parts = [&](int k, double bm[3], double bp[3]) {
+            const SEdge lo = solve(false, k, t), hi = solve(false, k, t + 1);
+            double hlo[3] = {0.0, 0.0, 0.0}, hhi[3] = {0.0, 0.0, 0.0};
+            if (second) {
+                swe_limited<LIM>(lo, solve(false, k, t - 1), hi, lt, hlo);
+                swe_limited<LIM>(hi, lo, solve(false, k, t + 2), lt, hhi);
+            }
+            swe_side_split(lo, hlo, true, hw, bm, bp);
+            swe_side_split(hi, hhi, false, hw, bm, bp);
+        };
+        double m0[3] = {0.0, 0.0, 0.0}, p0[3] = {0.0, 0.0, 0.0}, m1[3] = {0.0, 0.0, 0.0}, p1[3] = {0.0, 0.0, 0.0};
+        parts(e - 1, m0, p0);   // its part going to higher normal indices crosses the edge
+        parts(e, m1, p1);       // its part going to lower normal indices crosses the edge
+        // the transverse sweep's (h, its normal = our t, its tangential = our n)
+        f[0] -= 0.5 * lt * (p0[0] + m1[0]);
+        f[1] -= 0.5 * lt * (p0[2] + m1[2]);
+        f[2] -= 0.5 * lt * (p0[1] + m1[1]);
+    }
+}
+
+// f(Q_F) - f(Q_C) of the shallow water equations along the edge's normal, (h, n, t) order
+__device__ __forceinline__ void swe_flux_diff(const double qf[3], const double qc[3], int mn, double grav, double o[3])
+{
+    const int mt = 3 - mn;
+    auto flux = [&](const double* v, double* fl) {
+        const double ih = 1.0 / v[0];
+        fl[0] = v[mn];
+        fl[1] = fma(v[mn] * v[mn], ih, 0.5 * grav * v[0] * v[0]);
+        fl[2] = v[mn] * v[mt] * ih;
+    };
+    double a[3], b[3];
+    flux(qf, a);
+    flux(qc, b);
+    for (int m = 0; m < 3; ++m) o[m] = a[m] - b[m];
+}
+
 __device__ __forceinline__ UMed umed(const StepArgs& k)
 {
     UMed m;
@@ -125,12 +284,15 @@ __global__ void reflux_coarse_kernel(const RefluxRec* __restrict__ recs, int n, 
     const long long WH = (long long)W * (P.ny + 4);
     const double d = __ldg(dt + P.run) * P.dtscale;
     const double lx = d * P.dxinv, ly = d * P.dyinv;
-    const UMed md = umed(k);
     const int cn = R.dir == 0 ? R.ci : R.cj, cl = R.dir == 0 ? R.cj : R.ci;
     const int e = R.side > 0 ? cn + 1 : cn;   // C's east / north edge, or its west / south edge
     double am[3], ap[3], f[3], t[3], o[3];
-    edge_terms<LIM>(qc + P.qoff, W, WH, R.dir, e, cl, md, R.dir == 0 ? lx : ly, R.dir == 0 ? ly : lx, k.order,
-                    k.transverse, am, ap, f);
+    if (k.swe)
+        swe_edge_terms<LIM>(qc + P.qoff, W, WH, R.dir, e, cl, 0.5 * k.grav, R.dir == 0 ? lx : ly,
+                            R.dir == 0 ? ly : lx, k.order, k.transverse, am, ap, f);
+    else
+        edge_terms<LIM>(qc + P.qoff, W, WH, R.dir, e, cl, umed(k), R.dir == 0 ? lx : ly, R.dir == 0 ? ly : lx,
+                        k.order, k.transverse, am, ap, f);
     for (int m = 0; m < 3; ++m) t[m] = (R.side > 0 ? am[m] : -ap[m]) + f[m];
     to_puv(R.dir, t, o);
     for (int m = 0; m < 3; ++m) buf[3 * r + m] = -o[m];
@@ -155,7 +317,6 @@ __global__ void reflux_fine_kernel(const RefluxRec* __restrict__ recs, int n, co
     const long long WHc = (long long)Wc * (C.ny + 4), WHf = (long long)Wf * (F.ny + 4);
     const double d = __ldg(dt + F.run) * F.dtscale;
     const double lx = d * F.dxinv, ly = d * F.dyinv;
-    const UMed md = umed(k);
     const long long co = C.qoff + (long long)(R.cj + 2) * Wc + (R.ci + 2);
     double qC[3];
     for (int m = 0; m < 3; ++m) qC[m] = qc[co + m * WHc];
@@ -164,13 +325,23 @@ __global__ void reflux_fine_kernel(const RefluxRec* __restrict__ recs, int n, co
         const int fi = R.dir == 0 ? R.fi : R.fi + b, fj = R.dir == 0 ? R.fj + b : R.fj;
         const int fn = R.dir == 0 ? fi : fj, fl = R.dir == 0 ? fj : fi;
         const int e = R.side > 0 ? fn : fn + 1;   // the fine cell's west / south or east / north edge
-        double am[3], ap[3], f[3];
-        edge_terms<LIM>(qf + F.qoff, Wf, WHf, R.dir, e, fl, md, R.dir == 0 ? lx : ly, R.dir == 0 ? ly : lx,
-                        k.order, k.transverse, am, ap, f);
+        double am[3], ap[3], f[3], fl3[3];
         const long long fo = F.qoff + (long long)(fj + 2) * Wf + (fi + 2);
-        const double dp = qf[fo] - qC[0], dn = qf[fo + mn * WHf] - qC[mn];
-        // A (Q_F - Q_C) in the edge's order: (K dn, dp / rho, 0)
-        const double fl3[3] = {md.K * dn, dp * md.irho, 0.0};
+        if (k.swe) {
+            swe_edge_terms<LIM>(qf + F.qoff, Wf, WHf, R.dir, e, fl, 0.5 * k.grav, R.dir == 0 ? lx : ly,
+                                R.dir == 0 ? ly : lx, k.order, k.transverse, am, ap, f);
+            const double qF[3] = {qf[fo], qf[fo + WHf], qf[fo + 2 * WHf]};
+            swe_flux_diff(qF, qC, mn, k.grav, fl3);   // f(Q_F) - f(Q_C) in the edge's order
+        } else {
+            const UMed md = umed(k);
+            edge_terms<LIM>(qf + F.qoff, Wf, WHf, R.dir, e, fl, md, R.dir == 0 ? lx : ly, R.dir == 0 ? ly : lx,
+                            k.order, k.transverse, am, ap, f);
+            const double dp = qf[fo] - qC[0], dn = qf[fo + mn * WHf] - qC[mn];
+            // A (Q_F - Q_C) in the edge's order: (K dn, dp / rho, 0)
+            fl3[0] = md.K * dn;
+            fl3[1] = dp * md.irho;
+            fl3[2] = 0.0;
+        }
         double tt[3], o[3];
         for (int m = 0; m < 3; ++m) tt[m] = fl3[m] + (R.side > 0 ? -ap[m] : am[m]) + f[m];
         to_puv(R.dir, tt, o);
