@@ -172,7 +172,9 @@ def test_conservation_fix_three_levels_matches_oracle(orc):
 def test_conservation_fix_conserves_the_composite_integral():
     from gpu_amr_helpers import composite
     from paper_1808_02638_gb300.solver import Hierarchy
-    run = inputs.Run(*inputs.PULSE_DOMAIN, bc=(1, 1, 1, 1))
+    # the inward half of the ring focuses and the speeds grow by up to 9 % within a coarse step:
+    # CFL 0.7 keeps every step's CFL number below 1
+    run = inputs.Run(*inputs.PULSE_DOMAIN, bc=(1, 1, 1, 1), cfl=0.7)
     run.levels = inputs.amr_levels(run, 32, 4, [(0.2, 0.45)], [2002])
     q = [inputs.init_swe(run, lev, depth=lambda x, y: inputs.radial_pulse(x - 0.1, y + 0.05), u0=0.3, v0=-0.2)
          for lev in run.levels]
