@@ -10,8 +10,8 @@
  * A second system goes through the same step and AMR machinery (the framework takes any system
  * through its normal and transverse Riemann solvers, Sec. 3.1, 3.3): the nonlinear shallow
  * water equations on a flat bottom, q = (h, hu, hv), with the Roe solvers (system =
- * CLAW_SYS_SHALLOW_WATER; the level-step, ghost filling, averaging, regridding and the CFL
- * control apply; the adjoint and the conservation fix are acoustics-only).
+ * CLAW_SYS_SHALLOW_WATER; the level-step, ghost filling, averaging, regridding, the
+ * conservation fix and the CFL control apply; the adjoint is acoustics-only).
  *
  * Conventions shared by every entry point
  *   - Storage: a box (patch) with an nx x ny interior has CLAW_MBC = 2 ghost layers and is
@@ -251,7 +251,9 @@ int claw_medium_aux_adjoint(claw_ctx* ctx, int32_t level, const double* rho, con
                             const double* g_aux, double* g_rho, double* g_K, void* stream);
 
 /* ---- Conservation fix at coarse-fine interfaces (Sec. 2.3, "refluxing"), uniform medium.
- * For the acoustics system in conservation form (medium = 0), every coarse cell C of level
+ * For the acoustics system in conservation form (medium = 0) and for shallow water (whose Roe
+ * solver is conservative; A (Q_F - Q_C) below is then f(Q_F) - f(Q_C) with the equations'
+ * flux), every coarse cell C of level
  * fine_level-1 that the fine level does not cover but that shares an edge e with it is
  * corrected after the average so that the flux through e equals the average of the fine fluxes
  * through the r fine edges over the r substeps.  In flux form, with C left of e:

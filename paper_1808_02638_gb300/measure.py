@@ -3,7 +3,7 @@ plain path (one launch per patch, eager) on the same hierarchy, and the adjoint'
 
   python -m paper_1808_02638_gb300.measure [names...] [--nruns N] [--ncoarse N] [--every N] [--no-plain]
 
-(names: c0 c2 c3 c4 e1 swe1; default all; the options shrink the batched workload for a profiler)
+(names: c0 c2 c3 c4 e1 swe1 swe2; default all; the options shrink the batched workload for a profiler)
 
 Each workload reports interior cell-updates per second (a cell advanced one step on its level;
 ghost cells and halo recomputation are not counted), algorithmic HBM bytes per second (q read
@@ -279,6 +279,30 @@ def swe1(nsteps=50, n=2048):
                     "dt_final": float(H.dt[0])})
 
 
+def swe2():
+    """Shallow water through the AMR path: config 2's 3-level hierarchy (ratio 4 twice) with the
+    ring as depth and a mean flow (0.2, 0.1), with and without the conservation fix."""
+    run = inputs.config2()
+    q0 = [inputs.init_swe(run, lev, u0=0.2, v0=0.1) for lev in run.levels]
+    H = Hierarchy([run], [q0], system="shallow_water", grav=1.0)
+    H.init_dt()
+    tiling = tune_all(H)
+    ms = time_fused(H, 20)
+    plain = time_plain(H, 2)
+    R = Hierarchy([run], [q0], system="shallow_water", grav=1.0, reflux=True)
+    for L, t in tiling.items():
+        claw.claw_set_tiling(R.ctx, int(L), *t)
+    R.init_dt()
+    ms_r = time_fused(R, 20)
+    boxes = [len(l.boxes) for l in run.levels]
+    return _report(f"shallow water, 3-level AMR (boxes per level {boxes}), ring depth with a mean flow, "
+                   "20 coarse steps", H, ms, plain, FP64_INSTR_SWE, BYTES_UNIFORM,
+                   {"l2": "L2-resident", "tiling": tiling,
+                    "reflux": {"ms_per_coarse_step": ms_r, "overhead": ms_r / ms - 1.0,
+                               "launches_per_coarse_step": R.launches_per_coarse_step(),
+                               "status": claw.strerror(R.sync_status())}})
+
+
 def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=0.002, max_size=260):
     """Analog of the paper's benchmark (Sec. 4.1-4.2): radial pulse in a uniform medium, outflow
     (extrapolation) boundaries, van Leer, 3 levels of ratio 2 over a 1000^2 base tiled in 4 x 4
@@ -334,7 +358,7 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
             "note": "eager launches (the hierarchy changes at every regrid); wall clock includes the regrids"}
 
 
-WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4, "e1": e1, "swe1": swe1}
+WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4, "e1": e1, "swe1": swe1, "swe2": swe2}
 # (bench.py reports every workload above; e1 runs 200 coarse steps there)
 
 
