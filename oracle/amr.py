@@ -340,7 +340,7 @@ class OracleHierarchy:
         flags of level L-1 (oracle.regrid.flag_level, ghosts filled first), grown by `buffer`,
         kept `nest` cells inside level L-1, clustered with `cutoff` and `max_size` (fine cells);
         the new level L takes old level-L values where it had them, else the coarse interpolation.
-        Uniform medium (constant coefficient pools)."""
+        Uniform medium (constant coefficient pools) or shallow water."""
         from .regrid import new_boxes, transfer
         run = self.run
         for Lf in range(1, len(self.levels)):
@@ -353,8 +353,9 @@ class OracleHierarchy:
             boxes = new_boxes(coarse, self.q[Lf - 1], tol, buffer, cutoff, max_size, nest, old.ratio)
             new = type(old)(old.NX, old.NY, old.dx, old.dy, boxes, old.ratio)   # the caller's level type
             self.q[Lf] = transfer(old, self.q[Lf], new, coarse, self.q[Lf - 1], run.bc)
-            self.rho[Lf] = np.full(new.csize, float(self.rho[Lf].flat[0]) if self.rho[Lf].size else 1.0)
-            self.K[Lf] = np.full(new.csize, float(self.K[Lf].flat[0]) if self.K[Lf].size else 1.0)
+            if not self.swe:
+                self.rho[Lf] = np.full(new.csize, float(self.rho[Lf].flat[0]) if self.rho[Lf].size else 1.0)
+                self.K[Lf] = np.full(new.csize, float(self.K[Lf].flat[0]) if self.K[Lf].size else 1.0)
             self.levels[Lf] = new
         self._iface = {Lf: interface(self.levels, Lf, run.bc) for Lf in range(1, len(self.levels))} \
             if self.reflux else {}

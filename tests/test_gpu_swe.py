@@ -192,6 +192,30 @@ def test_conservation_fix_conserves_the_composite_integral():
     assert drift[False].max() >= 1e-6 * scale, drift[False]
 
 
+def test_regridding_matches_the_oracle(orc):
+    # flags, Berger-Rigoutsos boxes and the transfer are system-independent: the shallow-water
+    # hierarchy regridded every 4 coarse steps follows the oracle's
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300.solver import Hierarchy
+    params = dict(tol=0.02, buffer=2, cutoff=0.7, max_size=64, nest=2)
+    run_g, run_o = inputs.config2(), inputs.config2()   # each side rebuilds its own levels
+    q = [inputs.init_swe(run_g, lev, u0=0.2, v0=0.1) for lev in run_g.levels]
+    H = Hierarchy([run_g], [q], system="shallow_water", grav=G, reflux=True)
+    O = OracleHierarchy(run_o, q, reflux=True, system="shallow_water", grav=G)
+    H.init_dt()
+    for k in range(8):
+        H.coarse_step()
+        O.coarse_step()
+        if (k + 1) % 4 == 0:
+            H.regrid(**params)
+            O.regrid(**params)
+            for L in (1, 2):
+                assert np.array_equal(run_g.levels[L].boxes, run_o.levels[L].boxes)
+            _compare(run_g, H, O, TOLN)
+    _compare(run_g, H, O, TOLN)
+    assert H.sync_status() == 0
+
+
 def test_graph_replay_equals_eager():
     import torch
     run = inputs.config1(256, 32)
