@@ -1048,7 +1048,7 @@ int claw_fill_ghost(claw_ctx* ctx, int32_t L, double* q, const double* qc_old, c
     if (d.ninterp > 0 && (!qc_old || !qc_new || !(tau >= 0.0 && tau <= 1.0))) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = d.ncopy ? launch_fill_copy_rects(d.copies, d.ncopy, q, s) : cudaSuccess;
+    cudaError_t e = d.ncopy ? launch_fill_copy(d.copies, d.copy_start, d.ncopy_blocks, q, s) : cudaSuccess;
     ctx->launches += d.ncopy > 0;
     if (e == cudaSuccess) {
         e = launch_fill_interp(d.interps, d.ninterp, q, qc_old, qc_new, tau, s);
@@ -1185,7 +1185,7 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
     ctx->launches += 1;
     cudaError_t e = launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s);
     if (e == cudaSuccess && (flags & CLAW_ADVANCE_PUSH_GHOSTS) && d.ncopy) {
-        e = launch_fill_copy_rects(d.copies, d.ncopy, q_new, s);
+        e = launch_fill_copy(d.copies, d.copy_start, d.ncopy_blocks, q_new, s);
         ctx->launches += 1;
     }
     return cuda_rc(e);

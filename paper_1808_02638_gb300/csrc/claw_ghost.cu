@@ -130,48 +130,6 @@ __global__ void __launch_bounds__(kCopyThreads) fill_copy_kernel(const CopyRect*
     }
 }
 
-// One warp per rectangle (at most 32 rows): each lane issues up to kCopyBatch loads before its
-// stores.  No staging and no block barrier: a rectangle is one descriptor load, one round of
-// loads and one of stores, and every source is an interior cell (the host resolved the
-// boundary maps), so rectangles are independent.
-constexpr int kRectWarps = 8;
-
-__global__ void __launch_bounds__(kRectWarps * 32) fill_copy_rect_kernel(const CopyRect* __restrict__ rects, int n,
-                                                                        double* __restrict__ q, int ncomp)
-{
-    const int r = blockIdx.x * kRectWarps + (int)(threadIdx.x >> 5);
-    if (r >= n) return;
-    const int lane = threadIdx.x & 31;
-    const CopyRect R = rects[r];
-    const int cells = R.w * R.h, total = ncomp * cells;
-    for (int base = 0; base < total; base += 32 * kCopyBatch) {
-        double v[kCopyBatch];
-        long long dst[kCopyBatch];
-#pragma unroll
-        for (int j = 0; j < kCopyBatch; ++j) {
-            const int k = base + j * 32 + lane;
-            dst[j] = -1;
-            if (k < total) {
-                const int m = k / cells, e = k - m * cells;
-                const int y = e / R.w, x = e - y * R.w;
-                const double s = q[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx];
-                v[j] = negated(R.flags, m) ? -s : s;
-                dst[j] = R.dst + m * R.dplane + (long long)y * R.dpitch + x;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kCopyBatch; ++j)
-            if (dst[j] >= 0) q[dst[j]] = v[j];
-    }
-}
-
-cudaError_t launch_fill_copy_rects(const CopyRect* r, int n, double* q, cudaStream_t s, int ncomp)
-{
-    if (n <= 0) return cudaSuccess;
-    fill_copy_rect_kernel<<<div_up(n, kRectWarps), kRectWarps * 32, 0, s>>>(r, n, q, ncomp);
-    return cudaGetLastError();
-}
-
 // reverse: ghost adjoint flows into its source, then the ghost adjoint is cleared.  Sources
 // are interior cells and several ghosts may share one (extrapolation), hence the atomics.
 __global__ void __launch_bounds__(kCopyThreads) fill_copy_adjoint_kernel(const CopyRect* __restrict__ rects,

@@ -173,7 +173,6 @@ int adjoint_tile();   // the adjoint kernel's square tile edge
 // launchers (claw_ghost.cu)
 cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nblocks, double* q, cudaStream_t s,
                              int ncomp = 3);
-cudaError_t launch_fill_copy_rects(const CopyRect* r, int n, double* q, cudaStream_t s, int ncomp = 3);
 cudaError_t launch_fill_interp(const InterpCell* c, int n, double* q, const double* cold,
                                const double* cnew, double tau, cudaStream_t s);
 cudaError_t launch_fill_copy_adjoint(const CopyRect* r, const int* start, int nblocks, double* lam, cudaStream_t s,
