@@ -4,7 +4,6 @@
 // These are light, memory-bound kernels; the host builds compact task tables once per regrid
 // (claw_set_level) so that each launch is a flat loop over tasks.
 #include <cuda_runtime.h>
-#include <stdint.h>
 
 #include "claw_internal.h"
 
@@ -18,38 +17,24 @@ static inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 // its rectangles in shared memory with the running element count, and every thread takes
 // kCopyBatch elements of the flattened range with all loads issued before the stores (the
 // copy is latency-bound: one dependent load-store pair per thread would leave HBM idle).
-// A rectangle whose rows are contiguous, even-width and 16-byte aligned on both sides (the
-// two-cell strips of same-level neighbours) moves as pairs of doubles: one 16-byte load and
-// store per pair instead of two 8-byte ones.
 constexpr int kCopyThreads = 128;
 constexpr int kCopyChunk = 32;
 constexpr int kCopyBatch = 8;
 
 struct CopyChunk {
     CopyRect r[kCopyChunk];
-    int end[kCopyChunk];   // inclusive prefix of ncomp * (w / vw) * h
-    int vw[kCopyChunk];    // 2: the rectangle moves as pairs of doubles
+    int end[kCopyChunk];   // inclusive prefix of ncomp * w * h
     int n, total;
 };
 
-__device__ __forceinline__ bool pairable(const CopyRect& R)
-{
-    return (R.w % 2) == 0 && R.sx == 1 && ((R.dst | R.src | R.dplane | R.splane) & 1) == 0 &&
-           ((R.dpitch | R.sy) & 1) == 0;
-}
-
 __device__ __forceinline__ void stage_chunk(CopyChunk& c, const CopyRect* __restrict__ rects, int r0, int n,
-                                            int ncomp, bool pairs = false)
+                                            int ncomp)
 {
     const int tid = threadIdx.x;
-    if (tid < n) {
-        const CopyRect R = rects[r0 + tid];
-        c.r[tid] = R;
-        c.vw[tid] = pairs && pairable(R) ? 2 : 1;
-    }
+    if (tid < n) c.r[tid] = rects[r0 + tid];
     __syncthreads();
     if (tid < 32) {   // warp-inclusive scan of the element counts
-        int v = tid < n ? ncomp * (c.r[tid].w / c.vw[tid]) * c.r[tid].h : 0;
+        int v = tid < n ? ncomp * c.r[tid].w * c.r[tid].h : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, v, o);
@@ -64,20 +49,18 @@ __device__ __forceinline__ void stage_chunk(CopyChunk& c, const CopyRect* __rest
     __syncthreads();
 }
 
-// element k of the staged chunk -> (rectangle, component, x, y); x is the first of vw cells
+// element k of the staged chunk -> (rectangle, component, x, y)
 __device__ __forceinline__ void locate(const CopyChunk& c, int k, int& ri, int& m, int& x, int& y)
 {
     ri = 0;
     while (c.end[ri] <= k) ++ri;
     const CopyRect& R = c.r[ri];
-    const int vw = c.vw[ri];
     const int e0 = k - (ri ? c.end[ri - 1] : 0);
-    const int w = R.w / vw;
-    const int cells = w * R.h;
+    const int cells = R.w * R.h;
     m = e0 / cells;
     const int e = e0 - m * cells;
-    y = e / w;
-    x = (e - y * w) * vw;
+    y = e / R.w;
+    x = e - y * R.w;
 }
 
 __device__ __forceinline__ bool negated(int flags, int m)
@@ -87,44 +70,31 @@ __device__ __forceinline__ bool negated(int flags, int m)
 
 __global__ void __launch_bounds__(kCopyThreads) fill_copy_kernel(const CopyRect* __restrict__ rects,
                                                                  const int* __restrict__ start,
-                                                                 double* __restrict__ q, int ncomp, int pairs)
+                                                                 double* __restrict__ q, int ncomp)
 {
     __shared__ CopyChunk c;
     const int r_lo = start[blockIdx.x], r_hi = start[blockIdx.x + 1];
     for (int r0 = r_lo; r0 < r_hi; r0 += kCopyChunk) {
-        stage_chunk(c, rects, r0, min(kCopyChunk, r_hi - r0), ncomp, pairs != 0);
+        stage_chunk(c, rects, r0, min(kCopyChunk, r_hi - r0), ncomp);
         for (int base = 0; base < c.total; base += kCopyThreads * kCopyBatch) {
-            double2 v[kCopyBatch];
+            double v[kCopyBatch];
             long long dst[kCopyBatch];
-            bool pair[kCopyBatch];
 #pragma unroll
             for (int j = 0; j < kCopyBatch; ++j) {
                 const int k = base + j * kCopyThreads + (int)threadIdx.x;
                 dst[j] = -1;
-                pair[j] = false;
                 if (k < c.total) {
                     int ri, m, x, y;
                     locate(c, k, ri, m, x, y);
                     const CopyRect& R = c.r[ri];
-                    const long long src = R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx;
-                    const bool neg = negated(R.flags, m);
-                    pair[j] = c.vw[ri] == 2;
-                    if (pair[j]) {
-                        const double2 s = *reinterpret_cast<const double2*>(q + src);
-                        v[j] = neg ? make_double2(-s.x, -s.y) : s;
-                    } else {
-                        const double s = q[src];
-                        v[j].x = neg ? -s : s;
-                    }
+                    const double s = q[R.src + m * R.splane + (long long)y * R.sy + (long long)x * R.sx];
+                    v[j] = negated(R.flags, m) ? -s : s;
                     dst[j] = R.dst + m * R.dplane + (long long)y * R.dpitch + x;
                 }
             }
 #pragma unroll
-            for (int j = 0; j < kCopyBatch; ++j) {
-                if (dst[j] < 0) continue;
-                if (pair[j]) *reinterpret_cast<double2*>(q + dst[j]) = v[j];
-                else q[dst[j]] = v[j].x;
-            }
+            for (int j = 0; j < kCopyBatch; ++j)
+                if (dst[j] >= 0) q[dst[j]] = v[j];
         }
         __syncthreads();   // the chunk is restaged
     }
@@ -157,9 +127,7 @@ __global__ void __launch_bounds__(kCopyThreads) fill_copy_adjoint_kernel(const C
 cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nblocks, double* q, cudaStream_t s, int ncomp)
 {
     if (nblocks <= 0) return cudaSuccess;
-    // pairs of doubles need a 16-byte aligned pool (even offsets are checked per rectangle)
-    const int pairs = (reinterpret_cast<uintptr_t>(q) & 15) == 0;
-    fill_copy_kernel<<<nblocks, kCopyThreads, 0, s>>>(r, start, q, ncomp, pairs);
+    fill_copy_kernel<<<nblocks, kCopyThreads, 0, s>>>(r, start, q, ncomp);
     return cudaGetLastError();
 }
 
