@@ -328,16 +328,16 @@ def main():
     H = Hierarchy([run], [[q0]], rho0=1.0, K0=4.0, device=local)
     H.init_dt()
     from paper_1808_02638_gb300 import tune
-    tiling, tune_ms = tune.tune_level(H, 0, use_cache=False)
+    tiling, tune_ms = tune.tune_level(H, 0, use_cache=False, pull=True)
     stream = torch.cuda.current_stream()
     ctx = H.ctx
     H.coarse_step()
     H.coarse_step()
     torch.cuda.synchronize()
 
-    # per buffer parity two graphs: the persistent level-step launch that advances every patch
-    # and applies Eq. cfl on its last CTA, then the copy of the same-level / boundary ghosts of
-    # q^{n+1}; events bracket the step graph so the dominant kernel is timed on its own
+    # per buffer parity one graph: the persistent level-step launch that advances every patch,
+    # takes the same-level / boundary ghosts from their source cells and applies Eq. cfl on its
+    # last CTA; events bracket each replay so the kernel is timed on its launching stream
     stepper = H.fused_stepper()
     per_step_launches = stepper.launches_per_step
 
@@ -349,7 +349,7 @@ def main():
     torch.cuda.synchronize()
 
     K = args.steps
-    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(K)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(2)) for _ in range(K)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
     sampler.start()
@@ -363,8 +363,7 @@ def main():
     torch.cuda.synchronize()
     replicas.barrier(dist)
     clocks = sampler.stop()
-    kern_ms = [a.elapsed_time(b) for a, b, _ in evs]
-    fill_ms = [b.elapsed_time(c) for _, b, c in evs]
+    kern_ms = [a.elapsed_time(b) for a, b in evs]
     # every rank advances its own replica: the job's cell-updates over its slowest rank's time
     dev = torch.device("cuda", local)
     value, total_ms, _ = replicas.whole_job_rate(K * N_CELLS, start.elapsed_time(end), dist, dev)
@@ -392,8 +391,7 @@ def main():
     # end to end: the state lives on the host (pinned); every step copies q in, runs the
     # level-step through the C ABI and copies q^{n+1} back (Hierarchy.steps_from_host: the copy
     # out of one step overlaps the copy into the next, piece by piece)
-    H.fused = True          # first e2e step fills the ghosts; later steps carry pushed ghosts
-    H._ghosts_ready = False
+    H.fused = True          # one launch per step, ghosts pulled from their source cells
     e2e_steps = max(3, min(20, K // 4))
     qbytes = H.q[0][0].numel() * 8
     host_in = torch.empty_like(H.q[0][0], device="cpu").pin_memory()
@@ -446,7 +444,7 @@ def main():
                    "l2": "inputs larger than L2 (254 MB of q pools per replica)"},
         "step": "two CUDA-graph replays: the persistent level-step launch (all 4096 patches, Eq. cfl) and "
                 "the ghost copy of q^{n+1}",
-        "ghost_fill_ms": statistics.mean(fill_ms),
+        "ghosts": "pulled by the step kernel from their source cells (no ghost-copy launch)",
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_ISSUE_PEAK_G,
                      "unit": "G FP64 instructions/s", "frac": achieved_gops / FP64_ISSUE_PEAK_G, "traffic": traffic,
                      "per_cell_update": f"{ALG_FP64_INSTR_PER_CELL} FP64 instructions (25 DADD + 17 DFMA), "

@@ -184,10 +184,17 @@ int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q
  *   CLAW_ADVANCE_UPDATE_DT: after the step, Eq. cfl is applied on the device by the last CTA
  *     to finish (as claw_dt_update with level-0 dx, dy): dt[r] is replaced by the next time step
  *     and smax[r] reset.  Use it when this level-step ends the coarse step (a hierarchy of one
- *     level); dt is then both read and written by the launch.
- * Errors as claw_level_step, CLAW_EINVAL for unknown flags. */
+ *     level); dt is then both read and written by the launch;
+ *   CLAW_ADVANCE_PULL_GHOSTS: the step takes every same-level and physical-boundary ghost of
+ *     q_old from its source cell (an interior cell of q_old, with the boundary's sign flips)
+ *     instead of q_old's ghost cells, so those need no fill at all; ghosts interpolated from the
+ *     coarser level are still read from q_old and must be filled (claw_fill_ghost).  The ghost
+ *     cells of q_new are not written unless CLAW_ADVANCE_PUSH_GHOSTS is also given.
+ * Errors as claw_level_step, CLAW_EINVAL for unknown flags (and for PULL_GHOSTS on a level whose
+ * box planes exceed 2^29 elements). */
 #define CLAW_ADVANCE_PUSH_GHOSTS 1
 #define CLAW_ADVANCE_UPDATE_DT 2
+#define CLAW_ADVANCE_PULL_GHOSTS 4
 int claw_level_advance(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
                        const double* aux, double* dt, double* smax, int32_t flags, void* stream);
 

@@ -256,6 +256,7 @@ def claw_level_step(ctx, level, q_old, q_new, aux, dt, smax, stream=None):
 
 
 CLAW_ADVANCE_PUSH_GHOSTS = 1
+CLAW_ADVANCE_PULL_GHOSTS = 4
 CLAW_ADVANCE_UPDATE_DT = 2
 
 

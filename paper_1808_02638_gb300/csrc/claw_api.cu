@@ -168,6 +168,9 @@ void free_level(claw_ctx* ctx, int L)
     cudaFree(d.reflux_group);
     cudaFree(d.flagboxes);
     d.flagboxes = nullptr;
+    cudaFree(d.ring);
+    d.ring = nullptr;
+    d.ring_ok = false;
     d.reflux = nullptr;
     d.reflux_group = nullptr;
     d.nreflux = d.nreflux_groups = 0;
@@ -291,8 +294,9 @@ constexpr int kRectRows = 32;          // copy rectangles are split into pieces 
 constexpr long long kBlockCells = 256;   // cells per block of the copy kernel (about): one batch per thread
 
 int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::vector<InterpCell>& cells,
-                       std::vector<int>& start)
+                       std::vector<int>& start, std::vector<int2>* ring = nullptr, bool* ring_ok = nullptr)
 {
+    if (ring_ok) *ring_ok = true;
     LevelDev& d = ctx->lev[L];
     std::vector<Locator> loc(ctx->nruns), cloc(ctx->nruns);
     for (int r = 0; r < ctx->nruns; ++r) {
@@ -310,6 +314,7 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
         const int NX = level_nx(pr, L), NY = level_ny(pr, L);
         const int W = b.nx + 4;
         std::vector<GhostEntry> ent;
+        if (ring) d.hpatches[n].ring = (long long)ring->size() < (1LL << 31) ? (int)ring->size() : -1;
         for (int gj = b.jlo - 2; gj < b.jlo + b.ny + 2; ++gj)
             for (int gi = b.ilo - 2; gi < b.ilo + b.nx + 2; ++gi) {
                 if (gi >= b.ilo && gi < b.ilo + b.nx && gj >= b.jlo && gj < b.jlo + b.ny) continue;
@@ -322,8 +327,15 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
                 if (src >= 0) {
                     e.soff = cell_off(d.boxes[src], si, sj);
                     ent.push_back(e);
+                    if (ring) {   // ring order = this loop's order
+                        const long long rel = e.soff - d.boxes[src].qoff;
+                        if (rel >= (1LL << kRingOffBits) && ring_ok) *ring_ok = false;
+                        ring->push_back(make_int2(src, (int)(rel & ((1LL << kRingOffBits) - 1)) |
+                                                           (e.flags << kRingOffBits)));
+                    }
                     continue;
                 }
+                if (ring) ring->push_back(make_int2(-1, 0));
                 // space-time interpolation from level L-1 at the fine cell (si, sj)
                 if (L == 0) return CLAW_EINVAL;
                 InterpCell c;
@@ -934,7 +946,7 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         P.nx = b.nx;
         P.ny = b.ny;
         P.run = b.run;
-        P.pad = 0;
+        P.ring = -1;
         P.dxinv = 1.0 / level_dx(p, L);
         P.dyinv = 1.0 / level_dy(p, L);
         P.dtscale = 1.0;
@@ -949,8 +961,14 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     std::vector<InterpCell> cells;
     std::vector<AvgRect> avg;
     std::vector<int> qstart;
-    int rc = build_ghost_tables(ctx, L, rects, cells, qstart);
+    std::vector<int2> ring;
+    bool ring_ok = true;
+    int rc = build_ghost_tables(ctx, L, rects, cells, qstart, &ring, &ring_ok);
     if (rc) return rc;
+    d.ring_ok = ring_ok && (long long)ring.size() < (1LL << 31);
+    for (auto& P : d.hpatches)
+        if (!d.ring_ok) P.ring = -1;
+    if (d.ring_ok && (rc = upload(&d.ring, ring))) return rc;
     if ((rc = upload(&d.copy_start, qstart))) return rc;
     d.ncopy_blocks = qstart.empty() ? 0 : (int)qstart.size() - 1;
     d.max_rows = 0;
@@ -1160,7 +1178,8 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
 {
     int rc = check_step_args(ctx, L, q_old, q_new, aux, dt, smax);
     if (rc) return rc;
-    if (flags & ~(CLAW_ADVANCE_PUSH_GHOSTS | CLAW_ADVANCE_UPDATE_DT)) return CLAW_EINVAL;
+    if (flags & ~(CLAW_ADVANCE_PUSH_GHOSTS | CLAW_ADVANCE_UPDATE_DT | CLAW_ADVANCE_PULL_GHOSTS)) return CLAW_EINVAL;
+    if ((flags & CLAW_ADVANCE_PULL_GHOSTS) && !ctx->lev[L].ring_ok) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
     if (d.ntiles == 0) return CLAW_OK;
@@ -1174,6 +1193,7 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
         a.done = ctx->done;
         a.nruns = ctx->nruns;
     }
+    if (flags & CLAW_ADVANCE_PULL_GHOSTS) a.ring = d.ring;
     int staging = d.staging;
     if (staging >= 1) {
         a.tmaps = get_tmaps(ctx, L, q_old, s);

@@ -32,7 +32,7 @@ struct PatchDev {
     long long aoff;   // element offset of the first aux plane in the aux pool (CLAW_NAUX * coff)
     int nx, ny;       // interior size
     int run;          // index into the per-run dt / smax arrays
-    int pad;
+    int ring;         // first entry of the box's ghost ring in the level's ring table (-1: none)
     double dxinv, dyinv;
     double dtscale;   // this level's dt / level-0 dt = 1 / (ratio_1 ... ratio_L)
 };
@@ -125,11 +125,28 @@ struct LevelDev {
     int* reflux_group = nullptr;  // [ngroups + 1]: records of coarse cell g are [group[g], group[g+1])
     int nreflux_groups = 0;
     FlagBox* flagboxes = nullptr; // the boxes as flag-grid writers (built on first use)
+    int2* ring = nullptr;         // ghost sources of every box's ring (pulled ghosts), see RingEntry
+    bool ring_ok = false;
     // host copies
     std::vector<claw_box> boxes;
     std::vector<PatchDev> hpatches;
     std::vector<TileDev> htiles;
 };
+
+// Ghost ring of a box: its (nx+4)(ny+4) - nx ny ghost cells in row order of the padded box.
+// Entry {source box, source cell | sign flags << 29}: the ghost takes the source cell of that box
+// (plane-0 element relative to its qoff), u negated if bit 0 of the flags, v if bit 1; a source
+// box of -1 marks a ghost interpolated from the coarser level (read from the pool itself).
+constexpr int kRingOffBits = 29;
+__host__ __device__ inline int ring_index(int xp, int yp, int nx, int ny)   // -1: interior
+{
+    const int W = nx + 4;
+    if (yp < 2) return yp * W + xp;
+    if (yp >= ny + 2) return 2 * W + 4 * ny + (yp - ny - 2) * W + xp;
+    if (xp < 2) return 2 * W + (yp - 2) * 4 + xp;
+    if (xp >= nx + 2) return 2 * W + (yp - 2) * 4 + (xp - nx);
+    return -1;
+}
 
 struct StepArgs {
     const PatchDev* patches = nullptr;
@@ -147,6 +164,7 @@ struct StepArgs {
     double rho0 = 1.0, K0 = 1.0;   // uniform medium
     double grav = 0.0;             // shallow water
     int swe = 0;                   // 1: the shallow water system (the conservation fix reads it)
+    const int2* ring = nullptr;    // not null: same-level and boundary ghosts are pulled from sources
     // fused epilogue (0 = off)
     int dtupd = 0;                      // the last CTA applies Eq. cfl to dt and resets smax
     double* dt_out = nullptr;

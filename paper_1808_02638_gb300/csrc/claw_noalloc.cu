@@ -64,7 +64,7 @@ __global__ void noalloc_setup_kernel(unsigned char* s, int nx, int ny, double dx
         P->nx = nx;
         P->ny = ny;
         P->run = 0;
-        P->pad = 0;
+        P->ring = -1;
         P->dxinv = dxinv;
         P->dyinv = dyinv;
         P->dtscale = 1.0;

@@ -199,6 +199,45 @@ __device__ __forceinline__ void finish_cta(const StepArgs& A)
     *reinterpret_cast<volatile unsigned*>(A.done) = 0u;
 }
 
+// Same-level and physical-boundary ghosts of a staged tile, taken from their source cells in
+// q_old (the box's ghost ring table) instead of the pool's own ghost cells: only the frame of
+// width two around the tile can hold ghosts of its box.  Ghosts interpolated from the coarser
+// level keep the staged value.  The caller separates this from the staging and from the
+// tile's first reads with barriers.
+template <int SW, int QPL, int NT>
+__device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P, double* sq, int x0, int y0, int tx,
+                                            int ty)
+{
+    const int w = tx + 4, nf = 4 * (tx + ty + 4);
+    for (int k = (int)threadIdx.x; k < nf; k += NT) {
+        int xs, ys;
+        if (k < 4 * w) {   // rows 0, 1, ty+2, ty+3 of the staged tile
+            const int r = k / w;
+            xs = k - r * w;
+            ys = r < 2 ? r : ty + r;
+        } else {           // columns 0, 1, tx+2, tx+3 of rows 2 .. ty+1
+            const int kk = k - 4 * w, c = kk & 3;
+            ys = 2 + (kk >> 2);
+            xs = c < 2 ? c : tx + c;
+        }
+        const int ri = ring_index(x0 + xs, y0 + ys, P.nx, P.ny);
+        if (ri < 0) continue;
+        const int2 e = __ldg(&A.ring[P.ring + ri]);
+        if (e.x < 0) continue;
+        const PatchDev S = A.patches[e.x];
+        const long long sp = (long long)(S.nx + 4) * (S.ny + 4);
+        const double* src = A.qold + S.qoff + (e.y & ((1 << kRingOffBits) - 1));
+        const int fl = (int)((unsigned)e.y >> kRingOffBits);
+        const double a = __ldg(src), b = __ldg(src + sp), c = __ldg(src + 2 * sp);
+        const int i = xs + ys * SW;
+        sq[i] = a;
+        sq[QPL + i] = (fl & 1) ? -b : b;
+        sq[2 * QPL + i] = (fl & 2) ? -c : c;
+    }
+    // these generic writes precede later bulk copies (async proxy) into the same buffer
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ------------------------------------------------------------------------- the kernel
 // MED: 0 uniform medium (rho0, K0), 1 cell-wise aux planes.
 // STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered: the next tile streams in
@@ -304,6 +343,10 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                 if (ii < tx + 4 && jj < ty + 4) v = __ldg(src + m * WH + (long long)(y0 + jj) * W + (x0 + ii));
                 sq[k] = v;
             }
+            __syncthreads();
+        }
+        if (A.ring && P.ring >= 0) {
+            pull_ghosts<G::SW, G::QPL, NT>(A, P, sq, x0, y0, tx, ty);
             __syncthreads();
         }
 

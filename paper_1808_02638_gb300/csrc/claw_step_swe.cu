@@ -184,6 +184,10 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
             }
             __syncthreads();
         }
+        if (A.ring && P.ring >= 0) {
+            pull_ghosts<G::SW, G::QPL, NT>(A, P, sq, x0, y0, tx, ty);
+            __syncthreads();
+        }
         const double dt = __ldg(A.dt + P.run) * P.dtscale;
         const double lx = dt * P.dxinv, ly = dt * P.dyinv;
 

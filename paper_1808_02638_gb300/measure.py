@@ -57,10 +57,11 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def tune_all(H):
-    """autotuned tiling of every level (installed on H), keyed by level"""
+def tune_all(H, pull=False):
+    """autotuned tiling of every level (installed on H), keyed by level (pull: timed with the
+    ghosts taken from their source cells, as the one-level fused stepper runs)"""
     from . import tune
-    return {str(L): list(tune.tune_level(H, L, use_cache=False)[0]) for L in range(H.nlev)}
+    return {str(L): list(tune.tune_level(H, L, use_cache=False, pull=pull)[0]) for L in range(H.nlev)}
 
 
 def time_fused(H, ncoarse, warm=2):
@@ -270,7 +271,7 @@ def swe1(nsteps=50, n=2048):
     run = inputs.config1(n)
     H = Hierarchy([run], [[inputs.init_swe(run, run.levels[0])]], system="shallow_water", grav=1.0)
     H.init_dt()
-    tiling = tune_all(H)
+    tiling = tune_all(H, pull=True)
     ms = time_stepper(H, nsteps)
     plain = time_plain(H, 5)
     return _report(f"shallow water, {n}^2 as {(n // 32) ** 2} patches of 32^2, ring-pulse depth, g = 1, MC, "

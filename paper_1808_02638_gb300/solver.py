@@ -109,8 +109,7 @@ class Hierarchy:
                                           device=self.dev) if self.reflux else None
                               for L in range(1, self.nlev)]
         self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)
-        self.fused = False       # one-level hierarchies: step with Eq. cfl on the device, then push ghosts
-        self._ghosts_ready = False
+        self.fused = False       # one-level hierarchies: one launch per step (pulled ghosts, Eq. cfl on the device)
 
     def _layout(self, L):
         """(claw boxes, [(run, q base, coefficient base)], q size, coefficient size) of level L"""
@@ -181,7 +180,6 @@ class Hierarchy:
                 self.rbuf[Lf] = torch.zeros(max(1, claw.claw_reflux_buffer_size(self.ctx, Lf)),
                                             dtype=torch.float64, device=self.dev)
             self.__dict__.pop("_ghost_masks", None)
-        self._ghosts_ready = False
 
     # -------------------------------------------------------------- stepping
     def ratio(self, L):
@@ -226,16 +224,13 @@ class Hierarchy:
 
     def coarse_step(self, stream=None):
         if self.fused and self.nlev == 1 and not self.patchwise and not self.freeze_dt:
-            # the step applies Eq. cfl on its last CTA; the copied ghosts of q_new follow at once
-            if not self._ghosts_ready:
-                claw.claw_fill_ghost(self.ctx, 0, self.q[0][self.cur[0]], None, None, 0.0, stream)
-                self._ghosts_ready = True
+            # one launch: the step takes the ghosts from their source cells and applies Eq. cfl
+            # on its last CTA (the ghost cells of the pools are neither read nor written)
             src, dst = self.q[0][self.cur[0]], self.q[0][1 - self.cur[0]]
             claw.claw_level_advance(self.ctx, 0, src, dst, self.aux[0], self.dt, self.smax,
-                                    claw.CLAW_ADVANCE_PUSH_GHOSTS | claw.CLAW_ADVANCE_UPDATE_DT, stream)
+                                    claw.CLAW_ADVANCE_PULL_GHOSTS | claw.CLAW_ADVANCE_UPDATE_DT, stream)
             self.cur[0] ^= 1
             return
-        self._ghosts_ready = False
         self.advance(0, stream=stream)
         if self.freeze_dt:
             self.smax.zero_()
@@ -310,8 +305,8 @@ class Hierarchy:
 
     def fused_stepper(self):
         """One-level hierarchies: a stepper whose step() replays, for the current buffer parity,
-        a CUDA graph of the persistent level-step (Eq. cfl applied by its last CTA) and then a
-        graph of the ghost copy of q^{n+1} (same-level copies and physical boundaries)."""
+        a CUDA graph of the one launch of a step: the persistent level-step that takes its ghosts
+        from their source cells and applies Eq. cfl on its last CTA."""
         return FusedStepper(self)
 
     def sync_status(self):
@@ -350,18 +345,17 @@ class Hierarchy:
 
 
 class FusedStepper:
-    """Graphs of one level-step of a one-level hierarchy, one pair per buffer parity.
+    """Graphs of one level-step of a one-level hierarchy, one per buffer parity.
 
-    step(events) replays the step graph and the ghost-copy graph of the current parity and flips
-    the parity; `events` (three CUDA events, optional) are recorded before the step, between the
-    two graphs and after the copy, on the current stream."""
+    step(events) replays the graph of the current parity and flips the parity; `events` (two
+    CUDA events, optional) are recorded before and after it on the current stream."""
 
     def __init__(self, H: Hierarchy):
         if H.nlev != 1 or H.patchwise:
             raise ValueError("the fused stepper is for one-level hierarchies on the tiled path")
         self.H = H
         ctx = H.ctx
-        flags = claw.CLAW_ADVANCE_UPDATE_DT
+        flags = claw.CLAW_ADVANCE_UPDATE_DT | claw.CLAW_ADVANCE_PULL_GHOSTS
 
         def capture(fn):
             s = torch.cuda.Stream(device=H.dev)
@@ -372,37 +366,29 @@ class FusedStepper:
             torch.cuda.current_stream(H.dev).wait_stream(s)
             return g
 
-        claw.claw_fill_ghost(ctx, 0, H.q[0][H.cur[0]])
         self.c0 = H.cur[0]
-        self.graphs = []   # graphs[i] reads buffer c0 ^ i and writes the other: (step, ghost copy)
+        self.graphs = []   # graphs[i] reads buffer c0 ^ i and writes the other
         for _ in range(2):
             c = H.cur[0]
             qa, qb = H.q[0][c], H.q[0][1 - c]
             # one eager launch first (tensor-map cache, kernel attributes), then capture
             claw.claw_level_advance(ctx, 0, qa, qb, H.aux[0], H.dt, H.smax, flags)
-            claw.claw_fill_ghost(ctx, 0, qb)
-            gs = capture(lambda s, qa=qa, qb=qb: claw.claw_level_advance(ctx, 0, qa, qb, H.aux[0], H.dt, H.smax,
-                                                                          flags, s))
-            gf = capture(lambda s, qb=qb: claw.claw_fill_ghost(ctx, 0, qb, None, None, 0.0, s))
-            self.graphs.append((gs, gf))
+            self.graphs.append(capture(lambda s, qa=qa, qb=qb: claw.claw_level_advance(
+                ctx, 0, qa, qb, H.aux[0], H.dt, H.smax, flags, s)))
             H.cur[0] ^= 1
         torch.cuda.synchronize(H.dev)
         # launches of one step, counted by the library
         before = claw.claw_launch_count(ctx)
         claw.claw_level_advance(ctx, 0, H.q[0][H.cur[0]], H.q[0][1 - H.cur[0]], H.aux[0], H.dt, H.smax, flags)
-        claw.claw_fill_ghost(ctx, 0, H.q[0][1 - H.cur[0]])
         self.launches_per_step = claw.claw_launch_count(ctx) - before
         H.cur[0] ^= 1
 
     def step(self, events=None):
         H = self.H
-        gs, gf = self.graphs[H.cur[0] ^ self.c0]
+        g = self.graphs[H.cur[0] ^ self.c0]
         if events is not None:
             events[0].record()
-        gs.replay()
+        g.replay()
         if events is not None:
             events[1].record()
-        gf.replay()
-        if events is not None:
-            events[2].record()
         H.cur[0] ^= 1

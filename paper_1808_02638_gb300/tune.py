@@ -54,28 +54,30 @@ def _save(d):
     os.replace(tmp, CACHE)
 
 
-def time_tiling(H, L, tiling, reps=5):
-    """mean device time (ms) of one fused launch of level L with `tiling`"""
+def time_tiling(H, L, tiling, reps=5, pull=False):
+    """mean device time (ms) of one fused launch of level L with `tiling` (pull: with the ghosts
+    taken from their source cells, as the one-level fused path steps)"""
+    flags = claw.CLAW_ADVANCE_PULL_GHOSTS if pull else 0
     tx, ty, staging, threads = tiling
     claw.claw_set_tiling(H.ctx, L, tx, ty, staging, threads)
     src = H.q[L][H.cur[L]]
     dst = torch.empty_like(src)
     smax = torch.zeros_like(H.smax)
     for _ in range(2):
-        claw.claw_level_step(H.ctx, L, src, dst, H.aux[L], H.dt, smax)
+        claw.claw_level_advance(H.ctx, L, src, dst, H.aux[L], H.dt, smax, flags)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        claw.claw_level_step(H.ctx, L, src, dst, H.aux[L], H.dt, smax)
+        claw.claw_level_advance(H.ctx, L, src, dst, H.aux[L], H.dt, smax, flags)
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
 
 
-def tune_level(H, L, use_cache=True, candidates=None):
+def tune_level(H, L, use_cache=True, candidates=None, pull=False):
     """pick the fastest tiling for level L of hierarchy H, install it and return it with the
     timings (an empty dict when the choice came from the cache)"""
-    key = _key(H, L)
+    key = _key(H, L) + ("-pull" if pull else "")
     if use_cache:
         with _lock:
             hit = _load().get(key)
@@ -90,7 +92,7 @@ def tune_level(H, L, use_cache=True, candidates=None):
     timings = {}
     for c in candidates or candidates_for(H):
         try:
-            timings[c] = time_tiling(H, L, c)
+            timings[c] = time_tiling(H, L, c, pull=pull)
         except claw.ClawError:
             continue   # e.g. bulk-copy staging not allowed for this level
     best = min(timings, key=timings.get)

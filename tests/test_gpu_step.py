@@ -222,10 +222,12 @@ def _tilings():
 @pytest.mark.parametrize("tiling", _tilings())
 def test_full_size_bench_launch_path_sampled_parity(orc, tiling):
     # the launch path bench.py times, at its full size: 2048^2 as 4096 patches, the tiling the
-    # autotuner picks (or each candidate), CUDA-graph replays of the persistent level-step with
-    # the device Eq. cfl update followed by the ghost-copy graph.  At steps 0, 100 and 199:
-    # sampled patches equal the oracle's one-patch step from the same input, and every ghost of
-    # q^{n+1} equals the edge-extrapolated global field; after 200 steps the symmetries hold.
+    # autotuner picks (or each candidate), CUDA-graph replays of the one launch per step: the
+    # persistent level-step that takes every ghost from its source cell and applies the device
+    # Eq. cfl update.  The pools' ghost cells are poisoned with NaN first: the step must never
+    # read them.  At steps 0, 100 and 199 sampled patches equal the oracle's one-patch step from
+    # the same input, whose ghosts are the edge-extrapolated global field; after 200 steps the
+    # symmetries hold.
     from paper_1808_02638_gb300 import claw, tune
     from paper_1808_02638_gb300.solver import Hierarchy
     import torch
@@ -235,13 +237,19 @@ def test_full_size_bench_launch_path_sampled_parity(orc, tiling):
     H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
     H.init_dt()
     if tiling == "tuned":
-        tune.tune_level(H, 0, use_cache=False)
+        tune.tune_level(H, 0, use_cache=False, pull=True)
     else:
         claw.claw_set_tiling(H.ctx, 0, *tiling)
     H.coarse_step()
     H.coarse_step()
+    ghost = np.ones(lev.qsize, bool)
+    for nb in range(len(lev.boxes)):
+        inputs.box_view(ghost, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M] = False
+    gmask = torch.from_numpy(np.concatenate([ghost, np.zeros(H.q[0][0].numel() - ghost.size, bool)])).to(H.dev)
+    for k in range(2):
+        H.q[0][k][gmask] = float("nan")
     st = H.fused_stepper()
-    assert st.launches_per_step == 2
+    assert st.launches_per_step == 1
     rng = np.random.default_rng(7)
     sample = rng.choice(len(lev.boxes), 32, replace=False)
     ones = np.ones((36, 36))
@@ -256,27 +264,73 @@ def test_full_size_bench_launch_path_sampled_parity(orc, tiling):
         check = step in (0, 100, 199)
         if check:
             torch.cuda.synchronize()
-            before = H.pool(0).cpu().numpy()
+            gp = np.pad(glob_of(H.pool(0).cpu().numpy()), ((0, 0), (M, M), (M, M)), mode="edge")
             dt = float(H.dt[0])
         st.step()
         if check:
             torch.cuda.synchronize()
             after = H.pool(0).cpu().numpy()
-            scale = np.abs(after).max()
+            scale = np.nanmax(np.abs(after))
             for nb in sample:
-                qin = inputs.box_view(before, lev.qoff[nb], 32, 32, 3).copy()
+                ilo, jlo = int(lev.boxes[nb][0]), int(lev.boxes[nb][1])
+                qin = np.ascontiguousarray(gp[:, jlo:jlo + 36, ilo:ilo + 36])
                 want, _ = orc.step(qin, ones, 4 * ones, lev.dx, lev.dy, dt)
                 got = inputs.box_view(after, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
                 assert np.abs(got - want[:, M:-M, M:-M]).max() <= TOL1 * scale
-            gp = np.pad(glob_of(after), ((0, 0), (M, M), (M, M)), mode="edge")
-            for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
-                assert np.array_equal(inputs.box_view(after, lev.qoff[nb], 32, 32, 3),
-                                      gp[:, jlo:jlo + 36, ilo:ilo + 36])
-    p, u, v = glob_of(H.pool(0).cpu().numpy())
+    g = glob_of(H.pool(0).cpu().numpy())
+    assert np.isfinite(g).all()
+    p, u, v = g
     tol = 1e-12 * max(np.abs(p).max(), 1.0)
     assert np.abs(p - p.T).max() <= tol and np.abs(p - p[:, ::-1]).max() <= tol
     assert np.abs(u - v.T).max() <= tol and np.abs(u + u[:, ::-1]).max() <= tol
     assert H.sync_status() == 0
+
+
+def test_pulled_ghosts_equal_filled_ghosts_on_amr_and_walls():
+    # the pulled path against fill + step on boxes of mixed sizes with periodic and wall
+    # boundaries (sign flips), and on the finer level of a hierarchy (interpolated ghosts are
+    # filled, copied ones are pulled): bit for bit the same new state
+    import torch
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    for bc in ((1, 1, 2, 2), (2, 0, 1, 1)):
+        run = inputs.Run(*inputs.PULSE_DOMAIN, bc=bc)
+        run.levels = inputs.amr_levels(run, 32, 4, [(0.2, 0.45)], [2002])
+        q = [inputs.init_q(run, lev) for lev in run.levels]
+        for L, lev in enumerate(run.levels):
+            for nb, b in enumerate(lev.boxes):   # a velocity field so that the wall flips matter
+                v = inputs.box_view(q[L], lev.qoff[nb], int(b[2]), int(b[3]), 3)
+                v[1] = 0.3 * v[0]
+                v[2] = -0.2 * v[0]
+        H = Hierarchy([run], [q], rho0=1.0, K0=4.0)
+        H.init_dt()
+        for L in range(2):
+            qc = H.q[L - 1][H.cur[L - 1]] if L else None
+            a = H.q[L][H.cur[L]]
+            claw.claw_fill_ghost(H.ctx, L, a, qc, qc, 0.0)
+            ref = torch.zeros_like(a)
+            claw.claw_level_step(H.ctx, L, a, ref, None, H.dt, H.smax)
+            # pulled: the copied ghosts of a poisoned copy must not matter
+            b = a.clone()
+            ring_cells = torch.zeros_like(a, dtype=torch.bool)
+            lev = run.levels[L]
+            qbase = [qb for (ri, qb, _) in H.layout[L] if ri == 0][0]
+            mask = np.zeros(lev.qsize, bool)
+            for nb, bx in enumerate(lev.boxes):
+                nx, ny = int(bx[2]), int(bx[3])
+                m = inputs.box_view(mask, lev.qoff[nb], nx, ny, 3)
+                m[...] = True
+                m[:, M:-M, M:-M] = False
+            if L == 0:   # level 0 has no interpolated ghosts: poison them all
+                ring_cells[qbase:qbase + lev.qsize] = torch.from_numpy(mask).to(a.device)
+                b[ring_cells] = float("nan")
+            out = torch.zeros_like(a)
+            claw.claw_level_advance(H.ctx, L, b, out, None, H.dt, H.smax, claw.CLAW_ADVANCE_PULL_GHOSTS)
+            torch.cuda.synchronize()
+            inner = torch.from_numpy(~mask).to(a.device)
+            sl = slice(qbase, qbase + lev.qsize)
+            assert torch.equal(out[sl][inner], ref[sl][inner]), (bc, L)
+        assert H.sync_status() == 0
 
 
 def test_host_resident_steps_equal_device_steps():

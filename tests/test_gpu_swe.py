@@ -237,9 +237,10 @@ def test_graph_replay_equals_eager():
 
 def test_full_size_bench_path_sampled_parity(orc):
     # 2048^2 as 4096 patches of 32 x 32, the shallow-water bench workload, through the fused
-    # stepper (graphs of the persistent step with the device Eq. cfl update and the ghost
-    # copy) with the tuned tiling: sampled patches equal the oracle's one-patch step from the
-    # same input at steps 0, 40 and 79, and the radial symmetry holds at the end
+    # stepper (graphs of the one launch per step: the persistent step with ghosts pulled from
+    # their source cells and the device Eq. cfl update) with the tuned tiling: sampled patches
+    # equal the oracle's one-patch step from the same input (ghosts: the edge-extrapolated
+    # global field) at steps 0, 40 and 79, and the radial symmetry holds at the end
     import torch
     from paper_1808_02638_gb300 import tune
     run = inputs.config1()
@@ -247,16 +248,24 @@ def test_full_size_bench_path_sampled_parity(orc):
     q = inputs.init_swe(run, lev)
     H = _hier(run, q)
     H.init_dt()
-    tune.tune_level(H, 0, use_cache=False)
+    tune.tune_level(H, 0, use_cache=False, pull=True)
     H.coarse_step()
     st = H.fused_stepper()
+    assert st.launches_per_step == 1
     rng = np.random.default_rng(9)
     sample = rng.choice(len(lev.boxes), 32, replace=False)
+
+    def glob_of(pool):
+        g = np.zeros((3, 2048, 2048))
+        for nb, (ilo, jlo, bnx, bny) in enumerate(lev.boxes):
+            g[:, jlo:jlo + 32, ilo:ilo + 32] = inputs.box_view(pool, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
+        return g
+
     for step in range(80):
         check = step in (0, 40, 79)
         if check:
             torch.cuda.synchronize()
-            before = H.pool(0).cpu().numpy()
+            gp = np.pad(glob_of(H.pool(0).cpu().numpy()), ((0, 0), (M, M), (M, M)), mode="edge")
             dt = float(H.dt[0])
         st.step()
         if check:
@@ -264,7 +273,8 @@ def test_full_size_bench_path_sampled_parity(orc):
             after = H.pool(0).cpu().numpy()
             scale = np.abs(after).max()
             for nb in sample:
-                qin = inputs.box_view(before, lev.qoff[nb], 32, 32, 3).copy()
+                ilo, jlo = int(lev.boxes[nb][0]), int(lev.boxes[nb][1])
+                qin = np.ascontiguousarray(gp[:, jlo:jlo + 36, ilo:ilo + 36])
                 want, _ = orc.swe_step(qin, lev.dx, lev.dy, dt, G)
                 got = inputs.box_view(after, lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
                 assert np.abs(got - want[:, M:-M, M:-M]).max() <= TOL1 * scale
