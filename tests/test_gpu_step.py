@@ -473,8 +473,9 @@ def test_autotuner_installs_a_valid_tiling_and_keeps_parity(orc):
 
 @pytest.mark.parametrize("case", ["tiled_extrap", "tiled_periodic", "single_wall_16", "cellwise_32x16"])
 def test_fused_advance_equals_fill_step_update(case):
-    # claw_level_advance with the ghost push and the fused Eq. cfl reproduces fill + step +
-    # dt update bit for bit: interiors, ghosts of q_new, dt and the reset speed maximum
+    # the fused one-launch step (ghosts pulled from their sources, Eq. cfl on the last CTA)
+    # reproduces fill + step + dt update bit for bit: interiors, dt and the reset speed maximum;
+    # one more step with the ghost push as well gives q_new's ghosts equal to a fill
     from paper_1808_02638_gb300 import claw
     from paper_1808_02638_gb300.solver import Hierarchy
     import torch
@@ -506,12 +507,20 @@ def test_fused_advance_equals_fill_step_update(case):
         A.coarse_step()
         B.coarse_step()
     torch.cuda.synchronize()
-    # ghosts of the current buffer: A's are from the last fill of the buffer it read, so refill
-    claw.claw_fill_ghost(A.ctx, 0, A.pool(0))
     a, b = A.pool(0).cpu().numpy(), B.pool(0).cpu().numpy()
     for n, box in enumerate(lev.boxes):
-        va = inputs.box_view(a, lev.qoff[n], int(box[2]), int(box[3]), 3)
-        vb = inputs.box_view(b, lev.qoff[n], int(box[2]), int(box[3]), 3)
+        va = inputs.box_view(a, lev.qoff[n], int(box[2]), int(box[3]), 3)[:, 2:-2, 2:-2]
+        vb = inputs.box_view(b, lev.qoff[n], int(box[2]), int(box[3]), 3)[:, 2:-2, 2:-2]
         assert np.array_equal(va, vb)
     assert float(A.dt[0]) == float(B.dt[0]) and float(B.smax[0]) == 0.0
+    # push as well: the ghosts of q_new are those a fill gives
+    A.coarse_step()
+    src, dst = B.q[0][B.cur[0]], B.q[0][1 - B.cur[0]]
+    claw.claw_level_advance(B.ctx, 0, src, dst, B.aux[0], B.dt, B.smax,
+                            claw.CLAW_ADVANCE_PULL_GHOSTS | claw.CLAW_ADVANCE_PUSH_GHOSTS |
+                            claw.CLAW_ADVANCE_UPDATE_DT)
+    B.cur[0] ^= 1
+    claw.claw_fill_ghost(A.ctx, 0, A.pool(0))
+    torch.cuda.synchronize()
+    assert torch.equal(A.pool(0), B.pool(0))
     assert A.sync_status() == 0 and B.sync_status() == 0
