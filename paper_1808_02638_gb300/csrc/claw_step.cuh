@@ -227,12 +227,17 @@ __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P
         const PatchDev S = A.patches[e.x];
         const long long sp = (long long)(S.nx + 4) * (S.ny + 4);
         const double* src = A.qold + S.qoff + (e.y & ((1 << kRingOffBits) - 1));
-        const int fl = (int)((unsigned)e.y >> kRingOffBits);
-        const double a = __ldg(src), b = __ldg(src + sp), c = __ldg(src + 2 * sp);
+        const unsigned fl = (unsigned)e.y >> kRingOffBits;
+        // wall sign flips as sign-bit xors (integer pipe, not an FP64 negation)
+        const unsigned long long sb = (unsigned long long)(fl & 1u) << 63;
+        const unsigned long long sc = (unsigned long long)((fl >> 1) & 1u) << 63;
+        const double a = __ldg(src);
+        const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(src + sp));
+        const unsigned long long c = (unsigned long long)__double_as_longlong(__ldg(src + 2 * sp));
         const int i = xs + ys * SW;
         sq[i] = a;
-        sq[QPL + i] = (fl & 1) ? -b : b;
-        sq[2 * QPL + i] = (fl & 2) ? -c : c;
+        sq[QPL + i] = __longlong_as_double((long long)(b ^ sb));
+        sq[2 * QPL + i] = __longlong_as_double((long long)(c ^ sc));
     }
     // these generic writes precede later bulk copies (async proxy) into the same buffer
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
