@@ -1199,7 +1199,7 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
         a.tmaps = get_tmaps(ctx, L, q_old, s);
         if (!a.tmaps) staging = 0;
     }
-    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging);
+    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, a.ring != nullptr);
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;

@@ -165,6 +165,7 @@ struct StepArgs {
     double grav = 0.0;             // shallow water
     int swe = 0;                   // 1: the shallow water system (the conservation fix reads it)
     const int2* ring = nullptr;    // not null: same-level and boundary ghosts are pulled from sources
+                                   // (launch_step then picks the kernels that pull)
     // fused epilogue (0 = off)
     int dtupd = 0;                      // the last CTA applies Eq. cfl to dt and resets smax
     double* dt_out = nullptr;
@@ -183,7 +184,7 @@ enum : int { KIND_UNIFORM = 0, KIND_CELLWISE = 1, KIND_SWE = 2 };
 // launchers (claw_step.cu; kind: KIND_*)
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s);
-int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging);
+int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull = false);
 cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
                                 int medium, int limiter, int nsm, cudaStream_t s);   // grid: resident CTAs x nsm
 int adjoint_tile();   // the adjoint kernel's square tile edge

@@ -7,12 +7,17 @@
 
 namespace claw {
 
-static StepKernel pick(int kind, int limiter, int tx, int ty, int nt, int staging)
+static StepKernel pick(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull)
 {
     switch (kind) {
-    case KIND_UNIFORM: return step_kernel_uniform(limiter, tx, ty, nt, staging);
-    case KIND_CELLWISE: return step_kernel_cellwise(limiter, tx, ty, nt, staging);
-    case KIND_SWE: return step_kernel_swe(limiter, tx, ty, nt, staging);
+    case KIND_UNIFORM:
+        return pull ? step_kernel_uniform_pull(limiter, tx, ty, nt, staging)
+                    : step_kernel_uniform(limiter, tx, ty, nt, staging);
+    case KIND_CELLWISE:
+        return pull ? step_kernel_cellwise_pull(limiter, tx, ty, nt, staging)
+                    : step_kernel_cellwise(limiter, tx, ty, nt, staging);
+    case KIND_SWE:
+        return pull ? step_kernel_swe_pull(limiter, tx, ty, nt, staging) : step_kernel_swe(limiter, tx, ty, nt, staging);
     }
     return StepKernel{nullptr, 0, 0};
 }
@@ -33,9 +38,9 @@ static cudaError_t prepare(const StepKernel& k)
     return e;
 }
 
-int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging)
+int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull)
 {
-    StepKernel k = pick(kind, limiter, tx, ty, nt, staging);
+    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, pull);
     if (!k.fn || prepare(k) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k.fn, k.nt, k.smem) != cudaSuccess)
@@ -46,7 +51,7 @@ int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int stag
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s)
 {
-    StepKernel k = pick(kind, limiter, tx, ty, nt, staging);
+    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, a.ring != nullptr);
     if (!k.fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare(k);
     if (e != cudaSuccess) return e;

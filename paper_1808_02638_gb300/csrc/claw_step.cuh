@@ -248,7 +248,9 @@ __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P
 // STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered: the next tile streams in
 // during the whole of this one), 2 tensor bulk copies into one buffer (the next tile is requested
 // once this one's state has been read, in phase D) with registers capped for three CTAs per SM.
-template <int MED, int LIM, int TX, int TY, int NT, int STAGE>
+// PULL: same-level and boundary ghosts are taken from their source cells (a separate
+// instantiation: the mere presence of the pull code slowed the other kernels by up to 11 %).
+template <int MED, int LIM, int TX, int TY, int NT, int STAGE, bool PULL>
 __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const StepArgs A)
 {
     using G = Geo<TX, TY>;
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
             }
             __syncthreads();
         }
-        if (A.ring && P.ring >= 0) {
+        if (PULL && P.ring >= 0) {
             pull_ghosts<G::SW, G::QPL, NT>(A, P, sq, x0, y0, tx, ty);
             __syncthreads();
         }
@@ -707,11 +709,11 @@ struct StepKernel {
     int nt;
 };
 
-template <int MED, int LIM, int TX, int TY, int NT, int STAGE>
+template <int MED, int LIM, int TX, int TY, int NT, int STAGE, bool PULL>
 StepKernel step_kernel_entry()
 {
     StepKernel k;
-    k.fn = step_kernel<MED, LIM, TX, TY, NT, STAGE>;
+    k.fn = step_kernel<MED, LIM, TX, TY, NT, STAGE, PULL>;
     k.smem = Geo<TX, TY>::smem_bytes(STAGE == 1 ? 2 : 1);
     k.nt = NT;
     return k;
@@ -719,37 +721,41 @@ StepKernel step_kernel_entry()
 
 // all tile shapes and stagings of one medium and limiter
 // tile shapes x thread counts x stagings of one medium and limiter (nt = 0: the default)
-template <int MED, int LIM>
+template <int MED, int LIM, bool PULL>
 StepKernel step_kernel_select(int tx, int ty, int nt, int staging)
 {
     if (tx == 32 && ty == 32 && (nt == 0 || nt == 256))
-        return staging ? step_kernel_entry<MED, LIM, 32, 32, 256, 1>() : step_kernel_entry<MED, LIM, 32, 32, 256, 0>();
+        return staging ? step_kernel_entry<MED, LIM, 32, 32, 256, 1, PULL>() : step_kernel_entry<MED, LIM, 32, 32, 256, 0, PULL>();
     if (tx == 32 && ty == 32 && nt == 512)
-        return staging ? step_kernel_entry<MED, LIM, 32, 32, 512, 1>() : step_kernel_entry<MED, LIM, 32, 32, 512, 0>();
+        return staging ? step_kernel_entry<MED, LIM, 32, 32, 512, 1, PULL>() : step_kernel_entry<MED, LIM, 32, 32, 512, 0, PULL>();
     if (tx == 32 && ty == 16 && (nt == 0 || nt == 256)) {
-        if (staging == 2) return step_kernel_entry<MED, LIM, 32, 16, 256, 2>();
-        return staging ? step_kernel_entry<MED, LIM, 32, 16, 256, 1>() : step_kernel_entry<MED, LIM, 32, 16, 256, 0>();
+        if (staging == 2) return step_kernel_entry<MED, LIM, 32, 16, 256, 2, PULL>();
+        return staging ? step_kernel_entry<MED, LIM, 32, 16, 256, 1, PULL>() : step_kernel_entry<MED, LIM, 32, 16, 256, 0, PULL>();
     }
     if (tx == 16 && ty == 16 && (nt == 0 || nt == 128))
-        return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1>() : step_kernel_entry<MED, LIM, 16, 16, 128, 0>();
+        return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1, PULL>() : step_kernel_entry<MED, LIM, 16, 16, 128, 0, PULL>();
     return StepKernel{nullptr, 0, 0};
 }
 
-template <int MED>
+template <int MED, bool PULL>
 StepKernel step_kernel_for(int lim, int tx, int ty, int nt, int staging)
 {
     switch (lim) {
-    case CLAW_LIM_NONE: return step_kernel_select<MED, CLAW_LIM_NONE>(tx, ty, nt, staging);
-    case CLAW_LIM_MINMOD: return step_kernel_select<MED, CLAW_LIM_MINMOD>(tx, ty, nt, staging);
-    case CLAW_LIM_SUPERBEE: return step_kernel_select<MED, CLAW_LIM_SUPERBEE>(tx, ty, nt, staging);
-    case CLAW_LIM_VANLEER: return step_kernel_select<MED, CLAW_LIM_VANLEER>(tx, ty, nt, staging);
-    case CLAW_LIM_MC: return step_kernel_select<MED, CLAW_LIM_MC>(tx, ty, nt, staging);
+    case CLAW_LIM_NONE: return step_kernel_select<MED, CLAW_LIM_NONE, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_MINMOD: return step_kernel_select<MED, CLAW_LIM_MINMOD, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_SUPERBEE: return step_kernel_select<MED, CLAW_LIM_SUPERBEE, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_VANLEER: return step_kernel_select<MED, CLAW_LIM_VANLEER, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_MC: return step_kernel_select<MED, CLAW_LIM_MC, PULL>(tx, ty, nt, staging);
     }
     return StepKernel{nullptr, 0, 0};
 }
 
+// one translation unit per kernel family (pull: the instantiations taking pulled ghosts)
 StepKernel step_kernel_uniform(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_uniform_pull(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_cellwise(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_cellwise_pull(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_swe(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_swe_pull(int lim, int tx, int ty, int nt, int staging);
 
 }  // namespace claw

@@ -1,0 +1,9 @@
+// Instantiations of the fused level-step for a cell-wise medium that take pulled ghosts.
+#include "claw_step.cuh"
+
+namespace claw {
+StepKernel step_kernel_cellwise_pull(int lim, int tx, int ty, int nt, int staging)
+{
+    return step_kernel_for<1, true>(lim, tx, ty, nt, staging);
+}
+}  // namespace claw

@@ -91,8 +91,9 @@ __device__ __forceinline__ void tsplit(double d1, double d2, double d3, double u
 }
 }  // namespace swe
 
-// STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered).
-template <int LIM, int TX, int TY, int NT, int STAGE>
+// STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered).  PULL: ghosts taken from
+// their source cells (separate instantiations, as for acoustics).
+template <int LIM, int TX, int TY, int NT, int STAGE, bool PULL>
 __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
 {
     using G = Geo<TX, TY>;
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
             }
             __syncthreads();
         }
-        if (A.ring && P.ring >= 0) {
+        if (PULL && P.ring >= 0) {
             pull_ghosts<G::SW, G::QPL, NT>(A, P, sq, x0, y0, tx, ty);
             __syncthreads();
         }
@@ -467,36 +468,47 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
     if (tid == 0) finish_cta(A);
 }
 
-template <int LIM, int TX, int TY, int NT, int STAGE>
+template <int LIM, int TX, int TY, int NT, int STAGE, bool PULL>
 static StepKernel swe_entry()
 {
     StepKernel k;
-    k.fn = swe_step_kernel<LIM, TX, TY, NT, STAGE>;
+    k.fn = swe_step_kernel<LIM, TX, TY, NT, STAGE, PULL>;
     k.smem = SweGeo<TX, TY>::smem_bytes(STAGE ? 2 : 1);
     k.nt = NT;
     return k;
 }
 
-template <int LIM>
+template <int LIM, bool PULL>
 static StepKernel swe_select(int tx, int ty, int nt, int staging)
 {
     if (tx == 16 && ty == 16 && (nt == 0 || nt == 256))
-        return staging ? swe_entry<LIM, 16, 16, 256, 1>() : swe_entry<LIM, 16, 16, 256, 0>();
+        return staging ? swe_entry<LIM, 16, 16, 256, 1, PULL>() : swe_entry<LIM, 16, 16, 256, 0, PULL>();
     if (tx == 32 && ty == 16 && (nt == 0 || nt == 512))
-        return staging ? swe_entry<LIM, 32, 16, 512, 1>() : swe_entry<LIM, 32, 16, 512, 0>();
+        return staging ? swe_entry<LIM, 32, 16, 512, 1, PULL>() : swe_entry<LIM, 32, 16, 512, 0, PULL>();
+    return StepKernel{nullptr, 0, 0};
+}
+
+template <bool PULL>
+static StepKernel swe_for(int lim, int tx, int ty, int nt, int staging)
+{
+    switch (lim) {
+    case CLAW_LIM_NONE: return swe_select<CLAW_LIM_NONE, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_MINMOD: return swe_select<CLAW_LIM_MINMOD, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_SUPERBEE: return swe_select<CLAW_LIM_SUPERBEE, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_VANLEER: return swe_select<CLAW_LIM_VANLEER, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_MC: return swe_select<CLAW_LIM_MC, PULL>(tx, ty, nt, staging);
+    }
     return StepKernel{nullptr, 0, 0};
 }
 
 StepKernel step_kernel_swe(int lim, int tx, int ty, int nt, int staging)
 {
-    switch (lim) {
-    case CLAW_LIM_NONE: return swe_select<CLAW_LIM_NONE>(tx, ty, nt, staging);
-    case CLAW_LIM_MINMOD: return swe_select<CLAW_LIM_MINMOD>(tx, ty, nt, staging);
-    case CLAW_LIM_SUPERBEE: return swe_select<CLAW_LIM_SUPERBEE>(tx, ty, nt, staging);
-    case CLAW_LIM_VANLEER: return swe_select<CLAW_LIM_VANLEER>(tx, ty, nt, staging);
-    case CLAW_LIM_MC: return swe_select<CLAW_LIM_MC>(tx, ty, nt, staging);
-    }
-    return StepKernel{nullptr, 0, 0};
+    return swe_for<false>(lim, tx, ty, nt, staging);
+}
+
+StepKernel step_kernel_swe_pull(int lim, int tx, int ty, int nt, int staging)
+{
+    return swe_for<true>(lim, tx, ty, nt, staging);
 }
 
 }  // namespace claw
