@@ -389,8 +389,9 @@ def main():
                  "fused_over_plain": value / world / pv}
 
     # end to end: the state lives on the host (pinned); every step copies q in, runs the
-    # level-step through the C ABI and copies q^{n+1} back (Hierarchy.steps_from_host: the copy
-    # out of one step overlaps the copy into the next, piece by piece)
+    # level-step through the C ABI and copies q^{n+1} back (Hierarchy.steps_from_host: the level
+    # is stepped in pieces of boxes as they arrive, so copies in both directions and the steps
+    # overlap)
     H.fused = True          # one launch per step, ghosts pulled from their source cells
     e2e_steps = max(3, min(20, K // 4))
     qbytes = H.q[0][0].numel() * 8

@@ -198,6 +198,16 @@ int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q
 int claw_level_advance(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
                        const double* aux, double* dt, double* smax, int32_t flags, void* stream);
 
+/* claw_level_advance restricted to the boxes [box_begin, box_end) of the level (their tiles, in
+ * box order): a level-step taken in pieces, so that host copies of some boxes overlap the steps
+ * of others.  The pieces of one step, in any order, give bit for bit the claw_level_advance of
+ * the whole level.  flags: CLAW_ADVANCE_PULL_GHOSTS only (apply claw_dt_update after the last
+ * piece; push ghosts with claw_fill_ghost).  With pulled ghosts a piece reads the boxes it
+ * touches and their neighbours' interiors in q_old.  Errors as claw_level_advance. */
+int claw_level_advance_boxes(claw_ctx* ctx, int32_t level, int32_t box_begin, int32_t box_end,
+                             const double* q_old, double* q_new, const double* aux,
+                             const double* dt, double* smax, int32_t flags, void* stream);
+
 /* The same step with one kernel launch per box (the per-patch launch pattern of Sec. 3.1.2,
  * kept as the comparison baseline of the fused launch). */
 int claw_level_step_patchwise(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,

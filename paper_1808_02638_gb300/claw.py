@@ -74,6 +74,7 @@ _SIGNATURES = {
     "claw_level_step": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_level_step_patchwise": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_level_advance": ([VP, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
+    "claw_level_advance_boxes": ([VP, I32, I32, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
     "claw_level_step_noalloc": ([I32, I32, DBL, DBL, I32, I32, I32, DBL, DBL, VP, VP, VP, VP, VP, VP],
                                 ctypes.c_int),
     "claw_average_down": ([VP, I32, VP, VP, VP], ctypes.c_int),
@@ -258,6 +259,12 @@ def claw_level_step(ctx, level, q_old, q_new, aux, dt, smax, stream=None):
 CLAW_ADVANCE_PUSH_GHOSTS = 1
 CLAW_ADVANCE_PULL_GHOSTS = 4
 CLAW_ADVANCE_UPDATE_DT = 2
+
+
+def claw_level_advance_boxes(ctx, level, box_begin, box_end, q_old, q_new, aux, dt, smax, flags, stream=None):
+    _check("claw_level_advance_boxes", load().claw_level_advance_boxes(
+        ctx, level, int(box_begin), int(box_end), _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax),
+        int(flags), _stream(stream)))
 
 
 def claw_level_advance(ctx, level, q_old, q_new, aux, dt, smax, flags, stream=None):

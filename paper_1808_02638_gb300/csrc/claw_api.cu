@@ -1211,6 +1211,36 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
     return cuda_rc(e);
 }
 
+int claw_level_advance_boxes(claw_ctx* ctx, int32_t L, int32_t box_begin, int32_t box_end, const double* q_old,
+                             double* q_new, const double* aux, const double* dt, double* smax, int32_t flags,
+                             void* stream)
+{
+    int rc = check_step_args(ctx, L, q_old, q_new, aux, dt, smax);
+    if (rc) return rc;
+    if (flags & ~CLAW_ADVANCE_PULL_GHOSTS) return CLAW_EINVAL;
+    if ((flags & CLAW_ADVANCE_PULL_GHOSTS) && !ctx->lev[L].ring_ok) return CLAW_EINVAL;
+    LevelDev& d = ctx->lev[L];
+    if (box_begin < 0 || box_end > d.nboxes || box_begin > box_end) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    const auto& st = ctx->ptile_start[L];
+    if (box_begin == box_end || st[box_end] == st[box_begin]) return CLAW_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    StepArgs a = make_args(ctx, L, q_old, q_new, aux, dt, smax);
+    a.tiles = ctx->ptiles[L] + st[box_begin];
+    a.ntiles = st[box_end] - st[box_begin];
+    if (flags & CLAW_ADVANCE_PULL_GHOSTS) a.ring = d.ring;
+    int staging = d.staging;
+    if (staging >= 1) {
+        a.tmaps = get_tmaps(ctx, L, q_old, s);
+        if (!a.tmaps) staging = 0;
+    }
+    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, a.ring != nullptr);
+    if (per_sm <= 0) return CLAW_ECUDA;
+    const int grid = std::min(a.ntiles, per_sm * ctx->nsm);
+    ctx->launches += 1;
+    return cuda_rc(launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s));
+}
+
 int claw_level_step_patchwise(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,
                               const double* dt, double* smax, void* stream)
 {

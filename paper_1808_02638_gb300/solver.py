@@ -237,41 +237,90 @@ class Hierarchy:
         else:
             claw.claw_dt_update(self.ctx, 0, self.smax, self.dt, stream)
 
-    def steps_from_host(self, host_a, host_b, nsteps, chunks=8):
-        """One-level hierarchies: `nsteps` coarse steps with the state resident in pinned host
-        memory.  Every step copies the whole state from the host into the current pool, advances
-        it, and copies the new state back to the other host buffer; the next step reads that one.
-        The copies are split into `chunks` pieces on two copy streams, so that a piece can go back
-        in as soon as it has come out: the copy out of one step overlaps the copy into the next.
+    def _bands(self, nbands):
+        """contiguous box ranges of level 0 (about equal cells), their element ranges in the
+        pool, and for each range the ranges whose boxes its ghosts read (boxes that meet it
+        grown by two cells, with periodic images)"""
+        boxes = self.boxes[0]
+        cells = np.cumsum([int(b.nx) * int(b.ny) for b in boxes])
+        total = int(cells[-1])
+        cut = [0] + [int(np.searchsorted(cells, total * k / nbands, side="right")) for k in range(1, nbands)] + \
+            [len(boxes)]
+        cut = sorted(set(cut))
+        bands = [(cut[k], cut[k + 1]) for k in range(len(cut) - 1) if cut[k + 1] > cut[k]]
+        owner = np.zeros(len(boxes), dtype=np.int64)
+        for k, (b0, b1) in enumerate(bands):
+            owner[b0:b1] = k
+        run0 = self.runs[0]
+        NX, NY = run0.levels[0].NX, run0.levels[0].NY
+        shx = [0] + ([-NX, NX] if run0.bc[0] == 1 else [])
+        shy = [0] + ([-NY, NY] if run0.bc[2] == 1 else [])
+        lo = np.array([[b.run, b.ilo, b.jlo, b.ilo + b.nx, b.jlo + b.ny] for b in boxes], dtype=np.int64)
+        needs = []
+        for (b0, b1) in bands:
+            need = set()
+            for n in range(b0, b1):
+                r, i0, j0, i1, j1 = lo[n]
+                for sx in shx:
+                    for sy in shy:
+                        hit = (lo[:, 0] == r) & (lo[:, 1] + sx < i1 + 2) & (lo[:, 3] + sx > i0 - 2) & \
+                              (lo[:, 2] + sy < j1 + 2) & (lo[:, 4] + sy > j0 - 2)
+                        need.update(int(v) for v in np.unique(owner[hit]))
+            needs.append(sorted(need))
+        ranges = []
+        for (b0, b1) in bands:
+            last = boxes[b1 - 1]
+            ranges.append((int(boxes[b0].qoff), int(last.qoff) + 3 * (int(last.nx) + 4) * (int(last.ny) + 4)))
+        return bands, ranges, needs
+
+    def steps_from_host(self, host_a, host_b, nsteps, bands=8):
+        """One-level hierarchies of one run: `nsteps` coarse steps with the state resident in
+        pinned host memory.  Every step copies the state from the host into the current pool,
+        advances it, and copies the new state back into the other host buffer; the next step
+        reads that one.  The level is taken in `bands` pieces of boxes (claw_level_advance_boxes
+        with pulled ghosts): a piece is stepped as soon as it and the pieces its ghosts come from
+        have arrived, and copied back as soon as it is stepped, so that the copies in both
+        directions overlap each other and the steps.  Eq. cfl follows the last piece of a step.
         Returns the host buffer holding the final state."""
-        if self.nlev != 1:
-            raise ValueError("host-resident stepping is for one-level hierarchies")
+        if self.nlev != 1 or self.nruns != 1:
+            raise ValueError("host-resident stepping is for one-level hierarchies of one run")
+        if not hasattr(self, "_band_cache") or self._band_cache[0] != bands:
+            self._band_cache = (bands, self._bands(bands))
+        parts, ranges, needs = self._band_cache[1]
         comp = torch.cuda.current_stream(self.dev)
         s_in, s_out = torch.cuda.Stream(device=self.dev), torch.cuda.Stream(device=self.dev)
-        n = host_a.numel()
-        bounds = [(c * n // chunks, (c + 1) * n // chunks) for c in range(chunks)]
-        out_done = [None] * chunks
+        arrived = [torch.cuda.Event() for _ in parts]
+        stepped = [torch.cuda.Event() for _ in parts]
+        left = [None] * len(parts)
         src, dst = host_a, host_b
         s_in.wait_stream(comp)
+        flags = claw.CLAW_ADVANCE_PULL_GHOSTS
         for _ in range(nsteps):
-            q = self.q[0][self.cur[0]]
-            for c, (a, b) in enumerate(bounds):
-                if out_done[c] is not None:
-                    s_in.wait_event(out_done[c])   # this piece has left the device
+            q, qn = self.q[0][self.cur[0]], self.q[0][1 - self.cur[0]]
+            for k, (a, b) in enumerate(ranges):
+                if left[k] is not None:
+                    s_in.wait_event(left[k])   # this piece of the previous step is back on the host
                 with torch.cuda.stream(s_in):
                     q[a:b].copy_(src[a:b], non_blocking=True)
-            comp.wait_stream(s_in)
-            self.coarse_step()
-            s_out.wait_stream(comp)
-            qn = self.q[0][self.cur[0]]
-            for c, (a, b) in enumerate(bounds):
+                arrived[k].record(s_in)
+            for k, (b0, b1) in enumerate(parts):
+                for m in needs[k]:
+                    comp.wait_event(arrived[m])
+                claw.claw_level_advance_boxes(self.ctx, 0, b0, b1, q, qn, self.aux[0], self.dt, self.smax, flags,
+                                              comp)
+                stepped[k].record(comp)
+            claw.claw_dt_update(self.ctx, 0, self.smax, self.dt, comp)
+            for k, (a, b) in enumerate(ranges):
+                s_out.wait_event(stepped[k])
                 with torch.cuda.stream(s_out):
                     dst[a:b].copy_(qn[a:b], non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(s_out)
-                out_done[c] = ev
+                left[k] = ev
+            self.cur[0] ^= 1
             src, dst = dst, src
         comp.wait_stream(s_out)
+        comp.wait_stream(s_in)
         return src
 
     def launches_per_coarse_step(self):

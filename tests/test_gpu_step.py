@@ -334,8 +334,8 @@ def test_pulled_ghosts_equal_filled_ghosts_on_amr_and_walls():
 
 
 def test_host_resident_steps_equal_device_steps():
-    # the pipelined host loop (state copied in and out every step, in pieces on two streams)
-    # produces bit for bit the states of the same steps on the device
+    # the pipelined host loop (state copied in and out every step, the level stepped in pieces
+    # of boxes as they arrive) produces bit for bit the states of the same steps on the device
     import torch
     from paper_1808_02638_gb300.solver import Hierarchy
     run = inputs.config1(256, 32)
@@ -350,9 +350,41 @@ def test_host_resident_steps_equal_device_steps():
     ha.copy_(B.q[0][B.cur[0]])
     for _ in range(6):
         A.coarse_step()
-    out = B.steps_from_host(ha, hb, 6, chunks=5)
+    out = B.steps_from_host(ha, hb, 6, bands=5)
     torch.cuda.synchronize()
     assert torch.equal(out, A.pool(0).cpu()) and float(A.dt[0]) == float(B.dt[0])
+
+
+@pytest.mark.parametrize("bc,bands", [((1, 1, 1, 1), 7), ((2, 0, 1, 2), 3)])
+def test_host_resident_bands_follow_ghost_sources(bc, bands):
+    # periodic and wall boundaries: a piece waits for the pieces its ghosts come from,
+    # including the periodic images; the result equals the one-launch device steps bit for bit
+    import torch
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config1(256, 32)
+    run.bc = bc
+    q = inputs.init_q(run, run.levels[0])
+    v = q.reshape(-1)
+    A = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    B = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    for h in (A, B):
+        h.init_dt()
+        h.fused = True
+    _, _, needs = B._bands(bands)
+    if bc[0] == 1:   # the first piece reads the last one across the periodic boundary
+        assert len(needs) - 1 in needs[0]
+    ha = torch.empty_like(B.q[0][0], device="cpu").pin_memory()
+    hb = torch.empty_like(ha).pin_memory()
+    ha.copy_(B.q[0][B.cur[0]])
+    for _ in range(5):
+        A.coarse_step()
+    out = B.steps_from_host(ha, hb, 5, bands=bands)
+    torch.cuda.synchronize()
+    lev = run.levels[0]
+    for nb, b in enumerate(lev.boxes):
+        got = inputs.box_view(out.numpy(), lev.qoff[nb], 32, 32, 3)[:, M:-M, M:-M]
+        assert np.array_equal(got, A.interior(0, 0, nb)), nb
+    assert float(A.dt[0]) == float(B.dt[0]) and A.sync_status() == 0 and B.sync_status() == 0
 
 
 def test_errors_are_status_codes():
