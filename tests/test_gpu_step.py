@@ -355,7 +355,7 @@ def test_host_resident_steps_equal_device_steps():
     assert torch.equal(out, A.pool(0).cpu()) and float(A.dt[0]) == float(B.dt[0])
 
 
-@pytest.mark.parametrize("bc,bands", [((1, 1, 1, 1), 7), ((2, 0, 1, 2), 3)])
+@pytest.mark.parametrize("bc,bands", [((1, 1, 1, 1), 7), ((2, 0, 2, 2), 3)])
 def test_host_resident_bands_follow_ghost_sources(bc, bands):
     # periodic and wall boundaries: a piece waits for the pieces its ghosts come from,
     # including the periodic images; the result equals the one-launch device steps bit for bit
