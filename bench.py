@@ -394,11 +394,11 @@ def main():
     # overlap)
     H.fused = True          # one launch per step, ghosts pulled from their source cells
     e2e_steps = max(3, min(20, K // 4))
-    # bytes each way per step: the pool ranges of the pieces (boxes with their ghost frames)
-    qbytes = 8 * sum(b - a for a, b in H._bands(4)[1])
-    host_in = torch.empty_like(H.q[0][0], device="cpu").pin_memory()
-    host_in.copy_(H.q[0][H.cur[0]])
+    # the host holds the state in packed form (interiors only, 3 x 2048^2 doubles): the bytes
+    # each way per step
+    host_in = H.pack().cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
+    qbytes = host_in.numel() * 8
     H.steps_from_host(host_in, host_out, 2)   # warm-up: piece tables, streams, events
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

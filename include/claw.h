@@ -208,6 +208,19 @@ int claw_level_advance_boxes(claw_ctx* ctx, int32_t level, int32_t box_begin, in
                              const double* q_old, double* q_new, const double* aux,
                              const double* dt, double* smax, int32_t flags, void* stream);
 
+/* Packed interiors of a level: box after box in box order, each box's three planes of nx x ny
+ * interior cells (x fastest), no ghosts and no padding; box b starts at element
+ * 3 * sum over earlier boxes of nx * ny.  claw_packed_size: the doubles of a level's packed
+ * form (or minus an error code).  claw_pack_interiors copies the interiors of the boxes
+ * [box_begin, box_end) of the pool q into their places in `packed` (the whole level's packed
+ * buffer); claw_unpack_interiors the other way (ghost cells of q are not touched).  Device
+ * pointers; enqueued on `stream`.  Errors: CLAW_EINVAL, CLAW_ECUDA. */
+long long claw_packed_size(claw_ctx* ctx, int32_t level);
+int claw_pack_interiors(claw_ctx* ctx, int32_t level, int32_t box_begin, int32_t box_end,
+                        const double* q, double* packed, void* stream);
+int claw_unpack_interiors(claw_ctx* ctx, int32_t level, int32_t box_begin, int32_t box_end,
+                          const double* packed, double* q, void* stream);
+
 /* The same step with one kernel launch per box (the per-patch launch pattern of Sec. 3.1.2,
  * kept as the comparison baseline of the fused launch). */
 int claw_level_step_patchwise(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,

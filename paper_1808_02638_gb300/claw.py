@@ -75,6 +75,9 @@ _SIGNATURES = {
     "claw_level_step_patchwise": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_level_advance": ([VP, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
     "claw_level_advance_boxes": ([VP, I32, I32, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
+    "claw_packed_size": ([VP, I32], ctypes.c_longlong),
+    "claw_pack_interiors": ([VP, I32, I32, I32, VP, VP, VP], ctypes.c_int),
+    "claw_unpack_interiors": ([VP, I32, I32, I32, VP, VP, VP], ctypes.c_int),
     "claw_level_step_noalloc": ([I32, I32, DBL, DBL, I32, I32, I32, DBL, DBL, VP, VP, VP, VP, VP, VP],
                                 ctypes.c_int),
     "claw_average_down": ([VP, I32, VP, VP, VP], ctypes.c_int),
@@ -259,6 +262,23 @@ def claw_level_step(ctx, level, q_old, q_new, aux, dt, smax, stream=None):
 CLAW_ADVANCE_PUSH_GHOSTS = 1
 CLAW_ADVANCE_PULL_GHOSTS = 4
 CLAW_ADVANCE_UPDATE_DT = 2
+
+
+def claw_packed_size(ctx, level):
+    n = load().claw_packed_size(ctx, level)
+    if n < 0:
+        raise ClawError("claw_packed_size", -n)
+    return n
+
+
+def claw_pack_interiors(ctx, level, box_begin, box_end, q, packed, stream=None):
+    _check("claw_pack_interiors", load().claw_pack_interiors(ctx, level, int(box_begin), int(box_end), _ptr(q),
+                                                             _ptr(packed), _stream(stream)))
+
+
+def claw_unpack_interiors(ctx, level, box_begin, box_end, packed, q, stream=None):
+    _check("claw_unpack_interiors", load().claw_unpack_interiors(ctx, level, int(box_begin), int(box_end),
+                                                                 _ptr(packed), _ptr(q), _stream(stream)))
 
 
 def claw_level_advance_boxes(ctx, level, box_begin, box_end, q_old, q_new, aux, dt, smax, flags, stream=None):

@@ -170,6 +170,9 @@ void free_level(claw_ctx* ctx, int L)
     d.flagboxes = nullptr;
     cudaFree(d.ring);
     d.ring = nullptr;
+    cudaFree(d.poff);
+    d.poff = nullptr;
+    d.packed = 0;
     d.ring_ok = false;
     d.reflux = nullptr;
     d.reflux_group = nullptr;
@@ -973,6 +976,16 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     d.ncopy_blocks = qstart.empty() ? 0 : (int)qstart.size() - 1;
     d.max_rows = 0;
     for (const claw_box& b : d.boxes) d.max_rows = std::max(d.max_rows, b.ny + 4);
+    {   // packed interiors: box order, 3 planes of nx x ny each
+        std::vector<long long> poff(d.nboxes);
+        long long o = 0;
+        for (int n = 0; n < d.nboxes; ++n) {
+            poff[n] = o;
+            o += 3LL * d.boxes[n].nx * d.boxes[n].ny;
+        }
+        d.packed = o;
+        if ((rc = upload(&d.poff, poff))) return rc;
+    }
     if (L > 0) build_avg_tables(ctx, L, avg);
     if (L > 0) {
         std::vector<RefluxRec> rrec;
@@ -1239,6 +1252,35 @@ int claw_level_advance_boxes(claw_ctx* ctx, int32_t L, int32_t box_begin, int32_
     const int grid = std::min(a.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;
     return cuda_rc(launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s));
+}
+
+long long claw_packed_size(claw_ctx* ctx, int32_t L)
+{
+    if (!valid_level(ctx, L)) return -CLAW_EINVAL;
+    return ctx->lev[L].packed;
+}
+
+static int pack_call(claw_ctx* ctx, int L, int b0, int b1, double* q, double* packed, int unpack, void* stream)
+{
+    if (!valid_level(ctx, L) || !q || !packed) return CLAW_EINVAL;
+    const LevelDev& d = ctx->lev[L];
+    if (b0 < 0 || b1 > d.nboxes || b0 > b1) return CLAW_EINVAL;
+    if (b0 == b1) return CLAW_OK;
+    DevGuard g(ctx->device);
+    ctx->launches += 1;
+    return cuda_rc(launch_pack(d.patches, d.poff, b0, b1, d.max_rows - 4, q, packed, unpack, (cudaStream_t)stream));
+}
+
+int claw_pack_interiors(claw_ctx* ctx, int32_t L, int32_t box_begin, int32_t box_end, const double* q,
+                        double* packed, void* stream)
+{
+    return pack_call(ctx, L, box_begin, box_end, const_cast<double*>(q), packed, 0, stream);
+}
+
+int claw_unpack_interiors(claw_ctx* ctx, int32_t L, int32_t box_begin, int32_t box_end, const double* packed,
+                          double* q, void* stream)
+{
+    return pack_call(ctx, L, box_begin, box_end, q, const_cast<double*>(packed), 1, stream);
 }
 
 int claw_level_step_patchwise(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,

@@ -380,6 +380,39 @@ static inline dim3 box_rows_grid(int n, int max_rows)
     return dim3((unsigned)n, (unsigned)((max_rows + kBoxRows - 1) / kBoxRows));
 }
 
+// ------------------------------------------------------------------------ packed interiors
+// block (box b0 + x, chunk y of kBoxRows interior rows): the chunk's 3 x rows x nx cells between
+// the box's padded planes and its packed planes (3 planes of nx x ny at poff[b])
+__global__ void pack_kernel(const PatchDev* __restrict__ patches, const long long* __restrict__ poff, int b0,
+                            double* __restrict__ q, double* __restrict__ packed, int unpack)
+{
+    const int b = b0 + (int)blockIdx.x;
+    const PatchDev P = patches[b];
+    const int r0 = blockIdx.y * kBoxRows;
+    if (r0 >= P.ny) return;
+    const int rows = min(P.ny, r0 + kBoxRows) - r0;
+    const int W = P.nx + 4;
+    const long long WH = (long long)W * (P.ny + 4), NN = (long long)P.nx * P.ny;
+    const long long base = poff[b];
+    const int per = rows * P.nx, n = 3 * per;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int m = k / per, e = k - m * per;
+        const int r = r0 + e / P.nx, i = e % P.nx;
+        const long long qo = P.qoff + m * WH + (long long)(r + 2) * W + (i + 2);
+        const long long po = base + m * NN + (long long)r * P.nx + i;
+        if (unpack) q[qo] = packed[po];
+        else packed[po] = q[qo];
+    }
+}
+
+cudaError_t launch_pack(const PatchDev* p, const long long* poff, int b0, int b1, int max_rows, double* q,
+                        double* packed, int unpack, cudaStream_t s)
+{
+    if (b1 <= b0) return cudaSuccess;
+    pack_kernel<<<box_rows_grid(b1 - b0, max_rows), 256, 0, s>>>(p, poff, b0, q, packed, unpack);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_medium_aux(const PatchDev* p, int n, int max_rows, const double* rho, const double* K,
                               double* aux, cudaStream_t s)
 {

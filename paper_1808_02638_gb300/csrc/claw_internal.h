@@ -125,7 +125,9 @@ struct LevelDev {
     int* reflux_group = nullptr;  // [ngroups + 1]: records of coarse cell g are [group[g], group[g+1])
     int nreflux_groups = 0;
     FlagBox* flagboxes = nullptr; // the boxes as flag-grid writers (built on first use)
-    int2* ring = nullptr;         // ghost sources of every box's ring (pulled ghosts), see RingEntry
+    int2* ring = nullptr;         // ghost sources of every box's ring (pulled ghosts), see ring_index
+    long long* poff = nullptr;    // packed-interior offset of every box (3 nx ny doubles each)
+    long long packed = 0;         // doubles of the packed interiors of the level
     bool ring_ok = false;
     // host copies
     std::vector<claw_box> boxes;
@@ -229,6 +231,8 @@ cudaError_t launch_reflux_apply(const RefluxRec* rec, int n, const int* group, i
                                 const PatchDev* cp, const double* dt, const double* buf, double* qc, cudaStream_t s);
 cudaError_t launch_cfl_max(const PatchDev* p, int n, int max_rows, int medium, double c0, const double* aux,
                            double* smax, cudaStream_t s);
+cudaError_t launch_pack(const PatchDev* p, const long long* poff, int b0, int b1, int max_rows, double* q,
+                        double* packed, int unpack, cudaStream_t s);
 cudaError_t launch_cfl_max_state(const PatchDev* p, int n, int max_rows, double grav, const double* q,
                                  double* smax, cudaStream_t s);
 cudaError_t launch_dt_update(const double* minh, const double* cfl, int nruns, double* smax,

@@ -273,21 +273,44 @@ class Hierarchy:
             ranges.append((int(boxes[b0].qoff), int(last.qoff) + 3 * (int(last.nx) + 4) * (int(last.ny) + 4)))
         return bands, ranges, needs
 
+    def packed_size(self, L=0):
+        """doubles of level L's packed interiors (every box's three nx x ny planes, box order)"""
+        return claw.claw_packed_size(self.ctx, L)
+
+    def pack(self, L=0, out=None):
+        """level L's interiors in packed form (a device tensor)"""
+        out = torch.empty(self.packed_size(L), dtype=torch.float64, device=self.dev) if out is None else out
+        claw.claw_pack_interiors(self.ctx, L, 0, len(self.boxes[L]), self.q[L][self.cur[L]], out)
+        return out
+
     def steps_from_host(self, host_a, host_b, nsteps, bands=4):
         """One-level hierarchies of one run: `nsteps` coarse steps with the state resident in
-        pinned host memory.  Every step copies the state from the host into the current pool,
-        advances it, and copies the new state back into the other host buffer; the next step
-        reads that one.  The level is taken in `bands` pieces of boxes (claw_level_advance_boxes
-        with pulled ghosts): a piece is stepped as soon as it and the pieces its ghosts come from
-        have arrived, and copied back as soon as it is stepped, so that the copies in both
-        directions overlap each other and the steps.  Eq. cfl follows the last piece of a step.
-        Four pieces measured fastest on the 2048^2 workload (0.80 ms per step against 1.70 ms
-        for one piece).  Returns the host buffer holding the final state."""
+        pinned host memory, either as the level's pool (with ghost cells) or in packed form
+        (interiors only, see `pack`; chosen by the buffers' length).  Every step copies the state
+        from the host, advances it, and copies the new state back into the other host buffer;
+        the next step reads that one.  The level is taken in `bands` pieces of boxes
+        (claw_level_advance_boxes with pulled ghosts): a piece is stepped as soon as it and the
+        pieces its ghosts come from have arrived, and copied back as soon as it is stepped, so
+        that the copies in both directions overlap each other and the steps.  Packed pieces are
+        unpacked into the pool and packed out of it on the copy streams.  Eq. cfl follows the
+        last piece of a step.  Four pieces measured fastest on the 2048^2 workload.  Returns the
+        host buffer holding the final state."""
         if self.nlev != 1 or self.nruns != 1:
             raise ValueError("host-resident stepping is for one-level hierarchies of one run")
         if not hasattr(self, "_band_cache") or self._band_cache[0] != bands:
             self._band_cache = (bands, self._bands(bands))
         parts, ranges, needs = self._band_cache[1]
+        packed = host_a.numel() == self.packed_size(0)
+        if packed:
+            sizes = [3 * int(b.nx) * int(b.ny) for b in self.boxes[0]]
+            offs = np.concatenate([[0], np.cumsum(sizes)])
+            ranges = [(int(offs[b0]), int(offs[b1])) for (b0, b1) in parts]
+            if getattr(self, "_stage", None) is None or self._stage[0].numel() != host_a.numel():
+                self._stage = (torch.empty(host_a.numel(), dtype=torch.float64, device=self.dev),
+                               torch.empty(host_a.numel(), dtype=torch.float64, device=self.dev))
+            st_in, st_out = self._stage
+        elif host_a.numel() != self.q[0][0].numel():
+            raise ValueError("host buffers must hold the level's pool or its packed interiors")
         comp = torch.cuda.current_stream(self.dev)
         s_in, s_out = torch.cuda.Stream(device=self.dev), torch.cuda.Stream(device=self.dev)
         arrived = [torch.cuda.Event() for _ in parts]
@@ -295,6 +318,7 @@ class Hierarchy:
         left = [None] * len(parts)
         src, dst = host_a, host_b
         s_in.wait_stream(comp)
+        s_out.wait_stream(comp)
         flags = claw.CLAW_ADVANCE_PULL_GHOSTS
         for _ in range(nsteps):
             q, qn = self.q[0][self.cur[0]], self.q[0][1 - self.cur[0]]
@@ -302,7 +326,11 @@ class Hierarchy:
                 if left[k] is not None:
                     s_in.wait_event(left[k])   # this piece of the previous step is back on the host
                 with torch.cuda.stream(s_in):
-                    q[a:b].copy_(src[a:b], non_blocking=True)
+                    if packed:
+                        st_in[a:b].copy_(src[a:b], non_blocking=True)
+                        claw.claw_unpack_interiors(self.ctx, 0, parts[k][0], parts[k][1], st_in, q, s_in)
+                    else:
+                        q[a:b].copy_(src[a:b], non_blocking=True)
                 arrived[k].record(s_in)
             for k, (b0, b1) in enumerate(parts):
                 for m in needs[k]:
@@ -314,7 +342,11 @@ class Hierarchy:
             for k, (a, b) in enumerate(ranges):
                 s_out.wait_event(stepped[k])
                 with torch.cuda.stream(s_out):
-                    dst[a:b].copy_(qn[a:b], non_blocking=True)
+                    if packed:
+                        claw.claw_pack_interiors(self.ctx, 0, parts[k][0], parts[k][1], qn, st_out, s_out)
+                        dst[a:b].copy_(st_out[a:b], non_blocking=True)
+                    else:
+                        dst[a:b].copy_(qn[a:b], non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(s_out)
                 left[k] = ev

@@ -355,6 +355,35 @@ def test_host_resident_steps_equal_device_steps():
     assert torch.equal(out, A.pool(0).cpu()) and float(A.dt[0]) == float(B.dt[0])
 
 
+def test_host_resident_packed_interiors():
+    # the same loop with the host state in packed form (interiors only): unpacked into the pool
+    # and packed out of it piece by piece; equal to the device steps bit for bit
+    import torch
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config1(256, 32)
+    run.bc = (1, 1, 0, 0)
+    q = inputs.init_q(run, run.levels[0])
+    A = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    B = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    for h in (A, B):
+        h.init_dt()
+        h.fused = True
+    assert B.packed_size() == 3 * 256 * 256
+    ha = B.pack().cpu().pin_memory()
+    hb = torch.empty_like(ha).pin_memory()
+    for _ in range(7):
+        A.coarse_step()
+    out = B.steps_from_host(ha, hb, 7, bands=4)
+    torch.cuda.synchronize()
+    assert torch.equal(out, A.pack().cpu())
+    lev = run.levels[0]
+    v = out.numpy()
+    for nb, b in enumerate(lev.boxes):   # packed layout: box after box, three 32 x 32 planes
+        got = v[nb * 3 * 1024:(nb + 1) * 3 * 1024].reshape(3, 32, 32)
+        assert np.array_equal(got, A.interior(0, 0, nb))
+    assert float(A.dt[0]) == float(B.dt[0]) and B.sync_status() == 0
+
+
 @pytest.mark.parametrize("bc,bands", [((1, 1, 1, 1), 7), ((2, 0, 2, 2), 3)])
 def test_host_resident_bands_follow_ghost_sources(bc, bands):
     # periodic and wall boundaries: a piece waits for the pieces its ghosts come from,
