@@ -313,25 +313,40 @@ class Hierarchy:
             raise ValueError("host buffers must hold the level's pool or its packed interiors")
         comp = torch.cuda.current_stream(self.dev)
         s_in, s_out = torch.cuda.Stream(device=self.dev), torch.cuda.Stream(device=self.dev)
+        # packed form: the unpack and pack kernels run on their own streams, so that the copy
+        # streams carry copies only
+        s_un, s_pk = torch.cuda.Stream(device=self.dev), torch.cuda.Stream(device=self.dev)
         arrived = [torch.cuda.Event() for _ in parts]
         stepped = [torch.cuda.Event() for _ in parts]
+        landed = [torch.cuda.Event() for _ in parts]      # a packed piece is in the staging buffer
+        unpacked = [None] * len(parts)                    # ... and has been unpacked from it
+        packed_ev = [torch.cuda.Event() for _ in parts]   # a piece is packed into the out staging
         left = [None] * len(parts)
         src, dst = host_a, host_b
-        s_in.wait_stream(comp)
-        s_out.wait_stream(comp)
+        for st in (s_in, s_out, s_un, s_pk):
+            st.wait_stream(comp)
         flags = claw.CLAW_ADVANCE_PULL_GHOSTS
         for _ in range(nsteps):
             q, qn = self.q[0][self.cur[0]], self.q[0][1 - self.cur[0]]
             for k, (a, b) in enumerate(ranges):
                 if left[k] is not None:
                     s_in.wait_event(left[k])   # this piece of the previous step is back on the host
-                with torch.cuda.stream(s_in):
-                    if packed:
+                if packed:
+                    if unpacked[k] is not None:
+                        s_in.wait_event(unpacked[k])   # its staging slot has been read
+                    with torch.cuda.stream(s_in):
                         st_in[a:b].copy_(src[a:b], non_blocking=True)
-                        claw.claw_unpack_interiors(self.ctx, 0, parts[k][0], parts[k][1], st_in, q, s_in)
-                    else:
+                    landed[k].record(s_in)
+                    s_un.wait_event(landed[k])
+                    claw.claw_unpack_interiors(self.ctx, 0, parts[k][0], parts[k][1], st_in, q, s_un)
+                    ev = torch.cuda.Event()
+                    ev.record(s_un)
+                    unpacked[k] = ev
+                    arrived[k] = ev
+                else:
+                    with torch.cuda.stream(s_in):
                         q[a:b].copy_(src[a:b], non_blocking=True)
-                arrived[k].record(s_in)
+                    arrived[k].record(s_in)
             for k, (b0, b1) in enumerate(parts):
                 for m in needs[k]:
                     comp.wait_event(arrived[m])
@@ -340,20 +355,26 @@ class Hierarchy:
                 stepped[k].record(comp)
             claw.claw_dt_update(self.ctx, 0, self.smax, self.dt, comp)
             for k, (a, b) in enumerate(ranges):
-                s_out.wait_event(stepped[k])
-                with torch.cuda.stream(s_out):
-                    if packed:
-                        claw.claw_pack_interiors(self.ctx, 0, parts[k][0], parts[k][1], qn, st_out, s_out)
+                if packed:
+                    s_pk.wait_event(stepped[k])
+                    if left[k] is not None:
+                        s_pk.wait_event(left[k])   # its out staging slot has been copied out
+                    claw.claw_pack_interiors(self.ctx, 0, parts[k][0], parts[k][1], qn, st_out, s_pk)
+                    packed_ev[k].record(s_pk)
+                    s_out.wait_event(packed_ev[k])
+                    with torch.cuda.stream(s_out):
                         dst[a:b].copy_(st_out[a:b], non_blocking=True)
-                    else:
+                else:
+                    s_out.wait_event(stepped[k])
+                    with torch.cuda.stream(s_out):
                         dst[a:b].copy_(qn[a:b], non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(s_out)
                 left[k] = ev
             self.cur[0] ^= 1
             src, dst = dst, src
-        comp.wait_stream(s_out)
-        comp.wait_stream(s_in)
+        for st in (s_out, s_in, s_un, s_pk):
+            comp.wait_stream(st)
         return src
 
     def launches_per_coarse_step(self):
