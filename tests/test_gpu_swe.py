@@ -216,6 +216,26 @@ def test_regridding_matches_the_oracle(orc):
     assert H.sync_status() == 0
 
 
+@pytest.mark.parametrize("bc", [(2, 2, 2, 2), (1, 1, 0, 0)])
+def test_pulled_ghosts_equal_filled_ghosts(bc):
+    # the one-launch path (ghosts pulled from their sources, wall flips of hu and hv) against
+    # fill + step + dt update on 9 patches: bit for bit over 10 steps
+    import torch
+    run = _run(96, boxes=inputs.uniform_tiling(96, 96, 32, 32), bc=bc)
+    q = inputs.init_swe(run, run.levels[0], u0=0.25, v0=-0.15)
+    A, B = _hier(run, q), _hier(run, q)
+    B.fused = True
+    for h in (A, B):
+        h.init_dt()
+    for _ in range(10):
+        A.coarse_step()
+        B.coarse_step()
+    torch.cuda.synchronize()
+    for nb in range(len(run.levels[0].boxes)):
+        assert np.array_equal(A.interior(0, 0, nb), B.interior(0, 0, nb))
+    assert torch.equal(A.dt, B.dt) and A.sync_status() == 0 and B.sync_status() == 0
+
+
 def test_graph_replay_equals_eager():
     import torch
     run = inputs.config1(256, 32)
