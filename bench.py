@@ -469,6 +469,7 @@ def main():
         "clocks": clocks,
         "status": claw.strerror(status),
         "adjoint": per_config["c3"]["adjoint"] if per_config else None,
+        "adjoint_tape": per_config["c3"]["adjoint_tape"] if per_config else None,
         "per_config": per_config,
     }
     if not args.no_cpu_baseline and world == 1:

@@ -5,8 +5,11 @@ initial state and the medium (rho, K), through the hand-written adjoint kernels.
 `rollout(H, q0, rho, K, ncoarse, every)` is a torch.autograd.Function over `ncoarse` coarse
 steps of hierarchy H (any number of levels and runs).  The forward keeps a checkpoint of every
 level's state every `every` coarse steps; the backward recomputes one segment at a time from its
-checkpoint (recording each level-step's input state and the pre-average coarse state) and runs
-the reverse of the AMR time step of Sec. 2.2 on the device:
+checkpoint (recording each level-step's input state and the pre-average coarse state).  With
+`every=None` the forward records that tape for the whole rollout instead (memory: every
+level-step's input pool and every pre-average coarse pool, kept in HBM) and the backward
+recomputes nothing.  Either way the backward runs the reverse of the AMR time step of Sec. 2.2
+on the device:
 
   average (Sec. 2.3)        -> claw_average_down_adjoint
   fine substeps, last first -> claw_level_step_adjoint + claw_fill_ghost_adjoint (the
@@ -90,14 +93,25 @@ class _Rollout(torch.autograd.Function):
             else:   # time steps frozen at the caller's values (e.g. for finite differences)
                 H.freeze_dt = True
                 H.dt.copy_(dt)
-            checkpoints = []
-            for n in range(ncoarse):
-                if n % every == 0:
-                    checkpoints.append(([H.q[L][H.cur[L]].clone() for L in range(nlev)], H.dt.clone()))
-                H.coarse_step()
+            checkpoints, tapes = [], None
+            if every is None:   # the whole tape, recorded as the rollout runs
+                tapes = []
+                for n in range(ncoarse):
+                    dt_n = H.dt.clone()
+                    tapes.append((_advance_record(H, 0, None, None, 0.0), dt_n))
+                    if H.freeze_dt:
+                        H.smax.zero_()
+                    else:
+                        claw.claw_dt_update(H.ctx, 0, H.smax, H.dt)
+            else:
+                for n in range(ncoarse):
+                    if n % every == 0:
+                        checkpoints.append(([H.q[L][H.cur[L]].clone() for L in range(nlev)], H.dt.clone()))
+                    H.coarse_step()
             out = [H.q[L][H.cur[L]].clone() for L in range(nlev)]
         ctx.H, ctx.ncoarse, ctx.every, ctx.nlev = H, ncoarse, every, nlev
         ctx.checkpoints = checkpoints
+        ctx.tapes = tapes
         ctx.frozen = dt is not None
         H.freeze_dt = False
         return tuple(out)
@@ -107,6 +121,11 @@ class _Rollout(torch.autograd.Function):
         H, nlev, every, ncoarse = ctx.H, ctx.nlev, ctx.every, ctx.ncoarse
         lam = [g.clone() if g is not None else torch.zeros_like(H.q[L][0]) for L, g in enumerate(grads)]
         g_aux = [torch.zeros_like(H.aux[L]) if H.medium else None for L in range(nlev)]
+        if ctx.tapes is not None:
+            for node, dt in reversed(ctx.tapes):
+                H.dt.copy_(dt)   # frozen forward time step
+                _reverse(H, node, lam, g_aux)
+            ctx.tapes = None
         nseg = len(ctx.checkpoints)
         for s in reversed(range(nseg)):
             states, dt0 = ctx.checkpoints[s]
@@ -205,6 +224,7 @@ class LevelStep(torch.autograd.Function):
 def rollout(H, q0, rho=None, K=None, ncoarse=1, every=20, dt=None):
     """final states (one pool per level) after `ncoarse` coarse steps from q0 (pools per level),
     differentiable with respect to q0 and, for a cell-wise medium, the rho and K pools.
+    every: checkpoint interval of the recomputing backward, or None for the recorded tape.
     dt: None for Eq. cfl time steps, else a device tensor of per-run level-0 time steps used
     unchanged for every coarse step.  The gradient holds the time steps fixed either way."""
     nlev = H.nlev

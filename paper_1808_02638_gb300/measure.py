@@ -191,8 +191,9 @@ def _receiver_energy(H, outs):
 
 
 def time_adjoint(H, q, rho, K, ncoarse, every, passes=2):
-    """(forward ms, backward ms, gradients finite) of a checkpointed rollout and its reverse
-    sweep (eager launches); the last of `passes` passes is reported (the first warms up)"""
+    """(forward ms, backward ms, gradients finite) of a checkpointed rollout (every=None: with the
+    recorded tape) and its reverse sweep (eager launches); the last of `passes` passes is
+    reported (the first warms up)"""
     from .adjoint import rollout
     for _ in range(passes):
         tq, tr, tk = _tensors(H, q, "q"), _tensors(H, rho, "c"), _tensors(H, K, "c")
@@ -219,12 +220,17 @@ def config3(nsteps=400, every=20):
     tiling = tune_all(H)
     ms = time_fused(H, 40)
     fwd, bwd, ok = time_adjoint(H, [[q]], [[rho]], [[K]], nsteps, every)
+    tf, tb, tok = time_adjoint(H, [[q]], [[rho]], [[K]], nsteps, None)
     return _report("256x256 heterogeneous medium, 400 steps, checkpoints every 20, J = sum p^2 over the "
                    "16x16 receiver", H, ms, None, FP64_INSTR_CELLWISE, BYTES_CELLWISE,
                    {"tiling": tiling,
                     "adjoint": {"forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
                                 "gradients_finite": ok,
-                                "note": "eager launches; backward = segment recompute + adjoint steps"}})
+                                "note": "eager launches; backward = segment recompute + adjoint steps"},
+                    "adjoint_tape": {"forward_ms": tf, "backward_ms": tb, "backward_over_forward": tb / tf,
+                                     "gradients_finite": tok,
+                                     "note": "the forward records every level-step's input (HBM); "
+                                             "backward = adjoint steps only"}})
 
 
 def config4(nruns=64, ncoarse=100, every=20, plain=True):
@@ -239,6 +245,8 @@ def config4(nruns=64, ncoarse=100, every=20, plain=True):
     plain = time_plain(H, 2) if plain else None
     H.init_dt()
     fwd, bwd, ok = time_adjoint(H, qs, rhos, Ks, ncoarse, every)
+    H.init_dt()
+    tf, tb, tok = time_adjoint(H, qs, rhos, Ks, ncoarse, None)
     nbox = [sum(len(r.levels[L].boxes) for r, _, _ in runs) for L in range(2)]
     return _report(f"{nruns} independent 2-level runs (N in [64,256], ratio 4 on seeded annuli; boxes per "
                    f"level {nbox}), per-run heterogeneous media, all runs in one launch per level-step",
@@ -246,7 +254,11 @@ def config4(nruns=64, ncoarse=100, every=20, plain=True):
                    {"tiling": tiling,
                     "adjoint": {"coarse_steps": ncoarse, "every": every, "forward_ms": fwd, "backward_ms": bwd,
                                 "backward_over_forward": bwd / fwd, "gradients_finite": ok,
-                                "functional": "sum over runs of sum p^2 over each run's 16x16 receiver"}})
+                                "functional": "sum over runs of sum p^2 over each run's 16x16 receiver"},
+                    "adjoint_tape": {"forward_ms": tf, "backward_ms": tb, "backward_over_forward": tb / tf,
+                                     "gradients_finite": tok,
+                                     "note": "the forward records every level-step's input (HBM); "
+                                             "backward = adjoint steps only"}})
 
 
 def time_stepper(H, nsteps, warm=3):

@@ -45,6 +45,37 @@ def _compare(got, want, tol):
 
 
 @pytest.mark.parametrize("nlev", [1, 2])
+def test_recorded_tape_equals_recomputed_segments(nlev):
+    # every=None records the tape during the forward instead of recomputing segments in the
+    # backward: the same states enter the same reverse kernels, so the gradients are identical
+    import torch
+    from paper_1808_02638_gb300.adjoint import rollout
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = 32
+    run = inputs.Run(*inputs.PULSE_DOMAIN)
+    if nlev == 1:
+        run.levels = [inputs.Level(n, n, 2 / n, 2 / n, [(0, 0, n, n)])]
+    else:
+        run.levels = inputs.amr_levels(run, n, 4, [(0.2, 0.45)], [31])
+    r2 = inputs.smooth_field(21, n, n, 0.5, 2.0, sigma=3.0)
+    k2 = inputs.smooth_field(22, n, n, 1.0, 8.0, sigma=3.0)
+    q = [inputs.init_q(run, lev) for lev in run.levels]
+    rho = [inputs.coef_pool(lev, r2, 4 ** L) for L, lev in enumerate(run.levels)]
+    K = [inputs.coef_pool(lev, k2, 4 ** L) for L, lev in enumerate(run.levels)]
+    H = Hierarchy([run], [q], [rho], [K])
+    grads = []
+    for every in (3, None):
+        tq, tr, tk = _tensors(H, [q], "q"), _tensors(H, [rho], "c"), _tensors(H, [K], "c")
+        outs = rollout(H, tq, tr, tk, ncoarse=7, every=every)
+        J = _receiver_J(H, outs, run.levels[0], (18, 10, 6))
+        J.backward()
+        torch.cuda.synchronize()
+        grads.append([t.grad.clone() for t in tq + tr + tk] + [J.detach().clone()])
+    for a, b in zip(*grads):
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("nlev", [1, 2])
 def test_adjoint_matches_oracle_reverse_mode(nlev):
     import torch
     from oracle.amr import OracleHierarchy
