@@ -47,7 +47,9 @@ def _compare(got, want, tol):
 @pytest.mark.parametrize("nlev", [1, 2])
 def test_recorded_tape_equals_recomputed_segments(nlev):
     # every=None records the tape during the forward instead of recomputing segments in the
-    # backward: the same states enter the same reverse kernels, so the gradients are identical
+    # backward: the same states enter the same reverse kernels, so the functional is identical and
+    # the gradients agree to the rounding of the reverse kernels' FP64 atomics (their summation
+    # order is not fixed)
     import torch
     from paper_1808_02638_gb300.adjoint import rollout
     from paper_1808_02638_gb300.solver import Hierarchy
@@ -71,8 +73,9 @@ def test_recorded_tape_equals_recomputed_segments(nlev):
         J.backward()
         torch.cuda.synchronize()
         grads.append([t.grad.clone() for t in tq + tr + tk] + [J.detach().clone()])
-    for a, b in zip(*grads):
-        assert torch.equal(a, b)
+    assert torch.equal(grads[0][-1], grads[1][-1])
+    for a, b in zip(grads[0][:-1], grads[1][:-1]):
+        assert float((a - b).abs().max()) <= 1e-12 * max(float(b.abs().max()), 1e-300)
 
 
 @pytest.mark.parametrize("nlev", [1, 2])
