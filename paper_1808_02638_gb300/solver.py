@@ -23,6 +23,42 @@ def _align(n, a=inputs.ALIGN):
     return (n + a - 1) // a * a
 
 
+def band_plan(boxes, nbands, NX, NY, bc):
+    """Pieces of a level for stepping it in parts: `boxes` = [(ilo, jlo, nx, ny, qoff)] of one
+    run in pool order.  Returns (pieces, ranges, needs): contiguous box ranges of about equal
+    cells, their element ranges in the pool (q planes of the first box to the end of the last),
+    and for every piece the pieces whose boxes its ghosts read: the boxes that meet it grown by
+    two cells, with the periodic images of the domain [0, NX) x [0, NY) where bc says periodic."""
+    cells = np.cumsum([nx * ny for (_, _, nx, ny, _) in boxes])
+    total = int(cells[-1])
+    cut = [0] + [int(np.searchsorted(cells, total * k / nbands, side="right")) for k in range(1, nbands)] + \
+        [len(boxes)]
+    cut = sorted(set(cut))
+    pieces = [(cut[k], cut[k + 1]) for k in range(len(cut) - 1) if cut[k + 1] > cut[k]]
+    owner = np.zeros(len(boxes), dtype=np.int64)
+    for k, (b0, b1) in enumerate(pieces):
+        owner[b0:b1] = k
+    shx = [0] + ([-NX, NX] if bc[0] == 1 else [])
+    shy = [0] + ([-NY, NY] if bc[2] == 1 else [])
+    lo = np.array([[i0, j0, i0 + nx, j0 + ny] for (i0, j0, nx, ny, _) in boxes], dtype=np.int64)
+    needs = []
+    for (b0, b1) in pieces:
+        need = set()
+        for n in range(b0, b1):
+            i0, j0, i1, j1 = lo[n]
+            for sx in shx:
+                for sy in shy:
+                    hit = (lo[:, 0] + sx < i1 + 2) & (lo[:, 2] + sx > i0 - 2) & \
+                          (lo[:, 1] + sy < j1 + 2) & (lo[:, 3] + sy > j0 - 2)
+                    need.update(int(v) for v in np.unique(owner[hit]))
+        needs.append(sorted(need))
+    ranges = []
+    for (b0, b1) in pieces:
+        _, _, nx, ny, qoff = boxes[b1 - 1]
+        ranges.append((int(boxes[b0][4]), int(qoff) + 3 * (nx + 4) * (ny + 4)))
+    return pieces, ranges, needs
+
+
 class Hierarchy:
     """Device state of `runs` (a list of inputs.Run) on one context.
 
@@ -238,40 +274,11 @@ class Hierarchy:
             claw.claw_dt_update(self.ctx, 0, self.smax, self.dt, stream)
 
     def _bands(self, nbands):
-        """contiguous box ranges of level 0 (about equal cells), their element ranges in the
-        pool, and for each range the ranges whose boxes its ghosts read (boxes that meet it
-        grown by two cells, with periodic images)"""
-        boxes = self.boxes[0]
-        cells = np.cumsum([int(b.nx) * int(b.ny) for b in boxes])
-        total = int(cells[-1])
-        cut = [0] + [int(np.searchsorted(cells, total * k / nbands, side="right")) for k in range(1, nbands)] + \
-            [len(boxes)]
-        cut = sorted(set(cut))
-        bands = [(cut[k], cut[k + 1]) for k in range(len(cut) - 1) if cut[k + 1] > cut[k]]
-        owner = np.zeros(len(boxes), dtype=np.int64)
-        for k, (b0, b1) in enumerate(bands):
-            owner[b0:b1] = k
+        """the piece plan of level 0 for host-resident stepping (see band_plan)"""
         run0 = self.runs[0]
-        NX, NY = run0.levels[0].NX, run0.levels[0].NY
-        shx = [0] + ([-NX, NX] if run0.bc[0] == 1 else [])
-        shy = [0] + ([-NY, NY] if run0.bc[2] == 1 else [])
-        lo = np.array([[b.run, b.ilo, b.jlo, b.ilo + b.nx, b.jlo + b.ny] for b in boxes], dtype=np.int64)
-        needs = []
-        for (b0, b1) in bands:
-            need = set()
-            for n in range(b0, b1):
-                r, i0, j0, i1, j1 = lo[n]
-                for sx in shx:
-                    for sy in shy:
-                        hit = (lo[:, 0] == r) & (lo[:, 1] + sx < i1 + 2) & (lo[:, 3] + sx > i0 - 2) & \
-                              (lo[:, 2] + sy < j1 + 2) & (lo[:, 4] + sy > j0 - 2)
-                        need.update(int(v) for v in np.unique(owner[hit]))
-            needs.append(sorted(need))
-        ranges = []
-        for (b0, b1) in bands:
-            last = boxes[b1 - 1]
-            ranges.append((int(boxes[b0].qoff), int(last.qoff) + 3 * (int(last.nx) + 4) * (int(last.ny) + 4)))
-        return bands, ranges, needs
+        lev = run0.levels[0]
+        boxes = [(int(b.ilo), int(b.jlo), int(b.nx), int(b.ny), int(b.qoff)) for b in self.boxes[0]]
+        return band_plan(boxes, nbands, lev.NX, lev.NY, run0.bc)
 
     def packed_size(self, L=0):
         """doubles of level L's packed interiors (every box's three nx x ny planes, box order)"""
