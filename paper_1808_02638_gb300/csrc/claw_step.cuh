@@ -517,11 +517,6 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         //   x-fluctuation pressure into the cell D = (K/2) (ap + (1 - lx c) bp)
         // cell-wise medium: D = K ap + bp,  x-normal (K ap + bp/2, c au + bu/2)
         double cpa = 0, cpb = 0, cua = 0, cub = 0, cpay = 0, cpby = 0, cva = 0, cvb = 0, kDx = 0, kDy = 0;
-        double kT = 0, kU = 0;   // phase D's: read here, before thread 0 can rewrite s_k
-        if (MED == 0 && trans) {
-            kT = s_k[10];
-            kU = s_k[11];
-        }
         if (MED == 0) {
             cpa = s_k[0];
             cpb = s_k[1];
@@ -648,6 +643,11 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         // one staging buffer: the tile's state was last read in phase C (behind the barrier
         // above), so the next tile's copy can land while this one finishes
         if (STAGE == 2 && tid == 0 && t + (int)gridDim.x < A.ntiles) issue(t + gridDim.x, 0);
+        double kT = 0, kU = 0;
+        if (MED == 0 && trans) {
+            kT = s_k[10];
+            kU = s_k[11];
+        }
         double* dst = A.qnew + P.qoff;
 #pragma unroll
         for (int n = 0; n < NPER; ++n) {
@@ -676,17 +676,10 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
             dst[WH + o] = u;
             dst[2 * WH + o] = v;
         }
-        // Cell-wise medium: phase D reads the transverse fluxes over the wave-strength arrays,
-        // which the next tile's phase A rewrites, so all threads must finish first.  Uniform
-        // medium: phase D reads only D, E (written in phase C, next rewritten after the next
-        // tile's phase-B barrier) and registers, and the next tile's staging writes only the
-        // q buffer, which phase D does not read: no barrier is needed here.
-        if (MED != 0) __syncthreads();
+        __syncthreads();   // the staged tile and work arrays are reused by the next tile
         if (tid == 0) {
-            // every warp's atomics on this slot preceded the phase-A barrier; the slot is next
-            // written two tiles later, behind barriers thread 0 has not reached yet
             const unsigned long long m = s_tmax[it & 1];
-            s_tmax[it & 1] = 0ull;
+            s_tmax[it & 1] = 0ull;   // next written two tiles later, after two more barriers
             if (P.run != cur_run) {
                 flush();
                 cur_run = P.run;
