@@ -123,11 +123,12 @@ def config0():
     run = inputs.config0()
     H = Hierarchy([run], [[inputs.init_q(run, run.levels[0])]], rho0=1.0, K0=4.0)
     H.init_dt()
-    tiling = tune_all(H)
-    ms = time_fused(H, 50)
+    tiling = tune_all(H, pull=True)
+    ms = time_stepper(H, 50)
     plain = time_plain(H, 10)
     return _report("100x100 single grid, radial pulse, rho=1, K=4, MC, 50 steps", H, ms, plain,
-                   FP64_INSTR_UNIFORM, BYTES_UNIFORM, {"l2": "L2-resident (0.3 MB)", "tiling": tiling})
+                   FP64_INSTR_UNIFORM, BYTES_UNIFORM, {"l2": "L2-resident (0.3 MB)", "tiling": tiling,
+                                                       "path": "one launch per step (pulled ghosts)"})
 
 
 def config2():
@@ -217,13 +218,14 @@ def config3(nsteps=400, every=20):
     run, q, rho, K = _cellwise_single(256)
     H = Hierarchy([run], [[q]], [[rho]], [[K]])
     H.init_dt()
-    tiling = tune_all(H)
-    ms = time_fused(H, 40)
+    tiling = tune_all(H, pull=True)
+    ms = time_stepper(H, 40)
+    H.init_dt()
     fwd, bwd, ok = time_adjoint(H, [[q]], [[rho]], [[K]], nsteps, every)
     tf, tb, tok = time_adjoint(H, [[q]], [[rho]], [[K]], nsteps, None)
     return _report("256x256 heterogeneous medium, 400 steps, checkpoints every 20, J = sum p^2 over the "
                    "16x16 receiver", H, ms, None, FP64_INSTR_CELLWISE, BYTES_CELLWISE,
-                   {"tiling": tiling,
+                   {"tiling": tiling, "path": "one launch per step (pulled ghosts)",
                     "adjoint": {"forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
                                 "gradients_finite": ok,
                                 "note": "eager launches; backward = segment recompute + adjoint steps"},
