@@ -140,6 +140,11 @@ int claw_medium_aux(claw_ctx* ctx, int32_t level, const double* rho, const doubl
 int claw_fill_ghost(claw_ctx* ctx, int32_t level, double* q, const double* qc_old,
                     const double* qc_new, double tau, void* stream);
 
+/* Only the ghosts of claw_fill_ghost that are interpolated from the coarser level (nothing on
+ * level 0): what a level-step with CLAW_ADVANCE_PULL_GHOSTS still reads from q's ghost cells. */
+int claw_fill_ghost_interp(claw_ctx* ctx, int32_t level, double* q, const double* qc_old,
+                           const double* qc_new, double tau, void* stream);
+
 /* The same-level and physical-boundary ghosts (Sec. 2.2 items 1-2) of a one-plane pool such as
  * rho or K (box b at element coff[b]; no sign flips at walls).  Ghosts that would need the
  * coarser level are left as they are (coefficients of finer levels are given by the caller).

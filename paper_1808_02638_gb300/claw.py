@@ -67,6 +67,7 @@ _SIGNATURES = {
     "claw_fill_ghost": ([VP, I32, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_adjoint": ([VP, I32, VP, VP, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_coef": ([VP, I32, VP, VP], ctypes.c_int),
+    "claw_fill_ghost_interp": ([VP, I32, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_coef_adjoint": ([VP, I32, VP, VP], ctypes.c_int),
     "claw_cfl_max": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_cfl_max_state": ([VP, I32, VP, VP, VP], ctypes.c_int),
@@ -220,6 +221,11 @@ def claw_reflux_apply(ctx, fine_level, buf, dt, q_c_new, stream=None):
 def claw_medium_aux_adjoint(ctx, level, rho, K, g_aux, g_rho, g_K, stream=None):
     _check("claw_medium_aux_adjoint", load().claw_medium_aux_adjoint(
         ctx, level, _ptr(rho), _ptr(K), _ptr(g_aux), _ptr(g_rho), _ptr(g_K), _stream(stream)))
+
+
+def claw_fill_ghost_interp(ctx, level, q, qc_old=None, qc_new=None, tau=0.0, stream=None):
+    _check("claw_fill_ghost_interp", load().claw_fill_ghost_interp(ctx, level, _ptr(q), _ptr(qc_old), _ptr(qc_new),
+                                                                   DBL(tau), _stream(stream)))
 
 
 def claw_fill_ghost(ctx, level, q, qc_old=None, qc_new=None, tau=0.0, stream=None):

@@ -1088,6 +1088,19 @@ int claw_fill_ghost(claw_ctx* ctx, int32_t L, double* q, const double* qc_old, c
     return cuda_rc(e);
 }
 
+int claw_fill_ghost_interp(claw_ctx* ctx, int32_t L, double* q, const double* qc_old, const double* qc_new,
+                           double tau, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !q) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    const LevelDev& d = ctx->lev[L];
+    if (d.ninterp == 0) return CLAW_OK;
+    if (!qc_old || !qc_new || !(tau >= 0.0 && tau <= 1.0)) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    ctx->launches += 1;
+    return cuda_rc(launch_fill_interp(d.interps, d.ninterp, q, qc_old, qc_new, tau, (cudaStream_t)stream));
+}
+
 int claw_fill_ghost_coef(claw_ctx* ctx, int32_t L, double* a, void* stream)
 {
     if (!ctx || L < 0 || L >= CLAW_MAXLEV || !a) return CLAW_EINVAL;

@@ -146,6 +146,7 @@ class Hierarchy:
                               for L in range(1, self.nlev)]
         self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)
         self.fused = False       # one-level hierarchies: one launch per step (pulled ghosts, Eq. cfl on the device)
+        self.pull = True         # coarse steps pull same-level / boundary ghosts (fill only interpolated ones)
 
     def _layout(self, L):
         """(claw boxes, [(run, q base, coefficient base)], q size, coefficient size) of level L"""
@@ -242,12 +243,18 @@ class Hierarchy:
 
     def advance(self, L, cold=None, cnew=None, tau=0.0, stream=None):
         q = self.q[L][self.cur[L]]
-        claw.claw_fill_ghost(self.ctx, L, q, cold, cnew, tau, stream)
-        if self.reflux and L > 0:             # this substep's fine fluxes at level L's interface
-            claw.claw_reflux_fine(self.ctx, L, q, cold, self.dt, self.rbuf[L], stream)
-        if self.reflux and L + 1 < self.nlev:  # the coarse fluxes at the finer level's interface
-            claw.claw_reflux_coarse(self.ctx, L + 1, q, self.dt, self.rbuf[L + 1], stream)
-        self.step_level(L, stream)
+        if self.pull and not self.reflux and not self.patchwise:
+            # only the interpolated ghosts are filled; the step pulls the others from their sources
+            claw.claw_fill_ghost_interp(self.ctx, L, q, cold, cnew, tau, stream)
+            claw.claw_level_advance(self.ctx, L, q, self.q[L][1 - self.cur[L]], self.aux[L], self.dt, self.smax,
+                                    claw.CLAW_ADVANCE_PULL_GHOSTS, stream)
+        else:
+            claw.claw_fill_ghost(self.ctx, L, q, cold, cnew, tau, stream)
+            if self.reflux and L > 0:             # this substep's fine fluxes at level L's interface
+                claw.claw_reflux_fine(self.ctx, L, q, cold, self.dt, self.rbuf[L], stream)
+            if self.reflux and L + 1 < self.nlev:  # the coarse fluxes at the finer level's interface
+                claw.claw_reflux_coarse(self.ctx, L + 1, q, self.dt, self.rbuf[L + 1], stream)
+            self.step_level(L, stream)
         old, new = self.q[L][self.cur[L]], self.q[L][1 - self.cur[L]]
         if L + 1 < self.nlev:
             r = self.ratio(L + 1)
