@@ -297,7 +297,7 @@ constexpr int kRectRows = 32;          // copy rectangles are split into pieces 
 constexpr long long kBlockCells = 256;   // cells per block of the copy kernel (about): one batch per thread
 
 int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::vector<InterpCell>& cells,
-                       std::vector<int>& start, std::vector<int2>* ring = nullptr, bool* ring_ok = nullptr)
+                       std::vector<int>& start, std::vector<longlong2>* ring = nullptr, bool* ring_ok = nullptr)
 {
     if (ring_ok) *ring_ok = true;
     LevelDev& d = ctx->lev[L];
@@ -331,14 +331,13 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
                     e.soff = cell_off(d.boxes[src], si, sj);
                     ent.push_back(e);
                     if (ring) {   // ring order = this loop's order
-                        const long long rel = e.soff - d.boxes[src].qoff;
-                        if (rel >= (1LL << kRingOffBits) && ring_ok) *ring_ok = false;
-                        ring->push_back(make_int2(src, (int)(rel & ((1LL << kRingOffBits) - 1)) |
-                                                           (e.flags << kRingOffBits)));
+                        const long long pl = plane_of(d.boxes[src]);
+                        if (pl >= (1LL << kRingFlagShift) && ring_ok) *ring_ok = false;
+                        ring->push_back(make_longlong2(e.soff, pl | ((long long)e.flags << kRingFlagShift)));
                     }
                     continue;
                 }
-                if (ring) ring->push_back(make_int2(-1, 0));
+                if (ring) ring->push_back(make_longlong2(-1, 0));
                 // space-time interpolation from level L-1 at the fine cell (si, sj)
                 if (L == 0) return CLAW_EINVAL;
                 InterpCell c;
@@ -964,7 +963,7 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     std::vector<InterpCell> cells;
     std::vector<AvgRect> avg;
     std::vector<int> qstart;
-    std::vector<int2> ring;
+    std::vector<longlong2> ring;
     bool ring_ok = true;
     int rc = build_ghost_tables(ctx, L, rects, cells, qstart, &ring, &ring_ok);
     if (rc) return rc;

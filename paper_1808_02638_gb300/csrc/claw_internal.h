@@ -125,7 +125,7 @@ struct LevelDev {
     int* reflux_group = nullptr;  // [ngroups + 1]: records of coarse cell g are [group[g], group[g+1])
     int nreflux_groups = 0;
     FlagBox* flagboxes = nullptr; // the boxes as flag-grid writers (built on first use)
-    int2* ring = nullptr;         // ghost sources of every box's ring (pulled ghosts), see ring_index
+    longlong2* ring = nullptr;    // ghost sources of every box's ring (pulled ghosts), see ring_index
     long long* poff = nullptr;    // packed-interior offset of every box (3 nx ny doubles each)
     long long packed = 0;         // doubles of the packed interiors of the level
     bool ring_ok = false;
@@ -136,10 +136,11 @@ struct LevelDev {
 };
 
 // Ghost ring of a box: its (nx+4)(ny+4) - nx ny ghost cells in row order of the padded box.
-// Entry {source box, source cell | sign flags << 29}: the ghost takes the source cell of that box
-// (plane-0 element relative to its qoff), u negated if bit 0 of the flags, v if bit 1; a source
-// box of -1 marks a ghost interpolated from the coarser level (read from the pool itself).
-constexpr int kRingOffBits = 29;
+// Entry {source, plane | sign flags << 48}: the ghost takes the pool's plane-0 element `source`
+// and the elements one and two planes (`plane` elements) further, u negated if bit 0 of the
+// flags, v if bit 1; a source of -1 marks a ghost interpolated from the coarser level (read from
+// the pool itself).
+constexpr int kRingFlagShift = 48;
 __host__ __device__ inline int ring_index(int xp, int yp, int nx, int ny)   // -1: interior
 {
     const int W = nx + 4;
@@ -166,7 +167,7 @@ struct StepArgs {
     double rho0 = 1.0, K0 = 1.0;   // uniform medium
     double grav = 0.0;             // shallow water
     int swe = 0;                   // 1: the shallow water system (the conservation fix reads it)
-    const int2* ring = nullptr;    // not null: same-level and boundary ghosts are pulled from sources
+    const longlong2* ring = nullptr;   // not null: same-level and boundary ghosts are pulled from sources
                                    // (launch_step then picks the kernels that pull)
     // fused epilogue (0 = off)
     int dtupd = 0;                      // the last CTA applies Eq. cfl to dt and resets smax

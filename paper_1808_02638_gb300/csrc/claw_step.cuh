@@ -222,12 +222,11 @@ __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P
         }
         const int ri = ring_index(x0 + xs, y0 + ys, P.nx, P.ny);
         if (ri < 0) continue;
-        const int2 e = __ldg(&A.ring[P.ring + ri]);
+        const longlong2 e = __ldg(&A.ring[P.ring + ri]);
         if (e.x < 0) continue;
-        const PatchDev S = A.patches[e.x];
-        const long long sp = (long long)(S.nx + 4) * (S.ny + 4);
-        const double* src = A.qold + S.qoff + (e.y & ((1 << kRingOffBits) - 1));
-        const unsigned fl = (unsigned)e.y >> kRingOffBits;
+        const long long sp = e.y & ((1LL << kRingFlagShift) - 1);
+        const double* src = A.qold + e.x;
+        const unsigned fl = (unsigned)(e.y >> kRingFlagShift);
         // wall sign flips as sign-bit xors (integer pipe, not an FP64 negation)
         const unsigned long long sb = (unsigned long long)(fl & 1u) << 63;
         const unsigned long long sc = (unsigned long long)((fl >> 1) & 1u) << 63;
