@@ -59,9 +59,14 @@ def _events():
 
 def tune_all(H, pull=False):
     """autotuned tiling of every level (installed on H), keyed by level (pull: timed with the
-    ghosts taken from their source cells, as the one-level fused stepper runs)"""
+    ghosts taken from their source cells, as the one-level fused stepper runs); for the coarse
+    steps of a hierarchy, also whether each level pulls its copied ghosts or fills them first"""
     from . import tune
-    return {str(L): list(tune.tune_level(H, L, use_cache=False, pull=pull)[0]) for L in range(H.nlev)}
+    out = {str(L): list(tune.tune_level(H, L, use_cache=False, pull=pull)[0]) for L in range(H.nlev)}
+    if not pull:
+        for L in range(H.nlev):
+            out[str(L)].append("pull" if tune.choose_pull(H, L)[0] else "fill")
+    return out
 
 
 def time_fused(H, ncoarse, warm=2):
@@ -143,7 +148,7 @@ def config2():
     # the same hierarchy with the conservation fix of Sec. 2.3 (same tilings)
     R = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
     for L, t in tiling.items():
-        claw.claw_set_tiling(R.ctx, int(L), *t)
+        claw.claw_set_tiling(R.ctx, int(L), *t[:4])
     R.init_dt()
     ms_r = time_fused(R, 20)
     nrec = [claw.claw_reflux_count(R.ctx, L) for L in range(1, R.nlev)]
@@ -306,7 +311,7 @@ def swe2():
     plain = time_plain(H, 2)
     R = Hierarchy([run], [q0], system="shallow_water", grav=1.0, reflux=True)
     for L, t in tiling.items():
-        claw.claw_set_tiling(R.ctx, int(L), *t)
+        claw.claw_set_tiling(R.ctx, int(L), *t[:4])
     R.init_dt()
     ms_r = time_fused(R, 20)
     boxes = [len(l.boxes) for l in run.levels]

@@ -147,6 +147,7 @@ class Hierarchy:
         self.freeze_dt = False   # keep dt as set (no Eq. cfl update after a coarse step)
         self.fused = False       # one-level hierarchies: one launch per step (pulled ghosts, Eq. cfl on the device)
         self.pull = True         # coarse steps pull same-level / boundary ghosts (fill only interpolated ones)
+        self.pull_levels = [True] * self.nlev   # per level (the autotuner may prefer the copy launch)
 
     def _layout(self, L):
         """(claw boxes, [(run, q base, coefficient base)], q size, coefficient size) of level L"""
@@ -243,7 +244,7 @@ class Hierarchy:
 
     def advance(self, L, cold=None, cnew=None, tau=0.0, stream=None):
         q = self.q[L][self.cur[L]]
-        if self.pull and not self.reflux and not self.patchwise:
+        if self.pull and self.pull_levels[L] and not self.reflux and not self.patchwise:
             # only the interpolated ghosts are filled; the step pulls the others from their sources
             claw.claw_fill_ghost_interp(self.ctx, L, q, cold, cnew, tau, stream)
             claw.claw_level_advance(self.ctx, L, q, self.q[L][1 - self.cur[L]], self.aux[L], self.dt, self.smax,

@@ -104,5 +104,40 @@ def tune_level(H, L, use_cache=True, candidates=None, pull=False):
     return best, timings
 
 
+def choose_pull(H, L, reps=5):
+    """whether level L of H should pull its copied ghosts inside the step (one launch) or fill
+    them with the copy launch first: times both sequences with the installed tiling and records
+    the faster in H.pull_levels[L].  Small boxes put many ghosts in every tile's frame, where
+    the separate copy can win."""
+    src = H.q[L][H.cur[L]]
+    dst = torch.empty_like(src)
+    smax = torch.zeros_like(H.smax)
+    qc = H.q[L - 1][H.cur[L - 1]] if L else None
+    if float(H.dt.max()) <= 0.0:
+        H.init_dt()
+
+    def fill_step():
+        claw.claw_fill_ghost(H.ctx, L, src, qc, qc, 0.0)
+        claw.claw_level_step(H.ctx, L, src, dst, H.aux[L], H.dt, smax)
+
+    def pull_step():
+        claw.claw_fill_ghost_interp(H.ctx, L, src, qc, qc, 0.0)
+        claw.claw_level_advance(H.ctx, L, src, dst, H.aux[L], H.dt, smax, claw.CLAW_ADVANCE_PULL_GHOSTS)
+
+    times = {}
+    for name, fn in (("fill", fill_step), ("pull", pull_step)):
+        fn()
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / reps
+    H.pull_levels[L] = times["pull"] <= times["fill"]
+    return H.pull_levels[L], times
+
+
 def tune(H, use_cache=True):
     return [tune_level(H, L, use_cache) for L in range(H.nlev)]
