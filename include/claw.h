@@ -195,8 +195,8 @@ int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q
  *     instead of q_old's ghost cells, so those need no fill at all; ghosts interpolated from the
  *     coarser level are still read from q_old and must be filled (claw_fill_ghost).  The ghost
  *     cells of q_new are not written unless CLAW_ADVANCE_PUSH_GHOSTS is also given.
- * Errors as claw_level_step, CLAW_EINVAL for unknown flags (and for PULL_GHOSTS on a level whose
- * box planes exceed 2^29 elements). */
+ * Errors as claw_level_step, CLAW_EINVAL for unknown flags (and for PULL_GHOSTS on a level with
+ * more than 2^31 ghost cells). */
 #define CLAW_ADVANCE_PUSH_GHOSTS 1
 #define CLAW_ADVANCE_UPDATE_DT 2
 #define CLAW_ADVANCE_PULL_GHOSTS 4
