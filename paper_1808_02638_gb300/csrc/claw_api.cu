@@ -296,6 +296,21 @@ int make_interp(claw_ctx* ctx, int L, const claw_problem& pr, const Locator& cl,
 constexpr int kRectRows = 32;          // copy rectangles are split into pieces of at most this many rows
 constexpr long long kBlockCells = 256;   // cells per block of the copy kernel (about): one batch per thread
 
+// fn(lo, hi) over [0, n) in contiguous chunks on up to 16 host threads (ghost tables, regrid grids)
+template <typename F>
+void parallel_for(int n, F fn)
+{
+    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int nt = std::max(1, std::min(hw, n / 64));
+    if (nt <= 1) {
+        fn(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(fn, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
+    for (auto& x : th) x.join();
+}
+
 int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::vector<InterpCell>& cells,
                        std::vector<int>& start, std::vector<longlong2>* ring = nullptr, bool* ring_ok = nullptr)
 {
@@ -311,13 +326,21 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
         for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
             cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
 
-    for (int n = 0; n < d.nboxes; ++n) {
+    // per box, independently (threads): its copy rectangles, interpolated cells and ghost ring
+    struct BoxGhosts {
+        std::vector<CopyRect> rects;
+        std::vector<InterpCell> cells;
+        std::vector<longlong2> ring;
+        bool want_ring = false, ring_ok = true;
+        int rc = CLAW_OK;
+    };
+    std::vector<BoxGhosts> per(d.nboxes);
+    auto one_box = [&](int n, BoxGhosts& out) -> int {
         const claw_box& b = d.boxes[n];
         const claw_problem& pr = ctx->runs[b.run];
         const int NX = level_nx(pr, L), NY = level_ny(pr, L);
         const int W = b.nx + 4;
         std::vector<GhostEntry> ent;
-        if (ring) d.hpatches[n].ring = (long long)ring->size() < (1LL << 31) ? (int)ring->size() : -1;
         for (int gj = b.jlo - 2; gj < b.jlo + b.ny + 2; ++gj)
             for (int gi = b.ilo - 2; gi < b.ilo + b.nx + 2; ++gi) {
                 if (gi >= b.ilo && gi < b.ilo + b.nx && gj >= b.jlo && gj < b.jlo + b.ny) continue;
@@ -330,20 +353,20 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
                 if (src >= 0) {
                     e.soff = cell_off(d.boxes[src], si, sj);
                     ent.push_back(e);
-                    if (ring) {   // ring order = this loop's order
+                    if (out.want_ring) {   // ring order = this loop's order
                         const long long pl = plane_of(d.boxes[src]);
-                        if (pl >= (1LL << kRingFlagShift) && ring_ok) *ring_ok = false;
-                        ring->push_back(make_longlong2(e.soff, pl | ((long long)e.flags << kRingFlagShift)));
+                        if (pl >= (1LL << kRingFlagShift)) out.ring_ok = false;
+                        out.ring.push_back(make_longlong2(e.soff, pl | ((long long)e.flags << kRingFlagShift)));
                     }
                     continue;
                 }
-                if (ring) ring->push_back(make_longlong2(-1, 0));
+                if (out.want_ring) out.ring.push_back(make_longlong2(-1, 0));
                 // space-time interpolation from level L-1 at the fine cell (si, sj)
                 if (L == 0) return CLAW_EINVAL;
                 InterpCell c;
                 if (make_interp(ctx, L, pr, cloc[b.run], cell_off(b, gi, gj), plane_of(b), si, sj, fx | (fy << 1), c))
                     return CLAW_EINVAL;   // not properly nested
-                cells.push_back(c);
+                out.cells.push_back(c);
             }
         // row runs of copies (consecutive ghosts of a row with one source box, one sign and a
         // constant source step), then stacked into rectangles
@@ -396,7 +419,7 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
                 piece.h = std::min(kRectRows, o.h - k0);
                 piece.dst = c.dst + (long long)k0 * c.dpitch;
                 piece.src = c.src + (long long)k0 * c.sy;
-                rects.push_back(piece);
+                out.rects.push_back(piece);
             }
         };
         for (const RowRun& R : runs) {
@@ -431,6 +454,24 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
             }
         }
         for (const Open& o : open) emit(o);
+            return CLAW_OK;
+    };
+    parallel_for(d.nboxes, [&](int n0, int n1) {
+        for (int n = n0; n < n1; ++n) {
+            per[n].want_ring = ring != nullptr;
+            per[n].rc = one_box(n, per[n]);
+        }
+    });
+    for (int n = 0; n < d.nboxes; ++n) {
+        BoxGhosts& g = per[n];
+        if (g.rc) return g.rc;
+        rects.insert(rects.end(), g.rects.begin(), g.rects.end());
+        cells.insert(cells.end(), g.cells.begin(), g.cells.end());
+        if (ring) {
+            d.hpatches[n].ring = (long long)ring->size() < (1LL << 31) ? (int)ring->size() : -1;
+            ring->insert(ring->end(), g.ring.begin(), g.ring.end());
+            if (!g.ring_ok && ring_ok) *ring_ok = false;
+        }
     }
     // blocks of the copy kernel: consecutive rectangles up to about kBlockCells cells (and at
     // most 32 rectangles, the kernel's staging chunk)
@@ -687,21 +728,6 @@ std::pair<long long, int> inflection_cut(const std::vector<long long>& sig)
         }
     }
     return best;
-}
-
-// fn(lo, hi) over [0, n) in contiguous chunks on up to 16 host threads (grids of a regrid)
-template <typename F>
-void parallel_for(int n, F fn)
-{
-    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const int nt = std::max(1, std::min(hw, n / 64));
-    if (nt <= 1) {
-        fn(0, n);
-        return;
-    }
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(fn, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
-    for (auto& x : th) x.join();
 }
 
 // 2D prefix sum of a 0/1 grid: S(i, j) = sum over [0, i) x [0, j)
