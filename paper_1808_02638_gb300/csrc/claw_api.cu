@@ -731,14 +731,20 @@ std::pair<long long, int> inflection_cut(const std::vector<long long>& sig)
 }
 
 // 2D prefix sum of a 0/1 grid: S(i, j) = sum over [0, i) x [0, j)
+// (32-bit counts: grids below 2^31 cells; the table lives in a caller's buffer that is reused
+// from call to call, so that a regrid does not page in fresh memory for every grid)
 struct Prefix {
     int NX = 0, NY = 0;
-    std::vector<long long> P;
-    Prefix(const std::vector<unsigned char>& g, int nx, int ny, bool invert) : NX(nx), NY(ny), P((size_t)(nx + 1) * (ny + 1), 0)
+    std::vector<int>& P;
+    Prefix(const std::vector<unsigned char>& g, int nx, int ny, bool invert, std::vector<int>& buf)
+        : NX(nx), NY(ny), P(buf)
     {
+        P.resize((size_t)(nx + 1) * (ny + 1));
+        std::fill(P.begin(), P.begin() + (NX + 1), 0);   // row 0
         parallel_for(NY, [&](int j0, int j1) {   // prefix along each row
             for (int j = j0; j < j1; ++j) {
-                long long* row = &P[(size_t)(j + 1) * (NX + 1)];
+                int* row = &P[(size_t)(j + 1) * (NX + 1)];
+                row[0] = 0;
                 for (int i = 0; i < NX; ++i) row[i + 1] = row[i] + (((g[(size_t)j * NX + i] != 0) != invert) ? 1 : 0);
             }
         });
@@ -749,15 +755,16 @@ struct Prefix {
     }
     long long sum(int i0, int j0, int i1, int j1) const   // over [i0, i1) x [j0, j1)
     {
-        return P[(size_t)j1 * (NX + 1) + i1] - P[(size_t)j0 * (NX + 1) + i1] - P[(size_t)j1 * (NX + 1) + i0] +
-               P[(size_t)j0 * (NX + 1) + i0];
+        return (long long)P[(size_t)j1 * (NX + 1) + i1] - P[(size_t)j0 * (NX + 1) + i1] -
+               P[(size_t)j1 * (NX + 1) + i0] + P[(size_t)j0 * (NX + 1) + i0];
     }
 };
 
 std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int NY, double cutoff, int max_size,
                                 const std::vector<unsigned char>& allowed)
 {
-    const Prefix F(f, NX, NY, false), BAD(allowed, NX, NY, true);
+    static thread_local std::vector<int> bf, bb;
+    const Prefix F(f, NX, NY, false, bf), BAD(allowed, NX, NY, true, bb);
     std::vector<IBox> out, stack{IBox{0, 0, NX, NY}};
     while (!stack.empty()) {
         IBox b = stack.back();
@@ -1481,10 +1488,15 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     const claw_problem& p = ctx->runs[run];
     if (L + 1 >= p.nlev) return -CLAW_EINVAL;
     const int NX = level_nx(p, L), NY = level_ny(p, L), r = p.ratio[L + 1];
+    if ((long long)(NX + 1) * (NY + 1) >= (1LL << 31)) return -CLAW_EINVAL;
+    // scratch grids reused from call to call (no fresh pages per regrid)
+    static thread_local std::vector<unsigned char> fin, f, cov, allowed;
+    static thread_local std::vector<int> pfl, punc;
     // flags grown by `buffer` cells (square neighbourhood, clipped to the domain)
-    std::vector<unsigned char> fin(flags, flags + (size_t)NX * NY), f((size_t)NX * NY, 0);
+    fin.assign(flags, flags + (size_t)NX * NY);
+    f.resize((size_t)NX * NY);
     {
-        const Prefix FL(fin, NX, NY, false);
+        const Prefix FL(fin, NX, NY, false, pfl);
         parallel_for(NY, [&](int ja, int jb) {
             for (int j = ja; j < jb; ++j)
                 for (int i = 0; i < NX; ++i)
@@ -1493,15 +1505,15 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
         });
     }
     // keep cells `nest` cells inside the level's coverage (the domain outside counts as covered)
-    std::vector<unsigned char> cov((size_t)NX * NY, 0);
+    cov.assign((size_t)NX * NY, 0);
     for (const claw_box& b : ctx->lev[L].boxes)
         if (b.run == run)
             for (int j = b.jlo; j < b.jlo + b.ny; ++j)
                 for (int i = b.ilo; i < b.ilo + b.nx; ++i) cov[(size_t)j * NX + i] = 1;
     // uncovered cells of the square of radius `nest` around each cell, the square clipped to the
     // domain (the domain outside counts as covered)
-    const Prefix UNC(cov, NX, NY, true);
-    std::vector<unsigned char> allowed((size_t)NX * NY, 0);
+    const Prefix UNC(cov, NX, NY, true, punc);
+    allowed.resize((size_t)NX * NY);
     parallel_for(NY, [&](int ja, int jb) {
         for (int j = ja; j < jb; ++j)
             for (int i = 0; i < NX; ++i) {
