@@ -763,8 +763,8 @@ struct Prefix {
 std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int NY, double cutoff, int max_size,
                                 const std::vector<unsigned char>& allowed)
 {
-    static thread_local std::vector<int> bf, bb;
-    const Prefix F(f, NX, NY, false, bf), BAD(allowed, NX, NY, true, bb);
+    static thread_local std::vector<int> tl_bf, tl_bb;   // see claw_regrid_boxes
+    const Prefix F(f, NX, NY, false, tl_bf), BAD(allowed, NX, NY, true, tl_bb);
     std::vector<IBox> out, stack{IBox{0, 0, NX, NY}};
     while (!stack.empty()) {
         IBox b = stack.back();
@@ -1489,9 +1489,17 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     if (L + 1 >= p.nlev) return -CLAW_EINVAL;
     const int NX = level_nx(p, L), NY = level_ny(p, L), r = p.ratio[L + 1];
     if ((long long)(NX + 1) * (NY + 1) >= (1LL << 31)) return -CLAW_EINVAL;
-    // scratch grids reused from call to call (no fresh pages per regrid)
-    static thread_local std::vector<unsigned char> fin, f, cov, allowed;
-    static thread_local std::vector<int> pfl, punc;
+    // scratch grids reused from call to call (no fresh pages per regrid); named through local
+    // references, which the worker threads' lambdas capture (a thread_local named inside a
+    // lambda would be the worker's own, empty instance)
+    static thread_local std::vector<unsigned char> tl_fin, tl_f, tl_cov, tl_allowed;
+    static thread_local std::vector<int> tl_pfl, tl_punc;
+    std::vector<unsigned char>& fin = tl_fin;
+    std::vector<unsigned char>& f = tl_f;
+    std::vector<unsigned char>& cov = tl_cov;
+    std::vector<unsigned char>& allowed = tl_allowed;
+    std::vector<int>& pfl = tl_pfl;
+    std::vector<int>& punc = tl_punc;
     // flags grown by `buffer` cells (square neighbourhood, clipped to the domain)
     fin.assign(flags, flags + (size_t)NX * NY);
     f.resize((size_t)NX * NY);
