@@ -355,6 +355,50 @@ def test_host_resident_steps_equal_device_steps():
     assert torch.equal(out, A.pool(0).cpu()) and float(A.dt[0]) == float(B.dt[0])
 
 
+def test_pack_unpack_and_pieces_on_mixed_boxes():
+    # packed interiors of boxes of mixed sizes: pack then unpack restores the interiors and
+    # leaves ghost cells alone; stepping the level in pieces of boxes equals one launch
+    import torch
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    boxes = [(0, 0, 40, 24), (40, 0, 24, 24), (0, 24, 64, 40)]
+    run, q = single_grid(64, boxes=boxes, pulse=False, seed=41)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    H.init_dt()
+    n = H.packed_size()
+    assert n == 3 * (40 * 24 + 24 * 24 + 64 * 40)
+    packed = H.pack()
+    lev = run.levels[0]
+    off = 0
+    for nb, (i0, j0, nx, ny) in enumerate(boxes):
+        got = packed[off:off + 3 * nx * ny].view(3, ny, nx).cpu().numpy()
+        assert np.array_equal(got, H.interior(0, 0, nb))
+        off += 3 * nx * ny
+    pool = H.pool(0)
+    poisoned = torch.full_like(pool, float("nan"))
+    claw.claw_unpack_interiors(H.ctx, 0, 0, 3, packed, poisoned)
+    for nb in range(3):
+        assert np.array_equal(H.interior(0, 0, nb, pool=poisoned), H.interior(0, 0, nb))
+    assert torch.isnan(poisoned).any()   # ghost cells untouched
+    # pieces: boxes [0, 2) then [2, 3) against the whole level
+    claw.claw_fill_ghost(H.ctx, 0, pool)
+    whole, parts = torch.zeros_like(pool), torch.zeros_like(pool)
+    sm = torch.zeros_like(H.smax)
+    claw.claw_level_step(H.ctx, 0, pool, whole, None, H.dt, sm)
+    sm2 = torch.zeros_like(H.smax)
+    flags = claw.CLAW_ADVANCE_PULL_GHOSTS
+    claw.claw_level_advance_boxes(H.ctx, 0, 2, 3, pool, parts, None, H.dt, sm2, flags)
+    claw.claw_level_advance_boxes(H.ctx, 0, 0, 2, pool, parts, None, H.dt, sm2, flags)
+    torch.cuda.synchronize()
+    for nb in range(3):
+        assert np.array_equal(H.interior(0, 0, nb, pool=parts), H.interior(0, 0, nb, pool=whole))
+    assert float(sm2[0]) == float(sm[0])
+    with pytest.raises(claw.ClawError):
+        claw.claw_level_advance_boxes(H.ctx, 0, 2, 4, pool, parts, None, H.dt, sm2, flags)
+    with pytest.raises(claw.ClawError):
+        claw.claw_level_advance_boxes(H.ctx, 0, 0, 1, pool, parts, None, H.dt, sm2, claw.CLAW_ADVANCE_UPDATE_DT)
+
+
 def test_host_resident_packed_interiors():
     # the same loop with the host state in packed form (interiors only): unpacked into the pool
     # and packed out of it piece by piece; equal to the device steps bit for bit
