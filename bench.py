@@ -441,12 +441,12 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "2048x2048 cells on [-1,1]^2 as 4096 patches of 32x32 (+2 ghost layers), "
                                "radial pulse, rho=1, K=4, MC limiter, transverse corrections, same-level "
-                               "ghost copy, device CFL rule, per step one persistent level-step launch "
-                               "(Eq. cfl on its last CTA) and one ghost-copy launch under CUDA graphs",
+                               "ghosts, device CFL rule, per step one persistent level-step launch "
+                               "(ghosts pulled, Eq. cfl on its last CTA) replayed from a CUDA graph",
                    "global_batch": world * N_CELLS, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (254 MB of q pools per replica)"},
-        "step": "two CUDA-graph replays: the persistent level-step launch (all 4096 patches, Eq. cfl) and "
-                "the ghost copy of q^{n+1}",
+        "step": "one CUDA-graph replay of the persistent level-step launch (all 4096 patches, each tile's "
+                "ghosts pulled from their source cells, Eq. cfl on the last CTA)",
         "ghosts": "pulled by the step kernel from their source cells (no ghost-copy launch)",
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_ISSUE_PEAK_G,
                      "unit": "G FP64 instructions/s", "frac": achieved_gops / FP64_ISSUE_PEAK_G, "traffic": traffic,
