@@ -107,7 +107,10 @@ void claw_destroy(claw_ctx* ctx);
 /* Declares the boxes of level `level` of all runs (Sec. 2.2: disjoint boxes, nested in level
  * level-1, aligned to its cells).  Validates them on the host, builds and uploads the patch,
  * tile, ghost-source and averaging tables.  Levels must be set in increasing order; setting a
- * level again replaces its tables (and invalidates the tables of finer levels).
+ * level again replaces its tables (and invalidates the tables of finer levels).  A level's
+ * tables live in device memory that the context keeps from one setting of the level to the
+ * next (grown when too small) and overwrites after synchronising the device, so CUDA graphs
+ * captured before the call must not be replayed after it.
  * Errors: CLAW_EINVAL (overlap, out of domain, misaligned, improper nesting, odd nx/offset),
  * CLAW_ESTATE (level-1 not set), CLAW_ENOMEM, CLAW_ECUDA.  Synchronous. */
 int claw_set_level(claw_ctx* ctx, int32_t level, const claw_box* boxes, int32_t nboxes);
@@ -120,7 +123,9 @@ int claw_set_level(claw_ctx* ctx, int32_t level, const claw_box* boxes, int32_t 
  * the threads per CTA (0 = default).  Supported for acoustics: 32x32 with 256 or 512 threads,
  * 32x16 with 256, 16x16 with 128; claw_set_level installs 32x32, 256 threads.  Supported for
  * shallow water: 16x16 with 256 threads, 32x16 with 512; claw_set_level installs 16x16.
- * Staging 1 is installed when allowed.  Errors: CLAW_EINVAL. */
+ * Staging 1 is installed when allowed.  A new tile shape rewrites the level's tile lists in
+ * place (after synchronising the device): graphs captured before must not be replayed.
+ * Errors: CLAW_EINVAL, CLAW_ENOMEM, CLAW_ECUDA. */
 int claw_set_tiling(claw_ctx* ctx, int32_t level, int32_t tx, int32_t ty, int32_t staging,
                     int32_t threads);
 
@@ -149,7 +154,9 @@ int claw_fill_ghost_interp(claw_ctx* ctx, int32_t level, double* q, const double
  * rho or K (box b at element coff[b]; no sign flips at walls).  Ghosts that would need the
  * coarser level are left as they are (coefficients of finer levels are given by the caller).
  * The _adjoint call adds every such ghost's value into its source cell and zeroes the ghost:
- * the gradient with respect to the interior field from one with respect to the padded pool. */
+ * the gradient with respect to the interior field from one with respect to the padded pool.
+ * A context with a uniform medium builds these copy tables on the first call for a level
+ * (synchronously; CLAW_ESTATE if that first call is made while `stream` is being captured). */
 int claw_fill_ghost_coef(claw_ctx* ctx, int32_t level, double* a, void* stream);
 int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t level, double* g, void* stream);
 

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <new>
 #include <thread>
@@ -54,6 +55,7 @@ struct claw_ctx {
     unsigned long long stamp = 0;
     std::atomic<long long> launches{0};
     bool tma_ok[CLAW_MAXLEV] = {};
+    DevArena scratch;   // the transfer tables of a regrid
 };
 
 namespace {
@@ -139,50 +141,66 @@ long long cell_off(const claw_box& b, int i, int j)   // plane-0 element of leve
 }
 long long plane_of(const claw_box& b) { return (long long)(b.nx + 4) * (b.ny + 4); }
 
-template <class T>
-int upload(T** dst, const std::vector<T>& v)
-{
-    if (*dst) {
-        cudaFree(*dst);
+// The tables of one rebuild, packed into a host staging buffer (256-byte aligned pieces) and
+// copied into an arena in one call; each table pointer is set once the copy is done.
+struct ArenaPack {
+    std::vector<char> host;
+    std::vector<std::function<void(char*)>> place;
+    template <class T>
+    void add(T** dst, const std::vector<T>& v)
+    {
         *dst = nullptr;
+        if (v.empty()) return;
+        const size_t off = (host.size() + 255) / 256 * 256;
+        host.resize(off + v.size() * sizeof(T));
+        std::memcpy(host.data() + off, v.data(), v.size() * sizeof(T));
+        place.push_back([dst, off](char* base) { *dst = reinterpret_cast<T*>(base + off); });
     }
-    if (v.empty()) return CLAW_OK;
-    if (cudaMalloc((void**)dst, v.size() * sizeof(T)) != cudaSuccess) return CLAW_ENOMEM;
-    if (cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
-        return CLAW_ECUDA;
-    return CLAW_OK;
+    // The arena may still be read by kernels in flight from before the rebuild: the device is
+    // synchronised before it is overwritten.
+    int commit(DevArena& a)
+    {
+        if (host.empty()) return CLAW_OK;
+        if (a.dev && cudaDeviceSynchronize() != cudaSuccess) return CLAW_ECUDA;
+        if (host.size() > a.cap) {
+            cudaFree(a.dev);
+            a.dev = nullptr;
+            a.cap = 0;
+            const size_t want = host.size() + host.size() / 4;
+            if (cudaMalloc((void**)&a.dev, want) != cudaSuccess) return CLAW_ENOMEM;
+            a.cap = want;
+        }
+        if (cudaMemcpy(a.dev, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) return CLAW_ECUDA;
+        for (auto& f : place) f(a.dev);
+        return CLAW_OK;
+    }
+};
+
+void free_arena(DevArena& a)
+{
+    cudaFree(a.dev);
+    a.dev = nullptr;
+    a.cap = 0;
 }
 
+// Forgets a level's boxes and tables; the arenas stay allocated for the next rebuild
+// (claw_destroy frees them).
 void free_level(claw_ctx* ctx, int L)
 {
     LevelDev& d = ctx->lev[L];
-    cudaFree(d.patches);
-    cudaFree(d.tiles);
-    cudaFree(d.copies);
-    cudaFree(d.ccopies);
     d.ccopies = nullptr;
     d.nccopy = 0;
-    cudaFree(d.interps);
-    cudaFree(d.avgs);
-    cudaFree(d.reflux);
-    cudaFree(d.reflux_group);
-    cudaFree(d.flagboxes);
+    d.coef_built = false;
     d.flagboxes = nullptr;
-    cudaFree(d.ring);
     d.ring = nullptr;
-    cudaFree(d.poff);
     d.poff = nullptr;
     d.packed = 0;
     d.ring_ok = false;
     d.reflux = nullptr;
     d.reflux_group = nullptr;
     d.nreflux = d.nreflux_groups = 0;
-    cudaFree(d.copy_start);
-    cudaFree(d.ccopy_start);
     d.copy_start = d.ccopy_start = nullptr;
     d.ncopy_blocks = d.nccopy_blocks = 0;
-    cudaFree(ctx->ptiles[L]);
-    cudaFree(ctx->atiles[L]);
     ctx->atiles[L] = nullptr;
     ctx->natiles[L] = 0;
     for (auto& t : ctx->tmaps[L]) cudaFree(t.dev);
@@ -223,8 +241,8 @@ int build_tiles(claw_ctx* ctx, int L)
             }
     }
     start.push_back((int)t.size());
-    int rc = upload(&ctx->ptiles[L], t);
-    if (rc) return rc;
+    ArenaPack pack;
+    pack.add(&ctx->ptiles[L], t);
     ctx->ptile_start[L] = start;
     std::stable_sort(t.begin(), t.end(), [](const TileDev& a, const TileDev& b) {
         return (int)a.tx * a.ty > (int)b.tx * b.ty;
@@ -233,8 +251,7 @@ int build_tiles(claw_ctx* ctx, int L)
     d.ntiles = (int)t.size();
     for (auto& tm : ctx->tmaps[L]) cudaFree(tm.dev);
     ctx->tmaps[L].clear();
-    rc = upload(&d.tiles, t);
-    if (rc) return rc;
+    pack.add(&d.tiles, t);
     // adjoint tiles
     std::vector<TileDev> at;
     const int e = adjoint_tile();
@@ -253,7 +270,8 @@ int build_tiles(claw_ctx* ctx, int L)
             }
     }
     ctx->natiles[L] = (int)at.size();
-    return upload(&ctx->atiles[L], at);
+    pack.add(&ctx->atiles[L], at);
+    return pack.commit(d.tiletab);
 }
 
 struct GhostEntry {
@@ -462,17 +480,30 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
             per[n].rc = one_box(n, per[n]);
         }
     });
+    // concatenated in box order: sized first, then filled in parallel
+    std::vector<size_t> ro(d.nboxes + 1, 0), co(d.nboxes + 1, 0), go(d.nboxes + 1, 0);
     for (int n = 0; n < d.nboxes; ++n) {
-        BoxGhosts& g = per[n];
+        const BoxGhosts& g = per[n];
         if (g.rc) return g.rc;
-        rects.insert(rects.end(), g.rects.begin(), g.rects.end());
-        cells.insert(cells.end(), g.cells.begin(), g.cells.end());
+        ro[n + 1] = ro[n] + g.rects.size();
+        co[n + 1] = co[n] + g.cells.size();
+        go[n + 1] = go[n] + g.ring.size();
         if (ring) {
-            d.hpatches[n].ring = (long long)ring->size() < (1LL << 31) ? (int)ring->size() : -1;
-            ring->insert(ring->end(), g.ring.begin(), g.ring.end());
+            d.hpatches[n].ring = go[n] < (size_t)(1LL << 31) ? (int)go[n] : -1;
             if (!g.ring_ok && ring_ok) *ring_ok = false;
         }
     }
+    rects.resize(ro[d.nboxes]);
+    cells.resize(co[d.nboxes]);
+    if (ring) ring->resize(go[d.nboxes]);
+    parallel_for(d.nboxes, [&](int n0, int n1) {
+        for (int n = n0; n < n1; ++n) {
+            const BoxGhosts& g = per[n];
+            std::copy(g.rects.begin(), g.rects.end(), rects.begin() + ro[n]);
+            std::copy(g.cells.begin(), g.cells.end(), cells.begin() + co[n]);
+            if (ring) std::copy(g.ring.begin(), g.ring.end(), ring->begin() + go[n]);
+        }
+    });
     // blocks of the copy kernel: consecutive rectangles up to about kBlockCells cells (and at
     // most 32 rectangles, the kernel's staging chunk)
     start.assign(1, 0);
@@ -736,7 +767,8 @@ std::pair<long long, int> inflection_cut(const std::vector<long long>& sig)
 struct Prefix {
     int NX = 0, NY = 0;
     std::vector<int>& P;
-    Prefix(const std::vector<unsigned char>& g, int nx, int ny, bool invert, std::vector<int>& buf)
+    // g: nx x ny cells in rows of `pitch` bytes
+    Prefix(const unsigned char* g, size_t pitch, int nx, int ny, bool invert, std::vector<int>& buf)
         : NX(nx), NY(ny), P(buf)
     {
         P.resize((size_t)(nx + 1) * (ny + 1));
@@ -744,8 +776,9 @@ struct Prefix {
         parallel_for(NY, [&](int j0, int j1) {   // prefix along each row
             for (int j = j0; j < j1; ++j) {
                 int* row = &P[(size_t)(j + 1) * (NX + 1)];
+                const unsigned char* src = g + (size_t)j * pitch;
                 row[0] = 0;
-                for (int i = 0; i < NX; ++i) row[i + 1] = row[i] + (((g[(size_t)j * NX + i] != 0) != invert) ? 1 : 0);
+                for (int i = 0; i < NX; ++i) row[i + 1] = row[i] + (((src[i] != 0) != invert) ? 1 : 0);
             }
         });
         parallel_for(NX + 1, [&](int i0, int i1) {   // then down each column
@@ -764,7 +797,7 @@ std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int
                                 const std::vector<unsigned char>& allowed)
 {
     static thread_local std::vector<int> tl_bf, tl_bb;   // see claw_regrid_boxes
-    const Prefix F(f, NX, NY, false, tl_bf), BAD(allowed, NX, NY, true, tl_bb);
+    const Prefix F(f.data(), NX, NX, NY, false, tl_bf), BAD(allowed.data(), NX, NX, NY, true, tl_bb);
     std::vector<IBox> out, stack{IBox{0, 0, NX, NY}};
     while (!stack.empty()) {
         IBox b = stack.back();
@@ -833,6 +866,40 @@ long long flag_grid_offset(const claw_ctx* ctx, int L, int run)
     for (int r = 0; r < run; ++r)
         if (L < ctx->runs[r].nlev) off += (long long)level_nx(ctx->runs[r], L) * level_ny(ctx->runs[r], L);
     return off;
+}
+
+// ghost copies of one-plane coefficient pools: the same copies with offsets from coff and no
+// wall sign flips
+int build_coef_tables(claw_ctx* ctx, int L)
+{
+    LevelDev& d = ctx->lev[L];
+    std::vector<CopyRect> crects;
+    std::vector<InterpCell> unused;
+    std::vector<int> cstart;
+    const std::vector<claw_box> saved = d.boxes;
+    for (auto& b : d.boxes) b.qoff = b.coff;
+    int rc = build_ghost_tables(ctx, L, crects, unused, cstart);
+    d.boxes = saved;
+    if (rc) return rc;
+    for (auto& r : crects) r.flags = 0;
+    ArenaPack pack;
+    pack.add(&d.ccopy_start, cstart);
+    pack.add(&d.ccopies, crects);
+    if ((rc = pack.commit(d.coeftab))) return rc;
+    d.nccopy_blocks = cstart.empty() ? 0 : (int)cstart.size() - 1;
+    d.nccopy = (int)crects.size();
+    d.coef_built = true;
+    return CLAW_OK;
+}
+
+// coefficient tables of a uniform-medium level on first use (outside stream capture)
+int ensure_coef_tables(claw_ctx* ctx, int L, void* stream)
+{
+    if (ctx->lev[L].coef_built) return CLAW_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return CLAW_ESTATE;
+    return build_coef_tables(ctx, L);
 }
 
 }  // namespace
@@ -908,7 +975,13 @@ void claw_destroy(claw_ctx* ctx)
     {
         DevGuard g(ctx->device);
         cudaDeviceSynchronize();
-        for (int L = 0; L < CLAW_MAXLEV; ++L) free_level(ctx, L);
+        for (int L = 0; L < CLAW_MAXLEV; ++L) {
+            free_level(ctx, L);
+            free_arena(ctx->lev[L].tables);
+            free_arena(ctx->lev[L].tiletab);
+            free_arena(ctx->lev[L].coeftab);
+        }
+        free_arena(ctx->scratch);
         cudaFree(ctx->err);
         cudaFree(ctx->done);
         cudaFree(ctx->minh);
@@ -1003,8 +1076,9 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     d.ring_ok = ring_ok && (long long)ring.size() < (1LL << 31);
     for (auto& P : d.hpatches)
         if (!d.ring_ok) P.ring = -1;
-    if (d.ring_ok && (rc = upload(&d.ring, ring))) return rc;
-    if ((rc = upload(&d.copy_start, qstart))) return rc;
+    ArenaPack pack;
+    if (d.ring_ok) pack.add(&d.ring, ring);
+    pack.add(&d.copy_start, qstart);
     d.ncopy_blocks = qstart.empty() ? 0 : (int)qstart.size() - 1;
     d.max_rows = 0;
     for (const claw_box& b : d.boxes) d.max_rows = std::max(d.max_rows, b.ny + 4);
@@ -1016,39 +1090,43 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
             o += 3LL * d.boxes[n].nx * d.boxes[n].ny;
         }
         d.packed = o;
-        if ((rc = upload(&d.poff, poff))) return rc;
+        pack.add(&d.poff, poff);
+    }
+    {   // the boxes as writers into the level's flag grid
+        std::vector<FlagBox> fb(d.nboxes);
+        for (int n = 0; n < d.nboxes; ++n) {
+            const claw_box& b = d.boxes[n];
+            const int NX = level_nx(ctx->runs[b.run], L);
+            fb[n].qoff = b.qoff;
+            fb[n].goff = flag_grid_offset(ctx, L, b.run) + (long long)b.jlo * NX + b.ilo;
+            fb[n].nx = b.nx;
+            fb[n].ny = b.ny;
+            fb[n].pitch = NX;
+            fb[n].pad = 0;
+        }
+        pack.add(&d.flagboxes, fb);
     }
     if (L > 0) build_avg_tables(ctx, L, avg);
     if (L > 0) {
         std::vector<RefluxRec> rrec;
         std::vector<int> rgroup;
         build_reflux_tables(ctx, L, rrec, rgroup);
-        if ((rc = upload(&d.reflux, rrec)) || (rc = upload(&d.reflux_group, rgroup))) return rc;
+        pack.add(&d.reflux, rrec);
+        pack.add(&d.reflux_group, rgroup);
         d.nreflux = (int)rrec.size();
         d.nreflux_groups = rgroup.empty() ? 0 : (int)rgroup.size() - 1;
     }
-    // the same copies for one-plane pools: offsets from coff, no wall sign flips
-    std::vector<CopyRect> crects;
-    {
-        std::vector<claw_box> saved = d.boxes;
-        for (auto& b : d.boxes) b.qoff = b.coff;
-        std::vector<InterpCell> unused;
-        std::vector<int> cstart;
-        rc = build_ghost_tables(ctx, L, crects, unused, cstart);
-        if (!rc) rc = upload(&d.ccopy_start, cstart);
-        d.nccopy_blocks = cstart.empty() ? 0 : (int)cstart.size() - 1;
-        d.boxes = saved;
-        if (rc) return rc;
-        for (auto& r : crects) r.flags = 0;
-    }
-    if ((rc = upload(&d.ccopies, crects))) return rc;
-    d.nccopy = (int)crects.size();
-    if ((rc = upload(&d.patches, d.hpatches)) || (rc = upload(&d.copies, rects)) ||
-        (rc = upload(&d.interps, cells)) || (rc = upload(&d.avgs, avg)))
-        return rc;
+    pack.add(&d.patches, d.hpatches);
+    pack.add(&d.copies, rects);
+    pack.add(&d.interps, cells);
+    pack.add(&d.avgs, avg);
+    if ((rc = pack.commit(d.tables))) return rc;
     d.ncopy = (int)rects.size();
     d.ninterp = (int)cells.size();
     d.navg = (int)avg.size();
+    // a cell-wise medium fills its coefficient pools' ghosts: those tables are built now, a
+    // uniform medium builds them on first use
+    if (ctx->medium && (rc = build_coef_tables(ctx, L))) return rc;
     ctx->set[L] = true;
     rc = build_tiles(ctx, L);
     if (rc) {
@@ -1138,6 +1216,8 @@ int claw_fill_ghost_coef(claw_ctx* ctx, int32_t L, double* a, void* stream)
     if (!ctx || L < 0 || L >= CLAW_MAXLEV || !a) return CLAW_EINVAL;
     if (!ctx->set[L]) return CLAW_ESTATE;
     DevGuard g(ctx->device);
+    int rc = ensure_coef_tables(ctx, L, stream);
+    if (rc) return rc;
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nccopy > 0;
     return cuda_rc(d.nccopy ? launch_fill_copy(d.ccopies, d.ccopy_start, d.nccopy_blocks, a, (cudaStream_t)stream, 1)
@@ -1149,6 +1229,8 @@ int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t L, double* g, void* stre
     if (!ctx || L < 0 || L >= CLAW_MAXLEV || !g) return CLAW_EINVAL;
     if (!ctx->set[L]) return CLAW_ESTATE;
     DevGuard gd(ctx->device);
+    int rc = ensure_coef_tables(ctx, L, stream);
+    if (rc) return rc;
     const LevelDev& d = ctx->lev[L];
     ctx->launches += d.nccopy > 0;
     return cuda_rc(d.nccopy ? launch_fill_copy_adjoint(d.ccopies, d.ccopy_start, d.nccopy_blocks, g, (cudaStream_t)stream, 1)
@@ -1459,21 +1541,6 @@ int claw_flag_cells(claw_ctx* ctx, int32_t L, const double* q, double tol, uint8
     DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
     if (d.nboxes == 0) return CLAW_OK;
-    if (!d.flagboxes) {
-        std::vector<FlagBox> fb(d.nboxes);
-        for (int n = 0; n < d.nboxes; ++n) {
-            const claw_box& b = d.boxes[n];
-            const int NX = level_nx(ctx->runs[b.run], L);
-            fb[n].qoff = b.qoff;
-            fb[n].goff = flag_grid_offset(ctx, L, b.run) + (long long)b.jlo * NX + b.ilo;
-            fb[n].nx = b.nx;
-            fb[n].ny = b.ny;
-            fb[n].pitch = NX;
-            fb[n].pad = 0;
-        }
-        int rc = upload(&d.flagboxes, fb);
-        if (rc) return rc;
-    }
     ctx->launches += 1;
     return cuda_rc(launch_flags(d.flagboxes, d.nboxes, d.max_rows, q, tol, flags, (cudaStream_t)stream));
 }
@@ -1492,46 +1559,86 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     // scratch grids reused from call to call (no fresh pages per regrid); named through local
     // references, which the worker threads' lambdas capture (a thread_local named inside a
     // lambda would be the worker's own, empty instance)
-    static thread_local std::vector<unsigned char> tl_fin, tl_f, tl_cov, tl_allowed;
-    static thread_local std::vector<int> tl_pfl, tl_punc;
-    std::vector<unsigned char>& fin = tl_fin;
+    static thread_local std::vector<unsigned char> tl_f, tl_cov, tl_allowed;
+    static thread_local std::vector<int> tl_pfl, tl_punc, tl_rlo, tl_rhi;
     std::vector<unsigned char>& f = tl_f;
     std::vector<unsigned char>& cov = tl_cov;
     std::vector<unsigned char>& allowed = tl_allowed;
     std::vector<int>& pfl = tl_pfl;
     std::vector<int>& punc = tl_punc;
-    // flags grown by `buffer` cells (square neighbourhood, clipped to the domain)
-    fin.assign(flags, flags + (size_t)NX * NY);
-    f.resize((size_t)NX * NY);
+    std::vector<int>& rlo = tl_rlo;
+    std::vector<int>& rhi = tl_rhi;
+    // bounding box of the flags: the grids below cover only the window of it grown by `buffer`
+    // (clustering starts by trimming to the flags' bounding box, so the boxes are the same as
+    // over the whole level)
+    rlo.assign(NY, NX);
+    rhi.assign(NY, -1);
+    parallel_for(NY, [&](int ja, int jb) {
+        for (int j = ja; j < jb; ++j) {
+            const uint8_t* row = flags + (size_t)j * NX;
+            int lo = 0;
+            while (lo < NX && !row[lo]) ++lo;
+            if (lo == NX) continue;
+            int hi = NX - 1;
+            while (!row[hi]) --hi;
+            rlo[j] = lo;
+            rhi[j] = hi;
+        }
+    });
+    int bi0 = NX, bi1 = -1, bj0 = -1, bj1 = -1;
+    for (int j = 0; j < NY; ++j)
+        if (rhi[j] >= 0) {
+            bi0 = std::min(bi0, rlo[j]);
+            bi1 = std::max(bi1, rhi[j]);
+            if (bj0 < 0) bj0 = j;
+            bj1 = j;
+        }
+    if (bi1 < 0) return 0;
+    const int wi0 = std::max(0, bi0 - buffer), wi1 = std::min(NX, bi1 + 1 + buffer);
+    const int wj0 = std::max(0, bj0 - buffer), wj1 = std::min(NY, bj1 + 1 + buffer);
+    const int WX = wi1 - wi0, WY = wj1 - wj0;
+    // flags grown by `buffer` cells (square neighbourhood, clipped to the domain; no flag lies
+    // outside the window)
+    f.resize((size_t)WX * WY);
     {
-        const Prefix FL(fin, NX, NY, false, pfl);
-        parallel_for(NY, [&](int ja, int jb) {
+        const Prefix FL(flags + (size_t)wj0 * NX + wi0, NX, WX, WY, false, pfl);
+        parallel_for(WY, [&](int ja, int jb) {
             for (int j = ja; j < jb; ++j)
-                for (int i = 0; i < NX; ++i)
-                    f[(size_t)j * NX + i] = FL.sum(std::max(0, i - buffer), std::max(0, j - buffer),
-                                                  std::min(NX, i + buffer + 1), std::min(NY, j + buffer + 1)) > 0;
+                for (int i = 0; i < WX; ++i)
+                    f[(size_t)j * WX + i] = FL.sum(std::max(0, i - buffer), std::max(0, j - buffer),
+                                                   std::min(WX, i + buffer + 1), std::min(WY, j + buffer + 1)) > 0;
         });
     }
-    // keep cells `nest` cells inside the level's coverage (the domain outside counts as covered)
-    cov.assign((size_t)NX * NY, 0);
-    for (const claw_box& b : ctx->lev[L].boxes)
-        if (b.run == run)
-            for (int j = b.jlo; j < b.jlo + b.ny; ++j)
-                for (int i = b.ilo; i < b.ilo + b.nx; ++i) cov[(size_t)j * NX + i] = 1;
-    // uncovered cells of the square of radius `nest` around each cell, the square clipped to the
-    // domain (the domain outside counts as covered)
-    const Prefix UNC(cov, NX, NY, true, punc);
-    allowed.resize((size_t)NX * NY);
-    parallel_for(NY, [&](int ja, int jb) {
+    // keep cells `nest` cells inside the level's coverage: uncovered cells of the square of
+    // radius `nest` around each cell, the square clipped to the domain (the domain outside
+    // counts as covered); the coverage grid spans the window grown by `nest`
+    const int ci0 = std::max(0, wi0 - nest), ci1 = std::min(NX, wi1 + nest);
+    const int cj0 = std::max(0, wj0 - nest), cj1 = std::min(NY, wj1 + nest);
+    const int CX = ci1 - ci0, CY = cj1 - cj0;
+    cov.assign((size_t)CX * CY, 0);
+    for (const claw_box& b : ctx->lev[L].boxes) {
+        if (b.run != run) continue;
+        const int x0 = std::max(ci0, b.ilo), x1 = std::min(ci1, b.ilo + b.nx);
+        const int y0 = std::max(cj0, b.jlo), y1 = std::min(cj1, b.jlo + b.ny);
+        for (int j = y0; j < y1; ++j) std::memset(&cov[(size_t)(j - cj0) * CX + (x0 - ci0)], 1, std::max(0, x1 - x0));
+    }
+    const Prefix UNC(cov.data(), CX, CX, CY, true, punc);
+    allowed.resize((size_t)WX * WY);
+    parallel_for(WY, [&](int ja, int jb) {
         for (int j = ja; j < jb; ++j)
-            for (int i = 0; i < NX; ++i) {
-                const bool ok = UNC.sum(std::max(0, i - nest), std::max(0, j - nest), std::min(NX, i + nest + 1),
-                                        std::min(NY, j + nest + 1)) == 0;
-                allowed[(size_t)j * NX + i] = ok;
-                if (!ok) f[(size_t)j * NX + i] = 0;
+            for (int i = 0; i < WX; ++i) {
+                const int gi = wi0 + i, gj = wj0 + j;
+                const bool ok = UNC.sum(std::max(0, gi - nest) - ci0, std::max(0, gj - nest) - cj0,
+                                        std::min(NX, gi + nest + 1) - ci0, std::min(NY, gj + nest + 1) - cj0) == 0;
+                allowed[(size_t)j * WX + i] = ok;
+                if (!ok) f[(size_t)j * WX + i] = 0;
             }
     });
-    const std::vector<IBox> out = cluster_flags(f, NX, NY, cutoff, std::max(1, max_size / r), allowed);
+    std::vector<IBox> out = cluster_flags(f, WX, WY, cutoff, std::max(1, max_size / r), allowed);
+    for (IBox& b : out) {
+        b.i0 += wi0;
+        b.j0 += wj0;
+    }
     if ((long long)out.size() > max_boxes) return -CLAW_ENOMEM;
     for (size_t k = 0; k < out.size(); ++k) {
         boxes[4 * k] = out[k].i0 * r;
@@ -1563,11 +1670,19 @@ int claw_regrid_transfer(claw_ctx* ctx, int32_t L, const claw_box* old_boxes, in
     }
     for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
         cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
-    std::vector<RectCopy> copies;
-    std::vector<InterpRun> runs;
     const int r = d.ratio;
-    std::vector<unsigned char> mask;
-    for (const claw_box& b : d.boxes) {
+    // per new box, independently (threads): rectangles copied from old boxes, and row runs
+    // interpolated from the coarse level where no old box covers it
+    struct BoxTransfer {
+        std::vector<RectCopy> copies;
+        std::vector<InterpRun> runs;
+        int rc = CLAW_OK;
+    };
+    std::vector<BoxTransfer> per(d.nboxes);
+    auto one_box = [&](const claw_box& b, BoxTransfer& out) -> int {
+        std::vector<RectCopy>& copies = out.copies;
+        std::vector<InterpRun>& runs = out.runs;
+        std::vector<unsigned char> mask;
         // old boxes overlapping b: copied rectangles
         mask.assign((size_t)b.nx * b.ny, 0);
         std::vector<int> seen;
@@ -1619,21 +1734,32 @@ int claw_regrid_transfer(claw_ctx* ctx, int32_t L, const claw_box* old_boxes, in
                 i = e;
             }
         }
+        return CLAW_OK;
+    };
+    parallel_for(d.nboxes, [&](int n0, int n1) {
+        for (int n = n0; n < n1; ++n) per[n].rc = one_box(d.boxes[n], per[n]);
+    });
+    std::vector<RectCopy> copies;
+    std::vector<InterpRun> runs;
+    for (const BoxTransfer& t : per) {
+        if (t.rc) return t.rc;
+        copies.insert(copies.end(), t.copies.begin(), t.copies.end());
+        runs.insert(runs.end(), t.runs.begin(), t.runs.end());
     }
     RectCopy* dc = nullptr;
     InterpRun* di = nullptr;
-    int rc = upload(&dc, copies);
-    if (!rc) rc = upload(&di, runs);
+    ArenaPack pack;
+    pack.add(&dc, copies);
+    pack.add(&di, runs);
+    int rc = pack.commit(ctx->scratch);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (!rc) {
         e = launch_rect_copy(dc, (int)copies.size(), q_old, q_new, s);
         if (e == cudaSuccess) e = launch_interp_runs(di, (int)runs.size(), q_coarse, q_new, s);
         ctx->launches += (copies.size() > 0) + (runs.size() > 0);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the tables are freed below
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the scratch tables are reused by the next call
     }
-    cudaFree(dc);
-    cudaFree(di);
     return rc ? rc : cuda_rc(e);
 }
 

@@ -99,6 +99,14 @@ struct AvgRect {
 };
 
 // Per (level) device tables.
+// Device tables kept in one allocation that is reused (and grown when too small) from one
+// rebuild of a level to the next, so that a rebuild costs one host-to-device copy instead of
+// a cudaMalloc, a copy and a cudaFree per table.
+struct DevArena {
+    char* dev = nullptr;
+    size_t cap = 0;
+};
+
 struct LevelDev {
     int nboxes = 0;
     int ntiles = 0;
@@ -129,6 +137,10 @@ struct LevelDev {
     long long* poff = nullptr;    // packed-interior offset of every box (3 nx ny doubles each)
     long long packed = 0;         // doubles of the packed interiors of the level
     bool ring_ok = false;
+    bool coef_built = false;      // ccopies / ccopy_start built for the current boxes
+    DevArena tables;              // patches, copies, interps, avgs, reflux, ring, poff, copy_start
+    DevArena tiletab;             // the tile lists (rebuilt with the tiling)
+    DevArena coeftab;             // ccopies, ccopy_start
     // host copies
     std::vector<claw_box> boxes;
     std::vector<PatchDev> hpatches;

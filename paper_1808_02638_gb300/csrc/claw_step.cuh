@@ -40,7 +40,8 @@ namespace claw {
 // subtracts 1 in the exponent field.  MC keeps one FP64 add (|a| + |b|), minmod and
 // superbee none.  The exponent shifts are exact for magnitudes >= 2^-1021; below that the
 // result (itself below 2^-1020 in magnitude) may differ from the IEEE evaluation of the same
-// formula by less than 2^-1020.  van Leer needs a division and stays in FP64.
+// formula by less than 2^-1020.  van Leer needs a quotient: one correctly rounded reciprocal
+// and two products instead of a division (within two ulps of 2ab / (a + b)).
 namespace lim_bits {
 constexpr long long MAG = 0x7fffffffffffffffLL;
 constexpr long long SIGN = (long long)0x8000000000000000ULL;
@@ -80,9 +81,13 @@ template <> struct Lim<CLAW_LIM_SUPERBEE> {   // max(0, min(1, 2 theta), min(2, 
 };
 template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|): 2ab / (a + b)
     static __device__ __forceinline__ double f(double a, double b)
-    {
-        if (!(a * b > 0.0)) return 0.0;
-        return (2.0 * a * b) / (a + b);
+    {   // a (b r) with r = 1 / ((a + b) / 2); |b r| <= 2 as a and b share their sign
+        using namespace lim_bits;
+        const long long ia = bits(a), ib = bits(b);
+        const long long hs = (bits(a + b) & MAG) - ONE_EXP;   // |a + b| / 2, exact above 2^-1021
+        // below that the result is under 2^-1020 in magnitude: 0 (r would overflow)
+        if (!same_sign_nonzero(ia, ib, ia & MAG, ib & MAG) || hs < ONE_EXP) return 0.0;
+        return a * (b * __drcp_rn(val(hs | (ia & SIGN))));
     }
 };
 template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta))

@@ -323,13 +323,18 @@ def swe2():
                                "status": claw.strerror(R.sync_status())}})
 
 
-def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=0.002, max_size=260):
+def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=0.002, max_size=260,
+       reflux=True, per_patch=False):
     """Analog of the paper's benchmark (Sec. 4.1-4.2): radial pulse in a uniform medium, outflow
     (extrapolation) boundaries, van Leer, 3 levels of ratio 2 over a 1000^2 base tiled in 4 x 4
     patches of 250^2, patches of at most 260^2 generated by regridding (tol on neighbour
-    differences, buffer = regrid interval, cutoff 0.7, every 8 coarse steps); the fine levels are
-    built at t = 0 by regridding and set from the initial condition.  Times whole coarse steps
-    (eager launches: the hierarchy changes every regrid) including the regrids."""
+    differences, buffer = regrid interval, cutoff 0.7, every 8 coarse steps), the conservation
+    fix on; the fine levels are built at t = 0 by regridding and set from the initial condition.
+    Times whole coarse steps (eager launches: the hierarchy changes every regrid) including the
+    regrids, and splits the time into the sections of the paper's Fig. 4: advancing the solution
+    (with the conservation fix's flux records), ghost fill, regridding, updating (averaging and
+    the fix's corrections) and the rest.  per_patch: one step launch per patch instead of the
+    batched launch (the paper's launch pattern)."""
     import time
     run = inputs.Run(*inputs.PULSE_DOMAIN, limiter=3)
     d0 = 2.0 / base
@@ -340,7 +345,8 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
         n = base * ratio ** L
         run.levels.append(inputs.Level(n, n, 2.0 / n, 2.0 / n, np.zeros((0, 4), dtype=np.int32), ratio))
     q0 = [inputs.init_q(run, lev) for lev in run.levels]
-    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=reflux)
+    H.patchwise = bool(per_patch)
     params = dict(tol=tol, buffer=regrid_every, cutoff=cutoff, max_size=max_size, nest=2)
     for _ in range(nlev - 1):       # refine level by level at t = 0
         H.regrid(**params)
@@ -351,11 +357,14 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
         t[:a.size] = torch.from_numpy(a).to(t.device)
     H.init_dt()
     torch.cuda.synchronize()
+    H.sections = []
     cells = 0
+    patches = 0
     regrid_s = 0.0
     t0 = time.perf_counter()
     for k in range(ncoarse):
         cells += cell_updates_per_coarse_step(H)
+        patches += sum(len(lev.boxes) for lev in run.levels)
         H.coarse_step()
         if (k + 1) % regrid_every == 0:
             torch.cuda.synchronize()
@@ -365,21 +374,56 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
             regrid_s += time.perf_counter() - r0
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    sec = H.section_ms()
+    H.sections = None
+    sections = {"advance": sec.get("advance", 0.0) / 1e3, "ghost_fill": sec.get("fill", 0.0) / 1e3,
+                "regrid": regrid_s, "updating": sec.get("update", 0.0) / 1e3}
+    sections["other"] = wall - sum(sections.values())
+    sections["total"] = wall
     boxes = [len(lev.boxes) for lev in run.levels]
     ncells = [int(lev.ncells) for lev in run.levels]
+    status = claw.strerror(H.sync_status())
+    H.close()
     return {"workload": f"{base}^2 base, {nlev} levels of ratio {ratio}, patches <= {max_size}^2 by regridding "
                         f"(tol {tol}, cutoff {cutoff}, every {regrid_every} coarse steps), van Leer, radial pulse, "
-                        f"{ncoarse} coarse steps",
+                        f"conservation fix {'on' if reflux else 'off'}, {ncoarse} coarse steps, "
+                        f"{'one launch per patch' if per_patch else 'batched level-step launches'}",
             "coarse_steps": ncoarse, "simulated_time": float(ncoarse) * float(H.dt[0]),
             "cell_updates": cells, "wall_s": wall, "cell_updates_per_s": cells / wall,
+            "mean_patches_per_coarse_step": patches / ncoarse,
             "regrid_s": regrid_s, "regrids": ncoarse // regrid_every,
+            "sections_s": sections,
             "final_boxes_per_level": boxes, "final_cells_per_level": ncells,
-            "status": claw.strerror(H.sync_status()),
-            "note": "eager launches (the hierarchy changes at every regrid); wall clock includes the regrids"}
+            "status": status,
+            "note": "eager launches (the hierarchy changes at every regrid); wall clock includes the regrids; "
+                    "advance, ghost fill and updating are CUDA-event spans, regrid is host wall time with "
+                    "synchronisation, other = total - the rest"}
+
+
+def e3(ncoarse=200, cutoffs=(0.5, 0.7, 0.9), intervals=(2, 8, 16), paths=("batched", "per_patch")):
+    """Analog of the paper's parameter study (Sec. 4.3): the benchmark analog for every cutoff x
+    regrid interval, with the batched level-step launch and with one launch per patch.  Per
+    combination: cells advanced, mean patches over all levels per coarse step, and the time of
+    each section (Figs. 5-7)."""
+    rows = []
+    for cutoff in cutoffs:
+        for every in intervals:
+            for path in paths:
+                r = e1(ncoarse, cutoff=cutoff, regrid_every=every, per_patch=(path == "per_patch"))
+                rows.append({"cutoff": cutoff, "regrid_interval": every, "path": path,
+                             "cell_updates": r["cell_updates"],
+                             "mean_patches_per_coarse_step": r["mean_patches_per_coarse_step"],
+                             "sections_s": {k: round(v, 4) for k, v in r["sections_s"].items()},
+                             "cell_updates_per_s": r["cell_updates_per_s"], "status": r["status"]})
+                torch.cuda.empty_cache()
+    return {"workload": f"benchmark analog (1000^2 base, 3 levels of ratio 2, van Leer, conservation fix), "
+                        f"{ncoarse} coarse steps per combination",
+            "runs": rows}
 
 
 WORKLOADS = {"c0": config0, "c2": config2, "c3": config3, "c4": config4, "e1": e1, "swe1": swe1, "swe2": swe2}
 # (bench.py reports every workload above; e1 runs 200 coarse steps there)
+SWEEPS = {"e3": e3}   # run on request only: python -m paper_1808_02638_gb300.measure e3
 
 
 def run_all(names=None):
@@ -404,6 +448,8 @@ def main():
     torch.cuda.set_device(0)
     if a.names == ["c4"]:
         print(json.dumps({"c4": config4(a.nruns, a.ncoarse, a.every, not a.no_plain)}, indent=1))
+    elif a.names and all(n in SWEEPS for n in a.names):
+        print(json.dumps({n: SWEEPS[n]() for n in a.names}, indent=1))
     else:
         print(json.dumps(run_all(a.names or None), indent=1))
 

@@ -148,6 +148,8 @@ class Hierarchy:
         self.fused = False       # one-level hierarchies: one launch per step (pulled ghosts, Eq. cfl on the device)
         self.pull = True         # coarse steps pull same-level / boundary ghosts (fill only interpolated ones)
         self.pull_levels = [True] * self.nlev   # per level (the autotuner may prefer the copy launch)
+        # a list while sections of eager coarse steps are timed: (name, start event, end event)
+        self.sections = None
 
     def _layout(self, L):
         """(claw boxes, [(run, q base, coefficient base)], q size, coefficient size) of level L"""
@@ -242,28 +244,63 @@ class Hierarchy:
         fn = claw.claw_level_step_patchwise if self.patchwise else claw.claw_level_step
         fn(self.ctx, L, src, dst, self.aux[L], self.dt, self.smax, stream)
 
+    def _section(self, name, stream):
+        """Starts a timed section of an eager coarse step on the current stream; returns its end
+        event (to record when the section's launches are enqueued), or None when not timing."""
+        if self.sections is None or stream is not None or torch.cuda.is_current_stream_capturing():
+            return None
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        self.sections.append((name, s, e))
+        return e
+
+    def section_ms(self):
+        """{section: ms} summed over the sections timed since the last call (synchronises)"""
+        torch.cuda.synchronize()
+        out = {}
+        for name, s, e in self.sections or []:
+            out[name] = out.get(name, 0.0) + s.elapsed_time(e)
+        if self.sections is not None:
+            self.sections = []
+        return out
+
     def advance(self, L, cold=None, cnew=None, tau=0.0, stream=None):
         q = self.q[L][self.cur[L]]
         if self.pull and self.pull_levels[L] and not self.reflux and not self.patchwise:
             # only the interpolated ghosts are filled; the step pulls the others from their sources
+            e = self._section("fill", stream)
             claw.claw_fill_ghost_interp(self.ctx, L, q, cold, cnew, tau, stream)
+            if e is not None:
+                e.record()
+            e = self._section("advance", stream)
             claw.claw_level_advance(self.ctx, L, q, self.q[L][1 - self.cur[L]], self.aux[L], self.dt, self.smax,
                                     claw.CLAW_ADVANCE_PULL_GHOSTS, stream)
+            if e is not None:
+                e.record()
         else:
+            e = self._section("fill", stream)
             claw.claw_fill_ghost(self.ctx, L, q, cold, cnew, tau, stream)
+            if e is not None:
+                e.record()
+            e = self._section("advance", stream)
             if self.reflux and L > 0:             # this substep's fine fluxes at level L's interface
                 claw.claw_reflux_fine(self.ctx, L, q, cold, self.dt, self.rbuf[L], stream)
             if self.reflux and L + 1 < self.nlev:  # the coarse fluxes at the finer level's interface
                 claw.claw_reflux_coarse(self.ctx, L + 1, q, self.dt, self.rbuf[L + 1], stream)
             self.step_level(L, stream)
+            if e is not None:
+                e.record()
         old, new = self.q[L][self.cur[L]], self.q[L][1 - self.cur[L]]
         if L + 1 < self.nlev:
             r = self.ratio(L + 1)
             for k in range(r):
                 self.advance(L + 1, old, new, k / r, stream)
+            e = self._section("update", stream)
             claw.claw_average_down(self.ctx, L + 1, self.q[L + 1][self.cur[L + 1]], new, stream)
             if self.reflux:
                 claw.claw_reflux_apply(self.ctx, L + 1, self.rbuf[L + 1], self.dt, new, stream)
+            if e is not None:
+                e.record()
         self.cur[L] ^= 1
 
     def coarse_step(self, stream=None):

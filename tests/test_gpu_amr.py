@@ -141,6 +141,24 @@ def test_reflux_three_levels_matches_oracle():
     assert H.sync_status() == 0
 
 
+def test_reflux_van_leer_matches_oracle():
+    # the benchmark's limiter through the conservation fix's own edge solves
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    run.limiter = 3
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
+    O = OracleHierarchy(run, q0, [inputs.const_pool(l, 1.0) for l in run.levels],
+                        [inputs.const_pool(l, 4.0) for l in run.levels], reflux=True)
+    H.init_dt()
+    for _ in range(6):
+        H.coarse_step()
+        O.coarse_step()
+    _compare_all_levels(H, O, 0, TOLN)
+    assert H.sync_status() == 0
+
+
 def test_reflux_conserves_the_composite_integral_on_a_periodic_domain():
     from paper_1808_02638_gb300.solver import Hierarchy
     run = inputs.Run(*inputs.PULSE_DOMAIN, bc=(1, 1, 1, 1))
@@ -305,3 +323,71 @@ def test_regrid_keeps_the_reflux_conservation():
     # the transfer is conservative where it interpolates and the fine data it drops was
     # averaged into the coarse level: the composite integral survives the regrid
     assert (drift <= 1e-13 * 6.0).all(), drift
+
+
+def test_section_timing_leaves_the_result_alone():
+    # CUDA events around the sections of an eager coarse step change nothing in the state
+    import torch
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    A = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
+    B = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=True)
+    A.init_dt()
+    B.init_dt()
+    B.sections = []
+    for _ in range(3):
+        A.coarse_step()
+        B.coarse_step()
+    ms = B.section_ms()
+    assert set(ms) == {"fill", "advance", "update"} and all(v > 0.0 for v in ms.values())
+    assert B.sections == [] and B.section_ms() == {}
+    for L in range(len(run.levels)):
+        assert torch.equal(A.pool(L), B.pool(L))
+
+
+def test_benchmark_analog_paths_agree():
+    # a small benchmark analog: the batched launch and one launch per patch take the same
+    # hierarchy through the same regrids (identical states, hence identical flags and boxes)
+    from paper_1808_02638_gb300 import measure
+    kw = dict(ncoarse=6, base=160, max_size=48, regrid_every=2, tol=0.01)
+    a = measure.e1(**kw)
+    b = measure.e1(per_patch=True, **kw)
+    assert a["status"] == b["status"] == "ok"
+    assert a["cell_updates"] == b["cell_updates"] > 0
+    assert a["final_boxes_per_level"] == b["final_boxes_per_level"]
+    assert a["final_boxes_per_level"][2] > 0 and a["regrids"] == 3
+    for r in (a, b):
+        s = r["sections_s"]
+        assert min(s[k] for k in ("advance", "ghost_fill", "regrid", "updating")) > 0.0
+        assert abs(sum(v for k, v in s.items() if k != "total") - s["total"]) < 1e-9
+
+
+def test_coefficient_ghost_tables_of_a_uniform_medium_on_first_use():
+    # a uniform-medium context builds the one-plane ghost tables on the first call; they equal
+    # the ones a cell-wise context builds with its levels, also after the levels are set again
+    import torch
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    rho = [inputs.const_pool(l, 1.0) for l in run.levels]
+    K = [inputs.const_pool(l, 4.0) for l in run.levels]
+    U = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    C = Hierarchy([run], [q0], rho, K)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for rebuild in (False, True):
+        if rebuild:
+            for L in range(len(run.levels)):
+                claw.claw_set_level(U.ctx, L, U.boxes[L])
+        for L in range(len(run.levels)):
+            a = torch.rand(C.rho[L].shape, dtype=torch.float64, device="cuda", generator=g)
+            b = a.clone()
+            claw.claw_fill_ghost_coef(C.ctx, L, a)
+            claw.claw_fill_ghost_coef(U.ctx, L, b)
+            torch.cuda.synchronize()
+            assert torch.equal(a, b)
+            claw.claw_fill_ghost_coef_adjoint(C.ctx, L, a)
+            claw.claw_fill_ghost_coef_adjoint(U.ctx, L, b)
+            torch.cuda.synchronize()
+            assert torch.equal(a, b)
