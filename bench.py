@@ -393,7 +393,7 @@ def main():
     # is stepped in pieces of boxes as they arrive, so copies in both directions and the steps
     # overlap)
     H.fused = True          # one launch per step, ghosts pulled from their source cells
-    e2e_steps = max(3, min(20, K // 4))
+    e2e_steps = max(3, min(100, K // 2))
     # the host holds the state in packed form (interiors only, 3 x 2048^2 doubles): the bytes
     # each way per step
     host_in = H.pack().cpu().pin_memory()
