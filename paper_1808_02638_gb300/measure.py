@@ -324,7 +324,7 @@ def swe2():
 
 
 def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=0.002, max_size=260,
-       reflux=True, per_patch=False):
+       reflux=True, per_patch=False, tiling=((32, 16, 2, 256), (16, 16, 1, 128))):
     """Analog of the paper's benchmark (Sec. 4.1-4.2): radial pulse in a uniform medium, outflow
     (extrapolation) boundaries, van Leer, 3 levels of ratio 2 over a 1000^2 base tiled in 4 x 4
     patches of 250^2, patches of at most 260^2 generated by regridding (tol on neighbour
@@ -334,7 +334,9 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
     regrids, and splits the time into the sections of the paper's Fig. 4: advancing the solution
     (with the conservation fix's flux records), ghost fill, regridding, updating (averaging and
     the fix's corrections) and the rest.  per_patch: one step launch per patch instead of the
-    batched launch (the paper's launch pattern)."""
+    batched launch (the paper's launch pattern).  tiling: (tx, ty, staging, threads) per level,
+    kept through the regrids (default: 32 x 16 tiles on the base level's 250^2 patches, 16 x 16 on
+    the finer levels' smaller ones, the faster choices in a trial of five tilings)."""
     import time
     run = inputs.Run(*inputs.PULSE_DOMAIN, limiter=3)
     d0 = 2.0 / base
@@ -345,7 +347,7 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
         n = base * ratio ** L
         run.levels.append(inputs.Level(n, n, 2.0 / n, 2.0 / n, np.zeros((0, 4), dtype=np.int32), ratio))
     q0 = [inputs.init_q(run, lev) for lev in run.levels]
-    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=reflux)
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, reflux=reflux, tiling=tiling)
     H.patchwise = bool(per_patch)
     params = dict(tol=tol, buffer=regrid_every, cutoff=cutoff, max_size=max_size, nest=2)
     for _ in range(nlev - 1):       # refine level by level at t = 0
@@ -400,16 +402,16 @@ def e1(ncoarse=200, base=1000, nlev=3, ratio=2, cutoff=0.7, regrid_every=8, tol=
                     "synchronisation, other = total - the rest"}
 
 
-def e3(ncoarse=200, cutoffs=(0.5, 0.7, 0.9), intervals=(2, 8, 16), paths=("batched", "per_patch")):
+def e3(ncoarse=200, cutoffs=(0.5, 0.7, 0.9), intervals=(2, 8, 16), paths=("batched", "per_patch"), tiling=None):
     """Analog of the paper's parameter study (Sec. 4.3): the benchmark analog for every cutoff x
     regrid interval, with the batched level-step launch and with one launch per patch.  Per
     combination: cells advanced, mean patches over all levels per coarse step, and the time of
-    each section (Figs. 5-7)."""
+    each section (Figs. 5-7).  tiling: as in e1 (default here: the library's 32 x 32 tiles)."""
     rows = []
     for cutoff in cutoffs:
         for every in intervals:
             for path in paths:
-                r = e1(ncoarse, cutoff=cutoff, regrid_every=every, per_patch=(path == "per_patch"))
+                r = e1(ncoarse, cutoff=cutoff, regrid_every=every, per_patch=(path == "per_patch"), tiling=tiling)
                 rows.append({"cutoff": cutoff, "regrid_interval": every, "path": path,
                              "cell_updates": r["cell_updates"],
                              "mean_patches_per_coarse_step": r["mean_patches_per_coarse_step"],

@@ -108,8 +108,8 @@ class Hierarchy:
             self.boxes.append(boxes)
             self.layout.append(lay)
             claw.claw_set_level(self.ctx, L, boxes)
-            if tiling is not None:
-                claw.claw_set_tiling(self.ctx, L, *tiling)
+            if self.level_tiling(L) is not None:
+                claw.claw_set_tiling(self.ctx, L, *self.level_tiling(L))
             qh = np.zeros(max(qb, inputs.ALIGN))
             for (ri, qbase, _) in lay:
                 a = np.asarray(q0[ri][L], dtype=np.float64)
@@ -150,6 +150,17 @@ class Hierarchy:
         self.pull_levels = [True] * self.nlev   # per level (the autotuner may prefer the copy launch)
         # a list while sections of eager coarse steps are timed: (name, start event, end event)
         self.sections = None
+
+    def level_tiling(self, L):
+        """(tx, ty, staging, threads) installed on level L: `tiling` is one such tuple for every
+        level or a sequence of them per level (the last one for the levels beyond), or None for
+        the library's default"""
+        t = self.tiling
+        if t is None:
+            return None
+        if isinstance(t[0], (tuple, list)):
+            return tuple(t[min(L, len(t) - 1)])
+        return tuple(t)
 
     def _layout(self, L):
         """(claw boxes, [(run, q base, coefficient base)], q size, coefficient size) of level L"""
@@ -209,8 +220,8 @@ class Hierarchy:
             old_boxes, old_pool = self.boxes[Lf], self.q[Lf][self.cur[Lf]]
             boxes, lay, qb, _ = self._layout(Lf)
             claw.claw_set_level(self.ctx, Lf, boxes)   # also clears the finer levels' tables
-            if self.tiling is not None:
-                claw.claw_set_tiling(self.ctx, Lf, *self.tiling)
+            if self.level_tiling(Lf) is not None:
+                claw.claw_set_tiling(self.ctx, Lf, *self.level_tiling(Lf))
             new = torch.zeros(max(qb, inputs.ALIGN), dtype=torch.float64, device=self.dev)
             claw.claw_regrid_transfer(self.ctx, Lf, old_boxes, old_pool, new, qc)
             self.boxes[Lf], self.layout[Lf] = boxes, lay
