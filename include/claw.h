@@ -353,7 +353,7 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t level, int32_t run, const uint8_t* 
  * the conservative space interpolation from q_coarse (level-1, same time), read from the coarse
  * box holding the cell's parent with its ghosts, which must be filled (the new boxes lie two
  * coarse cells inside the coarse level, as claw_regrid_boxes makes them).  Waits for its
- * launches (the temporary tables are freed).  Errors: CLAW_EINVAL (a new box not nested in the
+ * launches (its tables sit in a scratch arena of the context that the next call reuses).  Errors: CLAW_EINVAL (a new box not nested in the
  * coarse level), CLAW_ESTATE, CLAW_ENOMEM, CLAW_ECUDA. */
 int claw_regrid_transfer(claw_ctx* ctx, int32_t level, const claw_box* old_boxes, int32_t n_old, const double* q_old,
                          double* q_new, const double* q_coarse, void* stream);

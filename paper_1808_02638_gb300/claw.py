@@ -173,10 +173,14 @@ def claw_regrid_boxes(ctx, level, run, flags_host, buffer, nest, cutoff, max_siz
     """new (ilo, jlo, nx, ny) boxes of level+1 for one run from its host flag grid (numpy uint8)"""
     import numpy as np
     f = np.ascontiguousarray(flags_host, dtype=np.uint8)
-    cap = max(16, f.size // 4)
-    out = np.zeros(4 * cap, dtype=np.int32)
-    n = load().claw_regrid_boxes(ctx, level, run, f.ctypes.data_as(ctypes.c_void_p), int(buffer), int(nest),
-                                 float(cutoff), int(max_size), out.ctypes.data_as(ctypes.c_void_p), cap)
+    # room for 65536 boxes first; a grid that makes more (at most one per cell) is clustered again
+    # with room for all of them
+    for cap in (min(65536, max(16, f.size)), max(16, f.size)):
+        out = np.empty(4 * cap, dtype=np.int32)
+        n = load().claw_regrid_boxes(ctx, level, run, f.ctypes.data_as(ctypes.c_void_p), int(buffer), int(nest),
+                                     float(cutoff), int(max_size), out.ctypes.data_as(ctypes.c_void_p), cap)
+        if n != -CLAW_ENOMEM:
+            break
     if n < 0:
         raise ClawError("claw_regrid_boxes", -n)
     return [tuple(int(v) for v in out[4 * k:4 * k + 4]) for k in range(n)]

@@ -277,6 +277,25 @@ def test_clustering_matches_the_oracle(seed):
             assert got == want
 
 
+def test_clustering_with_more_boxes_than_the_first_output_buffer():
+    # a checkerboard with cutoff 1 leaves one box per flagged cell: 131072 boxes, more than the
+    # binding's first output buffer holds, so the call is repeated with room for every cell
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = 512
+    run = inputs.Run(*inputs.PULSE_DOMAIN)
+    run.levels = [inputs.Level(n, n, 2.0 / n, 2.0 / n, [(0, 0, n, n)]),
+                  inputs.Level(2 * n, 2 * n, 1.0 / n, 1.0 / n, np.zeros((0, 4), dtype=np.int32), 2)]
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    jj, ii = np.mgrid[0:n, 0:n]
+    flags = ((ii + jj) % 2 == 0).astype(np.uint8)
+    got = claw.claw_regrid_boxes(H.ctx, 0, 0, flags, 0, 0, 1.0, 1024)
+    want = sorted((2 * int(i), 2 * int(j), 2, 2) for j, i in zip(*np.nonzero(flags)))
+    assert len(got) == n * n // 2 > 65536
+    assert sorted(got) == want
+
+
 def _run_with_regrid(hier, steps, every, params):
     for k in range(steps):
         hier.coarse_step()
