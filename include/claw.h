@@ -275,13 +275,30 @@ int claw_level_step_adjoint(claw_ctx* ctx, int32_t level, const double* q_old, c
                             double* lam_old, const double* aux, double* g_aux, const double* dt,
                             void* stream);
 
+/* claw_level_step_adjoint with the adjoint of the same-level and physical-boundary ghosts
+ * fused in (flags = CLAW_ADVANCE_PULL_GHOSTS; 0 is claw_level_step_adjoint): the kernel adds
+ * the adjoint of each such ghost cell of a box straight into the cell it was filled from (its
+ * entry in the level's ghost ring, u or v negated across a wall), which is what
+ * claw_fill_ghost_adjoint's copy part would do with it; those ghosts of lam_old stay zero.
+ * Ghosts interpolated from the coarser level keep their adjoint for
+ * claw_fill_ghost_interp_adjoint.  The same linear map as step adjoint + ghost-fill adjoint,
+ * summed in another order (FP64 atomics).  Errors: as claw_level_step_adjoint; CLAW_EINVAL for
+ * an unknown flag or a level without a ghost ring. */
+int claw_level_advance_adjoint(claw_ctx* ctx, int32_t level, const double* q_old, const double* lam_new,
+                               double* lam_old, const double* aux, double* g_aux, const double* dt,
+                               int32_t flags, void* stream);
+
 /* Reverse of claw_fill_ghost: every ghost adjoint of lam is added to the adjoint of its
  * source (a box interior of the level, or through the interpolation to lam_c_old /
  * lam_c_new, which may be NULL for level 0) and set to zero.  qc_old / qc_new are the coarse
- * states the forward fill read (for the minmod branches). */
+ * states the forward fill read (for the minmod branches).  claw_fill_ghost_interp_adjoint does
+ * the interpolated ghosts only (after claw_level_advance_adjoint with pulled ghosts). */
 int claw_fill_ghost_adjoint(claw_ctx* ctx, int32_t level, double* lam, double* lam_c_old,
                             double* lam_c_new, const double* qc_old, const double* qc_new,
                             double tau, void* stream);
+int claw_fill_ghost_interp_adjoint(claw_ctx* ctx, int32_t level, double* lam, double* lam_c_old,
+                                   double* lam_c_new, const double* qc_old, const double* qc_new,
+                                   double tau, void* stream);
 
 /* Reverse of claw_average_down: lam_f += (1/ratio^2) lam_c on the children, lam_c := 0 on the
  * covered coarse cells. */

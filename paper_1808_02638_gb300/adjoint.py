@@ -12,13 +12,15 @@ recomputes nothing.  Either way the backward runs the reverse of the AMR time st
 on the device:
 
   average (Sec. 2.3)        -> claw_average_down_adjoint
-  fine substeps, last first -> claw_level_step_adjoint + claw_fill_ghost_adjoint (the
+  fine substeps, last first -> claw_level_advance_adjoint + claw_fill_ghost_interp_adjoint (the
                                interpolation adjoint feeds the coarse old / new states)
-  coarse level-step         -> claw_level_step_adjoint + claw_fill_ghost_adjoint
+  coarse level-step         -> claw_level_advance_adjoint + claw_fill_ghost_interp_adjoint
 
-with the time steps frozen at their forward values.  The medium gradients leave through
-claw_medium_aux_adjoint and claw_fill_ghost_coef_adjoint.  This module only sequences calls:
-every arithmetic operation of the gradient runs in libclaw.so.
+with the time steps frozen at their forward values.  The step adjoint routes the adjoint of
+every same-level and boundary ghost to its source cell itself (H.pull, the default; with
+H.pull = False: claw_level_step_adjoint + claw_fill_ghost_adjoint, the same map).  The medium
+gradients leave through claw_medium_aux_adjoint and claw_fill_ghost_coef_adjoint.  This module
+only sequences calls: every arithmetic operation of the gradient runs in libclaw.so.
 """
 from __future__ import annotations
 
@@ -66,8 +68,13 @@ def _reverse(H, node, lam, g_aux, lam_cold=None, lam_cnew=None):
         claw.claw_average_down_adjoint(H.ctx, L + 1, lam[L + 1], lam_pre)
         for fnode in reversed(node.fine):
             _reverse(H, fnode, lam, g_aux, lam_cold=lam_in, lam_cnew=lam_pre)
-    claw.claw_level_step_adjoint(H.ctx, L, node.q_in, lam_pre, lam_in, H.aux[L], g_aux[L], H.dt)
-    claw.claw_fill_ghost_adjoint(H.ctx, L, lam_in, lam_cold, lam_cnew, node.cold, node.cnew, node.tau)
+    if H.pull:   # the ghost-copy adjoint fused into the step adjoint; the interpolation's apart
+        claw.claw_level_advance_adjoint(H.ctx, L, node.q_in, lam_pre, lam_in, H.aux[L], g_aux[L], H.dt,
+                                        claw.CLAW_ADVANCE_PULL_GHOSTS)
+        claw.claw_fill_ghost_interp_adjoint(H.ctx, L, lam_in, lam_cold, lam_cnew, node.cold, node.cnew, node.tau)
+    else:
+        claw.claw_level_step_adjoint(H.ctx, L, node.q_in, lam_pre, lam_in, H.aux[L], g_aux[L], H.dt)
+        claw.claw_fill_ghost_adjoint(H.ctx, L, lam_in, lam_cold, lam_cnew, node.cold, node.cnew, node.tau)
     lam[L] = lam_in
 
 

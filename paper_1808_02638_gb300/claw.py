@@ -66,6 +66,7 @@ _SIGNATURES = {
     "claw_reflux_apply": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_fill_ghost": ([VP, I32, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_adjoint": ([VP, I32, VP, VP, VP, VP, VP, DBL, VP], ctypes.c_int),
+    "claw_fill_ghost_interp_adjoint": ([VP, I32, VP, VP, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_coef": ([VP, I32, VP, VP], ctypes.c_int),
     "claw_fill_ghost_interp": ([VP, I32, VP, VP, VP, DBL, VP], ctypes.c_int),
     "claw_fill_ghost_coef_adjoint": ([VP, I32, VP, VP], ctypes.c_int),
@@ -84,6 +85,7 @@ _SIGNATURES = {
     "claw_average_down": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_average_down_adjoint": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_level_step_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "claw_level_advance_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
     "claw_sync_status": ([VP], ctypes.c_int),
     "claw_launch_count": ([VP], ctypes.c_int64),
     "claw_strerror": ([I32], ctypes.c_char_p),
@@ -244,6 +246,13 @@ def claw_fill_ghost_adjoint(ctx, level, lam, lam_c_old=None, lam_c_new=None, qc_
         _stream(stream)))
 
 
+def claw_fill_ghost_interp_adjoint(ctx, level, lam, lam_c_old=None, lam_c_new=None, qc_old=None, qc_new=None,
+                                   tau=0.0, stream=None):
+    _check("claw_fill_ghost_interp_adjoint", load().claw_fill_ghost_interp_adjoint(
+        ctx, level, _ptr(lam), _ptr(lam_c_old), _ptr(lam_c_new), _ptr(qc_old), _ptr(qc_new), float(tau),
+        _stream(stream)))
+
+
 def claw_fill_ghost_coef(ctx, level, a, stream=None):
     _check("claw_fill_ghost_coef", load().claw_fill_ghost_coef(ctx, level, _ptr(a), _stream(stream)))
 
@@ -327,6 +336,12 @@ def claw_average_down_adjoint(ctx, fine_level, lam_fine, lam_coarse, stream=None
 def claw_level_step_adjoint(ctx, level, q_old, lam_new, lam_old, aux, g_aux, dt, stream=None):
     _check("claw_level_step_adjoint", load().claw_level_step_adjoint(
         ctx, level, _ptr(q_old), _ptr(lam_new), _ptr(lam_old), _ptr(aux), _ptr(g_aux), _ptr(dt),
+        _stream(stream)))
+
+
+def claw_level_advance_adjoint(ctx, level, q_old, lam_new, lam_old, aux, g_aux, dt, flags, stream=None):
+    _check("claw_level_advance_adjoint", load().claw_level_advance_adjoint(
+        ctx, level, _ptr(q_old), _ptr(lam_new), _ptr(lam_old), _ptr(aux), _ptr(g_aux), _ptr(dt), int(flags),
         _stream(stream)))
 
 

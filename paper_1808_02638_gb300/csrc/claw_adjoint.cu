@@ -14,8 +14,10 @@
 // by the edge's thread and go to g_aux with global FP64 atomics; their chain rule to Z runs
 // once per gradient in claw_medium_aux_adjoint, not once per step.  The c^2 plane is folded
 // into c where it is read.  Contributions to cells shared with neighbouring tiles (the two
-// ghost layers) reach lam_old / g_aux through global FP64 atomics.  A uniform medium runs the
-// same code with constant medium planes and no medium adjoint.
+// ghost layers) reach lam_old / g_aux through global FP64 atomics.  Given the level's ghost ring
+// (A.ring), the contributions to the box's own ghost cells that the forward filled from cells of
+// the level go straight to those cells (the adjoint of the ghost copy, fused).  A uniform medium
+// runs the same code with constant medium planes and no medium adjoint.
 #include <cuda_runtime.h>
 
 #include "claw_step.cuh"
@@ -650,7 +652,22 @@ __global__ void __launch_bounds__(ANT, 2)
                 p += LAM(0, i, j);
                 u += LAM(1, i, j);
                 v += LAM(2, i, j);
-                const long long o = (long long)(y0 + j + 2) * W + (x0 + i + 2);
+                const int gx = x0 + i, gy = y0 + j;
+                if (A.ring && P.ring >= 0 && (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny)) {
+                    // a ghost of the box that the forward took from a cell of the level (same-level
+                    // copy or physical boundary): its adjoint goes straight to that cell, with the
+                    // wall sign flips; interpolated ghosts (source -1) keep theirs
+                    const longlong2 e = A.ring[P.ring + ring_index(gx + 2, gy + 2, P.nx, P.ny)];
+                    if (e.x >= 0) {
+                        const long long pl = e.y & ((1LL << kRingFlagShift) - 1);
+                        const int fl = (int)(e.y >> kRingFlagShift);
+                        if (p != 0.0) atomicAdd(lam_old + e.x, p);
+                        if (u != 0.0) atomicAdd(lam_old + e.x + pl, (fl & 1) ? -u : u);
+                        if (v != 0.0) atomicAdd(lam_old + e.x + 2 * pl, (fl & 2) ? -v : v);
+                        continue;
+                    }
+                }
+                const long long o = (long long)(gy + 2) * W + (gx + 2);
                 if (p != 0.0) atomicAdd(lo + o, p);
                 if (u != 0.0) atomicAdd(lo + WH + o, u);
                 if (v != 0.0) atomicAdd(lo + 2 * WH + o, v);

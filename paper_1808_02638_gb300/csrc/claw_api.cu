@@ -1237,6 +1237,19 @@ int claw_fill_ghost_coef_adjoint(claw_ctx* ctx, int32_t L, double* g, void* stre
                             : cudaSuccess);
 }
 
+int claw_fill_ghost_interp_adjoint(claw_ctx* ctx, int32_t L, double* lam, double* lco, double* lcn,
+                                   const double* qc_old, const double* qc_new, double tau, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !lam) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    const LevelDev& d = ctx->lev[L];
+    if (d.ninterp > 0 && (!qc_old || !qc_new)) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    ctx->launches += d.ninterp > 0;
+    return cuda_rc(launch_fill_interp_adjoint(d.interps, d.ninterp, lam, lco, lcn, qc_old, qc_new, tau,
+                                              (cudaStream_t)stream));
+}
+
 int claw_fill_ghost_adjoint(claw_ctx* ctx, int32_t L, double* lam, double* lco, double* lcn, const double* qc_old,
                             const double* qc_new, double tau, void* stream)
 {
@@ -1450,22 +1463,32 @@ int claw_average_down_adjoint(claw_ctx* ctx, int32_t fl, double* lf, double* lc,
     return cuda_rc(launch_average_adjoint(d.avgs, d.navg, d.ratio, lf, lc, (cudaStream_t)stream));
 }
 
-int claw_level_step_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const double* lam_new, double* lam_old,
-                            const double* aux, double* g_aux, const double* dt, void* stream)
+int claw_level_advance_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const double* lam_new,
+                               double* lam_old, const double* aux, double* g_aux, const double* dt, int32_t flags,
+                               void* stream)
 {
     if (!ctx || L < 0 || L >= CLAW_MAXLEV || !q_old || !lam_new || !lam_old || !dt) return CLAW_EINVAL;
+    if (flags & ~CLAW_ADVANCE_PULL_GHOSTS) return CLAW_EINVAL;
     if (!ctx->set[L]) return CLAW_ESTATE;
     if (ctx->kind() == KIND_SWE) return CLAW_EINVAL;   // the adjoint is written for acoustics
     if (ctx->medium == 1 && (!aux || !g_aux)) return CLAW_EINVAL;
-    DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
+    if ((flags & CLAW_ADVANCE_PULL_GHOSTS) && !d.ring_ok) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
     if (d.ntiles == 0) return CLAW_OK;
     StepArgs a = make_args(ctx, L, q_old, nullptr, aux, dt, nullptr);
     a.tiles = ctx->atiles[L];
     a.ntiles = ctx->natiles[L];
+    if (flags & CLAW_ADVANCE_PULL_GHOSTS) a.ring = d.ring;
     ctx->launches += 1;
     return cuda_rc(launch_step_adjoint(a, lam_new, lam_old, g_aux, ctx->medium, ctx->limiter, ctx->nsm,
                                        (cudaStream_t)stream));
+}
+
+int claw_level_step_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const double* lam_new, double* lam_old,
+                            const double* aux, double* g_aux, const double* dt, void* stream)
+{
+    return claw_level_advance_adjoint(ctx, L, q_old, lam_new, lam_old, aux, g_aux, dt, 0, stream);
 }
 
 static int reflux_check(claw_ctx* ctx, int L)

@@ -121,6 +121,45 @@ def test_adjoint_matches_oracle_reverse_mode(nlev):
     _compare([t.grad.cpu().numpy() for t in tk], gk, 1e-10)
 
 
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 2, 2), (2, 0, 2, 2)])
+def test_fused_ghost_adjoint_equals_the_separate_fill_adjoint(bc):
+    # the step adjoint that sends each same-level / boundary ghost's adjoint to its source cell
+    # (H.pull) against the step adjoint followed by the ghost-fill adjoint: the same map, summed
+    # in another order; level 0 in four boxes so that it has same-level ghosts too
+    import torch
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.adjoint import rollout
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = 32
+    run = inputs.Run(*inputs.PULSE_DOMAIN, bc=bc)
+    run.levels = inputs.amr_levels(run, n, 4, [(0.2, 0.45)], [31])
+    run.levels[0] = inputs.Level(n, n, 2 / n, 2 / n, inputs.uniform_tiling(n, n, 16, 16))
+    r2 = inputs.smooth_field(23, n, n, 0.5, 2.0, sigma=3.0)
+    k2 = inputs.smooth_field(24, n, n, 1.0, 8.0, sigma=3.0)
+    q = [inputs.init_q(run, lev) for lev in run.levels]
+    rho = [inputs.coef_pool(lev, r2, 4 ** L) for L, lev in enumerate(run.levels)]
+    K = [inputs.coef_pool(lev, k2, 4 ** L) for L, lev in enumerate(run.levels)]
+    H = Hierarchy([run], [q], [rho], [K])
+    grads = []
+    for pull in (True, False):
+        H.pull = pull
+        tq, tr, tk = _tensors(H, [q], "q"), _tensors(H, [rho], "c"), _tensors(H, [K], "c")
+        outs = rollout(H, tq, tr, tk, ncoarse=4, every=2)
+        # receiver on the first box of level 0 (cells 2..9 of its 16 x 16 interior)
+        v = outs[0][:3 * 20 * 20].view(3, 20, 20)
+        J = (v[0, M + 2:M + 10, M + 2:M + 10] ** 2).sum()
+        J.backward()
+        torch.cuda.synchronize()
+        grads.append([t.grad.clone() for t in tq + tr + tk] + [J.detach().clone()])
+    assert torch.equal(grads[0][-1], grads[1][-1])
+    for a, b in zip(grads[0][:-1], grads[1][:-1]):
+        assert float((a - b).abs().max()) <= 1e-12 * max(float(b.abs().max()), 1e-300)
+    assert max(float(g.abs().max()) for g in grads[0][:-1]) > 0.0
+    lam = torch.zeros_like(H.q[0][0])
+    with pytest.raises(claw.ClawError):
+        claw.claw_level_advance_adjoint(H.ctx, 0, H.q[0][0], lam, lam, H.aux[0], torch.zeros_like(H.aux[0]), H.dt, 8)
+
+
 @pytest.mark.parametrize("medium", ["uniform", "cellwise"])
 def test_level_step_function_matches_oracle_step_adjoint(medium):
     # one level-step as a torch.autograd.Function: the gradient of <w, q_new> (w on interiors)
