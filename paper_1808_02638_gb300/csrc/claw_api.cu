@@ -793,6 +793,46 @@ struct Prefix {
     }
 };
 
+// out[j * nx + i] = 1 when some cell of g within `rad` cells (square neighbourhood clipped to the
+// grid) is set (g != 0, or g == 0 with `invert`); g is nx x ny cells in rows of `pitch` bytes.
+// Separable: a running count along each row into `rows`, then one down each column.
+void dilate(const unsigned char* g, size_t pitch, int nx, int ny, int rad, bool invert,
+            std::vector<unsigned char>& rows, std::vector<unsigned char>& out)
+{
+    rows.resize((size_t)nx * ny);
+    out.resize((size_t)nx * ny);
+    rad = std::min(rad, std::max(nx, ny));
+    parallel_for(ny, [&](int j0, int j1) {
+        for (int j = j0; j < j1; ++j) {
+            const unsigned char* src = g + (size_t)j * pitch;
+            unsigned char* dst = &rows[(size_t)j * nx];
+            auto set = [&](int i) { return ((src[i] != 0) != invert) ? 1 : 0; };
+            int cnt = 0;
+            for (int i = 0; i <= std::min(rad, nx - 1); ++i) cnt += set(i);
+            for (int i = 0; i < nx; ++i) {
+                dst[i] = cnt > 0;
+                if (i + 1 + rad < nx) cnt += set(i + 1 + rad);
+                if (i - rad >= 0) cnt -= set(i - rad);
+            }
+        }
+    });
+    parallel_for(nx, [&](int i0, int i1) {
+        std::vector<int> cnt(i1 - i0, 0);
+        for (int j = 0; j <= std::min(rad, ny - 1); ++j)
+            for (int i = i0; i < i1; ++i) cnt[i - i0] += rows[(size_t)j * nx + i];
+        for (int j = 0; j < ny; ++j) {
+            unsigned char* dst = &out[(size_t)j * nx];
+            const unsigned char* add = j + 1 + rad < ny ? &rows[(size_t)(j + 1 + rad) * nx] : nullptr;
+            const unsigned char* sub = j - rad >= 0 ? &rows[(size_t)(j - rad) * nx] : nullptr;
+            for (int i = i0; i < i1; ++i) {
+                dst[i] = cnt[i - i0] > 0;
+                if (add) cnt[i - i0] += add[i];
+                if (sub) cnt[i - i0] -= sub[i];
+            }
+        }
+    });
+}
+
 std::vector<IBox> cluster_flags(const std::vector<unsigned char>& f, int NX, int NY, double cutoff, int max_size,
                                 const std::vector<unsigned char>& allowed)
 {
@@ -1579,16 +1619,18 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     if (L + 1 >= p.nlev) return -CLAW_EINVAL;
     const int NX = level_nx(p, L), NY = level_ny(p, L), r = p.ratio[L + 1];
     if ((long long)(NX + 1) * (NY + 1) >= (1LL << 31)) return -CLAW_EINVAL;
+    buffer = std::min(buffer, std::max(NX, NY));   // wider reaches change nothing
+    nest = std::min(nest, std::max(NX, NY));
     // scratch grids reused from call to call (no fresh pages per regrid); named through local
     // references, which the worker threads' lambdas capture (a thread_local named inside a
     // lambda would be the worker's own, empty instance)
-    static thread_local std::vector<unsigned char> tl_f, tl_cov, tl_allowed;
-    static thread_local std::vector<int> tl_pfl, tl_punc, tl_rlo, tl_rhi;
+    static thread_local std::vector<unsigned char> tl_f, tl_cov, tl_allowed, tl_rows, tl_near;
+    static thread_local std::vector<int> tl_rlo, tl_rhi;
     std::vector<unsigned char>& f = tl_f;
     std::vector<unsigned char>& cov = tl_cov;
     std::vector<unsigned char>& allowed = tl_allowed;
-    std::vector<int>& pfl = tl_pfl;
-    std::vector<int>& punc = tl_punc;
+    std::vector<unsigned char>& rows = tl_rows;
+    std::vector<unsigned char>& near = tl_near;
     std::vector<int>& rlo = tl_rlo;
     std::vector<int>& rhi = tl_rhi;
     // bounding box of the flags: the grids below cover only the window of it grown by `buffer`
@@ -1622,19 +1664,11 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     const int WX = wi1 - wi0, WY = wj1 - wj0;
     // flags grown by `buffer` cells (square neighbourhood, clipped to the domain; no flag lies
     // outside the window)
-    f.resize((size_t)WX * WY);
-    {
-        const Prefix FL(flags + (size_t)wj0 * NX + wi0, NX, WX, WY, false, pfl);
-        parallel_for(WY, [&](int ja, int jb) {
-            for (int j = ja; j < jb; ++j)
-                for (int i = 0; i < WX; ++i)
-                    f[(size_t)j * WX + i] = FL.sum(std::max(0, i - buffer), std::max(0, j - buffer),
-                                                   std::min(WX, i + buffer + 1), std::min(WY, j + buffer + 1)) > 0;
-        });
-    }
-    // keep cells `nest` cells inside the level's coverage: uncovered cells of the square of
-    // radius `nest` around each cell, the square clipped to the domain (the domain outside
-    // counts as covered); the coverage grid spans the window grown by `nest`
+    dilate(flags + (size_t)wj0 * NX + wi0, NX, WX, WY, buffer, false, rows, f);
+    // keep cells `nest` cells inside the level's coverage: no uncovered cell in the square of
+    // radius `nest` around the cell, the square clipped to the domain (the domain outside counts
+    // as covered); the coverage grid spans the window grown by `nest`, so the square of a window
+    // cell clipped to that grid is the square clipped to the domain
     const int ci0 = std::max(0, wi0 - nest), ci1 = std::min(NX, wi1 + nest);
     const int cj0 = std::max(0, wj0 - nest), cj1 = std::min(NY, wj1 + nest);
     const int CX = ci1 - ci0, CY = cj1 - cj0;
@@ -1645,17 +1679,17 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
         const int y0 = std::max(cj0, b.jlo), y1 = std::min(cj1, b.jlo + b.ny);
         for (int j = y0; j < y1; ++j) std::memset(&cov[(size_t)(j - cj0) * CX + (x0 - ci0)], 1, std::max(0, x1 - x0));
     }
-    const Prefix UNC(cov.data(), CX, CX, CY, true, punc);
+    dilate(cov.data(), CX, CX, CY, nest, true, rows, near);
     allowed.resize((size_t)WX * WY);
     parallel_for(WY, [&](int ja, int jb) {
-        for (int j = ja; j < jb; ++j)
+        for (int j = ja; j < jb; ++j) {
+            const unsigned char* nr = &near[(size_t)(j + wj0 - cj0) * CX + (wi0 - ci0)];
             for (int i = 0; i < WX; ++i) {
-                const int gi = wi0 + i, gj = wj0 + j;
-                const bool ok = UNC.sum(std::max(0, gi - nest) - ci0, std::max(0, gj - nest) - cj0,
-                                        std::min(NX, gi + nest + 1) - ci0, std::min(NY, gj + nest + 1) - cj0) == 0;
+                const bool ok = !nr[i];
                 allowed[(size_t)j * WX + i] = ok;
                 if (!ok) f[(size_t)j * WX + i] = 0;
             }
+        }
     });
     std::vector<IBox> out = cluster_flags(f, WX, WY, cutoff, std::max(1, max_size / r), allowed);
     for (IBox& b : out) {
