@@ -141,36 +141,85 @@ long long cell_off(const claw_box& b, int i, int j)   // plane-0 element of leve
 }
 long long plane_of(const claw_box& b) { return (long long)(b.nx + 4) * (b.ny + 4); }
 
-// The tables of one rebuild, packed into a host staging buffer (256-byte aligned pieces) and
-// copied into an arena in one call; each table pointer is set once the copy is done.
+// fn(lo, hi) over [0, n) in contiguous chunks on up to 16 host threads (ghost tables, regrid
+// grids), at least `grain` items a thread
+template <typename F>
+void parallel_for(int n, F fn, int grain = 64)
+{
+    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int nt = std::max(1, std::min(hw, n / std::max(1, grain)));
+    if (nt <= 1) {
+        fn(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(fn, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
+    for (auto& x : th) x.join();
+}
+
+// The tables of one rebuild: each table is one or more host pieces laid out back to back from a
+// 256-byte aligned offset.  commit() gathers the pieces into the arena's pinned staging buffer on
+// host threads, copies it to the device in one call and sets the table pointers.  The pieces are
+// read by commit(), so they must live until then.
 struct ArenaPack {
-    std::vector<char> host;
+    struct Piece {
+        const void* src;
+        size_t bytes, off;
+    };
+    std::vector<Piece> pieces;
     std::vector<std::function<void(char*)>> place;
+    size_t size = 0;
+    // a table from nparts vectors, part(k) being the k-th
+    template <class T, class Part>
+    void add_parts(T** dst, int nparts, Part part)
+    {
+        *dst = nullptr;
+        const size_t base = (size + 255) / 256 * 256;
+        size_t off = base;
+        for (int k = 0; k < nparts; ++k) {
+            const std::vector<T>& v = part(k);
+            if (v.empty()) continue;
+            pieces.push_back(Piece{v.data(), v.size() * sizeof(T), off});
+            off += v.size() * sizeof(T);
+        }
+        if (off == base) return;
+        size = off;
+        place.push_back([dst, base](char* b) { *dst = reinterpret_cast<T*>(b + base); });
+    }
     template <class T>
     void add(T** dst, const std::vector<T>& v)
     {
-        *dst = nullptr;
-        if (v.empty()) return;
-        const size_t off = (host.size() + 255) / 256 * 256;
-        host.resize(off + v.size() * sizeof(T));
-        std::memcpy(host.data() + off, v.data(), v.size() * sizeof(T));
-        place.push_back([dst, off](char* base) { *dst = reinterpret_cast<T*>(base + off); });
+        add_parts(dst, 1, [&](int) -> const std::vector<T>& { return v; });
+    }
+    // the tables laid out in h (size bytes)
+    void gather(char* h) const
+    {
+        parallel_for((int)pieces.size(), [&](int k0, int k1) {
+            for (int k = k0; k < k1; ++k) std::memcpy(h + pieces[k].off, pieces[k].src, pieces[k].bytes);
+        }, 256);
     }
     // The arena may still be read by kernels in flight from before the rebuild: the device is
     // synchronised before it is overwritten.
     int commit(DevArena& a)
     {
-        if (host.empty()) return CLAW_OK;
+        if (size == 0) return CLAW_OK;
         if (a.dev && cudaDeviceSynchronize() != cudaSuccess) return CLAW_ECUDA;
-        if (host.size() > a.cap) {
+        if (size > a.host_cap) {
+            cudaFreeHost(a.host);
+            a.host = nullptr;
+            a.host_cap = 0;
+            if (cudaMallocHost((void**)&a.host, size + size / 4) != cudaSuccess) return CLAW_ENOMEM;
+            a.host_cap = size + size / 4;
+        }
+        gather(a.host);
+        if (size > a.cap) {
             cudaFree(a.dev);
             a.dev = nullptr;
             a.cap = 0;
-            const size_t want = host.size() + host.size() / 4;
-            if (cudaMalloc((void**)&a.dev, want) != cudaSuccess) return CLAW_ENOMEM;
-            a.cap = want;
+            if (cudaMalloc((void**)&a.dev, size + size / 4) != cudaSuccess) return CLAW_ENOMEM;
+            a.cap = size + size / 4;
         }
-        if (cudaMemcpy(a.dev, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) return CLAW_ECUDA;
+        if (cudaMemcpy(a.dev, a.host, size, cudaMemcpyHostToDevice) != cudaSuccess) return CLAW_ECUDA;
         for (auto& f : place) f(a.dev);
         return CLAW_OK;
     }
@@ -179,8 +228,10 @@ struct ArenaPack {
 void free_arena(DevArena& a)
 {
     cudaFree(a.dev);
+    cudaFreeHost(a.host);
     a.dev = nullptr;
-    a.cap = 0;
+    a.host = nullptr;
+    a.cap = a.host_cap = 0;
 }
 
 // Forgets a level's boxes and tables; the arenas stay allocated for the next rebuild
@@ -241,17 +292,18 @@ int build_tiles(claw_ctx* ctx, int L)
             }
     }
     start.push_back((int)t.size());
+    // (the pieces are read by pack.commit: t keeps the box order, d.htiles the sorted copy)
     ArenaPack pack;
     pack.add(&ctx->ptiles[L], t);
     ctx->ptile_start[L] = start;
-    std::stable_sort(t.begin(), t.end(), [](const TileDev& a, const TileDev& b) {
+    d.htiles = t;
+    std::stable_sort(d.htiles.begin(), d.htiles.end(), [](const TileDev& a, const TileDev& b) {
         return (int)a.tx * a.ty > (int)b.tx * b.ty;
     });
-    d.htiles = t;
-    d.ntiles = (int)t.size();
+    d.ntiles = (int)d.htiles.size();
     for (auto& tm : ctx->tmaps[L]) cudaFree(tm.dev);
     ctx->tmaps[L].clear();
-    pack.add(&d.tiles, t);
+    pack.add(&d.tiles, d.htiles);
     // adjoint tiles
     std::vector<TileDev> at;
     const int e = adjoint_tile();
@@ -314,25 +366,26 @@ int make_interp(claw_ctx* ctx, int L, const claw_problem& pr, const Locator& cl,
 constexpr int kRectRows = 32;          // copy rectangles are split into pieces of at most this many rows
 constexpr long long kBlockCells = 256;   // cells per block of the copy kernel (about): one batch per thread
 
-// fn(lo, hi) over [0, n) in contiguous chunks on up to 16 host threads (ghost tables, regrid grids)
-template <typename F>
-void parallel_for(int n, F fn)
-{
-    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const int nt = std::max(1, std::min(hw, n / 64));
-    if (nt <= 1) {
-        fn(0, n);
-        return;
-    }
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(fn, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
-    for (auto& x : th) x.join();
-}
 
-int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::vector<InterpCell>& cells,
-                       std::vector<int>& start, std::vector<longlong2>* ring = nullptr, bool* ring_ok = nullptr)
+// ghost tasks of one box: copy rectangles, interpolated cells and (for pulled ghosts) its ring
+struct BoxGhosts {
+    std::vector<CopyRect> rects;
+    std::vector<InterpCell> cells;
+    std::vector<longlong2> ring;
+    bool want_ring = false, ring_ok = true;
+    int rc = CLAW_OK;
+};
+
+// ghost tables of a level, kept per box (the device tables are their concatenation in box order)
+struct GhostTables {
+    std::vector<BoxGhosts> per;
+    size_t nrects = 0, ncells = 0, nring = 0;
+    std::vector<int> start;   // blocks of the copy kernel over the concatenated rectangles
+    bool ring_ok = true;
+};
+
+int build_ghost_tables(claw_ctx* ctx, int L, GhostTables& gt, bool want_ring)
 {
-    if (ring_ok) *ring_ok = true;
     LevelDev& d = ctx->lev[L];
     std::vector<Locator> loc(ctx->nruns), cloc(ctx->nruns);
     for (int r = 0; r < ctx->nruns; ++r) {
@@ -345,23 +398,19 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
             cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
 
     // per box, independently (threads): its copy rectangles, interpolated cells and ghost ring
-    struct BoxGhosts {
-        std::vector<CopyRect> rects;
-        std::vector<InterpCell> cells;
-        std::vector<longlong2> ring;
-        bool want_ring = false, ring_ok = true;
-        int rc = CLAW_OK;
-    };
-    std::vector<BoxGhosts> per(d.nboxes);
+    std::vector<BoxGhosts>& per = gt.per;
+    per.assign(d.nboxes, BoxGhosts{});
     auto one_box = [&](int n, BoxGhosts& out) -> int {
         const claw_box& b = d.boxes[n];
         const claw_problem& pr = ctx->runs[b.run];
         const int NX = level_nx(pr, L), NY = level_ny(pr, L);
         const int W = b.nx + 4;
         std::vector<GhostEntry> ent;
-        for (int gj = b.jlo - 2; gj < b.jlo + b.ny + 2; ++gj)
-            for (int gi = b.ilo - 2; gi < b.ilo + b.nx + 2; ++gi) {
-                if (gi >= b.ilo && gi < b.ilo + b.nx && gj >= b.jlo && gj < b.jlo + b.ny) continue;
+        for (int gj = b.jlo - 2; gj < b.jlo + b.ny + 2; ++gj) {
+            // the ghost cells of row gj in row order: the whole padded row above and below the
+            // interior, else two cells on each side
+            const bool side_only = gj >= b.jlo && gj < b.jlo + b.ny;
+            for (int gi = b.ilo - 2; gi < b.ilo + b.nx + 2; gi += (side_only && gi == b.ilo - 1) ? b.nx + 1 : 1) {
                 int fx, fy;
                 const int si = bc_map(gi, NX, pr.bc[0], pr.bc[1], &fx);
                 const int sj = bc_map(gj, NY, pr.bc[2], pr.bc[3], &fy);
@@ -386,6 +435,7 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
                     return CLAW_EINVAL;   // not properly nested
                 out.cells.push_back(c);
             }
+        }
         // row runs of copies (consecutive ghosts of a row with one source box, one sign and a
         // constant source step), then stacked into rectangles
         struct RowRun {
@@ -476,48 +526,42 @@ int build_ghost_tables(claw_ctx* ctx, int L, std::vector<CopyRect>& rects, std::
     };
     parallel_for(d.nboxes, [&](int n0, int n1) {
         for (int n = n0; n < n1; ++n) {
-            per[n].want_ring = ring != nullptr;
+            per[n].want_ring = want_ring;
             per[n].rc = one_box(n, per[n]);
         }
-    });
-    // concatenated in box order: sized first, then filled in parallel
-    std::vector<size_t> ro(d.nboxes + 1, 0), co(d.nboxes + 1, 0), go(d.nboxes + 1, 0);
+    }, 4);
+    gt.nrects = gt.ncells = gt.nring = 0;
+    gt.ring_ok = true;
     for (int n = 0; n < d.nboxes; ++n) {
         const BoxGhosts& g = per[n];
         if (g.rc) return g.rc;
-        ro[n + 1] = ro[n] + g.rects.size();
-        co[n + 1] = co[n] + g.cells.size();
-        go[n + 1] = go[n] + g.ring.size();
-        if (ring) {
-            d.hpatches[n].ring = go[n] < (size_t)(1LL << 31) ? (int)go[n] : -1;
-            if (!g.ring_ok && ring_ok) *ring_ok = false;
+        if (want_ring) {
+            d.hpatches[n].ring = gt.nring < (size_t)(1LL << 31) ? (int)gt.nring : -1;
+            if (!g.ring_ok) gt.ring_ok = false;
         }
+        gt.nrects += g.rects.size();
+        gt.ncells += g.cells.size();
+        gt.nring += g.ring.size();
     }
-    rects.resize(ro[d.nboxes]);
-    cells.resize(co[d.nboxes]);
-    if (ring) ring->resize(go[d.nboxes]);
-    parallel_for(d.nboxes, [&](int n0, int n1) {
-        for (int n = n0; n < n1; ++n) {
-            const BoxGhosts& g = per[n];
-            std::copy(g.rects.begin(), g.rects.end(), rects.begin() + ro[n]);
-            std::copy(g.cells.begin(), g.cells.end(), cells.begin() + co[n]);
-            if (ring) std::copy(g.ring.begin(), g.ring.end(), ring->begin() + go[n]);
-        }
-    });
+    if (gt.nring >= (size_t)(1LL << 31)) gt.ring_ok = false;
     // blocks of the copy kernel: consecutive rectangles up to about kBlockCells cells (and at
     // most 32 rectangles, the kernel's staging chunk)
+    std::vector<int>& start = gt.start;
     start.assign(1, 0);
     long long cells_in = 0;
-    for (size_t i = 0; i < rects.size(); ++i) {
-        const long long c = (long long)rects[i].w * rects[i].h;
-        const int nin = (int)i - start.back();
-        if (nin > 0 && (cells_in + c > kBlockCells || nin >= 32)) {
-            start.push_back((int)i);
-            cells_in = 0;
+    int i = 0;
+    for (const BoxGhosts& g : per)
+        for (const CopyRect& rc : g.rects) {
+            const long long c = (long long)rc.w * rc.h;
+            const int nin = i - start.back();
+            if (nin > 0 && (cells_in + c > kBlockCells || nin >= 32)) {
+                start.push_back(i);
+                cells_in = 0;
+            }
+            cells_in += c;
+            ++i;
         }
-        cells_in += c;
-    }
-    if (!rects.empty()) start.push_back((int)rects.size());
+    if (gt.nrects) start.push_back((int)gt.nrects);
     return CLAW_OK;
 }
 
@@ -913,21 +957,20 @@ long long flag_grid_offset(const claw_ctx* ctx, int L, int run)
 int build_coef_tables(claw_ctx* ctx, int L)
 {
     LevelDev& d = ctx->lev[L];
-    std::vector<CopyRect> crects;
-    std::vector<InterpCell> unused;
-    std::vector<int> cstart;
+    GhostTables gt;
     const std::vector<claw_box> saved = d.boxes;
     for (auto& b : d.boxes) b.qoff = b.coff;
-    int rc = build_ghost_tables(ctx, L, crects, unused, cstart);
+    int rc = build_ghost_tables(ctx, L, gt, false);
     d.boxes = saved;
     if (rc) return rc;
-    for (auto& r : crects) r.flags = 0;
+    for (auto& g : gt.per)
+        for (auto& r : g.rects) r.flags = 0;
     ArenaPack pack;
-    pack.add(&d.ccopy_start, cstart);
-    pack.add(&d.ccopies, crects);
+    pack.add(&d.ccopy_start, gt.start);
+    pack.add_parts(&d.ccopies, d.nboxes, [&](int n) -> const std::vector<CopyRect>& { return gt.per[n].rects; });
     if ((rc = pack.commit(d.coeftab))) return rc;
-    d.nccopy_blocks = cstart.empty() ? 0 : (int)cstart.size() - 1;
-    d.nccopy = (int)crects.size();
+    d.nccopy_blocks = gt.start.empty() ? 0 : (int)gt.start.size() - 1;
+    d.nccopy = (int)gt.nrects;
     d.coef_built = true;
     return CLAW_OK;
 }
@@ -1105,51 +1148,47 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     d.tx = ctx->kind() == KIND_SWE ? 16 : 32;
     d.ty = ctx->kind() == KIND_SWE ? 16 : 32;
     d.staging = even ? 1 : 0;
-    std::vector<CopyRect> rects;
-    std::vector<InterpCell> cells;
+    GhostTables gt;
     std::vector<AvgRect> avg;
-    std::vector<int> qstart;
-    std::vector<longlong2> ring;
-    bool ring_ok = true;
-    int rc = build_ghost_tables(ctx, L, rects, cells, qstart, &ring, &ring_ok);
+    int rc = build_ghost_tables(ctx, L, gt, true);
     if (rc) return rc;
-    d.ring_ok = ring_ok && (long long)ring.size() < (1LL << 31);
+    d.ring_ok = gt.ring_ok;
     for (auto& P : d.hpatches)
         if (!d.ring_ok) P.ring = -1;
+    // every table stays alive until pack.commit reads it
     ArenaPack pack;
-    if (d.ring_ok) pack.add(&d.ring, ring);
-    pack.add(&d.copy_start, qstart);
-    d.ncopy_blocks = qstart.empty() ? 0 : (int)qstart.size() - 1;
+    if (d.ring_ok)
+        pack.add_parts(&d.ring, d.nboxes, [&](int n) -> const std::vector<longlong2>& { return gt.per[n].ring; });
+    pack.add(&d.copy_start, gt.start);
+    d.ncopy_blocks = gt.start.empty() ? 0 : (int)gt.start.size() - 1;
     d.max_rows = 0;
     for (const claw_box& b : d.boxes) d.max_rows = std::max(d.max_rows, b.ny + 4);
-    {   // packed interiors: box order, 3 planes of nx x ny each
-        std::vector<long long> poff(d.nboxes);
-        long long o = 0;
-        for (int n = 0; n < d.nboxes; ++n) {
-            poff[n] = o;
-            o += 3LL * d.boxes[n].nx * d.boxes[n].ny;
-        }
-        d.packed = o;
-        pack.add(&d.poff, poff);
+    // packed interiors: box order, 3 planes of nx x ny each
+    std::vector<long long> poff(d.nboxes);
+    long long o = 0;
+    for (int n = 0; n < d.nboxes; ++n) {
+        poff[n] = o;
+        o += 3LL * d.boxes[n].nx * d.boxes[n].ny;
     }
-    {   // the boxes as writers into the level's flag grid
-        std::vector<FlagBox> fb(d.nboxes);
-        for (int n = 0; n < d.nboxes; ++n) {
-            const claw_box& b = d.boxes[n];
-            const int NX = level_nx(ctx->runs[b.run], L);
-            fb[n].qoff = b.qoff;
-            fb[n].goff = flag_grid_offset(ctx, L, b.run) + (long long)b.jlo * NX + b.ilo;
-            fb[n].nx = b.nx;
-            fb[n].ny = b.ny;
-            fb[n].pitch = NX;
-            fb[n].pad = 0;
-        }
-        pack.add(&d.flagboxes, fb);
+    d.packed = o;
+    pack.add(&d.poff, poff);
+    // the boxes as writers into the level's flag grid
+    std::vector<FlagBox> fb(d.nboxes);
+    for (int n = 0; n < d.nboxes; ++n) {
+        const claw_box& b = d.boxes[n];
+        const int NX = level_nx(ctx->runs[b.run], L);
+        fb[n].qoff = b.qoff;
+        fb[n].goff = flag_grid_offset(ctx, L, b.run) + (long long)b.jlo * NX + b.ilo;
+        fb[n].nx = b.nx;
+        fb[n].ny = b.ny;
+        fb[n].pitch = NX;
+        fb[n].pad = 0;
     }
-    if (L > 0) build_avg_tables(ctx, L, avg);
+    pack.add(&d.flagboxes, fb);
+    std::vector<RefluxRec> rrec;
+    std::vector<int> rgroup;
     if (L > 0) {
-        std::vector<RefluxRec> rrec;
-        std::vector<int> rgroup;
+        build_avg_tables(ctx, L, avg);
         build_reflux_tables(ctx, L, rrec, rgroup);
         pack.add(&d.reflux, rrec);
         pack.add(&d.reflux_group, rgroup);
@@ -1157,12 +1196,12 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         d.nreflux_groups = rgroup.empty() ? 0 : (int)rgroup.size() - 1;
     }
     pack.add(&d.patches, d.hpatches);
-    pack.add(&d.copies, rects);
-    pack.add(&d.interps, cells);
+    pack.add_parts(&d.copies, d.nboxes, [&](int n) -> const std::vector<CopyRect>& { return gt.per[n].rects; });
+    pack.add_parts(&d.interps, d.nboxes, [&](int n) -> const std::vector<InterpCell>& { return gt.per[n].cells; });
     pack.add(&d.avgs, avg);
     if ((rc = pack.commit(d.tables))) return rc;
-    d.ncopy = (int)rects.size();
-    d.ninterp = (int)cells.size();
+    d.ncopy = (int)gt.nrects;
+    d.ninterp = (int)gt.ncells;
     d.navg = (int)avg.size();
     // a cell-wise medium fills its coefficient pools' ghosts: those tables are built now, a
     // uniform medium builds them on first use
@@ -1796,25 +1835,24 @@ int claw_regrid_transfer(claw_ctx* ctx, int32_t L, const claw_box* old_boxes, in
     parallel_for(d.nboxes, [&](int n0, int n1) {
         for (int n = n0; n < n1; ++n) per[n].rc = one_box(d.boxes[n], per[n]);
     });
-    std::vector<RectCopy> copies;
-    std::vector<InterpRun> runs;
+    size_t ncopies = 0, nruns = 0;
     for (const BoxTransfer& t : per) {
         if (t.rc) return t.rc;
-        copies.insert(copies.end(), t.copies.begin(), t.copies.end());
-        runs.insert(runs.end(), t.runs.begin(), t.runs.end());
+        ncopies += t.copies.size();
+        nruns += t.runs.size();
     }
     RectCopy* dc = nullptr;
     InterpRun* di = nullptr;
     ArenaPack pack;
-    pack.add(&dc, copies);
-    pack.add(&di, runs);
+    pack.add_parts(&dc, d.nboxes, [&](int n) -> const std::vector<RectCopy>& { return per[n].copies; });
+    pack.add_parts(&di, d.nboxes, [&](int n) -> const std::vector<InterpRun>& { return per[n].runs; });
     int rc = pack.commit(ctx->scratch);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (!rc) {
-        e = launch_rect_copy(dc, (int)copies.size(), q_old, q_new, s);
-        if (e == cudaSuccess) e = launch_interp_runs(di, (int)runs.size(), q_coarse, q_new, s);
-        ctx->launches += (copies.size() > 0) + (runs.size() > 0);
+        e = launch_rect_copy(dc, (int)ncopies, q_old, q_new, s);
+        if (e == cudaSuccess) e = launch_interp_runs(di, (int)nruns, q_coarse, q_new, s);
+        ctx->launches += (ncopies > 0) + (nruns > 0);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the scratch tables are reused by the next call
     }
     return rc ? rc : cuda_rc(e);

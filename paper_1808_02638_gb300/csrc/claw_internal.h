@@ -105,6 +105,8 @@ struct AvgRect {
 struct DevArena {
     char* dev = nullptr;
     size_t cap = 0;
+    char* host = nullptr;   // pinned staging buffer of the copy
+    size_t host_cap = 0;
 };
 
 struct LevelDev {
