@@ -8,12 +8,16 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <exception>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <unordered_map>
+#include <unistd.h>
 #include <utility>
 #include <vector>
 
@@ -143,18 +147,115 @@ long long plane_of(const claw_box& b) { return (long long)(b.nx + 4) * (b.ny + 4
 
 // fn(lo, hi) over [0, n) in contiguous chunks on up to 16 host threads (ghost tables, regrid
 // grids), at least `grain` items a thread
+// The host threads behind parallel_for: started once and kept, since starting 16 threads for
+// every pass of a regrid cost milliseconds.  run(n, fn) calls fn(0..n-1) on the workers and the
+// caller and returns when all are done; one run at a time.  A run from inside a worker (nested),
+// or in a process forked from the one that started the workers, goes serially.  The pool is
+// never destroyed: its idle workers end with the process.
+class HostPool {
+public:
+    static HostPool& get()
+    {
+        static HostPool* pool = new HostPool;
+        return *pool;
+    }
+    int threads() const { return getpid() == pid_ ? (int)workers_.size() + 1 : 1; }
+    void run(int n, const std::function<void(int)>& fn)
+    {
+        if (n <= 1 || in_worker() || threads() == 1) {
+            for (int k = 0; k < n; ++k) fn(k);
+            return;
+        }
+        std::lock_guard<std::mutex> one_run(run_m_);
+        Run r(fn, n);
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            cur_ = &r;
+            ++gen_;
+        }
+        cv_.notify_all();
+        std::exception_ptr err;
+        in_worker() = true;   // a parallel_for inside an item of this run goes serially
+        try {
+            work(r);
+        } catch (...) {   // stop handing out items, let the workers finish theirs, then rethrow
+            err = std::current_exception();
+            std::lock_guard<std::mutex> lk(m_);
+            r.left -= std::max(0, r.n - r.next.exchange(r.n)) + 1;
+        }
+        in_worker() = false;
+        // r lives on this frame: return only when every item is done and no worker holds r
+        {
+            std::unique_lock<std::mutex> lk(m_);
+            done_.wait(lk, [&] { return r.left <= 0 && r.users == 0; });
+            cur_ = nullptr;
+        }
+        if (err) std::rethrow_exception(err);
+    }
+
+private:
+    struct Run {
+        Run(const std::function<void(int)>& f, int count) : fn(f), n(count), left(count) {}
+        const std::function<void(int)>& fn;
+        const int n;
+        std::atomic<int> next{0};
+        int left;        // items not yet done (under m_)
+        int users = 0;   // workers holding this run (under m_)
+    };
+    HostPool() : pid_(getpid())
+    {
+        const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        for (int t = 1; t < hw; ++t) workers_.emplace_back([this] { loop(); });
+    }
+    static bool& in_worker()
+    {
+        static thread_local bool w = false;
+        return w;
+    }
+    void work(Run& r)   // take items of r until none are left
+    {
+        for (int k; (k = r.next.fetch_add(1)) < r.n;) {
+            r.fn(k);
+            std::lock_guard<std::mutex> lk(m_);
+            if (--r.left == 0) done_.notify_all();
+        }
+    }
+    void loop()
+    {
+        in_worker() = true;
+        unsigned long seen = 0;
+        for (;;) {
+            Run* r;
+            {
+                std::unique_lock<std::mutex> lk(m_);
+                cv_.wait(lk, [&] { return gen_ != seen && cur_ != nullptr; });
+                seen = gen_;
+                r = cur_;
+                ++r->users;
+            }
+            work(*r);
+            std::lock_guard<std::mutex> lk(m_);
+            if (--r->users == 0 && r->left == 0) done_.notify_all();
+        }
+    }
+    const pid_t pid_;
+    std::vector<std::thread> workers_;
+    std::mutex run_m_, m_;
+    std::condition_variable cv_, done_;
+    Run* cur_ = nullptr;
+    unsigned long gen_ = 0;
+};
+
 template <typename F>
 void parallel_for(int n, F fn, int grain = 64)
 {
-    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const int nt = std::max(1, std::min(hw, n / std::max(1, grain)));
+    HostPool& pool = HostPool::get();
+    const int nt = std::max(1, std::min(pool.threads(), n / std::max(1, grain)));
     if (nt <= 1) {
         fn(0, n);
         return;
     }
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(fn, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
-    for (auto& x : th) x.join();
+    pool.run(nt, [&](int t) { fn((int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt)); });
 }
 
 // The tables of one rebuild: each table is one or more host pieces laid out back to back from a
