@@ -1,6 +1,6 @@
-"""Host logic of stepping a level in pieces (no GPU): the pieces partition the boxes in pool
-order, their pool ranges cover each box's planes, and a piece waits exactly for the pieces whose
-boxes its two ghost layers touch, periodic images included."""
+"""Host logic of the solver (no GPU).  Stepping a level in pieces: the pieces partition the boxes
+in pool order, their pool ranges cover each box's planes, and a piece waits exactly for the pieces
+whose boxes its two ghost layers touch, periodic images included.  Per-level tilings."""
 import numpy as np
 
 from paper_1808_02638_gb300 import inputs
@@ -44,3 +44,17 @@ def test_more_pieces_than_rows_and_uneven_boxes():
     for k, (b0, b1) in enumerate(pieces):
         assert k in needs[k]
     assert np.all(np.diff([a for a, _ in ranges]) > 0)
+
+
+def test_level_tiling_per_level_or_shared():
+    # Hierarchy.level_tiling: one tuple for every level, or one per level with the last one
+    # standing for the levels beyond the sequence
+    from types import SimpleNamespace
+
+    from paper_1808_02638_gb300.solver import Hierarchy
+    one = SimpleNamespace(tiling=(32, 16, 2, 256))
+    assert [Hierarchy.level_tiling(one, L) for L in range(3)] == [(32, 16, 2, 256)] * 3
+    per = SimpleNamespace(tiling=((32, 16, 2, 256), [16, 16, 1, 128]))
+    assert [Hierarchy.level_tiling(per, L) for L in range(3)] == [(32, 16, 2, 256), (16, 16, 1, 128),
+                                                                   (16, 16, 1, 128)]
+    assert Hierarchy.level_tiling(SimpleNamespace(tiling=None), 0) is None
