@@ -365,6 +365,13 @@ int claw_flag_cells(claw_ctx* ctx, int32_t level, const double* q, double tol, u
  * max_boxes, -CLAW_EINVAL / -CLAW_ESTATE on bad arguments. */
 int claw_regrid_boxes(claw_ctx* ctx, int32_t level, int32_t run, const uint8_t* flags, int32_t buffer, int32_t nest,
                       double cutoff, int32_t max_size, int32_t* boxes, int32_t max_boxes);
+/* Host only, no context and no GPU: the same clustering for an nx x ny level whose boxes (for
+ * the nesting test; their run, qoff and coff are ignored) are cover[0..ncover), the new boxes in
+ * the cells of a level `ratio` times finer.  claw_regrid_boxes calls it with the run's boxes of
+ * `level`.  Same returns; -CLAW_EINVAL also for nx, ny or ratio below 1. */
+int claw_cluster_flags(int32_t nx, int32_t ny, int32_t ratio, const claw_box* cover, int32_t ncover,
+                       const uint8_t* flags, int32_t buffer, int32_t nest, double cutoff, int32_t max_size,
+                       int32_t* boxes, int32_t max_boxes);
 /* After claw_set_level(level, new boxes): every interior cell of the new boxes takes the value of
  * the old level (old_boxes with their qoff in q_old, host array) where an old box held it, else
  * the conservative space interpolation from q_coarse (level-1, same time), read from the coarse

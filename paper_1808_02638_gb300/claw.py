@@ -58,6 +58,7 @@ _SIGNATURES = {
     "claw_flag_grid_size": ([VP, I32], ctypes.c_longlong),
     "claw_flag_cells": ([VP, I32, VP, ctypes.c_double, VP, VP], ctypes.c_int),
     "claw_regrid_boxes": ([VP, I32, I32, VP, I32, I32, ctypes.c_double, I32, VP, I32], ctypes.c_int),
+    "claw_cluster_flags": ([I32, I32, I32, VP, I32, VP, I32, I32, ctypes.c_double, I32, VP, I32], ctypes.c_int),
     "claw_regrid_transfer": ([VP, I32, VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_reflux_count": ([VP, I32], ctypes.c_int),
     "claw_reflux_buffer_size": ([VP, I32], ctypes.c_int),
@@ -171,21 +172,39 @@ def claw_flag_cells(ctx, level, q, tol, flags, stream=None):
     _check("claw_flag_cells", load().claw_flag_cells(ctx, level, _ptr(q), float(tol), _ptr(flags), _stream(stream)))
 
 
+def _boxes_out(name, f, call):
+    """call(out pointer, capacity) -> count; room for 65536 boxes first, and a grid that makes more
+    (at most one per cell) is clustered again with room for all of them"""
+    import numpy as np
+    for cap in (min(65536, max(16, f.size)), max(16, f.size)):
+        out = np.empty(4 * cap, dtype=np.int32)
+        n = call(out.ctypes.data_as(ctypes.c_void_p), cap)
+        if n != -CLAW_ENOMEM:
+            break
+    if n < 0:
+        raise ClawError(name, -n)
+    return [tuple(int(v) for v in out[4 * k:4 * k + 4]) for k in range(n)]
+
+
 def claw_regrid_boxes(ctx, level, run, flags_host, buffer, nest, cutoff, max_size):
     """new (ilo, jlo, nx, ny) boxes of level+1 for one run from its host flag grid (numpy uint8)"""
     import numpy as np
     f = np.ascontiguousarray(flags_host, dtype=np.uint8)
-    # room for 65536 boxes first; a grid that makes more (at most one per cell) is clustered again
-    # with room for all of them
-    for cap in (min(65536, max(16, f.size)), max(16, f.size)):
-        out = np.empty(4 * cap, dtype=np.int32)
-        n = load().claw_regrid_boxes(ctx, level, run, f.ctypes.data_as(ctypes.c_void_p), int(buffer), int(nest),
-                                     float(cutoff), int(max_size), out.ctypes.data_as(ctypes.c_void_p), cap)
-        if n != -CLAW_ENOMEM:
-            break
-    if n < 0:
-        raise ClawError("claw_regrid_boxes", -n)
-    return [tuple(int(v) for v in out[4 * k:4 * k + 4]) for k in range(n)]
+    return _boxes_out("claw_regrid_boxes", f, lambda out, cap: load().claw_regrid_boxes(
+        ctx, level, run, f.ctypes.data_as(ctypes.c_void_p), int(buffer), int(nest), float(cutoff), int(max_size),
+        out, cap))
+
+
+def claw_cluster_flags(nx, ny, ratio, cover, flags_host, buffer, nest, cutoff, max_size):
+    """the same clustering without a context: cover = the level's (ilo, jlo, nx, ny) boxes"""
+    import numpy as np
+    f = np.ascontiguousarray(flags_host, dtype=np.uint8)
+    arr = (claw_box * max(1, len(cover)))()
+    for k, (i0, j0, bx, by) in enumerate(cover):
+        arr[k].ilo, arr[k].jlo, arr[k].nx, arr[k].ny = int(i0), int(j0), int(bx), int(by)
+    return _boxes_out("claw_cluster_flags", f, lambda out, cap: load().claw_cluster_flags(
+        int(nx), int(ny), int(ratio), ctypes.cast(arr, ctypes.c_void_p), len(cover), f.ctypes.data_as(ctypes.c_void_p),
+        int(buffer), int(nest), float(cutoff), int(max_size), out, cap))
 
 
 def claw_regrid_transfer(ctx, level, old_boxes, q_old, q_new, q_coarse, stream=None):

@@ -1751,13 +1751,24 @@ int claw_flag_cells(claw_ctx* ctx, int32_t L, const double* q, double tol, uint8
 int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flags, int32_t buffer, int32_t nest,
                       double cutoff, int32_t max_size, int32_t* boxes, int32_t max_boxes)
 {
-    if (!ctx || L < 0 || L + 1 >= CLAW_MAXLEV || run < 0 || run >= ctx->nruns || !flags || buffer < 0 || nest < 0 ||
-        !(cutoff > 0.0 && cutoff <= 1.0) || max_size < 1 || max_boxes < 0 || (max_boxes > 0 && !boxes))
-        return -CLAW_EINVAL;
+    if (!ctx || L < 0 || L + 1 >= CLAW_MAXLEV || run < 0 || run >= ctx->nruns) return -CLAW_EINVAL;
     if (!ctx->set[L]) return -CLAW_ESTATE;
     const claw_problem& p = ctx->runs[run];
     if (L + 1 >= p.nlev) return -CLAW_EINVAL;
-    const int NX = level_nx(p, L), NY = level_ny(p, L), r = p.ratio[L + 1];
+    std::vector<claw_box> cover;
+    for (const claw_box& b : ctx->lev[L].boxes)
+        if (b.run == run) cover.push_back(b);
+    return claw_cluster_flags(level_nx(p, L), level_ny(p, L), p.ratio[L + 1], cover.data(), (int32_t)cover.size(),
+                              flags, buffer, nest, cutoff, max_size, boxes, max_boxes);
+}
+
+int claw_cluster_flags(int32_t NX, int32_t NY, int32_t r, const claw_box* cover, int32_t ncover, const uint8_t* flags,
+                       int32_t buffer, int32_t nest, double cutoff, int32_t max_size, int32_t* boxes,
+                       int32_t max_boxes)
+{
+    if (NX < 1 || NY < 1 || r < 1 || ncover < 0 || (ncover > 0 && !cover) || !flags || buffer < 0 || nest < 0 ||
+        !(cutoff > 0.0 && cutoff <= 1.0) || max_size < 1 || max_boxes < 0 || (max_boxes > 0 && !boxes))
+        return -CLAW_EINVAL;
     if ((long long)(NX + 1) * (NY + 1) >= (1LL << 31)) return -CLAW_EINVAL;
     buffer = std::min(buffer, std::max(NX, NY));   // wider reaches change nothing
     nest = std::min(nest, std::max(NX, NY));
@@ -1813,8 +1824,8 @@ int claw_regrid_boxes(claw_ctx* ctx, int32_t L, int32_t run, const uint8_t* flag
     const int cj0 = std::max(0, wj0 - nest), cj1 = std::min(NY, wj1 + nest);
     const int CX = ci1 - ci0, CY = cj1 - cj0;
     cov.assign((size_t)CX * CY, 0);
-    for (const claw_box& b : ctx->lev[L].boxes) {
-        if (b.run != run) continue;
+    for (int k = 0; k < ncover; ++k) {
+        const claw_box& b = cover[k];
         const int x0 = std::max(ci0, b.ilo), x1 = std::min(ci1, b.ilo + b.nx);
         const int y0 = std::max(cj0, b.jlo), y1 = std::min(cj1, b.jlo + b.ny);
         for (int j = y0; j < y1; ++j) std::memset(&cov[(size_t)(j - cj0) * CX + (x0 - ci0)], 1, std::max(0, x1 - x0));
