@@ -55,9 +55,10 @@ def _hier(run, q, reflux):
                            [inputs.const_pool(l, 4.0) for l in run.levels], reflux=reflux)
 
 
-@pytest.mark.parametrize("nlev,ncoarse", [(2, 8), (3, 2)])
-def test_reflux_conserves_the_composite_integral_on_a_periodic_domain(orc, nlev, ncoarse):
-    run = inputs.Run(*inputs.PULSE_DOMAIN, bc=(1, 1, 1, 1))
+@pytest.mark.parametrize("nlev,ncoarse,limiter", [(2, 8, 4), (3, 2, 4), (2, 6, 3), (2, 6, 1), (2, 6, 2)])
+def test_reflux_conserves_the_composite_integral_on_a_periodic_domain(orc, nlev, ncoarse, limiter):
+    # MC, and van Leer (the benchmark's limiter), minmod and superbee
+    run = inputs.Run(*inputs.PULSE_DOMAIN, bc=(1, 1, 1, 1), limiter=limiter)
     annuli, seeds = [(0.2, 0.45), (0.25, 0.35)][:nlev - 1], [2002, 2003][:nlev - 1]
     run.levels = inputs.amr_levels(run, 32, 4, annuli, seeds)
     q0 = _flowing_pulse(run)
