@@ -26,6 +26,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# the problem both arms time (the GPU arm adds its launch, the reference arm its sample)
+WORKLOAD = ("2048x2048 cells on [-1,1]^2 as 4096 patches of 32x32 (+2 ghost layers), radial pulse, rho=1, "
+            "K=4, MC limiter, transverse corrections, same-level ghosts, extrapolation boundaries, Eq. cfl "
+            "time step")
 METRIC = "FP64 cell-updates/s fused-batched vs plain per-patch launch; % of HBM peak"
 UNIT = "cell-updates/s"
 N_CELLS = 2048 * 2048
@@ -275,9 +279,10 @@ def run_reference(args, rank: int, world: int):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "2048x2048 radial pulse as 4096 32x32 patches, rho=1, K=4, MC, "
-                                   "transverse on, one level-step per step (bounded sample)",
-                       "parallelism": f"{workers} host processes"},
+            "config": {"workload": WORKLOAD, "global_batch": N_CELLS,
+                       "parallelism": f"{workers} host processes",
+                       "launch": f"the C oracle on {npatch} of the 4096 patches per step (a bounded sample of "
+                                 f"the level-step; ghosts filled, the same input each step)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                              "sample": f"{npatch} of the 4096 patches per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -439,12 +444,11 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "2048x2048 cells on [-1,1]^2 as 4096 patches of 32x32 (+2 ghost layers), "
-                               "radial pulse, rho=1, K=4, MC limiter, transverse corrections, same-level "
-                               "ghosts, device CFL rule, per step one persistent level-step launch "
-                               "(ghosts pulled, Eq. cfl on its last CTA) replayed from a CUDA graph",
+        "config": {"workload": WORKLOAD,
                    "global_batch": world * N_CELLS, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2 (254 MB of q pools per replica)"},
+                   "l2": "inputs larger than L2 (254 MB of q pools per replica)",
+                   "launch": "per step one persistent level-step launch (ghosts pulled, Eq. cfl on its last "
+                             "CTA) replayed from a CUDA graph"},
         "step": "one CUDA-graph replay of the persistent level-step launch (all 4096 patches, each tile's "
                 "ghosts pulled from their source cells, Eq. cfl on the last CTA)",
         "ghosts": "pulled by the step kernel from their source cells (no ghost-copy launch)",
