@@ -53,3 +53,16 @@ def test_clustering_argument_errors():
     with pytest.raises(claw.ClawError):
         claw.claw_cluster_flags(8, 8, 0, [(0, 0, 8, 8)], flags, 1, 1, 0.7, 16)   # ratio 0
     assert claw.claw_cluster_flags(8, 8, 2, [(0, 0, 8, 8)], np.zeros((8, 8), np.uint8), 1, 1, 0.7, 16) == []
+
+
+def test_more_boxes_than_the_first_output_buffer():
+    # a checkerboard with cutoff 1 leaves one box per flagged cell: 131072 boxes, more than the
+    # binding's first output buffer, so the call is repeated with room for every cell
+    from paper_1808_02638_gb300 import build, claw
+    build.build()
+    n = 512
+    jj, ii = np.mgrid[0:n, 0:n]
+    flags = ((ii + jj) % 2 == 0).astype(np.uint8)
+    got = claw.claw_cluster_flags(n, n, 2, [(0, 0, n, n)], flags, 0, 0, 1.0, 1024)
+    assert len(got) == n * n // 2 > 65536
+    assert sorted(got) == sorted((2 * int(i), 2 * int(j), 2, 2) for j, i in zip(*np.nonzero(flags)))
