@@ -53,6 +53,8 @@ def dilate(flags, buffer):
     NY, NX = flags.shape
     for dj in range(-buffer, buffer + 1):
         for di in range(-buffer, buffer + 1):
+            if abs(dj) >= NY or abs(di) >= NX:   # the shifted grid lies outside the domain
+                continue
             src = flags[max(0, -dj):NY - max(0, dj), max(0, -di):NX - max(0, di)]
             out[max(0, dj):NY - max(0, -dj), max(0, di):NX - max(0, -di)] |= src
     return out
@@ -69,6 +71,8 @@ def nest_mask(lev, nest):
     NY, NX = cov.shape
     for dj in range(-nest, nest + 1):
         for di in range(-nest, nest + 1):
+            if abs(dj) >= NY or abs(di) >= NX:   # all outside the domain: covered
+                continue
             sh = np.ones_like(cov)   # outside the domain counts as covered
             sh[max(0, -dj):NY - max(0, dj), max(0, -di):NX - max(0, di)] = \
                 cov[max(0, dj):NY - max(0, -dj), max(0, di):NX - max(0, -di)]

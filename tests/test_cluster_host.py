@@ -66,3 +66,23 @@ def test_more_boxes_than_the_first_output_buffer():
     got = claw.claw_cluster_flags(n, n, 2, [(0, 0, n, n)], flags, 0, 0, 1.0, 1024)
     assert len(got) == n * n // 2 > 65536
     assert sorted(got) == sorted((2 * int(i), 2 * int(j), 2, 2) for j, i in zip(*np.nonzero(flags)))
+
+
+@pytest.mark.parametrize("NX,NY,fill,nest,buffer", [(1, 40, 0.5, 0, 0), (40, 1, 0.5, 1, 2), (17, 23, 1.0, 0, 0),
+                                                     (12, 12, 0.3, 20, 1), (64, 64, 0.02, 1, 30)])
+def test_clustering_degenerate_grids(NX, NY, fill, nest, buffer):
+    # one-cell-wide levels, a fully flagged level, a nesting reach wider than the level and a buffer
+    # wider than it: still the oracle's boxes
+    from oracle import regrid as org
+    from paper_1808_02638_gb300 import build, claw
+    build.build()
+    rng = np.random.default_rng(NX * 100 + NY)
+    flags = rng.random((NY, NX)) < fill
+    cover = [(0, 0, NX, NY)]
+    for cutoff, cap in ((0.7, 8), (1.0, 64), (0.5, 1000)):
+        got = claw.claw_cluster_flags(NX, NY, 2, cover, flags.astype(np.uint8), buffer, nest, cutoff, cap)
+        lev = inputs.Level(NX, NY, 1.0, 1.0, np.array(cover, dtype=np.int32))
+        m = org.nest_mask(lev, nest)
+        f = org.dilate(flags, buffer) & m
+        want = [(2 * i0, 2 * j0, 2 * nx, 2 * ny) for (i0, j0, nx, ny) in org.cluster(f, cutoff, max(1, cap // 2), m)]
+        assert got == want

@@ -167,3 +167,18 @@ def test_regrid_follows_the_flags_and_keeps_nesting(rg):
     # the state keeps stepping
     O.coarse_step()
     assert all(np.isfinite(q).all() for q in O.q)
+
+
+def test_reaches_wider_than_the_level():
+    # a buffer or nesting square wider than the level, clipped to the domain, is the whole level:
+    # one flag grows over everything; one uncovered cell disallows every cell, full coverage none
+    from oracle import regrid as org
+    flags = np.zeros((7, 9), bool)
+    flags[3, 4] = True
+    assert org.dilate(flags, 12).all()
+    full = inputs.Level(9, 7, 1.0, 1.0, np.array([(0, 0, 9, 7)], dtype=np.int32))
+    assert org.nest_mask(full, 15).all()
+    holed = inputs.Level(9, 7, 1.0, 1.0, np.array([(0, 0, 9, 3), (0, 3, 4, 4), (5, 3, 4, 4), (4, 4, 1, 3)],
+                                                  dtype=np.int32))   # cell (4, 3) uncovered
+    assert not org.nest_mask(holed, 15).any()
+    assert org.nest_mask(holed, 0).sum() == 9 * 7 - 1
