@@ -58,3 +58,16 @@ def test_level_tiling_per_level_or_shared():
     assert [Hierarchy.level_tiling(per, L) for L in range(3)] == [(32, 16, 2, 256), (16, 16, 1, 128),
                                                                    (16, 16, 1, 128)]
     assert Hierarchy.level_tiling(SimpleNamespace(tiling=None), 0) is None
+
+
+def test_cell_updates_count_every_level_step():
+    # the metric's unit: one interior cell advanced one step on its level, so a coarse step of a
+    # level-1 box counts r times its cells, of a level-2 box r^2 times
+    from paper_1808_02638_gb300.measure import cell_updates_per_coarse_step
+    from types import SimpleNamespace
+    run = inputs.Run(-1.0, -1.0, 1.0, 1.0)
+    run.levels = [inputs.Level(16, 16, 1.0, 1.0, [(0, 0, 16, 16)]),
+                  inputs.Level(64, 64, 1.0, 1.0, [(8, 8, 16, 8), (24, 8, 8, 8)], 4),
+                  inputs.Level(256, 256, 1.0, 1.0, [(40, 40, 8, 8)], 4)]
+    H = SimpleNamespace(runs=[run, run])
+    assert cell_updates_per_coarse_step(H) == 2 * (256 + 4 * (128 + 64) + 16 * 64)
