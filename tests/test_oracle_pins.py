@@ -501,3 +501,165 @@ def test_splitmix64_published_sequence():
     z = inputs.splitmix64(1234567, 5)
     assert [int(v) for v in z] == [6457827717110365317, 3203168211198807973, 9817491932198370423,
                                    4593380528125082431, 16408922859458223821]
+
+
+# ------------------------------------------------- transverse correction weight (reading 4)
+
+def _split_parts(rho, K, axis):
+    """the acoustics matrix of Sec. 4.1 for direction `axis` (0: A, 1: B) and its positive,
+    negative and absolute parts, from numpy's eigen-decomposition"""
+    Mat = np.zeros((3, 3))
+    Mat[0, 1 + axis] = K
+    Mat[1 + axis, 0] = 1.0 / rho
+    lam, R = np.linalg.eig(Mat)
+    lam, R = lam.real, R.real
+    Ri = np.linalg.inv(R)
+    plus = R @ np.diag(np.maximum(lam, 0.0)) @ Ri
+    minus = R @ np.diag(np.minimum(lam, 0.0)) @ Ri
+    return plus, minus, plus - minus
+
+
+def _scheme_symbol(rho, K, nux, nuy, thx, thy, transverse, cw):
+    """Amplification matrix of the unlimited (Lax-Wendroff) unsplit wave-propagation step with
+    constant coefficients, derived in Fourier space from Eq. wave_form_2d_2nd_order:
+      Q+ = Q - nux (A+ dQ_{i-1/2} + A- dQ_{i+1/2}) - nuy (B+ dQ_{j-1/2} + B- dQ_{j+1/2})
+             - nux (F_{i+1/2} - F_{i-1/2}) - nuy (G_{j+1/2} - G_{j-1/2}),
+    F = 1/2 |A|(I - nux|A|) dQ, the fluctuation D into a cell (A+dQ - cw C from its left edge,
+    A-dQ + cw C from its right edge, C = |A|(I - nux|A|) dQ) split by B+ onto its upper edge
+    and B- onto its lower edge with weight -nux/2 (and x <-> y).  Every edge quantity is
+    written relative to the cell right of / above it; a shift by one cell is a factor e^{i th}."""
+    I3 = np.eye(3)
+    Ap, Am, Aa = _split_parts(rho, K, 0)
+    Bp, Bm, Ba = _split_parts(rho, K, 1)
+    ex, ey = np.exp(1j * thx), np.exp(1j * thy)
+    jxl, jxr = 1 - 1 / ex, ex - 1        # Q_i - Q_{i-1} and Q_{i+1} - Q_i over Q_i
+    jyl, jyr = 1 - 1 / ey, ey - 1
+    Cx = Aa @ (I3 - nux * Aa)
+    Cy = Ba @ (I3 - nuy * Ba)
+    F = 0.5 * Cx * jxl                  # correction flux at the cell's left edge
+    G = 0.5 * Cy * jyl
+    if transverse:
+        D = (Ap - cw * Cx) * jxl + (Am + cw * Cx) * jxr
+        E = (Bp - cw * Cy) * jyl + (Bm + cw * Cy) * jyr
+        F = F - 0.5 * nuy * (Ap @ E / ex + Am @ E)   # from the cells left of and right of the edge
+        G = G - 0.5 * nux * (Bp @ D / ey + Bm @ D)
+    return I3 - nux * (Ap * jxl + Am * jxr) - nuy * (Bp * jyl + Bm * jyr) - nux * jxr * F - nuy * jyr * G
+
+
+def _oracle_amplification(orc, rho, K, dx, dy, dt, Nx, Ny, mx, my, transverse):
+    """one oracle step of e_m cos(phi) and e_m sin(phi), phi = th . (i, j), on a periodic grid;
+    returns the amplification matrix and its spread over the cells"""
+    thx, thy = 2 * np.pi * mx / Nx, 2 * np.pi * my / Ny
+    I, J = np.meshgrid(np.arange(-M, Nx + M), np.arange(-M, Ny + M))
+    phase = thx * I + thy * J
+    rh = padded(Nx, Ny, fill=rho)
+    kk = padded(Nx, Ny, fill=K)
+    G = np.zeros((3, 3), dtype=complex)
+    spread = 0.0
+    for m in range(3):
+        out = []
+        for wave in (np.cos(phase), np.sin(phase)):
+            q = padded(Nx, Ny, 3)
+            q[m] = wave
+            orc.fill_bc(q, (1, 1, 1, 1))
+            qn, _ = orc.step(q, rh, kk, dx, dy, dt, order=2, transverse=transverse, limiter=0)
+            out.append(interior(qn))
+        col = (out[0] + 1j * out[1]) * np.exp(-1j * interior(phase))[None]
+        G[:, m] = col.reshape(3, -1).mean(axis=1)
+        spread = max(spread, np.abs(col - G[:, m][:, None, None]).max())
+    return G, spread, thx, thy
+
+
+@pytest.mark.parametrize("mode", [(1, 1), (3, 2), (5, 4), (7, 5), (2, 6)])
+def test_transverse_correction_weight_fourier_symbol(orc, mode):
+    # With constant rho, K, periodic boundaries and no limiter the step is linear and shift
+    # invariant, so each Fourier mode is multiplied by a 3x3 matrix.  The oracle's matrix,
+    # measured by stepping cos / sin modes, must equal the symbol derived above with the
+    # correction propagated at full weight for transverse = 2 and at zero weight for
+    # transverse = 1; at these parameters the half weight is measurably different.
+    rho, K = 1.7, 3.1
+    c = np.sqrt(K / rho)
+    Nx, Ny = 16, 12
+    dx, dy = 0.1, 0.07
+    dt = 0.5 * dx / c
+    nux, nuy = dt / dx, dt / dy
+    assert nuy * c < 1.0
+    for transverse, cw in ((2, 1.0), (1, 0.0), (0, 0.0)):
+        G, spread, thx, thy = _oracle_amplification(orc, rho, K, dx, dy, dt, Nx, Ny, *mode, transverse)
+        assert spread < 1e-13                      # one mode in, the same mode out
+        want = _scheme_symbol(rho, K, nux, nuy, thx, thy, transverse, cw)
+        assert np.abs(G - want).max() < 1e-13, (transverse, np.abs(G - want).max())
+        if transverse == 2:
+            half = _scheme_symbol(rho, K, nux, nuy, thx, thy, transverse, 0.5)
+            assert np.abs(half - want).max() > 1e-3
+
+
+def test_scheme_symbol_is_second_order_accurate():
+    # the derived symbol against the exact propagator exp(-dt (i kx A + i ky B)) of the
+    # acoustics system: the one-step error falls like h^3 (second order) -- checks the
+    # derivation itself, independently of the oracle
+    from scipy.linalg import expm
+    rho, K = 1.7, 3.1
+    c = np.sqrt(K / rho)
+    kx, ky = 2.0, 1.3
+    A = np.array([[0, K, 0], [1 / rho, 0, 0], [0, 0, 0]])
+    B = np.array([[0, 0, K], [0, 0, 0], [1 / rho, 0, 0]])
+    errs = []
+    for h in (0.02, 0.01, 0.005):
+        dx, dy = h, 0.7 * h
+        dt = 0.5 * dx / c
+        want = expm(-dt * (1j * kx * A + 1j * ky * B))
+        got = _scheme_symbol(rho, K, dt / dx, dt / dy, kx * dx, ky * dy, 2, 1.0)
+        errs.append(np.abs(got - want).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 2.8), rates
+
+
+# ------------------------------------------------- subcycling time fraction (reading 8)
+
+def test_subcycling_time_fraction_exact_on_linear_data(orc):
+    # q linear in x and y solves q_t + A q_x + B q_y = 0 exactly as q(t) = q(0) - t (A qx + B qy)
+    # (constant gradients).  On such data every step of the method is exact up to rounding:
+    # each wave is the same on every edge (theta = 1, MC phi = 1), the correction and transverse
+    # terms are constant and cancel in the update, the minmod slopes of the interpolation are the
+    # gradient, and the time-linear coarse state is exact -- but only at the fine level's own time.
+    # So fine ghosts interpolated at the right fraction of the coarse step leave every fine cell
+    # and every coarse cell away from the (extrapolating) domain edge exact.
+    from oracle.amr import OracleHierarchy
+    r, Nc = 4, 32
+    d = 2.0 / Nc
+    run = inputs.Run(-1.0, -1.0, 1.0, 1.0)
+    L0 = inputs.Level(Nc, Nc, d, d, [(0, 0, Nc, Nc)])
+    L1 = inputs.Level(Nc * r, Nc * r, d / r, d / r, [(48, 52, 24, 20), (72, 52, 16, 28)], ratio=r)
+    run.levels = [L0, L1]
+    rho, K = 1.3, 2.9
+    g = np.array([[0.3, -0.2], [0.05, 0.2], [0.1, -0.15]])      # (p, u, v) x (d/dx, d/dy)
+    q0 = np.array([1.0, 0.1, -0.2])
+    rate = np.array([K * (g[1, 0] + g[2, 1]), g[0, 0] / rho, g[0, 1] / rho])   # A qx + B qy
+
+    def exact(x, y, t):
+        return (q0 - t * rate)[:, None, None] + g[:, 0, None, None] * x + g[:, 1, None, None] * y
+
+    pools = []
+    for lev in run.levels:
+        pool = np.zeros(lev.qsize)
+        for n, b in enumerate(lev.boxes):
+            x, y = inputs.cell_centres(run, lev, b)
+            inputs.box_view(pool, lev.qoff[n], int(b[2]), int(b[3]), 3)[:] = exact(x, y, 0.0)
+        pools.append(pool)
+    H = OracleHierarchy(run, pools, [inputs.const_pool(L, rho) for L in run.levels],
+                        [inputs.const_pool(L, K) for L in run.levels])
+    nsteps = 2
+    for _ in range(nsteps):
+        H.coarse_step()
+    t = float(np.sum(H.dt_history))
+    scale = np.abs(q0).max() + 1.0
+    for n, b in enumerate(L1.boxes):
+        x, y = inputs.cell_centres(run, L1, b)
+        err = np.abs(H.interior(1, n) - interior(exact(x, y, t))).max()
+        assert err < 1e-13 * scale, (n, err)
+    x, y = inputs.cell_centres(run, L0, L0.boxes[0])
+    e = np.abs(H.interior(0, 0) - interior(exact(x, y, t))).max(axis=0)
+    m = 2 * (nsteps + 1)
+    assert e[m:-m, m:-m].max() < 1e-13 * scale
+    assert e.max() > 1e-6           # the extrapolating edge is not exact: the data is not trivial
