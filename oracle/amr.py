@@ -353,9 +353,10 @@ class OracleHierarchy:
             boxes = new_boxes(coarse, self.q[Lf - 1], tol, buffer, cutoff, max_size, nest, old.ratio)
             new = type(old)(old.NX, old.NY, old.dx, old.dy, boxes, old.ratio)   # the caller's level type
             self.q[Lf] = transfer(old, self.q[Lf], new, coarse, self.q[Lf - 1], run.bc)
-            if not self.swe:
-                self.rho[Lf] = np.full(new.csize, float(self.rho[Lf].flat[0]) if self.rho[Lf].size else 1.0)
-                self.K[Lf] = np.full(new.csize, float(self.K[Lf].flat[0]) if self.K[Lf].size else 1.0)
+            if not self.swe:   # uniform medium: the value of level 0's first cell (level 0 keeps its boxes)
+                c0 = int(self.levels[0].coff[0])
+                self.rho[Lf] = np.full(new.csize, float(self.rho[0][c0]))
+                self.K[Lf] = np.full(new.csize, float(self.K[0][c0]))
             self.levels[Lf] = new
         self._iface = {Lf: interface(self.levels, Lf, run.bc) for Lf in range(1, len(self.levels))} \
             if self.reflux else {}

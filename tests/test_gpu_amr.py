@@ -3,6 +3,7 @@ fine-to-coarse averaging and recursive subcycling, and of many independent runs 
 one launch per level-step, against the oracle's AMR driver."""
 import numpy as np
 import pytest
+import torch
 
 from paper_1808_02638_gb300 import inputs
 
@@ -380,6 +381,63 @@ def test_benchmark_analog_paths_agree():
         s = r["sections_s"]
         assert min(s[k] for k in ("advance", "ghost_fill", "regrid", "updating")) > 0.0
         assert abs(sum(v for k, v in s.items() if k != "total") - s["total"]) < 1e-9
+
+
+def _analog_run(base, nlev, ratio):
+    """the benchmark analog's hierarchy (Sec. 4.1-4.2): a base level in 4 x 4 patches, van Leer,
+    outflow boundaries, finer levels empty until the first regrid"""
+    run = inputs.Run(*inputs.PULSE_DOMAIN, limiter=3)
+    d0, st = 2.0 / base, base // 4
+    run.levels = [inputs.Level(base, base, d0, d0, [(i, j, st, st) for j in range(0, base, st)
+                                                     for i in range(0, base, st)])]
+    for L in range(1, nlev):
+        n = base * ratio ** L
+        run.levels.append(inputs.Level(n, n, 2.0 / n, 2.0 / n, np.zeros((0, 4), dtype=np.int32), ratio))
+    return run
+
+
+def test_benchmark_analog_matches_the_oracle():
+    # the benchmark analog's combination at a size the oracle finishes in seconds: 3 levels of
+    # ratio 2, van Leer, the conservation fix on through the regrids, fine levels built at t = 0
+    # by regridding and then set from the initial condition, a regrid every 2 coarse steps with
+    # buffer 2 and cutoff 0.7, and patches capped at 24 fine cells so that clustering splits
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300.solver import Hierarchy
+    base, nlev, ratio, every = 96, 3, 2, 2
+    params = dict(tol=0.01, buffer=every, cutoff=0.7, max_size=24, nest=2)
+    run_g, run_o = _analog_run(base, nlev, ratio), _analog_run(base, nlev, ratio)
+    q0 = [inputs.init_q(run_g, lev) for lev in run_g.levels]
+    H = Hierarchy([run_g], [q0], rho0=1.0, K0=4.0, reflux=True, tiling=((32, 16, 2, 256), (16, 16, 1, 128)))
+    O = OracleHierarchy(run_o, q0, [inputs.const_pool(run_o.levels[0], 1.0)] + [np.ones(1)] * (nlev - 1),
+                        [inputs.const_pool(run_o.levels[0], 4.0)] + [np.full(1, 4.0)] * (nlev - 1), reflux=True)
+
+    def same_boxes():
+        for L in range(1, nlev):
+            assert np.array_equal(run_g.levels[L].boxes, run_o.levels[L].boxes), L
+        assert len(run_g.levels[2].boxes) > 0
+        assert max(int(b[2:].max()) for L in (1, 2) for b in run_g.levels[L].boxes) == 24
+
+    for _ in range(nlev - 1):
+        H.regrid(**params)
+        O.regrid(**params)
+        same_boxes()
+    for L, lev in enumerate(run_g.levels):
+        a = inputs.init_q(run_g, lev)
+        t = H.q[L][H.cur[L]]
+        t.zero_()
+        t[:a.size] = torch.from_numpy(a).to(t.device)
+        O.q[L] = inputs.init_q(run_o, run_o.levels[L])
+    H.init_dt()
+    for k in range(6):
+        H.coarse_step()
+        O.coarse_step()
+        if (k + 1) % every == 0:
+            H.regrid(**params)
+            O.regrid(**params)
+            same_boxes()
+    assert float(H.dt[0]) == pytest.approx(O.dt_history[-1], rel=1e-15)
+    _compare_all_levels(H, O, 0, TOLN)
+    assert H.sync_status() == 0
 
 
 def test_coefficient_ghost_tables_of_a_uniform_medium_on_first_use():

@@ -182,3 +182,18 @@ def test_reaches_wider_than_the_level():
                                                   dtype=np.int32))   # cell (4, 3) uncovered
     assert not org.nest_mask(holed, 15).any()
     assert org.nest_mask(holed, 0).sum() == 9 * 7 - 1
+
+
+def test_regrid_of_an_initially_empty_level_takes_the_uniform_medium_of_level_0():
+    # a level that starts without boxes has no coefficient value of its own: the regrid gives
+    # the new boxes the uniform medium of the base level
+    from oracle.amr import OracleHierarchy
+    run = inputs.Run(*inputs.PULSE_DOMAIN)
+    run.levels = [inputs.Level(32, 32, 2 / 32, 2 / 32, [(0, 0, 32, 32)]),
+                  inputs.Level(64, 64, 2 / 64, 2 / 64, np.zeros((0, 4), dtype=np.int32), 2)]
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    O = OracleHierarchy(run, q0, [inputs.const_pool(run.levels[0], 1.7), np.zeros(32)],
+                        [inputs.const_pool(run.levels[0], 3.1), np.zeros(32)])
+    O.regrid(tol=0.02, buffer=2, cutoff=0.7, max_size=64)
+    assert len(run.levels[1].boxes) > 0
+    assert np.all(O.rho[1] == 1.7) and np.all(O.K[1] == 3.1)
