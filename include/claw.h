@@ -129,6 +129,17 @@ int claw_set_level(claw_ctx* ctx, int32_t level, const claw_box* boxes, int32_t 
 int claw_set_tiling(claw_ctx* ctx, int32_t level, int32_t tx, int32_t ty, int32_t staging,
                     int32_t threads);
 
+/* Failure detection of the staged level-steps (no counterpart in the paper).  With staging 1
+ * or 2 a CTA waits on a shared-memory barrier for the bulk copy of each tile; the wait polls
+ * the barrier at most `polls` times (default 2^22, far beyond a normal copy).  When it gives
+ * up, the CTA records CLAW_ETIMEOUT in the device flag (read by claw_sync_status), waits again
+ * with the default bound for every copy it has issued (so that none lands after it exits),
+ * and stops without writing its remaining tiles: the new state of that step is incomplete.
+ * polls = 0 makes every staged CTA give up at its first tile, which is how the error path is
+ * tested.  Applies to the level-step calls issued after it on this context.
+ * Errors: CLAW_EINVAL (ctx NULL).  Host only, no device work. */
+int claw_set_wait_limit(claw_ctx* ctx, uint32_t polls);
+
 /* Per-cell coefficient planes for medium = 1 from one-plane pools rho, K (ghosts included):
  * aux holds, for every cell, Z = sqrt(K rho), c = sqrt(K/rho), K, c^2, 1/(Z_W+Z) and the
  * two wave-limiter projection factors of the edge to the west, and the same three for the

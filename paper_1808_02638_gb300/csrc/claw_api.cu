@@ -60,6 +60,7 @@ struct claw_ctx {
     std::atomic<long long> launches{0};
     bool tma_ok[CLAW_MAXLEV] = {};
     DevArena scratch;   // the transfer tables of a regrid
+    unsigned wait_polls = kWaitPolls;   // first-wait bound of the staged step kernels
 };
 
 namespace {
@@ -852,6 +853,7 @@ StepArgs make_args(claw_ctx* ctx, int L, const double* q_old, double* q_new, con
     a.K0 = ctx->K0;
     a.grav = ctx->grav;
     a.swe = ctx->kind() == KIND_SWE;
+    a.wait_polls = ctx->wait_polls;
     return a;
 }
 
@@ -1313,6 +1315,13 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         ctx->set[L] = false;
         return rc;
     }
+    return CLAW_OK;
+}
+
+int claw_set_wait_limit(claw_ctx* ctx, uint32_t polls)
+{
+    if (!ctx) return CLAW_EINVAL;
+    ctx->wait_polls = polls;
     return CLAW_OK;
 }
 

@@ -165,6 +165,9 @@ __host__ __device__ inline int ring_index(int xp, int yp, int nx, int ny)   // -
     return -1;
 }
 
+// default bound of a bounded mbarrier wait (polls; far beyond a normal copy)
+constexpr unsigned kWaitPolls = 1u << 22;
+
 struct StepArgs {
     const PatchDev* patches = nullptr;
     const TileDev* tiles = nullptr;
@@ -190,6 +193,9 @@ struct StepArgs {
     const double* cflv = nullptr;       // desired CFL per run
     unsigned int* done = nullptr;       // CTA completion counter (0 between launches)
     int nruns = 0;
+    // polls of a tile's first wait for its bulk copy before the CTA reports ERR_TIMEOUT; the
+    // copies still in flight are then awaited with the full bound kWaitPolls before it exits
+    unsigned wait_polls = kWaitPolls;
 };
 
 // error flag bits written by kernels

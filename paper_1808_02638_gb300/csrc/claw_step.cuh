@@ -163,10 +163,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, 
         : "memory");
 }
 
-// bounded wait: gives up after ~2^22 polls (well beyond a normal copy), reports a timeout
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity)
+// bounded wait: gives up after `polls` polls and reports it; never spins without a limit
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned polls = kWaitPolls)
 {
-    for (int it = 0; it < (1 << 22); ++it)
+    for (unsigned it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -334,11 +335,13 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
             // each buffer's barrier completes once per use: every other tile with two buffers,
             // every tile with one
             const unsigned par = STAGE == 1 ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1);
-            bool ok = mbar_wait_bounded(&bar[b], par);
-            if (__syncthreads_or(!ok)) {   // a copy never landed: report and stop this CTA
+            bool ok = mbar_wait_bounded(&bar[b], par, A.wait_polls);
+            if (__syncthreads_or(!ok)) {   // the copy is late or lost: report and stop this CTA
                 if (tid == 0) {
                     atomicOr(A.err, ERR_TIMEOUT);
-                    // let the prefetch in flight (if any) land before the CTA exits
+                    // no copy may land in this CTA's shared memory after it exits: wait, with the
+                    // full bound, for this tile's own copy and for the prefetch of the next one
+                    mbar_wait_bounded(&bar[b], par);
                     if (STAGE == 1 && tn < A.ntiles)
                         mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
                     finish_cta(A);   // keeps the completion count consistent

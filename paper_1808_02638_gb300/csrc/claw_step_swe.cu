@@ -165,10 +165,12 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
         if (STAGE) {
             const int tn = t + gridDim.x;
             if (tid == 0 && tn < A.ntiles) issue(tn, b ^ 1);
-            bool ok = mbar_wait_bounded(&bar[b], (unsigned)((it >> 1) & 1));
-            if (__syncthreads_or(!ok)) {
+            const unsigned par = (unsigned)((it >> 1) & 1);
+            bool ok = mbar_wait_bounded(&bar[b], par, A.wait_polls);
+            if (__syncthreads_or(!ok)) {   // late or lost copy: report, drain what is in flight, stop
                 if (tid == 0) {
                     atomicOr(A.err, ERR_TIMEOUT);
+                    mbar_wait_bounded(&bar[b], par);
                     if (tn < A.ntiles) mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
                     finish_cta(A);
                 }
