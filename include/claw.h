@@ -24,6 +24,11 @@
  *     device.  The library owns only its own tables, allocated in claw_set_level.
  *   - Every call that takes a stream enqueues work on it and returns without waiting; it
  *     launches no kernel when it returns an error.  Calls on one context are not thread-safe.
+ *   - Launches may be captured into CUDA graphs.  A staged level-step reads tensor-map
+ *     descriptors of its q_old pool that the context builds on first use outside a capture and
+ *     caches per pool; a descriptor that a capture has seen is kept until the level's tables
+ *     are rebuilt (claw_set_level, a tile-shape change in claw_set_tiling), so a graph stays
+ *     valid until then.
  *   - Errors are status codes (never aborts or traps).  Errors found on the device (NaN or
  *     Inf in a new state, a CFL number above 1, a bounded wait that expired) are recorded in
  *     a device flag and reported by claw_sync_status.
@@ -292,12 +297,39 @@ int claw_level_step_adjoint(claw_ctx* ctx, int32_t level, const double* q_old, c
  * entry in the level's ghost ring, u or v negated across a wall), which is what
  * claw_fill_ghost_adjoint's copy part would do with it; those ghosts of lam_old stay zero.
  * Ghosts interpolated from the coarser level keep their adjoint for
- * claw_fill_ghost_interp_adjoint.  The same linear map as step adjoint + ghost-fill adjoint,
- * summed in another order (FP64 atomics).  Errors: as claw_level_step_adjoint; CLAW_EINVAL for
+ * claw_fill_ghost_interp_adjoint.  Like the forward claw_level_advance with pulled ghosts, the
+ * kernel reads those same-level and boundary ghosts of q_old from their source cells, so only
+ * the interpolated ghosts of q_old need to be filled (a state written by a pulled-ghost step
+ * and then claw_fill_ghost_interp is enough).  The same linear map as step adjoint +
+ * ghost-fill adjoint, summed in another order (FP64 atomics).  Errors: as claw_level_step_adjoint; CLAW_EINVAL for
  * an unknown flag or a level without a ghost ring. */
 int claw_level_advance_adjoint(claw_ctx* ctx, int32_t level, const double* q_old, const double* lam_new,
                                double* lam_old, const double* aux, double* g_aux, const double* dt,
                                int32_t flags, void* stream);
+
+/* Differentiation by tape (no counterpart in the paper, which has no adjoint; the map
+ * differentiated is the level-step of Eq. wave_form_2d_2nd_order, Sec. 2.1).
+ * claw_level_advance_record is claw_level_advance (flags: CLAW_ADVANCE_PULL_GHOSTS and
+ * CLAW_ADVANCE_UPDATE_DT, with that call's meaning; without the pull every ghost of q_old must be
+ * filled) that also writes the step's intermediates to `tape`, a device
+ * buffer of CLAW_NAUX * coff-layout doubles (the size of the level's aux pool, owned by the
+ * caller): per padded cell, the normal-solver wave strengths and limited strengths of the
+ * edges west and south of the cell (the limiter's branch kept in the three lowest mantissa
+ * bits of the limited strength) and the cell's transverse fluctuation pressures.  The new state
+ * is the one claw_level_advance computes.  Cell-wise medium (medium = 1), order 2 (and a ghost
+ * ring for pulled ghosts).  Errors: CLAW_EINVAL, CLAW_ESTATE, CLAW_ECUDA. */
+int claw_level_advance_record(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
+                              const double* aux, double* dt, double* smax, int32_t flags, double* tape,
+                              void* stream);
+
+/* The adjoint of the recorded step from its tape alone (no q_old, no re-run of the forward):
+ * the same map as claw_level_advance_adjoint (flags: 0 or CLAW_ADVANCE_PULL_GHOSTS, with that
+ * call's meaning), accumulating (+=) into lam_old and g_aux (aux layout, the c^2 plane folded into
+ * c), dt frozen at the recorded step's.  The limiter branches are the recorded ones.  Cell-wise
+ * medium, order 2.  Errors: CLAW_EINVAL, CLAW_ESTATE, CLAW_ECUDA. */
+int claw_level_advance_adjoint_tape(claw_ctx* ctx, int32_t level, const double* tape, const double* lam_new,
+                                    double* lam_old, const double* aux, double* g_aux, const double* dt,
+                                    int32_t flags, void* stream);
 
 /* Reverse of claw_fill_ghost: every ghost adjoint of lam is added to the adjoint of its
  * source (a box interior of the level, or through the interpolation to lam_c_old /

@@ -78,9 +78,172 @@ def _reverse(H, node, lam, g_aux, lam_cold=None, lam_cnew=None):
     lam[L] = lam_in
 
 
+def _records_ok(H):
+    """whether the reverse can run from recorded step tapes (claw_level_advance_record): a
+    cell-wise medium and second order"""
+    return H.medium == 1 and all(r.order == 2 for r in H.runs)
+
+
+class _Tape:
+    """Device buffers of the level-steps of `ncoarse` coarse steps, kept per level in time
+    order: state(L, i) is the input of the i-th step of level L in the segment and
+    state(L, N_L) the level's state after the last one; pre[L][i] is what the i-th step of a
+    level with a finer one wrote before the finer level's average went into it (the coarse
+    "new" state of the space-time interpolation); dt[k] is the time step of coarse step k.
+    With `record`, rec[L][i] receives the i-th step's intermediates (claw_level_advance_record),
+    the reverse reads those instead of the states, and the finest level's states (which only
+    its own next step reads) live in two buffers.  A segment's recompute and its reverse only
+    ever touch these buffers (and the hierarchy's dt, smax, medium planes and the adjoint
+    buffers), so one CUDA graph replays any segment."""
+
+    def __init__(self, H, ncoarse, record=False):
+        self.n = ncoarse
+        self.record = record
+        counts = [ncoarse]
+        for L in range(1, H.nlev):
+            counts.append(counts[-1] * H.ratio(L))
+        self.counts = counts
+        nstate = [2 if record and L + 1 == H.nlev else counts[L] + 1 for L in range(H.nlev)]
+        self.states = [[torch.zeros_like(H.q[L][0]) for _ in range(nstate[L])] for L in range(H.nlev)]
+        self.pre = [[torch.zeros_like(H.q[L][0]) for _ in range(counts[L])] if L + 1 < H.nlev else []
+                    for L in range(H.nlev)]
+        self.rec = [[torch.empty_like(H.aux[L]) for _ in range(counts[L])] if record else []
+                    for L in range(H.nlev)]
+        self.dt = torch.zeros((ncoarse, H.nruns), dtype=torch.float64, device=H.dev)
+
+    def state(self, L, i):
+        return self.states[L][i % len(self.states[L])]
+
+
+def _record(H, T, L, i, cold=None, cnew=None, tau=0.0):
+    """the i-th step of level L of the tape (and its finer substeps), with the launches of
+    Hierarchy.advance: the interpolated ghosts filled, the others pulled by the step (or, on a
+    level the autotuner keeps on the copy launch, all filled)"""
+    q = T.state(L, i)
+    fine = L + 1 < H.nlev
+    dst = T.pre[L][i] if fine else T.state(L, i + 1)
+    if T.record:   # the level's own ghost launch choice, as in the forward
+        if H.pull_levels[L]:
+            if L:
+                claw.claw_fill_ghost_interp(H.ctx, L, q, cold, cnew, tau)
+            claw.claw_level_advance_record(H.ctx, L, q, dst, H.aux[L], H.dt, H.smax, claw.CLAW_ADVANCE_PULL_GHOSTS,
+                                           T.rec[L][i])
+        else:
+            claw.claw_fill_ghost(H.ctx, L, q, cold, cnew, tau)
+            claw.claw_level_advance_record(H.ctx, L, q, dst, H.aux[L], H.dt, H.smax, 0, T.rec[L][i])
+    elif H.pull_levels[L]:
+        if L:
+            claw.claw_fill_ghost_interp(H.ctx, L, q, cold, cnew, tau)
+        claw.claw_level_advance(H.ctx, L, q, dst, H.aux[L], H.dt, H.smax, claw.CLAW_ADVANCE_PULL_GHOSTS)
+    else:
+        claw.claw_fill_ghost(H.ctx, L, q, cold, cnew, tau)
+        claw.claw_level_step(H.ctx, L, q, dst, H.aux[L], H.dt, H.smax)
+    if fine:
+        r = H.ratio(L + 1)
+        for k in range(r):
+            _record(H, T, L + 1, i * r + k, q, dst, k / r)
+        nxt = T.state(L, i + 1)
+        nxt.copy_(dst)
+        claw.claw_average_down(H.ctx, L + 1, T.state(L + 1, (i + 1) * r), nxt)
+
+
+def _record_coarse(H, T, k, frozen):
+    T.dt[k].copy_(H.dt)
+    _record(H, T, 0, k)
+    if frozen:
+        H.smax.zero_()
+    else:
+        claw.claw_dt_update(H.ctx, 0, H.smax, H.dt)
+
+
+def _reverse_tape(H, T, L, i, lam, lbuf, g_aux, lam_cold=None, lam_cnew=None, tau=0.0, cold=None, cnew=None):
+    """adjoint of the i-th step of level L of the tape (and its substeps): lam[L] holds the
+    adjoint of the level's state after the step and becomes that of the state before it, in the
+    other buffer of lbuf[L]; the interpolation adjoint of the step's ghosts goes to lam_cold /
+    lam_cnew (the coarser level's old and pre-average new states)."""
+    lam_pre = lam[L]
+    lam_in = lbuf[L][1] if lam_pre is lbuf[L][0] else lbuf[L][0]
+    lam_in.zero_()
+    q = T.state(L, i)
+    if L + 1 < H.nlev:
+        r = H.ratio(L + 1)
+        # averaging: covered coarse adjoints move to the fine state and are zeroed
+        claw.claw_average_down_adjoint(H.ctx, L + 1, lam[L + 1], lam_pre)
+        for k in reversed(range(r)):
+            _reverse_tape(H, T, L + 1, i * r + k, lam, lbuf, g_aux, lam_in, lam_pre, k / r, q, T.pre[L][i])
+    if T.record:
+        claw.claw_level_advance_adjoint_tape(H.ctx, L, T.rec[L][i], lam_pre, lam_in, H.aux[L], g_aux[L], H.dt,
+                                             claw.CLAW_ADVANCE_PULL_GHOSTS)
+    else:
+        claw.claw_level_advance_adjoint(H.ctx, L, q, lam_pre, lam_in, H.aux[L], g_aux[L], H.dt,
+                                        claw.CLAW_ADVANCE_PULL_GHOSTS)
+    if L:
+        claw.claw_fill_ghost_interp_adjoint(H.ctx, L, lam_in, lam_cold, lam_cnew, cold, cnew, tau)
+    lam[L] = lam_in
+
+
+def _reverse_coarse(H, T, k, lam, lbuf, g_aux):
+    H.dt.copy_(T.dt[k])   # frozen forward time step
+    _reverse_tape(H, T, 0, k, lam, lbuf, g_aux)
+
+
+def _replayable(H, key, body):
+    """a CUDA graph of body() cached on the hierarchy under `key` (the hierarchy drops its graphs
+    when its levels or tilings change); body runs once eagerly before the capture (first-use
+    tables and kernel attributes)"""
+    cache = H.__dict__.setdefault("_graphs", {})
+    if key not in cache:
+        body()
+        s = torch.cuda.Stream(device=H.dev)
+        s.wait_stream(torch.cuda.current_stream(H.dev))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            body()
+        torch.cuda.current_stream(H.dev).wait_stream(s)
+        cache[key] = g
+    return cache[key]
+
+
+def _buffers(H, key, make):
+    cache = H.__dict__.setdefault("_graph_buffers", {})
+    if key not in cache:
+        cache[key] = make()
+    return cache[key]
+
+
+def _forward_segment(H, n, graphs):
+    """n coarse steps of the hierarchy (a CUDA graph when `graphs`); every level's state ends in
+    the buffer it started in"""
+    cur0 = list(H.cur)
+
+    def body():
+        for _ in range(n):
+            H.coarse_step()
+        for L in range(H.nlev):
+            if H.cur[L] != cur0[L]:
+                H.q[L][cur0[L]].copy_(H.q[L][H.cur[L]])
+                H.cur[L] = cur0[L]
+
+    if not graphs:
+        body()
+        return
+    key = ("fwd", n, H.freeze_dt, tuple(cur0))
+    if key in H.__dict__.get("_graphs", {}):
+        H._graphs[key].replay()
+        return
+    state = [[a.clone() for a in p] for p in H.q], H.dt.clone(), H.smax.clone()
+    g = _replayable(H, key, body)   # ran the body twice (eager and captured): put the state back
+    for L in range(H.nlev):
+        for b in range(2):
+            H.q[L][b].copy_(state[0][L][b])
+    H.dt.copy_(state[1])
+    H.smax.copy_(state[2])
+    g.replay()
+
+
 class _Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, H, ncoarse, every, nlev, dt, *tensors):
+    def forward(ctx, H, ncoarse, every, nlev, dt, graphs, records, *tensors):
         q0 = tensors[:nlev]
         rho = tensors[nlev:2 * nlev] if H.medium else [None] * nlev
         K = tensors[2 * nlev:3 * nlev] if H.medium else [None] * nlev
@@ -100,8 +263,9 @@ class _Rollout(torch.autograd.Function):
             else:   # time steps frozen at the caller's values (e.g. for finite differences)
                 H.freeze_dt = True
                 H.dt.copy_(dt)
-            checkpoints, tapes = [], None
-            if every is None:   # the whole tape, recorded as the rollout runs
+            frozen = H.freeze_dt
+            checkpoints, tapes, tape = [], None, None
+            if every is None and not H.pull:   # the whole tape, recorded as the rollout runs
                 tapes = []
                 for n in range(ncoarse):
                     dt_n = H.dt.clone()
@@ -110,50 +274,64 @@ class _Rollout(torch.autograd.Function):
                         H.smax.zero_()
                     else:
                         claw.claw_dt_update(H.ctx, 0, H.smax, H.dt)
+            elif every is None:   # the whole rollout as one tape, recorded as it runs
+                tape = _Tape(H, ncoarse)
+                for L in range(nlev):
+                    tape.state(L, 0).copy_(H.q[L][H.cur[L]])
+                for k in range(ncoarse):
+                    _record_coarse(H, tape, k, frozen)
+                for L in range(nlev):
+                    H.q[L][H.cur[L]].copy_(tape.state(L, tape.counts[L]))
             else:
-                for n in range(ncoarse):
-                    if n % every == 0:
-                        checkpoints.append(([H.q[L][H.cur[L]].clone() for L in range(nlev)], H.dt.clone()))
-                    H.coarse_step()
+                for s0 in range(0, ncoarse, every):
+                    checkpoints.append(([H.q[L][H.cur[L]].clone() for L in range(nlev)], H.dt.clone()))
+                    if H.pull:
+                        _forward_segment(H, min(every, ncoarse - s0), graphs)
+                    else:
+                        for _ in range(min(every, ncoarse - s0)):
+                            H.coarse_step()
             out = [H.q[L][H.cur[L]].clone() for L in range(nlev)]
         ctx.H, ctx.ncoarse, ctx.every, ctx.nlev = H, ncoarse, every, nlev
         ctx.checkpoints = checkpoints
         ctx.tapes = tapes
-        ctx.frozen = dt is not None
+        ctx.tape = tape
+        ctx.frozen = frozen
+        ctx.graphs = graphs
+        ctx.records = records
         H.freeze_dt = False
         return tuple(out)
 
     @staticmethod
     def backward(ctx, *grads):
         H, nlev, every, ncoarse = ctx.H, ctx.nlev, ctx.every, ctx.ncoarse
-        lam = [g.clone() if g is not None else torch.zeros_like(H.q[L][0]) for L, g in enumerate(grads)]
-        g_aux = [torch.zeros_like(H.aux[L]) if H.medium else None for L in range(nlev)]
-        if ctx.tapes is not None:
-            for node, dt in reversed(ctx.tapes):
-                H.dt.copy_(dt)   # frozen forward time step
-                _reverse(H, node, lam, g_aux)
-            ctx.tapes = None
-        nseg = len(ctx.checkpoints)
-        for s in reversed(range(nseg)):
-            states, dt0 = ctx.checkpoints[s]
-            n0, n1 = s * every, min((s + 1) * every, ncoarse)
-            # recompute the segment, recording each coarse step
-            for L in range(nlev):
-                H.cur[L] = 0
-                H.q[L][0].copy_(states[L])
-            H.dt.copy_(dt0)
-            tapes = []
-            for _ in range(n0, n1):
-                dt = H.dt.clone()
-                tapes.append((_advance_record(H, 0, None, None, 0.0), dt))
-                if ctx.frozen:
-                    H.smax.zero_()
+        if not H.pull:
+            g_aux = [torch.zeros_like(H.aux[L]) if H.medium else None for L in range(nlev)]
+            lam = [g.clone() if g is not None else torch.zeros_like(H.q[L][0]) for L, g in enumerate(grads)]
+            _backward_filled(ctx, H, lam, g_aux)
+        else:
+            # the adjoint and medium-adjoint buffers are the hierarchy's, so that the graphs of
+            # the reverse sweep can be replayed by later gradients
+            g_aux = _buffers(H, "g_aux", lambda: [torch.zeros_like(H.aux[L]) if H.medium else None
+                                                  for L in range(nlev)])
+            for g in g_aux:
+                if g is not None:
+                    g.zero_()
+            lbuf = _buffers(H, "lam", lambda: [(torch.zeros_like(H.q[L][0]), torch.zeros_like(H.q[L][0]))
+                                                for L in range(nlev)])
+            for L, g in enumerate(grads):
+                if g is None:
+                    lbuf[L][0].zero_()
                 else:
-                    claw.claw_dt_update(H.ctx, 0, H.smax, H.dt)
-            for node, dt in reversed(tapes):
-                H.dt.copy_(dt)   # frozen forward time step
-                _reverse(H, node, lam, g_aux)
-        grads_out = [None, None, None, None, None] + lam
+                    lbuf[L][0].copy_(g)
+            if ctx.tape is not None:   # the recorded tape: reverse only
+                T = ctx.tape
+                lam = [lbuf[L][0] for L in range(nlev)]
+                for k in reversed(range(T.n)):
+                    _reverse_coarse(H, T, k, lam, lbuf, g_aux)
+                ctx.tape = None
+            else:
+                lam = _backward_segments(ctx, H, lbuf, g_aux)
+        grads_out = [None, None, None, None, None, None, None] + [l.clone() for l in lam]
         if H.medium:
             g_rho, g_K = [], []
             for L in range(nlev):
@@ -166,6 +344,80 @@ class _Rollout(torch.autograd.Function):
                 g_K.append(gk)
             grads_out += g_rho + g_K
         return tuple(grads_out)
+
+
+def _backward_segments(ctx, H, lbuf, g_aux):
+    """reverse sweep over the checkpoint segments, last first: each segment is recomputed from
+    its checkpoint into the tape buffers and reversed, as one CUDA graph per segment length
+    (replayed for every segment of that length) when ctx.graphs"""
+    nlev, every, ncoarse = ctx.nlev, ctx.every, ctx.ncoarse
+    for s in reversed(range(len(ctx.checkpoints))):
+        states, dt0 = ctx.checkpoints[s]
+        n = min(every, ncoarse - s * every)
+        rec = ctx.records and _records_ok(H)
+        T = _buffers(H, ("tape", n, rec), lambda: _Tape(H, n, record=rec))
+        for L in range(nlev):
+            T.state(L, 0).copy_(states[L])
+        H.dt.copy_(dt0)
+
+        def body():
+            lam = [lbuf[L][0] for L in range(nlev)]
+            for k in range(n):
+                _record_coarse(H, T, k, ctx.frozen)
+            for k in reversed(range(n)):
+                _reverse_coarse(H, T, k, lam, lbuf, g_aux)
+            for L in range(nlev):   # the adjoint leaves in the buffer it came in
+                if lam[L] is not lbuf[L][0]:
+                    lbuf[L][0].copy_(lam[L])
+
+        if not ctx.graphs:
+            body()
+            continue
+        key = ("bwd", n, ctx.frozen, rec)
+        if key not in H.__dict__.get("_graphs", {}):
+            # the first run of the body (before the capture) must not count: save what it changes
+            saved = [l[0].clone() for l in lbuf], [g.clone() if g is not None else None for g in g_aux]
+            _replayable(H, key, body)
+            for L in range(nlev):
+                lbuf[L][0].copy_(saved[0][L])
+                if g_aux[L] is not None:
+                    g_aux[L].copy_(saved[1][L])
+            for L in range(nlev):
+                T.state(L, 0).copy_(states[L])
+            H.dt.copy_(dt0)
+        H._graphs[key].replay()
+    return [lbuf[L][0] for L in range(nlev)]
+
+
+def _backward_filled(ctx, H, lam, g_aux):
+    """the reverse sweep with every ghost filled before each step (H.pull = False)"""
+    nlev, every, ncoarse = ctx.nlev, ctx.every, ctx.ncoarse
+    if ctx.tapes is not None:
+        for node, dt in reversed(ctx.tapes):
+            H.dt.copy_(dt)   # frozen forward time step
+            _reverse(H, node, lam, g_aux)
+        ctx.tapes = None
+    nseg = len(ctx.checkpoints)
+    for s in reversed(range(nseg)):
+        states, dt0 = ctx.checkpoints[s]
+        n0, n1 = s * every, min((s + 1) * every, ncoarse)
+        # recompute the segment, recording each coarse step
+        for L in range(nlev):
+            H.cur[L] = 0
+            H.q[L][0].copy_(states[L])
+        H.dt.copy_(dt0)
+        tapes = []
+        for _ in range(n0, n1):
+            dt = H.dt.clone()
+            tapes.append((_advance_record(H, 0, None, None, 0.0), dt))
+            if ctx.frozen:
+                H.smax.zero_()
+            else:
+                claw.claw_dt_update(H.ctx, 0, H.smax, H.dt)
+        for node, dt in reversed(tapes):
+            H.dt.copy_(dt)   # frozen forward time step
+            _reverse(H, node, lam, g_aux)
+    return lam
 
 
 def _ghost_mask(H, L):
@@ -228,12 +480,19 @@ class LevelStep(torch.autograd.Function):
         return None, None, None, lam_old, g_rho, g_K
 
 
-def rollout(H, q0, rho=None, K=None, ncoarse=1, every=20, dt=None):
+def rollout(H, q0, rho=None, K=None, ncoarse=1, every=20, dt=None, graphs=True, records=True):
     """final states (one pool per level) after `ncoarse` coarse steps from q0 (pools per level),
     differentiable with respect to q0 and, for a cell-wise medium, the rho and K pools.
     every: checkpoint interval of the recomputing backward, or None for the recorded tape.
     dt: None for Eq. cfl time steps, else a device tensor of per-run level-0 time steps used
-    unchanged for every coarse step.  The gradient holds the time steps fixed either way."""
+    unchanged for every coarse step.  The gradient holds the time steps fixed either way.
+    graphs: the checkpointed forward segments and each segment's recompute-and-reverse run as
+    CUDA graphs cached on H (replayed by later rollouts of the same shape).
+    records: in the checkpointed backward, the recompute records every level-step's
+    intermediates (claw_level_advance_record) and the reverse reads them
+    (claw_level_advance_adjoint_tape) instead of re-running the forward inside the adjoint
+    kernel; cell-wise medium, second order.  Memory: an aux-sized tape per level-step of a
+    segment."""
     nlev = H.nlev
     tensors = list(q0) + (list(rho) + list(K) if H.medium else [])
-    return _Rollout.apply(H, ncoarse, every, nlev, dt, *tensors)
+    return _Rollout.apply(H, ncoarse, every, nlev, dt, bool(graphs), bool(records), *tensors)

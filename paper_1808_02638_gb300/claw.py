@@ -88,6 +88,8 @@ _SIGNATURES = {
     "claw_average_down_adjoint": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "claw_level_step_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_level_advance_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
+    "claw_level_advance_record": ([VP, I32, VP, VP, VP, VP, VP, I32, VP, VP], ctypes.c_int),
+    "claw_level_advance_adjoint_tape": ([VP, I32, VP, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
     "claw_sync_status": ([VP], ctypes.c_int),
     "claw_launch_count": ([VP], ctypes.c_int64),
     "claw_strerror": ([I32], ctypes.c_char_p),
@@ -366,6 +368,18 @@ def claw_level_step_adjoint(ctx, level, q_old, lam_new, lam_old, aux, g_aux, dt,
 def claw_level_advance_adjoint(ctx, level, q_old, lam_new, lam_old, aux, g_aux, dt, flags, stream=None):
     _check("claw_level_advance_adjoint", load().claw_level_advance_adjoint(
         ctx, level, _ptr(q_old), _ptr(lam_new), _ptr(lam_old), _ptr(aux), _ptr(g_aux), _ptr(dt), int(flags),
+        _stream(stream)))
+
+
+def claw_level_advance_record(ctx, level, q_old, q_new, aux, dt, smax, flags, tape, stream=None):
+    _check("claw_level_advance_record", load().claw_level_advance_record(
+        ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax), int(flags), _ptr(tape),
+        _stream(stream)))
+
+
+def claw_level_advance_adjoint_tape(ctx, level, tape, lam_new, lam_old, aux, g_aux, dt, flags, stream=None):
+    _check("claw_level_advance_adjoint_tape", load().claw_level_advance_adjoint_tape(
+        ctx, level, _ptr(tape), _ptr(lam_new), _ptr(lam_old), _ptr(aux), _ptr(g_aux), _ptr(dt), int(flags),
         _stream(stream)))
 
 

@@ -8,11 +8,12 @@
 //   normal Riemann -> q_old and the medium planes.
 // Each reverse phase is a gather where it can be (every adjoint written by one thread): the
 // wave-strength and state adjoints are stored per edge and summed per cell by the thread of
-// the cell (a shared-memory FP64 atomic costs an FP64-pipe slot on this part, like a DFMA);
-// only the per-cell medium adjoint (Z, c, K) accumulates with shared-memory atomics.  The
-// adjoints of the per-edge planes (1/(Z_L+Z_R) and the limiter projection factors) are owned
-// by the edge's thread and go to g_aux with global FP64 atomics; their chain rule to Z runs
-// once per gradient in claw_medium_aux_adjoint, not once per step.  The c^2 plane is folded
+// the cell (a shared-memory FP64 atomic costs an FP64-pipe slot on this part, like a DFMA).
+// The medium adjoints (per cell: Z, c, K; per edge: 1/(Z_L+Z_R) and the limiter projection
+// factors) go straight to g_aux with global FP64 reductions, which the L2 carries out, not
+// the FP64 pipe; the chain rule of the edge planes to Z runs once per gradient in
+// claw_medium_aux_adjoint, not once per step.  Zero tests of doubles are integer tests (a
+// double compare is an FP64-pipe instruction).  The c^2 plane is folded
 // into c where it is read.  Contributions to cells shared with neighbouring tiles (the two
 // ghost layers) reach lam_old / g_aux through global FP64 atomics.  Given the level's ghost ring
 // (A.ring), the contributions to the box's own ghost cells that the forward filled from cells of
@@ -102,6 +103,17 @@ template <> struct LimD<CLAW_LIM_MC> {
 
 constexpr int ATX = 16, ATY = 16, ANT = 384;
 
+// x != 0 on the integer pipe (+0 and -0 are zero)
+__device__ __forceinline__ bool nonzero(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
+}
+// x with its sign flipped when f is 1 (a sign-bit xor, not an FP64 negation)
+__device__ __forceinline__ double flip_sign(double x, int f)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(f & 1) << 63));
+}
+
 struct AGeo {
     static constexpr int SW = ATX + 4, SH = ATY + 4, QPL = SW * SH;
     static constexpr int XEW = ATX + 3, XEH = ATY + 2, XE = XEW * XEH;
@@ -144,9 +156,8 @@ struct AGeo {
     static constexpr int O_BVY = O_BPY + EN;
     static constexpr int O_FB = O_BVY + EN;             // adjoints of Fp, Fu, Gp, Gv
     static constexpr int O_GB = O_FB + 2 * FN;
-    static constexpr int O_MED = O_GB + 2 * GN;         // medium adjoints: Z, c, K planes
-    static constexpr int NMED = 3;
-    static size_t smem_bytes(int med) { return (size_t)(O_MED + (med ? NMED * QPL : 0)) * 8; }
+    static constexpr int O_END = O_GB + 2 * GN;
+    static size_t smem_bytes(int) { return (size_t)O_END * 8; }
 };
 static_assert(AUX_Z == 0 && AUX_C == 1 && AUX_K == 2, "medium adjoint planes are the first three aux planes");
 
@@ -192,7 +203,6 @@ __global__ void __launch_bounds__(ANT, 2)
     double* Fub = Fpb + G::FN;
     double* Gpb = sm + G::O_GB;
     double* Gvb = Gpb + G::GN;
-    double* medb = sm + G::O_MED;   // [3][QPL]: Z, c, K
 
     const int tid = threadIdx.x;
     const bool second = A.order == 2;
@@ -233,14 +243,13 @@ __global__ void __launch_bounds__(ANT, 2)
         auto YL = [](int c, int b) { return (c + 1) + b * G::YLW; };
         auto DI = [](int c, int r) { return c + (r + 1) * G::DW; };
         auto EI = [](int c, int r) { return (c + 1) + r * G::EW; };
-        auto medadd = [&](int k, int i, int j, double v) {   // k: AUX_Z, AUX_C or AUX_K
-            if (MED) atomicAdd(&medb[k * G::QPL + CI(i, j)], v);
+        // adjoint of medium plane k at tile-local cell (i, j): a cell plane (AUX_Z, AUX_C, AUX_K)
+        // or an edge plane (held at the edge's east / north cell); a global reduction
+        double* gmed = (MED && g_aux) ? g_aux + P.aoff : nullptr;
+        auto medadd = [&](int k, int i, int j, double v) {
+            if (MED && nonzero(v)) atomicAdd(gmed + k * WH + (long long)(y0 + j + 2) * W + (x0 + i + 2), v);
         };
-        // adjoint of an edge plane k (held at the edge's east / north cell (i, j)): global atomic
-        double* gedge = (MED && g_aux) ? g_aux + P.aoff : nullptr;
-        auto edgeadd = [&](int k, int i, int j, double v) {
-            if (MED && v != 0.0) atomicAdd(gedge + k * WH + (long long)(y0 + j + 2) * W + (x0 + i + 2), v);
-        };
+        auto edgeadd = medadd;
 
         // ---------------------------------------------------------------- stage, clear
         {
@@ -254,10 +263,12 @@ __global__ void __launch_bounds__(ANT, 2)
             }
             // accumulators only: every other work array is written before it is read
             for (int k = tid; k < G::O_M1X - G::O_A1B; k += ANT) sm[G::O_A1B + k] = 0.0;
-            if (MED)
-                for (int k = tid; k < G::NMED * G::QPL; k += ANT) medb[k] = 0.0;
         }
         __syncthreads();
+        if (A.ring && P.ring >= 0) {   // the ghosts the forward step pulled from their source cells
+            pull_ghosts<G::SW, G::QPL, ANT>(A, P, sp, x0, y0, tx, ty);
+            __syncthreads();
+        }
 
         // ---------------------------------------------------------------- forward recompute
         for (int k = tid; k < (ty + 2) * (tx + 3); k += ANT) {
@@ -586,7 +597,7 @@ __global__ void __launch_bounds__(ANT, 2)
                 if (a >= 1) g1 += M1x[XL(a - 1, r)];
                 if (a <= tx - 1) g2 += M2x[XL(a + 1, r)];
             }
-            if (g1 == 0.0 && g2 == 0.0) {
+            if (!nonzero(g1) && !nonzero(g2)) {
                 A1b[XE(a, r)] = 0.0;
                 A2b[XE(a, r)] = 0.0;
                 continue;
@@ -611,7 +622,7 @@ __global__ void __launch_bounds__(ANT, 2)
                 if (b >= 1) g1 += M1y[YL(c, b - 1)];
                 if (b <= ty - 1) g2 += M2y[YL(c, b + 1)];
             }
-            if (g1 == 0.0 && g2 == 0.0) {
+            if (!nonzero(g1) && !nonzero(g2)) {
                 B1b[YE(c, b)] = 0.0;
                 B2b[YE(c, b)] = 0.0;
                 continue;
@@ -661,25 +672,16 @@ __global__ void __launch_bounds__(ANT, 2)
                     if (e.x >= 0) {
                         const long long pl = e.y & ((1LL << kRingFlagShift) - 1);
                         const int fl = (int)(e.y >> kRingFlagShift);
-                        if (p != 0.0) atomicAdd(lam_old + e.x, p);
-                        if (u != 0.0) atomicAdd(lam_old + e.x + pl, (fl & 1) ? -u : u);
-                        if (v != 0.0) atomicAdd(lam_old + e.x + 2 * pl, (fl & 2) ? -v : v);
+                        if (nonzero(p)) atomicAdd(lam_old + e.x, p);
+                        if (nonzero(u)) atomicAdd(lam_old + e.x + pl, flip_sign(u, fl & 1));
+                        if (nonzero(v)) atomicAdd(lam_old + e.x + 2 * pl, flip_sign(v, (fl >> 1) & 1));
                         continue;
                     }
                 }
                 const long long o = (long long)(gy + 2) * W + (gx + 2);
-                if (p != 0.0) atomicAdd(lo + o, p);
-                if (u != 0.0) atomicAdd(lo + WH + o, u);
-                if (v != 0.0) atomicAdd(lo + 2 * WH + o, v);
-            }
-            if (MED && g_aux) {
-                double* ga = g_aux + P.aoff;
-                for (int k = tid; k < G::NMED * n4; k += ANT) {
-                    const int m = k / n4, rem = k - m * n4;
-                    const int jj = rem / w4, ii = rem - jj * w4;
-                    const double v = medb[m * G::QPL + jj * G::SW + ii];
-                    if (v != 0.0) atomicAdd(ga + m * WH + (long long)(y0 + jj) * W + (x0 + ii), v);
-                }
+                if (nonzero(p)) atomicAdd(lo + o, p);
+                if (nonzero(u)) atomicAdd(lo + WH + o, u);
+                if (nonzero(v)) atomicAdd(lo + 2 * WH + o, v);
             }
         }
         __syncthreads();   // shared memory is reused by the next tile

@@ -30,6 +30,7 @@ struct TmapCache {
     int tx = 0, ty = 0;
     void* dev = nullptr;   // CUtensorMap[nboxes]
     unsigned long long stamp = 0;
+    bool pinned = false;   // handed to a stream capture: a graph may read it until the level is rebuilt
 };
 
 struct claw_ctx {
@@ -423,6 +424,9 @@ int build_tiles(claw_ctx* ctx, int L)
                 at.push_back(T);
             }
     }
+    // largest first, like the step's tiles: the persistent CTAs end on small tiles
+    std::stable_sort(at.begin(), at.end(),
+                     [](const TileDev& a, const TileDev& b) { return (int)a.tx * a.ty > (int)b.tx * b.ty; });
     ctx->natiles[L] = (int)at.size();
     pack.add(&ctx->atiles[L], at);
     return pack.commit(d.tiletab);
@@ -780,13 +784,18 @@ const void* get_tmaps(claw_ctx* ctx, int L, const double* q, cudaStream_t s)
 {
     LevelDev& d = ctx->lev[L];
     auto& cache = ctx->tmaps[L];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return nullptr;
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
     for (auto& t : cache)
         if (t.q == q && t.tx == d.tx && t.ty == d.ty) {
             t.stamp = ++ctx->stamp;
+            // a captured launch keeps this device pointer: the entry must outlive the graph, so
+            // it is never evicted (only a rebuild of the level's tables frees it)
+            if (capturing) t.pinned = true;
             return t.dev;
         }
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    if (capturing) return nullptr;   // no descriptor is built inside a capture
     auto enc = encode_fn();
     if (!enc) return nullptr;
     // the copied box must fit inside every box's padded planes (else cooperative loads)
@@ -817,9 +826,14 @@ const void* get_tmaps(claw_ctx* ctx, int L, const double* q, cudaStream_t s)
         return nullptr;
     }
     t.stamp = ++ctx->stamp;
-    if (cache.size() >= 4) {   // evict the least recently used
-        auto old = std::min_element(cache.begin(), cache.end(),
-                                    [](const TmapCache& a, const TmapCache& b) { return a.stamp < b.stamp; });
+    // keep at most four entries that no capture has seen: evict the least recently used of those
+    // (pinned entries stay, however many)
+    size_t unpinned = 0;
+    for (const auto& c : cache) unpinned += !c.pinned;
+    if (unpinned >= 4) {
+        auto old = cache.end();
+        for (auto it = cache.begin(); it != cache.end(); ++it)
+            if (!it->pinned && (old == cache.end() || it->stamp < old->stamp)) old = it;
         cudaStreamSynchronize(s);
         cudaFree(old->dev);
         cache.erase(old);
@@ -1672,6 +1686,65 @@ int claw_level_advance_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, co
     ctx->launches += 1;
     return cuda_rc(launch_step_adjoint(a, lam_new, lam_old, g_aux, ctx->medium, ctx->limiter, ctx->nsm,
                                        (cudaStream_t)stream));
+}
+
+int claw_level_advance_record(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,
+                              double* dt, double* smax, int32_t flags, double* tape, void* stream)
+{
+    int rc = check_step_args(ctx, L, q_old, q_new, aux, dt, smax);
+    if (rc) return rc;
+    if (!tape || ctx->kind() != KIND_CELLWISE || ctx->order != 2) return CLAW_EINVAL;
+    if (flags & ~(CLAW_ADVANCE_PULL_GHOSTS | CLAW_ADVANCE_UPDATE_DT)) return CLAW_EINVAL;
+    const bool pull = (flags & CLAW_ADVANCE_PULL_GHOSTS) != 0;
+    if (pull && !ctx->lev[L].ring_ok) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    LevelDev& d = ctx->lev[L];
+    if (d.ntiles == 0) return CLAW_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    StepArgs a = make_args(ctx, L, q_old, q_new, aux, dt, smax);
+    if (flags & CLAW_ADVANCE_UPDATE_DT) {
+        a.dtupd = 1;
+        a.dt_out = dt;
+        a.minh = ctx->minh;
+        a.cflv = ctx->cflv;
+        a.done = ctx->done;
+        a.nruns = ctx->nruns;
+    }
+    if (pull) a.ring = d.ring;
+    a.tape = tape;
+    int staging = d.staging;
+    if (staging >= 1) {
+        a.tmaps = get_tmaps(ctx, L, q_old, s);
+        if (!a.tmaps) staging = 0;
+    }
+    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, pull, true);
+    if (per_sm <= 0) return CLAW_ECUDA;
+    const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
+    ctx->launches += 1;
+    return cuda_rc(launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s));
+}
+
+int claw_level_advance_adjoint_tape(claw_ctx* ctx, int32_t L, const double* tape, const double* lam_new,
+                                    double* lam_old, const double* aux, double* g_aux, const double* dt,
+                                    int32_t flags, void* stream)
+{
+    if (!ctx || L < 0 || L >= CLAW_MAXLEV || !tape || !lam_new || !lam_old || !aux || !g_aux || !dt)
+        return CLAW_EINVAL;
+    if (flags & ~CLAW_ADVANCE_PULL_GHOSTS) return CLAW_EINVAL;
+    if (!ctx->set[L]) return CLAW_ESTATE;
+    if (ctx->kind() != KIND_CELLWISE || ctx->order != 2) return CLAW_EINVAL;
+    LevelDev& d = ctx->lev[L];
+    if ((flags & CLAW_ADVANCE_PULL_GHOSTS) && !d.ring_ok) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    if (d.ntiles == 0) return CLAW_OK;
+    StepArgs a = make_args(ctx, L, nullptr, nullptr, aux, dt, nullptr);
+    a.tiles = ctx->atiles[L];
+    a.ntiles = ctx->natiles[L];
+    a.tape = const_cast<double*>(tape);
+    if (flags & CLAW_ADVANCE_PULL_GHOSTS) a.ring = d.ring;
+    ctx->launches += 1;
+    return cuda_rc(launch_step_adjoint_tape(a, lam_new, lam_old, g_aux, ctx->limiter, ctx->nsm,
+                                            (cudaStream_t)stream));
 }
 
 int claw_level_step_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, const double* lam_new, double* lam_old,

@@ -26,6 +26,32 @@ enum AuxPlane : int {
 };
 static_assert(CLAW_NAUX == 10, "aux plane count");
 
+// planes of a level-step's tape (claw_level_advance_record), laid out like the aux planes: the
+// intermediates of the cell-wise step at the edge west / south of each padded cell, and the
+// transverse fluctuation pressures of the cell.  The limited strengths carry the limiter's
+// branch (LimCode) in their three lowest mantissa bits.
+enum TapePlane : int {
+    TAPE_A1 = 0, TAPE_A2 = 1,   // wave strengths of the x-edge (left-, right-going)
+    TAPE_B1 = 2, TAPE_B2 = 3,   // of the y-edge
+    TAPE_M1 = 4, TAPE_M2 = 5,   // limited strengths of the x-edge
+    TAPE_N1 = 6, TAPE_N2 = 7,   // of the y-edge
+    TAPE_D = 8,                 // x-fluctuation pressure into the cell
+    TAPE_E = 9,                 // y-fluctuation pressure into the cell
+};
+constexpr int kTapePlanes = 10;
+static_assert(kTapePlanes == CLAW_NAUX, "a tape has the aux pool's size");
+
+// branch of a limited strength phi(b/a) a: its partial derivatives (d/da, d/db)
+enum LimCode : int {
+    LIMC_ZERO = 0,      // (0, 0)
+    LIMC_A = 1,         // (1, 0)
+    LIMC_B = 2,         // (0, 1)
+    LIMC_2A = 3,        // (2, 0)
+    LIMC_2B = 4,        // (0, 2)
+    LIMC_HALF = 5,      // (1/2, 1/2)
+    LIMC_SMOOTH = 6,    // van Leer: derivatives from the values
+};
+
 // One box of a level, as the kernels see it.
 struct PatchDev {
     long long qoff;   // element offset of the p plane in the q pool
@@ -196,6 +222,7 @@ struct StepArgs {
     // polls of a tile's first wait for its bulk copy before the CTA reports ERR_TIMEOUT; the
     // copies still in flight are then awaited with the full bound kWaitPolls before it exits
     unsigned wait_polls = kWaitPolls;
+    double* tape = nullptr;   // recording step (cell-wise medium): the level-step's tape, aux layout
 };
 
 // error flag bits written by kernels
@@ -207,10 +234,16 @@ enum : int { KIND_UNIFORM = 0, KIND_CELLWISE = 1, KIND_SWE = 2 };
 // launchers (claw_step.cu; kind: KIND_*)
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s);
-int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull = false);
+int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull = false,
+                         bool rec = false);
 cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
                                 int medium, int limiter, int nsm, cudaStream_t s);   // grid: resident CTAs x nsm
 int adjoint_tile();   // the adjoint kernel's square tile edge
+// the tape-driven adjoint of the cell-wise second-order step (claw_adjoint_tape.cu), on the tiles of
+// adjoint_tape_tile() (the same edge as adjoint_tile())
+cudaError_t launch_step_adjoint_tape(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
+                                     int limiter, int nsm, cudaStream_t s);
+int adjoint_tape_tile();
 
 // launchers (claw_ghost.cu)
 cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nblocks, double* q, cudaStream_t s,

@@ -7,8 +7,13 @@
 
 namespace claw {
 
-static StepKernel pick(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull)
+static StepKernel pick(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull, bool rec = false)
 {
+    if (rec) {
+        if (kind != KIND_CELLWISE) return StepKernel{nullptr, 0, 0};
+        return pull ? step_kernel_cellwise_record(limiter, tx, ty, nt, staging)
+                    : step_kernel_cellwise_record_fill(limiter, tx, ty, nt, staging);
+    }
     switch (kind) {
     case KIND_UNIFORM:
         return pull ? step_kernel_uniform_pull(limiter, tx, ty, nt, staging)
@@ -38,9 +43,9 @@ static cudaError_t prepare(const StepKernel& k)
     return e;
 }
 
-int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull)
+int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull, bool rec)
 {
-    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, pull);
+    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, pull, rec);
     if (!k.fn || prepare(k) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k.fn, k.nt, k.smem) != cudaSuccess)
@@ -51,7 +56,7 @@ int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int stag
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s)
 {
-    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, a.ring != nullptr);
+    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, a.ring != nullptr, a.tape != nullptr);
     if (!k.fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare(k);
     if (e != cudaSuccess) return e;

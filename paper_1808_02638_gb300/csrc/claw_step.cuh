@@ -55,9 +55,16 @@ __device__ __forceinline__ bool same_sign_nonzero(long long ia, long long ib, lo
 }
 }  // namespace lim_bits
 
+// fc(a, b, code) returns f(a, b) and the branch the value took (LimCode), for the tape of a
+// recording step; on the integer pipe like f.
 template <int L> struct Lim;
 template <> struct Lim<CLAW_LIM_NONE> {
     static __device__ __forceinline__ double f(double a, double) { return a; }
+    static __device__ __forceinline__ double fc(double a, double, int& code)
+    {
+        code = LIMC_A;
+        return a;
+    }
 };
 template <> struct Lim<CLAW_LIM_MINMOD> {   // max(0, min(1, theta)): sign(a) min(|a|, |b|)
     static __device__ __forceinline__ double f(double a, double b)
@@ -66,6 +73,14 @@ template <> struct Lim<CLAW_LIM_MINMOD> {   // max(0, min(1, theta)): sign(a) mi
         const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
         const long long m = ma < mb ? ma : mb;
         return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
+    }
+    static __device__ __forceinline__ double fc(double a, double b, int& code)
+    {
+        using namespace lim_bits;
+        const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
+        const bool nz = same_sign_nonzero(ia, ib, ma, mb);
+        code = !nz ? LIMC_ZERO : (ma < mb ? LIMC_A : LIMC_B);
+        return nz ? val((ma < mb ? ma : mb) | (ia & SIGN)) : 0.0;
     }
 };
 template <> struct Lim<CLAW_LIM_SUPERBEE> {   // max(0, min(1, 2 theta), min(2, theta))
@@ -78,6 +93,17 @@ template <> struct Lim<CLAW_LIM_SUPERBEE> {   // max(0, min(1, 2 theta), min(2, 
         const long long m = m1 > m2 ? m1 : m2;
         return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
     }
+    static __device__ __forceinline__ double fc(double a, double b, int& code)
+    {
+        using namespace lim_bits;
+        const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
+        const long long a2 = ma + ONE_EXP, b2 = mb + ONE_EXP;
+        const bool first_a = ma < b2, second_a2 = a2 < mb;
+        const long long m1 = first_a ? ma : b2, m2 = second_a2 ? a2 : mb;
+        const bool nz = same_sign_nonzero(ia, ib, ma, mb);
+        code = !nz ? LIMC_ZERO : (m1 > m2 ? (first_a ? LIMC_A : LIMC_2B) : (second_a2 ? LIMC_2A : LIMC_B));
+        return nz ? val((m1 > m2 ? m1 : m2) | (ia & SIGN)) : 0.0;
+    }
 };
 template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|): 2ab / (a + b)
     static __device__ __forceinline__ double f(double a, double b)
@@ -88,6 +114,12 @@ template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|
         // below that the result is under 2^-1020 in magnitude: 0 (r would overflow)
         if (!same_sign_nonzero(ia, ib, ia & MAG, ib & MAG) || hs < ONE_EXP) return 0.0;
         return a * (b * __drcp_rn(val(hs | (ia & SIGN))));
+    }
+    static __device__ __forceinline__ double fc(double a, double b, int& code)
+    {
+        const double m = f(a, b);
+        code = lim_bits::bits(m) & lim_bits::MAG ? LIMC_SMOOTH : LIMC_ZERO;
+        return m;
     }
 };
 template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta))
@@ -101,7 +133,25 @@ template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta)
         const long long m = sh < t2 ? sh : t2;
         return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
     }
+    static __device__ __forceinline__ double fc(double a, double b, int& code)
+    {
+        using namespace lim_bits;
+        const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
+        const long long t2 = (ma < mb ? ma : mb) + ONE_EXP;
+        long long sh = bits(val(ma) + val(mb)) - ONE_EXP;
+        sh = sh > 0 ? sh : 0;
+        const bool nz = same_sign_nonzero(ia, ib, ma, mb);
+        code = !nz ? LIMC_ZERO : (sh < t2 ? LIMC_HALF : (ma < mb ? LIMC_2A : LIMC_2B));
+        return nz ? val((sh < t2 ? sh : t2) | (ia & SIGN)) : 0.0;
+    }
 };
+
+// a limited strength with its branch in the three lowest mantissa bits (a relative change
+// below 2^-49; exact zeros stay zero)
+__device__ __forceinline__ double tag_code(double m, int code)
+{
+    return __longlong_as_double((__double_as_longlong(m) & ~7LL) | (long long)code);
+}
 
 // ------------------------------------------------------------------------- tile geometry
 template <int TX, int TY> struct Geo {
@@ -255,9 +305,13 @@ __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P
 // once this one's state has been read, in phase D) with registers capped for three CTAs per SM.
 // PULL: same-level and boundary ghosts are taken from their source cells (a separate
 // instantiation: the mere presence of the pull code slowed the other kernels by up to 11 %).
-template <int MED, int LIM, int TX, int TY, int NT, int STAGE, bool PULL>
+// REC (cell-wise medium): also write the step's intermediates to the tape A.tape (TapePlane);
+// each padded cell's entries come from the one tile that owns the cell (its interior, plus the
+// box's ghost frame next to it), so the tape is the same whatever the tiling.
+template <int MED, int LIM, int TX, int TY, int NT, int STAGE, bool PULL, bool REC = false>
 __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const StepArgs A)
 {
+    static_assert(!REC || MED == 1, "the tape records the cell-wise step");
     using G = Geo<TX, TY>;
     constexpr int NBUF = STAGE == 1 ? 2 : 1;
     constexpr int NPER = (TX * TY + NT - 1) / NT;
@@ -403,6 +457,14 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         auto AX = [&](int k, int i, int j) -> double {
             return __ldg(aux + k * WH + (long long)(y0 + j + 2) * W + (x0 + i + 2));
         };
+        // recording: the tile owns its interior and, at a box side, the two ghost layers there
+        const int olx = x0 == 0 ? -2 : 0, ohx = x0 + tx == P.nx ? tx + 2 : tx;
+        const int oly = y0 == 0 ? -2 : 0, ohy = y0 + ty == P.ny ? ty + 2 : ty;
+        double* tape = REC ? A.tape + P.aoff : nullptr;
+        auto rec = [&](int k, int i, int j, double v) {
+            if (REC && i >= olx && i < ohx && j >= oly && j < ohy)
+                tape[k * WH + (long long)(y0 + j + 2) * W + (x0 + i + 2)] = v;
+        };
 
         // ---------------------------------------------------------------- phase A: normal Riemann
         // x-edge a (between cells a-1 and a) on rows r in [-1, ty]
@@ -421,6 +483,8 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                     const double zr = AX(AUX_Z, a, r), zl = AX(AUX_Z, a - 1, r), is = AX(AUX_IXS, a, r);
                     a1 = fma(zr, du, -dp) * is;
                     a2 = fma(zl, du, dp) * is;
+                    rec(TAPE_A1, a, r, a1);
+                    rec(TAPE_A2, a, r, a2);
                 }
                 A1x[(r + 1) * G::XEW + (a + 1)] = a1;
                 A2x[(r + 1) * G::XEW + (a + 1)] = a2;
@@ -442,6 +506,8 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                     const double zr = AX(AUX_Z, c, bb), zl = AX(AUX_Z, c, bb - 1), is = AX(AUX_IYS, c, bb);
                     b1 = fma(zr, dv, -dp) * is;
                     b2 = fma(zl, dv, dp) * is;
+                    rec(TAPE_B1, c, bb, b1);
+                    rec(TAPE_B2, c, bb, b2);
                 }
                 B1y[(bb + 1) * G::YEW + (c + 1)] = b1;
                 B2y[(bb + 1) * G::YEW + (c + 1)] = b2;
@@ -480,8 +546,16 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                         Sx[(r + 1) * G::XLW + a] = m2 - m1;
                         Px[(r + 1) * G::XLW + a] = m1 + m2;
                     } else {
-                        m1 = Lim<LIM>::f(a1, A1x[e + 1] * AX(AUX_FX1, a, r));
-                        m2 = Lim<LIM>::f(a2, A2x[e - 1] * AX(AUX_FX2, a, r));
+                        if (REC) {
+                            int c1, c2;
+                            m1 = Lim<LIM>::fc(a1, A1x[e + 1] * AX(AUX_FX1, a, r), c1);
+                            m2 = Lim<LIM>::fc(a2, A2x[e - 1] * AX(AUX_FX2, a, r), c2);
+                            rec(TAPE_M1, a, r, tag_code(m1, c1));
+                            rec(TAPE_M2, a, r, tag_code(m2, c2));
+                        } else {
+                            m1 = Lim<LIM>::f(a1, A1x[e + 1] * AX(AUX_FX1, a, r));
+                            m2 = Lim<LIM>::f(a2, A2x[e - 1] * AX(AUX_FX2, a, r));
+                        }
                         const double kl = fma(-lx, AX(AUX_C2, a - 1, r), AX(AUX_C, a - 1, r));
                         const double kr = fma(-lx, AX(AUX_C2, a, r), AX(AUX_C, a, r));
                         const double e1 = kl * m1, e2 = kr * m2;
@@ -503,8 +577,16 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                         Sy[bb * G::YLW + (c + 1)] = m2 - m1;
                         Py[bb * G::YLW + (c + 1)] = m1 + m2;
                     } else {
-                        m1 = Lim<LIM>::f(b1, B1y[e + G::YEW] * AX(AUX_FY1, c, bb));
-                        m2 = Lim<LIM>::f(b2, B2y[e - G::YEW] * AX(AUX_FY2, c, bb));
+                        if (REC) {
+                            int c1, c2;
+                            m1 = Lim<LIM>::fc(b1, B1y[e + G::YEW] * AX(AUX_FY1, c, bb), c1);
+                            m2 = Lim<LIM>::fc(b2, B2y[e - G::YEW] * AX(AUX_FY2, c, bb), c2);
+                            rec(TAPE_N1, c, bb, tag_code(m1, c1));
+                            rec(TAPE_N2, c, bb, tag_code(m2, c2));
+                        } else {
+                            m1 = Lim<LIM>::f(b1, B1y[e + G::YEW] * AX(AUX_FY1, c, bb));
+                            m2 = Lim<LIM>::f(b2, B2y[e - G::YEW] * AX(AUX_FY2, c, bb));
+                        }
                         const double kl = fma(-ly, AX(AUX_C2, c, bb - 1), AX(AUX_C, c, bb - 1));
                         const double kr = fma(-ly, AX(AUX_C2, c, bb), AX(AUX_C, c, bb));
                         const double e1 = kl * m1, e2 = kr * m2;
@@ -567,8 +649,12 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
             } else {
                 const double Kc = AX(AUX_K, c, r), cc = AX(AUX_C, c, r);
                 if (trans) {
-                    Dx[(r + 1) * G::DW + c] = cw ? fma(Kc, apx, bpx) : Kc * apx;
-                    Ey[r * G::EW + c + 1] = cw ? fma(Kc, apy, bpy) : Kc * apy;
+                    const double dd = cw ? fma(Kc, apx, bpx) : Kc * apx;
+                    const double ee = cw ? fma(Kc, apy, bpy) : Kc * apy;
+                    Dx[(r + 1) * G::DW + c] = dd;
+                    Ey[r * G::EW + c + 1] = ee;
+                    rec(TAPE_D, c, r, dd);
+                    rec(TAPE_E, c, r, ee);
                 }
                 const double tpx = fma(0.5, bpx, Kc * apx), tux = fma(0.5, bux, cc * aux_);
                 const double tpy = fma(0.5, bpy, Kc * apy), tvy = fma(0.5, bvy, cc * avy);
@@ -591,6 +677,7 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                     else {
                         const double Kc = AX(AUX_K, c, r);
                         d = cw ? fma(Kc, apx, bpx) : Kc * apx;
+                        rec(TAPE_D, c, r, d);
                     }
                     Dx[(r + 1) * G::DW + c] = d;
                 } else {
@@ -604,6 +691,7 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                     else {
                         const double Kc = AX(AUX_K, c, r);
                         e = cw ? fma(Kc, apy, bpy) : Kc * apy;
+                        rec(TAPE_E, c, r, e);
                     }
                     Ey[r * G::EW + c + 1] = e;
                 }
@@ -716,11 +804,11 @@ struct StepKernel {
     int nt;
 };
 
-template <int MED, int LIM, int TX, int TY, int NT, int STAGE, bool PULL>
+template <int MED, int LIM, int TX, int TY, int NT, int STAGE, bool PULL, bool REC = false>
 StepKernel step_kernel_entry()
 {
     StepKernel k;
-    k.fn = step_kernel<MED, LIM, TX, TY, NT, STAGE, PULL>;
+    k.fn = step_kernel<MED, LIM, TX, TY, NT, STAGE, PULL, REC>;
     k.smem = Geo<TX, TY>::smem_bytes(STAGE == 1 ? 2 : 1);
     k.nt = NT;
     return k;
@@ -728,31 +816,35 @@ StepKernel step_kernel_entry()
 
 // all tile shapes and stagings of one medium and limiter
 // tile shapes x thread counts x stagings of one medium and limiter (nt = 0: the default)
-template <int MED, int LIM, bool PULL>
+template <int MED, int LIM, bool PULL, bool REC = false>
 StepKernel step_kernel_select(int tx, int ty, int nt, int staging)
 {
     if (tx == 32 && ty == 32 && (nt == 0 || nt == 256))
-        return staging ? step_kernel_entry<MED, LIM, 32, 32, 256, 1, PULL>() : step_kernel_entry<MED, LIM, 32, 32, 256, 0, PULL>();
+        return staging ? step_kernel_entry<MED, LIM, 32, 32, 256, 1, PULL, REC>()
+                       : step_kernel_entry<MED, LIM, 32, 32, 256, 0, PULL, REC>();
     if (tx == 32 && ty == 32 && nt == 512)
-        return staging ? step_kernel_entry<MED, LIM, 32, 32, 512, 1, PULL>() : step_kernel_entry<MED, LIM, 32, 32, 512, 0, PULL>();
+        return staging ? step_kernel_entry<MED, LIM, 32, 32, 512, 1, PULL, REC>()
+                       : step_kernel_entry<MED, LIM, 32, 32, 512, 0, PULL, REC>();
     if (tx == 32 && ty == 16 && (nt == 0 || nt == 256)) {
-        if (staging == 2) return step_kernel_entry<MED, LIM, 32, 16, 256, 2, PULL>();
-        return staging ? step_kernel_entry<MED, LIM, 32, 16, 256, 1, PULL>() : step_kernel_entry<MED, LIM, 32, 16, 256, 0, PULL>();
+        if (staging == 2) return step_kernel_entry<MED, LIM, 32, 16, 256, 2, PULL, REC>();
+        return staging ? step_kernel_entry<MED, LIM, 32, 16, 256, 1, PULL, REC>()
+                       : step_kernel_entry<MED, LIM, 32, 16, 256, 0, PULL, REC>();
     }
     if (tx == 16 && ty == 16 && (nt == 0 || nt == 128))
-        return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1, PULL>() : step_kernel_entry<MED, LIM, 16, 16, 128, 0, PULL>();
+        return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1, PULL, REC>()
+                       : step_kernel_entry<MED, LIM, 16, 16, 128, 0, PULL, REC>();
     return StepKernel{nullptr, 0, 0};
 }
 
-template <int MED, bool PULL>
+template <int MED, bool PULL, bool REC = false>
 StepKernel step_kernel_for(int lim, int tx, int ty, int nt, int staging)
 {
     switch (lim) {
-    case CLAW_LIM_NONE: return step_kernel_select<MED, CLAW_LIM_NONE, PULL>(tx, ty, nt, staging);
-    case CLAW_LIM_MINMOD: return step_kernel_select<MED, CLAW_LIM_MINMOD, PULL>(tx, ty, nt, staging);
-    case CLAW_LIM_SUPERBEE: return step_kernel_select<MED, CLAW_LIM_SUPERBEE, PULL>(tx, ty, nt, staging);
-    case CLAW_LIM_VANLEER: return step_kernel_select<MED, CLAW_LIM_VANLEER, PULL>(tx, ty, nt, staging);
-    case CLAW_LIM_MC: return step_kernel_select<MED, CLAW_LIM_MC, PULL>(tx, ty, nt, staging);
+    case CLAW_LIM_NONE: return step_kernel_select<MED, CLAW_LIM_NONE, PULL, REC>(tx, ty, nt, staging);
+    case CLAW_LIM_MINMOD: return step_kernel_select<MED, CLAW_LIM_MINMOD, PULL, REC>(tx, ty, nt, staging);
+    case CLAW_LIM_SUPERBEE: return step_kernel_select<MED, CLAW_LIM_SUPERBEE, PULL, REC>(tx, ty, nt, staging);
+    case CLAW_LIM_VANLEER: return step_kernel_select<MED, CLAW_LIM_VANLEER, PULL, REC>(tx, ty, nt, staging);
+    case CLAW_LIM_MC: return step_kernel_select<MED, CLAW_LIM_MC, PULL, REC>(tx, ty, nt, staging);
     }
     return StepKernel{nullptr, 0, 0};
 }
@@ -762,6 +854,8 @@ StepKernel step_kernel_uniform(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_uniform_pull(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_cellwise(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_cellwise_pull(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_cellwise_record(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_cellwise_record_fill(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_swe(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_swe_pull(int lim, int tx, int ty, int nt, int staging);
 

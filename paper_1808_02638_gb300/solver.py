@@ -231,6 +231,7 @@ class Hierarchy:
                 self.rbuf[Lf] = torch.zeros(max(1, claw.claw_reflux_buffer_size(self.ctx, Lf)),
                                             dtype=torch.float64, device=self.dev)
             self.__dict__.pop("_ghost_masks", None)
+            self.drop_graphs(buffers=True)
 
     # -------------------------------------------------------------- stepping
     def ratio(self, L):
@@ -480,6 +481,14 @@ class Hierarchy:
 
     def sync_status(self):
         return claw.claw_sync_status(self.ctx)
+
+    def drop_graphs(self, buffers=False):
+        """forgets the CUDA graphs the differentiable rollouts cached on this hierarchy (needed
+        after a tiling or a ghost-launch choice changes; Hierarchy.regrid and the autotuner call
+        it), and with `buffers` their tape and adjoint buffers too (the pools changed size)"""
+        self.__dict__.pop("_graphs", None)
+        if buffers:
+            self.__dict__.pop("_graph_buffers", None)
 
     # -------------------------------------------------------------- readback
     def pool(self, L):

@@ -60,6 +60,7 @@ def time_tiling(H, L, tiling, reps=5, pull=False):
     flags = claw.CLAW_ADVANCE_PULL_GHOSTS if pull else 0
     tx, ty, staging, threads = tiling
     claw.claw_set_tiling(H.ctx, L, tx, ty, staging, threads)
+    H.drop_graphs()
     src = H.q[L][H.cur[L]]
     dst = torch.empty_like(src)
     smax = torch.zeros_like(H.smax)
@@ -84,6 +85,7 @@ def tune_level(H, L, use_cache=True, candidates=None, pull=False):
         if hit:
             try:
                 claw.claw_set_tiling(H.ctx, L, *hit)
+                H.drop_graphs()
                 return tuple(hit), {}
             except claw.ClawError:
                 pass
@@ -97,6 +99,7 @@ def tune_level(H, L, use_cache=True, candidates=None, pull=False):
             continue   # e.g. bulk-copy staging not allowed for this level
     best = min(timings, key=timings.get)
     claw.claw_set_tiling(H.ctx, L, *best)
+    H.drop_graphs()
     with _lock:
         d = _load()
         d[key] = list(best)
@@ -136,6 +139,7 @@ def choose_pull(H, L, reps=5):
         torch.cuda.synchronize()
         times[name] = e0.elapsed_time(e1) / reps
     H.pull_levels[L] = times["pull"] <= times["fill"]
+    H.drop_graphs()
     return H.pull_levels[L], times
 
 

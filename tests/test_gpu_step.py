@@ -629,3 +629,36 @@ def test_fused_advance_equals_fill_step_update(case):
     torch.cuda.synchronize()
     assert torch.equal(A.pool(0), B.pool(0))
     assert A.sync_status() == 0 and B.sync_status() == 0
+
+
+def test_captured_graph_survives_descriptor_cache_churn(orc):
+    # a staged step captured into a CUDA graph reads the tensor-map descriptors of its pool; the
+    # context caches descriptors per pool and evicts old ones, but never one a capture has seen:
+    # after eager steps from more other pools than the cache holds, the graph still steps the
+    # right pool (equal to the eager step bit for bit)
+    import torch
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = 64
+    run, q = single_grid(n, pulse=False, seed=5)
+    H = Hierarchy([run], [[q]], rho0=1.3, K0=2.7, tiling=(32, 32, 1))
+    H.dt.fill_(0.005)
+    src, dst = H.q[0][0], H.q[0][1]
+    flags = claw.CLAW_ADVANCE_PULL_GHOSTS
+    claw.claw_level_advance(H.ctx, 0, src, dst, None, H.dt, H.smax, flags)   # descriptor of src cached
+    torch.cuda.synchronize()
+    want = dst.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        claw.claw_level_advance(H.ctx, 0, src, dst, None, H.dt, H.smax, flags, s)
+    torch.cuda.current_stream().wait_stream(s)
+    others = [src.clone() + 0.25 * k for k in range(1, 7)]
+    for o in others:   # six more pools through the cache
+        claw.claw_level_advance(H.ctx, 0, o, torch.empty_like(o), None, H.dt, H.smax, flags)
+    dst.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(H.interior(0, 0, 0, pool=dst), H.interior(0, 0, 0, pool=want))
+    assert H.sync_status() == 0
