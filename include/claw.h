@@ -283,8 +283,9 @@ int claw_average_down(claw_ctx* ctx, int32_t fine_level, const double* q_fine, d
  * lam_new, the adjoint of q_new (interior cells read), accumulates (+=) the adjoint of q_old
  * over all cells, ghosts included, into lam_old and the adjoint of the medium into g_aux
  * (medium = 1; may be NULL for medium = 0).  g_aux has the aux layout; the c^2 plane's
- * adjoint is folded into the c plane here (that plane of g_aux is left as it is), every other
- * plane receives its own adjoint.  The limiter branches of the forward step are recomputed
+ * adjoint is folded into the c plane here (that plane of g_aux is left as it is), the two
+ * 1/(Z_L+Z_R) planes receive their value times their adjoint (claw_medium_aux_adjoint expects
+ * that), every other plane its own adjoint.  The limiter branches of the forward step are recomputed
  * from q_old.  lam_old and g_aux must be zeroed by the caller
  * before the first accumulation. */
 int claw_level_step_adjoint(claw_ctx* ctx, int32_t level, const double* q_old, const double* lam_new,
@@ -348,7 +349,9 @@ int claw_fill_ghost_interp_adjoint(claw_ctx* ctx, int32_t level, double* lam, do
 int claw_average_down_adjoint(claw_ctx* ctx, int32_t fine_level, double* lam_fine,
                               double* lam_coarse, void* stream);
 
-/* Chain rule from the aux planes to rho and K: g_rho += d aux/d rho . g_aux, same for K. */
+/* Chain rule from the aux planes to rho and K: g_rho += d aux/d rho . g_aux, same for K, with
+ * g_aux as the adjoint calls leave it (each 1/(Z_L+Z_R) plane holding that value times its
+ * adjoint). */
 int claw_medium_aux_adjoint(claw_ctx* ctx, int32_t level, const double* rho, const double* K,
                             const double* g_aux, double* g_rho, double* g_K, void* stream);
 

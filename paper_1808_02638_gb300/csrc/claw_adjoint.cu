@@ -9,8 +9,8 @@
 // Each reverse phase is a gather where it can be (every adjoint written by one thread): the
 // wave-strength and state adjoints are stored per edge and summed per cell by the thread of
 // the cell (a shared-memory FP64 atomic costs an FP64-pipe slot on this part, like a DFMA).
-// The medium adjoints (per cell: Z, c, K; per edge: 1/(Z_L+Z_R) and the limiter projection
-// factors) go straight to g_aux with global FP64 reductions, which the L2 carries out, not
+// The medium adjoints (per cell: Z, c, K; per edge: 1/(Z_L+Z_R), as that value times its
+// adjoint, and the limiter projection factors) go straight to g_aux with global FP64 reductions, which the L2 carries out, not
 // the FP64 pipe; the chain rule of the edge planes to Z runs once per gradient in
 // claw_medium_aux_adjoint, not once per step.  Zero tests of doubles are integer tests (a
 // double compare is an FP64-pipe instruction).  The c^2 plane is folded
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(ANT, 2)
                     medadd(AUX_K, c, r, wG * dlo * gp);
                     medadd(AUX_C, c, r, wG * dlo * gv);
                     const double gpf = fma(Kc, dlo, -(klo * dme)), gvf = fma(cc, dlo, clo * dme);
-                    edgeadd(AUX_IYS, c, r, -0.5 * lx * fma(gpf, gp, gvf * gv));
+                    edgeadd(AUX_IYS, c, r, wG * fma(gpf, gp, gvf * gv));   // is x its adjoint
                 }
                 Db[DI(c, r)] = acc;
             }
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(ANT, 2)
                     medadd(AUX_K, c, r, wF * elo * fp);
                     medadd(AUX_C, c, r, wF * elo * fu);
                     const double fpf = fma(Kc, elo, -(klo * eme)), fuf = fma(cc, elo, clo * eme);
-                    edgeadd(AUX_IXS, c, r, -0.5 * ly * fma(fpf, fp, fuf * fu));
+                    edgeadd(AUX_IXS, c, r, wF * fma(fpf, fp, fuf * fu));
                 }
                 Eb[EI(c, r)] = acc;
             }
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(ANT, 2)
             A1b[XE(a, r)] = gn2 - gn1;              // adjoint of dp = p_a - p_{a-1}
             A2b[XE(a, r)] = fma(zr, gn1, zl * gn2); // adjoint of du
             if (MED) {
-                edgeadd(AUX_IXS, a, r, fma(n1, g1, n2 * g2));
+                edgeadd(AUX_IXS, a, r, fma(n1, gn1, n2 * gn2));   // is x its adjoint
                 medadd(AUX_Z, a, r, du * gn1);
                 medadd(AUX_Z, a - 1, r, du * gn2);
             }
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(ANT, 2)
             B1b[YE(c, b)] = gn2 - gn1;
             B2b[YE(c, b)] = fma(zr, gn1, zl * gn2);
             if (MED) {
-                edgeadd(AUX_IYS, c, b, fma(n1, g1, n2 * g2));
+                edgeadd(AUX_IYS, c, b, fma(n1, gn1, n2 * gn2));
                 medadd(AUX_Z, c, b, dv * gn1);
                 medadd(AUX_Z, c, b - 1, dv * gn2);
             }

@@ -15,7 +15,10 @@
 //   5. per cell: gather the jumps' adjoints into lam_old (global reductions; ghosts the forward
 //      pulled from a cell of the level go to that cell through the ghost ring).
 // Every medium adjoint is a global FP64 reduction into g_aux (carried out in the L2, not on the
-// FP64 pipe), with the aux layout and meaning of claw_level_step_adjoint.
+// FP64 pipe), with the aux layout and meaning of claw_level_step_adjoint (the 1/(Z_L+Z_R) planes
+// receive that value times its adjoint).  Accumulating the cell planes in shared memory instead
+// (one reduction per cell and plane) was measured slower: shared-memory FP64 atomics take
+// FP64-pipe slots.
 #include <cuda_runtime.h>
 
 #include "claw_step.cuh"
@@ -34,12 +37,15 @@ struct TGeo {
     static constexpr int YEW = TTX + 2, YE = YEW * (TTY + 3);   // y-edges b in [-1,ty+1], c in [-1,tx]
     static constexpr int XLW = TTX + 1, XL = XLW * (TTY + 2);   // limited x-edges a in [0,tx]
     static constexpr int YLW = TTX + 2, YL = YLW * (TTY + 1);   // limited y-edges b in [0,ty]
+    // the transverse gD / gE slots (read up to phase 2) share their space with the limiters'
+    // upwind slots (written from phase 3)
+    static constexpr int UN = (2 * YT + 2 * XT) > (2 * XL + 2 * YL) ? (2 * YT + 2 * XT) : (2 * XL + 2 * YL);
     static constexpr int O_GYLO = 0, O_GYHI = O_GYLO + YT, O_GXLO = O_GYHI + YT, O_GXHI = O_GXLO + XT;
-    static constexpr int O_CGX = O_GXHI + XT;         // gap, gau, gbp, gbu of the D cells
+    static constexpr int O_U1X = 0, O_U2X = O_U1X + XL, O_U1Y = O_U2X + XL, O_U2Y = O_U1Y + YL;
+    static constexpr int O_CGX = UN;                  // gap, gau, gbp, gbu of the D cells
     static constexpr int O_CGY = O_CGX + 4 * DN;      // gap, gav, gbp, gbv of the E cells
     static constexpr int O_A1B = O_CGY + 4 * EN, O_A2B = O_A1B + XE, O_B1B = O_A2B + XE, O_B2B = O_B1B + YE;
-    static constexpr int O_U1X = O_B2B + YE, O_U2X = O_U1X + XL, O_U1Y = O_U2X + XL, O_U2Y = O_U1Y + YL;
-    static constexpr int O_END = O_U2Y + YL;
+    static constexpr int O_END = O_B2B + YE;
     static size_t smem_bytes() { return (size_t)O_END * 8; }
 };
 
@@ -52,23 +58,39 @@ __device__ __forceinline__ double flip_sign(double x, int f)
     return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(f & 1) << 63));
 }
 
-// partial derivatives of phi(b/a) a at the branch the forward took (code in the tagged value m);
-// b is needed by van Leer only and computed by the caller then
-__device__ __forceinline__ void lim_partials(int code, double a, double b, double& da, double& db)
+// x 2^e for e in {-1, 0, 1} on the integer pipe (an exponent increment), the FP64 product where
+// that would leave the normal range (zeros, subnormals, overflow)
+__device__ __forceinline__ double mul_pow2(double x, int e)
+{
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return x;
+    if (ex > 1 && ex < 0x7fe) return __longlong_as_double(b + ((long long)e << 52));
+    return x * (e > 0 ? 2.0 : 0.5);
+}
+
+// the adjoint of a limited strength m = phi(b/a) a at the branch the forward took (code in the
+// tagged value m): own = g + (dm/da) gm, returns (dm/db) gm.  Every branch but van Leer's has
+// partials in {0, 1/2, 1, 2}, applied as exponent shifts; van Leer (2ab/(a+b)) needs b, which
+// the caller computes only then
+__device__ __forceinline__ double lim_adjoint(int code, double a, double b, double gm, double g, double& own)
 {
     switch (code) {
-    case LIMC_A: da = 1.0; db = 0.0; return;
-    case LIMC_B: da = 0.0; db = 1.0; return;
-    case LIMC_2A: da = 2.0; db = 0.0; return;
-    case LIMC_2B: da = 0.0; db = 2.0; return;
-    case LIMC_HALF: da = 0.5; db = 0.5; return;
-    case LIMC_SMOOTH: {   // 2ab/(a+b)
-        const double s = a + b, is2 = 1.0 / (s * s);
-        da = 2.0 * b * b * is2;
-        db = 2.0 * a * a * is2;
-        return;
+    case LIMC_A: own = g + gm; return 0.0;
+    case LIMC_B: own = g; return gm;
+    case LIMC_2A: own = g + mul_pow2(gm, 1); return 0.0;
+    case LIMC_2B: own = g; return mul_pow2(gm, 1);
+    case LIMC_HALF: {
+        const double h = mul_pow2(gm, -1);
+        own = g + h;
+        return h;
     }
-    default: da = 0.0; db = 0.0; return;
+    case LIMC_SMOOTH: {
+        const double s = a + b, is2 = 1.0 / (s * s);
+        own = fma(2.0 * b * b * is2, gm, g);
+        return 2.0 * a * a * is2 * gm;
+    }
+    default: own = g; return 0.0;
     }
 }
 
@@ -150,7 +172,7 @@ __global__ void __launch_bounds__(TNT, 4)
                 const double X = fma(Khi, U, chi * V), Y = fma(clo, V, -(Klo * U));
                 GYlo[c + jj * TTX] = is * X;
                 GYhi[c + jj * TTX] = is * Y;
-                medadd(AUX_IYS, c, jj, fma(Dlo, X, Dhi * Y));
+                medadd(AUX_IYS, c, jj, fma(Dlo, GYlo[c + jj * TTX], Dhi * GYhi[c + jj * TTX]));   // is x its adjoint
                 const double sl = is * Dlo, sh = is * Dhi;
                 medadd(AUX_K, c, jj, sl * U);
                 medadd(AUX_C, c, jj, sl * V);
@@ -174,7 +196,7 @@ __global__ void __launch_bounds__(TNT, 4)
                 const double X = fma(KR, U, cR * V), Y = fma(cL, V, -(KL * U));
                 GXlo[a + r * (TTX + 1)] = is * X;
                 GXhi[a + r * (TTX + 1)] = is * Y;
-                medadd(AUX_IXS, a, r, fma(EL, X, ER * Y));
+                medadd(AUX_IXS, a, r, fma(EL, GXlo[a + r * (TTX + 1)], ER * GXhi[a + r * (TTX + 1)]));
                 const double sl = is * EL, sh = is * ER;
                 medadd(AUX_K, a, r, sl * U);
                 medadd(AUX_C, a, r, sl * V);
@@ -274,22 +296,21 @@ __global__ void __launch_bounds__(TNT, 4)
             medadd(AUX_C, a, r, fma(-2.0 * lx, cr, 1.0) * (m2 * ge2));
             medadd(AUX_Z, a, r, (kr * m2) * gcp);
             medadd(AUX_Z, a - 1, r, -((kl * m1) * gcp));
-            double da, db;
             {   // left-going wave: upwind edge a+1
                 const double up = TP(TAPE_A1, a + 1, r), f = AX(AUX_FX1, a, r);
                 const int code = (int)(__double_as_longlong(m1) & 7);
-                lim_partials(code, TP(TAPE_A1, a, r), code == LIMC_SMOOTH ? up * f : 0.0, da, db);
-                const double dg = db * gm1;
-                A1b[XE(a, r)] = fma(da, gm1, g1);
+                double own;
+                const double dg = lim_adjoint(code, TP(TAPE_A1, a, r), code == LIMC_SMOOTH ? up * f : 0.0, gm1, g1, own);
+                A1b[XE(a, r)] = own;
                 U1x[XL(a, r)] = f * dg;   // to edge a+1
                 medadd(AUX_FX1, a, r, up * dg);
             }
             {   // right-going wave: upwind edge a-1
                 const double up = TP(TAPE_A2, a - 1, r), f = AX(AUX_FX2, a, r);
                 const int code = (int)(__double_as_longlong(m2) & 7);
-                lim_partials(code, TP(TAPE_A2, a, r), code == LIMC_SMOOTH ? up * f : 0.0, da, db);
-                const double dg = db * gm2;
-                A2b[XE(a, r)] = fma(da, gm2, g2);
+                double own;
+                const double dg = lim_adjoint(code, TP(TAPE_A2, a, r), code == LIMC_SMOOTH ? up * f : 0.0, gm2, g2, own);
+                A2b[XE(a, r)] = own;
                 U2x[XL(a, r)] = f * dg;   // to edge a-1
                 medadd(AUX_FX2, a, r, up * dg);
             }
@@ -323,22 +344,21 @@ __global__ void __launch_bounds__(TNT, 4)
             medadd(AUX_C, c, b, fma(-2.0 * ly, cr, 1.0) * (m2 * ge2));
             medadd(AUX_Z, c, b, (kr * m2) * gcp);
             medadd(AUX_Z, c, b - 1, -((kl * m1) * gcp));
-            double da, db;
             {
                 const double up = TP(TAPE_B1, c, b + 1), f = AX(AUX_FY1, c, b);
                 const int code = (int)(__double_as_longlong(m1) & 7);
-                lim_partials(code, TP(TAPE_B1, c, b), code == LIMC_SMOOTH ? up * f : 0.0, da, db);
-                const double dg = db * gm1;
-                B1b[YE(c, b)] = fma(da, gm1, g1);
+                double own;
+                const double dg = lim_adjoint(code, TP(TAPE_B1, c, b), code == LIMC_SMOOTH ? up * f : 0.0, gm1, g1, own);
+                B1b[YE(c, b)] = own;
                 U1y[YL(c, b)] = f * dg;   // to edge b+1
                 medadd(AUX_FY1, c, b, up * dg);
             }
             {
                 const double up = TP(TAPE_B2, c, b - 1), f = AX(AUX_FY2, c, b);
                 const int code = (int)(__double_as_longlong(m2) & 7);
-                lim_partials(code, TP(TAPE_B2, c, b), code == LIMC_SMOOTH ? up * f : 0.0, da, db);
-                const double dg = db * gm2;
-                B2b[YE(c, b)] = fma(da, gm2, g2);
+                double own;
+                const double dg = lim_adjoint(code, TP(TAPE_B2, c, b), code == LIMC_SMOOTH ? up * f : 0.0, gm2, g2, own);
+                B2b[YE(c, b)] = own;
                 U2y[YL(c, b)] = f * dg;   // to edge b-1
                 medadd(AUX_FY2, c, b, up * dg);
             }
@@ -366,7 +386,7 @@ __global__ void __launch_bounds__(TNT, 4)
             const double du = a1 + a2;                // is (Z_L + Z_R) du
             medadd(AUX_Z, a, r, du * gn1);
             medadd(AUX_Z, a - 1, r, du * gn2);
-            medadd(AUX_IXS, a, r, fma(a1, g1, a2 * g2) * (zl + zr));   // (a1 g1 + a2 g2) / is
+            medadd(AUX_IXS, a, r, fma(a1, g1, a2 * g2));   // is x the adjoint of is
         }
         for (int k = tid; k < (ty + 3) * (tx + 2); k += TNT) {
             const int b = k / (tx + 2) - 1, c = k - (b + 1) * (tx + 2) - 1;
@@ -386,7 +406,7 @@ __global__ void __launch_bounds__(TNT, 4)
             const double dv = b1 + b2;
             medadd(AUX_Z, c, b, dv * gn1);
             medadd(AUX_Z, c, b - 1, dv * gn2);
-            medadd(AUX_IYS, c, b, fma(b1, g1, b2 * g2) * (zl + zr));
+            medadd(AUX_IYS, c, b, fma(b1, g1, b2 * g2));
         }
         __syncthreads();
 

@@ -353,8 +353,9 @@ __global__ void medium_aux_adjoint_kernel(const PatchDev* __restrict__ patches, 
             const double zw = sqrt(k[e2] * r[e2]);
             const double zz = fma(zw, z, 1.0), s = zw + z;
             const double d1 = fma(zw, zw, 1.0), d2 = fma(z, z, 1.0);
-            // ixs = 1/s ; fx1 = zz/d1 ; fx2 = zz/d2  -> derivatives w.r.t. z (this cell)
-            gz += g[ip * WH + e] * (-1.0 / (s * s)) + g[p1 * WH + e] * (zw / d1) +
+            // ixs = 1/s ; fx1 = zz/d1 ; fx2 = zz/d2  -> derivatives w.r.t. z (this cell); the ixs
+            // plane holds ixs times its adjoint: d(1/s)/dz x adjoint = -(1/s^2) (s x plane) = -plane / s
+            gz += -g[ip * WH + e] / s + g[p1 * WH + e] * (zw / d1) +
                   g[p2 * WH + e] * (zw / d2 - zz * 2.0 * z / (d2 * d2));
             (void)po;
         };
@@ -363,7 +364,7 @@ __global__ void medium_aux_adjoint_kernel(const PatchDev* __restrict__ patches, 
             const double zr = sqrt(k[e2] * r[e2]);
             const double zz = fma(z, zr, 1.0), s = z + zr;
             const double d1 = fma(z, z, 1.0), d2 = fma(zr, zr, 1.0);
-            gz += g[ip * WH + e2] * (-1.0 / (s * s)) + g[p1 * WH + e2] * (zr / d1 - zz * 2.0 * z / (d1 * d1)) +
+            gz += -g[ip * WH + e2] / s + g[p1 * WH + e2] * (zr / d1 - zz * 2.0 * z / (d1 * d1)) +
                   g[p2 * WH + e2] * (zr / d2);
         };
         if (i > 0) edge_right(AUX_IXS, 0, AUX_FX1, AUX_FX2, e - 1);
