@@ -412,6 +412,13 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e2e_value, _, _ = replicas.whole_job_rate(e2e_steps * N_CELLS, e0.elapsed_time(e1), dist, dev)
+    # the copy bound of that loop: qbytes each way per step at the measured pinned-copy rates
+    # (each direction alone, and the aggregate of both at once)
+    from paper_1808_02638_gb300 import measure as _m
+    copies = _m.host_copy_bandwidth(device=dev.index if dev.index is not None else 0)
+    bound_s = max(qbytes / (copies["h2d_gbs"] * 1e9), qbytes / (copies["d2h_gbs"] * 1e9),
+                  2 * qbytes / (copies["both_gbs"] * 1e9))
+    copy_bound = world * N_CELLS / bound_s
 
     per_config = None
     if rank == 0 and not args.no_configs:
@@ -467,7 +474,10 @@ def main():
         "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm, "frac": achieved_gbs / hbm,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
         "plain_per_patch": plain,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes,
+                "copy_bound": copy_bound, "frac_of_copy_bound": e2e_value / copy_bound, "host_copies": copies,
+                "note": "copy bound = cell-updates per step / max(bytes/h2d, bytes/d2h, 2 bytes/both) with the "
+                        "host_copies rates measured in this run"},
         "gpu_launches": per_step_launches * K,
         "tuning_ms": {f"{a}x{b}/s{c}/t{d}": round(v, 4) for (a, b, c, d), v in tune_ms.items()},
         "clocks": clocks,

@@ -268,6 +268,56 @@ def config4(nruns=64, ncoarse=100, every=20, plain=True):
                                              "backward = adjoint steps only"}})
 
 
+def host_copy_bandwidth(nbytes=100 * 2 ** 20, reps=20, device=0):
+    """Pinned host <-> device copy rates (GB/s) with CUDA events: host to device alone, device to
+    host alone, and both at once on two streams (the aggregate bytes of both directions over the
+    time both take), each over `reps` copies of `nbytes` after two warm-up copies."""
+    dev = torch.device("cuda", device)
+    n = nbytes // 8
+    h_in = torch.empty(n, dtype=torch.float64).pin_memory()
+    h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    d_a = torch.empty(n, dtype=torch.float64, device=dev)
+    d_b = torch.empty(n, dtype=torch.float64, device=dev)
+    h_in.fill_(1.0)
+    d_b.fill_(2.0)
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) * 1e-3
+
+    def h2d():
+        d_a.copy_(h_in, non_blocking=True)
+
+    def d2h():
+        h_out.copy_(d_b, non_blocking=True)
+
+    def both():
+        cur = torch.cuda.current_stream(dev)
+        s_in.wait_stream(cur)
+        s_out.wait_stream(cur)
+        with torch.cuda.stream(s_in):
+            d_a.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            h_out.copy_(d_b, non_blocking=True)
+        cur.wait_stream(s_in)
+        cur.wait_stream(s_out)
+
+    t_in, t_out, t_both = timed(h2d), timed(d2h), timed(both)
+    return {"bytes": nbytes, "reps": reps, "h2d_gbs": reps * nbytes / t_in / 1e9,
+            "d2h_gbs": reps * nbytes / t_out / 1e9, "both_gbs": 2 * reps * nbytes / t_both / 1e9,
+            "method": "pinned host memory, CUDA events around reps copies on the current stream (both: "
+                      "one copy each way per rep on two streams)"}
+
+
 def time_stepper(H, nsteps, warm=3):
     """ms per step of a one-level hierarchy through its fused stepper (graph replays of the
     persistent step with the device Eq. cfl update, then of the ghost copy)"""

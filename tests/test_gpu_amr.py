@@ -107,6 +107,36 @@ def test_batched_independent_runs_two_levels_cellwise():
     assert H.sync_status() == 0
 
 
+def test_all_64_batched_runs_one_coarse_step_with_the_tuned_launch():
+    # the batched-runs workload at full breadth: all 64 independent 2-level runs (9226 boxes on
+    # level 1, per-run heterogeneous media) in one hierarchy, with the tiling and ghost-launch
+    # choice the autotuner installs for the benchmark, one coarse step, every run against its
+    # own oracle hierarchy
+    from oracle.amr import OracleHierarchy
+    from paper_1808_02638_gb300 import measure
+    from paper_1808_02638_gb300.solver import Hierarchy
+    runs = inputs.config4_runs(64)
+    qs, rhos, Ks, orcs = [], [], [], []
+    for run, rho2, K2 in runs:
+        q = [inputs.init_q(run, lev) for lev in run.levels]
+        r = [inputs.coef_pool(lev, rho2, 4 ** L) for L, lev in enumerate(run.levels)]
+        k = [inputs.coef_pool(lev, K2, 4 ** L) for L, lev in enumerate(run.levels)]
+        qs.append(q)
+        rhos.append(r)
+        Ks.append(k)
+        orcs.append(OracleHierarchy(run, q, r, k))
+    H = Hierarchy([r for r, _, _ in runs], qs, rhos, Ks)
+    H.init_dt()
+    measure.tune_all(H)   # times steps into scratch pools; the state keeps its interiors
+    H.init_dt()
+    H.coarse_step()
+    for O in orcs:
+        O.coarse_step()
+    worst = max(_compare_all_levels(H, orcs[ri], ri, TOL1) for ri in range(len(runs)))
+    assert worst <= TOL1
+    assert H.sync_status() == 0
+
+
 # ------------------------------------------------------------ conservation fix (Sec. 2.3)
 def _flowing_pulse(run):
     q = []
