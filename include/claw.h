@@ -226,6 +226,20 @@ int claw_level_step(claw_ctx* ctx, int32_t level, const double* q_old, double* q
 int claw_level_advance(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
                        const double* aux, double* dt, double* smax, int32_t flags, void* stream);
 
+/* claw_level_advance with CLAW_ADVANCE_PULL_GHOSTS (required) in which the step also evaluates
+ * the ghosts of q_old that come from the coarser level (Sec. 2.2: space-time interpolation,
+ * the same values claw_fill_ghost_interp writes) from qc_old, qc_new (the coarser level's
+ * states at the start and end of its step, device pools) at the time fraction tau in [0, 1],
+ * instead of reading them from q_old.  So one launch is the whole fine level-step: no ghost of
+ * q_old is read from q_old's ghost cells, and none is written.  For level 0, or a level without
+ * interpolated ghosts, it is claw_level_advance and qc_old, qc_new may be NULL.  Shallow water
+ * (no fused kernel) fills those ghosts of q_old with the interpolation launch first, on the same
+ * stream (two launches, the same values).
+ * Errors as claw_level_advance; CLAW_EINVAL without the pull flag or without coarse states. */
+int claw_level_advance_interp(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
+                              const double* aux, double* dt, double* smax, int32_t flags,
+                              const double* qc_old, const double* qc_new, double tau, void* stream);
+
 /* claw_level_advance restricted to the boxes [box_begin, box_end) of the level (their tiles, in
  * box order): a level-step taken in pieces, so that host copies of some boxes overlap the steps
  * of others.  The pieces of one step, in any order, give bit for bit the claw_level_advance of

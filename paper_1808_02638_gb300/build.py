@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         os.replace(obj + ".tmp", obj)
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(max(8, os.cpu_count() or 8), len(srcs))) as ex:
         results = list(ex.map(compile_one, srcs))
     objs = [o for o, _ in results]
     if verbose:

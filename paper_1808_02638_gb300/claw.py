@@ -79,6 +79,7 @@ _SIGNATURES = {
     "claw_level_step_patchwise": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
     "claw_level_advance": ([VP, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
     "claw_level_advance_boxes": ([VP, I32, I32, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
+    "claw_level_advance_interp": ([VP, I32, VP, VP, VP, VP, VP, I32, VP, VP, DBL, VP], ctypes.c_int),
     "claw_packed_size": ([VP, I32], ctypes.c_longlong),
     "claw_pack_interiors": ([VP, I32, I32, I32, VP, VP, VP], ctypes.c_int),
     "claw_unpack_interiors": ([VP, I32, I32, I32, VP, VP, VP], ctypes.c_int),
@@ -335,6 +336,13 @@ def claw_level_advance_boxes(ctx, level, box_begin, box_end, q_old, q_new, aux, 
 def claw_level_advance(ctx, level, q_old, q_new, aux, dt, smax, flags, stream=None):
     _check("claw_level_advance", load().claw_level_advance(
         ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax), int(flags), _stream(stream)))
+
+
+def claw_level_advance_interp(ctx, level, q_old, q_new, aux, dt, smax, flags, qc_old=None, qc_new=None, tau=0.0,
+                              stream=None):
+    _check("claw_level_advance_interp", load().claw_level_advance_interp(
+        ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax), int(flags), _ptr(qc_old), _ptr(qc_new),
+        DBL(tau), _stream(stream)))
 
 
 def claw_level_step_patchwise(ctx, level, q_old, q_new, aux, dt, smax, stream=None):

@@ -533,7 +533,7 @@ int build_ghost_tables(claw_ctx* ctx, int L, GhostTables& gt, bool want_ring)
                     }
                     continue;
                 }
-                if (out.want_ring) out.ring.push_back(make_longlong2(-1, 0));
+                if (out.want_ring) out.ring.push_back(make_longlong2(-1 - (long long)out.cells.size(), 0));
                 // space-time interpolation from level L-1 at the fine cell (si, sj)
                 if (L == 0) return CLAW_EINVAL;
                 InterpCell c;
@@ -1255,6 +1255,7 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         P.ny = b.ny;
         P.run = b.run;
         P.ring = -1;
+        P.interp = 0;
         P.dxinv = 1.0 / level_dx(p, L);
         P.dyinv = 1.0 / level_dy(p, L);
         P.dtscale = 1.0;
@@ -1272,6 +1273,13 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     d.ring_ok = gt.ring_ok;
     for (auto& P : d.hpatches)
         if (!d.ring_ok) P.ring = -1;
+    {   // each box's first interpolated cell in the concatenated table (box order)
+        long long c = 0;
+        for (int n = 0; n < d.nboxes; ++n) {
+            d.hpatches[n].interp = (int)c;
+            c += (long long)gt.per[n].cells.size();
+        }
+    }
     // every table stays alive until pack.commit reads it
     ArenaPack pack;
     if (d.ring_ok)
@@ -1529,18 +1537,34 @@ int claw_level_step(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new
     return cuda_rc(launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s));
 }
 
-int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux, double* dt,
-                       double* smax, int32_t flags, void* stream)
+static int level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux, double* dt,
+                         double* smax, int32_t flags, const double* qc_old, const double* qc_new, double tau,
+                         bool interp, void* stream)
 {
     int rc = check_step_args(ctx, L, q_old, q_new, aux, dt, smax);
     if (rc) return rc;
     if (flags & ~(CLAW_ADVANCE_PUSH_GHOSTS | CLAW_ADVANCE_UPDATE_DT | CLAW_ADVANCE_PULL_GHOSTS)) return CLAW_EINVAL;
     if ((flags & CLAW_ADVANCE_PULL_GHOSTS) && !ctx->lev[L].ring_ok) return CLAW_EINVAL;
-    DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
+    if (interp && d.ninterp > 0 &&
+        (!(flags & CLAW_ADVANCE_PULL_GHOSTS) || !qc_old || !qc_new || !(tau >= 0.0 && tau <= 1.0)))
+        return CLAW_EINVAL;
+    DevGuard g(ctx->device);
     if (d.ntiles == 0) return CLAW_OK;
     cudaStream_t s = (cudaStream_t)stream;
     StepArgs a = make_args(ctx, L, q_old, q_new, aux, dt, smax);
+    if (interp && d.ninterp > 0) {
+        if (ctx->kind() == KIND_SWE) {   // no fused kernel: the interpolation launch fills them first
+            cudaError_t e = launch_fill_interp(d.interps, d.ninterp, const_cast<double*>(q_old), qc_old, qc_new, tau, s);
+            ctx->launches += 1;
+            if (e != cudaSuccess) return CLAW_ECUDA;
+        } else {
+            a.interp = d.interps;
+            a.cold = qc_old;
+            a.cnew = qc_new;
+            a.tau = tau;
+        }
+    }
     if (flags & CLAW_ADVANCE_UPDATE_DT) {
         a.dtupd = 1;
         a.dt_out = dt;
@@ -1555,7 +1579,8 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
         a.tmaps = get_tmaps(ctx, L, q_old, s);
         if (!a.tmaps) staging = 0;
     }
-    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, a.ring != nullptr);
+    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, a.ring != nullptr,
+                                            false, a.interp != nullptr);
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;
@@ -1565,6 +1590,19 @@ int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_
         ctx->launches += 1;
     }
     return cuda_rc(e);
+}
+
+int claw_level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux, double* dt,
+                       double* smax, int32_t flags, void* stream)
+{
+    return level_advance(ctx, L, q_old, q_new, aux, dt, smax, flags, nullptr, nullptr, 0.0, false, stream);
+}
+
+int claw_level_advance_interp(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,
+                              double* dt, double* smax, int32_t flags, const double* qc_old, const double* qc_new,
+                              double tau, void* stream)
+{
+    return level_advance(ctx, L, q_old, q_new, aux, dt, smax, flags, qc_old, qc_new, tau, true, stream);
 }
 
 int claw_level_advance_boxes(claw_ctx* ctx, int32_t L, int32_t box_begin, int32_t box_end, const double* q_old,

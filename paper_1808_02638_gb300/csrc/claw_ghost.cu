@@ -5,7 +5,7 @@
 // (claw_set_level) so that each launch is a flat loop over tasks.
 #include <cuda_runtime.h>
 
-#include "claw_internal.h"
+#include "claw_interp.cuh"
 
 namespace claw {
 
@@ -140,16 +140,7 @@ cudaError_t launch_fill_copy_adjoint(const CopyRect* r, const int* start, int nb
 }
 
 // ------------------------------------------------------------------------ interpolation
-__device__ __forceinline__ double minmod(double a, double b)
-{
-    if (!(a * b > 0.0)) return 0.0;
-    return fabs(a) < fabs(b) ? a : b;
-}
-
-__device__ __forceinline__ double sgn_of(int flags, int m)
-{
-    return ((m == 1 && (flags & 1)) || (m == 2 && (flags & 2))) ? -1.0 : 1.0;
-}
+__device__ __forceinline__ double sgn_of(int flags, int m) { return interp_sign(flags, m); }
 
 // thread per (fine ghost cell, component)
 __global__ void fill_interp_kernel(const InterpCell* __restrict__ cells, int n, double* __restrict__ q,
@@ -160,15 +151,7 @@ __global__ void fill_interp_kernel(const InterpCell* __restrict__ cells, int n, 
     if (k >= 3 * n) return;
     const int i = k / 3, m = k - 3 * i;
     const InterpCell C = cells[i];
-    double Q[5];
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const long long o = C.src[s] + m * C.splane[s];
-        Q[s] = sgn_of(C.sflags[s], m) * ((1.0 - tau) * cold[o] + tau * cnew[o]);
-    }
-    const double sx = minmod(Q[2] - Q[0], Q[0] - Q[1]);
-    const double sy = minmod(Q[4] - Q[0], Q[0] - Q[3]);
-    q[C.dst + m * C.dplane] = sgn_of(C.flags, m) * (Q[0] + C.xi * sx + C.eta * sy);
+    q[C.dst + m * C.dplane] = interp_value(C, m, cold, cnew, tau);
 }
 
 __global__ void fill_interp_adjoint_kernel(const InterpCell* __restrict__ cells, int n,
@@ -181,11 +164,7 @@ __global__ void fill_interp_adjoint_kernel(const InterpCell* __restrict__ cells,
     const int i = k / 3, m = k - 3 * i;
     const InterpCell C = cells[i];
     double Q[5], G[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const long long o = C.src[s] + m * C.splane[s];
-        Q[s] = sgn_of(C.sflags[s], m) * ((1.0 - tau) * cold[o] + tau * cnew[o]);
-    }
+    interp_coarse(C, m, cold, cnew, tau, Q);
     const long long d = C.dst + m * C.dplane;
     const double g = sgn_of(C.flags, m) * lam[d];
     lam[d] = 0.0;

@@ -59,6 +59,7 @@ struct PatchDev {
     int nx, ny;       // interior size
     int run;          // index into the per-run dt / smax arrays
     int ring;         // first entry of the box's ghost ring in the level's ring table (-1: none)
+    int interp;       // first of the box's interpolated ghost cells in the level's InterpCell table
     double dxinv, dyinv;
     double dtscale;   // this level's dt / level-0 dt = 1 / (ratio_1 ... ratio_L)
 };
@@ -178,8 +179,9 @@ struct LevelDev {
 // Ghost ring of a box: its (nx+4)(ny+4) - nx ny ghost cells in row order of the padded box.
 // Entry {source, plane | sign flags << 48}: the ghost takes the pool's plane-0 element `source`
 // and the elements one and two planes (`plane` elements) further, u negated if bit 0 of the
-// flags, v if bit 1; a source of -1 marks a ghost interpolated from the coarser level (read from
-// the pool itself).
+// flags, v if bit 1; a source of -1 - j marks the box's j-th ghost interpolated from the coarser
+// level (entry PatchDev::interp + j of the level's InterpCell table), which the step either reads
+// from the pool (filled by claw_fill_ghost_interp) or evaluates itself (claw_level_advance_interp).
 constexpr int kRingFlagShift = 48;
 __host__ __device__ inline int ring_index(int xp, int yp, int nx, int ny)   // -1: interior
 {
@@ -223,6 +225,12 @@ struct StepArgs {
     // copies still in flight are then awaited with the full bound kWaitPolls before it exits
     unsigned wait_polls = kWaitPolls;
     double* tape = nullptr;   // recording step (cell-wise medium): the level-step's tape, aux layout
+    // pulled ghosts interpolated from the coarser level inside the step (not null: the ring's
+    // interpolated entries point into this table, evaluated from cold / cnew at tau)
+    const InterpCell* interp = nullptr;
+    const double* cold = nullptr;
+    const double* cnew = nullptr;
+    double tau = 0.0;
 };
 
 // error flag bits written by kernels
@@ -235,7 +243,7 @@ enum : int { KIND_UNIFORM = 0, KIND_CELLWISE = 1, KIND_SWE = 2 };
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s);
 int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull = false,
-                         bool rec = false);
+                         bool rec = false, bool interp = false);
 cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
                                 int medium, int limiter, int nsm, cudaStream_t s);   // grid: resident CTAs x nsm
 int adjoint_tile();   // the adjoint kernel's square tile edge

@@ -7,8 +7,15 @@
 
 namespace claw {
 
-static StepKernel pick(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull, bool rec = false)
+static StepKernel pick(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull, bool rec = false,
+                       bool interp = false)
 {
+    if (interp) {   // acoustics only; shallow water takes the interpolation launch first (claw_api.cu)
+        if (!pull || rec) return StepKernel{nullptr, 0, 0};
+        if (kind == KIND_UNIFORM) return step_kernel_uniform_interp(limiter, tx, ty, nt, staging);
+        if (kind == KIND_CELLWISE) return step_kernel_cellwise_interp(limiter, tx, ty, nt, staging);
+        return StepKernel{nullptr, 0, 0};
+    }
     if (rec) {
         if (kind != KIND_CELLWISE) return StepKernel{nullptr, 0, 0};
         return pull ? step_kernel_cellwise_record(limiter, tx, ty, nt, staging)
@@ -43,9 +50,9 @@ static cudaError_t prepare(const StepKernel& k)
     return e;
 }
 
-int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull, bool rec)
+int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull, bool rec, bool interp)
 {
-    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, pull, rec);
+    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, pull, rec, interp);
     if (!k.fn || prepare(k) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k.fn, k.nt, k.smem) != cudaSuccess)
@@ -56,7 +63,7 @@ int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int stag
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s)
 {
-    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, a.ring != nullptr, a.tape != nullptr);
+    StepKernel k = pick(kind, limiter, tx, ty, nt, staging, a.ring != nullptr, a.tape != nullptr, a.interp != nullptr);
     if (!k.fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare(k);
     if (e != cudaSuccess) return e;

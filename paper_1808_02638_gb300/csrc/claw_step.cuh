@@ -25,7 +25,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
-#include "claw_internal.h"
+#include "claw_interp.cuh"
 
 namespace claw {
 
@@ -258,9 +258,11 @@ __device__ __forceinline__ void finish_cta(const StepArgs& A)
 // Same-level and physical-boundary ghosts of a staged tile, taken from their source cells in
 // q_old (the box's ghost ring table) instead of the pool's own ghost cells: only the frame of
 // width two around the tile can hold ghosts of its box.  Ghosts interpolated from the coarser
-// level keep the staged value.  The caller separates this from the staging and from the
-// tile's first reads with barriers.
-template <int SW, int QPL, int NT>
+// level are evaluated from the coarse states in the instantiations with INTERP (the same
+// arithmetic as the ghost-fill kernel; a separate instantiation, as the code alone costs the
+// other kernels registers), else keep the staged value.  The caller separates this from the
+// staging and from the tile's first reads with barriers.
+template <int SW, int QPL, int NT, bool INTERP = false>
 __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P, double* sq, int x0, int y0, int tx,
                                             int ty)
 {
@@ -279,7 +281,16 @@ __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P
         const int ri = ring_index(x0 + xs, y0 + ys, P.nx, P.ny);
         if (ri < 0) continue;
         const longlong2 e = __ldg(&A.ring[P.ring + ri]);
-        if (e.x < 0) continue;
+        if (e.x < 0) {   // interpolated from the coarser level
+            if (INTERP) {
+                const InterpCell C = A.interp[P.interp + (int)(-1 - e.x)];
+                const int i = xs + ys * SW;
+                sq[i] = interp_value(C, 0, A.cold, A.cnew, A.tau);
+                sq[QPL + i] = interp_value(C, 1, A.cold, A.cnew, A.tau);
+                sq[2 * QPL + i] = interp_value(C, 2, A.cold, A.cnew, A.tau);
+            }
+            continue;
+        }
         const long long sp = e.y & ((1LL << kRingFlagShift) - 1);
         const double* src = A.qold + e.x;
         const unsigned fl = (unsigned)(e.y >> kRingFlagShift);
@@ -303,12 +314,13 @@ __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P
 // STAGE: 0 cooperative loads, 1 tensor bulk copies (double buffered: the next tile streams in
 // during the whole of this one), 2 tensor bulk copies into one buffer (the next tile is requested
 // once this one's state has been read, in phase D) with registers capped for three CTAs per SM.
-// PULL: same-level and boundary ghosts are taken from their source cells (a separate
-// instantiation: the mere presence of the pull code slowed the other kernels by up to 11 %).
+// PULL: 1 same-level and boundary ghosts are taken from their source cells (a separate
+// instantiation: the mere presence of the pull code slowed the other kernels by up to 11 %);
+// 2 those and the ghosts interpolated from the coarser level, evaluated in the step.
 // REC (cell-wise medium): also write the step's intermediates to the tape A.tape (TapePlane);
 // each padded cell's entries come from the one tile that owns the cell (its interior, plus the
 // box's ghost frame next to it), so the tape is the same whatever the tiling.
-template <int MED, int LIM, int TX, int TY, int NT, int STAGE, bool PULL, bool REC = false>
+template <int MED, int LIM, int TX, int TY, int NT, int STAGE, int PULL, bool REC = false>
 __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const StepArgs A)
 {
     static_assert(!REC || MED == 1, "the tape records the cell-wise step");
@@ -414,7 +426,7 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
             __syncthreads();
         }
         if (PULL && P.ring >= 0) {
-            pull_ghosts<G::SW, G::QPL, NT>(A, P, sq, x0, y0, tx, ty);
+            pull_ghosts<G::SW, G::QPL, NT, PULL == 2>(A, P, sq, x0, y0, tx, ty);
             __syncthreads();
         }
 
@@ -804,7 +816,7 @@ struct StepKernel {
     int nt;
 };
 
-template <int MED, int LIM, int TX, int TY, int NT, int STAGE, bool PULL, bool REC = false>
+template <int MED, int LIM, int TX, int TY, int NT, int STAGE, int PULL, bool REC = false>
 StepKernel step_kernel_entry()
 {
     StepKernel k;
@@ -816,7 +828,7 @@ StepKernel step_kernel_entry()
 
 // all tile shapes and stagings of one medium and limiter
 // tile shapes x thread counts x stagings of one medium and limiter (nt = 0: the default)
-template <int MED, int LIM, bool PULL, bool REC = false>
+template <int MED, int LIM, int PULL, bool REC = false>
 StepKernel step_kernel_select(int tx, int ty, int nt, int staging)
 {
     if (tx == 32 && ty == 32 && (nt == 0 || nt == 256))
@@ -836,7 +848,7 @@ StepKernel step_kernel_select(int tx, int ty, int nt, int staging)
     return StepKernel{nullptr, 0, 0};
 }
 
-template <int MED, bool PULL, bool REC = false>
+template <int MED, int PULL, bool REC = false>
 StepKernel step_kernel_for(int lim, int tx, int ty, int nt, int staging)
 {
     switch (lim) {
@@ -854,6 +866,8 @@ StepKernel step_kernel_uniform(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_uniform_pull(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_cellwise(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_cellwise_pull(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_uniform_interp(int lim, int tx, int ty, int nt, int staging);
+StepKernel step_kernel_cellwise_interp(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_cellwise_record(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_cellwise_record_fill(int lim, int tx, int ty, int nt, int staging);
 StepKernel step_kernel_swe(int lim, int tx, int ty, int nt, int staging);

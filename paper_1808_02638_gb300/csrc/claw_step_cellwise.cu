@@ -4,6 +4,6 @@
 namespace claw {
 StepKernel step_kernel_cellwise(int lim, int tx, int ty, int nt, int staging)
 {
-    return step_kernel_for<1, false>(lim, tx, ty, nt, staging);
+    return step_kernel_for<1, 0>(lim, tx, ty, nt, staging);
 }
 }  // namespace claw

@@ -5,6 +5,6 @@
 namespace claw {
 StepKernel step_kernel_cellwise_record_fill(int lim, int tx, int ty, int nt, int staging)
 {
-    return step_kernel_for<1, false, true>(lim, tx, ty, nt, staging);
+    return step_kernel_for<1, 0, true>(lim, tx, ty, nt, staging);
 }
 }  // namespace claw

@@ -4,6 +4,6 @@
 namespace claw {
 StepKernel step_kernel_uniform_pull(int lim, int tx, int ty, int nt, int staging)
 {
-    return step_kernel_for<0, true>(lim, tx, ty, nt, staging);
+    return step_kernel_for<0, 1>(lim, tx, ty, nt, staging);
 }
 }  // namespace claw

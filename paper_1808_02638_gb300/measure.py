@@ -65,7 +65,8 @@ def tune_all(H, pull=False):
     out = {str(L): list(tune.tune_level(H, L, use_cache=False, pull=pull)[0]) for L in range(H.nlev)}
     if not pull:
         for L in range(H.nlev):
-            out[str(L)].append("pull" if tune.choose_pull(H, L)[0] else "fill")
+            tune.choose_pull(H, L)
+            out[str(L)].append("pull+interp" if H.fuse_interp[L] else "pull" if H.pull_levels[L] else "fill")
     return out
 
 

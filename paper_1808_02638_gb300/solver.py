@@ -148,6 +148,9 @@ class Hierarchy:
         self.fused = False       # one-level hierarchies: one launch per step (pulled ghosts, Eq. cfl on the device)
         self.pull = True         # coarse steps pull same-level / boundary ghosts (fill only interpolated ones)
         self.pull_levels = [True] * self.nlev   # per level (the autotuner may prefer the copy launch)
+        # per pulling level: the step evaluates the interpolated ghosts too (one launch) instead of
+        # the interpolation launch filling them first (the autotuner decides)
+        self.fuse_interp = [False] * self.nlev
         # a list while sections of eager coarse steps are timed: (name, start event, end event)
         self.sections = None
 
@@ -278,7 +281,15 @@ class Hierarchy:
 
     def advance(self, L, cold=None, cnew=None, tau=0.0, stream=None):
         q = self.q[L][self.cur[L]]
-        if self.pull and self.pull_levels[L] and not self.reflux and not self.patchwise:
+        if self.pull and self.pull_levels[L] and not self.reflux and not self.patchwise and self.fuse_interp[L]:
+            # one launch: the step pulls the same-level and boundary ghosts from their sources and
+            # evaluates the ones interpolated from the coarser level itself
+            e = self._section("advance", stream)
+            claw.claw_level_advance_interp(self.ctx, L, q, self.q[L][1 - self.cur[L]], self.aux[L], self.dt,
+                                           self.smax, claw.CLAW_ADVANCE_PULL_GHOSTS, cold, cnew, tau, stream)
+            if e is not None:
+                e.record()
+        elif self.pull and self.pull_levels[L] and not self.reflux and not self.patchwise:
             # only the interpolated ghosts are filled; the step pulls the others from their sources
             e = self._section("fill", stream)
             claw.claw_fill_ghost_interp(self.ctx, L, q, cold, cnew, tau, stream)

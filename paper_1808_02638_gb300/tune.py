@@ -108,16 +108,19 @@ def tune_level(H, L, use_cache=True, candidates=None, pull=False):
 
 
 def choose_pull(H, L, reps=5):
-    """whether level L of H should pull its copied ghosts inside the step (one launch) or fill
-    them with the copy launch first: times both sequences with the installed tiling and records
-    the faster in H.pull_levels[L].  Small boxes put many ghosts in every tile's frame, where
-    the separate copy can win."""
+    """how level L of H gets its ghosts, timed with the installed tiling, the fastest recorded in
+    H.pull_levels[L] and H.fuse_interp[L]: every ghost filled by the copy and interpolation
+    launches before the step ("fill"), the interpolated ghosts filled and the others pulled by the
+    step ("pull"), or one launch that pulls the copied ghosts and evaluates the interpolated ones
+    ("pull+interp").  Small boxes put many ghosts in every tile's frame, where the separate
+    launches can win."""
     src = H.q[L][H.cur[L]]
     dst = torch.empty_like(src)
     smax = torch.zeros_like(H.smax)
     qc = H.q[L - 1][H.cur[L - 1]] if L else None
     if float(H.dt.max()) <= 0.0:
         H.init_dt()
+    flags = claw.CLAW_ADVANCE_PULL_GHOSTS
 
     def fill_step():
         claw.claw_fill_ghost(H.ctx, L, src, qc, qc, 0.0)
@@ -125,10 +128,14 @@ def choose_pull(H, L, reps=5):
 
     def pull_step():
         claw.claw_fill_ghost_interp(H.ctx, L, src, qc, qc, 0.0)
-        claw.claw_level_advance(H.ctx, L, src, dst, H.aux[L], H.dt, smax, claw.CLAW_ADVANCE_PULL_GHOSTS)
+        claw.claw_level_advance(H.ctx, L, src, dst, H.aux[L], H.dt, smax, flags)
 
+    def fused_step():
+        claw.claw_level_advance_interp(H.ctx, L, src, dst, H.aux[L], H.dt, smax, flags, qc, qc, 0.0)
+
+    options = (("fill", fill_step), ("pull", pull_step)) + ((("pull+interp", fused_step),) if L else ())
     times = {}
-    for name, fn in (("fill", fill_step), ("pull", pull_step)):
+    for name, fn in options:
         fn()
         fn()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -138,7 +145,9 @@ def choose_pull(H, L, reps=5):
         e1.record()
         torch.cuda.synchronize()
         times[name] = e0.elapsed_time(e1) / reps
-    H.pull_levels[L] = times["pull"] <= times["fill"]
+    best = min(times, key=times.get)
+    H.pull_levels[L] = best != "fill"
+    H.fuse_interp[L] = best == "pull+interp"
     H.drop_graphs()
     return H.pull_levels[L], times
 

@@ -32,14 +32,18 @@ def _compare_all_levels(H, O, run_index, tol):
     return worst
 
 
-def test_three_level_hierarchy_one_and_twenty_coarse_steps():
+@pytest.mark.parametrize("ghosts", ["pull", "pull+interp", "fill"])
+def test_three_level_hierarchy_one_and_twenty_coarse_steps(ghosts):
     # 64^2 base, ratio 4 twice, seeded patches of 8..64 cells on the annuli (the uneven AMR
-    # workload); uniform medium rho = 1, K = 4
+    # workload); uniform medium rho = 1, K = 4; each way the fine levels can get their ghosts
+    # (interpolated ones filled first, evaluated inside the one-launch step, or all filled)
     from oracle.amr import OracleHierarchy
     from paper_1808_02638_gb300.solver import Hierarchy
     run = inputs.config2()
     q0 = [inputs.init_q(run, lev) for lev in run.levels]
     H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    H.fuse_interp = [ghosts == "pull+interp"] * H.nlev
+    H.pull_levels = [ghosts != "fill"] * H.nlev
     O = OracleHierarchy(run, q0, [inputs.const_pool(l, 1.0) for l in run.levels],
                         [inputs.const_pool(l, 4.0) for l in run.levels])
     H.init_dt()
@@ -77,6 +81,39 @@ def test_fine_level_ghosts_match_oracle_fill():
     bx = lambda lev: [(int(b[0]), int(b[1]), int(b[2]), int(b[3]), int(o)) for b, o in zip(lev.boxes, lev.qoff)]
     oracle.level_fill_ghost(bx(L2), want, 3, L2.NX, L2.NY, run.bc, bx(L1), cold, cnew, 0.25, 4)
     assert rel_err(got, want) <= 1e-14
+
+
+@pytest.mark.parametrize("tiling", [(32, 32, 1, 256), (32, 16, 2, 256), (16, 16, 1, 128)])
+def test_step_evaluating_interpolated_ghosts_equals_fill_then_step(tiling):
+    # claw_level_advance_interp (one launch: same-level and boundary ghosts pulled, coarse-fine
+    # ghosts interpolated in space and time inside the step) against claw_fill_ghost_interp +
+    # claw_level_advance with pulled ghosts: the same arithmetic, bit for bit, on both fine
+    # levels of the 3-level hierarchy at a time fraction between two distinct coarse states
+    import torch
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, tiling=tiling)
+    H.init_dt()
+    H.coarse_step()   # two different coarse states on every level
+    flags = claw.CLAW_ADVANCE_PULL_GHOSTS
+    for L in (1, 2):
+        cold, cnew = H.q[L - 1][1 - H.cur[L - 1]], H.q[L - 1][H.cur[L - 1]]
+        q = H.q[L][H.cur[L]].clone()
+        a, b = torch.full_like(q, float("nan")), torch.full_like(q, float("nan"))
+        claw.claw_level_advance_interp(H.ctx, L, q, a, None, H.dt, H.smax, flags, cold, cnew, 0.25)
+        qf = q.clone()
+        claw.claw_fill_ghost_interp(H.ctx, L, qf, cold, cnew, 0.25)
+        claw.claw_level_advance(H.ctx, L, qf, b, None, H.dt, H.smax, flags)
+        torch.cuda.synchronize()
+        lev = run.levels[L]
+        for n in range(len(lev.boxes)):
+            assert np.array_equal(H.interior(0, L, n, pool=a), H.interior(0, L, n, pool=b)), (L, n)
+        assert torch.equal(q, H.q[L][H.cur[L]])   # q_old's ghost cells are neither needed nor written
+    with pytest.raises(claw.ClawError):   # coarse states are required where interpolated ghosts exist
+        claw.claw_level_advance_interp(H.ctx, 1, q, a, None, H.dt, H.smax, flags, None, None, 0.25)
+    assert H.sync_status() == 0
 
 
 def test_batched_independent_runs_two_levels_cellwise():
