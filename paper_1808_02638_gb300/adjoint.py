@@ -92,8 +92,9 @@ class _Tape:
     "new" state of the space-time interpolation); dt[k] is the time step of coarse step k.
     With `record`, rec[L][i] receives the i-th step's intermediates (claw_level_advance_record),
     the reverse reads those instead of the states, and the finest level's states (which only
-    its own next step reads) live in two buffers.  A segment's recompute and its reverse only
-    ever touch these buffers (and the hierarchy's dt, smax, medium planes and the adjoint
+    its own next step reads) live in two buffers.  The recording steps use the tape's own dtw and
+    smaxw; the reverse sweep reads the tape and sets the hierarchy's dt.  A segment's recompute
+    and its reverse only ever touch these buffers (and the medium planes and the adjoint
     buffers), so one CUDA graph replays any segment."""
 
     def __init__(self, H, ncoarse, record=False):
@@ -110,6 +111,10 @@ class _Tape:
         self.rec = [[torch.empty_like(H.aux[L]) for _ in range(counts[L])] if record else []
                     for L in range(H.nlev)]
         self.dt = torch.zeros((ncoarse, H.nruns), dtype=torch.float64, device=H.dev)
+        # the recording steps' own time step and speed maximum, so that a recompute can run
+        # beside a reverse sweep (which sets the hierarchy's dt) on another stream
+        self.dtw = torch.zeros(H.nruns, dtype=torch.float64, device=H.dev)
+        self.smaxw = torch.zeros(H.nruns, dtype=torch.float64, device=H.dev)
 
     def state(self, L, i):
         return self.states[L][i % len(self.states[L])]
@@ -118,26 +123,28 @@ class _Tape:
 def _record(H, T, L, i, cold=None, cnew=None, tau=0.0):
     """the i-th step of level L of the tape (and its finer substeps), with the launches of
     Hierarchy.advance: the interpolated ghosts filled, the others pulled by the step (or, on a
-    level the autotuner keeps on the copy launch, all filled)"""
+    level the autotuner keeps on the copy launch, all filled); time step T.dtw, speeds into
+    T.smaxw"""
     q = T.state(L, i)
+    dt, smax = T.dtw, T.smaxw
     fine = L + 1 < H.nlev
     dst = T.pre[L][i] if fine else T.state(L, i + 1)
     if T.record:   # the level's own ghost launch choice, as in the forward
         if H.pull_levels[L]:
             if L:
                 claw.claw_fill_ghost_interp(H.ctx, L, q, cold, cnew, tau)
-            claw.claw_level_advance_record(H.ctx, L, q, dst, H.aux[L], H.dt, H.smax, claw.CLAW_ADVANCE_PULL_GHOSTS,
+            claw.claw_level_advance_record(H.ctx, L, q, dst, H.aux[L], dt, smax, claw.CLAW_ADVANCE_PULL_GHOSTS,
                                            T.rec[L][i])
         else:
             claw.claw_fill_ghost(H.ctx, L, q, cold, cnew, tau)
-            claw.claw_level_advance_record(H.ctx, L, q, dst, H.aux[L], H.dt, H.smax, 0, T.rec[L][i])
+            claw.claw_level_advance_record(H.ctx, L, q, dst, H.aux[L], dt, smax, 0, T.rec[L][i])
     elif H.pull_levels[L]:
         if L:
             claw.claw_fill_ghost_interp(H.ctx, L, q, cold, cnew, tau)
-        claw.claw_level_advance(H.ctx, L, q, dst, H.aux[L], H.dt, H.smax, claw.CLAW_ADVANCE_PULL_GHOSTS)
+        claw.claw_level_advance(H.ctx, L, q, dst, H.aux[L], dt, smax, claw.CLAW_ADVANCE_PULL_GHOSTS)
     else:
         claw.claw_fill_ghost(H.ctx, L, q, cold, cnew, tau)
-        claw.claw_level_step(H.ctx, L, q, dst, H.aux[L], H.dt, H.smax)
+        claw.claw_level_step(H.ctx, L, q, dst, H.aux[L], dt, smax)
     if fine:
         r = H.ratio(L + 1)
         for k in range(r):
@@ -148,12 +155,12 @@ def _record(H, T, L, i, cold=None, cnew=None, tau=0.0):
 
 
 def _record_coarse(H, T, k, frozen):
-    T.dt[k].copy_(H.dt)
+    T.dt[k].copy_(T.dtw)
     _record(H, T, 0, k)
     if frozen:
-        H.smax.zero_()
+        T.smaxw.zero_()
     else:
-        claw.claw_dt_update(H.ctx, 0, H.smax, H.dt)
+        claw.claw_dt_update(H.ctx, 0, T.smaxw, T.dtw)
 
 
 def _reverse_tape(H, T, L, i, lam, lbuf, g_aux, lam_cold=None, lam_cnew=None, tau=0.0, cold=None, cnew=None):
@@ -278,10 +285,14 @@ class _Rollout(torch.autograd.Function):
                 tape = _Tape(H, ncoarse)
                 for L in range(nlev):
                     tape.state(L, 0).copy_(H.q[L][H.cur[L]])
+                tape.dtw.copy_(H.dt)
+                tape.smaxw.copy_(H.smax)
                 for k in range(ncoarse):
                     _record_coarse(H, tape, k, frozen)
                 for L in range(nlev):
                     H.q[L][H.cur[L]].copy_(tape.state(L, tape.counts[L]))
+                H.dt.copy_(tape.dtw)
+                H.smax.copy_(tape.smaxw)
             else:
                 for s0 in range(0, ncoarse, every):
                     checkpoints.append(([H.q[L][H.cur[L]].clone() for L in range(nlev)], H.dt.clone()))
@@ -346,46 +357,88 @@ class _Rollout(torch.autograd.Function):
         return tuple(grads_out)
 
 
+def _run(H, key, body, graphs, undo_first):
+    """body() as a cached CUDA graph (or eagerly): on first use it runs eagerly once and is
+    captured, and undo_first() then puts back the inputs that eager run changed"""
+    if not graphs:
+        body()
+        return
+    if key not in H.__dict__.get("_graphs", {}):
+        undo = undo_first()
+        _replayable(H, key, body)
+        undo()
+    H._graphs[key].replay()
+
+
 def _backward_segments(ctx, H, lbuf, g_aux):
-    """reverse sweep over the checkpoint segments, last first: each segment is recomputed from
-    its checkpoint into the tape buffers and reversed, as one CUDA graph per segment length
-    (replayed for every segment of that length) when ctx.graphs"""
+    """reverse sweep over the checkpoint segments, last first.  Segment s is reversed from its
+    tape while segment s-1 is recomputed from its checkpoint into the other tape on a second
+    stream (the two touch disjoint buffers: the recompute has its own dt and speed maximum), so
+    the recompute of all but the last segment overlaps with the reverse sweep.  With ctx.graphs
+    each such pair is one cached CUDA graph per (segment lengths, tape slot)."""
     nlev, every, ncoarse = ctx.nlev, ctx.every, ctx.ncoarse
-    for s in reversed(range(len(ctx.checkpoints))):
+    rec = ctx.records and _records_ok(H)
+    nseg = len(ctx.checkpoints)
+    lens = [min(every, ncoarse - s * every) for s in range(nseg)]
+    side = _buffers(H, "side_stream", lambda: torch.cuda.Stream(device=H.dev))
+
+    def tape(s):
+        return _buffers(H, ("tape", lens[s], rec, s % 2), lambda: _Tape(H, lens[s], record=rec))
+
+    def load(s):   # eager: checkpoint s into its tape's first states and recording time step
         states, dt0 = ctx.checkpoints[s]
-        n = min(every, ncoarse - s * every)
-        rec = ctx.records and _records_ok(H)
-        T = _buffers(H, ("tape", n, rec), lambda: _Tape(H, n, record=rec))
+        T = tape(s)
         for L in range(nlev):
             T.state(L, 0).copy_(states[L])
-        H.dt.copy_(dt0)
+        T.dtw.copy_(dt0)
+        T.smaxw.zero_()
 
-        def body():
-            lam = [lbuf[L][0] for L in range(nlev)]
-            for k in range(n):
-                _record_coarse(H, T, k, ctx.frozen)
-            for k in reversed(range(n)):
-                _reverse_coarse(H, T, k, lam, lbuf, g_aux)
-            for L in range(nlev):   # the adjoint leaves in the buffer it came in
-                if lam[L] is not lbuf[L][0]:
-                    lbuf[L][0].copy_(lam[L])
+    def recompute(s):
+        T = tape(s)
+        for k in range(lens[s]):
+            _record_coarse(H, T, k, ctx.frozen)
 
-        if not ctx.graphs:
-            body()
-            continue
-        key = ("bwd", n, ctx.frozen, rec)
-        if key not in H.__dict__.get("_graphs", {}):
-            # the first run of the body (before the capture) must not count: save what it changes
+    def reverse(s):
+        T = tape(s)
+        lam = [lbuf[L][0] for L in range(nlev)]
+        for k in reversed(range(lens[s])):
+            _reverse_coarse(H, T, k, lam, lbuf, g_aux)
+        for L in range(nlev):   # the adjoint leaves in the buffer it came in
+            if lam[L] is not lbuf[L][0]:
+                lbuf[L][0].copy_(lam[L])
+
+    last = nseg - 1
+    load(last)
+    _run(H, ("bwd-first", lens[last], ctx.frozen, rec, last % 2), lambda: recompute(last), ctx.graphs,
+         lambda: (lambda: load(last)))
+    for s in reversed(range(nseg)):
+        if s:
+            load(s - 1)
+
+        def body(s=s):
+            main = torch.cuda.current_stream(H.dev)
+            if s:
+                side.wait_stream(main)
+                with torch.cuda.stream(side):
+                    recompute(s - 1)
+            reverse(s)
+            if s:
+                main.wait_stream(side)
+
+        def undo_first(s=s):
             saved = [l[0].clone() for l in lbuf], [g.clone() if g is not None else None for g in g_aux]
-            _replayable(H, key, body)
-            for L in range(nlev):
-                lbuf[L][0].copy_(saved[0][L])
-                if g_aux[L] is not None:
-                    g_aux[L].copy_(saved[1][L])
-            for L in range(nlev):
-                T.state(L, 0).copy_(states[L])
-            H.dt.copy_(dt0)
-        H._graphs[key].replay()
+
+            def undo():
+                for L in range(nlev):
+                    lbuf[L][0].copy_(saved[0][L])
+                    if g_aux[L] is not None:
+                        g_aux[L].copy_(saved[1][L])
+                if s:
+                    load(s - 1)
+            return undo
+
+        key = ("bwd", lens[s], lens[s - 1] if s else 0, ctx.frozen, rec, s % 2)
+        _run(H, key, body, ctx.graphs, undo_first)
     return [lbuf[L][0] for L in range(nlev)]
 
 

@@ -228,6 +228,7 @@ def config3(nsteps=400, every=20):
     ms = time_stepper(H, 40)
     H.init_dt()
     fwd, bwd, ok = time_adjoint(H, [[q]], [[rho]], [[K]], nsteps, every)
+    H.drop_graphs(buffers=True)   # the segment tapes, before the whole-rollout tape
     tf, tb, tok = time_adjoint(H, [[q]], [[rho]], [[K]], nsteps, None)
     return _report("256x256 heterogeneous medium, 400 steps, checkpoints every 20, J = sum p^2 over the "
                    "16x16 receiver", H, ms, None, FP64_INSTR_CELLWISE, BYTES_CELLWISE,
@@ -253,6 +254,7 @@ def config4(nruns=64, ncoarse=100, every=20, plain=True):
     plain = time_plain(H, 2) if plain else None
     H.init_dt()
     fwd, bwd, ok = time_adjoint(H, qs, rhos, Ks, ncoarse, every)
+    H.drop_graphs(buffers=True)   # the segment tapes, before the whole-rollout tape
     H.init_dt()
     tf, tb, tok = time_adjoint(H, qs, rhos, Ks, ncoarse, None)
     nbox = [sum(len(r.levels[L].boxes) for r, _, _ in runs) for L in range(2)]
