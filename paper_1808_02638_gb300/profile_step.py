@@ -2,6 +2,12 @@
 32 x 32, for a profiler to capture single kernel launches.
 
   python -m paper_1808_02638_gb300.profile_step [uniform|cellwise|swe] [nsteps] [fused|split] [tx,ty,staging,threads] [limiter]
+  python -m paper_1808_02638_gb300.profile_step adjoint [nruns] [ncoarse] [every]
+
+adjoint: the first `nruns` runs of the batched two-level workload (cell-wise media), autotuned,
+a checkpointed rollout of `ncoarse` coarse steps and its reverse sweep, twice; the second
+reverse sweep (recording steps and tape adjoint kernels, CUDA-graph replays) runs between
+cudaProfilerStart and cudaProfilerStop, for `ncu --profile-from-start off`.
 
 uniform: radial pulse, rho = 1, K = 4; cellwise: the same tiling over the smoothed random
 medium of the heterogeneous workload; swe: shallow water (g = 1) with the ring pulse as depth.
@@ -17,8 +23,42 @@ from . import inputs
 from .solver import Hierarchy
 
 
+def adjoint(nruns, ncoarse, every):
+    import time
+    from . import measure
+    from .adjoint import rollout
+    runs = inputs.config4_runs(nruns)
+    qs = [[inputs.init_q(r, lev) for lev in r.levels] for r, _, _ in runs]
+    rhos = [[inputs.coef_pool(lev, r2, 4 ** L) for L, lev in enumerate(r.levels)] for r, r2, _ in runs]
+    Ks = [[inputs.coef_pool(lev, k2, 4 ** L) for L, lev in enumerate(r.levels)] for r, _, k2 in runs]
+    H = Hierarchy([r for r, _, _ in runs], qs, rhos, Ks)
+    H.init_dt()
+    tiling = measure.tune_all(H)
+    H.init_dt()
+    for p in range(2):
+        tq, tr, tk = measure._tensors(H, qs, "q"), measure._tensors(H, rhos, "c"), measure._tensors(H, Ks, "c")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs = rollout(H, tq, tr, tk, ncoarse=ncoarse, every=every)
+        J = measure._receiver_energy(H, outs)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if p:
+            torch.cuda.profiler.start()
+        J.backward()
+        torch.cuda.synchronize()
+        if p:
+            torch.cuda.profiler.stop()
+        t2 = time.perf_counter()
+    print("tiling", tiling, "forward ms", 1e3 * (t1 - t0), "backward ms", 1e3 * (t2 - t1), "status", H.sync_status())
+
+
 def main():
     medium = sys.argv[1] if len(sys.argv) > 1 else "uniform"
+    if medium == "adjoint":
+        args = [int(v) for v in sys.argv[2:5]]
+        adjoint(*(args + [8, 4, 2][len(args):]))
+        return
     nsteps = int(sys.argv[2]) if len(sys.argv) > 2 else 3
     fused = (sys.argv[3] if len(sys.argv) > 3 else "fused") == "fused"
     tiling = tuple(int(v) for v in sys.argv[4].split(",")) if len(sys.argv) > 4 else None
