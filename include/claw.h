@@ -269,8 +269,8 @@ int claw_level_step_patchwise(claw_ctx* ctx, int32_t level, const double* q_old,
                               const double* aux, const double* dt, double* smax, void* stream);
 
 /* The fused level-step of one box that allocates nothing: for callers that cannot allocate
- * device memory where they step (inside a CUDA-graph capture, under a host application's own
- * device-memory pool, in a loop that cannot take cudaMalloc's implicit synchronisation).
+ * device memory where they step (under a host application's own device-memory pool, in a loop
+ * that cannot take cudaMalloc's implicit synchronisation).
  * The paper has no counterpart; it exists for those callers.
  * q_old / q_new hold one box (p, u, v planes of (nx+4) x (ny+4) doubles at offset 0; the
  * ghosts of q_old are filled by the caller); aux (cell-wise medium, CLAW_NAUX planes at
@@ -279,8 +279,10 @@ int claw_level_step_patchwise(claw_ctx* ctx, int32_t level, const double* q_old,
  * staging.  The scratch (box descriptor, tile table, error word) is a fixed 256 KiB device
  * array that every device loading the library keeps until exit, so at most 16367 tiles of
  * 32 x 32 cells fit (e.g. 4064 x 4096 cells, not 4096 x 4096): larger boxes, and nx or ny
- * above 4096, return CLAW_EINVAL before any launch.  The first call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.  Every call
+ * above 4096, return CLAW_EINVAL before any launch.  The first call on a device looks up the
+ * array's device address synchronously (once per device, with that device current) and keeps
+ * it for the life of the process: after a cudaDeviceReset of that device the kept address is
+ * stale, so the entry point must not be called again on it.  Every call
  * rewrites the whole scratch it uses (device errors of this path are not reported), and all
  * calls share the one array: calls whose kernels overlap on the GPU (other streams, other
  * threads) race.  Errors: CLAW_EINVAL, CLAW_ECUDA. */
