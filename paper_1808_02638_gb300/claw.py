@@ -53,6 +53,7 @@ _SIGNATURES = {
     "claw_destroy": ([VP], None),
     "claw_set_level": ([VP, I32, ctypes.POINTER(claw_box), I32], ctypes.c_int),
     "claw_set_tiling": ([VP, I32, I32, I32, I32, I32], ctypes.c_int),
+    "claw_set_tile_walk": ([VP, I32, I32], ctypes.c_int),
     "claw_set_wait_limit": ([VP, ctypes.c_uint32], ctypes.c_int),
     "claw_medium_aux": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_medium_aux_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
@@ -159,6 +160,10 @@ def claw_set_level(ctx, level: int, boxes):
 
 def claw_set_tiling(ctx, level: int, tx: int, ty: int, staging: int, threads: int = 0):
     _check("claw_set_tiling", load().claw_set_tiling(ctx, level, tx, ty, staging, threads))
+
+
+def claw_set_tile_walk(ctx, level: int, walk: int):
+    _check("claw_set_tile_walk", load().claw_set_tile_walk(ctx, level, int(walk)))
 
 
 def claw_set_wait_limit(ctx, polls: int):

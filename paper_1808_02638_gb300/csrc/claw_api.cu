@@ -17,6 +17,7 @@ StepArgs make_args(claw_ctx* ctx, int L, const double* q_old, double* q_new, con
     a.tiles = d.tiles;
     a.tmaps = nullptr;
     a.ntiles = d.ntiles;
+    a.tcum = ctx->kind() == KIND_SWE ? nullptr : d.tcum;   // the shallow-water step strides
     a.qold = q_old;
     a.qnew = q_new;
     a.aux = aux;
@@ -209,6 +210,7 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     d.tx = ctx->kind() == KIND_SWE ? 16 : 32;
     d.ty = ctx->kind() == KIND_SWE ? 16 : 32;
     d.staging = even ? 1 : 0;
+    d.walk = ctx->kind() == KIND_SWE ? 0 : 1;
     GhostTables gt;
     std::vector<AvgRect> avg;
     int rc = build_ghost_tables(ctx, L, gt, true);
@@ -312,6 +314,16 @@ int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t st
     if (d.tx == tx && d.ty == ty) return CLAW_OK;
     d.tx = tx;
     d.ty = ty;
+    return build_tiles(ctx, L);
+}
+
+int claw_set_tile_walk(claw_ctx* ctx, int32_t L, int32_t walk)
+{
+    if (!valid_level(ctx, L) || walk < 0 || walk > 1 || (walk && ctx->kind() == KIND_SWE)) return CLAW_EINVAL;
+    DevGuard g(ctx->device);
+    LevelDev& d = ctx->lev[L];
+    if (d.walk == walk) return CLAW_OK;
+    d.walk = walk;
     return build_tiles(ctx, L);
 }
 
@@ -565,6 +577,7 @@ int claw_level_advance_boxes(claw_ctx* ctx, int32_t L, int32_t box_begin, int32_
     StepArgs a = make_args(ctx, L, q_old, q_new, aux, dt, smax);
     a.tiles = ctx->ptiles[L] + st[box_begin];
     a.ntiles = st[box_end] - st[box_begin];
+    a.tcum = nullptr;
     if (flags & CLAW_ADVANCE_PULL_GHOSTS) a.ring = d.ring;
     int staging = d.staging;
     if (staging >= 1) {
@@ -620,6 +633,7 @@ int claw_level_step_patchwise(claw_ctx* ctx, int32_t L, const double* q_old, dou
     for (int n = 0; n < d.nboxes; ++n) {
         a.tiles = ctx->ptiles[L] + st[n];
         a.ntiles = st[n + 1] - st[n];
+        a.tcum = nullptr;
         ctx->launches += 1;
         cudaError_t e = launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, 0, a.ntiles, s);
         if (e != cudaSuccess) return CLAW_ECUDA;
@@ -663,6 +677,7 @@ int claw_level_advance_adjoint(claw_ctx* ctx, int32_t L, const double* q_old, co
     StepArgs a = make_args(ctx, L, q_old, nullptr, aux, dt, nullptr);
     a.tiles = ctx->atiles[L];
     a.ntiles = ctx->natiles[L];
+    a.tcum = nullptr;
     if (flags & CLAW_ADVANCE_PULL_GHOSTS) a.ring = d.ring;
     ctx->launches += 1;
     return cuda_rc(launch_step_adjoint(a, lam_new, lam_old, g_aux, ctx->medium, ctx->limiter, ctx->nsm,
@@ -721,6 +736,7 @@ int claw_level_advance_adjoint_tape(claw_ctx* ctx, int32_t L, const double* tape
     StepArgs a = make_args(ctx, L, nullptr, nullptr, aux, dt, nullptr);
     a.tiles = ctx->atiles[L];
     a.ntiles = ctx->natiles[L];
+    a.tcum = nullptr;
     a.tape = const_cast<double*>(tape);
     if (flags & CLAW_ADVANCE_PULL_GHOSTS) a.ring = d.ring;
     ctx->launches += 1;

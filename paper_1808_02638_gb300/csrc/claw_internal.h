@@ -65,10 +65,14 @@ struct PatchDev {
 };
 
 // One tile of the fused step: interior cells [x0, x0+tx) x [y0, y0+ty) of box `patch`.
+// TILE_CARRY (column-walk tile lists only): the previous tile of the list is the tile directly
+// below this one, with the same columns: in the same box, or (uniform medium) in the same-level
+// box whose top side this box's bottom side covers exactly.
+enum : int { TILE_CARRY = 1 };
 struct TileDev {
     int patch;
     short x0, y0, tx, ty;
-    int pad;
+    int flags;
 };
 
 // Rectangle of ghost cells copied from interior cells of the same level (same-level copy and
@@ -144,8 +148,10 @@ struct LevelDev {
     int navg = 0;          // averaging rects into the coarser level
     int ratio = 1;
     int tx = 32, ty = 32, staging = 1, nt = 0;   // tile, staging, threads per CTA (0: default)
+    int walk = 0;          // 1: the step's tiles are column walks (tiles ordered up each column, tcum)
     PatchDev* patches = nullptr;
     TileDev* tiles = nullptr;
+    long long* tcum = nullptr;     // column walk: cumulative tile costs [ntiles + 1] (null otherwise)
     CopyRect* copies = nullptr;
     CopyRect* ccopies = nullptr;   // the same copies for one-plane coefficient pools (coff offsets)
     int nccopy = 0;
@@ -174,6 +180,7 @@ struct LevelDev {
     std::vector<claw_box> boxes;
     std::vector<PatchDev> hpatches;
     std::vector<TileDev> htiles;
+    std::vector<long long> htcum;
 };
 
 // Ghost ring of a box: its (nx+4)(ny+4) - nx ny ghost cells in row order of the padded box.
@@ -201,6 +208,9 @@ struct StepArgs {
     const TileDev* tiles = nullptr;
     const void* tmaps = nullptr;
     int ntiles = 0;
+    // column walk: cumulative tile costs [ntiles + 1]; CTA b of the grid takes the tiles whose
+    // costs start in [b, b + 1) / grid of the total.  Null: CTAs stride over the tiles by the grid.
+    const long long* tcum = nullptr;
     const double* qold = nullptr;
     double* qnew = nullptr;
     const double* aux = nullptr;

@@ -77,7 +77,7 @@ __global__ void noalloc_setup_kernel(unsigned char* s, int nx, int ny, double dx
         T->y0 = (short)(by * kTile);
         T->tx = (short)min(kTile, nx - bx * kTile);
         T->ty = (short)min(kTile, ny - by * kTile);
-        T->pad = 0;
+        T->flags = 0;
     }
 }
 

@@ -165,10 +165,29 @@ template <int TX, int TY> struct Geo {
     static constexpr int QBYTES = 3 * QPL * 8;
     // shared-memory carve (in doubles), q buffers first (128-byte aligned)
     static constexpr int QSTRIDE = (3 * QPL + 15) / 16 * 16;
+    // rows a tile hands to the tile above it in a column walk (top rows of each array):
+    // x-edge strengths 2 rows, y-edge strengths 3, limited x-edges 2, limited y-edges 1, D 1
+    static constexpr int C_A = 0, C_B = 4 * XEW, C_S = C_B + 6 * YEW, C_SY = C_S + 4 * XLW,
+                         C_D = C_SY + 2 * YLW, NCARRY = C_D + DW;
     static constexpr int NWORK = 2 * XEW * XEH + 2 * YEW * YEH + 2 * XLW * XLH + 2 * YLW * YLH +
-                                 DW * DH + EW * EH;
+                                 DW * DH + EW * EH + NCARRY;
     static size_t smem_bytes(int nbuf) { return (size_t)(nbuf * QSTRIDE + NWORK) * 8 + 64; }
 };
+
+// The tiles [*begin, *end) of CTA b of `grid` in a column walk: the contiguous range whose
+// cumulative cost (cum[i] = cost of tiles [0, i), cum[n] the total) starts at or after b / grid
+// of the total.  The ranges of all CTAs partition [0, n).
+__device__ __forceinline__ int walk_start(const long long* cum, int n, int b, int grid)
+{
+    const long long target = (long long)b * __ldg(cum + n) / grid;   // b < 2^20, cum[n] < 2^40
+    int lo = 0, hi = n;   // first i in [0, n] with cum[i] >= target
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(cum + mid) < target) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
 
 // ------------------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ unsigned smem_u32(const void* p)
@@ -339,23 +358,47 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
     double* Py = Sy + G::YLW * G::YLH;
     double* Dx = Py + G::YLW * G::YLH;              // x-fluctuation pressure into each cell
     double* Ey = Dx + G::DW * G::DH;                // y-fluctuation pressure into each cell
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ey + G::EW * G::EH);
+    double* Cy = Ey + G::EW * G::EH;                // rows carried to the next tile of a column walk
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(Cy + G::NCARRY);
     __shared__ unsigned long long s_tmax[2];   // per-tile speed max, double-buffered by tile parity
     __shared__ int s_flag;
+    __shared__ int s_range[2];                 // this CTA's tiles in a column walk
     __shared__ double s_k[16];                 // per-tile constants, written by thread 0
-
+    __shared__ double s_med[3];                // uniform medium Z0, c0, 1 / Z0, written by thread 0
 
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_tmax[0] = s_tmax[1] = 0ull;
         s_flag = 0;
+        if (MED == 0) {   // square roots and a division: thread 0 alone (all threads cost ~0.9 FP64 per cell)
+            s_med[0] = sqrt(A.K0 * A.rho0);
+            s_med[1] = sqrt(A.K0 / A.rho0);
+            s_med[2] = 1.0 / s_med[0];
+        }
         if (STAGE) {
             mbar_init(&bar[0], 1);
             mbar_init(&bar[1], 1);
             fence_barrier_init();
         }
+        if (A.tcum) {
+            s_range[0] = walk_start(A.tcum, A.ntiles, blockIdx.x, gridDim.x);
+            s_range[1] = walk_start(A.tcum, A.ntiles, blockIdx.x + 1, gridDim.x);
+        } else {
+            s_range[0] = blockIdx.x;
+            s_range[1] = A.ntiles;
+        }
     }
     __syncthreads();
+    // Column walk (A.tcum set): the CTA takes a contiguous range of tiles, and a tile flagged
+    // TILE_CARRY that follows its lower neighbour in the same range takes the rows the two share
+    // (edges of the rows between them) from that neighbour instead of recomputing them: the
+    // neighbour is the tile directly below in the same box or (uniform medium) in the same-level
+    // box below, whose shared rows hold the same values.  Otherwise the CTA strides over all
+    // tiles by the grid.
+    // The recording step keeps every tile whole (each writes the tape of the rows it owns).
+    const int t_begin = s_range[0], t_end = s_range[1];
+    const int t_step = A.tcum ? 1 : (int)gridDim.x;
+    const bool walk = !REC && A.tcum != nullptr;
 
     const CUtensorMap* tmaps = reinterpret_cast<const CUtensorMap*>(A.tmaps);
     int my_flag = 0;
@@ -370,9 +413,9 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
     // uniform medium constants (once per CTA)
     double Z0 = 0, c0 = 0, iZ = 0;
     if (MED == 0) {
-        Z0 = sqrt(A.K0 * A.rho0);
-        c0 = sqrt(A.K0 / A.rho0);
-        iZ = 1.0 / Z0;
+        Z0 = s_med[0];
+        c0 = s_med[1];
+        iZ = s_med[2];
     }
 
     auto issue = [&](int t, int b) {
@@ -380,12 +423,16 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         mbar_expect_tx(&bar[b], (unsigned)G::QBYTES);
         tma_load_3d(qbuf + b * G::QSTRIDE, &tmaps[T.patch], T.x0, T.y0, 0, &bar[b]);
     };
-    if (STAGE && tid == 0 && blockIdx.x < A.ntiles) issue(blockIdx.x, 0);
+    if (STAGE && tid == 0 && t_begin < t_end) issue(t_begin, 0);
 
     int it = 0;
-    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++it) {
+    for (int t = t_begin; t < t_end; t += t_step, ++it) {
         const int b = STAGE == 1 ? (it & 1) : 0;
         const TileDev T = A.tiles[t];
+        // carry: this tile's lowest rows come from the previous tile; hand: the next one takes
+        // this tile's top rows
+        const bool carry = walk && t > t_begin && (T.flags & TILE_CARRY);
+        const bool hand = walk && t + 1 < t_end && (A.tiles[t + 1].flags & TILE_CARRY);
         const PatchDev P = A.patches[T.patch];
         const int tx = T.tx, ty = T.ty, x0 = T.x0, y0 = T.y0;
         const int W = P.nx + 4;
@@ -396,8 +443,8 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         double* sv = sq + 2 * G::QPL;
 
         if (STAGE) {
-            const int tn = t + gridDim.x;
-            if (STAGE == 1 && tid == 0 && tn < A.ntiles) issue(tn, b ^ 1);
+            const int tn = t + t_step;
+            if (STAGE == 1 && tid == 0 && tn < t_end) issue(tn, b ^ 1);
             // each buffer's barrier completes once per use: every other tile with two buffers,
             // every tile with one
             const unsigned par = STAGE == 1 ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1);
@@ -408,7 +455,7 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                     // no copy may land in this CTA's shared memory after it exits: wait, with the
                     // full bound, for this tile's own copy and for the prefetch of the next one
                     mbar_wait_bounded(&bar[b], par);
-                    if (STAGE == 1 && tn < A.ntiles)
+                    if (STAGE == 1 && tn < t_end)
                         mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
                     finish_cta(A);   // keeps the completion count consistent
                 }
@@ -479,11 +526,28 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         };
 
         // ---------------------------------------------------------------- phase A: normal Riemann
+        // carried rows land in the lowest rows of the arrays, which this phase does not write
+        // (the previous tile's last reads of them were behind its end-of-tile barrier)
+        if (carry) {
+            for (int k = tid; k < G::NCARRY; k += NT) {
+                double* dst;
+                if (k < G::C_B) dst = k < 2 * G::XEW ? A1x + k : A2x + (k - 2 * G::XEW);
+                else if (k < G::C_S) dst = k < G::C_B + 3 * G::YEW ? B1y + (k - G::C_B) : B2y + (k - G::C_B - 3 * G::YEW);
+                else if (k < G::C_SY) dst = k < G::C_S + 2 * G::XLW ? Sx + (k - G::C_S) : Px + (k - G::C_S - 2 * G::XLW);
+                else if (k < G::C_D) dst = k < G::C_SY + G::YLW ? Sy + (k - G::C_SY) : Py + (k - G::C_SY - G::YLW);
+                else dst = Dx + (k - G::C_D);
+                *dst = Cy[k];
+            }
+        }
+        // first rows computed here: with a carry, the rows below come from the previous tile
+        const int rx0 = carry ? 1 : -1;   // x-edges and limited x-edges: rows [rx0, ty]
+        const int by0 = carry ? 2 : -1;   // y-edges: b in [by0, ty + 1]
+        const int ly0 = carry ? 1 : 0;    // limited y-edges: b in [ly0, ty]
         // x-edge a (between cells a-1 and a) on rows r in [-1, ty]
         {
-            const int w = tx + 3, n = (ty + 2) * w;
+            const int w = tx + 3, n = (ty + 1 - rx0) * w;
             for (int k = tid; k < n; k += NT) {
-                const int r = k / w - 1, a = k - (r + 1) * w - 1;
+                const int r = k / w + rx0, a = k - (r - rx0) * w - 1;
                 const int iR = (a + 2) + (r + 2) * G::SW;
                 const double dp = sp[iR] - sp[iR - 1];
                 const double du = su[iR] - su[iR - 1];
@@ -504,9 +568,9 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         }
         // y-edge b (between rows b-1 and b) on columns c in [-1, tx]
         {
-            const int w = tx + 2, n = (ty + 3) * w;
+            const int w = tx + 2, n = (ty + 2 - by0) * w;
             for (int k = tid; k < n; k += NT) {
-                const int bb = k / w - 1, c = k - (bb + 1) * w - 1;
+                const int bb = k / w + by0, c = k - (bb - by0) * w - 1;
                 const int iR = (c + 2) + (bb + 2) * G::SW;
                 const double dp = sp[iR] - sp[iR - G::SW];
                 const double dv = sv[iR] - sv[iR - G::SW];
@@ -546,9 +610,9 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         const double lx = s_k[12], ly = s_k[13];
         if (second) {
             {
-                const int w = tx + 1, n = (ty + 2) * w;
+                const int w = tx + 1, n = (ty + 1 - rx0) * w;
                 for (int k = tid; k < n; k += NT) {
-                    const int r = k / w - 1, a = k - (r + 1) * w;
+                    const int r = k / w + rx0, a = k - (r - rx0) * w;
                     const int e = (r + 1) * G::XEW + (a + 1);
                     const double a1 = A1x[e], a2 = A2x[e];
                     double m1, m2;
@@ -577,9 +641,9 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                 }
             }
             {
-                const int w = tx + 2, n = (ty + 1) * w;
+                const int w = tx + 2, n = (ty + 1 - ly0) * w;
                 for (int k = tid; k < n; k += NT) {
-                    const int bb = k / w, c = k - bb * w - 1;
+                    const int bb = k / w + ly0, c = k - (bb - ly0) * w - 1;
                     const int e = (bb + 1) * G::YEW + (c + 1);
                     const double b1 = B1y[e], b2 = B2y[e];
                     double m1, m2;
@@ -678,7 +742,7 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         // D on the ghost rows -1, ty and E on the ghost columns -1, tx (transverse only)
         if (trans) {
             const int n = 2 * (tx + ty);
-            for (int k = tid; k < n; k += NT) {
+            for (int k = tid + (carry ? tx : 0); k < n; k += NT) {   // row -1 is carried
                 if (k < 2 * tx) {
                     const int c = k % tx, r = (k < tx) ? -1 : ty;
                     const int ex = (r + 1) * G::XEW + (c + 1);
@@ -707,6 +771,22 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                     }
                     Ey[r * G::EW + c + 1] = e;
                 }
+            }
+        }
+        // hand the top rows of the edge arrays to the next tile (none of them is written from
+        // here to the end of the tile, but phase C2 reuses the strength arrays)
+        if (hand) {
+            for (int k = tid; k < G::C_D; k += NT) {
+                const double* src;
+                if (k < G::C_B) src = k < 2 * G::XEW ? A1x + ty * G::XEW + k : A2x + ty * G::XEW + (k - 2 * G::XEW);
+                else if (k < G::C_S)
+                    src = k < G::C_B + 3 * G::YEW ? B1y + ty * G::YEW + (k - G::C_B)
+                                                  : B2y + ty * G::YEW + (k - G::C_B - 3 * G::YEW);
+                else if (k < G::C_SY)
+                    src = k < G::C_S + 2 * G::XLW ? Sx + ty * G::XLW + (k - G::C_S)
+                                                  : Px + ty * G::XLW + (k - G::C_S - 2 * G::XLW);
+                else src = k < G::C_SY + G::YLW ? Sy + ty * G::YLW + (k - G::C_SY) : Py + ty * G::YLW + (k - G::C_SY - G::YLW);
+                Cy[k] = *src;
             }
         }
         __syncthreads();
@@ -749,12 +829,15 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
         // ---------------------------------------------------------------- phase D: update, store
         // one staging buffer: the tile's state was last read in phase C (behind the barrier
         // above), so the next tile's copy can land while this one finishes
-        if (STAGE == 2 && tid == 0 && t + (int)gridDim.x < A.ntiles) issue(t + gridDim.x, 0);
+        if (STAGE == 2 && tid == 0 && t + t_step < t_end) issue(t + t_step, 0);
         double kT = 0, kU = 0;
         if (MED == 0 && trans) {
             kT = s_k[10];
             kU = s_k[11];
         }
+        // D of row ty - 1 becomes the next tile's row -1 (final since the barrier ending phase C)
+        if (hand)
+            for (int k = tid; k < G::DW; k += NT) Cy[G::C_D + k] = Dx[ty * G::DW + k];
         double* dst = A.qnew + P.qoff;
 #pragma unroll
         for (int n = 0; n < NPER; ++n) {

@@ -5,6 +5,8 @@
 // tiles.
 #include "claw_host.h"
 
+#include <array>
+
 namespace claw_host {
 
 void free_arena(DevArena& a)
@@ -48,11 +50,65 @@ void free_level(claw_ctx* ctx, int L)
     d.boxes.clear();
     d.hpatches.clear();
     d.htiles.clear();
+    d.htcum.clear();
+    d.tcum = nullptr;
     ctx->set[L] = false;
 }
 
-// tiles of a level for its tiling: sorted by area (largest first) for the persistent walk,
-// and grouped by box for the per-box launches
+// The step's tiles as column walks: every column of tiles of a box bottom to top, continued
+// (cross) into the column of the same-level box directly above when that box has the same run,
+// ilo and nx (the columns then coincide); every tile but the first of such a chain is flagged
+// TILE_CARRY.  Crossing needs the shared rows to be the same in both boxes: the ghost states are
+// (they come from the box below, or from the same boundary image or coarse interpolation), but
+// a cell-wise medium's ghost coefficients are the caller's, so only the uniform medium crosses.
+// cum[i] is the cost of tiles [0, i): the cells of the tile and of the halo rows and columns it
+// computes edges on, plus a fixed per-tile share.
+static void column_walks(const LevelDev& d, bool cross, std::vector<TileDev>& out, std::vector<long long>& cum)
+{
+    const int nb = d.nboxes;
+    std::map<std::array<int, 4>, int> by_base;   // (run, ilo, nx, jlo) -> box
+    for (int n = 0; n < nb; ++n) {
+        const claw_box& b = d.boxes[n];
+        by_base[{b.run, b.ilo, b.nx, b.jlo}] = n;
+    }
+    std::vector<int> above(nb, -1), has_below(nb, 0);
+    for (int n = 0; n < nb; ++n) {
+        const claw_box& b = d.boxes[n];
+        auto it = by_base.find({b.run, b.ilo, b.nx, b.jlo + b.ny});
+        if (cross && it != by_base.end()) {
+            above[n] = it->second;
+            has_below[it->second] = 1;
+        }
+    }
+    out.clear();
+    cum.assign(1, 0);
+    for (int n0 = 0; n0 < nb; ++n0) {
+        if (has_below[n0]) continue;   // chains start at boxes with nothing aligned below
+        const claw_box& b0 = d.boxes[n0];
+        for (int x = 0; x < b0.nx; x += d.tx) {
+            bool first = true;
+            for (int n = n0; n >= 0; n = above[n]) {
+                const claw_box& b = d.boxes[n];
+                for (int y = 0; y < b.ny; y += d.ty) {
+                    TileDev T;
+                    T.patch = n;
+                    T.x0 = (short)x;
+                    T.y0 = (short)y;
+                    T.tx = (short)std::min(d.tx, b.nx - x);
+                    T.ty = (short)std::min(d.ty, b.ny - y);
+                    T.flags = first ? 0 : TILE_CARRY;
+                    first = false;
+                    out.push_back(T);
+                    const long long c = (long long)(T.tx + 3) * (T.ty + (T.flags ? 0 : 3)) + 64;
+                    cum.push_back(cum.back() + c);
+                }
+            }
+        }
+    }
+}
+
+// tiles of a level for its tiling: sorted by area (largest first) for the persistent walk, or
+// as column walks (d.walk), and grouped by box for the per-box launches
 int build_tiles(claw_ctx* ctx, int L)
 {
     LevelDev& d = ctx->lev[L];
@@ -69,7 +125,7 @@ int build_tiles(claw_ctx* ctx, int L)
                 T.y0 = (short)y;
                 T.tx = (short)std::min(d.tx, b.nx - x);
                 T.ty = (short)std::min(d.ty, b.ny - y);
-                T.pad = 0;
+                T.flags = 0;
                 t.push_back(T);
             }
     }
@@ -78,14 +134,21 @@ int build_tiles(claw_ctx* ctx, int L)
     ArenaPack pack;
     pack.add(&ctx->ptiles[L], t);
     ctx->ptile_start[L] = start;
-    d.htiles = t;
-    std::stable_sort(d.htiles.begin(), d.htiles.end(), [](const TileDev& a, const TileDev& b) {
-        return (int)a.tx * a.ty > (int)b.tx * b.ty;
-    });
+    d.htcum.clear();
+    if (d.walk) {
+        column_walks(d, ctx->kind() == KIND_UNIFORM, d.htiles, d.htcum);
+    } else {
+        d.htiles = t;
+        std::stable_sort(d.htiles.begin(), d.htiles.end(), [](const TileDev& a, const TileDev& b) {
+            return (int)a.tx * a.ty > (int)b.tx * b.ty;
+        });
+    }
     d.ntiles = (int)d.htiles.size();
     for (auto& tm : ctx->tmaps[L]) cudaFree(tm.dev);
     ctx->tmaps[L].clear();
     pack.add(&d.tiles, d.htiles);
+    d.tcum = nullptr;
+    if (d.walk) pack.add(&d.tcum, d.htcum);
     // adjoint tiles
     std::vector<TileDev> at;
     const int e = adjoint_tile();
@@ -99,7 +162,7 @@ int build_tiles(claw_ctx* ctx, int L)
                 T.y0 = (short)y;
                 T.tx = (short)std::min(e, b.nx - x);
                 T.ty = (short)std::min(e, b.ny - y);
-                T.pad = 0;
+                T.flags = 0;
                 at.push_back(T);
             }
     }

@@ -68,7 +68,7 @@ class Hierarchy:
     of the shallow water equations with gravity `grav` instead (no medium)."""
 
     def __init__(self, runs, q0, rho=None, K=None, rho0=1.0, K0=4.0, device=0, tiling=None, reflux=False,
-                 system="acoustics", grav=1.0):
+                 system="acoustics", grav=1.0, walk=None):
         self.runs = runs
         self.nruns = len(runs)
         self.nlev = max(len(r.levels) for r in runs)
@@ -103,13 +103,15 @@ class Hierarchy:
         self.boxes = []    # per level list of claw_box
         self.layout = []   # per level list of (run, qbase, cbase)
         self.tiling = tiling
+        # how the level-step's CTAs share the tiles (claw_set_tile_walk): None keeps the
+        # library's default, 0 strides, 1 column walks
+        self.walk = walk
         for L in range(self.nlev):
             boxes, lay, qb, cb = self._layout(L)
             self.boxes.append(boxes)
             self.layout.append(lay)
             claw.claw_set_level(self.ctx, L, boxes)
-            if self.level_tiling(L) is not None:
-                claw.claw_set_tiling(self.ctx, L, *self.level_tiling(L))
+            self._install_tiling(L)
             qh = np.zeros(max(qb, inputs.ALIGN))
             for (ri, qbase, _) in lay:
                 a = np.asarray(q0[ri][L], dtype=np.float64)
@@ -153,6 +155,12 @@ class Hierarchy:
         self.fuse_interp = [False] * self.nlev
         # a list while sections of eager coarse steps are timed: (name, start event, end event)
         self.sections = None
+
+    def _install_tiling(self, L):
+        if self.level_tiling(L) is not None:
+            claw.claw_set_tiling(self.ctx, L, *self.level_tiling(L))
+        if self.walk is not None:
+            claw.claw_set_tile_walk(self.ctx, L, self.walk)
 
     def level_tiling(self, L):
         """(tx, ty, staging, threads) installed on level L: `tiling` is one such tuple for every
@@ -223,8 +231,7 @@ class Hierarchy:
             old_boxes, old_pool = self.boxes[Lf], self.q[Lf][self.cur[Lf]]
             boxes, lay, qb, _ = self._layout(Lf)
             claw.claw_set_level(self.ctx, Lf, boxes)   # also clears the finer levels' tables
-            if self.level_tiling(Lf) is not None:
-                claw.claw_set_tiling(self.ctx, Lf, *self.level_tiling(Lf))
+            self._install_tiling(Lf)
             new = torch.zeros(max(qb, inputs.ALIGN), dtype=torch.float64, device=self.dev)
             claw.claw_regrid_transfer(self.ctx, Lf, old_boxes, old_pool, new, qc)
             self.boxes[Lf], self.layout[Lf] = boxes, lay

@@ -1,0 +1,170 @@
+"""Column-walk tile lists of the fused level-step (claw_set_tile_walk): CTAs that take contiguous
+stretches of tile columns and hand the edge values of shared rows from each tile to the one above
+give the same new states, dt and speed maxima, bit for bit, as CTAs striding over the tiles, on
+every tiling, with filled, pulled and step-interpolated ghosts, wall and periodic boundaries,
+uniform and cell-wise media, ragged tiles, box stacks that do and do not line up, and runs batched
+into one launch whose boxes sit at the same indices."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1808_02638_gb300 import inputs
+
+from gpu_helpers import lib_ready, single_grid
+
+pytestmark = pytest.mark.gpu
+
+TILINGS = [(32, 32, 1, 256), (32, 32, 0, 512), (32, 16, 2, 256), (32, 16, 1, 256), (16, 16, 1, 128),
+           (16, 16, 0, 128)]
+
+# 128 x 128 in boxes whose columns line up in some stacks and not in others; heights of 40 and
+# 48 give ragged tiles (8 rows) in the middle of a walk
+MIXED_BOXES = [(0, 0, 64, 40), (0, 40, 32, 40), (32, 40, 32, 40), (0, 80, 32, 48), (32, 80, 32, 48),
+               (64, 0, 32, 128), (96, 0, 32, 40), (96, 40, 32, 40), (96, 80, 32, 48)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib_ready()
+
+
+def _same(A, B, levels=None):
+    torch.cuda.synchronize()
+    for L in range(A.nlev) if levels is None else levels:
+        for ri, run in enumerate(A.runs):
+            if L >= len(run.levels):
+                continue
+            for n in range(len(run.levels[L].boxes)):
+                assert np.array_equal(A.interior(ri, L, n), B.interior(ri, L, n)), (ri, L, n)
+    assert torch.equal(A.dt, B.dt)
+    assert A.sync_status() == 0 and B.sync_status() == 0
+
+
+def _random_velocity(run, q, seed):
+    lev = run.levels[0]
+    for k, b in enumerate(lev.boxes):
+        v = inputs.box_view(q, lev.qoff[k], int(b[2]), int(b[3]), 3)
+        v[...] = inputs.uniform(seed + k, v.size).reshape(v.shape) - 0.5
+
+
+@pytest.mark.parametrize("tiling", TILINGS)
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 2, 2), (2, 0, 1, 1)])
+def test_single_level_walk_equals_stride_uniform_medium(tiling, bc):
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, q = single_grid(128, pulse=False, seed=300, bc=bc, boxes=MIXED_BOXES)
+    _random_velocity(run, q, 300)
+    A = Hierarchy([run], [[q]], rho0=1.0, K0=4.0, tiling=tiling, walk=1)
+    B = Hierarchy([run], [[q]], rho0=1.0, K0=4.0, tiling=tiling, walk=0)
+    for h in (A, B):
+        h.init_dt()
+        for _ in range(3):
+            h.coarse_step()
+        h.fused = True   # the one-launch step: pulled ghosts and Eq. cfl on the device
+        for _ in range(3):
+            h.coarse_step()
+    _same(A, B)
+
+
+@pytest.mark.parametrize("tiling", [(32, 32, 1, 256), (32, 16, 2, 256), (16, 16, 1, 128)])
+def test_single_level_walk_equals_stride_cellwise_medium(tiling):
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, q = single_grid(128, pulse=False, seed=310, bc=(2, 2, 1, 1), boxes=MIXED_BOXES)
+    _random_velocity(run, q, 310)
+    lev = run.levels[0]
+    rho = np.zeros(lev.csize)
+    K = np.zeros(lev.csize)
+    for k, b in enumerate(lev.boxes):
+        n = (int(b[2]) + 4) * (int(b[3]) + 4)
+        rho[lev.coff[k]:lev.coff[k] + n] = 0.5 + inputs.uniform(320 + k, n)
+        K[lev.coff[k]:lev.coff[k] + n] = 1.0 + 3.0 * inputs.uniform(340 + k, n)
+    A = Hierarchy([run], [[q]], [[rho]], [[K]], tiling=tiling, walk=1)
+    B = Hierarchy([run], [[q]], [[rho]], [[K]], tiling=tiling, walk=0)
+    for h in (A, B):
+        h.init_dt()
+        for _ in range(3):
+            h.coarse_step()
+        h.fused = True
+        for _ in range(2):
+            h.coarse_step()
+    _same(A, B)
+
+
+@pytest.mark.parametrize("ghosts", ["pull", "pull+interp", "fill"])
+def test_three_level_hierarchy_walk_equals_stride(ghosts):
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    hs = []
+    for walk in (1, 0):
+        H = Hierarchy([run], [q0], rho0=1.0, K0=4.0, tiling=(16, 16, 1, 128), walk=walk)
+        H.fuse_interp = [ghosts == "pull+interp"] * H.nlev
+        H.pull_levels = [ghosts != "fill"] * H.nlev
+        H.init_dt()
+        for _ in range(3):
+            H.coarse_step()
+        hs.append(H)
+    _same(*hs)
+
+
+def test_batched_runs_with_the_same_box_indices_walk_equals_stride():
+    # two runs with the same boxes in their own index spaces and different data: no walk may
+    # continue from one run's box into the other's
+    from paper_1808_02638_gb300.solver import Hierarchy
+    runs, qs = [], []
+    for seed in (400, 500):
+        run, q = single_grid(128, pulse=False, seed=seed, boxes=MIXED_BOXES)
+        _random_velocity(run, q, seed)
+        runs.append(run)
+        qs.append([q])
+    A = Hierarchy(runs, qs, rho0=1.0, K0=4.0, tiling=(32, 16, 2, 256), walk=1)
+    B = Hierarchy(runs, qs, rho0=1.0, K0=4.0, tiling=(32, 16, 2, 256), walk=0)
+    for h in (A, B):
+        h.init_dt()
+        for _ in range(4):
+            h.coarse_step()
+    _same(A, B)
+
+
+def test_recording_step_tape_is_the_same_under_both_tile_orders():
+    # the recording step keeps whole tiles under a column walk: the tape and the new state equal
+    # those of the striding CTAs
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, q = single_grid(128, pulse=False, seed=360, bc=(0, 0, 0, 0), boxes=MIXED_BOXES)
+    lev = run.levels[0]
+    rho = np.zeros(lev.csize)
+    K = np.zeros(lev.csize)
+    for k, b in enumerate(lev.boxes):
+        n = (int(b[2]) + 4) * (int(b[3]) + 4)
+        rho[lev.coff[k]:lev.coff[k] + n] = 0.5 + inputs.uniform(370 + k, n)
+        K[lev.coff[k]:lev.coff[k] + n] = 1.0 + 3.0 * inputs.uniform(380 + k, n)
+    out = []
+    for walk in (1, 0):
+        H = Hierarchy([run], [[q]], [[rho]], [[K]], tiling=(32, 16, 1, 256), walk=walk)
+        H.init_dt()
+        src = H.q[0][H.cur[0]]
+        dst = torch.full_like(src, float("nan"))
+        tape = torch.zeros_like(H.aux[0])   # the tape has the aux layout
+        claw.claw_level_advance_record(H.ctx, 0, src, dst, H.aux[0], H.dt, H.smax,
+                                       claw.CLAW_ADVANCE_PULL_GHOSTS, tape)
+        torch.cuda.synchronize()
+        assert H.sync_status() == 0
+        out.append((dst.cpu(), tape.cpu(), H.smax.cpu()))
+    (d1, t1, s1), (d0, t0, s0) = out
+    inner = ~torch.isnan(d0)
+    assert torch.equal(inner, ~torch.isnan(d1))
+    assert torch.equal(d1[inner], d0[inner])
+    assert torch.equal(t1, t0)
+    assert torch.equal(s1, s0)
+
+
+def test_walk_switch_rejects_bad_values():
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, q = single_grid(64)
+    H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
+    for bad in (-1, 2):
+        with pytest.raises(claw.ClawError):
+            claw.claw_set_tile_walk(H.ctx, 0, bad)
+    with pytest.raises(claw.ClawError):
+        claw.claw_set_tile_walk(H.ctx, 1, 1)   # level not set
