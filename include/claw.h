@@ -158,6 +158,14 @@ int claw_set_tile_walk(claw_ctx* ctx, int32_t level, int32_t walk);
  * Errors: CLAW_EINVAL (ctx NULL).  Host only, no device work. */
 int claw_set_wait_limit(claw_ctx* ctx, uint32_t polls);
 
+/* The wave limiter of the level-step (Sec. 2.1: a wave's strength scaled by phi(theta), theta
+ * the ratio of the upwind edge's strength of the same family to its own), elementwise on the
+ * current CUDA device: out[i] = phi(b[i] / a[i]) a[i], computed exactly as the step computes it
+ * (0 where a[i] b[i] <= 0; minmod, superbee and MC on the integer pipe, MC's (|a| + |b|) / 2
+ * rounded like the IEEE sum; van Leer within a relative 4 * 2^-53 of 2ab / (a + b)).  a, b, out: n device
+ * doubles.  For tests of the step's limiters.  Errors: CLAW_EINVAL, CLAW_ECUDA. */
+int claw_limiter_eval(int32_t limiter, int64_t n, const double* a, const double* b, double* out, void* stream);
+
 /* Per-cell coefficient planes for medium = 1 from one-plane pools rho, K (ghosts included):
  * aux holds, for every cell, Z = sqrt(K rho), c = sqrt(K/rho), K, c^2, 1/(Z_W+Z) and the
  * two wave-limiter projection factors of the edge to the west, and the same three for the

@@ -54,6 +54,7 @@ _SIGNATURES = {
     "claw_set_level": ([VP, I32, ctypes.POINTER(claw_box), I32], ctypes.c_int),
     "claw_set_tiling": ([VP, I32, I32, I32, I32, I32], ctypes.c_int),
     "claw_set_tile_walk": ([VP, I32, I32], ctypes.c_int),
+    "claw_limiter_eval": ([I32, ctypes.c_int64, VP, VP, VP, VP], ctypes.c_int),
     "claw_set_wait_limit": ([VP, ctypes.c_uint32], ctypes.c_int),
     "claw_medium_aux": ([VP, I32, VP, VP, VP, VP], ctypes.c_int),
     "claw_medium_aux_adjoint": ([VP, I32, VP, VP, VP, VP, VP, VP], ctypes.c_int),
@@ -164,6 +165,13 @@ def claw_set_tiling(ctx, level: int, tx: int, ty: int, staging: int, threads: in
 
 def claw_set_tile_walk(ctx, level: int, walk: int):
     _check("claw_set_tile_walk", load().claw_set_tile_walk(ctx, level, int(walk)))
+
+
+def claw_limiter_eval(limiter: int, a, b, out, stream=None):
+    n = a.numel()
+    if b.numel() != n or out.numel() != n:
+        raise ValueError("a, b and out must have the same size")
+    _check("claw_limiter_eval", load().claw_limiter_eval(int(limiter), n, _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
 
 
 def claw_set_wait_limit(ctx, polls: int):

@@ -285,6 +285,13 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     return CLAW_OK;
 }
 
+int claw_limiter_eval(int32_t limiter, int64_t n, const double* a, const double* b, double* out, void* stream)
+{
+    if (limiter < CLAW_LIM_NONE || limiter > CLAW_LIM_MC || n < 0 || (n > 0 && (!a || !b || !out)))
+        return CLAW_EINVAL;
+    return cuda_rc(launch_limiter_eval(limiter, n, a, b, out, (cudaStream_t)stream));
+}
+
 int claw_set_wait_limit(claw_ctx* ctx, uint32_t polls)
 {
     if (!ctx) return CLAW_EINVAL;

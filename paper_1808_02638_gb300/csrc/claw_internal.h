@@ -262,6 +262,9 @@ int adjoint_tile();   // the adjoint kernel's square tile edge
 cudaError_t launch_step_adjoint_tape(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
                                      int limiter, int nsm, cudaStream_t s);
 int adjoint_tape_tile();
+// the step's wave limiter elementwise (claw_step.cu)
+cudaError_t launch_limiter_eval(int limiter, long long n, const double* a, const double* b, double* out,
+                                cudaStream_t s);
 
 // launchers (claw_ghost.cu)
 cudaError_t launch_fill_copy(const CopyRect* r, const int* start, int nblocks, double* q, cudaStream_t s,

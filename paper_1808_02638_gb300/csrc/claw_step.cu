@@ -1,5 +1,6 @@
 // Dispatch of the fused level-step kernels (instantiated in claw_step_uniform.cu,
 // claw_step_cellwise.cu and claw_step_swe.cu).
+#include <algorithm>
 #include <mutex>
 #include <set>
 
@@ -68,6 +69,29 @@ cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty
     cudaError_t e = prepare(k);
     if (e != cudaSuccess) return e;
     k.fn<<<grid, k.nt, k.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int L>
+__global__ void limiter_eval_kernel(long long n, const double* a, const double* b, double* out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = Lim<L>::f(__ldg(a + i), __ldg(b + i));
+}
+
+cudaError_t launch_limiter_eval(int limiter, long long n, const double* a, const double* b, double* out,
+                                cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 4096);
+    switch (limiter) {
+    case CLAW_LIM_NONE: limiter_eval_kernel<CLAW_LIM_NONE><<<grid, 256, 0, s>>>(n, a, b, out); break;
+    case CLAW_LIM_MINMOD: limiter_eval_kernel<CLAW_LIM_MINMOD><<<grid, 256, 0, s>>>(n, a, b, out); break;
+    case CLAW_LIM_SUPERBEE: limiter_eval_kernel<CLAW_LIM_SUPERBEE><<<grid, 256, 0, s>>>(n, a, b, out); break;
+    case CLAW_LIM_VANLEER: limiter_eval_kernel<CLAW_LIM_VANLEER><<<grid, 256, 0, s>>>(n, a, b, out); break;
+    case CLAW_LIM_MC: limiter_eval_kernel<CLAW_LIM_MC><<<grid, 256, 0, s>>>(n, a, b, out); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -37,11 +37,13 @@ namespace claw {
 // FP64 is 1/64 of the FP32 rate on this part, so minmod, superbee and MC run on the integer
 // pipe: for non-negative doubles the bit patterns order like the values, so min / max of
 // magnitudes are 64-bit integer min / max, and doubling or halving a magnitude adds or
-// subtracts 1 in the exponent field.  MC keeps one FP64 add (|a| + |b|), minmod and
-// superbee none.  The exponent shifts are exact for magnitudes >= 2^-1021; below that the
+// subtracts 1 in the exponent field.  MC's sum |a| + |b| is the IEEE-754 sum rounded to
+// nearest even, formed on the integer pipe as well (add_mag), so none of the three issues an
+// FP64 instruction.  The exponent shifts are exact for magnitudes >= 2^-1021; below that the
 // result (itself below 2^-1020 in magnitude) may differ from the IEEE evaluation of the same
 // formula by less than 2^-1020.  van Leer needs a quotient: one correctly rounded reciprocal
-// and two products instead of a division (within two ulps of 2ab / (a + b)).
+// and two products instead of a division (four roundings: within a relative 4 * 2^-53 of
+// 2ab / (a + b)).
 namespace lim_bits {
 constexpr long long MAG = 0x7fffffffffffffffLL;
 constexpr long long SIGN = (long long)0x8000000000000000ULL;
@@ -52,6 +54,36 @@ __device__ __forceinline__ double val(long long b) { return __longlong_as_double
 __device__ __forceinline__ bool same_sign_nonzero(long long ia, long long ib, long long ma, long long mb)
 {
     return ((ia ^ ib) >= 0) & (ma != 0) & (mb != 0);
+}
+// The bit pattern of x + y for non-negative doubles x, y given by their bit patterns: the
+// exact sum rounded to nearest, ties to even (IEEE 754, Sec. 4.3.1 and 6.3 of the 2008
+// standard), on the integer pipe.  The smaller significand is aligned to the larger with three
+// extra low bits (guard, round and a sticky OR of every bit shifted out), the significands are
+// added, a carry out renormalises by one place (its lost bit joins the sticky bit), and the
+// rounding increment may carry into the exponent field, which is how the significand overflow
+// and the step from subnormal to normal come out right.  Subnormals take exponent 1 without the
+// hidden bit.  Overflow gives +inf; an infinite or NaN operand gives +inf or that NaN (quieted).
+__device__ __forceinline__ long long add_mag(long long x, long long y)
+{
+    constexpr long long FRAC = (1LL << 52) - 1, HID = 1LL << 52, INF = 0x7ff0000000000000LL;
+    const long long hi = x > y ? x : y, lo = x > y ? y : x;
+    const int eh = (int)(hi >> 52), el = (int)(lo >> 52);
+    if (eh == 2047) return (hi & FRAC) ? (hi | (1LL << 51)) : hi;
+    const int Eh = eh ? eh : 1, El = el ? el : 1;
+    const int d = Eh - El < 57 ? Eh - El : 57;   // Fl < 2^56: a shift by 57 already leaves only the sticky bit
+    const long long Fh = ((hi & FRAC) | (eh ? HID : 0)) << 3;
+    const long long Fl = ((lo & FRAC) | (el ? HID : 0)) << 3;
+    const long long al = (Fl >> d) | (long long)((Fl & ((1LL << d) - 1)) != 0);
+    long long S = Fh + al;
+    int E = Eh;
+    if (S >> 56) {
+        S = (S >> 1) | (S & 1);
+        ++E;
+    }
+    const long long m = S >> 3;
+    const int r = (int)(S & 7);
+    const long long res = ((long long)(E - 1) << 52) + m + (long long)((r > 4) | ((r == 4) & (int)(m & 1)));
+    return res >= INF ? INF : res;
 }
 }  // namespace lim_bits
 
@@ -128,7 +160,7 @@ template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta)
         using namespace lim_bits;
         const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
         const long long t2 = (ma < mb ? ma : mb) + ONE_EXP;
-        long long sh = bits(val(ma) + val(mb)) - ONE_EXP;   // the one FP64 add
+        long long sh = add_mag(ma, mb) - ONE_EXP;
         sh = sh > 0 ? sh : 0;   // a subnormal sum would wrap below zero
         const long long m = sh < t2 ? sh : t2;
         return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
@@ -138,7 +170,7 @@ template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta)
         using namespace lim_bits;
         const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
         const long long t2 = (ma < mb ? ma : mb) + ONE_EXP;
-        long long sh = bits(val(ma) + val(mb)) - ONE_EXP;
+        long long sh = add_mag(ma, mb) - ONE_EXP;
         sh = sh > 0 ? sh : 0;
         const bool nz = same_sign_nonzero(ia, ib, ma, mb);
         code = !nz ? LIMC_ZERO : (sh < t2 ? LIMC_HALF : (ma < mb ? LIMC_2A : LIMC_2B));
