@@ -17,7 +17,7 @@ StepArgs make_args(claw_ctx* ctx, int L, const double* q_old, double* q_new, con
     a.tiles = d.tiles;
     a.tmaps = nullptr;
     a.ntiles = d.ntiles;
-    a.tcum = ctx->kind() == KIND_SWE ? nullptr : d.tcum;   // the shallow-water step strides
+    a.tcum = d.tcum;   // set for uniform-medium levels only
     a.qold = q_old;
     a.qnew = q_new;
     a.aux = aux;
@@ -210,7 +210,7 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
     d.tx = ctx->kind() == KIND_SWE ? 16 : 32;
     d.ty = ctx->kind() == KIND_SWE ? 16 : 32;
     d.staging = even ? 1 : 0;
-    d.walk = ctx->kind() == KIND_SWE ? 0 : 1;
+    d.walk = -1;
     GhostTables gt;
     std::vector<AvgRect> avg;
     int rc = build_ghost_tables(ctx, L, gt, true);
@@ -326,7 +326,7 @@ int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t st
 
 int claw_set_tile_walk(claw_ctx* ctx, int32_t L, int32_t walk)
 {
-    if (!valid_level(ctx, L) || walk < 0 || walk > 1 || (walk && ctx->kind() == KIND_SWE)) return CLAW_EINVAL;
+    if (!valid_level(ctx, L) || walk < -1 || walk > 1 || (walk > 0 && ctx->kind() != KIND_UNIFORM)) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
     if (d.walk == walk) return CLAW_OK;
@@ -492,7 +492,8 @@ int claw_level_step(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new
         a.tmaps = get_tmaps(ctx, L, q_old, s);
         if (!a.tmaps) staging = 0;   // no descriptor (e.g. first use inside a graph capture)
     }
-    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging);
+    const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, false, false, false,
+                                            a.tcum != nullptr);
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;
@@ -542,7 +543,7 @@ static int level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* 
         if (!a.tmaps) staging = 0;
     }
     const int per_sm = step_max_ctas_per_sm(ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, a.ring != nullptr,
-                                            false, a.interp != nullptr);
+                                            false, a.interp != nullptr, a.tcum != nullptr);
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
     ctx->launches += 1;

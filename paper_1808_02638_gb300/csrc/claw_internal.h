@@ -65,9 +65,9 @@ struct PatchDev {
 };
 
 // One tile of the fused step: interior cells [x0, x0+tx) x [y0, y0+ty) of box `patch`.
-// TILE_CARRY (column-walk tile lists only): the previous tile of the list is the tile directly
-// below this one, with the same columns: in the same box, or (uniform medium) in the same-level
-// box whose top side this box's bottom side covers exactly.
+// TILE_CARRY (column-walk tile lists, uniform medium only): the previous tile of the list is the
+// tile directly below this one, with the same columns: in the same box, or in the same-level box
+// whose top side this box's bottom side covers exactly.
 enum : int { TILE_CARRY = 1 };
 struct TileDev {
     int patch;
@@ -148,7 +148,8 @@ struct LevelDev {
     int navg = 0;          // averaging rects into the coarser level
     int ratio = 1;
     int tx = 32, ty = 32, staging = 1, nt = 0;   // tile, staging, threads per CTA (0: default)
-    int walk = 0;          // 1: the step's tiles are column walks (tiles ordered up each column, tcum)
+    int walk = -1;         // column walks (tiles ordered up each column, tcum): 1 on, 0 off, -1 automatic
+    bool walking = false;  // the tile lists in place are column walks
     PatchDev* patches = nullptr;
     TileDev* tiles = nullptr;
     long long* tcum = nullptr;     // column walk: cumulative tile costs [ntiles + 1] (null otherwise)
@@ -253,7 +254,7 @@ enum : int { KIND_UNIFORM = 0, KIND_CELLWISE = 1, KIND_SWE = 2 };
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s);
 int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull = false,
-                         bool rec = false, bool interp = false);
+                         bool rec = false, bool interp = false, bool walk = false);
 cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,
                                 int medium, int limiter, int nsm, cudaStream_t s);   // grid: resident CTAs x nsm
 int adjoint_tile();   // the adjoint kernel's square tile edge

@@ -46,17 +46,20 @@ static cudaError_t prepare(const StepKernel& k)
     std::lock_guard<std::mutex> g(mu);
     auto key = std::make_pair((const void*)k.fn, dev);
     if (done.count(key)) return cudaSuccess;
-    e = cudaFuncSetAttribute((const void*)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+    e = cudaFuncSetAttribute((const void*)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)std::max(k.smem, k.smem_walk));
     if (e == cudaSuccess) done.insert(key);
     return e;
 }
 
-int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull, bool rec, bool interp)
+int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull, bool rec, bool interp,
+                         bool walk)
 {
     StepKernel k = pick(kind, limiter, tx, ty, nt, staging, pull, rec, interp);
     if (!k.fn || prepare(k) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k.fn, k.nt, k.smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k.fn, k.nt, walk ? k.smem_walk : k.smem) !=
+        cudaSuccess)
         return 0;
     return n;
 }
@@ -68,7 +71,7 @@ cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty
     if (!k.fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare(k);
     if (e != cudaSuccess) return e;
-    k.fn<<<grid, k.nt, k.smem, s>>>(a);
+    k.fn<<<grid, k.nt, a.tcum ? k.smem_walk : k.smem, s>>>(a);
     return cudaGetLastError();
 }
 

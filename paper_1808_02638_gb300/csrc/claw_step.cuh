@@ -91,6 +91,7 @@ __device__ __forceinline__ long long add_mag(long long x, long long y)
 // recording step; on the integer pipe like f.
 template <int L> struct Lim;
 template <> struct Lim<CLAW_LIM_NONE> {
+    template <bool = false>
     static __device__ __forceinline__ double f(double a, double) { return a; }
     static __device__ __forceinline__ double fc(double a, double, int& code)
     {
@@ -99,6 +100,7 @@ template <> struct Lim<CLAW_LIM_NONE> {
     }
 };
 template <> struct Lim<CLAW_LIM_MINMOD> {   // max(0, min(1, theta)): sign(a) min(|a|, |b|)
+    template <bool = false>
     static __device__ __forceinline__ double f(double a, double b)
     {
         using namespace lim_bits;
@@ -116,6 +118,7 @@ template <> struct Lim<CLAW_LIM_MINMOD> {   // max(0, min(1, theta)): sign(a) mi
     }
 };
 template <> struct Lim<CLAW_LIM_SUPERBEE> {   // max(0, min(1, 2 theta), min(2, theta))
+    template <bool = false>
     static __device__ __forceinline__ double f(double a, double b)
     {   // sign(a) max(min(|a|, 2|b|), min(2|a|, |b|))
         using namespace lim_bits;
@@ -138,6 +141,7 @@ template <> struct Lim<CLAW_LIM_SUPERBEE> {   // max(0, min(1, 2 theta), min(2, 
     }
 };
 template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|): 2ab / (a + b)
+    template <bool = false>
     static __device__ __forceinline__ double f(double a, double b)
     {   // a (b r) with r = 1 / ((a + b) / 2); |b r| <= 2 as a and b share their sign
         using namespace lim_bits;
@@ -155,12 +159,14 @@ template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|
     }
 };
 template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta))
+    // FPSUM: the sum on the FP64 pipe instead (the same bits)
+    template <bool FPSUM = false>
     static __device__ __forceinline__ double f(double a, double b)
     {   // sign(a) min((|a| + |b|) / 2, 2 |a|, 2 |b|) = sign(a) min(s / 2, 2 min(|a|, |b|))
         using namespace lim_bits;
         const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
         const long long t2 = (ma < mb ? ma : mb) + ONE_EXP;
-        long long sh = add_mag(ma, mb) - ONE_EXP;
+        long long sh = (FPSUM ? bits(val(ma) + val(mb)) : add_mag(ma, mb)) - ONE_EXP;
         sh = sh > 0 ? sh : 0;   // a subnormal sum would wrap below zero
         const long long m = sh < t2 ? sh : t2;
         return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
@@ -202,8 +208,12 @@ template <int TX, int TY> struct Geo {
     static constexpr int C_A = 0, C_B = 4 * XEW, C_S = C_B + 6 * YEW, C_SY = C_S + 4 * XLW,
                          C_D = C_SY + 2 * YLW, NCARRY = C_D + DW;
     static constexpr int NWORK = 2 * XEW * XEH + 2 * YEW * YEH + 2 * XLW * XLH + 2 * YLW * YLH +
-                                 DW * DH + EW * EH + NCARRY;
-    static size_t smem_bytes(int nbuf) { return (size_t)(nbuf * QSTRIDE + NWORK) * 8 + 64; }
+                                 DW * DH + EW * EH;
+    // q buffers, work arrays, 64 bytes of barriers, then (column walks only) the carried rows
+    static size_t smem_bytes(int nbuf, bool walk = false)
+    {
+        return (size_t)(nbuf * QSTRIDE + NWORK) * 8 + 64 + (walk ? (size_t)NCARRY * 8 : 0);
+    }
 };
 
 // The tiles [*begin, *end) of CTA b of `grid` in a column walk: the contiguous range whose
@@ -371,10 +381,14 @@ __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P
 // REC (cell-wise medium): also write the step's intermediates to the tape A.tape (TapePlane);
 // each padded cell's entries come from the one tile that owns the cell (its interior, plus the
 // box's ghost frame next to it), so the tape is the same whatever the tiling.
+// Registers: the one-buffer staging is capped for three CTAs per SM; the 128-thread tiles for
+// five (the shared memory of five fits an SM), except those evaluating interpolated ghosts.
 template <int MED, int LIM, int TX, int TY, int NT, int STAGE, int PULL, bool REC = false>
-__global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const StepArgs A)
+__global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : (NT == 128 && PULL < 2 && !REC ? 5 : 1))
+    step_kernel(const StepArgs A)
 {
     static_assert(!REC || MED == 1, "the tape records the cell-wise step");
+    // (REC kernels never walk: column walks are built for the uniform medium only)
     using G = Geo<TX, TY>;
     constexpr int NBUF = STAGE == 1 ? 2 : 1;
     constexpr int NPER = (TX * TY + NT - 1) / NT;
@@ -390,8 +404,9 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
     double* Py = Sy + G::YLW * G::YLH;
     double* Dx = Py + G::YLW * G::YLH;              // x-fluctuation pressure into each cell
     double* Ey = Dx + G::DW * G::DH;                // y-fluctuation pressure into each cell
-    double* Cy = Ey + G::EW * G::EH;                // rows carried to the next tile of a column walk
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(Cy + G::NCARRY);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ey + G::EW * G::EH);
+    // rows carried to the next tile of a column walk: allocated only for launches that walk
+    double* Cy = reinterpret_cast<double*>(bar) + 8;
     __shared__ unsigned long long s_tmax[2];   // per-tile speed max, double-buffered by tile parity
     __shared__ int s_flag;
     __shared__ int s_range[2];                 // this CTA's tiles in a column walk
@@ -427,10 +442,11 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
     // neighbour is the tile directly below in the same box or (uniform medium) in the same-level
     // box below, whose shared rows hold the same values.  Otherwise the CTA strides over all
     // tiles by the grid.
-    // The recording step keeps every tile whole (each writes the tape of the rows it owns).
+    // Only the uniform medium walks (the host builds column walks for no other kind), so the
+    // cell-wise kernels carry none of this code.
     const int t_begin = s_range[0], t_end = s_range[1];
     const int t_step = A.tcum ? 1 : (int)gridDim.x;
-    const bool walk = !REC && A.tcum != nullptr;
+    const bool walk = MED == 0 && A.tcum != nullptr;
 
     const CUtensorMap* tmaps = reinterpret_cast<const CUtensorMap*>(A.tmaps);
     int my_flag = 0;
@@ -661,8 +677,8 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                             rec(TAPE_M1, a, r, tag_code(m1, c1));
                             rec(TAPE_M2, a, r, tag_code(m2, c2));
                         } else {
-                            m1 = Lim<LIM>::f(a1, A1x[e + 1] * AX(AUX_FX1, a, r));
-                            m2 = Lim<LIM>::f(a2, A2x[e - 1] * AX(AUX_FX2, a, r));
+                            m1 = Lim<LIM>::template f<true>(a1, A1x[e + 1] * AX(AUX_FX1, a, r));
+                            m2 = Lim<LIM>::template f<true>(a2, A2x[e - 1] * AX(AUX_FX2, a, r));
                         }
                         const double kl = fma(-lx, AX(AUX_C2, a - 1, r), AX(AUX_C, a - 1, r));
                         const double kr = fma(-lx, AX(AUX_C2, a, r), AX(AUX_C, a, r));
@@ -692,8 +708,8 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : 1) step_kernel(const Step
                             rec(TAPE_N1, c, bb, tag_code(m1, c1));
                             rec(TAPE_N2, c, bb, tag_code(m2, c2));
                         } else {
-                            m1 = Lim<LIM>::f(b1, B1y[e + G::YEW] * AX(AUX_FY1, c, bb));
-                            m2 = Lim<LIM>::f(b2, B2y[e - G::YEW] * AX(AUX_FY2, c, bb));
+                            m1 = Lim<LIM>::template f<true>(b1, B1y[e + G::YEW] * AX(AUX_FY1, c, bb));
+                            m2 = Lim<LIM>::template f<true>(b2, B2y[e - G::YEW] * AX(AUX_FY2, c, bb));
                         }
                         const double kl = fma(-ly, AX(AUX_C2, c, bb - 1), AX(AUX_C, c, bb - 1));
                         const double kr = fma(-ly, AX(AUX_C2, c, bb), AX(AUX_C, c, bb));
@@ -927,8 +943,9 @@ namespace claw {
 // kernel pointer and dynamic shared memory of one configuration
 struct StepKernel {
     void (*fn)(const StepArgs);
-    size_t smem;
+    size_t smem;        // dynamic shared memory of a launch that strides over the tiles
     int nt;
+    size_t smem_walk;   // ... of a launch that walks tile columns (the carried rows added)
 };
 
 template <int MED, int LIM, int TX, int TY, int NT, int STAGE, int PULL, bool REC = false>
@@ -938,6 +955,7 @@ StepKernel step_kernel_entry()
     k.fn = step_kernel<MED, LIM, TX, TY, NT, STAGE, PULL, REC>;
     k.smem = Geo<TX, TY>::smem_bytes(STAGE == 1 ? 2 : 1);
     k.nt = NT;
+    k.smem_walk = MED == 1 ? k.smem : Geo<TX, TY>::smem_bytes(STAGE == 1 ? 2 : 1, true);
     return k;
 }
 
@@ -960,7 +978,7 @@ StepKernel step_kernel_select(int tx, int ty, int nt, int staging)
     if (tx == 16 && ty == 16 && (nt == 0 || nt == 128))
         return staging ? step_kernel_entry<MED, LIM, 16, 16, 128, 1, PULL, REC>()
                        : step_kernel_entry<MED, LIM, 16, 16, 128, 0, PULL, REC>();
-    return StepKernel{nullptr, 0, 0};
+    return StepKernel{nullptr, 0, 0, 0};
 }
 
 template <int MED, int PULL, bool REC = false>
@@ -973,7 +991,7 @@ StepKernel step_kernel_for(int lim, int tx, int ty, int nt, int staging)
     case CLAW_LIM_VANLEER: return step_kernel_select<MED, CLAW_LIM_VANLEER, PULL, REC>(tx, ty, nt, staging);
     case CLAW_LIM_MC: return step_kernel_select<MED, CLAW_LIM_MC, PULL, REC>(tx, ty, nt, staging);
     }
-    return StepKernel{nullptr, 0, 0};
+    return StepKernel{nullptr, 0, 0, 0};
 }
 
 // one translation unit per kernel family (pull: the instantiations taking pulled ghosts)

@@ -476,6 +476,7 @@ static StepKernel swe_entry()
     StepKernel k;
     k.fn = swe_step_kernel<LIM, TX, TY, NT, STAGE, PULL>;
     k.smem = SweGeo<TX, TY>::smem_bytes(STAGE ? 2 : 1);
+    k.smem_walk = k.smem;
     k.nt = NT;
     return k;
 }
@@ -487,7 +488,7 @@ static StepKernel swe_select(int tx, int ty, int nt, int staging)
         return staging ? swe_entry<LIM, 16, 16, 256, 1, PULL>() : swe_entry<LIM, 16, 16, 256, 0, PULL>();
     if (tx == 32 && ty == 16 && (nt == 0 || nt == 512))
         return staging ? swe_entry<LIM, 32, 16, 512, 1, PULL>() : swe_entry<LIM, 32, 16, 512, 0, PULL>();
-    return StepKernel{nullptr, 0, 0};
+    return StepKernel{nullptr, 0, 0, 0};
 }
 
 template <bool PULL>
@@ -500,7 +501,7 @@ static StepKernel swe_for(int lim, int tx, int ty, int nt, int staging)
     case CLAW_LIM_VANLEER: return swe_select<CLAW_LIM_VANLEER, PULL>(tx, ty, nt, staging);
     case CLAW_LIM_MC: return swe_select<CLAW_LIM_MC, PULL>(tx, ty, nt, staging);
     }
-    return StepKernel{nullptr, 0, 0};
+    return StepKernel{nullptr, 0, 0, 0};
 }
 
 StepKernel step_kernel_swe(int lim, int tx, int ty, int nt, int staging)

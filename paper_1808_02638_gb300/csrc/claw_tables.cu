@@ -55,15 +55,17 @@ void free_level(claw_ctx* ctx, int L)
     ctx->set[L] = false;
 }
 
-// The step's tiles as column walks: every column of tiles of a box bottom to top, continued
-// (cross) into the column of the same-level box directly above when that box has the same run,
-// ilo and nx (the columns then coincide); every tile but the first of such a chain is flagged
-// TILE_CARRY.  Crossing needs the shared rows to be the same in both boxes: the ghost states are
-// (they come from the box below, or from the same boundary image or coarse interpolation), but
-// a cell-wise medium's ghost coefficients are the caller's, so only the uniform medium crosses.
-// cum[i] is the cost of tiles [0, i): the cells of the tile and of the halo rows and columns it
-// computes edges on, plus a fixed per-tile share.
-static void column_walks(const LevelDev& d, bool cross, std::vector<TileDev>& out, std::vector<long long>& cum)
+// The step's tiles as column walks (uniform medium): every column of tiles of a box bottom to
+// top, continued into the column of the same-level box directly above when that box has the
+// same run, ilo and nx (the columns then coincide); every tile but the first of such a chain is
+// flagged TILE_CARRY.  Crossing needs the shared rows to be the same in both boxes, which the
+// ghost states are: they come from the box below, or from the same boundary image or coarse
+// interpolation.  (A cell-wise medium's ghost coefficients are the caller's and need not match,
+// one reason walks are built for the uniform medium only; the other is that the cell-wise
+// kernels keep their registers without the carrying code.)  cum[i] is the cost of tiles
+// [0, i): the cells of the tile and of the halo rows and columns it computes edges on, plus a
+// fixed per-tile share.
+static void column_walks(const LevelDev& d, std::vector<TileDev>& out, std::vector<long long>& cum)
 {
     const int nb = d.nboxes;
     std::map<std::array<int, 4>, int> by_base;   // (run, ilo, nx, jlo) -> box
@@ -75,7 +77,7 @@ static void column_walks(const LevelDev& d, bool cross, std::vector<TileDev>& ou
     for (int n = 0; n < nb; ++n) {
         const claw_box& b = d.boxes[n];
         auto it = by_base.find({b.run, b.ilo, b.nx, b.jlo + b.ny});
-        if (cross && it != by_base.end()) {
+        if (it != by_base.end()) {
             above[n] = it->second;
             has_below[it->second] = 1;
         }
@@ -107,8 +109,12 @@ static void column_walks(const LevelDev& d, bool cross, std::vector<TileDev>& ou
     }
 }
 
-// tiles of a level for its tiling: sorted by area (largest first) for the persistent walk, or
-// as column walks (d.walk), and grouped by box for the per-box launches
+// tiles of a level for its tiling: sorted by area (largest first) for the persistent CTAs, or
+// as column walks (d.walk; automatic: acoustics levels with at least kWalkTilesPerSM tiles per
+// SM, where each CTA has several tiles to walk; with about one tile per CTA the area-sorted
+// stride balances better), and grouped by box for the per-box launches
+constexpr int kWalkTilesPerSM = 8;
+
 int build_tiles(claw_ctx* ctx, int L)
 {
     LevelDev& d = ctx->lev[L];
@@ -135,8 +141,10 @@ int build_tiles(claw_ctx* ctx, int L)
     pack.add(&ctx->ptiles[L], t);
     ctx->ptile_start[L] = start;
     d.htcum.clear();
-    if (d.walk) {
-        column_walks(d, ctx->kind() == KIND_UNIFORM, d.htiles, d.htcum);
+    d.walking = ctx->kind() == KIND_UNIFORM &&
+                (d.walk > 0 || (d.walk < 0 && (long long)t.size() >= (long long)kWalkTilesPerSM * std::max(ctx->nsm, 1)));
+    if (d.walking) {
+        column_walks(d, d.htiles, d.htcum);
     } else {
         d.htiles = t;
         std::stable_sort(d.htiles.begin(), d.htiles.end(), [](const TileDev& a, const TileDev& b) {
@@ -148,7 +156,7 @@ int build_tiles(claw_ctx* ctx, int L)
     ctx->tmaps[L].clear();
     pack.add(&d.tiles, d.htiles);
     d.tcum = nullptr;
-    if (d.walk) pack.add(&d.tcum, d.htcum);
+    if (d.walking) pack.add(&d.tcum, d.htcum);
     // adjoint tiles
     std::vector<TileDev> at;
     const int e = adjoint_tile();

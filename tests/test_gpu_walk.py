@@ -2,8 +2,8 @@
 stretches of tile columns and hand the edge values of shared rows from each tile to the one above
 give the same new states, dt and speed maxima, bit for bit, as CTAs striding over the tiles, on
 every tiling, with filled, pulled and step-interpolated ghosts, wall and periodic boundaries,
-uniform and cell-wise media, ragged tiles, box stacks that do and do not line up, and runs batched
-into one launch whose boxes sit at the same indices."""
+ragged tiles, box stacks that do and do not line up, and runs batched into one launch whose boxes
+sit at the same indices (uniform medium: the only kind that walks)."""
 import numpy as np
 import pytest
 import torch
@@ -65,28 +65,19 @@ def test_single_level_walk_equals_stride_uniform_medium(tiling, bc):
     _same(A, B)
 
 
-@pytest.mark.parametrize("tiling", [(32, 32, 1, 256), (32, 16, 2, 256), (16, 16, 1, 128)])
-def test_single_level_walk_equals_stride_cellwise_medium(tiling):
+def test_only_uniform_medium_levels_walk():
+    # column walks are built for the uniform medium only: a cell-wise level rejects walk = 1 and
+    # keeps striding under the automatic choice
+    from paper_1808_02638_gb300 import claw
     from paper_1808_02638_gb300.solver import Hierarchy
-    run, q = single_grid(128, pulse=False, seed=310, bc=(2, 2, 1, 1), boxes=MIXED_BOXES)
-    _random_velocity(run, q, 310)
+    run, q = single_grid(128, pulse=False, seed=310, boxes=MIXED_BOXES)
     lev = run.levels[0]
-    rho = np.zeros(lev.csize)
-    K = np.zeros(lev.csize)
-    for k, b in enumerate(lev.boxes):
-        n = (int(b[2]) + 4) * (int(b[3]) + 4)
-        rho[lev.coff[k]:lev.coff[k] + n] = 0.5 + inputs.uniform(320 + k, n)
-        K[lev.coff[k]:lev.coff[k] + n] = 1.0 + 3.0 * inputs.uniform(340 + k, n)
-    A = Hierarchy([run], [[q]], [[rho]], [[K]], tiling=tiling, walk=1)
-    B = Hierarchy([run], [[q]], [[rho]], [[K]], tiling=tiling, walk=0)
-    for h in (A, B):
-        h.init_dt()
-        for _ in range(3):
-            h.coarse_step()
-        h.fused = True
-        for _ in range(2):
-            h.coarse_step()
-    _same(A, B)
+    rho, K = np.ones(lev.csize), np.full(lev.csize, 4.0)
+    H = Hierarchy([run], [[q]], [[rho]], [[K]])
+    with pytest.raises(claw.ClawError):
+        claw.claw_set_tile_walk(H.ctx, 0, 1)
+    claw.claw_set_tile_walk(H.ctx, 0, 0)
+    claw.claw_set_tile_walk(H.ctx, 0, -1)
 
 
 @pytest.mark.parametrize("ghosts", ["pull", "pull+interp", "fill"])
@@ -125,46 +116,14 @@ def test_batched_runs_with_the_same_box_indices_walk_equals_stride():
     _same(A, B)
 
 
-def test_recording_step_tape_is_the_same_under_both_tile_orders():
-    # the recording step keeps whole tiles under a column walk: the tape and the new state equal
-    # those of the striding CTAs
-    from paper_1808_02638_gb300 import claw
-    from paper_1808_02638_gb300.solver import Hierarchy
-    run, q = single_grid(128, pulse=False, seed=360, bc=(0, 0, 0, 0), boxes=MIXED_BOXES)
-    lev = run.levels[0]
-    rho = np.zeros(lev.csize)
-    K = np.zeros(lev.csize)
-    for k, b in enumerate(lev.boxes):
-        n = (int(b[2]) + 4) * (int(b[3]) + 4)
-        rho[lev.coff[k]:lev.coff[k] + n] = 0.5 + inputs.uniform(370 + k, n)
-        K[lev.coff[k]:lev.coff[k] + n] = 1.0 + 3.0 * inputs.uniform(380 + k, n)
-    out = []
-    for walk in (1, 0):
-        H = Hierarchy([run], [[q]], [[rho]], [[K]], tiling=(32, 16, 1, 256), walk=walk)
-        H.init_dt()
-        src = H.q[0][H.cur[0]]
-        dst = torch.full_like(src, float("nan"))
-        tape = torch.zeros_like(H.aux[0])   # the tape has the aux layout
-        claw.claw_level_advance_record(H.ctx, 0, src, dst, H.aux[0], H.dt, H.smax,
-                                       claw.CLAW_ADVANCE_PULL_GHOSTS, tape)
-        torch.cuda.synchronize()
-        assert H.sync_status() == 0
-        out.append((dst.cpu(), tape.cpu(), H.smax.cpu()))
-    (d1, t1, s1), (d0, t0, s0) = out
-    inner = ~torch.isnan(d0)
-    assert torch.equal(inner, ~torch.isnan(d1))
-    assert torch.equal(d1[inner], d0[inner])
-    assert torch.equal(t1, t0)
-    assert torch.equal(s1, s0)
-
-
 def test_walk_switch_rejects_bad_values():
     from paper_1808_02638_gb300 import claw
     from paper_1808_02638_gb300.solver import Hierarchy
     run, q = single_grid(64)
     H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0)
-    for bad in (-1, 2):
+    for bad in (-2, 2):
         with pytest.raises(claw.ClawError):
             claw.claw_set_tile_walk(H.ctx, 0, bad)
+    claw.claw_set_tile_walk(H.ctx, 0, -1)   # automatic
     with pytest.raises(claw.ClawError):
         claw.claw_set_tile_walk(H.ctx, 1, 1)   # level not set
