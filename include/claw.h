@@ -127,7 +127,9 @@ int claw_set_level(claw_ctx* ctx, int32_t level, const claw_box* boxes, int32_t 
  * nx and offsets) and
  * the threads per CTA (0 = default).  Supported for acoustics: 32x32 with 256 or 512 threads,
  * 32x16 with 256, 16x16 with 128; claw_set_level installs 32x32, 256 threads.  Supported for
- * shallow water: 16x16 with 256 threads, 32x16 with 512; claw_set_level installs 16x16.
+ * shallow water: 16x16 with 256 threads, 32x16 with 512; claw_set_level installs 16x16.  Once
+ * chosen here, a level's tiling stays through later claw_set_level calls (with staging 0 when
+ * the new boxes do not allow bulk copies), as does its claw_set_tile_walk choice.
  * Staging 1 is installed when allowed.  A new tile shape rewrites the level's tile lists in
  * place (after synchronising the device): graphs captured before must not be replayed.
  * Errors: CLAW_EINVAL, CLAW_ENOMEM, CLAW_ECUDA. */
@@ -459,9 +461,12 @@ int claw_cluster_flags(int32_t nx, int32_t ny, int32_t ratio, const claw_box* co
  * the old level (old_boxes with their qoff in q_old, host array) where an old box held it, else
  * the conservative space interpolation from q_coarse (level-1, same time), read from the coarse
  * box holding the cell's parent with its ghosts, which must be filled (the new boxes lie two
- * coarse cells inside the coarse level, as claw_regrid_boxes makes them).  Waits for its
- * launches (its tables sit in a scratch arena of the context that the next call reuses).  Errors: CLAW_EINVAL (a new box not nested in the
- * coarse level), CLAW_ESTATE, CLAW_ENOMEM, CLAW_ECUDA. */
+ * coarse cells inside the coarse level, as claw_regrid_boxes makes them).  On the device: the old
+ * boxes and the coarse boxes are painted into level-wide index grids (4 bytes per cell of the
+ * level and of the coarse level, kept by the context), then every new cell reads its source from
+ * them.  Waits for its launches (its tables sit in a scratch arena of the context that the next
+ * call reuses).  Errors: CLAW_EINVAL (an old box outside its level, or a new cell without a coarse
+ * parent: not nested; the other cells are written), CLAW_ESTATE, CLAW_ENOMEM, CLAW_ECUDA. */
 int claw_regrid_transfer(claw_ctx* ctx, int32_t level, const claw_box* old_boxes, int32_t n_old, const double* q_old,
                          double* q_new, const double* q_coarse, void* stream);
 

@@ -126,6 +126,7 @@ void claw_destroy(claw_ctx* ctx)
             free_arena(ctx->lev[L].coeftab);
         }
         free_arena(ctx->scratch);
+        cudaFree(ctx->xgrid);
         cudaFree(ctx->err);
         cudaFree(ctx->done);
         cudaFree(ctx->minh);
@@ -166,25 +167,29 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         }
         if ((b.nx & 1) || (b.qoff & 1)) even = false;
     }
-    // disjointness within each run (bucketed)
+    // the boxes of each run bucketed (kept for the table builds of this level and the next),
+    // and disjoint: boxes that overlap share a bucket
     {
-        std::vector<Locator> loc(ctx->nruns);
-        for (int r = 0; r < ctx->nruns; ++r) loc[r].boxes = &d.boxes;
-        for (int n = 0; n < nboxes; ++n) {
-            const claw_box& b = boxes[n];
-            // compare with boxes already added that share a bucket
-            for (int bj = floordiv(b.jlo, Locator::B); bj <= floordiv(b.jlo + b.ny - 1, Locator::B); ++bj)
-                for (int bi = floordiv(b.ilo, Locator::B); bi <= floordiv(b.ilo + b.nx - 1, Locator::B); ++bi) {
-                    auto it = loc[b.run].buckets.find(Locator::key(bi, bj));
-                    if (it == loc[b.run].buckets.end()) continue;
-                    for (int m : it->second) {
-                        const claw_box& o = boxes[m];
+        std::vector<std::vector<int>> sel(ctx->nruns);
+        for (int n = 0; n < nboxes; ++n) sel[boxes[n].run].push_back(n);
+        std::vector<Locator>& loc = ctx->loc[L];
+        loc.assign(ctx->nruns, Locator{});
+        for (int q = 0; q < ctx->nruns; ++q)
+            if (L < ctx->runs[q].nlev)
+                loc[q].build(&d.boxes, sel[q], level_nx(ctx->runs[q], L), level_ny(ctx->runs[q], L));
+        for (int q = 0; q < ctx->nruns; ++q) {
+            const Locator& lq = loc[q];
+            for (size_t k = 0; k + 1 < lq.start.size(); ++k)
+                for (int t = lq.start[k]; t < lq.start[k + 1]; ++t)
+                    for (int u = t + 1; u < lq.start[k + 1]; ++u) {
+                        const claw_box& b = boxes[lq.items[t]];
+                        const claw_box& o = boxes[lq.items[u]];
                         if (b.ilo < o.ilo + o.nx && o.ilo < b.ilo + b.nx && b.jlo < o.jlo + o.ny &&
-                            o.jlo < b.jlo + b.ny)
+                            o.jlo < b.jlo + b.ny) {
+                            loc.clear();
                             return CLAW_EINVAL;
+                        }
                     }
-                }
-            loc[b.run].add(b, n);
         }
     }
     // patch table
@@ -207,10 +212,14 @@ int claw_set_level(claw_ctx* ctx, int32_t L, const claw_box* boxes, int32_t nbox
         d.hpatches[n] = P;
     }
     ctx->tma_ok[L] = even;
-    d.tx = ctx->kind() == KIND_SWE ? 16 : 32;
-    d.ty = ctx->kind() == KIND_SWE ? 16 : 32;
-    d.staging = even ? 1 : 0;
-    d.walk = -1;
+    if (!d.tiling_set) {   // a level's first boxes; later calls keep the tiling chosen for it
+        d.tx = ctx->kind() == KIND_SWE ? 16 : 32;
+        d.ty = ctx->kind() == KIND_SWE ? 16 : 32;
+        d.nt = 0;
+        d.staging = even ? 1 : 0;
+    } else if (!even) {
+        d.staging = 0;
+    }
     GhostTables gt;
     std::vector<AvgRect> avg;
     int rc = build_ghost_tables(ctx, L, gt, true);
@@ -318,6 +327,7 @@ int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t st
     LevelDev& d = ctx->lev[L];
     d.staging = staging;
     d.nt = threads;
+    d.tiling_set = true;
     if (d.tx == tx && d.ty == ty) return CLAW_OK;
     d.tx = tx;
     d.ty = ty;

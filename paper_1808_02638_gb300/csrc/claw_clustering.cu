@@ -325,108 +325,67 @@ int claw_regrid_transfer(claw_ctx* ctx, int32_t L, const claw_box* old_boxes, in
     if (!ctx->set[L] || !ctx->set[L - 1]) return CLAW_ESTATE;
     DevGuard g(ctx->device);
     const LevelDev& d = ctx->lev[L];
-    std::vector<claw_box> olds(old_boxes, old_boxes + n_old);
-    std::vector<Locator> oloc(ctx->nruns), cloc(ctx->nruns);
-    for (int q = 0; q < ctx->nruns; ++q) {
-        oloc[q].boxes = &olds;
-        cloc[q].boxes = &ctx->lev[L - 1].boxes;
-    }
+    const LevelDev& c = ctx->lev[L - 1];
+    // the old boxes must lie in their run's level (they index the level-wide grid)
     for (int n = 0; n < n_old; ++n) {
-        if (olds[n].run < 0 || olds[n].run >= ctx->nruns) return CLAW_EINVAL;
-        oloc[olds[n].run].add(olds[n], n);
+        const claw_box& b = old_boxes[n];
+        if (b.run < 0 || b.run >= ctx->nruns || L >= ctx->runs[b.run].nlev) return CLAW_EINVAL;
+        const int NX = level_nx(ctx->runs[b.run], L), NY = level_ny(ctx->runs[b.run], L);
+        if (b.nx < 1 || b.ny < 1 || b.ilo < 0 || b.jlo < 0 || b.ilo + b.nx > NX || b.jlo + b.ny > NY || b.qoff < 0)
+            return CLAW_EINVAL;
     }
-    for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
-        cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
-    const int r = d.ratio;
-    // per new box, independently (threads): rectangles copied from old boxes, and row runs
-    // interpolated from the coarse level where no old box covers it
-    struct BoxTransfer {
-        std::vector<RectCopy> copies;
-        std::vector<InterpRun> runs;
-        int rc = CLAW_OK;
-    };
-    std::vector<BoxTransfer> per(d.nboxes);
-    auto one_box = [&](const claw_box& b, BoxTransfer& out) -> int {
-        std::vector<RectCopy>& copies = out.copies;
-        std::vector<InterpRun>& runs = out.runs;
-        std::vector<unsigned char> mask;
-        // old boxes overlapping b: copied rectangles
-        mask.assign((size_t)b.nx * b.ny, 0);
-        std::vector<int> seen;
-        for (int bj = floordiv(b.jlo, Locator::B); bj <= floordiv(b.jlo + b.ny - 1, Locator::B); ++bj)
-            for (int bi = floordiv(b.ilo, Locator::B); bi <= floordiv(b.ilo + b.nx - 1, Locator::B); ++bi) {
-                auto it = oloc[b.run].buckets.find(Locator::key(bi, bj));
-                if (it == oloc[b.run].buckets.end()) continue;
-                for (int m : it->second) {
-                    if (std::find(seen.begin(), seen.end(), m) != seen.end()) continue;
-                    seen.push_back(m);
-                    const claw_box& o = olds[m];
-                    const int i0 = std::max(b.ilo, o.ilo), i1 = std::min(b.ilo + b.nx, o.ilo + o.nx);
-                    const int j0 = std::max(b.jlo, o.jlo), j1 = std::min(b.jlo + b.ny, o.jlo + o.ny);
-                    if (i0 >= i1 || j0 >= j1) continue;
-                    copies.push_back(RectCopy{cell_off(b, i0, j0), cell_off(o, i0, j0), plane_of(b), plane_of(o), i1 - i0,
-                                              j1 - j0, b.nx + 4, o.nx + 4});
-                    for (int j = j0; j < j1; ++j)
-                        std::memset(&mask[(size_t)(j - b.jlo) * b.nx + (i0 - b.ilo)], 1, (size_t)(i1 - i0));
-                }
-            }
-        // the rest: row runs of cells over one coarse box each
-        for (int j = 0; j < b.ny; ++j) {
-            int i = 0;
-            while (i < b.nx) {
-                if (mask[(size_t)j * b.nx + i]) {
-                    ++i;
-                    continue;
-                }
-                const int gj = b.jlo + j, gi = b.ilo + i;
-                const int cm = cloc[b.run].find(floordiv(gi, r), floordiv(gj, r));
-                if (cm < 0) return CLAW_EINVAL;   // the new box is not nested in the coarse level
-                const claw_box& cb = ctx->lev[L - 1].boxes[cm];
-                int e = i + 1;
-                while (e < b.nx && !mask[(size_t)j * b.nx + e] && floordiv(b.ilo + e, r) < cb.ilo + cb.nx) ++e;
-                InterpRun R;
-                R.dst = cell_off(b, gi, gj);
-                R.dplane = plane_of(b);
-                R.cbase = cb.qoff;
-                R.cplane = plane_of(cb);
-                R.n = e - i;
-                R.gi0 = gi;
-                R.gj = gj;
-                R.cilo = cb.ilo;
-                R.cjlo = cb.jlo;
-                R.cpitch = cb.nx + 4;
-                R.r = r;
-                R.pad = 0;
-                runs.push_back(R);
-                i = e;
-            }
-        }
-        return CLAW_OK;
-    };
-    parallel_for(d.nboxes, [&](int n0, int n1) {
-        for (int n = n0; n < n1; ++n) per[n].rc = one_box(d.boxes[n], per[n]);
-    });
-    size_t ncopies = 0, nruns = 0;
-    for (const BoxTransfer& t : per) {
-        if (t.rc) return t.rc;
-        ncopies += t.copies.size();
-        nruns += t.runs.size();
+    auto xfer = [](const claw_box& b) { return XferBox{b.qoff, b.run, b.ilo, b.jlo, b.nx, b.ny, 0}; };
+    std::vector<XferBox> nb(d.nboxes), ob(n_old), cb(c.boxes.size());
+    int max_rows = 0;
+    for (int n = 0; n < d.nboxes; ++n) nb[n] = xfer(d.boxes[n]), max_rows = std::max(max_rows, d.boxes[n].ny);
+    for (int n = 0; n < n_old; ++n) ob[n] = xfer(old_boxes[n]), max_rows = std::max(max_rows, old_boxes[n].ny);
+    for (size_t n = 0; n < c.boxes.size(); ++n) cb[n] = xfer(c.boxes[n]), max_rows = std::max(max_rows, c.boxes[n].ny);
+    // per run: where its level grids start and their pitch
+    std::vector<long long> fgoff(ctx->nruns), cgoff(ctx->nruns);
+    std::vector<int> fpitch(ctx->nruns), cpitch(ctx->nruns);
+    long long fcells = 0, ccells = 0;
+    for (int q = 0; q < ctx->nruns; ++q) {
+        const claw_problem& p = ctx->runs[q];
+        fgoff[q] = fcells;
+        cgoff[q] = ccells;
+        fpitch[q] = L < p.nlev ? level_nx(p, L) : 0;
+        cpitch[q] = L - 1 < p.nlev ? level_nx(p, L - 1) : 0;
+        if (L < p.nlev) fcells += (long long)level_nx(p, L) * level_ny(p, L);
+        if (L - 1 < p.nlev) ccells += (long long)level_nx(p, L - 1) * level_ny(p, L - 1);
     }
-    RectCopy* dc = nullptr;
-    InterpRun* di = nullptr;
+    const size_t need = (size_t)(fcells + ccells);
+    if (need > ctx->xgrid_cap) {
+        cudaFree(ctx->xgrid);
+        ctx->xgrid = nullptr;
+        ctx->xgrid_cap = 0;
+        if (cudaMalloc((void**)&ctx->xgrid, need * sizeof(int)) != cudaSuccess) return CLAW_ENOMEM;
+        ctx->xgrid_cap = need;
+    }
+    XferBox *dnb = nullptr, *dob = nullptr, *dcb = nullptr;
+    long long *dfgoff = nullptr, *dcgoff = nullptr;
+    int *dfpitch = nullptr, *dcpitch = nullptr, *derr = nullptr;
+    const std::vector<int> zero(1, 0);
     ArenaPack pack;
-    pack.add_parts(&dc, d.nboxes, [&](int n) -> const std::vector<RectCopy>& { return per[n].copies; });
-    pack.add_parts(&di, d.nboxes, [&](int n) -> const std::vector<InterpRun>& { return per[n].runs; });
+    pack.add(&dnb, nb);
+    pack.add(&dob, ob);
+    pack.add(&dcb, cb);
+    pack.add(&dfgoff, fgoff);
+    pack.add(&dcgoff, cgoff);
+    pack.add(&dfpitch, fpitch);
+    pack.add(&dcpitch, cpitch);
+    pack.add(&derr, zero);
     int rc = pack.commit(ctx->scratch);
+    if (rc) return rc;
+    XferGrids gr{dfgoff, dfpitch, dcgoff, dcpitch, ctx->xgrid, ctx->xgrid + fcells};
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaSuccess;
-    if (!rc) {
-        e = launch_rect_copy(dc, (int)ncopies, q_old, q_new, s);
-        if (e == cudaSuccess) e = launch_interp_runs(di, (int)nruns, q_coarse, q_new, s);
-        ctx->launches += (ncopies > 0) + (nruns > 0);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the scratch tables are reused by the next call
-    }
-    return rc ? rc : cuda_rc(e);
+    cudaError_t e = launch_regrid_transfer(dnb, d.nboxes, dob, n_old, dcb, (int)cb.size(), max_rows, d.ratio, gr,
+                                           fcells, ccells, q_old, q_coarse, q_new, derr, s);
+    ctx->launches += 3;
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the scratch tables are reused by the next call
+    if (e != cudaSuccess) return CLAW_ECUDA;
+    return herr ? CLAW_EINVAL : CLAW_OK;   // a new box not nested in the coarse level
 }
 
 }  // extern "C"

@@ -36,6 +36,71 @@ struct TmapCache {
     bool pinned = false;   // handed to a stream capture: a graph may read it until the level is rebuilt
 };
 
+inline int floordiv(int a, int r) { return a >= 0 ? a / r : -((-a + r - 1) / r); }
+
+// The boxes of one run on one level, bucketed by B x B cells of the level (compressed rows:
+// bucket k lists its boxes in items[start[k] .. start[k+1]), in box order).
+struct Locator {
+    static constexpr int B = 16;
+    const std::vector<claw_box>* boxes = nullptr;
+    int nx = 0, ny = 0, nbx = 0, nby = 0;
+    std::vector<int> start, items;
+
+    // boxes: the level's boxes; sel: the indices of the run's boxes; the level is nx x ny
+    void build(const std::vector<claw_box>* bx, const std::vector<int>& sel, int nx_, int ny_)
+    {
+        boxes = bx;
+        nx = nx_;
+        ny = ny_;
+        nbx = (nx + B - 1) / B;
+        nby = (ny + B - 1) / B;
+        start.assign((size_t)nbx * nby + 1, 0);
+        auto span = [&](const claw_box& b, int& bi0, int& bi1, int& bj0, int& bj1) {
+            bi0 = std::max(0, b.ilo / B);
+            bj0 = std::max(0, b.jlo / B);
+            bi1 = std::min(nbx - 1, (b.ilo + b.nx - 1) / B);
+            bj1 = std::min(nby - 1, (b.jlo + b.ny - 1) / B);
+        };
+        for (int n : sel) {
+            int bi0, bi1, bj0, bj1;
+            span((*bx)[n], bi0, bi1, bj0, bj1);
+            for (int bj = bj0; bj <= bj1; ++bj)
+                for (int bi = bi0; bi <= bi1; ++bi) ++start[(size_t)bj * nbx + bi + 1];
+        }
+        for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+        items.assign(start.back(), 0);
+        std::vector<int> fill(start.begin(), start.end() - 1);
+        for (int n : sel) {
+            int bi0, bi1, bj0, bj1;
+            span((*bx)[n], bi0, bi1, bj0, bj1);
+            for (int bj = bj0; bj <= bj1; ++bj)
+                for (int bi = bi0; bi <= bi1; ++bi) items[fill[(size_t)bj * nbx + bi]++] = n;
+        }
+    }
+    // the box holding level cell (i, j), or -1
+    int find(int i, int j) const
+    {
+        if (i < 0 || j < 0 || i >= nx || j >= ny) return -1;
+        const size_t k = (size_t)(j / B) * nbx + i / B;
+        for (int t = start[k]; t < start[k + 1]; ++t) {
+            const claw_box& b = (*boxes)[items[t]];
+            if (i >= b.ilo && i < b.ilo + b.nx && j >= b.jlo && j < b.jlo + b.ny) return items[t];
+        }
+        return -1;
+    }
+    // f(n) for the boxes listed in the buckets meeting cells [i0, i1) x [j0, j1) (a box can come
+    // more than once)
+    template <class F>
+    void each(int i0, int j0, int i1, int j1, F f) const
+    {
+        const int bi0 = std::max(0, floordiv(i0, B)), bj0 = std::max(0, floordiv(j0, B));
+        const int bi1 = std::min(nbx - 1, floordiv(i1 - 1, B)), bj1 = std::min(nby - 1, floordiv(j1 - 1, B));
+        for (int bj = bj0; bj <= bj1; ++bj)
+            for (int bi = bi0; bi <= bi1; ++bi)
+                for (int t = start[(size_t)bj * nbx + bi]; t < start[(size_t)bj * nbx + bi + 1]; ++t) f(items[t]);
+    }
+};
+
 struct claw_ctx {
     int device = 0;
     int nsm = 0;
@@ -64,6 +129,9 @@ struct claw_ctx {
     std::atomic<long long> launches{0};
     bool tma_ok[CLAW_MAXLEV] = {};
     DevArena scratch;   // the transfer tables of a regrid
+    std::vector<Locator> loc[CLAW_MAXLEV];   // per level and run: the boxes bucketed (built by claw_set_level)
+    int* xgrid = nullptr;      // the index grids of a regrid transfer (fine then coarse), grown on use
+    size_t xgrid_cap = 0;      // ints
     unsigned wait_polls = kWaitPolls;   // first-wait bound of the staged step kernels
 };
 
@@ -115,35 +183,8 @@ inline int bc_map(int k, int n, int bclo, int bchi, int* flip)
     return k;
 }
 
-inline int floordiv(int a, int r) { return a >= 0 ? a / r : -((-a + r - 1) / r); }
 
 // boxes of one (run, level), bucketed for point lookups
-struct Locator {
-    static constexpr int B = 16;
-    std::unordered_map<long long, std::vector<int>> buckets;
-    const std::vector<claw_box>* boxes = nullptr;
-    std::vector<int> idx;   // global box index of each entry
-
-    static long long key(int bi, int bj) { return ((long long)bi << 32) ^ (unsigned)bj; }
-
-    void add(const claw_box& b, int n)
-    {
-        for (int bj = floordiv(b.jlo, B); bj <= floordiv(b.jlo + b.ny - 1, B); ++bj)
-            for (int bi = floordiv(b.ilo, B); bi <= floordiv(b.ilo + b.nx - 1, B); ++bi)
-                buckets[key(bi, bj)].push_back(n);
-    }
-    int find(int i, int j) const
-    {
-        auto it = buckets.find(key(floordiv(i, B), floordiv(j, B)));
-        if (it == buckets.end()) return -1;
-        for (int n : it->second) {
-            const claw_box& b = (*boxes)[n];
-            if (i >= b.ilo && i < b.ilo + b.nx && j >= b.jlo && j < b.jlo + b.ny) return n;
-        }
-        return -1;
-    }
-};
-
 inline long long cell_off(const claw_box& b, int i, int j)   // plane-0 element of level cell (i, j)
 {
     return b.qoff + (long long)(j - b.jlo + CLAW_MBC) * (b.nx + 2 * CLAW_MBC) + (i - b.ilo + CLAW_MBC);

@@ -102,13 +102,21 @@ struct FlagBox {
     long long qoff, goff;
     int nx, ny, pitch, pad;
 };
-struct RectCopy {     // w x h cells (3 planes) from one pool into another
-    long long dst, src, dplane, splane;
-    int w, h, dpitch, spitch;
+// A box in a level's index space with its pool offset, as the regrid transfer reads it.
+struct XferBox {
+    long long qoff;
+    int run, ilo, jlo, nx, ny, pad;
 };
-struct InterpRun {    // n fine cells of row gj from column gi0, interpolated from one coarse box
-    long long dst, dplane, cbase, cplane;   // cbase: the coarse box's qoff
-    int n, gi0, gj, cilo, cjlo, cpitch, r, pad;
+// The level-wide index grids of a regrid transfer: per run, the box covering each cell of the
+// fine level (old boxes) and of the coarse level, or -1.  Run q's grid starts at goff[q] with
+// row pitch pitch[q] (the level's NX).
+struct XferGrids {
+    const long long* fgoff;
+    const int* fpitch;
+    const long long* cgoff;
+    const int* cpitch;
+    int* fgrid;
+    int* cgrid;
 };
 
 // One fine ghost cell filled by space-time interpolation from the coarser level.
@@ -148,6 +156,7 @@ struct LevelDev {
     int navg = 0;          // averaging rects into the coarser level
     int ratio = 1;
     int tx = 32, ty = 32, staging = 1, nt = 0;   // tile, staging, threads per CTA (0: default)
+    bool tiling_set = false;   // claw_set_tiling chose tx, ty, staging, nt (kept by claw_set_level)
     int walk = -1;         // column walks (tiles ordered up each column, tcum): 1 on, 0 off, -1 automatic
     bool walking = false;  // the tile lists in place are column walks
     PatchDev* patches = nullptr;
@@ -292,8 +301,13 @@ cudaError_t launch_medium_aux_adjoint(const PatchDev* p, int n, int max_rows, co
 // regridding
 cudaError_t launch_flags(const FlagBox* boxes, int nb, int max_rows, const double* q, double tol,
                          unsigned char* flags, cudaStream_t s);
-cudaError_t launch_rect_copy(const RectCopy* c, int n, const double* src, double* dst, cudaStream_t s);
-cudaError_t launch_interp_runs(const InterpRun* r, int n, const double* qc, double* qf, cudaStream_t s);
+// regrid transfer (claw_regrid.cu): index grids painted with the old fine boxes and the coarse
+// boxes, then every cell of every new box copied from the old box covering it or interpolated
+// from the coarse level; *err |= 1 where a new cell has no coarse cell (not nested)
+cudaError_t launch_regrid_transfer(const XferBox* nb, int n_new, const XferBox* ob, int n_old, const XferBox* cb,
+                                   int n_coarse, int max_rows, int ratio, const XferGrids& g, long long fcells,
+                                   long long ccells, const double* q_old, const double* q_coarse, double* q_new,
+                                   int* err, cudaStream_t s);
 
 // conservation fix (uniform medium): buf holds 3 doubles per interface record (the coarse
 // parts) followed by 3 per record and fine edge (the fine parts, summed over the substeps)

@@ -51,6 +51,7 @@ void free_level(claw_ctx* ctx, int L)
     d.hpatches.clear();
     d.htiles.clear();
     d.htcum.clear();
+    ctx->loc[L].clear();
     d.tcum = nullptr;
     ctx->set[L] = false;
 }
@@ -216,15 +217,9 @@ constexpr long long kBlockCells = 256;   // cells per block of the copy kernel (
 int build_ghost_tables(claw_ctx* ctx, int L, GhostTables& gt, bool want_ring)
 {
     LevelDev& d = ctx->lev[L];
-    std::vector<Locator> loc(ctx->nruns), cloc(ctx->nruns);
-    for (int r = 0; r < ctx->nruns; ++r) {
-        loc[r].boxes = &d.boxes;
-        if (L > 0) cloc[r].boxes = &ctx->lev[L - 1].boxes;
-    }
-    for (int n = 0; n < d.nboxes; ++n) loc[d.boxes[n].run].add(d.boxes[n], n);
-    if (L > 0)
-        for (int n = 0; n < (int)ctx->lev[L - 1].boxes.size(); ++n)
-            cloc[ctx->lev[L - 1].boxes[n].run].add(ctx->lev[L - 1].boxes[n], n);
+    const std::vector<Locator>& loc = ctx->loc[L];
+    static const std::vector<Locator> none;
+    const std::vector<Locator>& cloc = L > 0 ? ctx->loc[L - 1] : none;
 
     // per box, independently (threads): its copy rectangles, interpolated cells and ghost ring
     std::vector<BoxGhosts>& per = gt.per;
@@ -402,13 +397,8 @@ void build_reflux_tables(claw_ctx* ctx, int L, std::vector<RefluxRec>& recs, std
     const LevelDev& f = ctx->lev[L];
     const LevelDev& c = ctx->lev[L - 1];
     const int r = f.ratio;
-    std::vector<Locator> floc(ctx->nruns), cloc(ctx->nruns);
-    for (int q = 0; q < ctx->nruns; ++q) {
-        floc[q].boxes = &f.boxes;
-        cloc[q].boxes = &c.boxes;
-    }
-    for (int n = 0; n < f.nboxes; ++n) floc[f.boxes[n].run].add(f.boxes[n], n);
-    for (int n = 0; n < (int)c.boxes.size(); ++n) cloc[c.boxes[n].run].add(c.boxes[n], n);
+    const std::vector<Locator>& floc = ctx->loc[L];
+    const std::vector<Locator>& cloc = ctx->loc[L - 1];
     auto wrap = [](int k, int n, int lo, int hi, bool& ok) {
         ok = true;
         if (k >= 0 && k < n) return k;
@@ -416,39 +406,45 @@ void build_reflux_tables(claw_ctx* ctx, int L, std::vector<RefluxRec>& recs, std
         ok = false;
         return k;
     };
+    // the records of each fine box on its own (host threads), then concatenated in box order
+    std::vector<std::vector<RefluxRec>> per(f.nboxes);
+    parallel_for(f.nboxes, [&](int n0, int n1) {
+        for (int nf = n0; nf < n1; ++nf) {
+            std::vector<RefluxRec>& out = per[nf];
+            const claw_box& b = f.boxes[nf];
+            const claw_problem& p = ctx->runs[b.run];
+            const int NXc = level_nx(p, L - 1), NYc = level_ny(p, L - 1);
+            const int I0 = b.ilo / r, I1 = (b.ilo + b.nx) / r, J0 = b.jlo / r, J1 = (b.jlo + b.ny) / r;
+            auto add = [&](int I, int J, int dir, int side, int fi, int fj) {
+                bool okx, oky;
+                const int Im = wrap(I, NXc, p.bc[0], p.bc[1], okx), Jm = wrap(J, NYc, p.bc[2], p.bc[3], oky);
+                if (!okx || !oky) return;
+                if (floc[b.run].find(Im * r, Jm * r) >= 0) return;   // covered: a fine-fine edge
+                const int nc = cloc[b.run].find(Im, Jm);
+                if (nc < 0) return;                                 // excluded by proper nesting
+                RefluxRec R;
+                R.cbox = nc;
+                R.fbox = nf;
+                R.ci = (short)(Im - c.boxes[nc].ilo);
+                R.cj = (short)(Jm - c.boxes[nc].jlo);
+                R.fi = (short)fi;
+                R.fj = (short)fj;
+                R.dir = (short)dir;
+                R.side = (short)side;
+                out.push_back(R);
+            };
+            for (int J = J0; J < J1; ++J) {
+                add(I1, J, 0, -1, b.nx - 1, J * r - b.jlo);
+                add(I0 - 1, J, 0, +1, 0, J * r - b.jlo);
+            }
+            for (int I = I0; I < I1; ++I) {
+                add(I, J1, 1, -1, I * r - b.ilo, b.ny - 1);
+                add(I, J0 - 1, 1, +1, I * r - b.ilo, 0);
+            }
+        }
+    }, 8);
     recs.clear();
-    for (int nf = 0; nf < f.nboxes; ++nf) {
-        const claw_box& b = f.boxes[nf];
-        const claw_problem& p = ctx->runs[b.run];
-        const int NXc = level_nx(p, L - 1), NYc = level_ny(p, L - 1);
-        const int I0 = b.ilo / r, I1 = (b.ilo + b.nx) / r, J0 = b.jlo / r, J1 = (b.jlo + b.ny) / r;
-        auto add = [&](int I, int J, int dir, int side, int fi, int fj) {
-            bool okx, oky;
-            const int Im = wrap(I, NXc, p.bc[0], p.bc[1], okx), Jm = wrap(J, NYc, p.bc[2], p.bc[3], oky);
-            if (!okx || !oky) return;
-            if (floc[b.run].find(Im * r, Jm * r) >= 0) return;   // covered: a fine-fine edge
-            const int nc = cloc[b.run].find(Im, Jm);
-            if (nc < 0) return;                                 // excluded by proper nesting
-            RefluxRec R;
-            R.cbox = nc;
-            R.fbox = nf;
-            R.ci = (short)(Im - c.boxes[nc].ilo);
-            R.cj = (short)(Jm - c.boxes[nc].jlo);
-            R.fi = (short)fi;
-            R.fj = (short)fj;
-            R.dir = (short)dir;
-            R.side = (short)side;
-            recs.push_back(R);
-        };
-        for (int J = J0; J < J1; ++J) {
-            add(I1, J, 0, -1, b.nx - 1, J * r - b.jlo);
-            add(I0 - 1, J, 0, +1, 0, J * r - b.jlo);
-        }
-        for (int I = I0; I < I1; ++I) {
-            add(I, J1, 1, -1, I * r - b.ilo, b.ny - 1);
-            add(I, J0 - 1, 1, +1, I * r - b.ilo, 0);
-        }
-    }
+    for (const auto& v : per) recs.insert(recs.end(), v.begin(), v.end());
     std::stable_sort(recs.begin(), recs.end(), [](const RefluxRec& x, const RefluxRec& y) {
         if (x.cbox != y.cbox) return x.cbox < y.cbox;
         if (x.cj != y.cj) return x.cj < y.cj;
@@ -461,29 +457,43 @@ void build_reflux_tables(claw_ctx* ctx, int L, std::vector<RefluxRec>& recs, std
     if (!recs.empty()) group.push_back((int)recs.size());
 }
 
-// coarse cells of level L-1 covered by each box of level L
+// coarse cells of level L-1 covered by each box of level L: per fine box (host threads), the
+// coarse boxes its footprint meets, found through the coarse level's buckets, in box order
 void build_avg_tables(claw_ctx* ctx, int L, std::vector<AvgRect>& out)
 {
     const LevelDev& f = ctx->lev[L];
     const LevelDev& c = ctx->lev[L - 1];
     const int r = f.ratio;
-    for (const claw_box& F : f.boxes)
-        for (const claw_box& C : c.boxes) {
-            if (C.run != F.run) continue;
-            const int i0 = std::max(F.ilo / r, C.ilo), i1 = std::min((F.ilo + F.nx) / r, C.ilo + C.nx);
-            const int j0 = std::max(F.jlo / r, C.jlo), j1 = std::min((F.jlo + F.ny) / r, C.jlo + C.ny);
-            if (i0 >= i1 || j0 >= j1) continue;
-            AvgRect a;
-            a.cdst = cell_off(C, i0, j0);
-            a.fsrc = cell_off(F, i0 * r, j0 * r);
-            a.cplane = plane_of(C);
-            a.fplane = plane_of(F);
-            a.w = i1 - i0;
-            a.h = j1 - j0;
-            a.cpitch = C.nx + 4;
-            a.fpitch = F.nx + 4;
-            out.push_back(a);
+    const std::vector<Locator>& cloc = ctx->loc[L - 1];
+    std::vector<std::vector<AvgRect>> per(f.nboxes);
+    parallel_for(f.nboxes, [&](int n0, int n1) {
+        std::vector<int> cand;
+        for (int nf = n0; nf < n1; ++nf) {
+            const claw_box& F = f.boxes[nf];
+            const int I0 = F.ilo / r, I1 = (F.ilo + F.nx) / r, J0 = F.jlo / r, J1 = (F.jlo + F.ny) / r;
+            cand.clear();
+            cloc[F.run].each(I0, J0, I1, J1, [&](int nc) { cand.push_back(nc); });
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            for (int nc : cand) {
+                const claw_box& C = c.boxes[nc];
+                const int i0 = std::max(I0, C.ilo), i1 = std::min(I1, C.ilo + C.nx);
+                const int j0 = std::max(J0, C.jlo), j1 = std::min(J1, C.jlo + C.ny);
+                if (i0 >= i1 || j0 >= j1) continue;
+                AvgRect a;
+                a.cdst = cell_off(C, i0, j0);
+                a.fsrc = cell_off(F, i0 * r, j0 * r);
+                a.cplane = plane_of(C);
+                a.fplane = plane_of(F);
+                a.w = i1 - i0;
+                a.h = j1 - j0;
+                a.cpitch = C.nx + 4;
+                a.fpitch = F.nx + 4;
+                per[nf].push_back(a);
+            }
         }
+    }, 8);
+    for (const auto& v : per) out.insert(out.end(), v.begin(), v.end());
 }
 
 // tensor-map descriptors of one level for a given q pool and tiling (cached per pool)
