@@ -384,7 +384,7 @@ __device__ __forceinline__ void pull_ghosts(const StepArgs& A, const PatchDev& P
 // Registers: the one-buffer staging is capped for three CTAs per SM; the 128-thread tiles for
 // five (the shared memory of five fits an SM), except those evaluating interpolated ghosts.
 template <int MED, int LIM, int TX, int TY, int NT, int STAGE, int PULL, bool REC = false>
-__global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : (NT == 128 && PULL < 2 && !REC ? 5 : 1))
+__global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : (NT == 128 && !REC ? 5 : 1))
     step_kernel(const StepArgs A)
 {
     static_assert(!REC || MED == 1, "the tape records the cell-wise step");
