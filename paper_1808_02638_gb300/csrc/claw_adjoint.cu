@@ -89,7 +89,7 @@ template <> struct LimD<CLAW_LIM_MC> {
         if (!same_sign_nonzero(ia, ib, ma, mb)) return 0.0;
         const bool amin = ma < mb;
         const long long t2 = (amin ? ma : mb) + ONE_EXP;
-        long long sh = add_mag(ma, mb) - ONE_EXP;
+        long long sh = bits(val(ma) + val(mb)) - ONE_EXP;
         sh = sh > 0 ? sh : 0;
         if (sh < t2) {
             da = db = 0.5;

@@ -93,6 +93,7 @@ template <int L> struct Lim;
 template <> struct Lim<CLAW_LIM_NONE> {
     template <bool = false>
     static __device__ __forceinline__ double f(double a, double) { return a; }
+    template <bool = false>
     static __device__ __forceinline__ double fc(double a, double, int& code)
     {
         code = LIMC_A;
@@ -108,6 +109,7 @@ template <> struct Lim<CLAW_LIM_MINMOD> {   // max(0, min(1, theta)): sign(a) mi
         const long long m = ma < mb ? ma : mb;
         return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
     }
+    template <bool = false>
     static __device__ __forceinline__ double fc(double a, double b, int& code)
     {
         using namespace lim_bits;
@@ -128,6 +130,7 @@ template <> struct Lim<CLAW_LIM_SUPERBEE> {   // max(0, min(1, 2 theta), min(2, 
         const long long m = m1 > m2 ? m1 : m2;
         return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
     }
+    template <bool = false>
     static __device__ __forceinline__ double fc(double a, double b, int& code)
     {
         using namespace lim_bits;
@@ -151,6 +154,7 @@ template <> struct Lim<CLAW_LIM_VANLEER> {   // (theta + |theta|) / (1 + |theta|
         if (!same_sign_nonzero(ia, ib, ia & MAG, ib & MAG) || hs < ONE_EXP) return 0.0;
         return a * (b * __drcp_rn(val(hs | (ia & SIGN))));
     }
+    template <bool = false>
     static __device__ __forceinline__ double fc(double a, double b, int& code)
     {
         const double m = f(a, b);
@@ -171,12 +175,13 @@ template <> struct Lim<CLAW_LIM_MC> {   // max(0, min((1 + theta)/2, 2, 2 theta)
         const long long m = sh < t2 ? sh : t2;
         return same_sign_nonzero(ia, ib, ma, mb) ? val(m | (ia & SIGN)) : 0.0;
     }
+    template <bool FPSUM = false>
     static __device__ __forceinline__ double fc(double a, double b, int& code)
     {
         using namespace lim_bits;
         const long long ia = bits(a), ib = bits(b), ma = ia & MAG, mb = ib & MAG;
         const long long t2 = (ma < mb ? ma : mb) + ONE_EXP;
-        long long sh = add_mag(ma, mb) - ONE_EXP;
+        long long sh = (FPSUM ? bits(val(ma) + val(mb)) : add_mag(ma, mb)) - ONE_EXP;
         sh = sh > 0 ? sh : 0;
         const bool nz = same_sign_nonzero(ia, ib, ma, mb);
         code = !nz ? LIMC_ZERO : (sh < t2 ? LIMC_HALF : (ma < mb ? LIMC_2A : LIMC_2B));
@@ -672,8 +677,8 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : (NT == 128 && !REC ? 5 : 
                     } else {
                         if (REC) {
                             int c1, c2;
-                            m1 = Lim<LIM>::fc(a1, A1x[e + 1] * AX(AUX_FX1, a, r), c1);
-                            m2 = Lim<LIM>::fc(a2, A2x[e - 1] * AX(AUX_FX2, a, r), c2);
+                            m1 = Lim<LIM>::template fc<true>(a1, A1x[e + 1] * AX(AUX_FX1, a, r), c1);
+                            m2 = Lim<LIM>::template fc<true>(a2, A2x[e - 1] * AX(AUX_FX2, a, r), c2);
                             rec(TAPE_M1, a, r, tag_code(m1, c1));
                             rec(TAPE_M2, a, r, tag_code(m2, c2));
                         } else {
@@ -703,8 +708,8 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : (NT == 128 && !REC ? 5 : 
                     } else {
                         if (REC) {
                             int c1, c2;
-                            m1 = Lim<LIM>::fc(b1, B1y[e + G::YEW] * AX(AUX_FY1, c, bb), c1);
-                            m2 = Lim<LIM>::fc(b2, B2y[e - G::YEW] * AX(AUX_FY2, c, bb), c2);
+                            m1 = Lim<LIM>::template fc<true>(b1, B1y[e + G::YEW] * AX(AUX_FY1, c, bb), c1);
+                            m2 = Lim<LIM>::template fc<true>(b2, B2y[e - G::YEW] * AX(AUX_FY2, c, bb), c2);
                             rec(TAPE_N1, c, bb, tag_code(m1, c1));
                             rec(TAPE_N2, c, bb, tag_code(m2, c2));
                         } else {
