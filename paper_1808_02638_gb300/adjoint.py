@@ -5,7 +5,9 @@ initial state and the medium (rho, K), through the hand-written adjoint kernels.
 `rollout(H, q0, rho, K, ncoarse, every)` is a torch.autograd.Function over `ncoarse` coarse
 steps of hierarchy H (any number of levels and runs).  The forward keeps a checkpoint of every
 level's state every `every` coarse steps; the backward recomputes one segment at a time from its
-checkpoint (recording each level-step's input state and the pre-average coarse state).  With
+checkpoint (recording each level-step's input state and the pre-average coarse state, or, for a
+cell-wise medium, each level-step's tape of intermediates); the last segment, the first to be
+reversed, is recorded by the forward itself when the steps can record.  With
 `every=None` the forward records that tape for the whole rollout instead (memory: every
 level-step's input pool and every pre-average coarse pool, kept in HBM) and the backward
 recomputes nothing.  Either way the backward runs the reverse of the AMR time step of Sec. 2.2
@@ -218,6 +220,31 @@ def _buffers(H, key, make):
     return cache[key]
 
 
+def _segment_tape(H, n, rec, s):
+    """the tape of checkpoint segment s (n coarse steps): two per length, by segment parity, so
+    that one segment can be recomputed while the next is reversed"""
+    return _buffers(H, ("tape", n, rec, s % 2), lambda: _Tape(H, n, record=rec))
+
+
+def _load_segment(H, T, states, dt0):
+    """a segment's starting states and recording time step into its tape (which then holds no
+    rollout's recorded segment: T.owner is set by the forward that records one)"""
+    T.owner = None
+    for L in range(H.nlev):
+        T.state(L, 0).copy_(states[L])
+    T.dtw.copy_(dt0)
+    T.smaxw.zero_()
+
+
+def _record_segment(H, T, n, frozen, s, graphs, reload):
+    """the recording steps of a segment into its tape (the cached graph of the segment's length,
+    parity and dt mode); reload() puts the starting state back after the graph's eager first run"""
+    def body():
+        for k in range(n):
+            _record_coarse(H, T, k, frozen)
+    _run(H, ("bwd-first", n, frozen, True, s % 2), body, graphs, lambda: reload)
+
+
 def _forward_segment(H, n, graphs):
     """n coarse steps of the hierarchy (a CUDA graph when `graphs`); every level's state ends in
     the buffer it started in"""
@@ -294,12 +321,28 @@ class _Rollout(torch.autograd.Function):
                 H.dt.copy_(tape.dtw)
                 H.smax.copy_(tape.smaxw)
             else:
-                for s0 in range(0, ncoarse, every):
+                # the last segment is the first one the backward reverses: with recording steps
+                # it is recorded into its tape now (a recording step costs about as much as a
+                # plain one), instead of being recomputed there before anything else can run
+                rec_last = H.pull and records and _records_ok(H)
+                nseg = (ncoarse + every - 1) // every
+                for s, s0 in enumerate(range(0, ncoarse, every)):
+                    n = min(every, ncoarse - s0)
                     checkpoints.append(([H.q[L][H.cur[L]].clone() for L in range(nlev)], H.dt.clone()))
-                    if H.pull:
-                        _forward_segment(H, min(every, ncoarse - s0), graphs)
+                    if rec_last and s == nseg - 1:
+                        T = _segment_tape(H, n, True, s)
+                        start = checkpoints[-1]
+                        _load_segment(H, T, *start)
+                        _record_segment(H, T, n, frozen, s, graphs, lambda: _load_segment(H, T, *start))
+                        for L in range(nlev):
+                            H.q[L][H.cur[L]].copy_(T.state(L, T.counts[L]))
+                        H.dt.copy_(T.dtw)
+                        H.smax.copy_(T.smaxw)
+                        T.owner = ctx
+                    elif H.pull:
+                        _forward_segment(H, n, graphs)
                     else:
-                        for _ in range(min(every, ncoarse - s0)):
+                        for _ in range(n):
                             H.coarse_step()
             out = [H.q[L][H.cur[L]].clone() for L in range(nlev)]
         ctx.H, ctx.ncoarse, ctx.every, ctx.nlev = H, ncoarse, every, nlev
@@ -383,15 +426,10 @@ def _backward_segments(ctx, H, lbuf, g_aux):
     side = _buffers(H, "side_stream", lambda: torch.cuda.Stream(device=H.dev))
 
     def tape(s):
-        return _buffers(H, ("tape", lens[s], rec, s % 2), lambda: _Tape(H, lens[s], record=rec))
+        return _segment_tape(H, lens[s], rec, s)
 
     def load(s):   # eager: checkpoint s into its tape's first states and recording time step
-        states, dt0 = ctx.checkpoints[s]
-        T = tape(s)
-        for L in range(nlev):
-            T.state(L, 0).copy_(states[L])
-        T.dtw.copy_(dt0)
-        T.smaxw.zero_()
+        _load_segment(H, tape(s), *ctx.checkpoints[s])
 
     def recompute(s):
         T = tape(s)
@@ -408,9 +446,11 @@ def _backward_segments(ctx, H, lbuf, g_aux):
                 lbuf[L][0].copy_(lam[L])
 
     last = nseg - 1
-    load(last)
-    _run(H, ("bwd-first", lens[last], ctx.frozen, rec, last % 2), lambda: recompute(last), ctx.graphs,
-         lambda: (lambda: load(last)))
+    if getattr(tape(last), "owner", None) is not ctx:   # not recorded by this rollout's forward
+        load(last)
+        _run(H, ("bwd-first", lens[last], ctx.frozen, rec, last % 2), lambda: recompute(last), ctx.graphs,
+             lambda: (lambda: load(last)))
+    tape(last).owner = None
     for s in reversed(range(nseg)):
         if s:
             load(s - 1)

@@ -114,6 +114,49 @@ def test_recorded_step_adjoint_equals_the_recomputing_adjoint(limiter):
     assert min(float(g.abs().max()) for g in grads[0][:-1]) > 0.0
 
 
+def test_rollouts_whose_backwards_interleave_keep_their_own_last_segment():
+    # the forward records its last checkpoint segment into a tape the hierarchy keeps for the
+    # backward; a second rollout of the same length in between overwrites that tape, so the first
+    # rollout's backward must recompute its last segment: every gradient equals the one its
+    # rollout gets alone
+    import torch
+    from paper_1808_02638_gb300.adjoint import rollout
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = 32
+    run = inputs.Run(*inputs.PULSE_DOMAIN)
+    run.levels = inputs.amr_levels(run, n, 4, [(0.2, 0.45)], [31])
+    r2 = inputs.smooth_field(27, n, n, 0.5, 2.0, sigma=3.0)
+    k2 = inputs.smooth_field(28, n, n, 1.0, 8.0, sigma=3.0)
+    qa = [inputs.init_q(run, lev) for lev in run.levels]
+    qb = [0.5 * a for a in qa]
+    rho = [inputs.coef_pool(lev, r2, 4 ** L) for L, lev in enumerate(run.levels)]
+    K = [inputs.coef_pool(lev, k2, 4 ** L) for L, lev in enumerate(run.levels)]
+    H = Hierarchy([run], [qa], [rho], [K])
+
+    def start(q):
+        tq, tr, tk = _tensors(H, [q], "q"), _tensors(H, [rho], "c"), _tensors(H, [K], "c")
+        outs = rollout(H, tq, tr, tk, ncoarse=5, every=2)
+        return tq + tr + tk, _receiver_J(H, outs, run.levels[0], (18, 10, 6))
+
+    def grads(ts):
+        torch.cuda.synchronize()
+        return [t.grad.clone() for t in ts]
+
+    alone = []
+    for q in (qa, qb):
+        ts, J = start(q)
+        J.backward()
+        alone.append(grads(ts))
+    ta, Ja = start(qa)
+    tb, Jb = start(qb)   # overwrites the tape of a's last segment
+    Jb.backward()
+    Ja.backward()
+    for got, want in ((grads(ta), alone[0]), (grads(tb), alone[1])):
+        for a, b in zip(got, want):
+            assert float((a - b).abs().max()) <= 1e-12 * max(float(b.abs().max()), 1e-300)
+    assert H.sync_status() == 0
+
+
 @pytest.mark.parametrize("tiling", [(32, 32, 1, 256), (32, 32, 0, 512), (32, 16, 1, 256), (32, 16, 2, 256),
                                     (16, 16, 1, 128)])
 def test_recorded_adjoint_matches_oracle_for_every_tiling(tiling):
