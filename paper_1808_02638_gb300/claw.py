@@ -51,7 +51,7 @@ DBL = ctypes.c_double
 _SIGNATURES = {
     "claw_create": ([ctypes.POINTER(VP), ctypes.POINTER(claw_problem), I32, I32], ctypes.c_int),
     "claw_destroy": ([VP], None),
-    "claw_set_level": ([VP, I32, ctypes.POINTER(claw_box), I32], ctypes.c_int),
+    "claw_set_level": ([VP, I32, VP, I32], ctypes.c_int),
     "claw_set_tiling": ([VP, I32, I32, I32, I32, I32], ctypes.c_int),
     "claw_set_tile_walk": ([VP, I32, I32], ctypes.c_int),
     "claw_limiter_eval": ([I32, ctypes.c_int64, VP, VP, VP, VP], ctypes.c_int),
@@ -154,9 +154,34 @@ def claw_destroy(ctx):
     load().claw_destroy(ctx)
 
 
-def claw_set_level(ctx, level: int, boxes):
+def box_array(n):
+    """a numpy record array of n boxes laid out like claw_box (fields run, ilo, jlo, nx, ny,
+    reserved, qoff, coff), which the box-taking calls pass without conversion"""
+    import numpy as np
+    return np.zeros(n, dtype=BOX_DTYPE()).view(np.recarray)
+
+
+def BOX_DTYPE():
+    import numpy as np
+    dt = np.dtype([("run", "<i4"), ("ilo", "<i4"), ("jlo", "<i4"), ("nx", "<i4"), ("ny", "<i4"),
+                   ("reserved", "<i4"), ("qoff", "<i8"), ("coff", "<i8")], align=True)
+    assert dt.itemsize == ctypes.sizeof(claw_box)
+    return dt
+
+
+def _boxes_arg(boxes):
+    """(keep-alive object, pointer, count) of a list of claw_box or a box_array"""
+    import numpy as np
+    if isinstance(boxes, np.ndarray) and boxes.dtype == BOX_DTYPE():
+        a = np.ascontiguousarray(boxes)
+        return a, ctypes.c_void_p(a.ctypes.data if len(a) else 0), len(a)
     arr = (claw_box * max(1, len(boxes)))(*boxes)
-    _check("claw_set_level", load().claw_set_level(ctx, level, arr, len(boxes)))
+    return arr, ctypes.cast(arr, ctypes.c_void_p), len(boxes)
+
+
+def claw_set_level(ctx, level: int, boxes):
+    keep, ptr, n = _boxes_arg(boxes)
+    _check("claw_set_level", load().claw_set_level(ctx, level, ptr, n))
 
 
 def claw_set_tiling(ctx, level: int, tx: int, ty: int, staging: int, threads: int = 0):
@@ -229,9 +254,8 @@ def claw_cluster_flags(nx, ny, ratio, cover, flags_host, buffer, nest, cutoff, m
 
 
 def claw_regrid_transfer(ctx, level, old_boxes, q_old, q_new, q_coarse, stream=None):
-    arr = (claw_box * max(1, len(old_boxes)))(*old_boxes)
-    _check("claw_regrid_transfer", load().claw_regrid_transfer(ctx, level, ctypes.cast(arr, ctypes.c_void_p),
-                                                               len(old_boxes), _ptr(q_old), _ptr(q_new),
+    keep, ptr, n = _boxes_arg(old_boxes)
+    _check("claw_regrid_transfer", load().claw_regrid_transfer(ctx, level, ptr, n, _ptr(q_old), _ptr(q_new),
                                                                _ptr(q_coarse), _stream(stream)))
 
 

@@ -104,13 +104,12 @@ class Run:
 
 def layout(boxes: np.ndarray, ncomp: int, align: int = ALIGN):
     """Element offsets of each box's first plane in a pool of `ncomp` planes per box."""
-    offs = np.zeros(len(boxes), dtype=np.int64)
-    o = 0
-    for n, (_, _, nx, ny) in enumerate(np.asarray(boxes).reshape(-1, 4)):
-        offs[n] = o
-        o += ncomp * (int(nx) + 2 * MBC) * (int(ny) + 2 * MBC)
-        o = (o + align - 1) // align * align
-    return offs, int(max(o, align))
+    b = np.asarray(boxes, dtype=np.int64).reshape(-1, 4)
+    sizes = ncomp * (b[:, 2] + 2 * MBC) * (b[:, 3] + 2 * MBC)
+    sizes = (sizes + align - 1) // align * align   # every box starts on an aligned offset
+    ends = np.cumsum(sizes)
+    offs = (ends - sizes).astype(np.int64)
+    return offs, int(max(int(ends[-1]) if len(ends) else 0, align))
 
 
 def box_view(pool: np.ndarray, off: int, nx: int, ny: int, ncomp: int) -> np.ndarray:

@@ -174,23 +174,24 @@ class Hierarchy:
         return tuple(t)
 
     def _layout(self, L):
-        """(claw boxes, [(run, q base, coefficient base)], q size, coefficient size) of level L"""
-        boxes, qb, cb = [], 0, 0
+        """(claw boxes as a claw.box_array, [(run, q base, coefficient base)], q size, coefficient
+        size) of level L"""
+        parts, qb, cb = [], 0, 0
         lay = []
         for ri, r in enumerate(self.runs):
             if L >= len(r.levels):
                 continue
             lev = r.levels[L]
             lay.append((ri, qb, cb))
-            for n, b in enumerate(lev.boxes):
-                bx = claw.claw_box()
-                bx.run = ri
-                bx.ilo, bx.jlo, bx.nx, bx.ny = (int(v) for v in b)
-                bx.qoff = qb + int(lev.qoff[n])
-                bx.coff = cb + int(lev.coff[n])
-                boxes.append(bx)
+            a = claw.box_array(len(lev.boxes))
+            a.run = ri
+            a.ilo, a.jlo, a.nx, a.ny = lev.boxes[:, 0], lev.boxes[:, 1], lev.boxes[:, 2], lev.boxes[:, 3]
+            a.qoff = qb + lev.qoff
+            a.coff = cb + lev.coff
+            parts.append(a)
             qb += _align(lev.qsize)
             cb += _align(lev.csize)
+        boxes = np.concatenate(parts).view(np.recarray) if parts else claw.box_array(0)
         return boxes, lay, qb, cb
 
     # -------------------------------------------------------------- regridding (Sec. 2.2)
