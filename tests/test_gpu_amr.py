@@ -8,7 +8,7 @@ import torch
 from paper_1808_02638_gb300 import inputs
 
 from gpu_amr_helpers import composite
-from gpu_helpers import lib_ready, rel_err
+from gpu_helpers import M, lib_ready, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL1, TOLN = 1e-12, 1e-10
@@ -391,6 +391,73 @@ def test_regrid_end_to_end_matches_the_oracle():
                 assert np.array_equal(run_g.levels[L].boxes, run_o.levels[L].boxes)
             _compare_all_levels(H, O, 0, TOLN)
     _compare_all_levels(H, O, 0, TOLN)
+    assert H.sync_status() == 0
+
+
+def test_regrid_transfer_on_the_device_equals_copy_and_interpolation():
+    # the device transfer (index grids painted with the old and the coarse boxes, a gather per
+    # new cell) against its definition evaluated on the host: every interior cell of a new box is
+    # the old box's value where one covered it, else the minmod-limited linear interpolation from
+    # the coarse cell's parent (ghosts filled); old boxes outside their level are rejected
+    import torch
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    H.init_dt()
+    H.coarse_step()
+    qc = H.q[0][H.cur[0]]
+    claw.claw_fill_ghost(H.ctx, 0, qc)
+    qc_h = qc.cpu().numpy()
+    old_boxes, old_pool = H.boxes[1].copy(), H.q[1][H.cur[1]]
+    old_h = old_pool.cpu().numpy()
+    lev1 = run.levels[1]
+    r = lev1.ratio
+    # the new level 1: every old box shifted by one coarse cell (partly over old data, partly not)
+    shifted = np.array([(int(b[0]) + r, int(b[1]) + r, int(b[2]), int(b[3])) for b in lev1.boxes], dtype=np.int32)
+    run.levels[1] = inputs.Level(lev1.NX, lev1.NY, lev1.dx, lev1.dy, shifted, r)
+    boxes, _, qb, _ = H._layout(1)
+    claw.claw_set_level(H.ctx, 1, boxes)
+    new = torch.zeros(max(qb, inputs.ALIGN), dtype=torch.float64, device=qc.device)
+    claw.claw_regrid_transfer(H.ctx, 1, old_boxes, old_pool, new, qc)
+    torch.cuda.synchronize()
+    got = new.cpu().numpy()
+    owner = np.full((lev1.NY, lev1.NX), -1)
+    for n, o in enumerate(old_boxes):
+        owner[o.jlo:o.jlo + o.ny, o.ilo:o.ilo + o.nx] = n
+    (cb,) = H.boxes[0]   # one coarse box covers level 0
+    cv = inputs.box_view(qc_h, int(cb.qoff), int(cb.nx), int(cb.ny), 3)
+
+    def minmod(a, b):
+        return np.where(a * b > 0, np.where(np.abs(a) < np.abs(b), a, b), 0.0)
+
+    ncopied = 0
+    for b in boxes:
+        nx, ny = int(b.nx), int(b.ny)
+        g = inputs.box_view(got, int(b.qoff), nx, ny, 3)[:, M:-M, M:-M]
+        gj, gi = np.meshgrid(np.arange(b.jlo, b.jlo + ny), np.arange(b.ilo, b.ilo + nx), indexing="ij")
+        I, J = gi // r, gj // r
+        ci, cj = I - int(cb.ilo) + M, J - int(cb.jlo) + M
+        q = cv[:, cj, ci]
+        sx = minmod(cv[:, cj, ci + 1] - q, q - cv[:, cj, ci - 1])
+        sy = minmod(cv[:, cj + 1, ci] - q, q - cv[:, cj - 1, ci])
+        xi = ((gi - I * r) + 0.5) / r - 0.5
+        eta = ((gj - J * r) + 0.5) / r - 0.5
+        want = q + xi * sx + eta * sy
+        own = owner[gj, gi]
+        for o in np.unique(own[own >= 0]):
+            O = old_boxes[o]
+            ov = inputs.box_view(old_h, int(O.qoff), int(O.nx), int(O.ny), 3)
+            m = own == o
+            want[:, m] = ov[:, gj[m] - O.jlo + M, gi[m] - O.ilo + M]
+            ncopied += int(m.sum())
+        assert np.allclose(g, want, rtol=1e-15, atol=1e-15)
+    assert ncopied > 0 and ncopied < sum(int(b.nx) * int(b.ny) for b in boxes)
+    bad = claw.box_array(1)
+    bad.ilo, bad.jlo, bad.nx, bad.ny = lev1.NX - 4, 0, 8, 8   # sticks out of the level
+    with pytest.raises(claw.ClawError):
+        claw.claw_regrid_transfer(H.ctx, 1, bad, old_pool, new, qc)
     assert H.sync_status() == 0
 
 
