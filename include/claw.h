@@ -138,13 +138,14 @@ int claw_set_tiling(claw_ctx* ctx, int32_t level, int32_t tx, int32_t ty, int32_
 
 /* Chooses how the persistent CTAs of a level's fused step share its tiles (Sec. 3.1.3 merges a
  * level's patch kernels into one launch; this is the order inside it).  walk = 0: each CTA
- * strides over the tiles, largest first.  walk = 1 (acoustics in a uniform medium only): the
+ * strides over the tiles, largest first.  walk = 1 (acoustics in a uniform medium, shallow water): the
  * tiles form columns, each box's tile columns continued into the same-level box directly above
  * when it has the same run, ilo and nx; every CTA takes one contiguous stretch of about equal
  * cost, and a tile that follows the tile below it in its CTA's stretch takes the edge values of
  * the rows they share from that tile instead of recomputing them.  Both give the same q_new, dt
  * and smax bit for bit.  walk = -1 (claw_set_level installs it): 1 for uniform-medium levels
- * with at least 8 tiles per SM, else 0.  Other kinds accept 0 and -1 (which means 0).  A
+ * with at least 8 tiles per SM, else 0 (shallow water measured faster striding).  A cell-wise
+ * medium accepts 0 and -1 (which means 0).  A
  * change rewrites the level's tile lists like claw_set_tiling.
  * Errors: CLAW_EINVAL, CLAW_ENOMEM, CLAW_ECUDA. */
 int claw_set_tile_walk(claw_ctx* ctx, int32_t level, int32_t walk);

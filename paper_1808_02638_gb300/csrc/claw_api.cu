@@ -17,7 +17,7 @@ StepArgs make_args(claw_ctx* ctx, int L, const double* q_old, double* q_new, con
     a.tiles = d.tiles;
     a.tmaps = nullptr;
     a.ntiles = d.ntiles;
-    a.tcum = d.tcum;   // set for uniform-medium levels only
+    a.tcum = d.tcum;   // set for walking levels only (not a cell-wise medium)
     a.qold = q_old;
     a.qnew = q_new;
     a.aux = aux;
@@ -336,7 +336,7 @@ int claw_set_tiling(claw_ctx* ctx, int32_t L, int32_t tx, int32_t ty, int32_t st
 
 int claw_set_tile_walk(claw_ctx* ctx, int32_t L, int32_t walk)
 {
-    if (!valid_level(ctx, L) || walk < -1 || walk > 1 || (walk > 0 && ctx->kind() != KIND_UNIFORM)) return CLAW_EINVAL;
+    if (!valid_level(ctx, L) || walk < -1 || walk > 1 || (walk > 0 && ctx->kind() == KIND_CELLWISE)) return CLAW_EINVAL;
     DevGuard g(ctx->device);
     LevelDev& d = ctx->lev[L];
     if (d.walk == walk) return CLAW_OK;

@@ -65,7 +65,7 @@ struct PatchDev {
 };
 
 // One tile of the fused step: interior cells [x0, x0+tx) x [y0, y0+ty) of box `patch`.
-// TILE_CARRY (column-walk tile lists, uniform medium only): the previous tile of the list is the
+// TILE_CARRY (column-walk tile lists; not a cell-wise medium): the previous tile of the list is the
 // tile directly below this one, with the same columns: in the same box, or in the same-level box
 // whose top side this box's bottom side covers exactly.
 enum : int { TILE_CARRY = 1 };

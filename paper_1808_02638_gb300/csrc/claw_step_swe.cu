@@ -51,7 +51,16 @@ template <int TX, int TY> struct SweGeo {
     static constexpr int DER = 3 * Q::QPL;       // P0 planes; reused for the x-edge h_p in PB
     static_assert(3 * XL <= DER, "limited x-edge parts fit over the derived planes");
     static constexpr int NWORK = DER + NE * (XE + YE) + 3 * YL + 6 * (DC + EC);
-    static size_t smem_bytes(int nbuf) { return (size_t)(nbuf * Q::QSTRIDE + NWORK) * 8 + 64; }
+    // rows a tile hands to the tile above it in a column walk: x-edge Roe states and strengths
+    // 2 rows, y-edge ones 3, limited x-edge parts 2, limited y-edge parts 1, the transverse parts
+    // of D one row
+    static constexpr int C_XE = 0, C_YE = NE * 2 * Q::XEW, C_XH = C_YE + NE * 3 * Q::YEW,
+                         C_YH = C_XH + 3 * 2 * Q::XLW, C_D = C_YH + 3 * Q::YLW, NCARRY = C_D + 6 * Q::DW;
+    // q buffers, work arrays, 64 bytes of barriers, then (column walks only) the carried rows
+    static size_t smem_bytes(int nbuf, bool walk = false)
+    {
+        return (size_t)(nbuf * Q::QSTRIDE + NWORK) * 8 + 64 + (walk ? (size_t)NCARRY * 8 : 0);
+    }
 };
 
 namespace swe {
@@ -111,9 +120,11 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
     double* Em = Dp + 3 * S::DC;              // y-fluctuation transverse parts: 3 planes of S::EC
     double* Ep = Em + 3 * S::EC;
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ep + 3 * S::EC);
+    double* Cy = reinterpret_cast<double*>(bar) + 8;   // carried rows (walking launches only)
     double* XH = der;                         // h_p of the limited x-edges (after PA)
     __shared__ unsigned long long s_tmax[2];
     __shared__ int s_flag;
+    __shared__ int s_range[2];
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -124,8 +135,20 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
             mbar_init(&bar[1], 1);
             fence_barrier_init();
         }
+        if (A.tcum) {
+            s_range[0] = walk_start(A.tcum, A.ntiles, blockIdx.x, gridDim.x);
+            s_range[1] = walk_start(A.tcum, A.ntiles, blockIdx.x + 1, gridDim.x);
+        } else {
+            s_range[0] = blockIdx.x;
+            s_range[1] = A.ntiles;
+        }
     }
     __syncthreads();
+    // column walks as in the acoustics kernel: a contiguous stretch of tiles per CTA, the rows a
+    // tile shares with the tile below it taken from that tile (through Cy) instead of recomputed
+    const int t_begin = s_range[0], t_end = s_range[1];
+    const int t_step = A.tcum ? 1 : (int)gridDim.x;
+    const bool walk = A.tcum != nullptr;
 
     const CUtensorMap* tmaps = reinterpret_cast<const CUtensorMap*>(A.tmaps);
     int my_flag = 0;
@@ -147,12 +170,18 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
         mbar_expect_tx(&bar[b], (unsigned)G::QBYTES);
         tma_load_3d(qbuf + b * G::QSTRIDE, &tmaps[T.patch], T.x0, T.y0, 0, &bar[b]);
     };
-    if (STAGE && tid == 0 && blockIdx.x < A.ntiles) issue(blockIdx.x, 0);
+    if (STAGE && tid == 0 && t_begin < t_end) issue(t_begin, 0);
 
     int it = 0;
-    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++it) {
+    for (int t = t_begin; t < t_end; t += t_step, ++it) {
         const int b = STAGE ? (it & 1) : 0;
         const TileDev T = A.tiles[t];
+        const bool carry = walk && t > t_begin && (T.flags & TILE_CARRY);
+        const bool hand = walk && t + 1 < t_end && (A.tiles[t + 1].flags & TILE_CARRY);
+        // first rows computed: with a carry, the rows below come from the previous tile
+        const int rx0 = carry ? 1 : -1;   // x-edges and limited x-edges: rows [rx0, ty]
+        const int by0 = carry ? 2 : -1;   // y-edges: b in [by0, ty + 1]
+        const int ly0 = carry ? 1 : 0;    // limited y-edges: b in [ly0, ty]
         const PatchDev P = A.patches[T.patch];
         const int tx = T.tx, ty = T.ty, x0 = T.x0, y0 = T.y0;
         const int W = P.nx + 4;
@@ -163,15 +192,15 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
         const double* sv = sq + 2 * G::QPL;
 
         if (STAGE) {
-            const int tn = t + gridDim.x;
-            if (tid == 0 && tn < A.ntiles) issue(tn, b ^ 1);
+            const int tn = t + t_step;
+            if (tid == 0 && tn < t_end) issue(tn, b ^ 1);
             const unsigned par = (unsigned)((it >> 1) & 1);
             bool ok = mbar_wait_bounded(&bar[b], par, A.wait_polls);
             if (__syncthreads_or(!ok)) {   // late or lost copy: report, drain what is in flight, stop
                 if (tid == 0) {
                     atomicOr(A.err, ERR_TIMEOUT);
                     mbar_wait_bounded(&bar[b], par);
-                    if (tn < A.ntiles) mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+                    if (tn < t_end) mbar_wait_bounded(&bar[b ^ 1], (unsigned)(((it + 1) >> 1) & 1));
                     finish_cta(A);
                 }
                 return;
@@ -195,10 +224,34 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
         const double lx = dt * P.dxinv, ly = dt * P.dyinv;
 
         // ------------------------------------------------------------ P0: per staged cell
+        // (with a carry only the staged rows from 3 on, tile rows 1.., feed this tile's edges)
+        // The carried edge rows land in the lowest rows of XE, YE, YH and D, which this tile
+        // writes no earlier than PA; the previous tile's last reads of them were behind its
+        // end-of-tile barrier.  (XH shares memory with der and is restored after PA.)
+        if (carry) {
+            for (int k = tid; k < S::C_XH; k += NT) {
+                if (k < S::C_YE) {
+                    const int q = k / (2 * G::XEW), o = k - q * 2 * G::XEW;
+                    XE[q * S::XE + o] = Cy[k];
+                } else {
+                    const int kk = k - S::C_YE, q = kk / (3 * G::YEW), o = kk - q * 3 * G::YEW;
+                    YE[q * S::YE + o] = Cy[k];
+                }
+            }
+            for (int k = tid; k < S::NCARRY - S::C_YH; k += NT) {
+                if (k < 3 * G::YLW) {
+                    const int q = k / G::YLW;
+                    YH[q * S::YL + (k - q * G::YLW)] = Cy[S::C_YH + k];
+                } else {
+                    const int kk = k - 3 * G::YLW, q = kk / G::DW, o = kk - q * G::DW;
+                    (q < 3 ? Dm + q * S::DC : Dp + (q - 3) * S::DC)[o] = Cy[S::C_D + kk];
+                }
+            }
+        }
         {
-            const int w = tx + 4, n = (ty + 4) * w;
+            const int w = tx + 4, j0 = carry ? 3 : 0, n = (ty + 4 - j0) * w;
             for (int k = tid; k < n; k += NT) {
-                const int jj = k / w, ii = k - jj * w;
+                const int jj = k / w + j0, ii = k - (jj - j0) * w;
                 const int i = ii + jj * G::SW;
                 const double h = sh[i];
                 const bool corner = (ii == 0 || ii == w - 1) && (jj == 0 || jj == ty + 3);
@@ -214,9 +267,9 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
         // ------------------------------------------------------------ PA: Roe solves
         unsigned long long m = 0ull;
         {   // x-edge a (cells a-1 | a) on rows r in [-1, ty]
-            const int w = tx + 3, n = (ty + 2) * w;
+            const int w = tx + 3, n = (ty + 1 - rx0) * w;
             for (int k = tid; k < n; k += NT) {
-                const int r = k / w - 1, a = k - (r + 1) * w - 1;
+                const int r = k / w + rx0, a = k - (r - rx0) * w - 1;
                 const int iR = (a + 2) + (r + 2) * G::SW, iL = iR - 1;
                 const double inv = 1.0 / (der[iL] + der[iR]);
                 const double un = (der[G::QPL + iL] + der[G::QPL + iR]) * inv;
@@ -240,9 +293,9 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
             }
         }
         {   // y-edge b (rows b-1 | b) on columns c in [-1, tx]; normal momentum hv
-            const int w = tx + 2, n = (ty + 3) * w;
+            const int w = tx + 2, n = (ty + 2 - by0) * w;
             for (int k = tid; k < n; k += NT) {
-                const int bb = k / w - 1, cc = k - (bb + 1) * w - 1;
+                const int bb = k / w + by0, cc = k - (bb - by0) * w - 1;
                 const int iR = (cc + 2) + (bb + 2) * G::SW, iL = iR - G::SW;
                 const double inv = 1.0 / (der[iL] + der[iR]);
                 const double un = (der[2 * G::QPL + iL] + der[2 * G::QPL + iR]) * inv;
@@ -303,18 +356,23 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
             out[2 * ol + o] = fma(hl * k3, k3, 0.5 * k3) * mu3;
         };
         if (second) {
+            if (carry)   // the carried limited x-edge rows, now that PA has read der
+                for (int k = tid; k < S::C_YH - S::C_XH; k += NT) {
+                    const int q = k / (2 * G::XLW), o = k - q * 2 * G::XLW;
+                    XH[q * S::XL + o] = Cy[S::C_XH + k];
+                }
             {
-                const int w = tx + 1, n = (ty + 2) * w;
+                const int w = tx + 1, n = (ty + 1 - rx0) * w;
                 for (int k = tid; k < n; k += NT) {
-                    const int r = k / w - 1, a = k - (r + 1) * w;
+                    const int r = k / w + rx0, a = k - (r - rx0) * w;
                     const int e = (r + 1) * G::XEW + (a + 1);
                     limited(XE, S::XE, e, e - 1, e + 1, lx, XH, (r + 1) * G::XLW + a, S::XL);
                 }
             }
             {
-                const int w = tx + 2, n = (ty + 1) * w;
+                const int w = tx + 2, n = (ty + 1 - ly0) * w;
                 for (int k = tid; k < n; k += NT) {
-                    const int bb = k / w, cc = k - bb * w - 1;
+                    const int bb = k / w + ly0, cc = k - (bb - ly0) * w - 1;
                     const int e = (bb + 1) * G::YEW + (cc + 1);
                     limited(YE, S::YE, e, e - G::YEW, e + G::YEW, ly, YH, bb * G::YLW + (cc + 1), S::YL);
                 }
@@ -410,7 +468,7 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
         }
         if (trans) {   // transverse parts of the ghost rows -1, ty (x) and ghost columns -1, tx (y)
             const int n = 2 * (tx + ty);
-            for (int k = tid; k < n; k += NT) {
+            for (int k = tid + (carry ? tx : 0); k < n; k += NT) {   // row -1 is carried
                 if (k < 2 * tx) xcell(k % tx, k < tx ? -1 : ty, nullptr);
                 else {
                     const int kk = k - 2 * tx;
@@ -418,9 +476,35 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
                 }
             }
         }
+        // hand the top rows of the edge arrays to the next tile (all final by now)
+        if (hand) {
+            for (int k = tid; k < S::C_D; k += NT) {
+                double v;
+                if (k < S::C_YE) {
+                    const int q = k / (2 * G::XEW), o = k - q * 2 * G::XEW;
+                    v = XE[q * S::XE + ty * G::XEW + o];
+                } else if (k < S::C_XH) {
+                    const int kk = k - S::C_YE, q = kk / (3 * G::YEW), o = kk - q * 3 * G::YEW;
+                    v = YE[q * S::YE + ty * G::YEW + o];
+                } else if (k < S::C_YH) {
+                    const int kk = k - S::C_XH, q = kk / (2 * G::XLW), o = kk - q * 2 * G::XLW;
+                    v = XH[q * S::XL + ty * G::XLW + o];
+                } else {
+                    const int kk = k - S::C_YH, q = kk / G::YLW, o = kk - q * G::YLW;
+                    v = YH[q * S::YL + ty * G::YLW + o];
+                }
+                Cy[k] = v;
+            }
+        }
         __syncthreads();
 
         // ------------------------------------------------------------ PD: update, store
+        // D of row ty - 1 becomes the next tile's row -1 (final since the barrier ending PC)
+        if (hand)
+            for (int k = tid; k < 6 * G::DW; k += NT) {
+                const int q = k / G::DW, o = k - q * G::DW;
+                Cy[S::C_D + k] = (q < 3 ? Dm + q * S::DC : Dp + (q - 3) * S::DC)[ty * G::DW + o];
+            }
         const double kT = 0.5 * lx * ly;
         double* dst = A.qnew + P.qoff;
 #pragma unroll
@@ -476,7 +560,7 @@ static StepKernel swe_entry()
     StepKernel k;
     k.fn = swe_step_kernel<LIM, TX, TY, NT, STAGE, PULL>;
     k.smem = SweGeo<TX, TY>::smem_bytes(STAGE ? 2 : 1);
-    k.smem_walk = k.smem;
+    k.smem_walk = SweGeo<TX, TY>::smem_bytes(STAGE ? 2 : 1, true);
     k.nt = NT;
     return k;
 }

@@ -56,17 +56,17 @@ void free_level(claw_ctx* ctx, int L)
     ctx->set[L] = false;
 }
 
-// The step's tiles as column walks (uniform medium): every column of tiles of a box bottom to
-// top, continued into the column of the same-level box directly above when that box has the
-// same run, ilo and nx (the columns then coincide); every tile but the first of such a chain is
-// flagged TILE_CARRY.  Crossing needs the shared rows to be the same in both boxes, which the
-// ghost states are: they come from the box below, or from the same boundary image or coarse
-// interpolation.  (A cell-wise medium's ghost coefficients are the caller's and need not match,
-// one reason walks are built for the uniform medium only; the other is that the cell-wise
-// kernels keep their registers without the carrying code.)  cum[i] is the cost of tiles
-// [0, i): the cells of the tile and of the halo rows and columns it computes edges on, plus a
-// fixed per-tile share.
-static void column_walks(const LevelDev& d, std::vector<TileDev>& out, std::vector<long long>& cum)
+// The step's tiles as column walks (uniform medium, shallow water): every column of tiles of a
+// box bottom to top, continued into the column of the same-level box directly above when that
+// box has the same run, ilo and nx (the columns then coincide), cut into pieces of `piece`
+// tiles; every tile but the first of a piece is flagged TILE_CARRY.  Crossing into the box above
+// needs the shared rows to be the same in both boxes, which the ghost states are: they come from
+// the box below, or from the same boundary image or coarse interpolation.  (A cell-wise
+// medium's ghost coefficients are the caller's and need not match, one reason walks are not
+// built for it; the other is that the cell-wise kernels keep their registers without the
+// carrying code.)  cum[i] is the cost of tiles [0, i): the cells of the tile and of the halo
+// rows and columns it computes edges on, plus a fixed per-tile share.
+static void column_walks(const LevelDev& d, int piece, std::vector<TileDev>& out, std::vector<long long>& cum)
 {
     const int nb = d.nboxes;
     std::map<std::array<int, 4>, int> by_base;   // (run, ilo, nx, jlo) -> box
@@ -83,13 +83,15 @@ static void column_walks(const LevelDev& d, std::vector<TileDev>& out, std::vect
             has_below[it->second] = 1;
         }
     }
-    out.clear();
-    cum.assign(1, 0);
+    // every column chain, then cut into pieces of `piece` tiles; the pieces are laid out band by
+    // band (the first piece of every chain, then the second, ...), so that the CTAs that run at
+    // the same time work side by side and share their ghost columns in L2
+    std::vector<std::vector<TileDev>> chains;
     for (int n0 = 0; n0 < nb; ++n0) {
         if (has_below[n0]) continue;   // chains start at boxes with nothing aligned below
         const claw_box& b0 = d.boxes[n0];
         for (int x = 0; x < b0.nx; x += d.tx) {
-            bool first = true;
+            std::vector<TileDev> ch;
             for (int n = n0; n >= 0; n = above[n]) {
                 const claw_box& b = d.boxes[n];
                 for (int y = 0; y < b.ny; y += d.ty) {
@@ -99,14 +101,29 @@ static void column_walks(const LevelDev& d, std::vector<TileDev>& out, std::vect
                     T.y0 = (short)y;
                     T.tx = (short)std::min(d.tx, b.nx - x);
                     T.ty = (short)std::min(d.ty, b.ny - y);
-                    T.flags = first ? 0 : TILE_CARRY;
-                    first = false;
-                    out.push_back(T);
-                    const long long c = (long long)(T.tx + 3) * (T.ty + (T.flags ? 0 : 3)) + 64;
-                    cum.push_back(cum.back() + c);
+                    T.flags = ch.size() % piece ? TILE_CARRY : 0;
+                    ch.push_back(T);
                 }
             }
+            chains.push_back(std::move(ch));
         }
+    }
+    out.clear();
+    cum.assign(1, 0);
+    for (size_t band = 0;; ++band) {
+        bool any = false;
+        for (const auto& ch : chains) {
+            const size_t k0 = band * piece;
+            if (k0 >= ch.size()) continue;
+            any = true;
+            for (size_t k = k0; k < std::min(ch.size(), k0 + piece); ++k) {
+                const TileDev& T = ch[k];
+                out.push_back(T);
+                const long long c = (long long)(T.tx + 3) * (T.ty + (T.flags ? 0 : 3)) + 64;
+                cum.push_back(cum.back() + c);
+            }
+        }
+        if (!any) break;
     }
 }
 
@@ -142,10 +159,17 @@ int build_tiles(claw_ctx* ctx, int L)
     pack.add(&ctx->ptiles[L], t);
     ctx->ptile_start[L] = start;
     d.htcum.clear();
-    d.walking = ctx->kind() == KIND_UNIFORM &&
-                (d.walk > 0 || (d.walk < 0 && (long long)t.size() >= (long long)kWalkTilesPerSM * std::max(ctx->nsm, 1)));
+    // automatic: uniform-medium acoustics only (the shallow-water step issues 6 % fewer FP64
+    // instructions with walks but ran 1.5 % slower on the 2048^2 workload, with two CTAs per SM)
+    d.walking = ctx->kind() != KIND_CELLWISE &&
+                (d.walk > 0 || (d.walk < 0 && ctx->kind() == KIND_UNIFORM &&
+                                (long long)t.size() >= (long long)kWalkTilesPerSM * std::max(ctx->nsm, 1)));
     if (d.walking) {
-        column_walks(d, d.htiles, d.htcum);
+        // pieces of about the tiles one CTA takes (three CTAs per SM, a guess: the launch picks
+        // its grid later), at least 4 and at most 64
+        const int piece = (int)std::min<long long>(64, std::max<long long>(4, ((long long)t.size() + 3LL * ctx->nsm - 1) /
+                                                                                 std::max(1, 3 * ctx->nsm)));
+        column_walks(d, piece, d.htiles, d.htcum);
     } else {
         d.htiles = t;
         std::stable_sort(d.htiles.begin(), d.htiles.end(), [](const TileDev& a, const TileDev& b) {

@@ -163,7 +163,7 @@ def main():
     elif medium == "swe":
         run = inputs.config1()
         H = Hierarchy([run], [[inputs.init_swe(run, run.levels[0])]], tiling=tiling, system="shallow_water",
-                      grav=1.0)
+                      grav=1.0, walk=walk)
     else:
         run, r2, k2 = inputs.config3(n)
         run.levels = [inputs.Level(n, n, 2.0 / n, 2.0 / n, inputs.uniform_tiling(n, n, 32, 32))]

@@ -3,7 +3,8 @@ stretches of tile columns and hand the edge values of shared rows from each tile
 give the same new states, dt and speed maxima, bit for bit, as CTAs striding over the tiles, on
 every tiling, with filled, pulled and step-interpolated ghosts, wall and periodic boundaries,
 ragged tiles, box stacks that do and do not line up, and runs batched into one launch whose boxes
-sit at the same indices (uniform medium: the only kind that walks)."""
+sit at the same indices; acoustics in a uniform medium and shallow water (a cell-wise medium does
+not walk)."""
 import numpy as np
 import pytest
 import torch
@@ -63,6 +64,43 @@ def test_single_level_walk_equals_stride_uniform_medium(tiling, bc):
         for _ in range(3):
             h.coarse_step()
     _same(A, B)
+
+
+SWE_TILINGS = [(16, 16, 1, 256), (16, 16, 0, 256), (32, 16, 1, 512), (32, 16, 0, 512)]
+
+
+@pytest.mark.parametrize("tiling", SWE_TILINGS)
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 2, 2)])
+def test_shallow_water_walk_equals_stride(tiling, bc):
+    # the shallow-water step hands over its Roe states, strengths, limited parts and transverse
+    # parts of the shared rows the same way
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run, _ = single_grid(128, bc=bc, boxes=MIXED_BOXES)
+    q = inputs.init_swe(run, run.levels[0], u0=0.2, v0=-0.1)
+    A = Hierarchy([run], [[q]], tiling=tiling, system="shallow_water", grav=1.0, walk=1)
+    B = Hierarchy([run], [[q]], tiling=tiling, system="shallow_water", grav=1.0, walk=0)
+    for h in (A, B):
+        h.init_dt()
+        for _ in range(3):
+            h.coarse_step()
+        h.fused = True
+        for _ in range(3):
+            h.coarse_step()
+    _same(A, B)
+
+
+def test_shallow_water_three_levels_walk_equals_stride():
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q = [inputs.init_swe(run, lev, u0=0.2, v0=0.1) for lev in run.levels]
+    hs = []
+    for walk in (1, 0):
+        H = Hierarchy([run], [q], tiling=(16, 16, 1, 256), system="shallow_water", grav=1.0, walk=walk)
+        H.init_dt()
+        for _ in range(2):
+            H.coarse_step()
+        hs.append(H)
+    _same(*hs)
 
 
 def test_only_uniform_medium_levels_walk():
