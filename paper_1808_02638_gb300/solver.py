@@ -353,7 +353,8 @@ class Hierarchy:
         """the piece plan of level 0 for host-resident stepping (see band_plan)"""
         run0 = self.runs[0]
         lev = run0.levels[0]
-        boxes = [(int(b.ilo), int(b.jlo), int(b.nx), int(b.ny), int(b.qoff)) for b in self.boxes[0]]
+        b = self.boxes[0]
+        boxes = list(zip(b.ilo.tolist(), b.jlo.tolist(), b.nx.tolist(), b.ny.tolist(), b.qoff.tolist()))
         return band_plan(boxes, nbands, lev.NX, lev.NY, run0.bc)
 
     def packed_size(self, L=0):
@@ -388,8 +389,8 @@ class Hierarchy:
             self._band_cache = (bands, self._bands(bands))
         parts, ranges, needs = self._band_cache[1]
         if packed:
-            sizes = [3 * int(b.nx) * int(b.ny) for b in self.boxes[0]]
-            offs = np.concatenate([[0], np.cumsum(sizes)])
+            b = self.boxes[0]
+            offs = np.concatenate([[0], np.cumsum(3 * b.nx.astype(np.int64) * b.ny)])
             ranges = [(int(offs[b0]), int(offs[b1])) for (b0, b1) in parts]
             if getattr(self, "_stage", None) is None or self._stage[0].numel() != host_a.numel():
                 self._stage = (torch.empty(host_a.numel(), dtype=torch.float64, device=self.dev),

@@ -29,7 +29,7 @@ _lock = threading.Lock()
 
 
 def _key(H, L):
-    sizes = sorted((int(b.nx), int(b.ny)) for b in H.boxes[L])
+    sizes = sorted(zip(H.boxes[L].nx.tolist(), H.boxes[L].ny.tolist()))
     hist = {}
     for s in sizes:
         hist[s] = hist.get(s, 0) + 1
