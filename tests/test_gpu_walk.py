@@ -154,6 +154,24 @@ def test_batched_runs_with_the_same_box_indices_walk_equals_stride():
     _same(A, B)
 
 
+@pytest.mark.parametrize("boxes", [[(0, 0, 64, 64)], [(0, 0, 32, 8), (0, 8, 32, 8), (0, 16, 16, 16), (16, 16, 16, 16)]])
+def test_walk_on_a_level_with_fewer_tiles_than_ctas(boxes):
+    # a forced walk on a tiny level: most CTAs get an empty stretch, chains of one or two tiles
+    from paper_1808_02638_gb300.solver import Hierarchy
+    n = max(b[0] + b[2] for b in boxes)
+    run, q = single_grid(n, pulse=False, seed=600, boxes=boxes)
+    _random_velocity(run, q, 600)
+    hs = []
+    for walk in (1, 0):
+        H = Hierarchy([run], [[q]], rho0=1.0, K0=4.0, tiling=(32, 16, 2, 256), walk=walk)
+        H.init_dt()
+        H.fused = True
+        for _ in range(4):
+            H.coarse_step()
+        hs.append(H)
+    _same(*hs)
+
+
 def test_walk_switch_rejects_bad_values():
     from paper_1808_02638_gb300 import claw
     from paper_1808_02638_gb300.solver import Hierarchy
