@@ -264,6 +264,31 @@ int claw_level_advance_interp(claw_ctx* ctx, int32_t level, const double* q_old,
                               const double* aux, double* dt, double* smax, int32_t flags,
                               const double* qc_old, const double* qc_new, double tau, void* stream);
 
+/* One fill of a fine level's ghost cells that come from the coarser level, as
+ * claw_fill_ghost_interp(ctx, level, q, qc_old, qc_new, tau) writes them. */
+typedef struct {
+    int32_t level;          /* the fine level (>= 1) */
+    int32_t reserved;       /* 0 */
+    double* q;              /* that level's pool whose interpolated ghost cells are written */
+    const double* qc_old;   /* level - 1 states at the start and end of its step (device pools) */
+    const double* qc_new;
+    double tau;             /* time fraction in [0, 1] */
+} claw_fill_job;
+
+/* claw_level_advance, and in the same launch the interpolated-ghost fills of `jobs` (0, 1 or 2),
+ * done by extra CTAs beside those that step the tiles (Sec. 2.2: each fine substep needs its
+ * ghosts interpolated from the coarser level at its own time).  A job must concern this level
+ * (its next substep, into q_new's ghost cells, which the step does not write) or the next finer
+ * one (its first substep: tau 0, from this level's q_old as both coarse states).  The result is
+ * that of claw_level_advance followed by claw_fill_ghost_interp for each job, on the same stream.
+ * Shallow water (no fill CTAs in its kernel) launches the fills after the step instead.
+ * Errors as claw_level_advance; CLAW_EINVAL for more than 2 jobs, a job of another level, a
+ * level not set, NULL pools, tau outside [0, 1], a job writing q_old, or a job reading q_new
+ * as a coarse state. */
+int claw_level_advance_fill(claw_ctx* ctx, int32_t level, const double* q_old, double* q_new,
+                            const double* aux, double* dt, double* smax, int32_t flags,
+                            const claw_fill_job* jobs, int32_t njobs, void* stream);
+
 /* claw_level_advance restricted to the boxes [box_begin, box_end) of the level (their tiles, in
  * box order): a level-step taken in pieces, so that host copies of some boxes overlap the steps
  * of others.  The pieces of one step, in any order, give bit for bit the claw_level_advance of

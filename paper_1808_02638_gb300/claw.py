@@ -43,6 +43,11 @@ class claw_box(ctypes.Structure):
                 ("qoff", ctypes.c_int64), ("coff", ctypes.c_int64)]
 
 
+class claw_fill_job(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("reserved", ctypes.c_int32), ("q", ctypes.c_void_p),
+                ("qc_old", ctypes.c_void_p), ("qc_new", ctypes.c_void_p), ("tau", ctypes.c_double)]
+
+
 _lib = None
 VP = ctypes.c_void_p
 I32 = ctypes.c_int32
@@ -82,6 +87,7 @@ _SIGNATURES = {
     "claw_level_advance": ([VP, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
     "claw_level_advance_boxes": ([VP, I32, I32, I32, VP, VP, VP, VP, VP, I32, VP], ctypes.c_int),
     "claw_level_advance_interp": ([VP, I32, VP, VP, VP, VP, VP, I32, VP, VP, DBL, VP], ctypes.c_int),
+    "claw_level_advance_fill": ([VP, I32, VP, VP, VP, VP, VP, I32, VP, I32, VP], ctypes.c_int),
     "claw_packed_size": ([VP, I32], ctypes.c_longlong),
     "claw_pack_interiors": ([VP, I32, I32, I32, VP, VP, VP], ctypes.c_int),
     "claw_unpack_interiors": ([VP, I32, I32, I32, VP, VP, VP], ctypes.c_int),
@@ -380,6 +386,17 @@ def claw_level_advance_interp(ctx, level, q_old, q_new, aux, dt, smax, flags, qc
     _check("claw_level_advance_interp", load().claw_level_advance_interp(
         ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax), int(flags), _ptr(qc_old), _ptr(qc_new),
         DBL(tau), _stream(stream)))
+
+
+def claw_level_advance_fill(ctx, level, q_old, q_new, aux, dt, smax, flags, jobs=(), stream=None):
+    """claw_level_advance plus, in the same launch, the interpolated-ghost fills `jobs`: tuples
+    (fine level, pool, coarse old, coarse new, tau)"""
+    arr = (claw_fill_job * max(len(jobs), 1))()
+    for n, (lev, q, qc_old, qc_new, tau) in enumerate(jobs):
+        arr[n] = claw_fill_job(int(lev), 0, _ptr(q), _ptr(qc_old), _ptr(qc_new), float(tau))
+    _check("claw_level_advance_fill", load().claw_level_advance_fill(
+        ctx, level, _ptr(q_old), _ptr(q_new), _ptr(aux), _ptr(dt), _ptr(smax), int(flags),
+        ctypes.cast(arr, VP), len(jobs), _stream(stream)))
 
 
 def claw_level_step_patchwise(ctx, level, q_old, q_new, aux, dt, smax, stream=None):

@@ -512,10 +512,21 @@ int claw_level_step(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new
 
 static int level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux, double* dt,
                          double* smax, int32_t flags, const double* qc_old, const double* qc_new, double tau,
-                         bool interp, void* stream)
+                         bool interp, void* stream, const claw_fill_job* jobs = nullptr, int njobs = 0)
 {
     int rc = check_step_args(ctx, L, q_old, q_new, aux, dt, smax);
     if (rc) return rc;
+    if (njobs < 0 || njobs > 2 || (njobs > 0 && !jobs)) return CLAW_EINVAL;
+    for (int j = 0; j < njobs; ++j) {
+        // a job fills level L's or level L+1's interpolated ghosts: never those of q_old (which
+        // the step reads), from coarse states the step does not write
+        const claw_fill_job& J = jobs[j];
+        if ((J.level != L && J.level != L + 1) || J.level < 1 || J.level >= CLAW_MAXLEV || !ctx->set[J.level])
+            return CLAW_EINVAL;
+        if (!J.q || !J.qc_old || !J.qc_new || !(J.tau >= 0.0 && J.tau <= 1.0)) return CLAW_EINVAL;
+        if (J.q == q_old || J.qc_old == q_new || J.qc_new == q_new || (J.level != L && J.q == q_new))
+            return CLAW_EINVAL;
+    }
     if (flags & ~(CLAW_ADVANCE_PUSH_GHOSTS | CLAW_ADVANCE_UPDATE_DT | CLAW_ADVANCE_PULL_GHOSTS)) return CLAW_EINVAL;
     if ((flags & CLAW_ADVANCE_PULL_GHOSTS) && !ctx->lev[L].ring_ok) return CLAW_EINVAL;
     LevelDev& d = ctx->lev[L];
@@ -556,8 +567,26 @@ static int level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* 
                                             false, a.interp != nullptr, a.tcum != nullptr);
     if (per_sm <= 0) return CLAW_ECUDA;
     const int grid = std::min(d.ntiles, per_sm * ctx->nsm);
+    for (int j = 0; j < njobs; ++j) {
+        const LevelDev& f = ctx->lev[jobs[j].level];
+        if (f.ninterp == 0) continue;
+        FillJob& F = a.fills[a.nfill++];
+        F.cells = f.interps;
+        F.n = f.ninterp;
+        F.q = jobs[j].q;
+        F.cold = jobs[j].qc_old;
+        F.cnew = jobs[j].qc_new;
+        F.tau = jobs[j].tau;
+    }
     ctx->launches += 1;
-    cudaError_t e = launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s);
+    cudaError_t e = launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s,
+                                per_sm * ctx->nsm - grid);
+    if (ctx->kind() == KIND_SWE)   // no fill CTAs in the shallow-water kernel: a launch per job
+        for (int j = 0; j < a.nfill && e == cudaSuccess; ++j) {
+            e = launch_fill_interp(a.fills[j].cells, a.fills[j].n, a.fills[j].q, a.fills[j].cold, a.fills[j].cnew,
+                                   a.fills[j].tau, s);
+            ctx->launches += 1;
+        }
     if (e == cudaSuccess && (flags & CLAW_ADVANCE_PUSH_GHOSTS) && d.ncopy) {
         e = launch_fill_copy(d.copies, d.copy_start, d.ncopy_blocks, q_new, s);
         ctx->launches += 1;
@@ -576,6 +605,13 @@ int claw_level_advance_interp(claw_ctx* ctx, int32_t L, const double* q_old, dou
                               double tau, void* stream)
 {
     return level_advance(ctx, L, q_old, q_new, aux, dt, smax, flags, qc_old, qc_new, tau, true, stream);
+}
+
+int claw_level_advance_fill(claw_ctx* ctx, int32_t L, const double* q_old, double* q_new, const double* aux,
+                            double* dt, double* smax, int32_t flags, const claw_fill_job* jobs, int32_t njobs,
+                            void* stream)
+{
+    return level_advance(ctx, L, q_old, q_new, aux, dt, smax, flags, nullptr, nullptr, 0.0, false, stream, jobs, njobs);
 }
 
 int claw_level_advance_boxes(claw_ctx* ctx, int32_t L, int32_t box_begin, int32_t box_end, const double* q_old,

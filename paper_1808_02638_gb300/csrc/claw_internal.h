@@ -130,6 +130,17 @@ struct InterpCell {
     int flags;            // wall sign flips of the fine ghost itself
 };
 
+// A fill of a fine level's interpolated ghost cells (cells, n) in pool q from the coarse states
+// cold, cnew at time fraction tau, run by spare CTAs of a level-step launch.
+struct FillJob {
+    const InterpCell* cells = nullptr;
+    int n = 0;
+    double* q = nullptr;
+    const double* cold = nullptr;
+    const double* cnew = nullptr;
+    double tau = 0.0;
+};
+
 // Coarse cells [0,w) x [0,h) at cdst, each the mean of r x r fine cells at fsrc.
 struct AvgRect {
     long long cdst, fsrc;
@@ -251,6 +262,11 @@ struct StepArgs {
     const double* cold = nullptr;
     const double* cnew = nullptr;
     double tau = 0.0;
+    // CTAs [step_grid, gridDim.x) of the launch fill interpolated ghosts (fills[0, nfill)) instead
+    // of stepping tiles; step_grid 0: every CTA steps tiles
+    int step_grid = 0;
+    int nfill = 0;
+    FillJob fills[2];
 };
 
 // error flag bits written by kernels
@@ -260,8 +276,9 @@ enum : int { ERR_NAN = 1, ERR_CFL = 2, ERR_TIMEOUT = 4 };
 enum : int { KIND_UNIFORM = 0, KIND_CELLWISE = 1, KIND_SWE = 2 };
 
 // launchers (claw_step.cu; kind: KIND_*)
+// a.nfill > 0 (not shallow water): the launch adds up to max(spare, 1) CTAs for the fill jobs
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
-                        int grid, cudaStream_t s);
+                        int grid, cudaStream_t s, int spare = 0);
 int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull = false,
                          bool rec = false, bool interp = false, bool walk = false);
 cudaError_t launch_step_adjoint(const StepArgs& a, const double* lam_new, double* lam_old, double* g_aux,

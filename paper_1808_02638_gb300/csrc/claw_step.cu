@@ -65,13 +65,23 @@ int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int stag
 }
 
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
-                        int grid, cudaStream_t s)
+                        int grid, cudaStream_t s, int spare)
 {
     StepKernel k = pick(kind, limiter, tx, ty, nt, staging, a.ring != nullptr, a.tape != nullptr, a.interp != nullptr);
     if (!k.fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare(k);
     if (e != cudaSuccess) return e;
-    k.fn<<<grid, k.nt, a.tcum ? k.smem_walk : k.smem, s>>>(a);
+    long long items = 0;   // (ghost cell, component) pairs of the fill jobs
+    for (int j = 0; j < a.nfill; ++j) items += 3LL * a.fills[j].n;
+    if (items > 0 && kind != KIND_SWE) {
+        // one pair per thread where the spare CTA slots allow, else the slots stride over them
+        StepArgs b = a;
+        b.step_grid = grid;
+        const int extra = (int)std::min<long long>((items + k.nt - 1) / k.nt, std::max(spare, 1));
+        k.fn<<<grid + extra, k.nt, a.tcum ? k.smem_walk : k.smem, s>>>(b);
+    } else {
+        k.fn<<<grid, k.nt, a.tcum ? k.smem_walk : k.smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -321,6 +321,29 @@ __device__ __forceinline__ void finish_cta(const StepArgs& A)
     *reinterpret_cast<volatile unsigned*>(A.done) = 0u;
 }
 
+// The fill jobs of a launch, run by its CTAs from A.step_grid on: one thread per (ghost cell,
+// component), striding over the jobs' cells together, each value as the ghost-fill kernel
+// computes it.  The cells written are ghosts that no tile of the launch reads or writes.
+template <int NT>
+__device__ __forceinline__ void fill_jobs(const StepArgs& A)
+{
+    const long long n0 = 3LL * A.fills[0].n;
+    const long long n = n0 + (A.nfill > 1 ? 3LL * A.fills[1].n : 0LL);
+    const long long stride = (long long)(gridDim.x - A.step_grid) * NT;
+    for (long long k = (long long)(blockIdx.x - A.step_grid) * NT + threadIdx.x; k < n; k += stride) {
+        const bool second = k >= n0;
+        const InterpCell* cells = second ? A.fills[1].cells : A.fills[0].cells;
+        double* q = second ? A.fills[1].q : A.fills[0].q;
+        const double* cold = second ? A.fills[1].cold : A.fills[0].cold;
+        const double* cnew = second ? A.fills[1].cnew : A.fills[0].cnew;
+        const double tau = second ? A.fills[1].tau : A.fills[0].tau;
+        const long long kk = second ? k - n0 : k;
+        const int c = (int)(kk / 3), m = (int)(kk - 3LL * c);
+        const InterpCell C = cells[c];
+        q[C.dst + m * C.dplane] = interp_value(C, m, cold, cnew, tau);
+    }
+}
+
 // Same-level and physical-boundary ghosts of a staged tile, taken from their source cells in
 // q_old (the box's ghost ring table) instead of the pool's own ghost cells: only the frame of
 // width two around the tile can hold ghosts of its box.  Ghosts interpolated from the coarser
@@ -397,6 +420,13 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : (NT == 128 && !REC ? 5 : 
     using G = Geo<TX, TY>;
     constexpr int NBUF = STAGE == 1 ? 2 : 1;
     constexpr int NPER = (TX * TY + NT - 1) / NT;
+    if (A.step_grid && blockIdx.x >= A.step_grid) {   // a fill CTA: no tiles, no shared memory
+        fill_jobs<NT>(A);
+        if (threadIdx.x == 0) finish_cta(A);
+        return;
+    }
+    // the CTAs that step tiles
+    const int nstep = A.step_grid ? A.step_grid : (int)gridDim.x;
     extern __shared__ __align__(128) double smem[];
     double* qbuf = smem;                            // NBUF x QSTRIDE
     double* A1x = smem + NBUF * G::QSTRIDE;         // x-edge wave strengths, family 1 / 2
@@ -433,8 +463,8 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : (NT == 128 && !REC ? 5 : 
             fence_barrier_init();
         }
         if (A.tcum) {
-            s_range[0] = walk_start(A.tcum, A.ntiles, blockIdx.x, gridDim.x);
-            s_range[1] = walk_start(A.tcum, A.ntiles, blockIdx.x + 1, gridDim.x);
+            s_range[0] = walk_start(A.tcum, A.ntiles, blockIdx.x, nstep);
+            s_range[1] = walk_start(A.tcum, A.ntiles, blockIdx.x + 1, nstep);
         } else {
             s_range[0] = blockIdx.x;
             s_range[1] = A.ntiles;
@@ -450,7 +480,7 @@ __global__ void __launch_bounds__(NT, STAGE == 2 ? 3 : (NT == 128 && !REC ? 5 : 
     // Only the uniform medium walks (the host builds column walks for no other kind), so the
     // cell-wise kernels carry none of this code.
     const int t_begin = s_range[0], t_end = s_range[1];
-    const int t_step = A.tcum ? 1 : (int)gridDim.x;
+    const int t_step = A.tcum ? 1 : nstep;
     const bool walk = MED == 0 && A.tcum != nullptr;
 
     const CUtensorMap* tmaps = reinterpret_cast<const CUtensorMap*>(A.tmaps);

@@ -153,6 +153,10 @@ class Hierarchy:
         # per pulling level: the step evaluates the interpolated ghosts too (one launch) instead of
         # the interpolation launch filling them first (the autotuner decides)
         self.fuse_interp = [False] * self.nlev
+        # levels whose interpolated ghosts are filled by the launch before their substep (spare CTAs
+        # of the previous substep's step, or of the coarser level's step for the first one)
+        # instead of by a launch of their own
+        self.fill_ahead = True
         # a list while sections of eager coarse steps are timed: (name, start event, end event)
         self.sections = None
 
@@ -287,25 +291,48 @@ class Hierarchy:
             self.sections = []
         return out
 
-    def advance(self, L, cold=None, cnew=None, tau=0.0, stream=None):
+    def _plain_pull(self, L):
+        """level L's substeps pull their same-level and boundary ghosts and read the interpolated
+        ones from their pool (filled by a launch before)"""
+        return self.pull and self.pull_levels[L] and not self.reflux and not self.patchwise and not self.fuse_interp[L]
+
+    def advance(self, L, cold=None, cnew=None, tau=0.0, stream=None, filled=False, tau_next=None):
+        """One substep of level L (at time fraction tau of the coarser level's step, whose states
+        are cold, cnew) followed by the finer levels' substeps.  filled: the interpolated ghosts of
+        this substep are in its pool already; tau_next: the time fraction of level L's next substep
+        in the same coarser step (None after the last).  Returns whether the launch also filled
+        the next substep's interpolated ghosts."""
         q = self.q[L][self.cur[L]]
+        dst = self.q[L][1 - self.cur[L]]
+        filled_next = False
+        child_filled = False
         if self.pull and self.pull_levels[L] and not self.reflux and not self.patchwise and self.fuse_interp[L]:
             # one launch: the step pulls the same-level and boundary ghosts from their sources and
             # evaluates the ones interpolated from the coarser level itself
             e = self._section("advance", stream)
-            claw.claw_level_advance_interp(self.ctx, L, q, self.q[L][1 - self.cur[L]], self.aux[L], self.dt,
+            claw.claw_level_advance_interp(self.ctx, L, q, dst, self.aux[L], self.dt,
                                            self.smax, claw.CLAW_ADVANCE_PULL_GHOSTS, cold, cnew, tau, stream)
             if e is not None:
                 e.record()
-        elif self.pull and self.pull_levels[L] and not self.reflux and not self.patchwise:
-            # only the interpolated ghosts are filled; the step pulls the others from their sources
-            e = self._section("fill", stream)
-            claw.claw_fill_ghost_interp(self.ctx, L, q, cold, cnew, tau, stream)
-            if e is not None:
-                e.record()
+        elif self._plain_pull(L):
+            # only the interpolated ghosts are filled (by the launch before when filling ahead);
+            # the step pulls the others from their sources
+            if not (filled and self.fill_ahead):
+                e = self._section("fill", stream)
+                claw.claw_fill_ghost_interp(self.ctx, L, q, cold, cnew, tau, stream)
+                if e is not None:
+                    e.record()
+            jobs = []
+            if self.fill_ahead:
+                if L > 0 and tau_next is not None:   # this level's next substep, into dst
+                    jobs.append((L, dst, cold, cnew, tau_next))
+                    filled_next = True
+                if L + 1 < self.nlev and self._plain_pull(L + 1):   # the finer level's first substep
+                    jobs.append((L + 1, self.q[L + 1][self.cur[L + 1]], q, q, 0.0))
+                    child_filled = True
             e = self._section("advance", stream)
-            claw.claw_level_advance(self.ctx, L, q, self.q[L][1 - self.cur[L]], self.aux[L], self.dt, self.smax,
-                                    claw.CLAW_ADVANCE_PULL_GHOSTS, stream)
+            claw.claw_level_advance_fill(self.ctx, L, q, dst, self.aux[L], self.dt, self.smax,
+                                         claw.CLAW_ADVANCE_PULL_GHOSTS, jobs, stream)
             if e is not None:
                 e.record()
         else:
@@ -324,8 +351,10 @@ class Hierarchy:
         old, new = self.q[L][self.cur[L]], self.q[L][1 - self.cur[L]]
         if L + 1 < self.nlev:
             r = self.ratio(L + 1)
+            filled = child_filled
             for k in range(r):
-                self.advance(L + 1, old, new, k / r, stream)
+                filled = self.advance(L + 1, old, new, k / r, stream, filled=filled,
+                                      tau_next=(k + 1) / r if k + 1 < r else None)
             e = self._section("update", stream)
             claw.claw_average_down(self.ctx, L + 1, self.q[L + 1][self.cur[L + 1]], new, stream)
             if self.reflux:
@@ -333,6 +362,7 @@ class Hierarchy:
             if e is not None:
                 e.record()
         self.cur[L] ^= 1
+        return filled_next
 
     def coarse_step(self, stream=None):
         if self.fused and self.nlev == 1 and not self.patchwise and not self.freeze_dt:

@@ -110,10 +110,11 @@ def tune_level(H, L, use_cache=True, candidates=None, pull=False):
 def choose_pull(H, L, reps=5):
     """how level L of H gets its ghosts, timed with the installed tiling, the fastest recorded in
     H.pull_levels[L] and H.fuse_interp[L]: every ghost filled by the copy and interpolation
-    launches before the step ("fill"), the interpolated ghosts filled and the others pulled by the
-    step ("pull"), or one launch that pulls the copied ghosts and evaluates the interpolated ones
-    ("pull+interp").  Small boxes put many ghosts in every tile's frame, where the separate
-    launches can win."""
+    launches before the step ("fill"), the interpolated ghosts filled (by spare CTAs of the launch
+    before when H.fill_ahead, timed as a step launch carrying one such fill) and the others pulled
+    by the step ("pull"), or one launch that pulls the copied ghosts and evaluates the
+    interpolated ones ("pull+interp").  Small boxes put many ghosts in every tile's frame, where
+    the separate launches can win."""
     src = H.q[L][H.cur[L]]
     dst = torch.empty_like(src)
     smax = torch.zeros_like(H.smax)
@@ -127,6 +128,9 @@ def choose_pull(H, L, reps=5):
         claw.claw_level_step(H.ctx, L, src, dst, H.aux[L], H.dt, smax)
 
     def pull_step():
+        if H.fill_ahead and L:   # the fill rides on the step launch before: one launch with its job
+            claw.claw_level_advance_fill(H.ctx, L, src, dst, H.aux[L], H.dt, smax, flags, [(L, dst, qc, qc, 0.0)])
+            return
         claw.claw_fill_ghost_interp(H.ctx, L, src, qc, qc, 0.0)
         claw.claw_level_advance(H.ctx, L, src, dst, H.aux[L], H.dt, smax, flags)
 

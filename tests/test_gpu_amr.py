@@ -32,11 +32,12 @@ def _compare_all_levels(H, O, run_index, tol):
     return worst
 
 
-@pytest.mark.parametrize("ghosts", ["pull", "pull+interp", "fill"])
+@pytest.mark.parametrize("ghosts", ["pull", "pull, own fill launches", "pull+interp", "fill"])
 def test_three_level_hierarchy_one_and_twenty_coarse_steps(ghosts):
     # 64^2 base, ratio 4 twice, seeded patches of 8..64 cells on the annuli (the uneven AMR
     # workload); uniform medium rho = 1, K = 4; each way the fine levels can get their ghosts
-    # (interpolated ones filled first, evaluated inside the one-launch step, or all filled)
+    # (interpolated ones filled by the launch before, or by a launch of their own, evaluated
+    # inside the one-launch step, or all filled)
     from oracle.amr import OracleHierarchy
     from paper_1808_02638_gb300.solver import Hierarchy
     run = inputs.config2()
@@ -44,6 +45,7 @@ def test_three_level_hierarchy_one_and_twenty_coarse_steps(ghosts):
     H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
     H.fuse_interp = [ghosts == "pull+interp"] * H.nlev
     H.pull_levels = [ghosts != "fill"] * H.nlev
+    H.fill_ahead = ghosts != "pull, own fill launches"
     O = OracleHierarchy(run, q0, [inputs.const_pool(l, 1.0) for l in run.levels],
                         [inputs.const_pool(l, 4.0) for l in run.levels])
     H.init_dt()
@@ -56,6 +58,78 @@ def test_three_level_hierarchy_one_and_twenty_coarse_steps(ghosts):
         O.coarse_step()
     _compare_all_levels(H, O, 0, TOLN)
     assert H.sync_status() == 0
+
+
+@pytest.mark.parametrize("medium", ["uniform", "cellwise"])
+def test_fill_ahead_equals_own_fill_launches_with_fewer_launches(medium):
+    # the interpolated ghosts of every fine substep written by spare CTAs of the launch before
+    # (the previous substep's step, or the coarser level's step for the first substep at tau 0)
+    # give the same pools, ghost cells included, as their own fill launches, bit for bit
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    if medium == "uniform":
+        kw = dict(rho0=1.0, K0=4.0)
+        args = ([run], [q0])
+    else:   # a smooth random medium (the heterogeneous workload's kind), injected per level
+        r0 = inputs.smooth_field(11, 64, 64, 0.5, 2.0)
+        k0 = inputs.smooth_field(12, 64, 64, 1.0, 6.0)
+        rhos = [inputs.coef_pool(lev, r0, 4 ** L) for L, lev in enumerate(run.levels)]
+        Ks = [inputs.coef_pool(lev, k0, 4 ** L) for L, lev in enumerate(run.levels)]
+        kw = {}
+        args = ([run], [q0], [rhos], [Ks])
+    Hs = []
+    for ahead in (True, False):
+        H = Hierarchy(*args, **kw)
+        H.fill_ahead = ahead
+        H.init_dt()
+        n0 = claw.claw_launch_count(H.ctx)
+        for _ in range(3):
+            H.coarse_step()
+        torch.cuda.synchronize()
+        Hs.append((H, (claw.claw_launch_count(H.ctx) - n0) / 3))
+    (A, la), (B, lb) = Hs
+    for L in range(A.nlev):
+        assert A.cur[L] == B.cur[L]
+        for c in range(2):
+            assert torch.equal(A.q[L][c], B.q[L][c]), (L, c)
+    assert torch.equal(A.dt, B.dt)
+    # 3 levels of ratio 4: 1 + 4 + 16 level-steps, 4 + 16 interpolation fills, 4 + 1 averages, 1 dt
+    assert lb == 47 and la == 27, (la, lb)
+    assert A.sync_status() == 0 and B.sync_status() == 0
+    A.close()
+    B.close()
+
+
+def test_advance_fill_rejects_jobs_it_cannot_run():
+    from paper_1808_02638_gb300 import claw
+    from paper_1808_02638_gb300.solver import Hierarchy
+    run = inputs.config2()
+    q0 = [inputs.init_q(run, lev) for lev in run.levels]
+    H = Hierarchy([run], [q0], rho0=1.0, K0=4.0)
+    H.init_dt()
+    P = claw.CLAW_ADVANCE_PULL_GHOSTS
+    q1, d1 = H.q[1][0], H.q[1][1]
+    q0a, q0b = H.q[0][0], H.q[0][1]
+    q2 = H.q[2][0]
+    bad = [
+        [(1, d1, q0a, q0b, 0.25)] * 3,              # more than two jobs
+        [(1, q1, q0a, q0b, 0.25)],                  # writes the step's q_old
+        [(1, d1, q0a, q0b, 1.5)],                   # tau outside [0, 1]
+        [(2, q2, d1, d1, 0.0)],                     # reads the step's q_new as a coarse state
+        [(3, q2, q1, q1, 0.0)],                     # not this level nor the next finer one
+        [(0, q0a, q1, q1, 0.0)],                    # level 0 has no coarser level
+    ]
+    for jobs in bad:
+        with pytest.raises(claw.ClawError) as e:
+            claw.claw_level_advance_fill(H.ctx, 1, q1, d1, H.aux[1], H.dt, H.smax, P, jobs)
+        assert e.value.status == claw.CLAW_EINVAL, jobs
+    claw.claw_level_advance_fill(H.ctx, 1, q1, d1, H.aux[1], H.dt, H.smax, P,
+                                 [(1, d1, q0a, q0b, 0.25), (2, q2, q1, q1, 0.0)])
+    torch.cuda.synchronize()
+    assert H.sync_status() == 0
+    H.close()
 
 
 def test_fine_level_ghosts_match_oracle_fill():
