@@ -579,8 +579,10 @@ static int level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* 
         F.tau = jobs[j].tau;
     }
     ctx->launches += 1;
+    // fill CTAs: the slots the tiles leave free, at least one per SM (those run as the step's
+    // CTAs retire)
     cudaError_t e = launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s,
-                                per_sm * ctx->nsm - grid);
+                                std::max(per_sm * ctx->nsm - grid, ctx->nsm));
     if (ctx->kind() == KIND_SWE)   // no fill CTAs in the shallow-water kernel: a launch per job
         for (int j = 0; j < a.nfill && e == cudaSuccess; ++j) {
             e = launch_fill_interp(a.fills[j].cells, a.fills[j].n, a.fills[j].q, a.fills[j].cold, a.fills[j].cnew,

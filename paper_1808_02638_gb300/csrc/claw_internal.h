@@ -277,6 +277,7 @@ enum : int { KIND_UNIFORM = 0, KIND_CELLWISE = 1, KIND_SWE = 2 };
 
 // launchers (claw_step.cu; kind: KIND_*)
 // a.nfill > 0 (not shallow water): the launch adds up to max(spare, 1) CTAs for the fill jobs
+// (CTAs from index grid on)
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s, int spare = 0);
 int step_max_ctas_per_sm(int kind, int limiter, int tx, int ty, int nt, int staging, bool pull = false,

@@ -74,7 +74,7 @@ cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty
     long long items = 0;   // (ghost cell, component) pairs of the fill jobs
     for (int j = 0; j < a.nfill; ++j) items += 3LL * a.fills[j].n;
     if (items > 0 && kind != KIND_SWE) {
-        // one pair per thread where the spare CTA slots allow, else the slots stride over them
+        // one pair per thread where `spare` CTAs allow, else those CTAs stride over them
         StepArgs b = a;
         b.step_grid = grid;
         const int extra = (int)std::min<long long>((items + k.nt - 1) / k.nt, std::max(spare, 1));
