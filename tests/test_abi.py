@@ -37,7 +37,7 @@ def test_library_loads_and_binding_covers_the_header():
 def test_binding_structs_match_header_layout(tmp_path):
     # the C compiler's offsets of every field of the header's structs equal the binding's
     from paper_1808_02638_gb300 import claw
-    structs = {"claw_problem": claw.claw_problem, "claw_box": claw.claw_box}
+    structs = {"claw_problem": claw.claw_problem, "claw_box": claw.claw_box, "claw_fill_job": claw.claw_fill_job}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "claw.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
