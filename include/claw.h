@@ -281,7 +281,6 @@ typedef struct {
  * (its next substep, into q_new's ghost cells, which the step does not write) or the next finer
  * one (its first substep: tau 0, from this level's q_old as both coarse states).  The result is
  * that of claw_level_advance followed by claw_fill_ghost_interp for each job, on the same stream.
- * Shallow water (no fill CTAs in its kernel) launches the fills after the step instead.
  * Errors as claw_level_advance; CLAW_EINVAL for more than 2 jobs, a job of another level, a
  * level not set, NULL pools, tau outside [0, 1], a job writing q_old, or a job reading q_new
  * as a coarse state. */

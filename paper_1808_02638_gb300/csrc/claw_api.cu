@@ -583,12 +583,6 @@ static int level_advance(claw_ctx* ctx, int32_t L, const double* q_old, double* 
     // CTAs retire)
     cudaError_t e = launch_step(a, ctx->kind(), ctx->limiter, d.tx, d.ty, d.nt, staging, grid, s,
                                 std::max(per_sm * ctx->nsm - grid, ctx->nsm));
-    if (ctx->kind() == KIND_SWE)   // no fill CTAs in the shallow-water kernel: a launch per job
-        for (int j = 0; j < a.nfill && e == cudaSuccess; ++j) {
-            e = launch_fill_interp(a.fills[j].cells, a.fills[j].n, a.fills[j].q, a.fills[j].cold, a.fills[j].cnew,
-                                   a.fills[j].tau, s);
-            ctx->launches += 1;
-        }
     if (e == cudaSuccess && (flags & CLAW_ADVANCE_PUSH_GHOSTS) && d.ncopy) {
         e = launch_fill_copy(d.copies, d.copy_start, d.ncopy_blocks, q_new, s);
         ctx->launches += 1;

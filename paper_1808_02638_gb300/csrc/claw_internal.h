@@ -276,7 +276,7 @@ enum : int { ERR_NAN = 1, ERR_CFL = 2, ERR_TIMEOUT = 4 };
 enum : int { KIND_UNIFORM = 0, KIND_CELLWISE = 1, KIND_SWE = 2 };
 
 // launchers (claw_step.cu; kind: KIND_*)
-// a.nfill > 0 (not shallow water): the launch adds up to max(spare, 1) CTAs for the fill jobs
+// a.nfill > 0: the launch adds up to max(spare, 1) CTAs for the fill jobs
 // (CTAs from index grid on)
 cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty, int nt, int staging,
                         int grid, cudaStream_t s, int spare = 0);

@@ -73,7 +73,7 @@ cudaError_t launch_step(const StepArgs& a, int kind, int limiter, int tx, int ty
     if (e != cudaSuccess) return e;
     long long items = 0;   // (ghost cell, component) pairs of the fill jobs
     for (int j = 0; j < a.nfill; ++j) items += 3LL * a.fills[j].n;
-    if (items > 0 && kind != KIND_SWE) {
+    if (items > 0) {
         // one pair per thread where `spare` CTAs allow, else those CTAs stride over them
         StepArgs b = a;
         b.step_grid = grid;

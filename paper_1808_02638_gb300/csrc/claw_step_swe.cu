@@ -109,6 +109,12 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
     using S = SweGeo<TX, TY>;
     constexpr int NBUF = STAGE ? 2 : 1;
     constexpr int NPER = (TX * TY + NT - 1) / NT;
+    if (A.step_grid && blockIdx.x >= A.step_grid) {   // a fill CTA (as in the acoustics kernel)
+        fill_jobs<NT>(A);
+        if (threadIdx.x == 0) finish_cta(A);
+        return;
+    }
+    const int nstep = A.step_grid ? A.step_grid : (int)gridDim.x;   // the CTAs that step tiles
     extern __shared__ __align__(128) double smem[];
     double* qbuf = smem;
     double* der = smem + NBUF * G::QSTRIDE;   // sqrt(h), hu/sqrt(h), hv/sqrt(h)
@@ -136,8 +142,8 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
             fence_barrier_init();
         }
         if (A.tcum) {
-            s_range[0] = walk_start(A.tcum, A.ntiles, blockIdx.x, gridDim.x);
-            s_range[1] = walk_start(A.tcum, A.ntiles, blockIdx.x + 1, gridDim.x);
+            s_range[0] = walk_start(A.tcum, A.ntiles, blockIdx.x, nstep);
+            s_range[1] = walk_start(A.tcum, A.ntiles, blockIdx.x + 1, nstep);
         } else {
             s_range[0] = blockIdx.x;
             s_range[1] = A.ntiles;
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(NT, 1) swe_step_kernel(const StepArgs A)
     // column walks as in the acoustics kernel: a contiguous stretch of tiles per CTA, the rows a
     // tile shares with the tile below it taken from that tile (through Cy) instead of recomputed
     const int t_begin = s_range[0], t_end = s_range[1];
-    const int t_step = A.tcum ? 1 : (int)gridDim.x;
+    const int t_step = A.tcum ? 1 : nstep;
     const bool walk = A.tcum != nullptr;
 
     const CUtensorMap* tmaps = reinterpret_cast<const CUtensorMap*>(A.tmaps);

@@ -60,7 +60,7 @@ def test_three_level_hierarchy_one_and_twenty_coarse_steps(ghosts):
     assert H.sync_status() == 0
 
 
-@pytest.mark.parametrize("medium", ["uniform", "cellwise"])
+@pytest.mark.parametrize("medium", ["uniform", "cellwise", "shallow_water"])
 def test_fill_ahead_equals_own_fill_launches_with_fewer_launches(medium):
     # the interpolated ghosts of every fine substep written by spare CTAs of the launch before
     # (the previous substep's step, or the coarser level's step for the first substep at tau 0)
@@ -72,6 +72,9 @@ def test_fill_ahead_equals_own_fill_launches_with_fewer_launches(medium):
     if medium == "uniform":
         kw = dict(rho0=1.0, K0=4.0)
         args = ([run], [q0])
+    elif medium == "shallow_water":   # the second system: a flowing ring as depth
+        kw = dict(system="shallow_water", grav=1.0)
+        args = ([run], [[inputs.init_swe(run, lev, u0=0.2, v0=0.1) for lev in run.levels]])
     else:   # a smooth random medium (the heterogeneous workload's kind), injected per level
         r0 = inputs.smooth_field(11, 64, 64, 0.5, 2.0)
         k0 = inputs.smooth_field(12, 64, 64, 1.0, 6.0)
